@@ -1,0 +1,168 @@
+/*
+ * etale.h — C ABI of the GB300 (sm_103a) ETALE index: a dynamic graph
+ * approximate-nearest-neighbour index kept resident in GPU memory and
+ * maintained in batches (insert, delete with repair, reclaim, search).
+ *
+ * Paper: "ETALE: Evolving Topology with Accelerated Lock-free Execution for
+ * Dynamic Graph ANN Search on GPUs", arXiv 2607.02543.
+ *
+ * Conventions for every call
+ *  - Returns an etale_status; nothing throws across this boundary.  On a
+ *    non-OK status, etale_last_error() gives a one-line reason.
+ *  - Pointer arguments may be device pointers or host pointers (pageable or
+ *    pinned); the library detects which.  Host inputs are copied to device
+ *    staging inside the call; host outputs are written before the call
+ *    returns.  The caller owns every buffer it passes in.
+ *  - The library owns the index memory (vectors, reference words, slab pool,
+ *    free and retired stacks, scratch), allocated once by etale_create for
+ *    the whole id capacity.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Every call synchronises `stream` before it returns.
+ *  - Ids are uint32, assigned fresh and ascending by etale_insert, never
+ *    reused (reusing one would clear a deletion flag, Proposition 1), so
+ *    `capacity` is a lifetime insert budget.  0xFFFFFFFF is "no id".
+ *  - Distances are squared L2 (ETALE_L2) or 1 - <x, y> (ETALE_IP), fp32,
+ *    computed in one fixed operation order (see the design notes).
+ *  - An index is not thread-safe: calls on one index must not overlap.
+ */
+#ifndef ETALE_H
+#define ETALE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ETALE_NIL 0xFFFFFFFFu
+
+typedef struct etale_index etale_index; /* opaque, library-owned */
+
+typedef enum { ETALE_L2 = 0, ETALE_IP = 1 } etale_metric;
+
+typedef enum {
+    ETALE_OK = 0,
+    ETALE_EINVAL = 1,     /* bad argument; the index is unchanged             */
+    ETALE_ENOMEM = 2,     /* device allocation failed or slab pool exhausted  */
+    ETALE_ECAPACITY = 3,  /* the id budget would be exceeded; unchanged        */
+    ETALE_ECUDA = 4,      /* a CUDA runtime error; the index may be unusable   */
+    ETALE_ETIMEOUT = 5,   /* a bounded device wait gave up                     */
+    ETALE_EINTERNAL = 6   /* a device-side consistency check failed            */
+} etale_status;
+
+typedef enum { ETALE_MODE_DETERMINISTIC = 0, ETALE_MODE_LOCKFREE = 1 } etale_mode;
+
+/* Build-time and maintenance knobs.  Zero selects the default.             */
+typedef struct {
+    uint32_t build_beam;  /* EF_BUILD (Sec. 5.6); default 64                  */
+    float alpha;          /* RobustPrune slack (Sec. 3.4.1); default 1.2      */
+    uint32_t max_hops;    /* expansion cap of one BeamSearch; default 4*beam  */
+    uint32_t max_cand;    /* RobustPrune candidates kept; default 2*build_beam */
+    uint32_t refine;      /* refine pass (Sec. 3.4.1): 0 default (= 2),
+                             1 off, 2 batch peers found within two hops       */
+    uint64_t max_batch;   /* insert sub-batch cap; default capacity/100       */
+    uint64_t pool_slabs;  /* slab pool size P; default 2*capacity + 4*(R+1)*max_batch */
+    uint32_t n_entry;     /* entry-set size |E|; default 1024                 */
+    uint32_t mode;        /* etale_mode; default deterministic                */
+    uint32_t cas_budget;  /* lock-free publish attempts (Alg. 1); default 16  */
+    uint32_t reserved[6];
+} etale_config;
+
+typedef struct {
+    uint64_t live;            /* delta = 0 with a slab                        */
+    uint64_t tombstones;      /* delta = 1 with a slab (relays)               */
+    uint64_t reclaimed;       /* delta = 1, slab freed                        */
+    uint64_t next_id;         /* ids handed out so far                        */
+    uint64_t capacity;        /* C                                            */
+    uint64_t pool_slabs;      /* P                                            */
+    uint64_t free_slabs;      /* on the free stack                            */
+    uint64_t retired_slabs;   /* on the retired stack (0 between calls)       */
+    uint64_t used_slabs;      /* P - free - retired                           */
+    uint32_t n_entries;       /* |E| currently                                */
+    uint32_t degree;          /* R                                            */
+    uint64_t n_publish;       /* successful publications (Algorithm 1)        */
+    uint64_t n_cas_retry;     /* failed CAS attempts                          */
+    uint64_t n_dropped;       /* offers dropped after the attempt budget      */
+    uint64_t n_expand;        /* BeamSearch expansions                        */
+    uint64_t n_dist;          /* distance evaluations in BeamSearch           */
+    uint64_t device_bytes;    /* index memory held on the device              */
+} etale_stats_t;
+
+/* Fill *cfg with the defaults (all fields resolved except those that depend
+ * on capacity, which stay 0 until etale_create).                           */
+etale_status etale_config_default(etale_config *cfg);
+
+/* Create an empty index (Definition 1: identifier space C = capacity, slab
+ * capacity R = degree, vector dimension m = dim).  degree must be 1..64;
+ * dim >= 1; capacity < 2^32 - 1.  cfg may be NULL.  *out receives the
+ * handle; on error *out is NULL and nothing is allocated.                   */
+etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree,
+                          uint64_t capacity, const etale_config *cfg, etale_index **out);
+
+/* Free every device and host resource of the index.  NULL is a no-op.       */
+etale_status etale_destroy(etale_index *idx);
+
+/* Insert n vectors (row-major n x dim fp32) as fresh nodes (Algorithm 2 with
+ * a refine pass).  out_ids (may be NULL) receives the n ids, ascending from
+ * the current next_id.  The batch is cut into sub-batches of
+ * min(remaining, max(1, live), max_batch); each sub-batch is one round:
+ * all members search the graph as it was before the sub-batch, prune, publish
+ * their own slabs, then offer reverse edges.  ECAPACITY if next_id + n
+ * exceeds capacity (index unchanged).                                      */
+etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n,
+                          uint32_t *out_ids, void *stream);
+
+/* Delete ids (Algorithm 3): tombstone each live id, then repair every live
+ * out-neighbour of the deleted nodes.  Ids never inserted, already deleted
+ * or repeated are no-ops.  *n_deleted (may be NULL) receives the number of
+ * ids tombstoned by this call.                                              */
+etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n,
+                          uint64_t *n_deleted, void *stream);
+
+/* Reclaim (Algorithm 4): recompute the entry set from the live nodes,
+ * republish every live node that points at a tombstone without those
+ * entries (compaction), then free every tombstone's slab.  Afterwards the
+ * resident slab count equals the live count (Proposition 3).               */
+etale_status etale_reclaim(etale_index *idx, void *stream);
+
+/* Batched k-NN query (BeamSearch with beam max(beam, k)).  queries: nq x dim
+ * fp32.  out_ids / out_dists: nq x k, nearest first; a search that finds
+ * fewer than k live nodes pads with ETALE_NIL and +inf.  Only nodes whose
+ * reference word read during the search has delta = 0 are returned
+ * (Proposition 1).                                                         */
+etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
+                          uint32_t beam, uint32_t *out_ids, float *out_dists, void *stream);
+
+/* Exact k nearest live nodes by brute force (measurement support for
+ * Recall@10, Sec. 5.2): canonical fp32 distances, ties by smaller id.       */
+etale_status etale_ground_truth(etale_index *idx, const float *queries, uint64_t nq,
+                                uint32_t k, uint32_t *out_ids, float *out_dists, void *stream);
+
+/* Copy the logical graph of ids [0, n) to HOST buffers: deleted[n],
+ * has_slab[n], degree[n] (uint8), nbr_ids[n*R] and nbr_rho[n*R] (entries
+ * beyond the degree are ETALE_NIL / 0).  n must be <= next_id.             */
+etale_status etale_export_graph(etale_index *idx, uint64_t n, uint8_t *deleted,
+                                uint8_t *has_slab, uint8_t *degree, uint32_t *nbr_ids,
+                                float *nbr_rho, void *stream);
+
+/* Copy the current entry set to a HOST buffer of capacity n_entry; *n
+ * receives its size.                                                       */
+etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n);
+
+etale_status etale_stats(etale_index *idx, etale_stats_t *out);
+
+/* Resolved configuration of an index.                                      */
+etale_status etale_get_config(const etale_index *idx, etale_config *out);
+
+/* One-line description of the last error on this index (or of the last
+ * failed etale_create when idx is NULL).  Never NULL.                      */
+const char *etale_last_error(const etale_index *idx);
+
+/* Kernel launches issued by this index so far (for launch accounting).     */
+uint64_t etale_kernel_launches(const etale_index *idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ETALE_H */

@@ -1,0 +1,226 @@
+"""Thin ctypes binding of include/etale.h (argument marshalling only).
+
+Every step of the index runs in libetale.so on the GPU.  There is no CPU
+fallback: loading fails loudly when the library has not been built or no CUDA
+device is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libetale.so")
+NIL = 0xFFFFFFFF
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECAPACITY", 4: "ECUDA", 5: "ETIMEOUT", 6: "EINTERNAL"}
+MODES = {"deterministic": 0, "lockfree": 1}
+REFINE = {"default": 0, "off": 1, "peers": 2}
+
+
+class EtaleError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("build_beam", C.c_uint32), ("alpha", C.c_float), ("max_hops", C.c_uint32),
+                ("max_cand", C.c_uint32), ("refine", C.c_uint32), ("max_batch", C.c_uint64),
+                ("pool_slabs", C.c_uint64), ("n_entry", C.c_uint32), ("mode", C.c_uint32),
+                ("cas_budget", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("live", C.c_uint64), ("tombstones", C.c_uint64), ("reclaimed", C.c_uint64),
+                ("next_id", C.c_uint64), ("capacity", C.c_uint64), ("pool_slabs", C.c_uint64),
+                ("free_slabs", C.c_uint64), ("retired_slabs", C.c_uint64), ("used_slabs", C.c_uint64),
+                ("n_entries", C.c_uint32), ("degree", C.c_uint32), ("n_publish", C.c_uint64),
+                ("n_cas_retry", C.c_uint64), ("n_dropped", C.c_uint64), ("n_expand", C.c_uint64),
+                ("n_dist", C.c_uint64), ("device_bytes", C.c_uint64)]
+
+
+EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_insert", "etale_delete",
+           "etale_reclaim", "etale_search", "etale_ground_truth", "etale_export_graph",
+           "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
+           "etale_kernel_launches"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libetale.so and declare every entry point.  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2607_02543_gb300.build.build()")
+        lib = C.CDLL(path)
+        P, U32, U64 = C.c_void_p, C.c_uint32, C.c_uint64
+        sig = {
+            "etale_config_default": ([C.POINTER(Config)], C.c_int),
+            "etale_create": ([U32, C.c_int, U32, U64, C.POINTER(Config), C.POINTER(P)], C.c_int),
+            "etale_destroy": ([P], C.c_int),
+            "etale_insert": ([P, P, U64, P, P], C.c_int),
+            "etale_delete": ([P, P, U64, C.POINTER(U64), P], C.c_int),
+            "etale_reclaim": ([P, P], C.c_int),
+            "etale_search": ([P, P, U64, U32, U32, P, P, P], C.c_int),
+            "etale_ground_truth": ([P, P, U64, U32, P, P, P], C.c_int),
+            "etale_export_graph": ([P, U64, P, P, P, P, P, P], C.c_int),
+            "etale_get_entries": ([P, P, C.POINTER(U32)], C.c_int),
+            "etale_stats": ([P, C.POINTER(Stats)], C.c_int),
+            "etale_get_config": ([P, C.POINTER(Config)], C.c_int),
+            "etale_last_error": ([P], C.c_char_p),
+            "etale_kernel_launches": ([P], U64),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes, f.restype = args, res
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    """Device or host address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Index:
+    """One ETALE index on the current CUDA device (see include/etale.h)."""
+
+    def __init__(self, dim: int, metric: str, degree: int, capacity: int, *, build_beam: int = 0,
+                 alpha: float = 0.0, max_hops: int = 0, max_cand: int = 0, refine: str = "default",
+                 max_batch: int = 0, pool_slabs: int = 0, n_entry: int = 0, mode: str = "deterministic",
+                 cas_budget: int = 0):
+        self.lib = load()
+        cfg = Config()
+        self.lib.etale_config_default(C.byref(cfg))
+        if build_beam:
+            cfg.build_beam = build_beam
+        if alpha:
+            cfg.alpha = alpha
+        cfg.max_hops, cfg.max_cand = max_hops, max_cand
+        cfg.refine = REFINE[refine]
+        cfg.max_batch, cfg.pool_slabs = max_batch, pool_slabs
+        if n_entry:
+            cfg.n_entry = n_entry
+        cfg.mode = MODES[mode]
+        if cas_budget:
+            cfg.cas_budget = cas_budget
+        h = C.c_void_p()
+        st = self.lib.etale_create(dim, 0 if metric == "l2" else 1, degree, capacity, C.byref(cfg), C.byref(h))
+        if st:
+            raise EtaleError(st, self.lib.etale_last_error(None).decode())
+        self.h = h
+        self.dim, self.degree, self.capacity, self.metric = dim, degree, capacity, metric
+
+    def _check(self, st: int):
+        if st:
+            raise EtaleError(st, self.lib.etale_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.etale_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- updates -----------------------------------------------------------
+    def insert(self, vecs, stream=None):
+        """Insert rows (torch tensor on any device, or numpy); returns the new ids."""
+        if not _is_cuda(vecs):
+            vecs = np.ascontiguousarray(vecs, dtype=np.float32)
+        n = vecs.shape[0]
+        ids = np.empty(n, np.uint32)
+        self._check(self.lib.etale_insert(self.h, _ptr(vecs), n, _ptr(ids), _stream(stream)))
+        return ids
+
+    def delete(self, ids, stream=None) -> int:
+        if not _is_cuda(ids):
+            ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        n = C.c_uint64(0)
+        self._check(self.lib.etale_delete(self.h, _ptr(ids), ids.shape[0], C.byref(n), _stream(stream)))
+        return int(n.value)
+
+    def reclaim(self, stream=None):
+        self._check(self.lib.etale_reclaim(self.h, _stream(stream)))
+
+    # --- queries -----------------------------------------------------------
+    def _outputs(self, q, k):
+        if _is_cuda(q):
+            import torch
+            return (torch.empty((q.shape[0], k), dtype=torch.int32, device=q.device),
+                    torch.empty((q.shape[0], k), dtype=torch.float32, device=q.device))
+        return np.empty((q.shape[0], k), np.uint32), np.empty((q.shape[0], k), np.float32)
+
+    def search(self, queries, k: int, beam: int, stream=None, out=None):
+        if not _is_cuda(queries):
+            queries = np.ascontiguousarray(queries, dtype=np.float32)
+        ids, dist = out if out is not None else self._outputs(queries, k)
+        self._check(self.lib.etale_search(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
+                                          _ptr(dist), _stream(stream)))
+        return ids, dist
+
+    def ground_truth(self, queries, k: int, stream=None):
+        if not _is_cuda(queries):
+            queries = np.ascontiguousarray(queries, dtype=np.float32)
+        ids, dist = self._outputs(queries, k)
+        self._check(self.lib.etale_ground_truth(self.h, _ptr(queries), queries.shape[0], k, _ptr(ids),
+                                                _ptr(dist), _stream(stream)))
+        return ids, dist
+
+    # --- introspection -----------------------------------------------------
+    def export_graph(self, n: int | None = None):
+        """(deleted, has_slab, degree, nbr_ids[n, R], nbr_rho[n, R]) over ids [0, n)."""
+        n = self.stats()["next_id"] if n is None else n
+        R = self.degree
+        de, hs, dg = (np.empty(n, np.uint8) for _ in range(3))
+        ids = np.empty((n, R), np.uint32)
+        rho = np.empty((n, R), np.float32)
+        if n:
+            self._check(self.lib.etale_export_graph(self.h, n, _ptr(de), _ptr(hs), _ptr(dg), _ptr(ids),
+                                                    _ptr(rho), None))
+        return de, hs, dg, ids, rho
+
+    def entries(self) -> np.ndarray:
+        cap = self.config()["n_entry"]
+        out = np.empty(max(cap, 1), np.uint32)
+        n = C.c_uint32(0)
+        self._check(self.lib.etale_get_entries(self.h, _ptr(out), C.byref(n)))
+        return out[:n.value].copy()
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.lib.etale_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def config(self) -> dict:
+        c = Config()
+        self._check(self.lib.etale_get_config(self.h, C.byref(c)))
+        return {f: getattr(c, f) for f, _ in Config._fields_ if f != "reserved"}
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.etale_kernel_launches(self.h))

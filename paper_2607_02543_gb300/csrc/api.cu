@@ -1,0 +1,681 @@
+// api.cu — the C ABI (include/etale.h): memory ownership, phase
+// orchestration and the host side of the epoch discipline.  Each phase is a
+// separate launch on the caller's stream and every phase that publishes is
+// followed by the recycle launch (Sec. 3.3, Lemma 1, Definition 2).
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/etale.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace etale;
+
+namespace etale {
+std::atomic<unsigned long long> g_kernel_launches{0};
+}
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+bool grow(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes) return true;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    b.bytes = want;
+    return true;
+}
+
+template <class T>
+T *as(DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+u32 bits_for(u64 v) {
+    u32 b = 1;
+    while (b < 32 && (v >> b) != 0) b++;
+    return b;
+}
+
+}  // namespace
+
+struct etale_index {
+    int device = 0, num_sms = 0;
+    etale_config cfg{};
+    u32 dim = 0, mp = 0, R = 0, metric = 0;
+    u64 capacity = 0, pool = 0;
+    float alpha2 = 0.f;
+    // index memory
+    float *x = nullptr;
+    u64 *ref = nullptr;
+    uint2 *slab = nullptr;
+    u32 *free_stack = nullptr, *retired = nullptr, *entries = nullptr;
+    u64 *ctr = nullptr;
+    u64 *host_ctr = nullptr;   // pinned mirror
+    // scratch
+    DevBuf stage, qpad, out_ids, out_dist, exp_keys, exp_count, F_id, F_rho, F_n;
+    DevBuf of_key, of_val, of_key2, of_val2, of_src, of_rho, seg_flags, seg_scan, seg_start, sort_scr, scan_scr;
+    DevBuf live_flags, live_rank, live_scan_scr, tomb_bits;
+    DevBuf del_ids, del_vals, del_ids2, del_vals2, del_ok, del_scan, dt, pair_key, pair_val, pair_key2, pair_val2,
+        pair_K, pair_Kn, pair_flags, pair_scan, pair_seg, counts;
+    DevBuf ex_del, ex_hs, ex_deg, ex_ids, ex_rho;
+    // host-side state
+    u64 next_id = 0, live = 0, tombs = 0, reclaimed = 0;
+    u32 n_entries = 0;
+    u64 free_lb = 0;
+    u64 device_bytes = 0;
+    SearchTuning tune;
+    std::string err = "no error";
+
+    Dev dev() const {
+        Dev d;
+        d.x = x; d.ref = ref; d.slab = slab; d.free_stack = free_stack; d.retired = retired; d.ctr = ctr;
+        d.entries = entries; d.dim = dim; d.mp = mp; d.R = R; d.metric = metric; d.alpha2 = alpha2;
+        d.n_entries = n_entries; d.capacity = capacity; d.pool = pool;
+        return d;
+    }
+
+    etale_status fail(etale_status s, const char *fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return s;
+    }
+    etale_status cuda_fail(cudaError_t e, const char *where) {
+        return fail(ETALE_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+    }
+};
+
+#define CK(expr, where)                                                     \
+    do {                                                                    \
+        cudaError_t _e = (expr);                                            \
+        if (_e != cudaSuccess) return idx->cuda_fail(_e, where);            \
+    } while (0)
+
+namespace {
+
+// Read the device counters (synchronises the stream).
+etale_status read_ctr(etale_index *idx, cudaStream_t st) {
+    CK(cudaMemcpyAsync(idx->host_ctr, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost, st), "read counters");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return ETALE_OK;
+}
+
+etale_status check_device_errors(etale_index *idx, cudaStream_t st) {
+    etale_status s = read_ctr(idx, st);
+    if (s != ETALE_OK) return s;
+    idx->free_lb = idx->host_ctr[C_FREE];
+    const u64 e = idx->host_ctr[C_ERR];
+    if (e) {
+        u64 z = 0;
+        cudaMemcpy(idx->ctr + C_ERR, &z, sizeof z, cudaMemcpyHostToDevice);
+        if (e & ERR_TIMEOUT) return idx->fail(ETALE_ETIMEOUT, "a bounded device wait gave up");
+        if (e & ERR_NOMEM) return idx->fail(ETALE_ENOMEM, "slab pool exhausted during a launch");
+        if (e & ERR_CAS) return idx->fail(ETALE_EINTERNAL, "a publication lost a CAS that had no competitor");
+        if (e & ERR_OVERFLOW) return idx->fail(ETALE_EINTERNAL, "a candidate list overflowed its bound");
+        return idx->fail(ETALE_EINTERNAL, "device error bits 0x%llx", e);
+    }
+    return ETALE_OK;
+}
+
+// Make sure a phase that may pop `need` slabs cannot exhaust the pool.
+etale_status ensure_pool(etale_index *idx, u64 need, cudaStream_t st) {
+    if (idx->free_lb >= need) {
+        idx->free_lb -= need;
+        return ETALE_OK;
+    }
+    etale_status s = read_ctr(idx, st);
+    if (s != ETALE_OK) return s;
+    idx->free_lb = idx->host_ctr[C_FREE];
+    if (idx->free_lb < need)
+        return idx->fail(ETALE_ENOMEM, "slab pool: %llu free, a phase may need %llu", (unsigned long long)idx->free_lb,
+                         (unsigned long long)need);
+    idx->free_lb -= need;
+    return ETALE_OK;
+}
+
+etale_status recycle(etale_index *idx, cudaStream_t st) {
+    CK(launch_recycle(idx->dev(), st), "recycle");
+    g_kernel_launches++;
+    return ETALE_OK;
+}
+
+etale_status recompute_entries(etale_index *idx, cudaStream_t st) {
+    const u64 n = idx->next_id;
+    const u32 S = (u32)(idx->live < idx->cfg.n_entry ? idx->live : idx->cfg.n_entry);
+    idx->n_entries = S;
+    if (S == 0 || n == 0) return ETALE_OK;
+    if (!grow(idx->live_flags, n * 4) || !grow(idx->live_rank, n * 4) ||
+        !grow(idx->live_scan_scr, scan_scratch_elems((u32)n) * 4))
+        return idx->fail(ETALE_ENOMEM, "scratch allocation (entries)");
+    ScanScratch ss;
+    scan_scratch_carve(ss, as<u32>(idx->live_scan_scr), (u32)n);
+    Dev d = idx->dev();
+    CK(launch_live_flags(d, n, as<u32>(idx->live_flags), st), "live flags");
+    CK(exclusive_scan(as<u32>(idx->live_flags), as<u32>(idx->live_rank), (u32)n, ss, st), "live scan");
+    CK(launch_entries_select(d, n, as<u32>(idx->live_flags), as<u32>(idx->live_rank), idx->live, S, st),
+       "entries select");
+    g_kernel_launches += 3;
+    return ETALE_OK;
+}
+
+// Sort offers by target (stable), segment them, fold (deterministic) or
+// publish each offer (lock-free).
+// `targets` bounds the number of distinct targets (each publishes at most
+// once per phase in deterministic mode; lock-free retries are rare and a dry
+// pool is reported by the device).
+etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t st) {
+    Dev d = idx->dev();
+    Offers of{as<u32>(idx->of_key), as<u32>(idx->of_val), as<u32>(idx->of_key2), as<u32>(idx->of_val2),
+              as<u32>(idx->of_src), as<float>(idx->of_rho), nslots};
+    const bool lockfree = idx->cfg.mode == ETALE_MODE_LOCKFREE;
+    etale_status s = ensure_pool(idx, std::min<u64>(nslots, targets), st);
+    if (s != ETALE_OK) return s;
+    u64 *seg_count = as<u64>(idx->counts) + 0;
+    if (!lockfree) {
+        SortScratch ss;
+        sort_scratch_carve(ss, as<u32>(idx->sort_scr), nslots);
+        CK(radix_sort_pairs(of.key, of.val, of.key_alt, of.val_alt, nslots, bits_for(idx->capacity), ss, st),
+           "offer sort");
+        ScanScratch sc;
+        scan_scratch_carve(sc, as<u32>(idx->scan_scr), nslots);
+        CK(make_segments(of.key, nslots, (u32)idx->capacity, as<u32>(idx->seg_flags), as<u32>(idx->seg_scan),
+                         as<u32>(idx->seg_start), seg_count, sc, st),
+           "offer segments");
+        g_kernel_launches += 3 * ((bits_for(idx->capacity) + 7) / 8) * 2 + 4;
+    }
+    CK(launch_offer_fold(d, of, as<u32>(idx->seg_start), seg_count, lockfree ? idx->cfg.cas_budget : 0, idx->num_sms,
+                         st),
+       "offer fold");
+    g_kernel_launches++;
+    return recycle(idx, st);
+}
+
+etale_status size_batch_scratch(etale_index *idx, u64 b) {
+    const u64 R = idx->R, H = idx->cfg.max_hops ? idx->cfg.max_hops : 4ull * idx->cfg.build_beam;
+    const u64 slots = b * R;
+    bool ok = grow(idx->exp_keys, b * H * 8) && grow(idx->exp_count, b * 4) && grow(idx->F_id, slots * 4) &&
+              grow(idx->F_rho, slots * 4) && grow(idx->F_n, b * 4) && grow(idx->of_key, slots * 4) &&
+              grow(idx->of_val, slots * 4) && grow(idx->of_key2, slots * 4) && grow(idx->of_val2, slots * 4) &&
+              grow(idx->of_src, slots * 4) && grow(idx->of_rho, slots * 4) && grow(idx->seg_flags, slots * 4) &&
+              grow(idx->seg_scan, slots * 4) && grow(idx->seg_start, (slots + 1) * 4) &&
+              grow(idx->sort_scr, sort_scratch_elems((u32)slots) * 4) &&
+              grow(idx->scan_scr, scan_scratch_elems((u32)slots) * 4) && grow(idx->counts, 64);
+    return ok ? ETALE_OK : idx->fail(ETALE_ENOMEM, "scratch allocation (insert batch of %llu)", (unsigned long long)b);
+}
+
+etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st) {
+    Dev d = idx->dev();
+    const u32 L = idx->cfg.build_beam;
+    const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    const u32 R = idx->R;
+    const u32 slots = b * R;
+    Offers of{as<u32>(idx->of_key), as<u32>(idx->of_val), as<u32>(idx->of_key2), as<u32>(idx->of_val2),
+              as<u32>(idx->of_src), as<float>(idx->of_rho), slots};
+    // 1. BeamSearch of every member on the graph before the sub-batch
+    CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr, as<u64>(idx->exp_keys),
+                     as<u32>(idx->exp_count), idx->tune, idx->num_sms, st),
+       "insert search");
+    g_kernel_launches++;
+    // 2. forward edges, own slab, offers
+    etale_status s = ensure_pool(idx, b, st);
+    if (s != ETALE_OK) return s;
+    CK(launch_prune_insert(d, first, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
+                           as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st),
+       "prune insert");
+    g_kernel_launches++;
+    s = recycle(idx, st);
+    if (s != ETALE_OK) return s;
+    // 3. reverse offers (targets are nodes that existed before the sub-batch)
+    s = run_offers(idx, slots, idx->live, st);
+    if (s != ETALE_OK) return s;
+    // 4. refine pass
+    const u32 rmode = idx->cfg.refine == 1 ? 0 : idx->cfg.refine;
+    if (rmode) {
+        s = ensure_pool(idx, b, st);
+        if (s != ETALE_OK) return s;
+        CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st), "refine");
+        g_kernel_launches++;
+        s = recycle(idx, st);
+        if (s != ETALE_OK) return s;
+        s = run_offers(idx, slots, idx->live + b, st);
+        if (s != ETALE_OK) return s;
+    }
+    return ETALE_OK;
+}
+
+struct StreamCopy {
+    // stage host inputs to device memory
+    static etale_status in(etale_index *idx, DevBuf &buf, const void *src, size_t bytes, const void **dev,
+                           cudaStream_t st) {
+        if (is_device_ptr(src)) {
+            *dev = src;
+            return ETALE_OK;
+        }
+        if (!grow(buf, bytes)) return idx->fail(ETALE_ENOMEM, "staging allocation of %zu bytes", bytes);
+        CK(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, st), "copy input");
+        *dev = buf.p;
+        return ETALE_OK;
+    }
+};
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+etale_status etale_config_default(etale_config *cfg) {
+    if (!cfg) return ETALE_EINVAL;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->build_beam = 64;
+    cfg->alpha = 1.2f;
+    cfg->refine = 2;
+    cfg->n_entry = 1024;
+    cfg->mode = ETALE_MODE_DETERMINISTIC;
+    cfg->cas_budget = 16;
+    return ETALE_OK;
+}
+
+etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, uint64_t capacity,
+                          const etale_config *cfg_in, etale_index **out) {
+    if (!out) { g_create_error = "out is NULL"; return ETALE_EINVAL; }
+    *out = nullptr;
+    if (dim == 0 || degree == 0 || degree > (u32)MAX_R || capacity == 0 || capacity >= 0xFFFFFFFFull ||
+        (metric != ETALE_L2 && metric != ETALE_IP)) {
+        g_create_error = "invalid dim, metric, degree (1..64) or capacity";
+        return ETALE_EINVAL;
+    }
+    etale_config cfg;
+    etale_config_default(&cfg);
+    if (cfg_in) {
+        if (cfg_in->build_beam) cfg.build_beam = cfg_in->build_beam;
+        if (cfg_in->alpha > 0.f) cfg.alpha = cfg_in->alpha;
+        cfg.max_hops = cfg_in->max_hops;
+        cfg.max_cand = cfg_in->max_cand;
+        if (cfg_in->refine) cfg.refine = cfg_in->refine;
+        cfg.max_batch = cfg_in->max_batch;
+        cfg.pool_slabs = cfg_in->pool_slabs;
+        if (cfg_in->n_entry) cfg.n_entry = cfg_in->n_entry;
+        cfg.mode = cfg_in->mode;
+        if (cfg_in->cas_budget) cfg.cas_budget = cfg_in->cas_budget;
+    }
+    if (cfg.refine > 2 || cfg.mode > 1 || cfg.build_beam > 256) {
+        g_create_error = "refine must be 0..2, mode 0..1, build_beam <= 256";
+        return ETALE_EINVAL;
+    }
+    if (cfg.max_cand == 0) cfg.max_cand = 2 * cfg.build_beam;
+    if (cfg.max_batch == 0) cfg.max_batch = capacity / 100 ? capacity / 100 : 1;
+    if (cfg.pool_slabs == 0) cfg.pool_slabs = 2 * capacity + 4ull * (degree + 1) * cfg.max_batch;
+    if (cfg.pool_slabs >= 0xFFFFFFFFull) {
+        g_create_error = "pool_slabs must be below 2^32 - 1";
+        return ETALE_EINVAL;
+    }
+    etale_index *idx = new etale_index();
+    idx->cfg = cfg;
+    idx->dim = dim;
+    idx->mp = (dim + 3) / 4 * 4;
+    idx->R = degree;
+    idx->metric = (u32)metric;
+    idx->capacity = capacity;
+    idx->pool = cfg.pool_slabs;
+    idx->alpha2 = cfg.alpha * cfg.alpha;
+    cudaGetDevice(&idx->device);
+    cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device);
+    const size_t xb = (size_t)capacity * idx->mp * 4, rb = (size_t)capacity * 8;
+    const size_t sb = (size_t)idx->pool * degree * 8, pb = (size_t)idx->pool * 4;
+    bool ok = cudaMalloc(&idx->x, xb) == cudaSuccess && cudaMalloc(&idx->ref, rb) == cudaSuccess &&
+              cudaMalloc(&idx->slab, sb) == cudaSuccess && cudaMalloc(&idx->free_stack, pb) == cudaSuccess &&
+              cudaMalloc(&idx->retired, pb) == cudaSuccess &&
+              cudaMalloc(&idx->ctr, C_NCTR * sizeof(u64)) == cudaSuccess &&
+              cudaMalloc(&idx->entries, (size_t)cfg.n_entry * 4) == cudaSuccess &&
+              cudaMallocHost(&idx->host_ctr, C_NCTR * sizeof(u64)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        g_create_error = "device allocation failed";
+        etale_destroy(idx);
+        return ETALE_ENOMEM;
+    }
+    idx->device_bytes = xb + rb + sb + 2 * pb;
+    // refs <- <0, 0, NIL>; free stack <- all slabs; counters
+    std::vector<u64> ctr(C_NCTR, 0);
+    ctr[C_FREE] = idx->pool;
+    bool ok2 = cudaMemset(idx->ref, 0, rb) == cudaSuccess;
+    {
+        // NIL slab field: low 32 bits all ones
+        std::vector<u64> chunk(1 << 20, ref_pack(0, 0, NIL));
+        for (size_t o = 0; o < capacity && ok2; o += chunk.size()) {
+            size_t n = std::min(chunk.size(), (size_t)(capacity - o));
+            ok2 = cudaMemcpy(idx->ref + o, chunk.data(), n * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        std::vector<u32> fs(1 << 20);
+        for (size_t o = 0; o < idx->pool && ok2; o += fs.size()) {
+            size_t n = std::min(fs.size(), (size_t)(idx->pool - o));
+            for (size_t i = 0; i < n; i++) fs[i] = (u32)(idx->pool - 1 - (o + i));
+            ok2 = cudaMemcpy(idx->free_stack + o, fs.data(), n * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    }
+    ok2 = ok2 && cudaMemcpy(idx->ctr, ctr.data(), C_NCTR * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+          cudaMemset(idx->x, 0, xb) == cudaSuccess;
+    if (!ok2) {
+        g_create_error = std::string("device initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
+        etale_destroy(idx);
+        return ETALE_ECUDA;
+    }
+    idx->free_lb = idx->pool;
+    *out = idx;
+    return ETALE_OK;
+}
+
+etale_status etale_destroy(etale_index *idx) {
+    if (!idx) return ETALE_OK;
+    cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
+    cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
+    if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
+    DevBuf *bufs[] = {&idx->stage, &idx->qpad, &idx->out_ids, &idx->out_dist, &idx->exp_keys, &idx->exp_count,
+                      &idx->F_id, &idx->F_rho, &idx->F_n, &idx->of_key, &idx->of_val, &idx->of_key2,
+                      &idx->of_val2, &idx->of_src, &idx->of_rho, &idx->seg_flags, &idx->seg_scan, &idx->seg_start,
+                      &idx->sort_scr, &idx->scan_scr, &idx->live_flags, &idx->live_rank, &idx->live_scan_scr,
+                      &idx->tomb_bits, &idx->del_ids, &idx->del_vals, &idx->del_ids2, &idx->del_vals2,
+                      &idx->del_ok, &idx->del_scan, &idx->dt, &idx->pair_key, &idx->pair_val, &idx->pair_key2,
+                      &idx->pair_val2, &idx->pair_K, &idx->pair_Kn, &idx->pair_flags, &idx->pair_scan,
+                      &idx->pair_seg, &idx->counts, &idx->ex_del, &idx->ex_hs, &idx->ex_deg, &idx->ex_ids,
+                      &idx->ex_rho};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    delete idx;
+    return ETALE_OK;
+}
+
+etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n, uint32_t *out_ids, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (n == 0) return ETALE_OK;
+    if (!vecs) return idx->fail(ETALE_EINVAL, "vecs is NULL");
+    if (idx->next_id + n > idx->capacity)
+        return idx->fail(ETALE_ECAPACITY, "insert of %llu would exceed capacity %llu (next id %llu)",
+                         (unsigned long long)n, (unsigned long long)idx->capacity, (unsigned long long)idx->next_id);
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *src = nullptr;
+    etale_status s = StreamCopy::in(idx, idx->stage, vecs, (size_t)n * idx->dim * 4, &src, st);
+    if (s != ETALE_OK) return s;
+    const u64 first_all = idx->next_id;
+    CK(launch_ingest(idx->x + first_all * idx->mp, idx->mp, (const float *)src, idx->dim, n, st), "ingest");
+    g_kernel_launches++;
+    u64 done = 0;
+    const u64 maxb = idx->cfg.max_batch;
+    s = size_batch_scratch(idx, std::min<u64>(n, maxb));
+    if (s != ETALE_OK) return s;
+    while (done < n) {
+        u64 b = n - done;
+        const u64 cap = idx->live ? idx->live : 1;
+        if (b > cap) b = cap;
+        if (b > maxb) b = maxb;
+        const u32 first = (u32)idx->next_id;
+        idx->next_id += b;
+        s = insert_subbatch(idx, first, (u32)b, st);
+        if (s != ETALE_OK) return s;
+        idx->live += b;
+        s = recompute_entries(idx, st);
+        if (s != ETALE_OK) return s;
+        done += b;
+    }
+    std::vector<u32> ids;
+    if (out_ids) {
+        ids.resize(n);
+        for (u64 i = 0; i < n; i++) ids[i] = (u32)(first_all + i);
+        CK(cudaMemcpyAsync(out_ids, ids.data(), n * 4, cudaMemcpyDefault, st), "write ids");
+    }
+    return check_device_errors(idx, st);   // synchronises before `ids` goes away
+}
+
+etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uint64_t *n_deleted, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (n_deleted) *n_deleted = 0;
+    if (n == 0) return ETALE_OK;
+    if (!ids) return idx->fail(ETALE_EINVAL, "ids is NULL");
+    if (n > 0x7FFFFFFFull / MAX_R) return idx->fail(ETALE_EINVAL, "delete batch too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    const u32 R = idx->R;
+    const u64 slots = n * R;
+    bool ok = grow(idx->del_ids, n * 4) && grow(idx->del_vals, n * 4) && grow(idx->del_ids2, n * 4) &&
+              grow(idx->del_vals2, n * 4) && grow(idx->del_ok, n * 4) && grow(idx->del_scan, n * 4) &&
+              grow(idx->dt, n * 4) && grow(idx->pair_key, slots * 4) && grow(idx->pair_val, slots * 4) &&
+              grow(idx->pair_key2, slots * 4) && grow(idx->pair_val2, slots * 4) &&
+              grow(idx->pair_K, slots * R * 8) && grow(idx->pair_Kn, slots * 4) &&
+              grow(idx->pair_flags, slots * 4) && grow(idx->pair_scan, slots * 4) &&
+              grow(idx->pair_seg, (slots + 1) * 4) && grow(idx->counts, 64) &&
+              grow(idx->sort_scr, sort_scratch_elems((u32)std::max<u64>(slots, n)) * 4) &&
+              grow(idx->scan_scr, scan_scratch_elems((u32)std::max<u64>(slots, n)) * 4);
+    if (!ok) return idx->fail(ETALE_ENOMEM, "scratch allocation (delete batch of %llu)", (unsigned long long)n);
+    if (is_device_ptr(ids)) {
+        CK(cudaMemcpyAsync(idx->del_ids.p, ids, n * 4, cudaMemcpyDeviceToDevice, st), "copy ids");
+    } else {
+        CK(cudaMemcpyAsync(idx->del_ids.p, ids, n * 4, cudaMemcpyHostToDevice, st), "copy ids");
+    }
+    Dev d = idx->dev();
+    SortScratch ss;
+    sort_scratch_carve(ss, as<u32>(idx->sort_scr), (u32)std::max<u64>(slots, n));
+    ScanScratch sc;
+    scan_scratch_carve(sc, as<u32>(idx->scan_scr), (u32)std::max<u64>(slots, n));
+    // sorted ids (payload unused)
+    CK(launch_fill_offer_keys(as<u32>(idx->del_vals2), as<u32>(idx->del_vals), (u32)n, 0, st), "iota");
+    CK(radix_sort_pairs(as<u32>(idx->del_ids), as<u32>(idx->del_vals), as<u32>(idx->del_ids2),
+                        as<u32>(idx->del_vals2), (u32)n, 32, ss, st),
+       "sort ids");
+    u64 *n_dt = as<u64>(idx->counts) + 1;
+    u64 *seg_count = as<u64>(idx->counts) + 2;
+    CK(launch_tombstone(d, as<u32>(idx->del_ids), (u32)n, idx->next_id, as<u32>(idx->del_ok), st), "tombstone");
+    CK(exclusive_scan(as<u32>(idx->del_ok), as<u32>(idx->del_scan), (u32)n, sc, st), "tombstone scan");
+    CK(launch_compact_ok(as<u32>(idx->del_ids), as<u32>(idx->del_ok), as<u32>(idx->del_scan), (u32)n,
+                         as<u32>(idx->dt), n_dt, st),
+       "tombstone compaction");
+    g_kernel_launches += 4 * 3 + 6;
+    // repair: K(u, a) per pair, then one fold per a
+    const u32 invalid = (u32)idx->capacity;
+    CK(launch_fill_offer_keys(as<u32>(idx->pair_key), as<u32>(idx->pair_val), (u32)slots, invalid, st), "fill pairs");
+    CK(launch_repair_k(d, as<u32>(idx->dt), n_dt, (u32)n, as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                       as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), idx->num_sms, st),
+       "repair K");
+    g_kernel_launches += 2;
+    const bool lockfree = idx->cfg.mode == ETALE_MODE_LOCKFREE;
+    etale_status s = ensure_pool(idx, std::min<u64>(slots, idx->live), st);
+    if (s != ETALE_OK) return s;
+    if (!lockfree) {
+        CK(radix_sort_pairs(as<u32>(idx->pair_key), as<u32>(idx->pair_val), as<u32>(idx->pair_key2),
+                            as<u32>(idx->pair_val2), (u32)slots, bits_for(idx->capacity), ss, st),
+           "pair sort");
+        CK(make_segments(as<u32>(idx->pair_key), (u32)slots, invalid, as<u32>(idx->pair_flags),
+                         as<u32>(idx->pair_scan), as<u32>(idx->pair_seg), seg_count, sc, st),
+           "pair segments");
+        g_kernel_launches += 3 * ((bits_for(idx->capacity) + 7) / 8) * 2 + 4;
+    }
+    CK(launch_repair_fold(d, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                          as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), as<u32>(idx->pair_seg), seg_count, slots,
+                          lockfree ? idx->cfg.cas_budget : 0, idx->num_sms, st),
+       "repair fold");
+    g_kernel_launches++;
+    s = recycle(idx, st);
+    if (s != ETALE_OK) return s;
+    u64 k = 0;
+    CK(cudaMemcpyAsync(&k, n_dt, sizeof k, cudaMemcpyDeviceToHost, st), "read count");
+    s = check_device_errors(idx, st);   // synchronises
+    idx->live -= k;
+    idx->tombs += k;
+    if (n_deleted) *n_deleted = k;
+    return s;
+}
+
+etale_status etale_reclaim(etale_index *idx, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    etale_status s = recompute_entries(idx, st);
+    if (s != ETALE_OK) return s;
+    const u64 n = idx->next_id;
+    if (n == 0) return ETALE_OK;
+    if (!grow(idx->tomb_bits, ((n + 31) / 32) * 4)) return idx->fail(ETALE_ENOMEM, "scratch allocation (reclaim)");
+    Dev d = idx->dev();
+    CK(launch_tomb_bits(d, n, as<u32>(idx->tomb_bits), st), "tombstone bitmap");
+    s = ensure_pool(idx, idx->live, st);
+    if (s != ETALE_OK) return s;
+    CK(launch_compact(d, n, as<u32>(idx->tomb_bits), st), "compaction");
+    g_kernel_launches += 2;
+    s = recycle(idx, st);
+    if (s != ETALE_OK) return s;
+    CK(launch_reclaim_tombstones(d, n, st), "reclaim");
+    g_kernel_launches++;
+    s = recycle(idx, st);
+    if (s != ETALE_OK) return s;
+    s = check_device_errors(idx, st);
+    idx->reclaimed += idx->tombs;
+    idx->tombs = 0;
+    return s;
+}
+
+static etale_status search_common(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
+                                  uint32_t *out_ids, float *out_dists, void *stream, bool exact) {
+    if (!idx) return ETALE_EINVAL;
+    if (nq == 0) return ETALE_OK;
+    if (!queries || !out_ids || !out_dists || k == 0) return idx->fail(ETALE_EINVAL, "null buffer or k == 0");
+    if (exact && k > 32) return idx->fail(ETALE_EINVAL, "ground truth supports k <= 32");
+    const u32 L = beam > k ? beam : k;
+    if (!exact && L > 256) return idx->fail(ETALE_EINVAL, "beam must be <= 256");
+    if (nq > 0xFFFFFFFFull) return idx->fail(ETALE_EINVAL, "too many queries");
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *src = nullptr;
+    etale_status s = StreamCopy::in(idx, idx->stage, queries, (size_t)nq * idx->dim * 4, &src, st);
+    if (s != ETALE_OK) return s;
+    if (!grow(idx->qpad, (size_t)nq * idx->mp * 4)) return idx->fail(ETALE_ENOMEM, "query staging");
+    CK(launch_ingest(as<float>(idx->qpad), idx->mp, (const float *)src, idx->dim, nq, st), "query ingest");
+    const bool dev_out = is_device_ptr(out_ids) && is_device_ptr(out_dists);
+    u32 *oid = out_ids;
+    float *od = out_dists;
+    if (!dev_out) {
+        if (!grow(idx->out_ids, nq * k * 4) || !grow(idx->out_dist, nq * k * 4))
+            return idx->fail(ETALE_ENOMEM, "output staging");
+        oid = as<u32>(idx->out_ids);
+        od = as<float>(idx->out_dist);
+    }
+    Dev d = idx->dev();
+    if (exact) {
+        CK(launch_ground_truth(d, idx->next_id, as<float>(idx->qpad), (u32)nq, k, oid, od, idx->num_sms, st),
+           "ground truth");
+    } else {
+        const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+        CK(launch_search(d, as<float>(idx->qpad), (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, idx->tune,
+                         idx->num_sms, st),
+           "search");
+    }
+    g_kernel_launches += 2;
+    if (!dev_out) {
+        CK(cudaMemcpyAsync(out_ids, oid, nq * k * 4, cudaMemcpyDeviceToHost, st), "copy ids out");
+        CK(cudaMemcpyAsync(out_dists, od, nq * k * 4, cudaMemcpyDeviceToHost, st), "copy dists out");
+    }
+    return check_device_errors(idx, st);
+}
+
+etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
+                          uint32_t *out_ids, float *out_dists, void *stream) {
+    return search_common(idx, queries, nq, k, beam, out_ids, out_dists, stream, false);
+}
+
+etale_status etale_ground_truth(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t *out_ids,
+                                float *out_dists, void *stream) {
+    return search_common(idx, queries, nq, k, 0, out_ids, out_dists, stream, true);
+}
+
+etale_status etale_export_graph(etale_index *idx, uint64_t n, uint8_t *deleted, uint8_t *has_slab, uint8_t *degree,
+                                uint32_t *nbr_ids, float *nbr_rho, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (n > idx->next_id) return idx->fail(ETALE_EINVAL, "n exceeds next_id");
+    if (n == 0) return ETALE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const u64 R = idx->R;
+    if (!grow(idx->ex_del, n) || !grow(idx->ex_hs, n) || !grow(idx->ex_deg, n) || !grow(idx->ex_ids, n * R * 4) ||
+        !grow(idx->ex_rho, n * R * 4))
+        return idx->fail(ETALE_ENOMEM, "export staging");
+    CK(launch_export(idx->dev(), n, as<unsigned char>(idx->ex_del), as<unsigned char>(idx->ex_hs),
+                     as<unsigned char>(idx->ex_deg), as<u32>(idx->ex_ids), as<float>(idx->ex_rho), st),
+       "export");
+    g_kernel_launches++;
+    CK(cudaMemcpyAsync(deleted, idx->ex_del.p, n, cudaMemcpyDefault, st), "export copy");
+    CK(cudaMemcpyAsync(has_slab, idx->ex_hs.p, n, cudaMemcpyDefault, st), "export copy");
+    CK(cudaMemcpyAsync(degree, idx->ex_deg.p, n, cudaMemcpyDefault, st), "export copy");
+    CK(cudaMemcpyAsync(nbr_ids, idx->ex_ids.p, n * R * 4, cudaMemcpyDefault, st), "export copy");
+    CK(cudaMemcpyAsync(nbr_rho, idx->ex_rho.p, n * R * 4, cudaMemcpyDefault, st), "export copy");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return ETALE_OK;
+}
+
+etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n) {
+    if (!idx || !out || !n) return ETALE_EINVAL;
+    *n = idx->n_entries;
+    if (idx->n_entries == 0) return ETALE_OK;
+    cudaError_t e = cudaMemcpy(out, idx->entries, (size_t)idx->n_entries * 4, cudaMemcpyDefault);
+    return e == cudaSuccess ? ETALE_OK : idx->cuda_fail(e, "copy entries");
+}
+
+etale_status etale_stats(etale_index *idx, etale_stats_t *o) {
+    if (!idx || !o) return ETALE_EINVAL;
+    cudaError_t e = cudaMemcpy(idx->host_ctr, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return idx->cuda_fail(e, "read counters");
+    memset(o, 0, sizeof *o);
+    const u64 *c = idx->host_ctr;
+    o->live = idx->live;
+    o->tombstones = idx->tombs;
+    o->reclaimed = idx->reclaimed;
+    o->next_id = idx->next_id;
+    o->capacity = idx->capacity;
+    o->pool_slabs = idx->pool;
+    o->free_slabs = c[C_FREE] - std::min(c[C_POP], c[C_FREE]);
+    o->retired_slabs = c[C_RET];
+    o->used_slabs = idx->pool - o->free_slabs - o->retired_slabs;
+    o->n_entries = idx->n_entries;
+    o->degree = idx->R;
+    o->n_publish = c[C_PUBLISH];
+    o->n_cas_retry = c[C_CAS_RETRY];
+    o->n_dropped = c[C_DROPPED];
+    o->n_expand = c[C_EXPAND];
+    o->n_dist = c[C_DIST];
+    o->device_bytes = idx->device_bytes;
+    return ETALE_OK;
+}
+
+etale_status etale_get_config(const etale_index *idx, etale_config *out) {
+    if (!idx || !out) return ETALE_EINVAL;
+    *out = idx->cfg;
+    return ETALE_OK;
+}
+
+const char *etale_last_error(const etale_index *idx) {
+    return idx ? idx->err.c_str() : g_create_error.c_str();
+}
+
+uint64_t etale_kernel_launches(const etale_index *) { return g_kernel_launches.load(); }
+
+}  // extern "C"

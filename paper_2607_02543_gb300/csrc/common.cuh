@@ -1,0 +1,296 @@
+// common.cuh — device-side building blocks of the ETALE index for sm_103a.
+//
+// State (Definition 1): vectors x[C][mp] fp32 (rows zero-padded to mp, a
+// multiple of 4, so every row is 16-byte aligned for bulk copies), one 64-bit
+// reference word per id, and a pool of P slabs of R entries {u32 id; f32 rho}.
+// Slabs come from a free stack and go back through a retired stack that the
+// host recycles between launches (Sec. 3.3, Lemma 1).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace etale {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u32 NIL = 0xFFFFFFFFu;
+constexpr u64 KEY_INF = ~0ull;
+constexpr u32 FULL = 0xFFFFFFFFu;
+constexpr int MAX_R = 64;
+
+// ---- device error word (bit flags, OR-ed by kernels, read by the host) ----
+enum : u32 {
+    ERR_NOMEM = 1u,        // free stack ran dry during a launch
+    ERR_TIMEOUT = 2u,      // a bounded mbarrier wait gave up
+    ERR_CAS = 4u,          // a deterministic-mode CAS lost (must not happen)
+    ERR_OVERFLOW = 8u,     // a scratch list overflowed its bound
+};
+
+// ---- pool / statistics counters (one u64 array in device memory) ----------
+enum : int {
+    C_FREE = 0,        // entries on the free stack at launch start
+    C_POP = 1,         // pops taken during the current launch
+    C_RET = 2,         // entries on the retired stack
+    C_ERR = 3,         // error bits
+    C_PUBLISH = 4,
+    C_CAS_RETRY = 5,
+    C_DROPPED = 6,
+    C_EXPAND = 7,
+    C_DIST = 8,
+    C_WORK = 9,        // work-queue counter (reset before each persistent launch)
+    C_WORK2 = 10,
+    C_COUNT_A = 11,    // scratch counts produced on the device
+    C_COUNT_B = 12,
+    C_NCTR = 16
+};
+
+// ---- reference word r(u) = <delta, d, s>: bit 63 delta, bits 48..55 d,
+//      bits 0..31 s (NIL = no slab).  Same packing as the paper's single
+//      64-bit word; the bit positions are this library's choice.
+__host__ __device__ __forceinline__ u64 ref_pack(u32 del, u32 d, u32 s) {
+    return ((u64)(del & 1u) << 63) | ((u64)(d & 0xFFu) << 48) | (u64)s;
+}
+__host__ __device__ __forceinline__ u32 ref_del(u64 r) { return (u32)(r >> 63); }
+__host__ __device__ __forceinline__ u32 ref_deg(u64 r) { return (u32)(r >> 48) & 0xFFu; }
+__host__ __device__ __forceinline__ u32 ref_slab(u64 r) { return (u32)r; }
+
+// ---- (rho, id) total order: fp32 bits mapped to an unsigned order ---------
+__host__ __device__ __forceinline__ u32 fbits(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    u32 u;
+    __builtin_memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float bitsf(u32 u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    __builtin_memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ u32 f2ord(float f) {
+    u32 u = fbits(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float ord2f(u32 o) {
+    u32 u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    return bitsf(u);
+}
+__host__ __device__ __forceinline__ u64 mkkey(float rho, u32 id) {
+    return ((u64)f2ord(rho) << 32) | id;
+}
+__host__ __device__ __forceinline__ u32 key_id(u64 k) { return (u32)k; }
+__host__ __device__ __forceinline__ float key_rho(u64 k) { return ord2f((u32)(k >> 32)); }
+
+// ---- index view passed by value to every kernel ---------------------------
+struct Dev {
+    float *x;          // C x mp
+    u64 *ref;          // C
+    uint2 *slab;       // P x R   {id, rho bits}
+    u32 *free_stack;   // P
+    u32 *retired;      // P
+    u64 *ctr;          // C_NCTR counters
+    u32 *entries;      // n_entry
+    u32 dim, mp, R, metric;
+    float alpha2;
+    u32 n_entries;
+    u64 capacity, pool;
+};
+
+// ---- canonical distance ------------------------------------------------------
+// Element i belongs to partial j = (i mod 128) / 4.  Each partial is a fused
+// multiply-add chain over its elements in ascending i, from +0.  The 32
+// partials are combined as q[j] = p[j] + p[j + h] for h = 16, 8, 4, 2, 1.
+// G lanes (an aligned group) cooperate on one distance: lane g of the group
+// owns partials g, g + G, g + 2G, ...; the tree levels h >= G are summed in
+// the lane, the levels h < G by xor shuffles.  Every lane of the group
+// returns the same value.  Explicit _rn intrinsics keep the compiler from
+// contracting or reordering anything.
+template <int G>
+__device__ __forceinline__ float canon_dist(const float *__restrict__ a, const float *__restrict__ b,
+                                            int mp, int metric, int g) {
+    constexpr int T = 32 / G;
+    float p[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        const int j = g + G * t;
+        float acc = 0.0f;
+        for (int base = 0; base < mp; base += 128) {
+            const int i = base + 4 * j;
+            if (i < mp) {
+                const float4 u = *reinterpret_cast<const float4 *>(a + i);
+                const float4 v = *reinterpret_cast<const float4 *>(b + i);
+                if (metric == 0) {
+                    float d0 = __fsub_rn(u.x, v.x), d1 = __fsub_rn(u.y, v.y);
+                    float d2 = __fsub_rn(u.z, v.z), d3 = __fsub_rn(u.w, v.w);
+                    acc = __fmaf_rn(d0, d0, acc);
+                    acc = __fmaf_rn(d1, d1, acc);
+                    acc = __fmaf_rn(d2, d2, acc);
+                    acc = __fmaf_rn(d3, d3, acc);
+                } else {
+                    acc = __fmaf_rn(u.x, v.x, acc);
+                    acc = __fmaf_rn(u.y, v.y, acc);
+                    acc = __fmaf_rn(u.z, v.z, acc);
+                    acc = __fmaf_rn(u.w, v.w, acc);
+                }
+            }
+        }
+        p[t] = acc;
+    }
+#pragma unroll
+    for (int hh = T / 2; hh >= 1; hh >>= 1)
+#pragma unroll
+        for (int t = 0; t < hh; t++) p[t] = __fadd_rn(p[t], p[t + hh]);
+    float s = p[0];
+#pragma unroll
+    for (int h = G / 2; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
+    return metric == 0 ? s : __fsub_rn(1.0f, s);
+}
+
+// ---- small warp helpers -------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ u32 lanemask_lt() {
+    u32 m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Ascending bitonic sort of n (a power of two, >= 32) u64 keys in shared
+// memory by one warp.
+__device__ __forceinline__ void warp_sort_u64(u64 *a, int n) {
+    const int lane = lane_id();
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < n; i += 32) {
+                int l = i ^ j;
+                if (l > i) {
+                    u64 x = a[i], y = a[l];
+                    bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[l] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Bitonic sort of one u64 per lane across the warp (ascending by lane).
+__device__ __forceinline__ u64 warp_sort32(u64 v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            u64 o = __shfl_xor_sync(FULL, v, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            u64 lo = v < o ? v : o, hi = v < o ? o : v;
+            v = (lower == up) ? lo : hi;
+        }
+    }
+    return v;
+}
+
+__device__ __forceinline__ int next_pow2(int n) {
+    int p = 32;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// ---- slab pool: AllocSlab / RetireSlab (Sec. 3.3) ----------------------------
+// Inside one launch the free stack is only popped and the retired stack only
+// pushed, each through one atomic counter; the host-ordered recycle kernel
+// moves retired entries back between launches.
+__device__ __forceinline__ u32 alloc_slab(const Dev &d) {
+    u64 i = atomicAdd(&d.ctr[C_POP], 1ull);
+    u64 nfree = d.ctr[C_FREE];
+    if (i >= nfree) {
+        atomicOr(&d.ctr[C_ERR], (u64)ERR_NOMEM);
+        return NIL;
+    }
+    return d.free_stack[nfree - 1 - i];
+}
+__device__ __forceinline__ void retire_slab(const Dev &d, u32 s) {
+    u64 j = atomicAdd(&d.ctr[C_RET], 1ull);
+    d.retired[j] = s;
+}
+
+// Warp-cooperative Publish(u, N) (Algorithm 1).  All 32 lanes call it with
+// the same arguments; ids/rho hold the n <= R entries (shared memory) and
+// `snap` is the reference word the caller read before building N.  The CAS
+// installs <delta of snap, n, fresh slab> only if r(u) still equals snap;
+// returns true on success.  On a lost CAS the fresh slab is retired and false
+// is returned (the caller retries or drops the update).
+__device__ __forceinline__ bool warp_publish(const Dev &d, u32 u, const u32 *ids, const float *rho,
+                                             int n, u64 snap) {
+    const int lane = lane_id();
+    u32 s2 = 0;
+    if (lane == 0) s2 = alloc_slab(d);
+    s2 = __shfl_sync(FULL, s2, 0);
+    if (s2 == NIL) return false;
+    uint2 *dst = d.slab + (u64)s2 * d.R;
+    for (int j = lane; j < n; j += 32) dst[j] = make_uint2(ids[j], __float_as_uint(rho[j]));
+    __threadfence();           // slab contents visible before the reference
+    __syncwarp();
+    int ok = 0;
+    if (lane == 0) {
+        u64 nw = ref_pack(ref_del(snap), (u32)n, s2);   // carry the deletion flag
+        u64 old = atomicCAS(&d.ref[u], snap, nw);
+        if (old == snap) {
+            ok = 1;
+            if (ref_slab(snap) != NIL) retire_slab(d, ref_slab(snap));
+            atomicAdd(&d.ctr[C_PUBLISH], 1ull);
+        } else {
+            retire_slab(d, s2);
+            atomicAdd(&d.ctr[C_CAS_RETRY], 1ull);
+        }
+    }
+    ok = __shfl_sync(FULL, ok, 0);
+    return ok != 0;
+}
+
+__device__ __forceinline__ u64 ld_ref(const Dev &d, u32 id) {
+    return *reinterpret_cast<volatile const u64 *>(d.ref + id);
+}
+
+// ---- bulk (TMA, non-tensor) copies into shared memory with an mbarrier -----
+__device__ __forceinline__ u32 smem_addr(const void *p) {
+    return static_cast<u32>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64 *bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// Bounded wait on the given phase parity.  Returns false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity, u32 limit) {
+    for (u32 it = 0; it < limit; it++) {
+        u32 done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr u32 WAIT_LIMIT = 1u << 22;   // each try_wait suspends ~1 us at most
+
+}  // namespace etale

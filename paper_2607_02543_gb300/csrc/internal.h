@@ -1,0 +1,89 @@
+// internal.h — host-side launchers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace etale {
+
+struct SearchTuning {
+    u32 stage_rows = 16;   // rows gathered per bulk-copy batch
+    u32 seen_bits = 10;    // log2 of the evaluated-id cache slots
+};
+
+// search.cu
+size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
+cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
+                          u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count,
+                          const SearchTuning &tune, int num_sms, cudaStream_t st);
+
+// Offer lists: a payload index p names (src[p], rho[p]); key[p] is the target
+// id or `invalid` (= capacity) for an empty slot.
+struct Offers {
+    u32 *key, *val;        // sorted in place (val = payload index)
+    u32 *key_alt, *val_alt;
+    u32 *src;
+    float *rho;
+    u32 n;                 // slots
+};
+
+// update.cu
+cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
+                                u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
+                                const Offers &of, int num_sms, cudaStream_t st);
+cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
+                              u32 lockfree_budget, int num_sms, cudaStream_t st);
+cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
+                          int num_sms, cudaStream_t st);
+cudaError_t launch_tombstone(const Dev &d, const u32 *sorted_ids, u32 n, u64 next_id, u32 *ok_flags,
+                             cudaStream_t st);
+cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
+                            u32 *pair_val, uint2 *pair_K, u32 *pair_Kn, int num_sms, cudaStream_t st);
+// budget == 0: deterministic, one warp per segment of equal targets;
+// budget > 0: lock-free, one warp per pair slot (n_pairs slots).
+cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key, const u32 *pair_val,
+                               const uint2 *pair_K, const u32 *pair_Kn, const u32 *seg_start,
+                               const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st);
+cudaError_t launch_compact(const Dev &d, u64 next_id, const u32 *tomb_bits, cudaStream_t st);
+cudaError_t launch_reclaim_tombstones(const Dev &d, u64 next_id, cudaStream_t st);
+
+// util.cu
+struct ScanScratch {
+    u32 *lvl[4];
+    u32 lvl_n[4];
+    int levels;
+};
+size_t scan_scratch_elems(u32 n);
+void scan_scratch_carve(ScanScratch &s, u32 *buf, u32 n);
+cudaError_t exclusive_scan(const u32 *in, u32 *out, u32 n, const ScanScratch &s, cudaStream_t st);
+
+struct SortScratch {
+    u32 *hist;             // 256 * tiles
+    u32 *hist_scan;
+    ScanScratch scan;
+};
+size_t sort_scratch_elems(u32 n);
+void sort_scratch_carve(SortScratch &s, u32 *buf, u32 n);
+// Stable LSD radix sort of (key, val) by the low `key_bits` bits of key.  The
+// result ends in (key, val); (key_alt, val_alt) are scratch of equal size.
+cudaError_t radix_sort_pairs(u32 *key, u32 *val, u32 *key_alt, u32 *val_alt, u32 n, u32 key_bits,
+                             const SortScratch &s, cudaStream_t st);
+// Segments of equal keys among sorted keys (keys equal to `invalid` sort last
+// and are ignored): seg_start[0..count] and the count in *seg_count.
+cudaError_t make_segments(const u32 *key, u32 n, u32 invalid, u32 *flags, u32 *scan_out,
+                          u32 *seg_start, u64 *seg_count, const ScanScratch &s, cudaStream_t st);
+
+cudaError_t launch_recycle(const Dev &d, cudaStream_t st);
+cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st);
+cudaError_t launch_live_flags(const Dev &d, u64 next_id, u32 *flags, cudaStream_t st);
+cudaError_t launch_entries_select(const Dev &d, u64 next_id, const u32 *flags, const u32 *rank, u64 live,
+                                  u32 S, cudaStream_t st);
+cudaError_t launch_tomb_bits(const Dev &d, u64 next_id, u32 *bits, cudaStream_t st);
+cudaError_t launch_compact_ok(const u32 *ids, const u32 *flags, const u32 *scan, u32 n, u32 *out,
+                              u64 *count, cudaStream_t st);
+cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 nq, u32 k, u32 *out_ids,
+                                float *out_dist, int num_sms, cudaStream_t st);
+cudaError_t launch_export(const Dev &d, u64 n, unsigned char *del, unsigned char *hs, unsigned char *deg,
+                          u32 *ids, float *rho, cudaStream_t st);
+cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaStream_t st);
+
+}  // namespace etale

@@ -1,0 +1,304 @@
+// search.cu — BeamSearch (Sec. 3.4.1) for inserts and queries, one warp per
+// query, persistent grid fed by an atomic work counter.
+//
+// Per expansion the warp reads the expanded node's slab (the reference word
+// was read when the node entered the beam), drops neighbours it has already
+// evaluated, gathers the remaining neighbour rows into shared memory with
+// bulk (TMA) copies completing on an mbarrier, computes their canonical
+// distances with 8 lanes per distance, and merges them into the beam.
+//
+// Visited set.  The beam semantics are those of an exact visited set: an id
+// evaluated once is never evaluated again.  The kernel keeps only a lossy
+// direct-mapped cache of evaluated ids (no false positives) and, when the
+// cache misses, may evaluate an id a second time.  That changes nothing:
+// once the beam is full its worst key only decreases, so an id that left the
+// beam or was refused is refused again (its key is the same), and an id still
+// in the beam is recognised in the merge by its equal key and dropped.
+#include "common.cuh"
+#include "internal.h"
+
+namespace etale {
+
+struct SearchArgs {
+    Dev d;
+    const float *q;      // query rows, stride mp floats, 16-byte aligned
+    u32 nq, L, max_hops, mode;   // mode 0: query, 1: insert
+    u32 k;
+    u32 *out_ids;
+    float *out_dist;
+    u64 *exp_keys;       // insert: nq x max_hops expanded non-tombstone keys
+    u32 *exp_count;
+    u32 stage_rows, seen_slots, seen_bits;
+};
+
+struct WarpSmem {
+    float *qv;       // mp
+    float *stage;    // stage_rows x mp
+    u64 *bkey0, *bkey1;          // beam keys, double-buffered (L each)
+    u64 *bref0, *bref1;          // reference word sampled when the entry was evaluated
+    unsigned char *bflag0, *bflag1;   // expanded flag
+    __device__ __forceinline__ u64 *bkey(int c) const { return c ? bkey1 : bkey0; }
+    __device__ __forceinline__ u64 *bref(int c) const { return c ? bref1 : bref0; }
+    __device__ __forceinline__ unsigned char *bflag(int c) const { return c ? bflag1 : bflag0; }
+    u64 *nkey;       // 32
+    u64 *nref;       // 32
+    u32 *cid;        // 32 candidate ids
+    u64 *ckey;       // 32
+    u64 *cref;       // 32
+    u32 *seen;       // seen_slots
+    u64 *bar;        // mbarrier
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
+    size_t b = 0;
+    b += align_up((size_t)mp * 4, 128);
+    b += align_up((size_t)stage_rows * mp * 4, 128);
+    b += 2 * align_up((size_t)L * 8, 16) * 2;
+    b += 2 * align_up((size_t)L, 16);
+    b += 32 * 8 * 2 + 32 * 4 + 32 * 8 * 2;
+    b += align_up((size_t)seen_slots * 4, 16);
+    b += 16;
+    return align_up(b, 128);
+}
+
+__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
+    WarpSmem s;
+    s.qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 128);
+    s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * mp * 4, 128);
+    s.bkey0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    s.bkey1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    s.bref0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    s.bref1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    s.bflag0 = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
+    s.bflag1 = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
+    s.nkey = reinterpret_cast<u64 *>(p); p += 32 * 8;
+    s.nref = reinterpret_cast<u64 *>(p); p += 32 * 8;
+    s.ckey = reinterpret_cast<u64 *>(p); p += 32 * 8;
+    s.cref = reinterpret_cast<u64 *>(p); p += 32 * 8;
+    s.cid = reinterpret_cast<u32 *>(p); p += 32 * 4;
+    s.seen = reinterpret_cast<u32 *>(p); p += align_up((size_t)seen_slots * 4, 16);
+    s.bar = reinterpret_cast<u64 *>(p);
+    return s;
+}
+
+__device__ __forceinline__ u32 seen_slot(u32 id, u32 bits) { return (id * 2654435761u) >> (32 - bits); }
+
+// Evaluate the candidate ids held one per lane (NIL = none) and merge them
+// into the beam.  Returns the new beam size.  `phase` tracks the mbarrier.
+__device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, int &cur, u32 &phase,
+                          u64 &ndist, bool &timeout) {
+    const Dev &d = a.d;
+    const int lane = lane_id();
+    const u32 mp = d.mp;
+    u32 mask = __ballot_sync(FULL, my_id != NIL);
+    const int cnt = __popc(mask);
+    if (cnt == 0) return n;
+    if (my_id != NIL) s.cid[__popc(mask & lanemask_lt())] = my_id;
+    __syncwarp();
+    const u32 rowb = mp * 4;
+    for (int b0 = 0; b0 < cnt; b0 += (int)a.stage_rows) {
+        const int nb = min((int)a.stage_rows, cnt - b0);
+        if (lane == 0) {
+            // generic-proxy reads of the stage (previous batch) before async-proxy writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(s.bar, (u32)nb * rowb);
+        }
+        __syncwarp();
+        u64 rf = 0;
+        if (lane < nb) {
+            const u32 id = s.cid[b0 + lane];
+            bulk_g2s(s.stage + (size_t)lane * mp, d.x + (size_t)id * mp, rowb, s.bar);
+            rf = ld_ref(d, id);
+        }
+        if (!mbar_wait(s.bar, phase, WAIT_LIMIT)) {
+            timeout = true;
+            mbar_wait(s.bar, phase, WAIT_LIMIT);   // let copies in flight land
+        }
+        phase ^= 1u;
+        if (lane < nb) s.cref[b0 + lane] = rf;
+        // 8 lanes per distance, 4 distances per round
+        const int grp = lane >> 3, g = lane & 7;
+        for (int r0 = 0; r0 < nb; r0 += 4) {
+            const int c = r0 + grp;
+            const int cc = c < nb ? c : nb - 1;   // idle groups recompute a valid row
+            float dist = canon_dist<8>(s.qv, s.stage + (size_t)cc * mp, (int)mp, (int)d.metric, g);
+            if (c < nb && g == 0) s.ckey[b0 + c] = mkkey(dist, s.cid[b0 + c]);
+        }
+        __syncwarp();
+    }
+    ndist += cnt;
+    // this lane's candidate (sorted rank among valid keys)
+    u64 key = lane < cnt ? s.ckey[lane] : KEY_INF;
+    u64 ref = lane < cnt ? s.cref[lane] : 0;
+    if (lane < cnt) s.seen[seen_slot(key_id(key), a.seen_bits)] = key_id(key);
+    const u64 *bk = s.bkey(cur);
+    // drop keys that cannot enter a full beam, and keys already in the beam
+    if (key != KEY_INF) {
+        if (n == (int)a.L && key >= bk[n - 1]) {
+            key = KEY_INF;
+        } else {
+            int lo = 0, hi = n;                      // first beam key >= key
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (bk[mid] < key) lo = mid + 1; else hi = mid; }
+            if (lo < n && bk[lo] == key) key = KEY_INF;
+        }
+    }
+    // rank among surviving new keys (keys are distinct)
+    int rank = 0;
+    for (int j = 0; j < 32; j++) {
+        u64 o = __shfl_sync(FULL, key, j);
+        rank += (o < key);
+    }
+    const u32 vm = __ballot_sync(FULL, key != KEY_INF);
+    const int c = __popc(vm);
+    if (c == 0) return n;
+    if (key != KEY_INF) { s.nkey[rank] = key; s.nref[rank] = ref; }
+    __syncwarp();
+    const int nxt = cur ^ 1;
+    const int L = (int)a.L;
+    for (int i = lane; i < n; i += 32) {             // beam entries move down
+        u64 bkey = bk[i];
+        int lo = 0, hi = c;
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (s.nkey[mid] < bkey) lo = mid + 1; else hi = mid; }
+        int pos = i + lo;
+        if (pos < L) {
+            s.bkey(nxt)[pos] = bkey;
+            s.bref(nxt)[pos] = s.bref(cur)[i];
+            s.bflag(nxt)[pos] = s.bflag(cur)[i];
+        }
+    }
+    if (lane < c) {                                   // new entries slot in
+        u64 nk = s.nkey[lane];
+        int lo = 0, hi = n;
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (bk[mid] < nk) lo = mid + 1; else hi = mid; }
+        int pos = lane + lo;
+        if (pos < L) {
+            s.bkey(nxt)[pos] = nk;
+            s.bref(nxt)[pos] = s.nref[lane];
+            s.bflag(nxt)[pos] = 0;
+        }
+    }
+    __syncwarp();
+    cur = nxt;
+    return min(L, n + c);
+}
+
+__global__ void __launch_bounds__(128) search_kernel(SearchArgs a) {
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 mp = d.mp;
+    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, a.seen_slots);
+    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, a.seen_slots);
+    if (lane == 0) mbar_init(s.bar, 1);
+    __syncwarp();
+    u32 phase = 0;
+    u64 nexp_tot = 0, ndist = 0;
+    bool timeout = false;
+    for (;;) {
+        u32 qi = 0;
+        if (lane == 0) qi = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= a.nq) break;
+        const float *qrow = a.q + (size_t)qi * mp;
+        for (u32 i = lane * 4; i < mp; i += 128)
+            *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
+        for (u32 i = lane; i < a.seen_slots; i += 32) s.seen[i] = NIL;
+        __syncwarp();
+        int cur = 0, n = 0;
+        // seed the beam from the entry set E
+        for (u32 e0 = 0; e0 < d.n_entries; e0 += 32) {
+            u32 id = (e0 + lane < d.n_entries) ? d.entries[e0 + lane] : NIL;
+            n = eval_merge(a, s, id, n, cur, phase, ndist, timeout);
+        }
+        u32 hops = 0, nexp = 0;
+        for (;;) {
+            int first = -1;
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                int i = i0 + lane;
+                u32 m = __ballot_sync(FULL, i < n && !s.bflag(cur)[i]);
+                if (m) { first = i0 + __ffs(m) - 1; break; }
+            }
+            if (first < 0 || hops >= a.max_hops) break;
+            hops++;
+            const u64 r = s.bref(cur)[first];
+            const u64 bkey = s.bkey(cur)[first];
+            __syncwarp();
+            if (lane == 0) s.bflag(cur)[first] = 1;
+            if (a.mode == 1 && lane == 0 && !ref_del(r)) a.exp_keys[(size_t)qi * a.max_hops + nexp] = bkey;
+            if (!ref_del(r)) nexp++;
+            const u32 sl = ref_slab(r), deg = ref_deg(r);
+            __syncwarp();
+            if (sl == NIL) continue;
+            for (u32 j0 = 0; j0 < deg; j0 += 32) {
+                u32 nb = NIL;
+                if (j0 + lane < deg) {
+                    nb = d.slab[(size_t)sl * d.R + j0 + lane].x;
+                    if (s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
+                }
+                n = eval_merge(a, s, nb, n, cur, phase, ndist, timeout);
+            }
+        }
+        nexp_tot += hops;
+        if (a.mode == 0) {
+            // first k beam entries whose sampled delta is 0
+            u32 c = 0;
+            for (int i0 = 0; i0 < n && c < a.k; i0 += 32) {
+                int i = i0 + lane;
+                bool ok = i < n && !ref_del(s.bref(cur)[i]);
+                u32 m = __ballot_sync(FULL, ok);
+                u32 pos = c + __popc(m & lanemask_lt());
+                if (ok && pos < a.k) {
+                    a.out_ids[(size_t)qi * a.k + pos] = key_id(s.bkey(cur)[i]);
+                    a.out_dist[(size_t)qi * a.k + pos] = key_rho(s.bkey(cur)[i]);
+                }
+                c += __popc(m);
+            }
+            for (u32 p = c + lane; p < a.k; p += 32) {
+                a.out_ids[(size_t)qi * a.k + p] = NIL;
+                a.out_dist[(size_t)qi * a.k + p] = __int_as_float(0x7f800000);
+            }
+        } else if (lane == 0) {
+            a.exp_count[qi] = nexp;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        atomicAdd(&d.ctr[C_EXPAND], nexp_tot);
+        atomicAdd(&d.ctr[C_DIST], ndist);
+        if (timeout) atomicOr(&d.ctr[C_ERR], (u64)ERR_TIMEOUT);
+    }
+}
+
+size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
+    return 4 * search_warp_bytes(mp, L, stage_rows, seen_slots);
+}
+
+cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
+                          u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count,
+                          const SearchTuning &tune, int num_sms, cudaStream_t st) {
+    if (nq == 0) return cudaSuccess;
+    SearchArgs a;
+    a.d = d; a.q = q; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode; a.k = k;
+    a.out_ids = out_ids; a.out_dist = out_dist; a.exp_keys = exp_keys; a.exp_count = exp_count;
+    a.stage_rows = tune.stage_rows;
+    a.seen_bits = tune.seen_bits;
+    a.seen_slots = 1u << tune.seen_bits;
+    size_t smem = search_smem_bytes(d.mp, L, a.stage_rows, a.seen_slots);
+    cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u32 blocks = (u32)(per_sm * num_sms);
+    u32 need = (nq + 3) / 4;
+    if (blocks > need) blocks = need;
+    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    if (e != cudaSuccess) return e;
+    search_kernel<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace etale

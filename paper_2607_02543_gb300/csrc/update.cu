@@ -1,0 +1,859 @@
+// update.cu — RobustPrune, Publish-based update kernels: forward edges and
+// own slab (Algorithm 2), reverse-edge offers, the refine pass, tombstoning
+// and repair (Algorithm 3), compaction and reclaim (Algorithm 4).
+//
+// Deterministic mode groups offers by target (a stable radix sort by target
+// id keeps sources ascending) and lets one warp fold a target's offers in
+// order and publish once.  Lock-free mode gives each offer its own warp,
+// which snapshots the target, builds the new list and publishes it with a
+// compare-and-swap, retrying up to the attempt budget (Algorithm 1).
+#include "common.cuh"
+#include "internal.h"
+
+namespace etale {
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+// ---------------------------------------------------------------------------
+// RobustPrune over n candidates whose keys ck[0..n) are sorted ascending
+// (rho = distance to the owner).  Equal adjacent keys collapse to one.  The
+// head is kept; every later candidate p' with alpha^2 * d(head, p') <= rho(p')
+// is dropped; stop at R.  Distances between candidates are canonical
+// distances of rows in global memory.  Scratch: alive[n], idx[n].
+// ---------------------------------------------------------------------------
+__device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx,
+                          u32 *out_id, float *out_rho) {
+    const int lane = lane_id();
+    const int grp = lane >> 3, g = lane & 7;
+    for (int i = lane; i < n; i += 32) alive[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1 : 0;
+    __syncwarp();
+    int nout = 0, start = 0;
+    const int R = (int)d.R;
+    while (nout < R) {
+        int head = -1;
+        for (int i0 = start; i0 < n; i0 += 32) {
+            int i = i0 + lane;
+            u32 m = __ballot_sync(FULL, i < n && alive[i]);
+            if (m) { head = i0 + __ffs(m) - 1; break; }
+        }
+        if (head < 0) break;
+        const u64 hk = ck[head];
+        if (lane == 0) { out_id[nout] = key_id(hk); out_rho[nout] = key_rho(hk); }
+        nout++;
+        if (nout == R) break;
+        int m_cnt = 0;
+        for (int i0 = head + 1; i0 < n; i0 += 32) {
+            int i = i0 + lane;
+            bool ok = i < n && alive[i];
+            u32 m = __ballot_sync(FULL, ok);
+            if (ok) idx[m_cnt + __popc(m & lanemask_lt())] = (u32)i;
+            m_cnt += __popc(m);
+        }
+        __syncwarp();
+        const float *hrow = d.x + (size_t)key_id(hk) * d.mp;
+        for (int r0 = 0; r0 < m_cnt; r0 += 4) {
+            const int c = r0 + grp;
+            const int cc = c < m_cnt ? c : m_cnt - 1;
+            const u32 j = idx[cc];
+            const u64 kj = ck[j];
+            float dd = canon_dist<8>(hrow, d.x + (size_t)key_id(kj) * d.mp, (int)d.mp, (int)d.metric, g);
+            if (c < m_cnt && g == 0 && __fmul_rn(d.alpha2, dd) <= key_rho(kj)) alive[j] = 0;
+        }
+        __syncwarp();
+        start = head + 1;
+    }
+    __syncwarp();
+    return nout;
+}
+
+// Load N(u) into shared memory; returns the degree and the snapshot word.
+__device__ __forceinline__ int load_list(const Dev &d, u32 u, u32 *ids, float *rho, u64 &snap) {
+    const int lane = lane_id();
+    u64 r = 0;
+    if (lane == 0) r = ld_ref(d, u);
+    r = __shfl_sync(FULL, r, 0);
+    snap = r;
+    const u32 s = ref_slab(r);
+    const int n = s == NIL ? 0 : (int)ref_deg(r);
+    for (int j = lane; j < n; j += 32) {
+        uint2 e = d.slab[(size_t)s * d.R + j];
+        ids[j] = e.x;
+        rho[j] = __uint_as_float(e.y);
+    }
+    __syncwarp();
+    return n;
+}
+
+__device__ __forceinline__ bool warp_same_list(const u32 *a, const float *ar, int na, const u32 *b,
+                                               const float *br, int nb) {
+    if (na != nb) return false;
+    const int lane = lane_id();
+    bool diff = false;
+    for (int j = lane; j < na; j += 32)
+        diff |= (a[j] != b[j]) || (__float_as_uint(ar[j]) != __float_as_uint(br[j]));
+    return __ballot_sync(FULL, diff) == 0;
+}
+
+__device__ __forceinline__ bool warp_contains(const u32 *ids, int n, u32 v) {
+    bool hit = false;
+    for (int j = lane_id(); j < n; j += 32) hit |= ids[j] == v;
+    return __ballot_sync(FULL, hit) != 0;
+}
+
+// Apply one offer (v, rho) to the list in place (Algorithm 2, reverse edge):
+// a present id is a no-op; below R the entry is inserted in (rho, id) order;
+// at R the list is RobustPrune(list + v) about the owner (tombstones drop).
+// Scratch: keys[np], alive[np], idx[np] with np >= R + 1 (power of two).
+__device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, float vr, u64 *keys,
+                           unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho) {
+    const int lane = lane_id();
+    if (warp_contains(ids, n, v)) return n;
+    const u64 kv = mkkey(vr, v);
+    if (n < (int)d.R) {
+        int pos = 0;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            int j = j0 + lane;
+            pos += __popc(__ballot_sync(FULL, j < n && mkkey(rho[j], ids[j]) < kv));
+        }
+        u32 tid[2];
+        float tr[2];
+        int c = 0;
+        for (int j = pos + lane; j < n; j += 32, c++) { tid[c] = ids[j]; tr[c] = rho[j]; }
+        __syncwarp();
+        c = 0;
+        for (int j = pos + lane; j < n; j += 32, c++) { ids[j + 1] = tid[c]; rho[j + 1] = tr[c]; }
+        if (lane == 0) { ids[pos] = v; rho[pos] = vr; }
+        __syncwarp();
+        return n + 1;
+    }
+    for (int i = lane; i < np; i += 32) {
+        u64 k = KEY_INF;
+        if (i < n) {
+            if (!ref_del(ld_ref(d, ids[i]))) k = mkkey(rho[i], ids[i]);
+        } else if (i == n) {
+            k = kv;
+        }
+        keys[i] = k;
+    }
+    __syncwarp();
+    warp_sort_u64(keys, np);
+    int cn = 0;
+    for (int i0 = 0; i0 < np; i0 += 32) cn += __popc(__ballot_sync(FULL, keys[i0 + lane] != KEY_INF));
+    int nout = warp_prune(d, keys, cn, alive, idx, oid, orho);
+    for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
+    __syncwarp();
+    return nout;
+}
+
+// ---------------------------------------------------------------------------
+// Forward edges: F_v = RobustPrune(C_v) with C_v the expanded non-tombstone
+// nodes of v's search (nearest max_cand); Publish(v, F_v); emit offers.
+// ---------------------------------------------------------------------------
+struct PruneInsArgs {
+    Dev d;
+    u32 first, b;
+    const u64 *exp_keys;
+    const u32 *exp_count;
+    u32 max_hops, max_cand, np;
+    u32 *F_id;
+    float *F_rho;
+    u32 *F_n;
+    Offers of;
+};
+
+__host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R) {
+    return al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4);
+}
+
+__global__ void __launch_bounds__(128) prune_insert_kernel(PruneInsArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 R = d.R;
+    char *p = smem + warp * prune_ins_warp_bytes(a.np, R);
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
+    u32 *idx = reinterpret_cast<u32 *>(p); p += al16((size_t)a.np * 4);
+    u32 *oid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
+    float *orho = reinterpret_cast<float *>(p);
+    for (;;) {
+        u32 t = 0;
+        if (lane == 0) t = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.b) break;
+        const u32 cnt = a.exp_count[t];
+        for (u32 i = lane; i < a.np; i += 32) keys[i] = i < cnt ? a.exp_keys[(size_t)t * a.max_hops + i] : KEY_INF;
+        __syncwarp();
+        warp_sort_u64(keys, (int)a.np);
+        const int n = (int)min(cnt, a.max_cand);
+        const int nout = warp_prune(d, keys, n, alive, idx, oid, orho);
+        const u32 v = a.first + t;
+        u64 snap = 0;
+        if (lane == 0) snap = ld_ref(d, v);
+        snap = __shfl_sync(FULL, snap, 0);
+        if (!warp_publish(d, v, oid, orho, nout, snap) && lane == 0)
+            atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+        const u32 invalid = (u32)d.capacity;
+        for (u32 j = lane; j < R; j += 32) {
+            const size_t o = (size_t)t * R + j;
+            const bool ok = (int)j < nout;
+            a.F_id[o] = ok ? oid[j] : NIL;
+            a.F_rho[o] = ok ? orho[j] : 0.0f;
+            a.of.key[o] = ok ? oid[j] : invalid;
+            a.of.val[o] = (u32)o;
+            a.of.src[o] = v;
+            a.of.rho[o] = ok ? orho[j] : 0.0f;
+        }
+        if (lane == 0) a.F_n[t] = (u32)nout;
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
+                                u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
+                                const Offers &of, int num_sms, cudaStream_t st) {
+    if (b == 0) return cudaSuccess;
+    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, F_id, F_rho, F_n, of};
+    u32 np = 32;
+    while (np < max_hops) np <<= 1;
+    a.np = np;
+    size_t smem = 4 * prune_ins_warp_bytes(np, d.R);
+    cudaError_t e = cudaFuncSetAttribute(prune_insert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_insert_kernel, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u32 blocks = (u32)(per_sm * num_sms), need = (b + 3) / 4;
+    if (blocks > need) blocks = need;
+    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    if (e != cudaSuccess) return e;
+    prune_insert_kernel<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reverse offers.  Deterministic: one warp per target segment, offers in
+// ascending source order, one publish.  Lock-free: one warp per offer,
+// CAS-published with retries up to `budget` (Algorithm 1).
+// ---------------------------------------------------------------------------
+struct FoldArgs {
+    Dev d;
+    Offers of;
+    const u32 *seg_start;
+    const u64 *seg_count;
+    u32 budget;   // 0 = deterministic
+    u32 np;
+};
+
+__host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R) {
+    return 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4);
+}
+
+__global__ void __launch_bounds__(128) offer_fold_kernel(FoldArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 R = d.R;
+    char *p = smem + warp * fold_warp_bytes(a.np, R);
+    const size_t lb = al16((size_t)R * 4 + 4);
+    u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
+    float *lrho = reinterpret_cast<float *>(p); p += lb;
+    u32 *oid0 = reinterpret_cast<u32 *>(p); p += lb;
+    float *orho0 = reinterpret_cast<float *>(p); p += lb;
+    u32 *tid = reinterpret_cast<u32 *>(p); p += lb;
+    float *trho = reinterpret_cast<float *>(p); p += lb;
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
+    u32 *idx = reinterpret_cast<u32 *>(p);
+    const u64 nwork = a.budget ? (u64)a.of.n : *a.seg_count;
+    for (;;) {
+        u64 t = 0;
+        if (lane == 0) t = atomicAdd(&d.ctr[C_WORK], 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= nwork) break;
+        if (a.budget == 0) {
+            const u32 lo = a.seg_start[t], hi = a.seg_start[t + 1];
+            const u32 w = a.of.key[lo];
+            u64 snap;
+            const int n0 = load_list(d, w, lid, lrho, snap);
+            for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
+            __syncwarp();
+            int n = n0;
+            for (u32 q = lo; q < hi; q++) {
+                const u32 pi = a.of.val[q];
+                n = apply_offer(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
+                                tid, trho);
+            }
+            if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
+                if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+            }
+        } else {
+            const u32 w = a.of.key[t];
+            if (w >= (u32)d.capacity) continue;
+            const u32 v = a.of.src[t];
+            const float vr = a.of.rho[t];
+            bool done = false;
+            for (u32 att = 0; att < a.budget && !done; att++) {
+                u64 snap;
+                const int n0 = load_list(d, w, lid, lrho, snap);
+                for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
+                __syncwarp();
+                const int n = apply_offer(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho);
+                if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
+                done = warp_publish(d, w, lid, lrho, n, snap);
+                u64 err = 0;
+                if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
+                if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
+            }
+            if (!done && lane == 0) atomicAdd(&d.ctr[C_DROPPED], 1ull);
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
+                              u32 budget, int num_sms, cudaStream_t st) {
+    if (of.n == 0) return cudaSuccess;
+    FoldArgs a{d, of, seg_start, seg_count, budget, 0};
+    u32 np = 32;
+    while (np < d.R + 1) np <<= 1;
+    a.np = np;
+    size_t smem = 4 * fold_warp_bytes(np, d.R);
+    cudaError_t e = cudaFuncSetAttribute(offer_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, offer_fold_kernel, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u32 blocks = (u32)(per_sm * num_sms), need = (of.n + 3) / 4;
+    if (blocks > need) blocks = need;
+    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    if (e != cudaSuccess) return e;
+    offer_fold_kernel<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Refine pass (reading of Sec. 3.4.1): member v re-selects its edges from
+// N(v) and the lists of its neighbours (two hops; mode 2 admits only members
+// of the same sub-batch), keeps the nearest max_cand, prunes, publishes if
+// the list changed, and offers the edges it gained.
+// ---------------------------------------------------------------------------
+struct RefineArgs {
+    Dev d;
+    u32 first, b, mode, max_cand, cap, np;
+    Offers of;
+};
+
+__host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R) {
+    return 4 * al16((size_t)R * 4) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) +
+           al16((size_t)cap * 4);
+}
+
+__global__ void __launch_bounds__(64) refine_kernel(RefineArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 R = d.R;
+    char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R);
+    u32 *nid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
+    float *nrho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
+    u32 *oid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
+    float *orho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
+    u64 *buf = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
+    u32 *idx = reinterpret_cast<u32 *>(p); p += al16((size_t)a.np * 4);
+    u32 *uid = reinterpret_cast<u32 *>(p);
+    const int grp = lane >> 3, g = lane & 7;
+    for (;;) {
+        u32 t = 0;
+        if (lane == 0) t = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.b) break;
+        const u32 v = a.first + t;
+        u64 snap;
+        const int dv = load_list(d, v, nid, nrho, snap);
+        // 1. raw two-hop ids (v, members of N(v), and for mode 2 non-members
+        //    of the sub-batch excluded), kept as u64 for the sort
+        int nraw = 0;
+        bool overflow = false;
+        for (int i = 0; i < dv; i++) {
+            const u64 rw = ld_ref(d, nid[i]);
+            const u32 s = ref_slab(rw);
+            const int dw = s == NIL ? 0 : (int)ref_deg(rw);
+            for (int j0 = 0; j0 < dw; j0 += 32) {
+                u32 y = NIL;
+                if (j0 + lane < dw) y = d.slab[(size_t)s * R + j0 + lane].x;
+                bool ok = y != NIL && y != v;
+                if (ok && a.mode == 2) ok = y >= a.first && y < a.first + a.b;
+                if (ok) {
+                    for (int k = 0; k < dv; k++) ok &= nid[k] != y;
+                }
+                u32 m = __ballot_sync(FULL, ok);
+                int pos = nraw + __popc(m & lanemask_lt());
+                if (ok) {
+                    if (pos < (int)a.cap) buf[pos] = y;
+                    else overflow = true;
+                }
+                nraw += __popc(m);
+            }
+        }
+        if (__any_sync(FULL, overflow)) {
+            if (lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_OVERFLOW);
+            nraw = min(nraw, (int)a.cap);
+        }
+        int np2 = 32;
+        while (np2 < nraw) np2 <<= 1;
+        for (int i = nraw + lane; i < np2; i += 32) buf[i] = KEY_INF;
+        __syncwarp();
+        warp_sort_u64(buf, np2);
+        // 2. unique live ids
+        int nu = 0;
+        for (int i0 = 0; i0 < nraw; i0 += 32) {
+            int i = i0 + lane;
+            bool ok = i < nraw && (i == 0 || buf[i] != buf[i - 1]);
+            u32 y = ok ? (u32)buf[i] : NIL;
+            if (ok && a.mode != 2) ok = !ref_del(ld_ref(d, y));
+            u32 m = __ballot_sync(FULL, ok);
+            if (ok) uid[nu + __popc(m & lanemask_lt())] = y;
+            nu += __popc(m);
+        }
+        __syncwarp();
+        // 3. distances to v, then the live members of N(v)
+        const float *vrow = d.x + (size_t)v * d.mp;
+        for (int r0 = 0; r0 < nu; r0 += 4) {
+            const int c = r0 + grp;
+            const int cc = c < nu ? c : nu - 1;
+            const u32 y = uid[cc];
+            float dd = canon_dist<8>(vrow, d.x + (size_t)y * d.mp, (int)d.mp, (int)d.metric, g);
+            if (c < nu && g == 0) buf[c] = mkkey(dd, y);
+        }
+        __syncwarp();
+        int nc = nu;
+        for (int j0 = 0; j0 < dv; j0 += 32) {
+            int j = j0 + lane;
+            bool ok = j < dv && !ref_del(ld_ref(d, nid[j]));
+            u32 m = __ballot_sync(FULL, ok);
+            if (ok) buf[nc + __popc(m & lanemask_lt())] = mkkey(nrho[j], nid[j]);
+            nc += __popc(m);
+        }
+        int np3 = 32;
+        while (np3 < nc) np3 <<= 1;
+        for (int i = nc + lane; i < np3; i += 32) buf[i] = KEY_INF;
+        __syncwarp();
+        warp_sort_u64(buf, np3);
+        const int n = min(nc, (int)a.max_cand);
+        const int nout = warp_prune(d, buf, n, alive, idx, oid, orho);
+        if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
+            if (!warp_publish(d, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+        }
+        const u32 invalid = (u32)d.capacity;
+        for (u32 j = lane; j < R; j += 32) {
+            const size_t o = (size_t)t * R + j;
+            bool gained = false;
+            if ((int)j < nout) {
+                gained = true;
+                for (int k = 0; k < dv; k++) gained &= nid[k] != oid[j];
+            }
+            a.of.key[o] = gained ? oid[j] : invalid;
+            a.of.val[o] = (u32)o;
+            a.of.src[o] = v;
+            a.of.rho[o] = gained ? orho[j] : 0.0f;
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
+                          int num_sms, cudaStream_t st) {
+    if (b == 0) return cudaSuccess;
+    RefineArgs a;
+    a.d = d; a.first = first; a.b = b; a.mode = mode; a.max_cand = max_cand; a.of = of;
+    u32 cap = d.R * d.R;
+    if (cap > 4096) cap = 4096;
+    a.cap = cap;
+    u32 np = 32;
+    while (np < cap + d.R) np <<= 1;
+    a.np = np;
+    const size_t wb = refine_warp_bytes(np, cap, d.R);
+    const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
+    size_t smem = warps * wb;
+    cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_kernel, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u32 blocks = (u32)(per_sm * num_sms), need = (b + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    if (e != cudaSuccess) return e;
+    refine_kernel<<<blocks, 32 * warps, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Delete: tombstone CAS <0,d,s> -> <1,d,s> over ids sorted ascending; a
+// repeated, unknown, already deleted or reclaimed id is a no-op.
+// ---------------------------------------------------------------------------
+__global__ void tombstone_kernel(Dev d, const u32 *ids, u32 n, u64 next_id, u32 *ok) {
+    u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u32 u = ids[i];
+    u32 res = 0;
+    if ((i == 0 || ids[i - 1] != u) && (u64)u < next_id) {
+        for (int att = 0; att < 64; att++) {
+            const u64 r = ld_ref(d, u);
+            if (ref_del(r) || ref_slab(r) == NIL) break;
+            if (atomicCAS(&d.ref[u], r, r | (1ull << 63)) == r) { res = 1; break; }
+        }
+    }
+    ok[i] = res;
+}
+
+cudaError_t launch_tombstone(const Dev &d, const u32 *sorted_ids, u32 n, u64 next_id, u32 *ok, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    tombstone_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, sorted_ids, n, next_id, ok);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Repair, step 1: for deleted u with B = N(u) and each live a in B,
+// K(u, a) = RobustPrune_a(B \ {a}).  The distances among B are computed once
+// per u into a table; the prune reads the table.
+// ---------------------------------------------------------------------------
+struct RepairKArgs {
+    Dev d;
+    const u32 *dt;
+    const u64 *n_dt;
+    u32 max_n;
+    u32 *pair_key, *pair_val;
+    uint2 *pair_K;
+    u32 *pair_Kn;
+};
+
+__host__ __device__ inline size_t repk_warp_bytes(u32 R) {
+    return 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)R * 8 * 2) + al16(2 * R);
+}
+
+__global__ void __launch_bounds__(128) repair_k_kernel(RepairKArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 R = d.R;
+    char *p = smem + warp * repk_warp_bytes(R);
+    u32 *bid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
+    u32 *bdel = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
+    u32 *cj = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
+    float *M = reinterpret_cast<float *>(p); p += al16((size_t)R * R * 4);
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)R * 8 * 2);
+    unsigned char *alive = reinterpret_cast<unsigned char *>(p);
+    const int grp = lane >> 3, g = lane & 7;
+    const u64 nd = *a.n_dt;
+    const u32 invalid = (u32)d.capacity;
+    int npk = 32;
+    while (npk < (int)R) npk <<= 1;
+    for (;;) {
+        u64 i = 0;
+        if (lane == 0) i = atomicAdd(&d.ctr[C_WORK], 1ull);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= nd) break;
+        const u32 u = a.dt[i];
+        u64 r = 0;
+        if (lane == 0) r = ld_ref(d, u);
+        r = __shfl_sync(FULL, r, 0);
+        const u32 s = ref_slab(r);
+        const int nb = s == NIL ? 0 : (int)ref_deg(r);
+        for (int j = lane; j < nb; j += 32) {
+            bid[j] = d.slab[(size_t)s * R + j].x;
+            bdel[j] = ref_del(ld_ref(d, bid[j]));
+        }
+        __syncwarp();
+        // distance table among B (symmetric)
+        for (int x = 0; x < nb; x++) {
+            const float *xr = d.x + (size_t)bid[x] * d.mp;
+            for (int y0 = x + 1; y0 < nb; y0 += 4) {
+                const int y = y0 + grp;
+                const int yy = y < nb ? y : nb - 1;
+                float dd = canon_dist<8>(xr, d.x + (size_t)bid[yy] * d.mp, (int)d.mp, (int)d.metric, g);
+                if (y < nb && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
+            }
+        }
+        __syncwarp();
+        for (int ja = 0; ja < (int)R; ja++) {
+            const size_t slot = (size_t)i * R + ja;
+            if (ja >= nb || bdel[ja]) {
+                if (lane == 0) { a.pair_key[slot] = invalid; a.pair_val[slot] = (u32)slot; a.pair_Kn[slot] = 0; }
+                continue;
+            }
+            // candidates b in B, b != a, live; key (d(a, b), b), payload index jb
+            for (int t = lane; t < npk; t += 32) {
+                u64 k = KEY_INF;
+                if (t < nb && t != ja && !bdel[t]) k = mkkey(M[ja * R + t], bid[t]);
+                keys[t] = k;
+            }
+            __syncwarp();
+            warp_sort_u64(keys, npk);
+            int nc = 0;
+            for (int t0 = 0; t0 < npk; t0 += 32) nc += __popc(__ballot_sync(FULL, keys[t0 + lane] != KEY_INF));
+            // table index of each sorted candidate
+            for (int t = lane; t < nc; t += 32) {
+                const u32 id = key_id(keys[t]);
+                u32 jb = 0;
+                for (int q = 0; q < nb; q++) if (bid[q] == id) jb = (u32)q;
+                cj[t] = jb;
+                alive[t] = 1;
+            }
+            __syncwarp();
+            int nk = 0, start = 0;
+            while (nk < (int)R) {
+                int head = -1;
+                for (int t0 = start; t0 < nc; t0 += 32) {
+                    int t = t0 + lane;
+                    u32 m = __ballot_sync(FULL, t < nc && alive[t]);
+                    if (m) { head = t0 + __ffs(m) - 1; break; }
+                }
+                if (head < 0) break;
+                if (lane == 0) {
+                    const u64 hk = keys[head];
+                    a.pair_K[slot * R + nk] = make_uint2(key_id(hk), __float_as_uint(key_rho(hk)));
+                }
+                nk++;
+                if (nk == (int)R) break;
+                const u32 hj = cj[head];
+                for (int t = head + 1 + lane; t < nc; t += 32) {
+                    if (alive[t] && __fmul_rn(d.alpha2, M[hj * R + cj[t]]) <= key_rho(keys[t])) alive[t] = 0;
+                }
+                __syncwarp();
+                start = head + 1;
+            }
+            if (lane == 0) { a.pair_key[slot] = bid[ja]; a.pair_val[slot] = (u32)slot; a.pair_Kn[slot] = (u32)nk; }
+            __syncwarp();
+        }
+    }
+}
+
+cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
+                            u32 *pair_val, uint2 *pair_K, u32 *pair_Kn, int num_sms, cudaStream_t st) {
+    if (max_n == 0) return cudaSuccess;
+    RepairKArgs a{d, dt, n_dt, max_n, pair_key, pair_val, pair_K, pair_Kn};
+    size_t smem = 4 * repk_warp_bytes(d.R);
+    cudaError_t e = cudaFuncSetAttribute(repair_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_k_kernel, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u32 blocks = (u32)(per_sm * num_sms), need = (max_n + 3) / 4;
+    if (blocks > need) blocks = need;
+    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    if (e != cudaSuccess) return e;
+    repair_k_kernel<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Repair, step 2: for each live a, in ascending u:
+// N <- RobustPrune_a((N \ {u}) + K(u, a)); publish once if changed.
+// Lock-free mode (seg_start == NULL): one warp per (u, a) pair, CAS retries.
+// ---------------------------------------------------------------------------
+struct RepairFoldArgs {
+    Dev d;
+    const u32 *dt, *pair_key, *pair_val;
+    const uint2 *pair_K;
+    const u32 *pair_Kn;
+    const u32 *seg_start;
+    const u64 *seg_count;
+    u64 n_pairs;
+    u32 budget, np;
+};
+
+__host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R) {
+    return 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4);
+}
+
+__device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
+                            unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho) {
+    const int lane = lane_id();
+    for (int i = lane; i < np; i += 32) {
+        u64 k = KEY_INF;
+        if (i < n) {
+            if (lid[i] != u && !ref_del(ld_ref(d, lid[i]))) k = mkkey(lrho[i], lid[i]);
+        } else if (i < n + nk) {
+            const uint2 e = K[i - n];
+            if (!ref_del(ld_ref(d, e.x))) k = mkkey(__uint_as_float(e.y), e.x);
+        }
+        keys[i] = k;
+    }
+    __syncwarp();
+    warp_sort_u64(keys, np);
+    int cn = 0;
+    for (int i0 = 0; i0 < np; i0 += 32) cn += __popc(__ballot_sync(FULL, keys[i0 + lane] != KEY_INF));
+    const int nout = warp_prune(d, keys, cn, alive, idx, tid, trho);
+    for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
+    __syncwarp();
+    return nout;
+}
+
+__global__ void __launch_bounds__(128) repair_fold_kernel(RepairFoldArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 R = d.R;
+    char *p = smem + warp * repf_warp_bytes(a.np, R);
+    const size_t lb = al16((size_t)R * 4 + 4);
+    u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
+    float *lrho = reinterpret_cast<float *>(p); p += lb;
+    u32 *oid0 = reinterpret_cast<u32 *>(p); p += lb;
+    float *orho0 = reinterpret_cast<float *>(p); p += lb;
+    u32 *tid = reinterpret_cast<u32 *>(p); p += lb;
+    float *trho = reinterpret_cast<float *>(p); p += lb;
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
+    u32 *idx = reinterpret_cast<u32 *>(p);
+    const u64 nwork = a.budget ? a.n_pairs : *a.seg_count;
+    for (;;) {
+        u64 t = 0;
+        if (lane == 0) t = atomicAdd(&d.ctr[C_WORK], 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= nwork) break;
+        if (a.budget == 0) {
+            const u32 lo = a.seg_start[t], hi = a.seg_start[t + 1];
+            const u32 w = a.pair_key[lo];
+            u64 snap;
+            const int n0 = load_list(d, w, lid, lrho, snap);
+            for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
+            __syncwarp();
+            int n = n0;
+            for (u32 q = lo; q < hi; q++) {
+                const u32 pv = a.pair_val[q];
+                n = repair_apply(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
+                                 alive, idx, (int)a.np, tid, trho);
+            }
+            if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
+                if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+            }
+        } else {
+            const u32 w = a.pair_key[t];
+            if (w >= (u32)d.capacity) continue;
+            const u32 pv = a.pair_val[t];
+            bool done = false;
+            for (u32 att = 0; att < a.budget && !done; att++) {
+                u64 snap;
+                const int n0 = load_list(d, w, lid, lrho, snap);
+                for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
+                __syncwarp();
+                const int n = repair_apply(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
+                                           (int)a.pair_Kn[pv], keys, alive, idx, (int)a.np, tid, trho);
+                if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
+                done = warp_publish(d, w, lid, lrho, n, snap);
+                u64 err = 0;
+                if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
+                if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
+            }
+            if (!done && lane == 0) atomicAdd(&d.ctr[C_DROPPED], 1ull);
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key, const u32 *pair_val,
+                                    const uint2 *pair_K, const u32 *pair_Kn, const u32 *seg_start,
+                                    const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0};
+    u32 np = 32;
+    while (np < 2 * d.R) np <<= 1;
+    a.np = np;
+    size_t smem = 4 * repf_warp_bytes(np, d.R);
+    cudaError_t e = cudaFuncSetAttribute(repair_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_fold_kernel, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    u64 need = (n_pairs + 3) / 4;
+    u32 blocks = (u32)(per_sm * num_sms);
+    if ((u64)blocks > need) blocks = (u32)need;
+    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    if (e != cudaSuccess) return e;
+    repair_fold_kernel<<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reclaim phase 1 (compaction): every live node with a tombstoned neighbour
+// republishes its list without those entries, order and rho kept.  One warp
+// per 32 consecutive ids; tombstones are read from a bitmap.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const u32 *tomb_bits) {
+    __shared__ u32 sid[8][MAX_R];
+    __shared__ float srho[8][MAX_R];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const u64 base = ((u64)blockIdx.x * 8 + warp) * 32;
+    if (base >= next_id) return;
+    const u64 myid = base + lane;
+    const u64 myref = myid < next_id ? ld_ref(d, (u32)myid) : ref_pack(1, 0, NIL);
+    const u32 R = d.R;
+    for (int t = 0; t < 32; t++) {
+        const u64 r = __shfl_sync(FULL, myref, t);
+        if (ref_del(r) || ref_slab(r) == NIL) continue;
+        const u32 s = ref_slab(r);
+        const int n = (int)ref_deg(r);
+        bool dirty = false;
+        u32 ids[2];
+        float rhos[2];
+        bool keep[2];
+        int c = 0;
+        for (int j = lane; j < n; j += 32, c++) {
+            uint2 e = d.slab[(size_t)s * R + j];
+            ids[c] = e.x;
+            rhos[c] = __uint_as_float(e.y);
+            const bool dead = (tomb_bits[e.x >> 5] >> (e.x & 31)) & 1u;
+            keep[c] = !dead;
+            dirty |= dead;
+        }
+        if (!__any_sync(FULL, dirty)) continue;
+        int nk = 0;
+        c = 0;
+        for (int j0 = 0; j0 < n; j0 += 32, c++) {
+            const int j = j0 + lane;
+            const bool k = j < n && keep[c];
+            const u32 m = __ballot_sync(FULL, k);
+            if (k) { sid[warp][nk + __popc(m & lanemask_lt())] = ids[c]; srho[warp][nk + __popc(m & lanemask_lt())] = rhos[c]; }
+            nk += __popc(m);
+        }
+        __syncwarp();
+        // a lost CAS here means another writer touched the node during the
+        // reclaim launch, which the launch discipline forbids
+        if (!warp_publish(d, (u32)(base + t), sid[warp], srho[warp], nk, r) && lane == 0)
+            atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_compact(const Dev &d, u64 next_id, const u32 *tomb_bits, cudaStream_t st) {
+    if (next_id == 0) return cudaSuccess;
+    u64 warps = (next_id + 31) / 32;
+    compact_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(d, next_id, tomb_bits);
+    return cudaGetLastError();
+}
+
+// Reclaim phase 2: CAS <1,d,s> -> <1,0,NIL> and retire s.
+__global__ void reclaim_tomb_kernel(Dev d, u64 next_id) {
+    const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= next_id) return;
+    const u64 r = ld_ref(d, (u32)u);
+    if (!ref_del(r) || ref_slab(r) == NIL) return;
+    if (atomicCAS(&d.ref[u], r, ref_pack(1, 0, NIL)) == r) retire_slab(d, ref_slab(r));
+    else atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+}
+
+cudaError_t launch_reclaim_tombstones(const Dev &d, u64 next_id, cudaStream_t st) {
+    if (next_id == 0) return cudaSuccess;
+    reclaim_tomb_kernel<<<(unsigned)((next_id + 255) / 256), 256, 0, st>>>(d, next_id);
+    return cudaGetLastError();
+}
+
+}  // namespace etale

@@ -1,0 +1,446 @@
+// util.cu — scans, a stable LSD radix sort, segmenting, the pool recycle
+// step, ingest, entry-set selection, brute-force ground truth and graph
+// export.
+#include "common.cuh"
+#include "internal.h"
+
+namespace etale {
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of u32, 2048 elements per block, recursive on block sums.
+// ---------------------------------------------------------------------------
+constexpr u32 SCAN_TILE = 2048;
+
+__global__ void __launch_bounds__(256) scan_tile_kernel(const u32 *in, u32 *out, u32 n, u32 *sums) {
+    __shared__ u32 wsum[8];
+    const u32 base = blockIdx.x * SCAN_TILE;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    u32 v[8];
+    u32 tot = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const u32 i = base + tid * 8 + k;
+        v[k] = i < n ? in[i] : 0u;
+        tot += v[k];
+    }
+    u32 incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    u32 woff = 0;
+    for (int w = 0; w < warp; w++) woff += wsum[w];
+    u32 run = woff + incl - tot;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const u32 i = base + tid * 8 + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (tid == 255 && sums) sums[blockIdx.x] = woff + incl;
+}
+
+__global__ void scan_add_kernel(u32 *out, u32 n, const u32 *offs) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / SCAN_TILE];
+}
+
+size_t scan_scratch_elems(u32 n) {
+    size_t tot = 0;
+    u32 m = n;
+    for (int l = 0; l < 4 && m > SCAN_TILE; l++) {
+        m = (m + SCAN_TILE - 1) / SCAN_TILE;
+        tot += m;
+    }
+    return tot + 16;
+}
+
+void scan_scratch_carve(ScanScratch &s, u32 *buf, u32 n) {
+    s.levels = 0;
+    u32 m = n;
+    while (m > SCAN_TILE && s.levels < 4) {
+        m = (m + SCAN_TILE - 1) / SCAN_TILE;
+        s.lvl[s.levels] = buf;
+        s.lvl_n[s.levels] = m;
+        buf += m;
+        s.levels++;
+    }
+}
+
+static cudaError_t scan_rec(const u32 *in, u32 *out, u32 n, const ScanScratch &s, int level, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const u32 tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 1) {
+        scan_tile_kernel<<<1, 256, 0, st>>>(in, out, n, nullptr);
+        return cudaGetLastError();
+    }
+    if (level >= s.levels) return cudaErrorInvalidValue;
+    u32 *sums = s.lvl[level];
+    scan_tile_kernel<<<tiles, 256, 0, st>>>(in, out, n, sums);
+    cudaError_t e = scan_rec(sums, sums, tiles, s, level + 1, st);
+    if (e != cudaSuccess) return e;
+    scan_add_kernel<<<(n + 255) / 256, 256, 0, st>>>(out, n, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan(const u32 *in, u32 *out, u32 n, const ScanScratch &s, cudaStream_t st) {
+    return scan_rec(in, out, n, s, 0, st);
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, 8 bits per pass.  A block (8 warps) owns a tile of
+// 2048 keys; warp w owns keys [256w, 256w + 256) of the tile and walks them
+// in order, so ranks inside a bucket follow the input order.
+// ---------------------------------------------------------------------------
+constexpr u32 SORT_TILE = 2048;
+
+__global__ void __launch_bounds__(256) radix_hist_kernel(const u32 *key, u32 n, u32 shift, u32 *hist, u32 tiles) {
+    __shared__ u32 h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const u32 base = blockIdx.x * SORT_TILE;
+    for (u32 i = threadIdx.x; i < SORT_TILE; i += 256) {
+        const u32 g = base + i;
+        if (g < n) atomicAdd(&h[(key[g] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) radix_scatter_kernel(const u32 *kin, const u32 *vin, u32 *kout, u32 *vout,
+                                                            u32 n, u32 shift, const u32 *offs, u32 tiles) {
+    __shared__ u32 wc[8][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 8 * 256; i += 256) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const u32 base = blockIdx.x * SORT_TILE + warp * 256;
+    for (int s = 0; s < 8; s++) {
+        const u32 g = base + s * 32 + lane;
+        if (g < n) atomicAdd(&wc[warp][(kin[g] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps, per bucket, plus the block's global offset
+        const int b = tid;
+        u32 run = offs[b * tiles + blockIdx.x];
+        for (int w = 0; w < 8; w++) {
+            const u32 c = wc[w][b];
+            wc[w][b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int s = 0; s < 8; s++) {
+        const u32 g = base + s * 32 + lane;
+        const bool ok = g < n;
+        const u32 k = ok ? kin[g] : 0u;
+        const u32 dg = ok ? ((k >> shift) & 255u) : 256u + lane;   // idle lanes get private buckets
+        const u32 peers = __match_any_sync(FULL, dg);
+        const u32 rank = __popc(peers & lanemask_lt());
+        if (ok) {
+            const u32 pos = wc[warp][dg] + rank;
+            kout[pos] = k;
+            vout[pos] = vin[g];
+        }
+        __syncwarp();
+        if (ok && rank == 0) wc[warp][dg] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+size_t sort_scratch_elems(u32 n) {
+    const u32 tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    return 2 * (size_t)256 * tiles + scan_scratch_elems(256 * tiles) + 32;
+}
+
+void sort_scratch_carve(SortScratch &s, u32 *buf, u32 n) {
+    const u32 tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    s.hist = buf;
+    s.hist_scan = buf + 256 * tiles;
+    scan_scratch_carve(s.scan, buf + 2 * 256 * tiles, 256 * tiles);
+}
+
+cudaError_t radix_sort_pairs(u32 *key, u32 *val, u32 *key_alt, u32 *val_alt, u32 n, u32 key_bits,
+                             const SortScratch &s, cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    const u32 tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    const u32 passes = (key_bits + 7) / 8;
+    u32 *ki = key, *vi = val, *ko = key_alt, *vo = val_alt;
+    for (u32 p = 0; p < passes; p++) {
+        const u32 shift = 8 * p;
+        radix_hist_kernel<<<tiles, 256, 0, st>>>(ki, n, shift, s.hist, tiles);
+        cudaError_t e = exclusive_scan(s.hist, s.hist_scan, 256 * tiles, s.scan, st);
+        if (e != cudaSuccess) return e;
+        radix_scatter_kernel<<<tiles, 256, 0, st>>>(ki, vi, ko, vo, n, shift, s.hist_scan, tiles);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        u32 *t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    if (ki != key) {
+        cudaError_t e = cudaMemcpyAsync(key, ki, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(val, vi, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Segments of equal keys in a sorted array.
+// ---------------------------------------------------------------------------
+__global__ void seg_flags_kernel(const u32 *key, u32 n, u32 invalid, u32 *flags) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u32 k = key[i];
+    flags[i] = (k != invalid && (i == 0 || key[i - 1] != k)) ? 1u : 0u;
+}
+
+__global__ void seg_write_kernel(const u32 *key, u32 n, u32 invalid, const u32 *flags, const u32 *scan,
+                                 u32 *seg_start, u64 *seg_count) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flags[i]) seg_start[scan[i]] = i;
+    const bool last_valid = key[i] != invalid && (i + 1 == n || key[i + 1] == invalid);
+    if (last_valid) {
+        const u32 cnt = scan[i] + flags[i];
+        seg_start[cnt] = i + 1;
+        *seg_count = cnt;
+    }
+    if (i == 0 && key[0] == invalid) *seg_count = 0;
+}
+
+cudaError_t make_segments(const u32 *key, u32 n, u32 invalid, u32 *flags, u32 *scan_out, u32 *seg_start,
+                          u64 *seg_count, const ScanScratch &s, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(seg_count, 0, sizeof(u64), st);
+    if (e != cudaSuccess || n == 0) return e;
+    seg_flags_kernel<<<(n + 255) / 256, 256, 0, st>>>(key, n, invalid, flags);
+    e = exclusive_scan(flags, scan_out, n, s, st);
+    if (e != cudaSuccess) return e;
+    seg_write_kernel<<<(n + 255) / 256, 256, 0, st>>>(key, n, invalid, flags, scan_out, seg_start, seg_count);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Host-ordered recycle between launches: retired stack -> free stack.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) recycle_kernel(Dev d) {
+    __shared__ u64 sh[3];
+    if (threadIdx.x == 0) {
+        const u64 nfree = d.ctr[C_FREE];
+        const u64 pops = d.ctr[C_POP] < nfree ? d.ctr[C_POP] : nfree;
+        sh[0] = nfree - pops;
+        sh[1] = d.ctr[C_RET];
+    }
+    __syncthreads();
+    const u64 base = sh[0], nret = sh[1];
+    for (u64 i = threadIdx.x; i < nret; i += 1024) d.free_stack[base + i] = d.retired[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.ctr[C_FREE] = base + nret;
+        d.ctr[C_POP] = 0;
+        d.ctr[C_RET] = 0;
+    }
+}
+
+cudaError_t launch_recycle(const Dev &d, cudaStream_t st) {
+    recycle_kernel<<<1, 1024, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+// Copy n rows of dim floats into rows of mp floats, zero padding.
+__global__ void ingest_kernel(float *x, u32 mp, const float *src, u32 dim, u64 n) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * mp) return;
+    const u64 r = i / mp, c = i % mp;
+    x[i] = c < dim ? src[r * dim + c] : 0.0f;
+}
+
+cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const u64 tot = n * mp;
+    ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, mp, src, dim, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Entry set: the live ids of rank floor(j * L / S), j = 0..S-1.
+// ---------------------------------------------------------------------------
+__global__ void live_flags_kernel(Dev d, u64 next_id, u32 *flags) {
+    const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= next_id) return;
+    const u64 r = d.ref[u];
+    flags[u] = (!ref_del(r) && ref_slab(r) != NIL) ? 1u : 0u;
+}
+
+cudaError_t launch_live_flags(const Dev &d, u64 next_id, u32 *flags, cudaStream_t st) {
+    if (next_id == 0) return cudaSuccess;
+    live_flags_kernel<<<(unsigned)((next_id + 255) / 256), 256, 0, st>>>(d, next_id, flags);
+    return cudaGetLastError();
+}
+
+__global__ void entries_select_kernel(Dev d, u64 next_id, const u32 *flags, const u32 *rank, u64 L, u32 S) {
+    const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= next_id || !flags[u]) return;
+    const u64 r = rank[u];
+    const u64 j = (r * S + L - 1) / L;        // smallest j with j * L / S >= r
+    if (j < S && (j * L) / S == r) d.entries[j] = (u32)u;
+}
+
+cudaError_t launch_entries_select(const Dev &d, u64 next_id, const u32 *flags, const u32 *rank, u64 live, u32 S,
+                                  cudaStream_t st) {
+    if (next_id == 0 || S == 0) return cudaSuccess;
+    entries_select_kernel<<<(unsigned)((next_id + 255) / 256), 256, 0, st>>>(d, next_id, flags, rank, live, S);
+    return cudaGetLastError();
+}
+
+// One bit per id: delta of the reference word.
+__global__ void tomb_bits_kernel(Dev d, u64 next_id, u32 *bits) {
+    const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 nw = (next_id + 31) / 32;
+    if (u >= nw * 32) return;
+    const bool del = u < next_id && ref_del(d.ref[u]);
+    const u32 m = __ballot_sync(FULL, del);
+    if ((threadIdx.x & 31) == 0) bits[u >> 5] = m;
+}
+
+cudaError_t launch_tomb_bits(const Dev &d, u64 next_id, u32 *bits, cudaStream_t st) {
+    if (next_id == 0) return cudaSuccess;
+    const u64 tot = (next_id + 31) / 32 * 32;
+    tomb_bits_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, next_id, bits);
+    return cudaGetLastError();
+}
+
+// Stable compaction of ids whose flag is set.
+__global__ void compact_ok_kernel(const u32 *ids, const u32 *flags, const u32 *scan, u32 n, u32 *out, u64 *count) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flags[i]) out[scan[i]] = ids[i];
+    if (i == n - 1) *count = scan[i] + flags[i];
+}
+
+cudaError_t launch_compact_ok(const u32 *ids, const u32 *flags, const u32 *scan, u32 n, u32 *out, u64 *count,
+                              cudaStream_t st) {
+    if (n == 0) return cudaMemsetAsync(count, 0, sizeof(u64), st);
+    compact_ok_kernel<<<(n + 255) / 256, 256, 0, st>>>(ids, flags, scan, n, out, count);
+    return cudaGetLastError();
+}
+
+__global__ void fill_keys_kernel(u32 *key, u32 *val, u32 n, u32 invalid) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = invalid;
+    val[i] = i;
+}
+
+cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    fill_keys_kernel<<<(n + 255) / 256, 256, 0, st>>>(key, val, n, invalid);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Brute-force exact k nearest live nodes (k <= 32), canonical distances.
+// A block of 8 warps owns 8 queries; rows are streamed through shared memory
+// in tiles shared by the 8 warps; each warp keeps its top-k in a sorted
+// register list (one key per lane).
+// ---------------------------------------------------------------------------
+constexpr int GT_TILE = 32;
+
+__global__ void __launch_bounds__(256) gt_kernel(Dev d, u64 next_id, const float *q, u32 nq, u32 k, u32 *out_ids,
+                                                 float *out_dist) {
+    extern __shared__ __align__(16) float gsm[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const u32 mp = d.mp;
+    float *rows = gsm;                               // GT_TILE x mp
+    float *qv = gsm + GT_TILE * mp + warp * mp;      // 8 x mp
+    __shared__ u64 rref[GT_TILE];
+    const u32 qi = blockIdx.x * 8 + warp;
+    const bool active = qi < nq;
+    if (active)
+        for (u32 i = lane * 4; i < mp; i += 128)
+            *reinterpret_cast<float4 *>(qv + i) = *reinterpret_cast<const float4 *>(q + (size_t)qi * mp + i);
+    u64 best = KEY_INF;   // lane j holds the j-th smallest key (sorted across lanes)
+    const int grp = lane >> 3, g = lane & 7;
+    for (u64 t0 = 0; t0 < next_id; t0 += GT_TILE) {
+        __syncthreads();
+        const int nrow = (int)min((u64)GT_TILE, next_id - t0);
+        for (int i = threadIdx.x; i < nrow * (int)(mp / 4); i += 256) {
+            const int r = i / (mp / 4), c = i % (mp / 4);
+            reinterpret_cast<float4 *>(rows + (size_t)r * mp)[c] =
+                reinterpret_cast<const float4 *>(d.x + (t0 + r) * mp)[c];
+        }
+        if (threadIdx.x < nrow) rref[threadIdx.x] = d.ref[t0 + threadIdx.x];
+        __syncthreads();
+        if (!active) continue;
+        u64 cand = KEY_INF;
+        for (int r0 = 0; r0 < nrow; r0 += 4) {
+            const int r = r0 + grp;
+            const int rr = r < nrow ? r : nrow - 1;
+            float dd = canon_dist<8>(qv, rows + (size_t)rr * mp, (int)mp, (int)d.metric, g);
+            // lane (r - r0) * 8 + 0 holds row r's distance; gather into lane r
+            const u64 rf = rref[rr];
+            const bool live = r < nrow && !ref_del(rf) && ref_slab(rf) != NIL;
+            const u64 kk = live ? mkkey(dd, (u32)(t0 + r)) : KEY_INF;
+            for (int t = 0; t < 4; t++) {
+                u64 v = __shfl_sync(FULL, kk, t * 8);
+                if (lane == r0 + t) cand = v;
+            }
+        }
+        // merge 32 candidates into the sorted best list: sort candidates,
+        // then take the k smallest of the union via a bitonic merge step
+        cand = warp_sort32(cand);
+        u64 rev = __shfl_sync(FULL, cand, 31 - lane);
+        u64 lo = best < rev ? best : rev;          // bitonic: lo holds the 32 smallest
+        best = warp_sort32(lo);
+    }
+    if (active && lane < (int)k) {
+        out_ids[(size_t)qi * k + lane] = best == KEY_INF ? NIL : key_id(best);
+        out_dist[(size_t)qi * k + lane] = best == KEY_INF ? __int_as_float(0x7f800000) : key_rho(best);
+    }
+}
+
+cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 nq, u32 k, u32 *out_ids,
+                                float *out_dist, int num_sms, cudaStream_t st) {
+    if (nq == 0) return cudaSuccess;
+    if (k > 32) return cudaErrorInvalidValue;
+    size_t smem = (size_t)(GT_TILE + 8) * d.mp * 4;
+    cudaError_t e = cudaFuncSetAttribute(gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gt_kernel<<<(nq + 7) / 8, 256, smem, st>>>(d, next_id, q, nq, k, out_ids, out_dist);
+    return cudaGetLastError();
+}
+
+// Logical graph export.
+__global__ void export_kernel(Dev d, u64 n, unsigned char *del, unsigned char *hs, unsigned char *deg, u32 *ids,
+                              float *rho) {
+    const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    const u64 r = d.ref[u];
+    const u32 s = ref_slab(r);
+    const u32 dg = s == NIL ? 0 : ref_deg(r);
+    del[u] = (unsigned char)ref_del(r);
+    hs[u] = s != NIL;
+    deg[u] = (unsigned char)dg;
+    for (u32 j = 0; j < d.R; j++) {
+        if (j < dg) {
+            const uint2 e = d.slab[(size_t)s * d.R + j];
+            ids[u * d.R + j] = e.x;
+            rho[u * d.R + j] = __uint_as_float(e.y);
+        } else {
+            ids[u * d.R + j] = NIL;
+            rho[u * d.R + j] = 0.0f;
+        }
+    }
+}
+
+cudaError_t launch_export(const Dev &d, u64 n, unsigned char *del, unsigned char *hs, unsigned char *deg, u32 *ids,
+                          float *rho, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    export_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d, n, del, hs, deg, ids, rho);
+    return cudaGetLastError();
+}
+
+}  // namespace etale

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA index (through the C ABI) against the oracle.
+
+Deterministic mode must reproduce the oracle's logical graph bit for bit
+(ids, degrees, deletion flags, and the fp32 bits of every stored distance)
+and its search results; lock-free mode must keep every invariant and stay
+within 0.005 Recall@10 of the oracle.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2607_02543_gb300 import workloads as W
+from tests.graph_checks import check_graph, recall_at_k, NIL
+from tests.pair import make_pair, graphs_equal, churn_round
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "line5_hand.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2607_02543_gb300 import build
+    build.build()
+
+
+def _assert_same_graph(g, o, R, where):
+    probs = graphs_equal(g.export_graph(), o.dump(), R)
+    assert not probs, f"{where}: " + "; ".join(probs)
+
+
+def test_hand_derived_line(oracle_mod):
+    gold = json.load(open(GOLD))
+    g, o = make_pair(oracle_mod, gold["dim"], "l2", gold["degree"], 100, build_beam=gold["build_beam"],
+                     alpha=gold["alpha"], refine="off", max_batch=gold["max_batch"], n_entry=gold["n_entry"])
+    X = np.zeros((5, gold["dim"]), np.float32)
+    X[:, 0] = gold["points_x"]
+    assert g.insert(X).tolist() == [0, 1, 2, 3, 4]
+    o.insert(X)
+    de, hs, dg, ids, rho = g.export_graph()
+    for u, (nb, rr) in gold["after_inserts"].items():
+        u = int(u)
+        assert ids[u, :dg[u]].tolist() == nb and rho[u, :dg[u]].tolist() == [float(x) for x in rr]
+    assert g.delete(np.array(gold["delete"], np.uint32)) == 1
+    de, hs, dg, ids, rho = g.export_graph()
+    for u, (nb, rr) in gold["after_delete"].items():
+        u = int(u)
+        assert ids[u, :dg[u]].tolist() == nb and rho[u, :dg[u]].tolist() == [float(x) for x in rr]
+    assert de.tolist() == gold["deleted_flags_after_delete"]
+    g.reclaim()
+    s = g.stats()
+    assert s["live"] == gold["after_reclaim_live"] and s["used_slabs"] == gold["after_reclaim_used_slabs"]
+    q = np.zeros((1, gold["dim"]), np.float32)
+    q[0, 0] = gold["query_x"]
+    rid, rd = g.search(q, gold["k"], gold["beam"])
+    assert rid[0].tolist() == gold["query_result"][0]
+    assert rd[0].tolist() == [float(x) for x in gold["query_result"][1]]
+
+
+CASES = [
+    # (dim, metric, degree, kind, n_base, build_beam)
+    (128, "l2", 32, "gauss", 2000, 64),      # several tiles of every kernel
+    (37, "l2", 16, "gauss", 900, 32),        # ragged dimension (rows padded to 40)
+    (96, "ip", 64, "unit", 1200, 64),        # inner product, degree 64 (two slab chunks)
+    (128, "l2", 32, "int", 1500, 96),        # integer-valued (exact distances)
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"d{c[0]}-{c[1]}-R{c[2]}-{c[3]}")
+def test_deterministic_parity(oracle_mod, case):
+    dim, metric, R, kind, n, beam = case
+    w = W.Workload(f"parity-{kind}", n, dim, metric, R, beam, 3, max(1, n // 100), max(1, n // 100), 300, 10,
+                   beam, 16, kind)
+    plan = W.make_plan(w)
+    g, o = make_pair(oracle_mod, dim, metric, R, w.capacity, build_beam=beam)
+    gi = g.insert(plan.base)
+    oi = o.insert(plan.base)
+    assert gi.tolist() == oi.tolist()
+    g.reclaim(); o.reclaim()
+    _assert_same_graph(g, o, R, "after build")
+    assert g.entries().tolist() == o.entries().tolist()
+    for r in range(w.rounds):
+        dele, ng, no, _, _ = churn_round(g, o, plan, r, w.n_delete)
+        assert ng == no == dele.size
+        _assert_same_graph(g, o, R, f"after round {r}")
+    gs, gd = g.search(plan.queries, w.k, w.search_beam)
+    os_, od = o.search(plan.queries, w.k, w.search_beam)
+    assert (gs == os_).all()
+    assert (gd.view(np.uint32) == od.view(np.uint32)).all()
+    s = g.stats()
+    assert s["used_slabs"] == s["live"] and s["tombstones"] == 0
+
+
+def test_small_workload_full(oracle_mod):
+    """The 10,000 x 128 mixture workload: build, 5 rounds of 100 + 100 churn,
+    1,000 queries (k = 10, beam 64) after every round, deterministic mode."""
+    w = W.SMALL
+    plan = W.make_plan(w)
+    g, o = make_pair(oracle_mod, w.dim, w.metric, w.degree, w.capacity, build_beam=w.build_beam)
+    g.insert(plan.base); o.insert(plan.base)
+    g.reclaim(); o.reclaim()
+    _assert_same_graph(g, o, w.degree, "after build")
+    ever = np.zeros(w.capacity, bool)
+    for r in range(w.rounds):
+        dele, ng, no, _, _ = churn_round(g, o, plan, r, w.n_delete)
+        ever[dele] = True
+        _assert_same_graph(g, o, w.degree, f"after round {r}")
+        gs, gd = g.search(plan.queries, w.k, w.search_beam)
+        os_, od = o.search(plan.queries, w.k, w.search_beam)
+        assert (gs == os_).all(), f"round {r}: search ids differ"
+        assert np.array_equal(gd.view(np.uint32), od.view(np.uint32))
+        assert not np.isin(gs[gs != NIL], np.nonzero(ever)[0]).any()
+        gt, _ = o.exact_knn(plan.queries, w.k)
+        rec = recall_at_k(gs, gt)
+        assert rec >= 0.95, f"round {r}: Recall@10 {rec:.4f}"
+    X = np.concatenate([plan.base] + plan.inserts)
+    check_graph(g.export_graph(), w.degree, after_reclaim=True, vectors=X, dist=oracle_mod.dist, sample=300)
+
+
+def test_edge_cases(oracle_mod):
+    import torch
+    rng = np.random.default_rng(11)
+    g, o = make_pair(oracle_mod, 24, "l2", 8, 200, build_beam=16, n_entry=4)
+    # empty index: every result is padding
+    ids, d = g.search(rng.normal(size=(3, 24)).astype(np.float32), 5, 16)
+    assert (ids == NIL).all() and np.isinf(d).all()
+    X = rng.normal(size=(150, 24)).astype(np.float32)
+    g.insert(X[:1]); o.insert(X[:1])           # a single node, no edges
+    ids, d = g.search(X[:2], 5, 16)
+    assert ids[:, 0].tolist() == [0, 0] and (ids[:, 1:] == NIL).all()
+    g.insert(X[1:]); o.insert(X[1:])
+    _assert_same_graph(g, o, 8, "ragged build")
+    # repeated, unknown and already-deleted ids are no-ops
+    assert g.delete(np.array([5, 5, 5, 4000, 7], np.uint32)) == 2
+    assert o.delete(np.array([5, 5, 5, 4000, 7], np.uint32)) == 2
+    assert g.delete(np.array([5], np.uint32)) == 0
+    _assert_same_graph(g, o, 8, "after delete")
+    # device inputs and outputs give the same answer as host buffers
+    q = rng.normal(size=(40, 24)).astype(np.float32)
+    hi, hd = g.search(q, 7, 16)
+    di, dd = g.search(torch.from_numpy(q).cuda(), 7, 16)
+    assert (di.cpu().numpy().view(np.uint32) == hi).all() and np.array_equal(dd.cpu().numpy(), hd)
+    # k larger than the live set: results end in padding, exactly as the oracle's
+    ids, d = g.search(q[:1], 160, 8)
+    oids, od = o.search(q[:1], 160, 8)
+    assert (ids == oids).all() and np.array_equal(d, od)
+    first_pad = int(np.argmax(ids[0] == NIL)) if (ids[0] == NIL).any() else 160
+    assert first_pad <= 148 and (ids[0, first_pad:] == NIL).all() and np.isinf(d[0, first_pad:]).all()
+    # capacity is a lifetime budget
+    from paper_2607_02543_gb300 import EtaleError
+    with pytest.raises(EtaleError):
+        g.insert(rng.normal(size=(51, 24)).astype(np.float32))
+    # delete everything, reclaim, insert again into the empty index
+    g.delete(np.arange(150, dtype=np.uint32)); o.delete(np.arange(150, dtype=np.uint32))
+    g.reclaim(); o.reclaim()
+    s = g.stats()
+    assert s["live"] == 0 and s["used_slabs"] == 0 and s["n_entries"] == 0
+    Y = rng.normal(size=(30, 24)).astype(np.float32)
+    assert g.insert(Y).tolist() == list(range(150, 180))
+    o.insert(Y)
+    _assert_same_graph(g, o, 8, "reinsert after emptying")
+
+
+def test_ground_truth_kernel(oracle_mod):
+    w = W.scaled(W.SMALL, 3000, n_queries=200)
+    plan = W.make_plan(w)
+    g, o = make_pair(oracle_mod, w.dim, w.metric, w.degree, w.capacity, build_beam=32)
+    g.insert(plan.base); o.insert(plan.base)
+    dele = np.arange(0, 3000, 7, dtype=np.uint32)
+    g.delete(dele); o.delete(dele)
+    gi, gd = g.ground_truth(plan.queries, 10)
+    oi, od = o.exact_knn(plan.queries, 10)
+    # fp32 canonical vs fp64 ranking: identical unless two distances tie in fp32
+    agree = (gi == oi).mean()
+    assert agree > 0.999
+    assert not np.isin(gi, dele).any()
+    assert np.allclose(gd, od, rtol=1e-5)
+
+
+def test_lockfree_invariants_and_recall(oracle_mod):
+    w = W.scaled(W.SMALL, 4000, n_queries=500, rounds=3)
+    plan = W.make_plan(w)
+    g, _ = make_pair(oracle_mod, w.dim, w.metric, w.degree, w.capacity, build_beam=w.build_beam,
+                     mode="lockfree", with_oracle=False)
+    o = oracle_mod.Oracle(w.dim, w.metric, w.degree, w.capacity, build_beam=w.build_beam, refine=2)
+    g.insert(plan.base); o.insert(plan.base)
+    g.reclaim(); o.reclaim()
+    X = np.concatenate([plan.base] + plan.inserts)
+    ever = np.zeros(w.capacity, bool)
+    for r in range(w.rounds):
+        # both sides delete the same ids (chosen from the oracle's live set)
+        dump = o.dump()
+        live = np.nonzero((dump[0] == 0) & (dump[1] == 1))[0].astype(np.uint32)
+        dele = W.choose_deletes(plan.delete_rng, live, w.n_delete)
+        assert g.delete(dele) == o.delete(dele) == dele.size
+        ever[dele] = True
+        g.insert(plan.inserts[r]); o.insert(plan.inserts[r])
+        d1 = g.export_graph()
+        check_graph(d1, w.degree, vectors=X, dist=oracle_mod.dist, sample=200)
+        assert (d1[0][ever[:d1[0].size]] == 1).all()
+        g.reclaim(); o.reclaim()
+        d2 = g.export_graph()
+        check_graph(d2, w.degree, after_reclaim=True)
+        s = g.stats()
+        assert s["used_slabs"] == s["live"]
+    gs, _ = g.search(plan.queries, 10, 64)
+    os_, _ = o.search(plan.queries, 10, 64)
+    gt, _ = o.exact_knn(plan.queries, 10)
+    rg, ro = recall_at_k(gs, gt), recall_at_k(os_, gt)
+    assert not np.isin(gs[gs != NIL], np.nonzero(ever)[0]).any()
+    assert rg >= 0.95 and abs(rg - ro) <= 0.005, (rg, ro)
