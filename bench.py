@@ -1,0 +1,363 @@
+"""Benchmark: ms per 1% churn round (delete + insert + refine + reclaim) and
+query throughput at k = 10 on a 1,000,000 x 128 integer-valued mixture
+(degree 32, build beam 128, 10,000 deletes + 10,000 inserts per round,
+10,000 queries, lock-free mode), on one GB300 per rank.
+
+One step = one churn round followed by one 10,000-query batch.  Prints one
+JSON line (rank 0).  `--impl reference` times the CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_02543_gb300 import workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="etale", choices=["etale", "reference"])
+    ap.add_argument("--workload", default="int256-1m-d128", choices=["int256-1m-d128", "gauss64-10k-d128"])
+    ap.add_argument("--mode", default="lockfree", choices=["lockfree", "deterministic"])
+    ap.add_argument("--search-beam", type=int, default=0,
+                    help="EF_SEARCH; default: the smallest of 64..256 reaching Recall@10 >= 0.95")
+    ap.add_argument("--n-entry", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
+    ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
+    return ap.parse_args()
+
+
+def workload(name: str, n_live: int = 0) -> W.Workload:
+    w = W.SIFT_LIKE_1M if name == "int256-1m-d128" else W.SMALL
+    return W.scaled(w, n_live) if n_live else w
+
+
+def load_peaks():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(w: W.Workload, n_sample: int, ops: int, n_entry: int, rounds: int = 1):
+    """Build the oracle on n_sample points of the workload's mixture (untimed),
+    then time `rounds` batches of `ops` deletes + `ops` inserts + reclaim.
+    Per-operation costs are scaled to the workload's round (n_delete deletes,
+    n_insert inserts; reclaim scaled linearly in the live count)."""
+    import oracle
+    ws = W.scaled(w, n_sample, n_queries=16, rounds=rounds)
+    ws = W.dataclasses.replace(ws, n_delete=ops, n_insert=ops)
+    p = W.make_plan(ws)
+    o = oracle.Oracle(w.dim, w.metric, w.degree, ws.capacity, build_beam=w.build_beam, refine=2,
+                      n_entry=n_entry)
+    o.insert(p.base)
+    o.reclaim()
+    alive = np.zeros(ws.capacity, bool)
+    alive[:n_sample] = True
+    per_round = []
+    for r in range(rounds):
+        dele = W.choose_deletes(p.delete_rng, np.nonzero(alive)[0].astype(np.uint32), ops)
+        t0 = time.perf_counter()
+        o.delete(dele)
+        t1 = time.perf_counter()
+        ids = o.insert(p.inserts[r])
+        t2 = time.perf_counter()
+        o.reclaim()
+        t3 = time.perf_counter()
+        alive[dele] = False
+        alive[ids] = True
+        t_del, t_ins, t_rec = (t1 - t0) / ops, (t2 - t1) / ops, (t3 - t2)
+        est = (w.n_delete * t_del + w.n_insert * t_ins + t_rec * (w.n_base / n_sample)) * 1e3
+        per_round.append(est)
+    return per_round, {"n_sample": n_sample, "ops": ops}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_entry = args.n_entry
+    per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry,
+                              rounds=args.warmup + args.steps)
+    timed = per[args.warmup:]
+    v = float(np.mean(timed))
+    sample = (f"oracle built on {info['n_sample']} points of the same mixture (untimed); each step times "
+              f"{info['ops']} deletes + {info['ops']} inserts + reclaim, scaled per operation to "
+              f"{w.n_delete} + {w.n_insert} and reclaim linearly to {w.n_base} live")
+    out = {"impl": "reference", "metric": "ms per 1% churn round", "value": v, "unit": "ms",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": config_dict(w, args),
+           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(w, args):
+    return {"workload": w.name, "n_live": w.n_base, "dim": w.dim, "metric": w.metric, "degree": w.degree,
+            "build_beam": w.build_beam, "churn_per_round": [w.n_delete, w.n_insert],
+            "queries_per_step": w.n_queries, "k": w.k, "search_beam": args.search_beam or w.search_beam,
+            "mode": args.mode, "n_entry": args.n_entry,
+            "l2": "working set (index > 600 MB) larger than L2; no flush" if w.n_base >= 1_000_000 else
+                  "small index; no flush", "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    w = workload(args.workload, args.n_live)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2607_02543_gb300 import Index, build as B
+    B.build()
+    total_rounds = args.warmup + args.steps * (1 if args.no_e2e else 2)
+    wr = W.dataclasses.replace(w, rounds=total_rounds)
+    plan = W.make_plan(wr)
+    n_entry = args.n_entry
+    idx = Index(w.dim, w.metric, w.degree, wr.capacity, build_beam=w.build_beam, mode=args.mode,
+                n_entry=n_entry)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    idx.insert(torch.from_numpy(plan.base).to(dev), stream)
+    idx.reclaim(stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    # every round's delete choice, precomputed on the host from the live set
+    alive = np.zeros(wr.capacity, bool)
+    alive[:w.n_base] = True
+    next_id = w.n_base
+    dels = []
+    for r in range(total_rounds):
+        d = W.choose_deletes(plan.delete_rng, np.nonzero(alive)[0].astype(np.uint32), w.n_delete)
+        alive[d] = False
+        alive[next_id:next_id + w.n_insert] = True
+        next_id += w.n_insert
+        dels.append(d)
+    d_del = [torch.from_numpy(d.astype(np.int32)).to(dev) for d in dels]
+    d_ins = [torch.from_numpy(x).to(dev) for x in plan.inserts]
+    d_q = torch.from_numpy(plan.queries).to(dev)
+    out_ids = torch.empty((w.n_queries, w.k), dtype=torch.int32, device=dev)
+    out_d = torch.empty((w.n_queries, w.k), dtype=torch.float32, device=dev)
+
+    def round_dev(r):
+        idx.delete(d_del[r], stream)
+        idx.insert(d_ins[r], stream)
+        idx.reclaim(stream)
+
+    # EF_SEARCH: the smallest beam whose Recall@10 reaches 0.95 (Sec. 5.6),
+    # chosen on the built index before any timed work
+    gt_ids, _ = idx.ground_truth(d_q, w.k, stream)
+    gt_np = gt_ids.cpu().numpy().view(np.uint32)
+
+    def recall_of(ids_t):
+        got = ids_t.cpu().numpy().view(np.uint32)
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w.k for a, b in zip(got, gt_np)]))
+
+    sweep = []
+    if args.search_beam:
+        beam = args.search_beam
+    else:
+        beam = 256
+        for b in (64, 96, 128, 160, 192, 256):
+            idx.search(d_q, w.k, b, stream, out=(out_ids, out_d))
+            rec = recall_of(out_ids)
+            sweep.append([b, rec])
+            if rec >= 0.95:
+                beam = b
+                break
+    args.search_beam = beam
+    for r in range(args.warmup):
+        round_dev(r)
+        idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    idx.set_profiling(True)
+    idx.profile(reset=True)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("timed")
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
+    l0 = idx.kernel_launches()
+    s0 = idx.stats()
+    search_stats = []
+    torch.cuda.synchronize()
+    barrier()
+    for i in range(args.steps):
+        r = args.warmup + i
+        ev[i][0].record(stream)
+        round_dev(r)
+        ev[i][1].record(stream)
+        a = idx.stats()
+        ev[i][2].record(stream)
+        idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+        ev[i][3].record(stream)
+        b = idx.stats()
+        search_stats.append((a, b))
+    torch.cuda.synchronize()
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
+    barrier()
+    clk = clocks.stop()
+    prof = idx.profile(reset=True)
+    idx.set_profiling(False)
+    launches = idx.kernel_launches() - l0
+    maint_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    search_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    ms_round = float(np.mean(maint_ms))
+    ms_search = float(np.mean(search_ms))
+    # recall of the last query batch against the exact live top-k
+    gt_ids, _ = idx.ground_truth(d_q, w.k, stream)
+    gt_np = gt_ids.cpu().numpy().view(np.uint32)
+    recall = recall_of(out_ids)
+    # algorithmic bytes of the query-search launch
+    m, R = w.dim, w.degree
+    nexp = np.mean([b["n_expand"] - a["n_expand"] for a, b in search_stats])
+    ndist = np.mean([b["n_dist"] - a["n_dist"] for a, b in search_stats])
+    alg_bytes = nexp * 8 * R + ndist * (4 * m + 8) + w.n_queries * (4 * m + 8 * w.k)
+    peak, peak_kind = load_peaks()
+    sq_ms, sq_n = prof["search_query"]
+    kernel_ms = sq_ms / max(sq_n, 1)          # one query-mode search_kernel launch per step
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    phases = {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]}
+    # e2e: same rounds through the API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_del = [torch.from_numpy(dels[args.warmup + args.steps + i].astype(np.int32)).pin_memory().numpy()
+                 for i in range(args.steps)]
+        h_ins = [torch.from_numpy(plan.inserts[args.warmup + args.steps + i]).pin_memory().numpy()
+                 for i in range(args.steps)]
+        h_q = torch.from_numpy(plan.queries).pin_memory().numpy()
+        torch.cuda.synchronize()
+        walls = []
+        for i in range(args.steps):
+            t = time.perf_counter()
+            idx.delete(h_del[i].view(np.uint32), stream)
+            idx.insert(h_ins[i], stream)
+            idx.reclaim(stream)
+            walls.append((time.perf_counter() - t) * 1e3)
+        t = time.perf_counter()
+        idx.search(h_q, w.k, beam, stream)
+        e2e_search = (time.perf_counter() - t) * 1e3
+        e2e = {"value": float(np.mean(walls)), "unit": "ms",
+               "h2d_bytes_per_step": int(w.n_insert * m * 4 + w.n_delete * 4 + w.n_queries * m * 4),
+               "d2h_bytes_per_step": int(w.n_insert * 4 + 8 + w.n_queries * w.k * 8),
+               "qps": w.n_queries / (e2e_search * 1e-3)}
+    # max over ranks
+    vals = torch.tensor([ms_round, ms_search], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_round, ms_search = float(vals[0]), float(vals[1])
+    st = idx.stats()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry, rounds=1)
+        cpu = {"value": float(np.mean(per)), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"oracle on {info['n_sample']} points of the same mixture, one batch of "
+                         f"{info['ops']} deletes + {info['ops']} inserts + reclaim timed on one host core, "
+                         f"scaled per operation to {w.n_delete} + {w.n_insert} and reclaim linearly to "
+                         f"{w.n_base} live"}
+    if rank == 0:
+        out = {"metric": "ms per 1% churn round", "value": ms_round, "unit": "ms", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": config_dict(w, args),
+               "recall_at_10": recall, "beam_sweep": sweep, "qps": world * w.n_queries / (ms_search * 1e-3),
+               "search_ms_per_10k": ms_search, "build_s": build_s,
+               "roofline": {"bound": "hbm", "kernel": "search_kernel (query mode)", "achieved": achieved,
+                            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                            "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                            "kernel_ms": kernel_ms},
+               "phase_ms_per_step": phases,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+               "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

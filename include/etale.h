@@ -159,8 +159,35 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out);
  * failed etale_create when idx is NULL).  Never NULL.                      */
 const char *etale_last_error(const etale_index *idx);
 
-/* Kernel launches issued by this index so far (for launch accounting).     */
+/* Kernel launches issued by this library so far (launch accounting).      */
 uint64_t etale_kernel_launches(const etale_index *idx);
+
+/* Opt-in phase timing.  When enabled, CUDA events are recorded on the
+ * caller's stream around every phase below; durations accumulate per phase
+ * and are folded in when a call synchronises.  Off by default (no events).  */
+typedef enum {
+    ETALE_PH_SEED = 0,        /* entry-set seeding kernel (inserts and queries) */
+    ETALE_PH_SEARCH_INSERT,   /* BeamSearch kernel, insert mode                 */
+    ETALE_PH_PRUNE,           /* forward RobustPrune + own publish              */
+    ETALE_PH_OFFER_SORT,      /* offer sort + segmenting (deterministic mode)   */
+    ETALE_PH_OFFER_FOLD,      /* reverse-offer publication                       */
+    ETALE_PH_REFINE,          /* refine pass selection + publish                */
+    ETALE_PH_DELETE_PREP,     /* id sort, tombstone CAS, compaction of ids      */
+    ETALE_PH_REPAIR_K,        /* replacement sets K(u, a)                       */
+    ETALE_PH_REPAIR_FOLD,     /* repair publication (pair sort included)        */
+    ETALE_PH_ENTRIES,         /* entry-set recomputation                        */
+    ETALE_PH_COMPACT,         /* reclaim phase 1 (bitmap + compaction)          */
+    ETALE_PH_RECLAIM,         /* reclaim phase 2                                */
+    ETALE_PH_SEARCH_QUERY,    /* BeamSearch kernel, query mode                  */
+    ETALE_PH_RECYCLE,         /* retired -> free stack                          */
+    ETALE_PH_COUNT
+} etale_phase;
+
+etale_status etale_set_profiling(etale_index *idx, int enable);
+
+/* Copy accumulated milliseconds and launch counts for the first n phases
+ * (either pointer may be NULL); reset = 1 clears the accumulators.         */
+etale_status etale_get_profile(etale_index *idx, double *ms, uint64_t *count, uint32_t n, int reset);
 
 #ifdef __cplusplus
 }

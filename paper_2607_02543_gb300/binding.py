@@ -46,7 +46,9 @@ class Stats(C.Structure):
 EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_insert", "etale_delete",
            "etale_reclaim", "etale_search", "etale_ground_truth", "etale_export_graph",
            "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
-           "etale_kernel_launches"]
+           "etale_kernel_launches", "etale_set_profiling", "etale_get_profile"]
+PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
+          "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
 _lock = threading.Lock()
 _lib = None
@@ -77,6 +79,8 @@ def load(path: str = LIB_PATH):
             "etale_get_config": ([P, C.POINTER(Config)], C.c_int),
             "etale_last_error": ([P], C.c_char_p),
             "etale_kernel_launches": ([P], U64),
+            "etale_set_profiling": ([P, C.c_int], C.c_int),
+            "etale_get_profile": ([P, P, P, U32, C.c_int], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -224,3 +228,14 @@ class Index:
 
     def kernel_launches(self) -> int:
         return int(self.lib.etale_kernel_launches(self.h))
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.etale_set_profiling(self.h, int(on)))
+
+    def profile(self, reset: bool = False) -> dict:
+        """{phase: (milliseconds, launches)} accumulated while profiling was on."""
+        n = len(PHASES)
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.uint64)
+        self._check(self.lib.etale_get_profile(self.h, _ptr(ms), _ptr(cnt), n, int(reset)))
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}

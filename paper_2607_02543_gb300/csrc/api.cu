@@ -82,7 +82,7 @@ struct etale_index {
     DevBuf live_flags, live_rank, live_scan_scr, tomb_bits;
     DevBuf del_ids, del_vals, del_ids2, del_vals2, del_ok, del_scan, dt, pair_key, pair_val, pair_key2, pair_val2,
         pair_K, pair_Kn, pair_flags, pair_scan, pair_seg, counts;
-    DevBuf ex_del, ex_hs, ex_deg, ex_ids, ex_rho;
+    DevBuf ex_del, ex_hs, ex_deg, ex_ids, ex_rho, seed;
     // host-side state
     u64 next_id = 0, live = 0, tombs = 0, reclaimed = 0;
     u32 n_entries = 0;
@@ -90,6 +90,14 @@ struct etale_index {
     u64 device_bytes = 0;
     SearchTuning tune;
     std::string err = "no error";
+    // phase timing (opt-in)
+    static constexpr int MAXREC = 2048;
+    bool prof = false;
+    std::vector<cudaEvent_t> pev;
+    int prec_phase[MAXREC];
+    int nrec = 0, open_phase = -1;
+    double pms[ETALE_PH_COUNT] = {0};
+    u64 pcnt[ETALE_PH_COUNT] = {0};
 
     Dev dev() const {
         Dev d;
@@ -121,10 +129,49 @@ struct etale_index {
 
 namespace {
 
+// Fold recorded phase events into the accumulators (the stream has been
+// synchronised by the caller).
+void prof_flush(etale_index *idx) {
+    for (int i = 0; i < idx->nrec; i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, idx->pev[2 * i], idx->pev[2 * i + 1]) == cudaSuccess) {
+            idx->pms[idx->prec_phase[i]] += ms;
+            idx->pcnt[idx->prec_phase[i]]++;
+        }
+    }
+    cudaGetLastError();
+    idx->nrec = 0;
+}
+
+void prof_begin(etale_index *idx, int phase, cudaStream_t st) {
+    if (!idx->prof) return;
+    if (idx->nrec == etale_index::MAXREC) {
+        cudaStreamSynchronize(st);
+        prof_flush(idx);
+    }
+    cudaEventRecord(idx->pev[2 * idx->nrec], st);
+    idx->open_phase = phase;
+}
+
+void prof_end(etale_index *idx, cudaStream_t st) {
+    if (!idx->prof || idx->open_phase < 0) return;
+    cudaEventRecord(idx->pev[2 * idx->nrec + 1], st);
+    idx->prec_phase[idx->nrec++] = idx->open_phase;
+    idx->open_phase = -1;
+}
+
+struct PhaseScope {
+    etale_index *idx;
+    cudaStream_t st;
+    PhaseScope(etale_index *i, int ph, cudaStream_t s) : idx(i), st(s) { prof_begin(i, ph, s); }
+    ~PhaseScope() { prof_end(idx, st); }
+};
+
 // Read the device counters (synchronises the stream).
 etale_status read_ctr(etale_index *idx, cudaStream_t st) {
     CK(cudaMemcpyAsync(idx->host_ctr, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost, st), "read counters");
     CK(cudaStreamSynchronize(st), "synchronize");
+    if (idx->prof) prof_flush(idx);
     return ETALE_OK;
 }
 
@@ -162,6 +209,7 @@ etale_status ensure_pool(etale_index *idx, u64 need, cudaStream_t st) {
 }
 
 etale_status recycle(etale_index *idx, cudaStream_t st) {
+    PhaseScope ps(idx, ETALE_PH_RECYCLE, st);
     CK(launch_recycle(idx->dev(), st), "recycle");
     g_kernel_launches++;
     return ETALE_OK;
@@ -178,6 +226,7 @@ etale_status recompute_entries(etale_index *idx, cudaStream_t st) {
     ScanScratch ss;
     scan_scratch_carve(ss, as<u32>(idx->live_scan_scr), (u32)n);
     Dev d = idx->dev();
+    PhaseScope ps(idx, ETALE_PH_ENTRIES, st);
     CK(launch_live_flags(d, n, as<u32>(idx->live_flags), st), "live flags");
     CK(exclusive_scan(as<u32>(idx->live_flags), as<u32>(idx->live_rank), (u32)n, ss, st), "live scan");
     CK(launch_entries_select(d, n, as<u32>(idx->live_flags), as<u32>(idx->live_rank), idx->live, S, st),
@@ -200,6 +249,7 @@ etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t 
     if (s != ETALE_OK) return s;
     u64 *seg_count = as<u64>(idx->counts) + 0;
     if (!lockfree) {
+        PhaseScope ps(idx, ETALE_PH_OFFER_SORT, st);
         SortScratch ss;
         sort_scratch_carve(ss, as<u32>(idx->sort_scr), nslots);
         CK(radix_sort_pairs(of.key, of.val, of.key_alt, of.val_alt, nslots, bits_for(idx->capacity), ss, st),
@@ -211,9 +261,12 @@ etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t 
            "offer segments");
         g_kernel_launches += 3 * ((bits_for(idx->capacity) + 7) / 8) * 2 + 4;
     }
-    CK(launch_offer_fold(d, of, as<u32>(idx->seg_start), seg_count, lockfree ? idx->cfg.cas_budget : 0, idx->num_sms,
-                         st),
-       "offer fold");
+    {
+        PhaseScope ps(idx, ETALE_PH_OFFER_FOLD, st);
+        CK(launch_offer_fold(d, of, as<u32>(idx->seg_start), seg_count, lockfree ? idx->cfg.cas_budget : 0,
+                             idx->num_sms, st),
+           "offer fold");
+    }
     g_kernel_launches++;
     return recycle(idx, st);
 }
@@ -240,16 +293,28 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     Offers of{as<u32>(idx->of_key), as<u32>(idx->of_val), as<u32>(idx->of_key2), as<u32>(idx->of_val2),
               as<u32>(idx->of_src), as<float>(idx->of_rho), slots};
     // 1. BeamSearch of every member on the graph before the sub-batch
-    CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr, as<u64>(idx->exp_keys),
-                     as<u32>(idx->exp_count), idx->tune, idx->num_sms, st),
-       "insert search");
-    g_kernel_launches++;
+    if (!grow(idx->seed, (size_t)b * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
+    {
+        PhaseScope ps(idx, ETALE_PH_SEED, st);
+        CK(launch_seed(d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed), st), "insert seed");
+    }
+    {
+        PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
+        CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr,
+                         as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), idx->tune,
+                         idx->num_sms, st),
+           "insert search");
+    }
+    g_kernel_launches += 2;
     // 2. forward edges, own slab, offers
     etale_status s = ensure_pool(idx, b, st);
     if (s != ETALE_OK) return s;
-    CK(launch_prune_insert(d, first, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
-                           as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st),
-       "prune insert");
+    {
+        PhaseScope ps(idx, ETALE_PH_PRUNE, st);
+        CK(launch_prune_insert(d, first, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
+                               as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st),
+           "prune insert");
+    }
     g_kernel_launches++;
     s = recycle(idx, st);
     if (s != ETALE_OK) return s;
@@ -261,7 +326,10 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     if (rmode) {
         s = ensure_pool(idx, b, st);
         if (s != ETALE_OK) return s;
-        CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st), "refine");
+        {
+            PhaseScope ps(idx, ETALE_PH_REFINE, st);
+            CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st), "refine");
+        }
         g_kernel_launches++;
         s = recycle(idx, st);
         if (s != ETALE_OK) return s;
@@ -398,6 +466,7 @@ etale_status etale_destroy(etale_index *idx) {
     cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
     cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
     if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
+    for (cudaEvent_t e : idx->pev) cudaEventDestroy(e);
     DevBuf *bufs[] = {&idx->stage, &idx->qpad, &idx->out_ids, &idx->out_dist, &idx->exp_keys, &idx->exp_count,
                       &idx->F_id, &idx->F_rho, &idx->F_n, &idx->of_key, &idx->of_val, &idx->of_key2,
                       &idx->of_val2, &idx->of_src, &idx->of_rho, &idx->seg_flags, &idx->seg_scan, &idx->seg_start,
@@ -406,7 +475,7 @@ etale_status etale_destroy(etale_index *idx) {
                       &idx->del_ok, &idx->del_scan, &idx->dt, &idx->pair_key, &idx->pair_val, &idx->pair_key2,
                       &idx->pair_val2, &idx->pair_K, &idx->pair_Kn, &idx->pair_flags, &idx->pair_scan,
                       &idx->pair_seg, &idx->counts, &idx->ex_del, &idx->ex_hs, &idx->ex_deg, &idx->ex_ids,
-                      &idx->ex_rho};
+                      &idx->ex_rho, &idx->seed};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete idx;
@@ -484,6 +553,7 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
     ScanScratch sc;
     scan_scratch_carve(sc, as<u32>(idx->scan_scr), (u32)std::max<u64>(slots, n));
     // sorted ids (payload unused)
+    prof_begin(idx, ETALE_PH_DELETE_PREP, st);
     CK(launch_fill_offer_keys(as<u32>(idx->del_vals2), as<u32>(idx->del_vals), (u32)n, 0, st), "iota");
     CK(radix_sort_pairs(as<u32>(idx->del_ids), as<u32>(idx->del_vals), as<u32>(idx->del_ids2),
                         as<u32>(idx->del_vals2), (u32)n, 32, ss, st),
@@ -496,16 +566,20 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
                          as<u32>(idx->dt), n_dt, st),
        "tombstone compaction");
     g_kernel_launches += 4 * 3 + 6;
+    prof_end(idx, st);
     // repair: K(u, a) per pair, then one fold per a
     const u32 invalid = (u32)idx->capacity;
+    prof_begin(idx, ETALE_PH_REPAIR_K, st);
     CK(launch_fill_offer_keys(as<u32>(idx->pair_key), as<u32>(idx->pair_val), (u32)slots, invalid, st), "fill pairs");
     CK(launch_repair_k(d, as<u32>(idx->dt), n_dt, (u32)n, as<u32>(idx->pair_key), as<u32>(idx->pair_val),
                        as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), idx->num_sms, st),
        "repair K");
     g_kernel_launches += 2;
+    prof_end(idx, st);
     const bool lockfree = idx->cfg.mode == ETALE_MODE_LOCKFREE;
     etale_status s = ensure_pool(idx, std::min<u64>(slots, idx->live), st);
     if (s != ETALE_OK) return s;
+    prof_begin(idx, ETALE_PH_REPAIR_FOLD, st);
     if (!lockfree) {
         CK(radix_sort_pairs(as<u32>(idx->pair_key), as<u32>(idx->pair_val), as<u32>(idx->pair_key2),
                             as<u32>(idx->pair_val2), (u32)slots, bits_for(idx->capacity), ss, st),
@@ -520,6 +594,7 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
                           lockfree ? idx->cfg.cas_budget : 0, idx->num_sms, st),
        "repair fold");
     g_kernel_launches++;
+    prof_end(idx, st);
     s = recycle(idx, st);
     if (s != ETALE_OK) return s;
     u64 k = 0;
@@ -540,14 +615,20 @@ etale_status etale_reclaim(etale_index *idx, void *stream) {
     if (n == 0) return ETALE_OK;
     if (!grow(idx->tomb_bits, ((n + 31) / 32) * 4)) return idx->fail(ETALE_ENOMEM, "scratch allocation (reclaim)");
     Dev d = idx->dev();
-    CK(launch_tomb_bits(d, n, as<u32>(idx->tomb_bits), st), "tombstone bitmap");
     s = ensure_pool(idx, idx->live, st);
     if (s != ETALE_OK) return s;
-    CK(launch_compact(d, n, as<u32>(idx->tomb_bits), st), "compaction");
+    {
+        PhaseScope ps(idx, ETALE_PH_COMPACT, st);
+        CK(launch_tomb_bits(d, n, as<u32>(idx->tomb_bits), st), "tombstone bitmap");
+        CK(launch_compact(d, n, as<u32>(idx->tomb_bits), st), "compaction");
+    }
     g_kernel_launches += 2;
     s = recycle(idx, st);
     if (s != ETALE_OK) return s;
-    CK(launch_reclaim_tombstones(d, n, st), "reclaim");
+    {
+        PhaseScope ps(idx, ETALE_PH_RECLAIM, st);
+        CK(launch_reclaim_tombstones(d, n, st), "reclaim");
+    }
     g_kernel_launches++;
     s = recycle(idx, st);
     if (s != ETALE_OK) return s;
@@ -587,9 +668,16 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
            "ground truth");
     } else {
         const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
-        CK(launch_search(d, as<float>(idx->qpad), (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, idx->tune,
-                         idx->num_sms, st),
+        if (!grow(idx->seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
+        {
+            PhaseScope ps(idx, ETALE_PH_SEED, st);
+            CK(launch_seed(d, as<float>(idx->qpad), (u32)nq, L, as<u64>(idx->seed), st), "query seed");
+        }
+        PhaseScope ps(idx, ETALE_PH_SEARCH_QUERY, st);
+        CK(launch_search(d, as<float>(idx->qpad), (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->seed),
+                         idx->tune, idx->num_sms, st),
            "search");
+        g_kernel_launches++;
     }
     g_kernel_launches += 2;
     if (!dev_out) {
@@ -677,5 +765,29 @@ const char *etale_last_error(const etale_index *idx) {
 }
 
 uint64_t etale_kernel_launches(const etale_index *) { return g_kernel_launches.load(); }
+
+etale_status etale_set_profiling(etale_index *idx, int enable) {
+    if (!idx) return ETALE_EINVAL;
+    if (enable && idx->pev.empty()) {
+        idx->pev.resize(2 * etale_index::MAXREC);
+        for (auto &e : idx->pev)
+            if (cudaEventCreate(&e) != cudaSuccess) return idx->cuda_fail(cudaGetLastError(), "event create");
+    }
+    idx->prof = enable != 0;
+    idx->nrec = 0;
+    return ETALE_OK;
+}
+
+etale_status etale_get_profile(etale_index *idx, double *ms, uint64_t *count, uint32_t n, int reset) {
+    if (!idx) return ETALE_EINVAL;
+    if (n > ETALE_PH_COUNT) n = ETALE_PH_COUNT;
+    for (uint32_t i = 0; i < n; i++) {
+        if (ms) ms[i] = idx->pms[i];
+        if (count) count[i] = idx->pcnt[i];
+    }
+    if (reset)
+        for (int i = 0; i < ETALE_PH_COUNT; i++) { idx->pms[i] = 0; idx->pcnt[i] = 0; }
+    return ETALE_OK;
+}
 
 }  // extern "C"

@@ -12,8 +12,11 @@ struct SearchTuning {
 
 // search.cu
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
+// seed_kernel: top-L of the entry set per query into `seed` (nq x L); it
+// must precede the search launch that reads `seed`.
+cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st);
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
-                          u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count,
+                          u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st);
 
 // Offer lists: a payload index p names (src[p], rho[p]); key[p] is the target

@@ -22,6 +22,7 @@ namespace etale {
 struct SearchArgs {
     Dev d;
     const float *q;      // query rows, stride mp floats, 16-byte aligned
+    const u64 *seed;     // nq x L initial beams (top-L of the entry set), KEY_INF padded
     u32 nq, L, max_hops, mode;   // mode 0: query, 1: insert
     u32 k;
     u32 *out_ids;
@@ -184,7 +185,99 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, in
     return min(L, n + c);
 }
 
-__global__ void __launch_bounds__(128) search_kernel(SearchArgs a) {
+
+// ---------------------------------------------------------------------------
+// Seeding: for each query, the L nearest members of the entry set E by
+// (rho, id) (the beam after evaluating every entry point).  A block of 8 warps
+// (8 queries) stages 32 entry rows at a time in shared memory; each warp
+// computes its 32 distances and merges them into a sorted running top-L.
+// ---------------------------------------------------------------------------
+constexpr int SEED_TILE = 32;
+
+struct SeedArgs {
+    Dev d;
+    const float *q;
+    u32 nq, L;
+    u64 *seed;
+};
+
+__host__ __device__ inline size_t seed_warp_bytes(u32 mp, u32 L) {
+    return align_up((size_t)mp * 4, 16) + 2 * align_up((size_t)L * 8, 16) + 32 * 8;
+}
+
+__global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
+    extern __shared__ __align__(16) char ssm[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const u32 mp = d.mp, L = a.L;
+    float *tile = reinterpret_cast<float *>(ssm);
+    char *p = ssm + align_up((size_t)SEED_TILE * mp * 4, 16) + warp * seed_warp_bytes(mp, L);
+    float *qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 16);
+    u64 *bk0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    u64 *bk1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    u64 *nk = reinterpret_cast<u64 *>(p);
+    const u32 qi = blockIdx.x * 8 + warp;
+    const bool active = qi < a.nq;
+    if (active)
+        for (u32 i = lane * 4; i < mp; i += 128)
+            *reinterpret_cast<float4 *>(qv + i) = *reinterpret_cast<const float4 *>(a.q + (size_t)qi * mp + i);
+    const int grp = lane >> 3, g = lane & 7;
+    const u32 S = d.n_entries;
+    int n = 0, cur = 0;
+    for (u32 t0 = 0; t0 < S; t0 += SEED_TILE) {
+        const int nt = (int)min((u32)SEED_TILE, S - t0);
+        __syncthreads();
+        const u32 f4 = mp / 4;
+        for (u32 i = threadIdx.x; i < (u32)nt * f4; i += 256) {
+            const u32 r = i / f4, c = i % f4;
+            reinterpret_cast<float4 *>(tile + (size_t)r * mp)[c] =
+                reinterpret_cast<const float4 *>(d.x + (size_t)d.entries[t0 + r] * mp)[c];
+        }
+        __syncthreads();
+        if (!active) continue;
+        u64 key = KEY_INF;
+        for (int r0 = 0; r0 < nt; r0 += 4) {
+            const int c = r0 + grp;
+            const int cc = c < nt ? c : nt - 1;
+            const float dist = canon_dist<8>(qv, tile + (size_t)cc * mp, (int)mp, (int)d.metric, g);
+            const u64 kk = mkkey(dist, d.entries[t0 + cc]);
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const u64 v = __shfl_sync(FULL, kk, t * 8);
+                if (lane == r0 + t && r0 + t < nt) key = v;
+            }
+        }
+        u64 *bk = cur ? bk1 : bk0, *bn = cur ? bk0 : bk1;
+        if (key != KEY_INF && n == (int)L && key >= bk[n - 1]) key = KEY_INF;
+        int rank = 0;
+        for (int j = 0; j < 32; j++) rank += (__shfl_sync(FULL, key, j) < key);
+        const int c = __popc(__ballot_sync(FULL, key != KEY_INF));
+        if (c == 0) continue;
+        if (key != KEY_INF) nk[rank] = key;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const u64 bkey = bk[i];
+            int lo = 0, hi = c;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (nk[mid] < bkey) lo = mid + 1; else hi = mid; }
+            if (i + lo < (int)L) bn[i + lo] = bkey;
+        }
+        if (lane < c) {
+            const u64 k2 = nk[lane];
+            int lo = 0, hi = n;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (bk[mid] < k2) lo = mid + 1; else hi = mid; }
+            if (lane + lo < (int)L) bn[lane + lo] = k2;
+        }
+        __syncwarp();
+        cur ^= 1;
+        n = min((int)L, n + c);
+    }
+    if (active) {
+        const u64 *bk = cur ? bk1 : bk0;
+        for (u32 i = lane; i < L; i += 32) a.seed[(size_t)qi * L + i] = (int)i < n ? bk[i] : KEY_INF;
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) search_kernel(SearchArgs a) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -206,12 +299,20 @@ __global__ void __launch_bounds__(128) search_kernel(SearchArgs a) {
             *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
         for (u32 i = lane; i < a.seen_slots; i += 32) s.seen[i] = NIL;
         __syncwarp();
-        int cur = 0, n = 0;
-        // seed the beam from the entry set E
-        for (u32 e0 = 0; e0 < d.n_entries; e0 += 32) {
-            u32 id = (e0 + lane < d.n_entries) ? d.entries[e0 + lane] : NIL;
-            n = eval_merge(a, s, id, n, cur, phase, ndist, timeout);
+        // initial beam: the L nearest members of the entry set E, computed by
+        // seed_kernel; the reference words are sampled here
+        int cur = 0;
+        const int n0 = (int)min(a.L, d.n_entries);
+        for (int i = lane; i < n0; i += 32) {
+            const u64 k = a.seed[(size_t)qi * a.L + i];
+            const u32 id = key_id(k);
+            s.bkey(0)[i] = k;
+            s.bref(0)[i] = ld_ref(d, id);
+            s.bflag(0)[i] = 0;
+            s.seen[seen_slot(id, a.seen_bits)] = id;
         }
+        int n = n0;
+        __syncwarp();
         u32 hops = 0, nexp = 0;
         for (;;) {
             int first = -1;
@@ -275,12 +376,22 @@ size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
     return 4 * search_warp_bytes(mp, L, stage_rows, seen_slots);
 }
 
+cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st) {
+    if (nq == 0 || d.n_entries == 0) return cudaSuccess;
+    SeedArgs a{d, q, nq, L, seed};
+    size_t smem = align_up((size_t)SEED_TILE * d.mp * 4, 16) + 8 * seed_warp_bytes(d.mp, L);
+    cudaError_t e = cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    seed_kernel<<<(nq + 7) / 8, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
-                          u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count,
+                          u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st) {
     if (nq == 0) return cudaSuccess;
     SearchArgs a;
-    a.d = d; a.q = q; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode; a.k = k;
+    a.d = d; a.q = q; a.seed = seed; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode; a.k = k;
     a.out_ids = out_ids; a.out_dist = out_dist; a.exp_keys = exp_keys; a.exp_count = exp_count;
     a.stage_rows = tune.stage_rows;
     a.seen_bits = tune.seen_bits;

@@ -533,8 +533,16 @@ struct RepairKArgs {
     u32 *pair_Kn;
 };
 
+// sort width for K: the warp bitonic sort needs a power of two >= 32
+__host__ __device__ inline u32 repk_np(u32 R) {
+    u32 np = 32;
+    while (np < R) np <<= 1;
+    return np;
+}
+
 __host__ __device__ inline size_t repk_warp_bytes(u32 R) {
-    return 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)R * 8 * 2) + al16(2 * R);
+    const u32 np = repk_np(R);
+    return 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)np * 8) + al16(np);
 }
 
 __global__ void __launch_bounds__(128) repair_k_kernel(RepairKArgs a) {
@@ -547,13 +555,12 @@ __global__ void __launch_bounds__(128) repair_k_kernel(RepairKArgs a) {
     u32 *bdel = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     u32 *cj = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *M = reinterpret_cast<float *>(p); p += al16((size_t)R * R * 4);
-    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)R * 8 * 2);
+    const int npk = (int)repk_np(R);
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)npk * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p);
     const int grp = lane >> 3, g = lane & 7;
     const u64 nd = *a.n_dt;
     const u32 invalid = (u32)d.capacity;
-    int npk = 32;
-    while (npk < (int)R) npk <<= 1;
     for (;;) {
         u64 i = 0;
         if (lane == 0) i = atomicAdd(&d.ctr[C_WORK], 1ull);
