@@ -66,7 +66,15 @@ typedef struct {
     uint32_t n_entry;     /* entry-set size |E|; default 1024                 */
     uint32_t mode;        /* etale_mode; default deterministic                */
     uint32_t cas_budget;  /* lock-free publish attempts (Alg. 1); default 16  */
-    uint32_t reserved[6];
+    uint32_t stage_kb;    /* per-warp shared-memory stage of candidate rows
+                             for RobustPrune, KB; 0 = read rows from L2     */
+    uint32_t gram;        /* distances inside reverse-offer and repair
+                             RobustPrunes: 0 default (tensor cores in
+                             lock-free mode, canonical fp32 in deterministic
+                             mode), 1 canonical fp32, 2 tensor-core Gram
+                             tile (bf16 inputs, fp32 accumulation; exact for
+                             integer-valued data of magnitude <= 256)       */
+    uint32_t reserved[4];
 } etale_config;
 
 typedef struct {

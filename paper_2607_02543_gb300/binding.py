@@ -31,7 +31,8 @@ class Config(C.Structure):
     _fields_ = [("build_beam", C.c_uint32), ("alpha", C.c_float), ("max_hops", C.c_uint32),
                 ("max_cand", C.c_uint32), ("refine", C.c_uint32), ("max_batch", C.c_uint64),
                 ("pool_slabs", C.c_uint64), ("n_entry", C.c_uint32), ("mode", C.c_uint32),
-                ("cas_budget", C.c_uint32), ("reserved", C.c_uint32 * 6)]
+                ("cas_budget", C.c_uint32), ("stage_kb", C.c_uint32), ("gram", C.c_uint32),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class Stats(C.Structure):
@@ -114,7 +115,7 @@ class Index:
     def __init__(self, dim: int, metric: str, degree: int, capacity: int, *, build_beam: int = 0,
                  alpha: float = 0.0, max_hops: int = 0, max_cand: int = 0, refine: str = "default",
                  max_batch: int = 0, pool_slabs: int = 0, n_entry: int = 0, mode: str = "deterministic",
-                 cas_budget: int = 0):
+                 cas_budget: int = 0, stage_kb: int = 0, gram: str = "default"):
         self.lib = load()
         cfg = Config()
         self.lib.etale_config_default(C.byref(cfg))
@@ -130,6 +131,8 @@ class Index:
         cfg.mode = MODES[mode]
         if cas_budget:
             cfg.cas_budget = cas_budget
+        cfg.stage_kb = stage_kb
+        cfg.gram = {"default": 0, "canonical": 1, "tensor": 2}[gram]
         h = C.c_void_p()
         st = self.lib.etale_create(dim, 0 if metric == "l2" else 1, degree, capacity, C.byref(cfg), C.byref(h))
         if st:

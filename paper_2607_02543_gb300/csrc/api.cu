@@ -103,7 +103,8 @@ struct etale_index {
         Dev d;
         d.x = x; d.ref = ref; d.slab = slab; d.free_stack = free_stack; d.retired = retired; d.ctr = ctr;
         d.entries = entries; d.dim = dim; d.mp = mp; d.R = R; d.metric = metric; d.alpha2 = alpha2;
-        d.n_entries = n_entries; d.capacity = capacity; d.pool = pool;
+        d.n_entries = n_entries; d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
+        d.gram = cfg.gram == 2 ? 1u : 0u;
         return d;
     }
 
@@ -393,6 +394,17 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         if (cfg_in->n_entry) cfg.n_entry = cfg_in->n_entry;
         cfg.mode = cfg_in->mode;
         if (cfg_in->cas_budget) cfg.cas_budget = cfg_in->cas_budget;
+        cfg.stage_kb = cfg_in->stage_kb;
+        cfg.gram = cfg_in->gram;
+    }
+    if (cfg.gram > 2) {
+        g_create_error = "gram must be 0..2";
+        return ETALE_EINVAL;
+    }
+    if (cfg.gram == 0) cfg.gram = cfg.mode == ETALE_MODE_LOCKFREE ? 2 : 1;
+    if (cfg.stage_kb > 64) {
+        g_create_error = "stage_kb must be <= 64";
+        return ETALE_EINVAL;
     }
     if (cfg.refine > 2 || cfg.mode > 1 || cfg.build_beam > 256) {
         g_create_error = "refine must be 0..2, mode 0..1, build_beam <= 256";

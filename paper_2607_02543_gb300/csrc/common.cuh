@@ -101,6 +101,8 @@ struct Dev {
     float alpha2;
     u32 n_entries;
     u64 capacity, pool;
+    u32 stage_bytes;   // per-warp RobustPrune row stage (0: rows read from L2)
+    u32 gram;          // 1: domination tests of small prunes use the tensor-core Gram tile
 };
 
 // ---- canonical distance ------------------------------------------------------

@@ -7,6 +7,8 @@
 // order and publish once.  Lock-free mode gives each offer its own warp,
 // which snapshots the target, builds the new list and publishes it with a
 // compare-and-swap, retrying up to the attempt budget (Algorithm 1).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -15,18 +17,245 @@ namespace etale {
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 
 // ---------------------------------------------------------------------------
+// Row staging: the rows of the first `ns` candidates are copied into shared
+// memory by bulk (TMA) copies completing on the warp's mbarrier; later
+// candidates are read from global memory.
+// ---------------------------------------------------------------------------
+struct Stage {
+    float *rows;     // ns_cap x mp floats, 16-byte aligned (nullptr: no staging)
+    int ns_cap;
+    u64 *bar;        // this warp's mbarrier
+    u32 phase;
+    bool timeout;
+    char *gram;      // GRAM_BYTES for the tensor-core Gram path (nullptr: canonical path)
+};
+
+// Tensor-core Gram tile: up to 64 candidates, K staged 128 columns at a time
+// as bf16 rows of GRAM_RS elements (16-byte pad: conflict-free ldmatrix); the
+// 64 x 64 fp32 result reuses the same bytes.
+constexpr int GRAM_N = 64;
+constexpr int GRAM_RS = 136;
+constexpr size_t GRAM_BYTES = (size_t)GRAM_N * GRAM_RS * 2 + GRAM_N * 4;   // rows (or table) + norms
+
+// Shared-memory bytes for a stage of ns rows plus its mbarrier.
+__host__ __device__ inline size_t stage_bytes(u32 ns, u32 mp) { return al16((size_t)ns * mp * 4) + 16; }
+
+// Carve a stage at p (16-byte aligned) and initialise the warp's mbarrier.
+__device__ __forceinline__ Stage stage_init(char *p, u32 ns, u32 mp, char *gram = nullptr) {
+    Stage st;
+    st.rows = ns ? reinterpret_cast<float *>(p) : nullptr;
+    st.ns_cap = (int)ns;
+    st.bar = reinterpret_cast<u64 *>(p + al16((size_t)ns * mp * 4));
+    st.phase = 0;
+    st.timeout = false;
+    st.gram = gram;
+    if (lane_id() == 0) mbar_init(st.bar, 1);
+    __syncwarp();
+    return st;
+}
+
+__device__ __forceinline__ void stage_done(const Dev &d, const Stage &st) {
+    if (st.timeout && lane_id() == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_TIMEOUT);
+}
+
+// Warps per block (<= 4) such that a block's shared memory stays <= 200 KB.
+inline int warps_for(size_t per_warp) {
+    int w = 4;
+    while (w > 1 && (size_t)w * per_warp > 200 * 1024) w >>= 1;
+    return w;
+}
+
+// Rows that fit a per-warp stage of `budget` bytes, capped at `want`.
+inline u32 stage_cap(u32 mp, u32 want, u32 budget) {
+    u32 cap = budget / (mp * 4u);
+    return cap < want ? cap : want;
+}
+
+template <class IdOf>
+__device__ __forceinline__ void stage_rows_by(const Dev &d, Stage &st, int ns, IdOf id_of) {
+    const int lane = lane_id();
+    if (ns <= 0) return;
+    const u32 rowb = d.mp * 4;
+    if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(st.bar, (u32)ns * rowb);
+    }
+    __syncwarp();
+    for (int i = lane; i < ns; i += 32)
+        bulk_g2s(st.rows + (size_t)i * d.mp, d.x + (size_t)id_of(i) * d.mp, rowb, st.bar);
+    if (!mbar_wait(st.bar, st.phase, WAIT_LIMIT)) {
+        st.timeout = true;
+        mbar_wait(st.bar, st.phase, WAIT_LIMIT);
+    }
+    st.phase ^= 1u;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void stage_rows(const Dev &d, Stage &st, const u64 *ck, int ns) {
+    stage_rows_by(d, st, ns, [&](int i) { return key_id(ck[i]); });
+}
+
+
+// ---------------------------------------------------------------------------
+// Candidate Gram tile on the tensor cores (mma.sync m16n8k16, bf16 inputs,
+// fp32 accumulation): G = X X^T for the n <= 64 candidate rows X, one warp.
+// Squared L2 follows as (G_ii - G_ij) + (G_jj - G_ij), inner product as
+// 1 - G_ij.  Inputs rounded to bf16 are exact for integer-valued data of
+// magnitude <= 256, and so is every product and partial sum while the norms
+// stay below 2^24; then each distance equals the canonical one bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ldsm_x4(u32 &r0, u32 &r1, u32 &r2, u32 &r3, u32 addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16_16816(float *c, u32 a0, u32 a1, u32 a2, u32 a3, u32 b0, u32 b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
+    u32 r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// Writes the n x n Gram into T (fp32, row stride GRAM_N) and the diagonal into
+// nrm.  T and the bf16 rows share `buf`.
+__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, float *&T, float *&nrm) {
+    const int lane = lane_id();
+    __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(buf);
+    T = reinterpret_cast<float *>(buf);
+    nrm = reinterpret_cast<float *>(buf + (size_t)GRAM_N * GRAM_RS * 2);
+    const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
+    float acc[4][8][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 8; b++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[a][b][c] = 0.f;
+    const u32 xs = smem_addr(X);
+    for (int k0 = 0; k0 < (int)d.mp; k0 += 128) {
+        // stage columns [k0, k0 + 128) of every candidate row as bf16 (zero pad)
+        __syncwarp();
+        const int col = k0 + 4 * lane;                   // 32 lanes x float4 = 128 columns
+        for (int r0 = 0; r0 < nm * 16; r0 += 16) {
+            float4 v[16];                                // 16 row loads in flight per lane
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const int r = r0 + t;
+                v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < n && col < (int)d.mp)
+                    v[t] = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
+            }
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const uint2 pk = make_uint2(pack_bf16(v[t].x, v[t].y), pack_bf16(v[t].z, v[t].w));
+                *reinterpret_cast<uint2 *>(X + (size_t)(r0 + t) * GRAM_RS + 4 * lane) = pk;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int ks = 0; ks < 8; ks++) {
+#pragma unroll
+            for (int mt = 0; mt < 4; mt++) {
+                if (mt >= nm) break;
+                u32 a0, a1, a2, a3;
+                const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                const int ac = 16 * ks + 8 * (lane >> 4);
+                ldsm_x4(a0, a1, a2, a3, xs + (u32)((ar * GRAM_RS + ac) * 2));
+#pragma unroll
+                for (int nt = 0; nt < 8; nt += 2) {
+                    if (nt >= nn) break;
+                    u32 b0, b1, b2, b3;
+                    const int br = 8 * nt + (lane & 7) + 8 * (lane >> 4);
+                    const int bc = 16 * ks + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(b0, b1, b2, b3, xs + (u32)((br * GRAM_RS + bc) * 2));
+                    mma_bf16_16816(acc[mt][nt], a0, a1, a2, a3, b0, b1);
+                    mma_bf16_16816(acc[mt][nt + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // write the accumulators over the staged rows
+#pragma unroll
+    for (int mt = 0; mt < 4; mt++) {
+        if (mt >= nm) break;
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            if (nt >= nn) break;
+            const int r = 16 * mt + (lane >> 2), c = 8 * nt + 2 * (lane & 3);
+            T[r * GRAM_N + c] = acc[mt][nt][0];
+            T[r * GRAM_N + c + 1] = acc[mt][nt][1];
+            T[(r + 8) * GRAM_N + c] = acc[mt][nt][2];
+            T[(r + 8) * GRAM_N + c + 1] = acc[mt][nt][3];
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) nrm[i] = T[i * GRAM_N + i];
+    __syncwarp();
+}
+
+// RobustPrune on a Gram table: same rule and order as warp_prune.
+__device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *out_id,
+                               float *out_rho, Stage &st) {
+    const int lane = lane_id();
+    float *T, *nrm;
+    warp_gram(d, ck, n, st.gram, T, nrm);
+    for (int i = lane; i < n; i += 32) alive[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1 : 0;
+    __syncwarp();
+    int nout = 0, start = 0;
+    const int R = (int)d.R;
+    while (nout < R) {
+        int head = -1;
+        for (int i0 = start; i0 < n; i0 += 32) {
+            int i = i0 + lane;
+            u32 m = __ballot_sync(FULL, i < n && alive[i]);
+            if (m) { head = i0 + __ffs(m) - 1; break; }
+        }
+        if (head < 0) break;
+        const u64 hk = ck[head];
+        if (lane == 0) { out_id[nout] = key_id(hk); out_rho[nout] = key_rho(hk); }
+        nout++;
+        if (nout == R) break;
+        const float nh = nrm[head];
+        for (int j = head + 1 + lane; j < n; j += 32) {
+            if (!alive[j]) continue;
+            const float g = T[head * GRAM_N + j];
+            // (n_h - g) + (n_j - g): every intermediate stays as small as the result
+            const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
+            if (__fmul_rn(d.alpha2, dd) <= key_rho(ck[j])) alive[j] = 0;
+        }
+        __syncwarp();
+        start = head + 1;
+    }
+    __syncwarp();
+    return nout;
+}
+// ---------------------------------------------------------------------------
 // RobustPrune over n candidates whose keys ck[0..n) are sorted ascending
 // (rho = distance to the owner).  Equal adjacent keys collapse to one.  The
 // head is kept; every later candidate p' with alpha^2 * d(head, p') <= rho(p')
 // is dropped; stop at R.  Distances between candidates are canonical
-// distances of rows in global memory.  Scratch: alive[n], idx[n].
+// distances, 8 lanes per distance, rows taken from the stage when staged.
+// Scratch: alive[n], idx[n].
 // ---------------------------------------------------------------------------
-__device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx,
-                          u32 *out_id, float *out_rho) {
+__device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx, u32 *out_id,
+                          float *out_rho, Stage &st) {
+    if (st.gram && n <= GRAM_N) return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
     const int lane = lane_id();
     const int grp = lane >> 3, g = lane & 7;
+    const int ns = st.rows ? min(n, st.ns_cap) : 0;
+    stage_rows(d, st, ck, ns);
     for (int i = lane; i < n; i += 32) alive[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1 : 0;
     __syncwarp();
+    auto row = [&](int i) -> const float * {
+        return i < ns ? st.rows + (size_t)i * d.mp : d.x + (size_t)key_id(ck[i]) * d.mp;
+    };
     int nout = 0, start = 0;
     const int R = (int)d.R;
     while (nout < R) {
@@ -50,13 +279,13 @@ __device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *ali
             m_cnt += __popc(m);
         }
         __syncwarp();
-        const float *hrow = d.x + (size_t)key_id(hk) * d.mp;
+        const float *hrow = row(head);
         for (int r0 = 0; r0 < m_cnt; r0 += 4) {
             const int c = r0 + grp;
             const int cc = c < m_cnt ? c : m_cnt - 1;
             const u32 j = idx[cc];
             const u64 kj = ck[j];
-            float dd = canon_dist<8>(hrow, d.x + (size_t)key_id(kj) * d.mp, (int)d.mp, (int)d.metric, g);
+            float dd = canon_dist<8>(hrow, row((int)j), (int)d.mp, (int)d.metric, g);
             if (c < m_cnt && g == 0 && __fmul_rn(d.alpha2, dd) <= key_rho(kj)) alive[j] = 0;
         }
         __syncwarp();
@@ -105,7 +334,7 @@ __device__ __forceinline__ bool warp_contains(const u32 *ids, int n, u32 v) {
 // at R the list is RobustPrune(list + v) about the owner (tombstones drop).
 // Scratch: keys[np], alive[np], idx[np] with np >= R + 1 (power of two).
 __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, float vr, u64 *keys,
-                           unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho) {
+                           unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho, Stage &st) {
     const int lane = lane_id();
     if (warp_contains(ids, n, v)) return n;
     const u64 kv = mkkey(vr, v);
@@ -139,7 +368,7 @@ __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, flo
     warp_sort_u64(keys, np);
     int cn = 0;
     for (int i0 = 0; i0 < np; i0 += 32) cn += __popc(__ballot_sync(FULL, keys[i0 + lane] != KEY_INF));
-    int nout = warp_prune(d, keys, cn, alive, idx, oid, orho);
+    int nout = warp_prune(d, keys, cn, alive, idx, oid, orho, st);
     for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
     __syncwarp();
     return nout;
@@ -154,23 +383,25 @@ struct PruneInsArgs {
     u32 first, b;
     const u64 *exp_keys;
     const u32 *exp_count;
-    u32 max_hops, max_cand, np;
+    u32 max_hops, max_cand, np, ns;
     u32 *F_id;
     float *F_rho;
     u32 *F_n;
     Offers of;
 };
 
-__host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R) {
-    return al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4);
+__host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u32 mp) {
+    return stage_bytes(ns, mp) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4);
 }
 
-__global__ void __launch_bounds__(128) prune_insert_kernel(PruneInsArgs a) {
+__global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * prune_ins_warp_bytes(a.np, R);
+    char *p = smem + warp * prune_ins_warp_bytes(a.np, R, a.ns, d.mp);
+    Stage st = stage_init(p, a.ns, d.mp);
+    p += stage_bytes(a.ns, d.mp);
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
     u32 *idx = reinterpret_cast<u32 *>(p); p += al16((size_t)a.np * 4);
@@ -186,7 +417,7 @@ __global__ void __launch_bounds__(128) prune_insert_kernel(PruneInsArgs a) {
         __syncwarp();
         warp_sort_u64(keys, (int)a.np);
         const int n = (int)min(cnt, a.max_cand);
-        const int nout = warp_prune(d, keys, n, alive, idx, oid, orho);
+        const int nout = warp_prune(d, keys, n, alive, idx, oid, orho, st);
         const u32 v = a.first + t;
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
@@ -207,28 +438,32 @@ __global__ void __launch_bounds__(128) prune_insert_kernel(PruneInsArgs a) {
         if (lane == 0) a.F_n[t] = (u32)nout;
         __syncwarp();
     }
+    stage_done(d, st);
 }
 
 cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
                                 u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
                                 const Offers &of, int num_sms, cudaStream_t st) {
     if (b == 0) return cudaSuccess;
-    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, F_id, F_rho, F_n, of};
+    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, 0, F_id, F_rho, F_n, of};
     u32 np = 32;
     while (np < max_hops) np <<= 1;
     a.np = np;
-    size_t smem = 4 * prune_ins_warp_bytes(np, d.R);
+    a.ns = stage_cap(d.mp, max_cand, d.stage_bytes);
+    const size_t wb = prune_ins_warp_bytes(np, d.R, a.ns, d.mp);
+    const int W = warps_for(wb);
+    size_t smem = W * wb;
     cudaError_t e = cudaFuncSetAttribute(prune_insert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_insert_kernel, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_insert_kernel, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    u32 blocks = (u32)(per_sm * num_sms), need = (b + 3) / 4;
+    u32 blocks = (u32)(per_sm * num_sms), need = (b + W - 1) / W;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    prune_insert_kernel<<<blocks, 128, smem, st>>>(a);
+    prune_insert_kernel<<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -243,19 +478,24 @@ struct FoldArgs {
     const u32 *seg_start;
     const u64 *seg_count;
     u32 budget;   // 0 = deterministic
-    u32 np;
+    u32 np, ns, gram;
 };
 
-__host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R) {
-    return 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4);
+__host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
+    return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) +
+           al16((size_t)np * 4) + (gram ? al16(GRAM_BYTES) : 0);
 }
 
-__global__ void __launch_bounds__(128) offer_fold_kernel(FoldArgs a) {
+__global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * fold_warp_bytes(a.np, R);
+    char *p = smem + warp * fold_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
+    char *gbuf = a.gram ? p : nullptr;
+    if (a.gram) p += al16(GRAM_BYTES);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += stage_bytes(a.ns, d.mp);
     const size_t lb = al16((size_t)R * 4 + 4);
     u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
     float *lrho = reinterpret_cast<float *>(p); p += lb;
@@ -283,7 +523,7 @@ __global__ void __launch_bounds__(128) offer_fold_kernel(FoldArgs a) {
             for (u32 q = lo; q < hi; q++) {
                 const u32 pi = a.of.val[q];
                 n = apply_offer(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
-                                tid, trho);
+                                tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
                 if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
@@ -299,7 +539,7 @@ __global__ void __launch_bounds__(128) offer_fold_kernel(FoldArgs a) {
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
-                const int n = apply_offer(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho);
+                const int n = apply_offer(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, w, lid, lrho, n, snap);
                 u64 err = 0;
@@ -310,27 +550,31 @@ __global__ void __launch_bounds__(128) offer_fold_kernel(FoldArgs a) {
         }
         __syncwarp();
     }
+    stage_done(d, st);
 }
 
 cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
                               u32 budget, int num_sms, cudaStream_t st) {
     if (of.n == 0) return cudaSuccess;
-    FoldArgs a{d, of, seg_start, seg_count, budget, 0};
+    FoldArgs a{d, of, seg_start, seg_count, budget, 0, 0, d.gram};
     u32 np = 32;
     while (np < d.R + 1) np <<= 1;
     a.np = np;
-    size_t smem = 4 * fold_warp_bytes(np, d.R);
+    a.ns = d.gram ? 0 : stage_cap(d.mp, d.R + 1, d.stage_bytes);
+    const size_t wb = fold_warp_bytes(np, d.R, a.ns, d.mp, a.gram);
+    const int W = warps_for(wb);
+    size_t smem = W * wb;
     cudaError_t e = cudaFuncSetAttribute(offer_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, offer_fold_kernel, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, offer_fold_kernel, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    u32 blocks = (u32)(per_sm * num_sms), need = (of.n + 3) / 4;
+    u32 blocks = (u32)(per_sm * num_sms), need = (of.n + W - 1) / W;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    offer_fold_kernel<<<blocks, 128, smem, st>>>(a);
+    offer_fold_kernel<<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -342,21 +586,23 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
 // ---------------------------------------------------------------------------
 struct RefineArgs {
     Dev d;
-    u32 first, b, mode, max_cand, cap, np;
+    u32 first, b, mode, max_cand, cap, np, ns;
     Offers of;
 };
 
-__host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R) {
-    return 4 * al16((size_t)R * 4) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) +
-           al16((size_t)cap * 4);
+__host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 ns, u32 mp) {
+    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + al16((size_t)np * 8) + al16(np) +
+           al16((size_t)np * 4) + al16((size_t)cap * 4);
 }
 
-__global__ void __launch_bounds__(64) refine_kernel(RefineArgs a) {
+__global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R);
+    char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R, a.ns, d.mp);
+    Stage st = stage_init(p, a.ns, d.mp);
+    p += stage_bytes(a.ns, d.mp);
     u32 *nid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *nrho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
     u32 *oid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
@@ -444,7 +690,7 @@ __global__ void __launch_bounds__(64) refine_kernel(RefineArgs a) {
         __syncwarp();
         warp_sort_u64(buf, np3);
         const int n = min(nc, (int)a.max_cand);
-        const int nout = warp_prune(d, buf, n, alive, idx, oid, orho);
+        const int nout = warp_prune(d, buf, n, alive, idx, oid, orho, st);
         if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
             if (!warp_publish(d, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         }
@@ -463,6 +709,7 @@ __global__ void __launch_bounds__(64) refine_kernel(RefineArgs a) {
         }
         __syncwarp();
     }
+    stage_done(d, st);
 }
 
 cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
@@ -476,7 +723,8 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     u32 np = 32;
     while (np < cap + d.R) np <<= 1;
     a.np = np;
-    const size_t wb = refine_warp_bytes(np, cap, d.R);
+    a.ns = stage_cap(d.mp, max_cand, d.stage_bytes);
+    const size_t wb = refine_warp_bytes(np, cap, d.R, a.ns, d.mp);
     const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
     size_t smem = warps * wb;
     cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -527,7 +775,7 @@ struct RepairKArgs {
     Dev d;
     const u32 *dt;
     const u64 *n_dt;
-    u32 max_n;
+    u32 max_n, ns;
     u32 *pair_key, *pair_val;
     uint2 *pair_K;
     u32 *pair_Kn;
@@ -540,17 +788,20 @@ __host__ __device__ inline u32 repk_np(u32 R) {
     return np;
 }
 
-__host__ __device__ inline size_t repk_warp_bytes(u32 R) {
+__host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp) {
     const u32 np = repk_np(R);
-    return 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)np * 8) + al16(np);
+    return stage_bytes(ns, mp) + 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)np * 8) +
+           al16(np);
 }
 
-__global__ void __launch_bounds__(128) repair_k_kernel(RepairKArgs a) {
+__global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * repk_warp_bytes(R);
+    char *p = smem + warp * repk_warp_bytes(R, a.ns, d.mp);
+    Stage st = stage_init(p, a.ns, d.mp);
+    p += stage_bytes(a.ns, d.mp);
     u32 *bid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     u32 *bdel = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     u32 *cj = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
@@ -577,13 +828,18 @@ __global__ void __launch_bounds__(128) repair_k_kernel(RepairKArgs a) {
             bdel[j] = ref_del(ld_ref(d, bid[j]));
         }
         __syncwarp();
-        // distance table among B (symmetric)
+        // distance table among B (symmetric), rows staged in shared memory
+        const int nsb = st.rows ? min(nb, st.ns_cap) : 0;
+        stage_rows_by(d, st, nsb, [&](int i) { return bid[i]; });
+        auto brow = [&](int i) -> const float * {
+            return i < nsb ? st.rows + (size_t)i * d.mp : d.x + (size_t)bid[i] * d.mp;
+        };
         for (int x = 0; x < nb; x++) {
-            const float *xr = d.x + (size_t)bid[x] * d.mp;
+            const float *xr = brow(x);
             for (int y0 = x + 1; y0 < nb; y0 += 4) {
                 const int y = y0 + grp;
                 const int yy = y < nb ? y : nb - 1;
-                float dd = canon_dist<8>(xr, d.x + (size_t)bid[yy] * d.mp, (int)d.mp, (int)d.metric, g);
+                float dd = canon_dist<8>(xr, brow(yy), (int)d.mp, (int)d.metric, g);
                 if (y < nb && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
             }
         }
@@ -639,24 +895,27 @@ __global__ void __launch_bounds__(128) repair_k_kernel(RepairKArgs a) {
             __syncwarp();
         }
     }
+    stage_done(d, st);
 }
 
 cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
                             u32 *pair_val, uint2 *pair_K, u32 *pair_Kn, int num_sms, cudaStream_t st) {
     if (max_n == 0) return cudaSuccess;
-    RepairKArgs a{d, dt, n_dt, max_n, pair_key, pair_val, pair_K, pair_Kn};
-    size_t smem = 4 * repk_warp_bytes(d.R);
+    RepairKArgs a{d, dt, n_dt, max_n, stage_cap(d.mp, d.R, d.stage_bytes), pair_key, pair_val, pair_K, pair_Kn};
+    const size_t wb = repk_warp_bytes(d.R, a.ns, d.mp);
+    const int W = warps_for(wb);
+    size_t smem = W * wb;
     cudaError_t e = cudaFuncSetAttribute(repair_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_k_kernel, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_k_kernel, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    u32 blocks = (u32)(per_sm * num_sms), need = (max_n + 3) / 4;
+    u32 blocks = (u32)(per_sm * num_sms), need = (max_n + W - 1) / W;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    repair_k_kernel<<<blocks, 128, smem, st>>>(a);
+    repair_k_kernel<<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -673,15 +932,16 @@ struct RepairFoldArgs {
     const u32 *seg_start;
     const u64 *seg_count;
     u64 n_pairs;
-    u32 budget, np;
+    u32 budget, np, ns, gram;
 };
 
-__host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R) {
-    return 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4);
+__host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
+    return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) +
+           al16((size_t)np * 4) + (gram ? al16(GRAM_BYTES) : 0);
 }
 
 __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
-                            unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho) {
+                            unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho, Stage &st) {
     const int lane = lane_id();
     for (int i = lane; i < np; i += 32) {
         u64 k = KEY_INF;
@@ -697,18 +957,22 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     warp_sort_u64(keys, np);
     int cn = 0;
     for (int i0 = 0; i0 < np; i0 += 32) cn += __popc(__ballot_sync(FULL, keys[i0 + lane] != KEY_INF));
-    const int nout = warp_prune(d, keys, cn, alive, idx, tid, trho);
+    const int nout = warp_prune(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
     return nout;
 }
 
-__global__ void __launch_bounds__(128) repair_fold_kernel(RepairFoldArgs a) {
+__global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * repf_warp_bytes(a.np, R);
+    char *p = smem + warp * repf_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
+    char *gbuf = a.gram ? p : nullptr;
+    if (a.gram) p += al16(GRAM_BYTES);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += stage_bytes(a.ns, d.mp);
     const size_t lb = al16((size_t)R * 4 + 4);
     u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
     float *lrho = reinterpret_cast<float *>(p); p += lb;
@@ -736,7 +1000,7 @@ __global__ void __launch_bounds__(128) repair_fold_kernel(RepairFoldArgs a) {
             for (u32 q = lo; q < hi; q++) {
                 const u32 pv = a.pair_val[q];
                 n = repair_apply(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
-                                 alive, idx, (int)a.np, tid, trho);
+                                 alive, idx, (int)a.np, tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
                 if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
@@ -752,7 +1016,7 @@ __global__ void __launch_bounds__(128) repair_fold_kernel(RepairFoldArgs a) {
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
                 const int n = repair_apply(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
-                                           (int)a.pair_Kn[pv], keys, alive, idx, (int)a.np, tid, trho);
+                                           (int)a.pair_Kn[pv], keys, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, w, lid, lrho, n, snap);
                 u64 err = 0;
@@ -763,29 +1027,33 @@ __global__ void __launch_bounds__(128) repair_fold_kernel(RepairFoldArgs a) {
         }
         __syncwarp();
     }
+    stage_done(d, st);
 }
 
 cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key, const u32 *pair_val,
                                     const uint2 *pair_K, const u32 *pair_Kn, const u32 *seg_start,
                                     const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0};
+    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0, 0, d.gram};
     u32 np = 32;
     while (np < 2 * d.R) np <<= 1;
     a.np = np;
-    size_t smem = 4 * repf_warp_bytes(np, d.R);
+    a.ns = d.gram ? 0 : stage_cap(d.mp, 2 * d.R, d.stage_bytes);
+    const size_t wb = repf_warp_bytes(np, d.R, a.ns, d.mp, a.gram);
+    const int W = warps_for(wb);
+    size_t smem = W * wb;
     cudaError_t e = cudaFuncSetAttribute(repair_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_fold_kernel, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_fold_kernel, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    u64 need = (n_pairs + 3) / 4;
+    u64 need = (n_pairs + W - 1) / W;
     u32 blocks = (u32)(per_sm * num_sms);
     if ((u64)blocks > need) blocks = (u32)need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    repair_fold_kernel<<<blocks, 128, smem, st>>>(a);
+    repair_fold_kernel<<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -11,10 +11,12 @@ ORACLE_REFINE = {"off": 0, "peers": 2}
 
 
 def make_pair(oracle_mod, dim, metric, degree, capacity, *, build_beam=64, alpha=1.2, refine="peers",
-              max_batch=0, n_entry=0, mode="deterministic", max_cand=0, max_hops=0, with_oracle=True):
+              max_batch=0, n_entry=0, mode="deterministic", max_cand=0, max_hops=0, with_oracle=True,
+              gram="default", stage_kb=0):
     from paper_2607_02543_gb300 import Index
     g = Index(dim, metric, degree, capacity, build_beam=build_beam, alpha=alpha, refine=refine,
-              max_batch=max_batch, n_entry=n_entry, mode=mode, max_cand=max_cand, max_hops=max_hops)
+              max_batch=max_batch, n_entry=n_entry, mode=mode, max_cand=max_cand, max_hops=max_hops,
+              gram=gram, stage_kb=stage_kb)
     o = None
     if with_oracle:
         o = oracle_mod.Oracle(dim, metric, degree, capacity, build_beam=build_beam, alpha=alpha,

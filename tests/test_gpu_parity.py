@@ -63,21 +63,29 @@ def test_hand_derived_line(oracle_mod):
 
 
 CASES = [
-    # (dim, metric, degree, kind, n_base, build_beam)
-    (128, "l2", 32, "gauss", 2000, 64),      # several tiles of every kernel
-    (37, "l2", 16, "gauss", 900, 32),        # ragged dimension (rows padded to 40)
-    (96, "ip", 64, "unit", 1200, 64),        # inner product, degree 64 (two slab chunks)
-    (128, "l2", 32, "int", 1500, 96),        # integer-valued (exact distances)
+    # (dim, metric, degree, kind, n_base, build_beam, gpu options)
+    (128, "l2", 32, "gauss", 2000, 64, {}),      # several tiles of every kernel
+    (37, "l2", 16, "gauss", 900, 32, {}),        # ragged dimension (rows padded to 40)
+    (96, "ip", 64, "unit", 1200, 64, {}),        # inner product, degree 64 (two slab chunks)
+    (128, "l2", 32, "int", 1500, 96, {}),        # integer-valued (exact distances)
+    # tensor-core Gram tiles in the reverse-offer and repair prunes: on
+    # integer-valued data of magnitude <= 256 every bf16 product and fp32 sum
+    # is exact, so the result must still match the oracle bit for bit
+    (128, "l2", 32, "int", 1500, 96, {"gram": "tensor"}),
+    (200, "l2", 24, "int", 800, 48, {"gram": "tensor"}),   # two K chunks of 128, ragged
+    # rows staged in shared memory by bulk copies (canonical arithmetic)
+    (128, "l2", 32, "gauss", 1200, 64, {"stage_kb": 24}),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"d{c[0]}-{c[1]}-R{c[2]}-{c[3]}")
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"d{c[0]}-{c[1]}-R{c[2]}-{c[3]}-" +
+                         ("-".join(f"{k}{v}" for k, v in c[6].items()) or "base"))
 def test_deterministic_parity(oracle_mod, case):
-    dim, metric, R, kind, n, beam = case
+    dim, metric, R, kind, n, beam, opts = case
     w = W.Workload(f"parity-{kind}", n, dim, metric, R, beam, 3, max(1, n // 100), max(1, n // 100), 300, 10,
                    beam, 16, kind)
     plan = W.make_plan(w)
-    g, o = make_pair(oracle_mod, dim, metric, R, w.capacity, build_beam=beam)
+    g, o = make_pair(oracle_mod, dim, metric, R, w.capacity, build_beam=beam, **opts)
     gi = g.insert(plan.base)
     oi = o.insert(plan.base)
     assert gi.tolist() == oi.tolist()
