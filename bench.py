@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--search-beam", type=int, default=0,
                     help="EF_SEARCH; default: the smallest of 64..256 reaching Recall@10 >= 0.95")
     ap.add_argument("--n-entry", type=int, default=4096)
+    ap.add_argument("--max-cand", type=int, default=64,
+                    help="RobustPrune candidates kept; 64 fits the tensor-core Gram tile (library default: 2 * build beam)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
@@ -165,7 +167,7 @@ def config_dict(w, args):
     return {"workload": w.name, "n_live": w.n_base, "dim": w.dim, "metric": w.metric, "degree": w.degree,
             "build_beam": w.build_beam, "churn_per_round": [w.n_delete, w.n_insert],
             "queries_per_step": w.n_queries, "k": w.k, "search_beam": args.search_beam or w.search_beam,
-            "mode": args.mode, "n_entry": args.n_entry,
+            "mode": args.mode, "n_entry": args.n_entry, "max_cand": args.max_cand or 2 * w.build_beam,
             "l2": "working set (index > 600 MB) larger than L2; no flush" if w.n_base >= 1_000_000 else
                   "small index; no flush", "parallelism": f"replicas x{args.gpus}"}
 
@@ -196,7 +198,7 @@ def main():
     plan = W.make_plan(wr)
     n_entry = args.n_entry
     idx = Index(w.dim, w.metric, w.degree, wr.capacity, build_beam=w.build_beam, mode=args.mode,
-                n_entry=n_entry)
+                n_entry=n_entry, max_cand=args.max_cand)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()

@@ -7,7 +7,7 @@ namespace etale {
 
 struct SearchTuning {
     u32 stage_rows = 16;   // rows gathered per bulk-copy batch
-    u32 seen_bits = 10;    // log2 of the evaluated-id cache slots
+    u32 seen_bits = 9;     // log2 of the evaluated-id cache slots
 };
 
 // search.cu

@@ -35,13 +35,10 @@ struct SearchArgs {
 struct WarpSmem {
     float *qv;       // mp
     float *stage;    // stage_rows x mp
-    u64 *bkey0, *bkey1;          // beam keys, double-buffered (L each)
-    u64 *bref0, *bref1;          // reference word sampled when the entry was evaluated
-    unsigned char *bflag0, *bflag1;   // expanded flag
-    __device__ __forceinline__ u64 *bkey(int c) const { return c ? bkey1 : bkey0; }
-    __device__ __forceinline__ u64 *bref(int c) const { return c ? bref1 : bref0; }
-    __device__ __forceinline__ unsigned char *bflag(int c) const { return c ? bflag1 : bflag0; }
-    u64 *nkey;       // 32
+    u64 *bkey;       // beam keys (L), ascending
+    u64 *bref;       // reference word sampled when the entry was evaluated
+    unsigned char *bflag;   // expanded flag
+    u64 *nkey;       // 32: surviving new keys, sorted
     u64 *nref;       // 32
     u32 *cid;        // 32 candidate ids
     u64 *ckey;       // 32
@@ -56,8 +53,8 @@ __host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_row
     size_t b = 0;
     b += align_up((size_t)mp * 4, 128);
     b += align_up((size_t)stage_rows * mp * 4, 128);
-    b += 2 * align_up((size_t)L * 8, 16) * 2;
-    b += 2 * align_up((size_t)L, 16);
+    b += 2 * align_up((size_t)L * 8, 16);
+    b += align_up((size_t)L, 16);
     b += 32 * 8 * 2 + 32 * 4 + 32 * 8 * 2;
     b += align_up((size_t)seen_slots * 4, 16);
     b += 16;
@@ -68,12 +65,9 @@ __device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 see
     WarpSmem s;
     s.qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 128);
     s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * mp * 4, 128);
-    s.bkey0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
-    s.bkey1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
-    s.bref0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
-    s.bref1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
-    s.bflag0 = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
-    s.bflag1 = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
+    s.bkey = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    s.bref = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
+    s.bflag = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
     s.nkey = reinterpret_cast<u64 *>(p); p += 32 * 8;
     s.nref = reinterpret_cast<u64 *>(p); p += 32 * 8;
     s.ckey = reinterpret_cast<u64 *>(p); p += 32 * 8;
@@ -86,10 +80,75 @@ __device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 see
 
 __device__ __forceinline__ u32 seen_slot(u32 id, u32 bits) { return (id * 2654435761u) >> (32 - bits); }
 
+__device__ __forceinline__ int lower_bound(const u64 *a, int n, u64 key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Merge the candidate keys held one per lane (KEY_INF = none) into the beam
+// in place.  Only keys that can enter the beam take part; entries before the
+// first insertion point do not move.  Returns the new beam size.
+__device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L) {
+    const int lane = lane_id();
+    const u64 *bk = s.bkey;
+    // drop keys that cannot enter a full beam, and keys already in the beam
+    int lb = 0;
+    if (key != KEY_INF) {
+        if (n == L && key >= bk[n - 1]) {
+            key = KEY_INF;
+        } else {
+            lb = lower_bound(bk, n, key);
+            if (lb < n && bk[lb] == key) key = KEY_INF;
+        }
+    }
+    const u32 vm = __ballot_sync(FULL, key != KEY_INF);
+    if (vm == 0) return n;
+    int rank = 0;
+    for (u32 m = vm; m; m &= m - 1) {
+        const u64 o = __shfl_sync(FULL, key, __ffs(m) - 1);
+        rank += (o < key);
+    }
+    const int c = __popc(vm);
+    if (key != KEY_INF) { s.nkey[rank] = key; s.nref[rank] = ref; }
+    // the first insertion point is the lower bound of the smallest new key
+    int p0 = (key != KEY_INF && rank == 0) ? lb : 0x7fffffff;
+    for (int o = 16; o >= 1; o >>= 1) p0 = min(p0, __shfl_xor_sync(FULL, p0, o));
+    __syncwarp();
+    // move entries [p0, n) down, last chunk first so no unread entry is overwritten
+    const int nmove = n - p0;
+    for (int c0 = ((nmove - 1) >> 5) << 5; c0 >= 0 && nmove > 0; c0 -= 32) {
+        const int i = p0 + c0 + lane;
+        u64 k2 = 0, r2 = 0;
+        unsigned char f2 = 0;
+        int pos = 0x7fffffff;
+        if (c0 + lane < nmove) {
+            k2 = bk[i];
+            r2 = s.bref[i];
+            f2 = s.bflag[i];
+            int cnt = 0;
+            for (int j = 0; j < c; j++) cnt += (s.nkey[j] < k2);
+            pos = i + cnt;
+        }
+        __syncwarp();
+        if (pos < L) { s.bkey[pos] = k2; s.bref[pos] = r2; s.bflag[pos] = f2; }
+        __syncwarp();
+    }
+    if (key != KEY_INF) {
+        const int pos = lb + rank;
+        if (pos < L) { s.bkey[pos] = key; s.bref[pos] = ref; s.bflag[pos] = 0; }
+    }
+    __syncwarp();
+    return min(L, n + c);
+}
+
 // Evaluate the candidate ids held one per lane (NIL = none) and merge them
 // into the beam.  Returns the new beam size.  `phase` tracks the mbarrier.
-__device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, int &cur, u32 &phase,
-                          u64 &ndist, bool &timeout) {
+__device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u32 &phase, u64 &ndist,
+                          bool &timeout) {
     const Dev &d = a.d;
     const int lane = lane_id();
     const u32 mp = d.mp;
@@ -130,61 +189,11 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, in
         __syncwarp();
     }
     ndist += cnt;
-    // this lane's candidate (sorted rank among valid keys)
-    u64 key = lane < cnt ? s.ckey[lane] : KEY_INF;
-    u64 ref = lane < cnt ? s.cref[lane] : 0;
+    const u64 key = lane < cnt ? s.ckey[lane] : KEY_INF;
+    const u64 ref = lane < cnt ? s.cref[lane] : 0;
     if (lane < cnt) s.seen[seen_slot(key_id(key), a.seen_bits)] = key_id(key);
-    const u64 *bk = s.bkey(cur);
-    // drop keys that cannot enter a full beam, and keys already in the beam
-    if (key != KEY_INF) {
-        if (n == (int)a.L && key >= bk[n - 1]) {
-            key = KEY_INF;
-        } else {
-            int lo = 0, hi = n;                      // first beam key >= key
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (bk[mid] < key) lo = mid + 1; else hi = mid; }
-            if (lo < n && bk[lo] == key) key = KEY_INF;
-        }
-    }
-    // rank among surviving new keys (keys are distinct)
-    int rank = 0;
-    for (int j = 0; j < 32; j++) {
-        u64 o = __shfl_sync(FULL, key, j);
-        rank += (o < key);
-    }
-    const u32 vm = __ballot_sync(FULL, key != KEY_INF);
-    const int c = __popc(vm);
-    if (c == 0) return n;
-    if (key != KEY_INF) { s.nkey[rank] = key; s.nref[rank] = ref; }
-    __syncwarp();
-    const int nxt = cur ^ 1;
-    const int L = (int)a.L;
-    for (int i = lane; i < n; i += 32) {             // beam entries move down
-        u64 bkey = bk[i];
-        int lo = 0, hi = c;
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (s.nkey[mid] < bkey) lo = mid + 1; else hi = mid; }
-        int pos = i + lo;
-        if (pos < L) {
-            s.bkey(nxt)[pos] = bkey;
-            s.bref(nxt)[pos] = s.bref(cur)[i];
-            s.bflag(nxt)[pos] = s.bflag(cur)[i];
-        }
-    }
-    if (lane < c) {                                   // new entries slot in
-        u64 nk = s.nkey[lane];
-        int lo = 0, hi = n;
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (bk[mid] < nk) lo = mid + 1; else hi = mid; }
-        int pos = lane + lo;
-        if (pos < L) {
-            s.bkey(nxt)[pos] = nk;
-            s.bref(nxt)[pos] = s.nref[lane];
-            s.bflag(nxt)[pos] = 0;
-        }
-    }
-    __syncwarp();
-    cur = nxt;
-    return min(L, n + c);
+    return merge_beam(s, key, ref, n, (int)a.L);
 }
-
 
 // ---------------------------------------------------------------------------
 // Seeding: for each query, the L nearest members of the entry set E by
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(128, 1) search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -301,44 +310,64 @@ __global__ void __launch_bounds__(128, 1) search_kernel(SearchArgs a) {
         __syncwarp();
         // initial beam: the L nearest members of the entry set E, computed by
         // seed_kernel; the reference words are sampled here
-        int cur = 0;
         const int n0 = (int)min(a.L, d.n_entries);
         for (int i = lane; i < n0; i += 32) {
             const u64 k = a.seed[(size_t)qi * a.L + i];
             const u32 id = key_id(k);
-            s.bkey(0)[i] = k;
-            s.bref(0)[i] = ld_ref(d, id);
-            s.bflag(0)[i] = 0;
+            s.bkey[i] = k;
+            s.bref[i] = ld_ref(d, id);
+            s.bflag[i] = 0;
             s.seen[seen_slot(id, a.seen_bits)] = id;
         }
         int n = n0;
         __syncwarp();
         u32 hops = 0, nexp = 0;
+        // slab entries of the predicted next expansion, loaded ahead of use
+        u32 pf_id = NIL, pf0 = NIL, pf1 = NIL;
         for (;;) {
             int first = -1;
             for (int i0 = 0; i0 < n; i0 += 32) {
                 int i = i0 + lane;
-                u32 m = __ballot_sync(FULL, i < n && !s.bflag(cur)[i]);
+                u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
                 if (m) { first = i0 + __ffs(m) - 1; break; }
             }
             if (first < 0 || hops >= a.max_hops) break;
             hops++;
-            const u64 r = s.bref(cur)[first];
-            const u64 bkey = s.bkey(cur)[first];
+            const u64 r = s.bref[first];
+            const u64 bkey = s.bkey[first];
+            const u32 fid = key_id(bkey);
+            const u32 sl = ref_slab(r), deg = sl == NIL ? 0 : ref_deg(r);
+            u32 e0 = NIL, e1 = NIL;
+            if (fid == pf_id) {
+                e0 = pf0; e1 = pf1;
+            } else {
+                if ((u32)lane < deg) e0 = d.slab[(size_t)sl * d.R + lane].x;
+                if ((u32)lane + 32 < deg) e1 = d.slab[(size_t)sl * d.R + lane + 32].x;
+            }
+            // predict the next expansion: the next unexpanded beam entry
+            pf_id = NIL;
+            for (int i0 = first + 1; i0 < n; i0 += 32) {
+                int i = i0 + lane;
+                u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
+                if (m) {
+                    const int nx = i0 + __ffs(m) - 1;
+                    const u64 r2 = s.bref[nx];
+                    const u32 s2 = ref_slab(r2), d2 = s2 == NIL ? 0 : ref_deg(r2);
+                    pf_id = key_id(s.bkey[nx]);
+                    pf0 = (u32)lane < d2 ? d.slab[(size_t)s2 * d.R + lane].x : NIL;
+                    pf1 = (u32)lane + 32 < d2 ? d.slab[(size_t)s2 * d.R + lane + 32].x : NIL;
+                    break;
+                }
+            }
             __syncwarp();
-            if (lane == 0) s.bflag(cur)[first] = 1;
+            if (lane == 0) s.bflag[first] = 1;
             if (a.mode == 1 && lane == 0 && !ref_del(r)) a.exp_keys[(size_t)qi * a.max_hops + nexp] = bkey;
             if (!ref_del(r)) nexp++;
-            const u32 sl = ref_slab(r), deg = ref_deg(r);
             __syncwarp();
-            if (sl == NIL) continue;
             for (u32 j0 = 0; j0 < deg; j0 += 32) {
-                u32 nb = NIL;
-                if (j0 + lane < deg) {
-                    nb = d.slab[(size_t)sl * d.R + j0 + lane].x;
-                    if (s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
-                }
-                n = eval_merge(a, s, nb, n, cur, phase, ndist, timeout);
+                u32 nb = j0 == 0 ? e0 : e1;
+                if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
+                n = eval_merge(a, s, nb, n, phase, ndist, timeout);
             }
         }
         nexp_tot += hops;
@@ -347,12 +376,12 @@ __global__ void __launch_bounds__(128, 1) search_kernel(SearchArgs a) {
             u32 c = 0;
             for (int i0 = 0; i0 < n && c < a.k; i0 += 32) {
                 int i = i0 + lane;
-                bool ok = i < n && !ref_del(s.bref(cur)[i]);
+                bool ok = i < n && !ref_del(s.bref[i]);
                 u32 m = __ballot_sync(FULL, ok);
                 u32 pos = c + __popc(m & lanemask_lt());
                 if (ok && pos < a.k) {
-                    a.out_ids[(size_t)qi * a.k + pos] = key_id(s.bkey(cur)[i]);
-                    a.out_dist[(size_t)qi * a.k + pos] = key_rho(s.bkey(cur)[i]);
+                    a.out_ids[(size_t)qi * a.k + pos] = key_id(s.bkey[i]);
+                    a.out_dist[(size_t)qi * a.k + pos] = key_rho(s.bkey[i]);
                 }
                 c += __popc(m);
             }

@@ -383,15 +383,16 @@ struct PruneInsArgs {
     u32 first, b;
     const u64 *exp_keys;
     const u32 *exp_count;
-    u32 max_hops, max_cand, np, ns;
+    u32 max_hops, max_cand, np, ns, gram;
     u32 *F_id;
     float *F_rho;
     u32 *F_n;
     Offers of;
 };
 
-__host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u32 mp) {
-    return stage_bytes(ns, mp) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4);
+__host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
+    return stage_bytes(ns, mp) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4) +
+           (gram ? al16(GRAM_BYTES) : 0);
 }
 
 __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
@@ -399,8 +400,10 @@ __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * prune_ins_warp_bytes(a.np, R, a.ns, d.mp);
-    Stage st = stage_init(p, a.ns, d.mp);
+    char *p = smem + warp * prune_ins_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
+    char *gbuf = a.gram ? p : nullptr;
+    if (a.gram) p += al16(GRAM_BYTES);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf);
     p += stage_bytes(a.ns, d.mp);
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
@@ -445,12 +448,14 @@ cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_k
                                 u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
                                 const Offers &of, int num_sms, cudaStream_t st) {
     if (b == 0) return cudaSuccess;
-    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, 0, F_id, F_rho, F_n, of};
+    // the Gram tile covers the prune only when every candidate fits in it
+    const u32 gram = d.gram && max_cand <= (u32)GRAM_N ? 1u : 0u;
+    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, 0, gram, F_id, F_rho, F_n, of};
     u32 np = 32;
     while (np < max_hops) np <<= 1;
     a.np = np;
-    a.ns = stage_cap(d.mp, max_cand, d.stage_bytes);
-    const size_t wb = prune_ins_warp_bytes(np, d.R, a.ns, d.mp);
+    a.ns = gram ? 0 : stage_cap(d.mp, max_cand, d.stage_bytes);
+    const size_t wb = prune_ins_warp_bytes(np, d.R, a.ns, d.mp, gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
     cudaError_t e = cudaFuncSetAttribute(prune_insert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -586,13 +591,13 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
 // ---------------------------------------------------------------------------
 struct RefineArgs {
     Dev d;
-    u32 first, b, mode, max_cand, cap, np, ns;
+    u32 first, b, mode, max_cand, cap, np, ns, gram;
     Offers of;
 };
 
-__host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 ns, u32 mp) {
+__host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 ns, u32 mp, u32 gram) {
     return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + al16((size_t)cap * 4);
+           al16((size_t)np * 4) + al16((size_t)cap * 4) + (gram ? al16(GRAM_BYTES) : 0);
 }
 
 __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
@@ -600,8 +605,10 @@ __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R, a.ns, d.mp);
-    Stage st = stage_init(p, a.ns, d.mp);
+    char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R, a.ns, d.mp, a.gram);
+    char *gbuf = a.gram ? p : nullptr;
+    if (a.gram) p += al16(GRAM_BYTES);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf);
     p += stage_bytes(a.ns, d.mp);
     u32 *nid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *nrho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
@@ -723,8 +730,9 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     u32 np = 32;
     while (np < cap + d.R) np <<= 1;
     a.np = np;
-    a.ns = stage_cap(d.mp, max_cand, d.stage_bytes);
-    const size_t wb = refine_warp_bytes(np, cap, d.R, a.ns, d.mp);
+    a.gram = d.gram;
+    a.ns = d.gram ? 0 : stage_cap(d.mp, max_cand, d.stage_bytes);
+    const size_t wb = refine_warp_bytes(np, cap, d.R, a.ns, d.mp, a.gram);
     const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
     size_t smem = warps * wb;
     cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
