@@ -214,6 +214,44 @@ __host__ __device__ inline size_t seed_warp_bytes(u32 mp, u32 L) {
     return align_up((size_t)mp * 4, 16) + 2 * align_up((size_t)L * 8, 16) + 32 * 8;
 }
 
+// In-place merge of the keys held one per lane (KEY_INF = none) into a sorted
+// top-L list of keys (the seed kernel's variant of merge_beam: keys only).
+__device__ int seed_merge(u64 *bk, u64 *nk, u64 key, int n, int L) {
+    const int lane = lane_id();
+    int lb = 0;
+    if (key != KEY_INF) {
+        if (n == L && key >= bk[n - 1]) key = KEY_INF;
+        else lb = lower_bound(bk, n, key);
+    }
+    const u32 vm = __ballot_sync(FULL, key != KEY_INF);
+    if (vm == 0) return n;
+    int rank = 0;
+    for (u32 m = vm; m; m &= m - 1) rank += (__shfl_sync(FULL, key, __ffs(m) - 1) < key);
+    const int c = __popc(vm);
+    if (key != KEY_INF) nk[rank] = key;
+    int p0 = (key != KEY_INF && rank == 0) ? lb : 0x7fffffff;
+    for (int o = 16; o >= 1; o >>= 1) p0 = min(p0, __shfl_xor_sync(FULL, p0, o));
+    __syncwarp();
+    const int nmove = n - p0;
+    for (int c0 = ((nmove - 1) >> 5) << 5; c0 >= 0 && nmove > 0; c0 -= 32) {
+        const int i = p0 + c0 + lane;
+        u64 k2 = 0;
+        int pos = 0x7fffffff;
+        if (c0 + lane < nmove) {
+            k2 = bk[i];
+            int cnt = 0;
+            for (int j = 0; j < c; j++) cnt += (nk[j] < k2);
+            pos = i + cnt;
+        }
+        __syncwarp();
+        if (pos < L) bk[pos] = k2;
+        __syncwarp();
+    }
+    if (key != KEY_INF && lb + rank < L) bk[lb + rank] = key;
+    __syncwarp();
+    return min(L, n + c);
+}
+
 __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     extern __shared__ __align__(16) char ssm[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -232,7 +270,7 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
             *reinterpret_cast<float4 *>(qv + i) = *reinterpret_cast<const float4 *>(a.q + (size_t)qi * mp + i);
     const int grp = lane >> 3, g = lane & 7;
     const u32 S = d.n_entries;
-    int n = 0, cur = 0;
+    int n = 0;
     for (u32 t0 = 0; t0 < S; t0 += SEED_TILE) {
         const int nt = (int)min((u32)SEED_TILE, S - t0);
         __syncthreads();
@@ -256,33 +294,10 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
                 if (lane == r0 + t && r0 + t < nt) key = v;
             }
         }
-        u64 *bk = cur ? bk1 : bk0, *bn = cur ? bk0 : bk1;
-        if (key != KEY_INF && n == (int)L && key >= bk[n - 1]) key = KEY_INF;
-        int rank = 0;
-        for (int j = 0; j < 32; j++) rank += (__shfl_sync(FULL, key, j) < key);
-        const int c = __popc(__ballot_sync(FULL, key != KEY_INF));
-        if (c == 0) continue;
-        if (key != KEY_INF) nk[rank] = key;
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-            const u64 bkey = bk[i];
-            int lo = 0, hi = c;
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (nk[mid] < bkey) lo = mid + 1; else hi = mid; }
-            if (i + lo < (int)L) bn[i + lo] = bkey;
-        }
-        if (lane < c) {
-            const u64 k2 = nk[lane];
-            int lo = 0, hi = n;
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (bk[mid] < k2) lo = mid + 1; else hi = mid; }
-            if (lane + lo < (int)L) bn[lane + lo] = k2;
-        }
-        __syncwarp();
-        cur ^= 1;
-        n = min((int)L, n + c);
+        n = seed_merge(bk0, nk, key, n, (int)L);
     }
     if (active) {
-        const u64 *bk = cur ? bk1 : bk0;
-        for (u32 i = lane; i < L; i += 32) a.seed[(size_t)qi * L + i] = (int)i < n ? bk[i] : KEY_INF;
+        for (u32 i = lane; i < L; i += 32) a.seed[(size_t)qi * L + i] = (int)i < n ? bk0[i] : KEY_INF;
     }
 }
 

@@ -783,7 +783,7 @@ struct RepairKArgs {
     Dev d;
     const u32 *dt;
     const u64 *n_dt;
-    u32 max_n, ns;
+    u32 max_n, ns, gram;
     u32 *pair_key, *pair_val;
     uint2 *pair_K;
     u32 *pair_Kn;
@@ -796,10 +796,10 @@ __host__ __device__ inline u32 repk_np(u32 R) {
     return np;
 }
 
-__host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp) {
+__host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp, u32 gram) {
     const u32 np = repk_np(R);
     return stage_bytes(ns, mp) + 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)np * 8) +
-           al16(np);
+           al16(np) + (gram ? al16(GRAM_BYTES) : 0);
 }
 
 __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
@@ -807,8 +807,10 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * repk_warp_bytes(R, a.ns, d.mp);
-    Stage st = stage_init(p, a.ns, d.mp);
+    char *p = smem + warp * repk_warp_bytes(R, a.ns, d.mp, a.gram);
+    char *gbuf = a.gram ? p : nullptr;
+    if (a.gram) p += al16(GRAM_BYTES);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf);
     p += stage_bytes(a.ns, d.mp);
     u32 *bid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     u32 *bdel = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
@@ -836,7 +838,8 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
             bdel[j] = ref_del(ld_ref(d, bid[j]));
         }
         __syncwarp();
-        // distance table among B (symmetric), rows staged in shared memory
+        // distance table among B (symmetric).  These distances become the
+        // stored rho of replacement edges, so they stay canonical.
         const int nsb = st.rows ? min(nb, st.ns_cap) : 0;
         stage_rows_by(d, st, nsb, [&](int i) { return bid[i]; });
         auto brow = [&](int i) -> const float * {
@@ -909,8 +912,8 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
 cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
                             u32 *pair_val, uint2 *pair_K, u32 *pair_Kn, int num_sms, cudaStream_t st) {
     if (max_n == 0) return cudaSuccess;
-    RepairKArgs a{d, dt, n_dt, max_n, stage_cap(d.mp, d.R, d.stage_bytes), pair_key, pair_val, pair_K, pair_Kn};
-    const size_t wb = repk_warp_bytes(d.R, a.ns, d.mp);
+    RepairKArgs a{d, dt, n_dt, max_n, stage_cap(d.mp, d.R, d.stage_bytes), 0u, pair_key, pair_val, pair_K, pair_Kn};
+    const size_t wb = repk_warp_bytes(d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
     cudaError_t e = cudaFuncSetAttribute(repair_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
