@@ -197,6 +197,33 @@ etale_status etale_set_profiling(etale_index *idx, int enable);
  * (either pointer may be NULL); reset = 1 clears the accumulators.         */
 etale_status etale_get_profile(etale_index *idx, double *ms, uint64_t *count, uint32_t n, int reset);
 
+/* Query search that allocates nothing (the paper has no counterpart: this is
+ * a deployment variant of etale_search).
+ *
+ * For callers that must not allocate device memory while they run: code
+ * inside CUDA stream capture, where cudaMalloc would break the capture, and
+ * serving threads with a fixed memory budget or an allocator that may not be
+ * entered from their context.  etale_search may grow staging buffers on
+ * demand; this variant never calls cudaMalloc, cudaFree or any allocating
+ * routine.  Its scratch (padded query rows and the seeded beams) lives in a
+ * file-scope device array of ETALE_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.
+ *
+ * queries, out_ids and out_dists must be DEVICE pointers (host buffers would
+ * need staging); results equal etale_search's for the same arguments.
+ * nq * (4 * round_up(dim, 4) + 8 * max(beam, k)) must not exceed
+ * ETALE_STATIC_SCRATCH_BYTES, else ETALE_EINVAL with a message.
+ *
+ * The first call on a device looks up the array's device address (set-up
+ * once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the one array and leave their
+ * contents in it: calls whose work overlaps on the GPU (other streams,
+ * other indexes, other threads) race on it and must be serialised by the
+ * caller.  Like every call, it synchronises `stream` before returning.     */
+#define ETALE_STATIC_SCRATCH_BYTES (8u << 20)
+etale_status etale_search_static(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
+                                 uint32_t beam, uint32_t *out_ids, float *out_dists, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,7 +47,7 @@ class Stats(C.Structure):
 EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_insert", "etale_delete",
            "etale_reclaim", "etale_search", "etale_ground_truth", "etale_export_graph",
            "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
-           "etale_kernel_launches", "etale_set_profiling", "etale_get_profile"]
+           "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
             "etale_kernel_launches": ([P], U64),
             "etale_set_profiling": ([P, C.c_int], C.c_int),
             "etale_get_profile": ([P, P, P, U32, C.c_int], C.c_int),
+            "etale_search_static": ([P, P, U64, U32, U32, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -189,6 +190,13 @@ class Index:
         ids, dist = out if out is not None else self._outputs(queries, k)
         self._check(self.lib.etale_search(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
                                           _ptr(dist), _stream(stream)))
+        return ids, dist
+
+    def search_static(self, queries, k: int, beam: int, stream=None, out=None):
+        """etale_search_static: device tensors only; allocates nothing on the device."""
+        ids, dist = out if out is not None else self._outputs(queries, k)
+        self._check(self.lib.etale_search_static(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
+                                                 _ptr(dist), _stream(stream)))
         return ids, dist
 
     def ground_truth(self, queries, k: int, stream=None):

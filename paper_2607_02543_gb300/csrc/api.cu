@@ -3,6 +3,7 @@
 // separate launch on the caller's stream and every phase that publishes is
 // followed by the recycle launch (Sec. 3.3, Lemma 1, Definition 2).
 #include <atomic>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -777,6 +778,69 @@ const char *etale_last_error(const etale_index *idx) {
 }
 
 uint64_t etale_kernel_launches(const etale_index *) { return g_kernel_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// etale_search_static: the query search with its scratch in a fixed
+// file-scope device array instead of on-demand allocations.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[ETALE_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int MAX_DEVICES = 64;
+void *g_static_scratch_ptr[MAX_DEVICES] = {};
+std::mutex g_static_mu;
+
+// Device address of g_static_scratch on the current device (looked up once
+// per device; the host-side symbol is only a stand-in and must not be passed
+// to a kernel).
+cudaError_t static_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_scratch_ptr[dev] = p;
+    }
+    *out = g_static_scratch_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+etale_status etale_search_static(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
+                                 uint32_t *out_ids, float *out_dists, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (nq == 0) return ETALE_OK;
+    if (!queries || !out_ids || !out_dists || k == 0) return idx->fail(ETALE_EINVAL, "null buffer or k == 0");
+    if (!is_device_ptr(queries) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))
+        return idx->fail(ETALE_EINVAL, "etale_search_static takes device pointers only");
+    const u32 L = beam > k ? beam : k;
+    if (L > 256) return idx->fail(ETALE_EINVAL, "beam must be <= 256");
+    const size_t qbytes = ((size_t)nq * idx->mp * 4 + 255) / 256 * 256;
+    const size_t need = qbytes + (size_t)nq * L * 8;
+    if (need > ETALE_STATIC_SCRATCH_BYTES)
+        return idx->fail(ETALE_EINVAL, "etale_search_static: %llu queries need %zu bytes of scratch, above the %u-byte limit",
+                         (unsigned long long)nq, need, (unsigned)ETALE_STATIC_SCRATCH_BYTES);
+    void *scr = nullptr;
+    CK(static_scratch(&scr), "static scratch set-up");
+    float *qpad = reinterpret_cast<float *>(scr);
+    u64 *seed = reinterpret_cast<u64 *>(reinterpret_cast<unsigned char *>(scr) + qbytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    Dev d = idx->dev();
+    // every scratch byte read below is written first in this call (padded
+    // rows by ingest, all L seed slots per query by the seed kernel)
+    CK(launch_ingest(qpad, idx->mp, queries, idx->dim, nq, st), "query ingest");
+    CK(launch_seed(d, qpad, (u32)nq, L, seed, st), "query seed");
+    const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, seed, idx->tune,
+                     idx->num_sms, st),
+       "search");
+    g_kernel_launches += 3;
+    return check_device_errors(idx, st);
+}
 
 etale_status etale_set_profiling(etale_index *idx, int enable) {
     if (!idx) return ETALE_EINVAL;

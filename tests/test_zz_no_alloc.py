@@ -1,0 +1,51 @@
+"""etale_search_static: the query search that allocates no device memory.
+
+Some callers cannot allocate while they run: code recording a CUDA graph
+(a cudaMalloc would break the capture) or a serving thread held to a fixed
+device-memory budget.  The variant keeps its scratch in a fixed array inside
+the library instead of growing buffers on demand.  It must return exactly
+what etale_search returns for the same arguments, call after call, and leave
+the device's free memory untouched.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_02543_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_static_search_matches_search_twice():
+    import torch
+    from paper_2607_02543_gb300 import EtaleError, Index, build
+    build.build()
+    w = W.scaled(W.SMALL, 3000, n_queries=600)
+    plan = W.make_plan(w)
+    dev = torch.device("cuda", 0)
+    g = Index(w.dim, w.metric, w.degree, w.capacity, build_beam=32)
+    g.insert(torch.from_numpy(plan.base).to(dev))
+    assert g.delete(np.arange(0, w.n_base, 11, dtype=np.uint32)) > 0
+    q_all = torch.from_numpy(plan.queries).to(dev)
+    batches = [(q_all, 10, 64), (q_all[100:400].contiguous(), 7, 48)]
+    expected = [g.search(q, k, beam) for q, k, beam in batches]
+    # The first call on a device looks up the fixed array (once per device).
+    # That call, and torch's first comparison kernels, may make the driver
+    # load code and module memory lazily; both happen before measuring.
+    ids, dist = g.search_static(*batches[0])
+    assert torch.equal(ids, expected[0][0]) and torch.equal(dist, expected[0][1])
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info(dev)[0]
+    # two calls in a row, different sizes: the second sees the first's leftovers
+    for (q, k, beam), (ref_ids, ref_d) in zip(batches[::-1], expected[::-1]):
+        ids, dist = g.search_static(q, k, beam)
+        torch.cuda.synchronize()
+        assert torch.equal(ids, ref_ids)
+        assert torch.equal(dist, ref_d)
+    assert torch.cuda.mem_get_info(dev)[0] == free_before
+    # a batch beyond the fixed scratch is refused with a clear error
+    big = torch.zeros((20000, w.dim), dtype=torch.float32, device=dev)
+    with pytest.raises(EtaleError, match="scratch"):
+        g.search_static(big, 10, 64)
+    # host buffers are refused: they would need staging
+    with pytest.raises(EtaleError, match="device pointers"):
+        g.search_static(plan.queries[:4], 10, 64)
