@@ -109,7 +109,7 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # the CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(w: W.Workload, n_sample: int, ops: int, n_entry: int, rounds: int = 1):
+def oracle_sample(w: W.Workload, n_sample: int, ops: int, n_entry: int, rounds: int = 1, max_cand: int = 0):
     """Build the oracle on n_sample points of the workload's mixture (untimed),
     then time `rounds` batches of `ops` deletes + `ops` inserts + reclaim.
     Per-operation costs are scaled to the workload's round (n_delete deletes,
@@ -119,7 +119,7 @@ def oracle_sample(w: W.Workload, n_sample: int, ops: int, n_entry: int, rounds: 
     ws = W.dataclasses.replace(ws, n_delete=ops, n_insert=ops)
     p = W.make_plan(ws)
     o = oracle.Oracle(w.dim, w.metric, w.degree, ws.capacity, build_beam=w.build_beam, refine=2,
-                      n_entry=n_entry)
+                      n_entry=n_entry, max_cand=max_cand)
     o.insert(p.base)
     o.reclaim()
     alive = np.zeros(ws.capacity, bool)
@@ -148,7 +148,7 @@ def run_reference(args, w):
         return
     n_entry = args.n_entry
     per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry,
-                              rounds=args.warmup + args.steps)
+                              rounds=args.warmup + args.steps, max_cand=args.max_cand)
     timed = per[args.warmup:]
     v = float(np.mean(timed))
     sample = (f"oracle built on {info['n_sample']} points of the same mixture (untimed); each step times "
@@ -336,7 +336,8 @@ def main():
     st = idx.stats()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry, rounds=1)
+        per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry, rounds=1,
+                                  max_cand=args.max_cand)
         cpu = {"value": float(np.mean(per)), "unit": "ms", "cores": 1, "kind": "oracle",
                "sample": f"oracle on {info['n_sample']} points of the same mixture, one batch of "
                          f"{info['ops']} deletes + {info['ops']} inserts + reclaim timed on one host core, "

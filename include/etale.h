@@ -74,8 +74,16 @@ typedef struct {
                              mode), 1 canonical fp32, 2 tensor-core Gram
                              tile (bf16 inputs, fp32 accumulation; exact for
                              integer-valued data of magnitude <= 256)       */
-    uint32_t reserved[4];
+    uint32_t copies;      /* reduced-precision search copies kept beside the
+                             fp32 rows: bit 0 BF16, bit 1 FP8-E4M3 with a
+                             per-vector scale max|x| / 448; default none    */
+    uint32_t rerank;      /* reduced-precision query search re-scores its
+                             rerank * k best live candidates in exact fp32;
+                             default 4, at most 64 / k candidates used      */
+    uint32_t reserved[2];
 } etale_config;
+
+typedef enum { ETALE_PREC_FP32 = 0, ETALE_PREC_BF16 = 1, ETALE_PREC_FP8 = 2 } etale_precision;
 
 typedef struct {
     uint64_t live;            /* delta = 0 with a slab                        */
@@ -133,6 +141,20 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n,
  * entries (compaction), then free every tombstone's slab.  Afterwards the
  * resident slab count equals the live count (Proposition 3).               */
 etale_status etale_reclaim(etale_index *idx, void *stream);
+
+/* Distance precision of query searches (etale_search and
+ * etale_search_static): FP32 (default) or a copy kept by `copies`.  With
+ * BF16 or FP8 the beam is scored on the reduced rows (fp32 arithmetic on
+ * dequantised values) and the rerank * k best live candidates are re-scored
+ * with the canonical fp32 distance before the k results are chosen, so
+ * returned distances are exact fp32.  EINVAL if the copy is not kept.       */
+etale_status etale_set_search_precision(etale_index *idx, etale_precision p);
+
+/* Copy the reduced-precision codes of ids [first, first + n) to HOST
+ * buffers (either may be NULL): bf16 as uint16 bits, n x dim; fp8 as bytes,
+ * n x dim, with scales[n].                                                 */
+etale_status etale_export_copies(etale_index *idx, uint64_t first, uint64_t n, uint16_t *bf16,
+                                 uint8_t *fp8, float *scales);
 
 /* Batched k-NN query (BeamSearch with beam max(beam, k)).  queries: nq x dim
  * fp32.  out_ids / out_dists: nq x k, nearest first; a search that finds

@@ -32,7 +32,7 @@ class Config(C.Structure):
                 ("max_cand", C.c_uint32), ("refine", C.c_uint32), ("max_batch", C.c_uint64),
                 ("pool_slabs", C.c_uint64), ("n_entry", C.c_uint32), ("mode", C.c_uint32),
                 ("cas_budget", C.c_uint32), ("stage_kb", C.c_uint32), ("gram", C.c_uint32),
-                ("reserved", C.c_uint32 * 4)]
+                ("copies", C.c_uint32), ("rerank", C.c_uint32), ("reserved", C.c_uint32 * 2)]
 
 
 class Stats(C.Structure):
@@ -47,7 +47,8 @@ class Stats(C.Structure):
 EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_insert", "etale_delete",
            "etale_reclaim", "etale_search", "etale_ground_truth", "etale_export_graph",
            "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
-           "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static"]
+           "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static",
+           "etale_set_search_precision", "etale_export_copies"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
@@ -83,6 +84,8 @@ def load(path: str = LIB_PATH):
             "etale_set_profiling": ([P, C.c_int], C.c_int),
             "etale_get_profile": ([P, P, P, U32, C.c_int], C.c_int),
             "etale_search_static": ([P, P, U64, U32, U32, P, P, P], C.c_int),
+            "etale_set_search_precision": ([P, C.c_int], C.c_int),
+            "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -116,7 +119,8 @@ class Index:
     def __init__(self, dim: int, metric: str, degree: int, capacity: int, *, build_beam: int = 0,
                  alpha: float = 0.0, max_hops: int = 0, max_cand: int = 0, refine: str = "default",
                  max_batch: int = 0, pool_slabs: int = 0, n_entry: int = 0, mode: str = "deterministic",
-                 cas_budget: int = 0, stage_kb: int = 0, gram: str = "default"):
+                 cas_budget: int = 0, stage_kb: int = 0, gram: str = "default", copies: tuple = (),
+                 rerank: int = 0):
         self.lib = load()
         cfg = Config()
         self.lib.etale_config_default(C.byref(cfg))
@@ -134,6 +138,9 @@ class Index:
             cfg.cas_budget = cas_budget
         cfg.stage_kb = stage_kb
         cfg.gram = {"default": 0, "canonical": 1, "tensor": 2}[gram]
+        cfg.copies = (1 if "bf16" in copies else 0) | (2 if "fp8" in copies else 0)
+        if rerank:
+            cfg.rerank = rerank
         h = C.c_void_p()
         st = self.lib.etale_create(dim, 0 if metric == "l2" else 1, degree, capacity, C.byref(cfg), C.byref(h))
         if st:
@@ -191,6 +198,22 @@ class Index:
         self._check(self.lib.etale_search(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
                                           _ptr(dist), _stream(stream)))
         return ids, dist
+
+    def set_search_precision(self, prec: str):
+        """"fp32", "bf16" or "fp8" for later query searches."""
+        self._check(self.lib.etale_set_search_precision(self.h, {"fp32": 0, "bf16": 1, "fp8": 2}[prec]))
+
+    def export_copies(self, first: int, n: int):
+        """(bf16 bits uint16[n, dim] or None, fp8 codes uint8[n, dim] or None, scales float32[n] or None)."""
+        cfg = self.config()
+        b = np.empty((n, self.dim), np.uint16) if cfg["copies"] & 1 else None
+        f = np.empty((n, self.dim), np.uint8) if cfg["copies"] & 2 else None
+        sc = np.empty(n, np.float32) if cfg["copies"] & 2 else None
+        nul = C.c_void_p(None)
+        self._check(self.lib.etale_export_copies(self.h, first, n, _ptr(b) if b is not None else nul,
+                                                 _ptr(f) if f is not None else nul,
+                                                 _ptr(sc) if sc is not None else nul))
+        return b, f, sc
 
     def search_static(self, queries, k: int, beam: int, stream=None, out=None):
         """etale_search_static: device tensors only; allocates nothing on the device."""

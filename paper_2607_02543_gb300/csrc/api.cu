@@ -76,6 +76,11 @@ struct etale_index {
     uint2 *slab = nullptr;
     u32 *free_stack = nullptr, *retired = nullptr, *entries = nullptr;
     u64 *ctr = nullptr;
+    unsigned short *xb = nullptr;   // bf16 copy
+    unsigned char *x8 = nullptr;    // fp8 copy
+    float *x8s = nullptr;
+    u32 mb = 0, m8 = 0;
+    u32 search_prec = 0;
     u64 *host_ctr = nullptr;   // pinned mirror
     // scratch
     DevBuf stage, qpad, out_ids, out_dist, exp_keys, exp_count, F_id, F_rho, F_n;
@@ -106,6 +111,7 @@ struct etale_index {
         d.entries = entries; d.dim = dim; d.mp = mp; d.R = R; d.metric = metric; d.alpha2 = alpha2;
         d.n_entries = n_entries; d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
         d.gram = cfg.gram == 2 ? 1u : 0u;
+        d.xb = xb; d.x8 = x8; d.x8s = x8s; d.mb = mb; d.m8 = m8;
         return d;
     }
 
@@ -370,6 +376,7 @@ etale_status etale_config_default(etale_config *cfg) {
     cfg->n_entry = 1024;
     cfg->mode = ETALE_MODE_DETERMINISTIC;
     cfg->cas_budget = 16;
+    cfg->rerank = 4;
     return ETALE_OK;
 }
 
@@ -397,6 +404,12 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         if (cfg_in->cas_budget) cfg.cas_budget = cfg_in->cas_budget;
         cfg.stage_kb = cfg_in->stage_kb;
         cfg.gram = cfg_in->gram;
+        cfg.copies = cfg_in->copies;
+        if (cfg_in->rerank) cfg.rerank = cfg_in->rerank;
+    }
+    if (cfg.copies > 3) {
+        g_create_error = "copies is a bitmask of 1 (bf16) and 2 (fp8)";
+        return ETALE_EINVAL;
     }
     if (cfg.gram > 2) {
         g_create_error = "gram must be 0..2";
@@ -437,13 +450,20 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
               cudaMalloc(&idx->ctr, C_NCTR * sizeof(u64)) == cudaSuccess &&
               cudaMalloc(&idx->entries, (size_t)cfg.n_entry * 4) == cudaSuccess &&
               cudaMallocHost(&idx->host_ctr, C_NCTR * sizeof(u64)) == cudaSuccess;
+    idx->mb = (idx->mp + 7) / 8 * 8;
+    idx->m8 = (idx->mp + 15) / 16 * 16;
+    if (ok && (cfg.copies & 1)) ok = cudaMalloc(&idx->xb, (size_t)capacity * idx->mb * 2) == cudaSuccess;
+    if (ok && (cfg.copies & 2))
+        ok = cudaMalloc(&idx->x8, (size_t)capacity * idx->m8) == cudaSuccess &&
+             cudaMalloc(&idx->x8s, (size_t)capacity * 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         g_create_error = "device allocation failed";
         etale_destroy(idx);
         return ETALE_ENOMEM;
     }
-    idx->device_bytes = xb + rb + sb + 2 * pb;
+    idx->device_bytes = xb + rb + sb + 2 * pb + (idx->xb ? (size_t)capacity * idx->mb * 2 : 0) +
+                        (idx->x8 ? (size_t)capacity * (idx->m8 + 4) : 0);
     // refs <- <0, 0, NIL>; free stack <- all slabs; counters
     std::vector<u64> ctr(C_NCTR, 0);
     ctr[C_FREE] = idx->pool;
@@ -478,6 +498,7 @@ etale_status etale_destroy(etale_index *idx) {
     if (!idx) return ETALE_OK;
     cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
     cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
+    cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s);
     if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
     for (cudaEvent_t e : idx->pev) cudaEventDestroy(e);
     DevBuf *bufs[] = {&idx->stage, &idx->qpad, &idx->out_ids, &idx->out_dist, &idx->exp_keys, &idx->exp_count,
@@ -508,7 +529,8 @@ etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n, uint3
     if (s != ETALE_OK) return s;
     const u64 first_all = idx->next_id;
     CK(launch_ingest(idx->x + first_all * idx->mp, idx->mp, (const float *)src, idx->dim, n, st), "ingest");
-    g_kernel_launches++;
+    CK(launch_ingest_copies(idx->dev(), first_all, n, st), "ingest copies");
+    g_kernel_launches += 2;
     u64 done = 0;
     const u64 maxb = idx->cfg.max_batch;
     s = size_batch_scratch(idx, std::min<u64>(n, maxb));
@@ -659,6 +681,7 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
     if (exact && k > 32) return idx->fail(ETALE_EINVAL, "ground truth supports k <= 32");
     const u32 L = beam > k ? beam : k;
     if (!exact && L > 256) return idx->fail(ETALE_EINVAL, "beam must be <= 256");
+    if (!exact && idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
     if (nq > 0xFFFFFFFFull) return idx->fail(ETALE_EINVAL, "too many queries");
     cudaStream_t st = (cudaStream_t)stream;
     const void *src = nullptr;
@@ -684,11 +707,12 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
         if (!grow(idx->seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
         {
             PhaseScope ps(idx, ETALE_PH_SEED, st);
-            CK(launch_seed(d, as<float>(idx->qpad), (u32)nq, L, as<u64>(idx->seed), st), "query seed");
+            CK(launch_seed(d, as<float>(idx->qpad), (u32)nq, L, as<u64>(idx->seed), st, idx->search_prec),
+               "query seed");
         }
         PhaseScope ps(idx, ETALE_PH_SEARCH_QUERY, st);
         CK(launch_search(d, as<float>(idx->qpad), (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->seed),
-                         idx->tune, idx->num_sms, st),
+                         idx->tune, idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
            "search");
         g_kernel_launches++;
     }
@@ -833,13 +857,45 @@ etale_status etale_search_static(etale_index *idx, const float *queries, uint64_
     // every scratch byte read below is written first in this call (padded
     // rows by ingest, all L seed slots per query by the seed kernel)
     CK(launch_ingest(qpad, idx->mp, queries, idx->dim, nq, st), "query ingest");
-    CK(launch_seed(d, qpad, (u32)nq, L, seed, st), "query seed");
+    CK(launch_seed(d, qpad, (u32)nq, L, seed, st, idx->search_prec), "query seed");
     const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
     CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, seed, idx->tune,
-                     idx->num_sms, st),
+                     idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
        "search");
     g_kernel_launches += 3;
     return check_device_errors(idx, st);
+}
+
+etale_status etale_set_search_precision(etale_index *idx, etale_precision p) {
+    if (!idx) return ETALE_EINVAL;
+    if (p == ETALE_PREC_BF16 && !idx->xb) return idx->fail(ETALE_EINVAL, "no bf16 copy kept (config.copies bit 0)");
+    if (p == ETALE_PREC_FP8 && !idx->x8) return idx->fail(ETALE_EINVAL, "no fp8 copy kept (config.copies bit 1)");
+    if ((u32)p > 2) return idx->fail(ETALE_EINVAL, "unknown precision");
+    idx->search_prec = (u32)p;
+    return ETALE_OK;
+}
+
+etale_status etale_export_copies(etale_index *idx, uint64_t first, uint64_t n, uint16_t *bf16, uint8_t *fp8,
+                                 float *scales) {
+    if (!idx) return ETALE_EINVAL;
+    if (first + n > idx->next_id) return idx->fail(ETALE_EINVAL, "range beyond next_id");
+    if (n == 0) return ETALE_OK;
+    if (bf16) {
+        if (!idx->xb) return idx->fail(ETALE_EINVAL, "no bf16 copy kept");
+        cudaError_t e = cudaMemcpy2D(bf16, (size_t)idx->dim * 2, idx->xb + first * idx->mb, (size_t)idx->mb * 2,
+                                     (size_t)idx->dim * 2, n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return idx->cuda_fail(e, "export bf16");
+    }
+    if (fp8 || scales) {
+        if (!idx->x8) return idx->fail(ETALE_EINVAL, "no fp8 copy kept");
+        cudaError_t e = cudaSuccess;
+        if (fp8)
+            e = cudaMemcpy2D(fp8, idx->dim, idx->x8 + first * idx->m8, idx->m8, idx->dim, n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && scales) e = cudaMemcpy(scales, idx->x8s + first, n * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return idx->cuda_fail(e, "export fp8");
+    }
+    return ETALE_OK;
 }
 
 etale_status etale_set_profiling(etale_index *idx, int enable) {

@@ -103,6 +103,11 @@ struct Dev {
     u64 capacity, pool;
     u32 stage_bytes;   // per-warp RobustPrune row stage (0: rows read from L2)
     u32 gram;          // 1: domination tests of small prunes use the tensor-core Gram tile
+    // reduced-precision copies (query search only)
+    unsigned short *xb;  // C x mb bf16 bits (nullptr if not kept)
+    unsigned char *x8;   // C x m8 e4m3 codes (nullptr if not kept)
+    float *x8s;          // C per-vector scales
+    u32 mb, m8;          // row strides in elements (16-byte rows)
 };
 
 // ---- canonical distance ------------------------------------------------------

@@ -14,10 +14,13 @@ struct SearchTuning {
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
 // seed_kernel: top-L of the entry set per query into `seed` (nq x L); it
 // must precede the search launch that reads `seed`.
-cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st);
+cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec = 0);
+// prec: 0 fp32, 1 bf16 copy, 2 fp8 copy (query mode only; the best
+// min(rerank * k, 64) live candidates are re-scored in canonical fp32).
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
-                          const SearchTuning &tune, int num_sms, cudaStream_t st);
+                          const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec = 0,
+                          u32 rerank = 4);
 
 // Offer lists: a payload index p names (src[p], rho[p]); key[p] is the target
 // id or `invalid` (= capacity) for an empty slot.
@@ -77,6 +80,7 @@ cudaError_t make_segments(const u32 *key, u32 n, u32 invalid, u32 *flags, u32 *s
 
 cudaError_t launch_recycle(const Dev &d, cudaStream_t st);
 cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st);
+cudaError_t launch_ingest_copies(const Dev &d, u64 first, u64 n, cudaStream_t st);
 cudaError_t launch_live_flags(const Dev &d, u64 next_id, u32 *flags, cudaStream_t st);
 cudaError_t launch_entries_select(const Dev &d, u64 next_id, const u32 *flags, const u32 *rank, u64 live,
                                   u32 S, cudaStream_t st);

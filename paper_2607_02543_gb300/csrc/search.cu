@@ -14,6 +14,9 @@
 // once the beam is full its worst key only decreases, so an id that left the
 // beam or was refused is refused again (its key is the same), and an id still
 // in the beam is recognised in the merge by its equal key and dropped.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -30,7 +33,77 @@ struct SearchArgs {
     u64 *exp_keys;       // insert: nq x max_hops expanded non-tombstone keys
     u32 *exp_count;
     u32 stage_rows, seen_slots, seen_bits;
+    u32 rowb;            // bytes per gathered row (fp32, bf16 or fp8 copy)
+    u32 rerank;          // reduced precision: re-scored candidates (<= 64)
 };
+
+// Row gathered for a neighbour: the fp32 row or its reduced-precision copy.
+template <int P>
+__device__ __forceinline__ const void *row_src(const Dev &d, u32 id) {
+    if (P == 1) return d.xb + (size_t)id * d.mb;
+    if (P == 2) return d.x8 + (size_t)id * d.m8;
+    return d.x + (size_t)id * d.mp;
+}
+
+// Four dequantised elements [i, i + 4) of a staged row.
+template <int P>
+__device__ __forceinline__ float4 load4(const void *row, int i, float scale) {
+    if (P == 1) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(reinterpret_cast<const unsigned short *>(row) + i);
+        return make_float4(__uint_as_float(w.x << 16), __uint_as_float(w.x & 0xFFFF0000u),
+                           __uint_as_float(w.y << 16), __uint_as_float(w.y & 0xFFFF0000u));
+    } else if (P == 2) {
+        const unsigned int w = *reinterpret_cast<const unsigned int *>(reinterpret_cast<const unsigned char *>(row) + i);
+        const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
+        const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+        return make_float4(__fmul_rn(a.x, scale), __fmul_rn(a.y, scale), __fmul_rn(b.x, scale), __fmul_rn(b.y, scale));
+    } else {
+        return *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(row) + i);
+    }
+}
+
+// The canonical reduction tree (see canon_dist) over a staged row of
+// precision P, 8 lanes per distance: fp32 arithmetic on dequantised values.
+template <int P>
+__device__ __forceinline__ float qdist(const float *__restrict__ q, const void *row, float scale, int mp, int metric,
+                                       int g) {
+    if (P == 0) return canon_dist<8>(q, reinterpret_cast<const float *>(row), mp, metric, g);
+    float p[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int j = g + 8 * t;
+        float acc = 0.0f;
+        for (int base = 0; base < mp; base += 128) {
+            const int i = base + 4 * j;
+            if (i < mp) {
+                const float4 u = *reinterpret_cast<const float4 *>(q + i);
+                const float4 v = load4<P>(row, i, scale);
+                if (metric == 0) {
+                    float d0 = __fsub_rn(u.x, v.x), d1 = __fsub_rn(u.y, v.y);
+                    float d2 = __fsub_rn(u.z, v.z), d3 = __fsub_rn(u.w, v.w);
+                    acc = __fmaf_rn(d0, d0, acc);
+                    acc = __fmaf_rn(d1, d1, acc);
+                    acc = __fmaf_rn(d2, d2, acc);
+                    acc = __fmaf_rn(d3, d3, acc);
+                } else {
+                    acc = __fmaf_rn(u.x, v.x, acc);
+                    acc = __fmaf_rn(u.y, v.y, acc);
+                    acc = __fmaf_rn(u.z, v.z, acc);
+                    acc = __fmaf_rn(u.w, v.w, acc);
+                }
+            }
+        }
+        p[t] = acc;
+    }
+    p[0] = __fadd_rn(p[0], p[2]);
+    p[1] = __fadd_rn(p[1], p[3]);
+    float s = __fadd_rn(p[0], p[1]);
+#pragma unroll
+    for (int h = 4; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
+    return metric == 0 ? s : __fsub_rn(1.0f, s);
+}
 
 struct WarpSmem {
     float *qv;       // mp
@@ -49,10 +122,10 @@ struct WarpSmem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
+__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 rowb) {
     size_t b = 0;
     b += align_up((size_t)mp * 4, 128);
-    b += align_up((size_t)stage_rows * mp * 4, 128);
+    b += align_up((size_t)stage_rows * rowb, 128);
     b += 2 * align_up((size_t)L * 8, 16);
     b += align_up((size_t)L, 16);
     b += 32 * 8 * 2 + 32 * 4 + 32 * 8 * 2;
@@ -61,10 +134,10 @@ __host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_row
     return align_up(b, 128);
 }
 
-__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
+__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 rowb) {
     WarpSmem s;
     s.qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 128);
-    s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * mp * 4, 128);
+    s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * rowb, 128);
     s.bkey = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     s.bref = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     s.bflag = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
@@ -147,6 +220,7 @@ __device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L) {
 
 // Evaluate the candidate ids held one per lane (NIL = none) and merge them
 // into the beam.  Returns the new beam size.  `phase` tracks the mbarrier.
+template <int P>
 __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u32 &phase, u64 &ndist,
                           bool &timeout) {
     const Dev &d = a.d;
@@ -157,7 +231,9 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
     if (cnt == 0) return n;
     if (my_id != NIL) s.cid[__popc(mask & lanemask_lt())] = my_id;
     __syncwarp();
-    const u32 rowb = mp * 4;
+    const u32 rowb = a.rowb;
+    unsigned char *stage = reinterpret_cast<unsigned char *>(s.stage);
+    float *scl = reinterpret_cast<float *>(s.nref);   // fp8 scales of the batch (nref is free here)
     for (int b0 = 0; b0 < cnt; b0 += (int)a.stage_rows) {
         const int nb = min((int)a.stage_rows, cnt - b0);
         if (lane == 0) {
@@ -169,8 +245,9 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
         u64 rf = 0;
         if (lane < nb) {
             const u32 id = s.cid[b0 + lane];
-            bulk_g2s(s.stage + (size_t)lane * mp, d.x + (size_t)id * mp, rowb, s.bar);
+            bulk_g2s(stage + (size_t)lane * rowb, row_src<P>(d, id), rowb, s.bar);
             rf = ld_ref(d, id);
+            if (P == 2) scl[lane] = d.x8s[id];
         }
         if (!mbar_wait(s.bar, phase, WAIT_LIMIT)) {
             timeout = true;
@@ -180,10 +257,11 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
         if (lane < nb) s.cref[b0 + lane] = rf;
         // 8 lanes per distance, 4 distances per round
         const int grp = lane >> 3, g = lane & 7;
+        __syncwarp();
         for (int r0 = 0; r0 < nb; r0 += 4) {
             const int c = r0 + grp;
             const int cc = c < nb ? c : nb - 1;   // idle groups recompute a valid row
-            float dist = canon_dist<8>(s.qv, s.stage + (size_t)cc * mp, (int)mp, (int)d.metric, g);
+            float dist = qdist<P>(s.qv, stage + (size_t)cc * rowb, P == 2 ? scl[cc] : 1.0f, (int)mp, (int)d.metric, g);
             if (c < nb && g == 0) s.ckey[b0 + c] = mkkey(dist, s.cid[b0 + c]);
         }
         __syncwarp();
@@ -208,6 +286,7 @@ struct SeedArgs {
     const float *q;
     u32 nq, L;
     u64 *seed;
+    u32 rowb;   // bytes per entry row in the tile (fp32 row or its copy)
 };
 
 __host__ __device__ inline size_t seed_warp_bytes(u32 mp, u32 L) {
@@ -252,13 +331,15 @@ __device__ int seed_merge(u64 *bk, u64 *nk, u64 key, int n, int L) {
     return min(L, n + c);
 }
 
+template <int P>
 __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     extern __shared__ __align__(16) char ssm[];
+    __shared__ float tscale[SEED_TILE];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 mp = d.mp, L = a.L;
-    float *tile = reinterpret_cast<float *>(ssm);
-    char *p = ssm + align_up((size_t)SEED_TILE * mp * 4, 16) + warp * seed_warp_bytes(mp, L);
+    unsigned char *tile = reinterpret_cast<unsigned char *>(ssm);
+    char *p = ssm + align_up((size_t)SEED_TILE * a.rowb, 16) + warp * seed_warp_bytes(mp, L);
     float *qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 16);
     u64 *bk0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     u64 *bk1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
@@ -274,19 +355,21 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     for (u32 t0 = 0; t0 < S; t0 += SEED_TILE) {
         const int nt = (int)min((u32)SEED_TILE, S - t0);
         __syncthreads();
-        const u32 f4 = mp / 4;
+        const u32 f4 = a.rowb / 16;
         for (u32 i = threadIdx.x; i < (u32)nt * f4; i += 256) {
             const u32 r = i / f4, c = i % f4;
-            reinterpret_cast<float4 *>(tile + (size_t)r * mp)[c] =
-                reinterpret_cast<const float4 *>(d.x + (size_t)d.entries[t0 + r] * mp)[c];
+            reinterpret_cast<uint4 *>(tile + (size_t)r * a.rowb)[c] =
+                reinterpret_cast<const uint4 *>(row_src<P>(d, d.entries[t0 + r]))[c];
         }
+        if (P == 2 && threadIdx.x < (u32)nt) tscale[threadIdx.x] = d.x8s[d.entries[t0 + threadIdx.x]];
         __syncthreads();
         if (!active) continue;
         u64 key = KEY_INF;
         for (int r0 = 0; r0 < nt; r0 += 4) {
             const int c = r0 + grp;
             const int cc = c < nt ? c : nt - 1;
-            const float dist = canon_dist<8>(qv, tile + (size_t)cc * mp, (int)mp, (int)d.metric, g);
+            const float dist = qdist<P>(qv, tile + (size_t)cc * a.rowb, P == 2 ? tscale[cc] : 1.0f, (int)mp,
+                                        (int)d.metric, g);
             const u64 kk = mkkey(dist, d.entries[t0 + cc]);
 #pragma unroll
             for (int t = 0; t < 4; t++) {
@@ -301,13 +384,14 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     }
 }
 
+template <int P>
 __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 mp = d.mp;
-    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, a.seen_slots);
-    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, a.seen_slots);
+    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
+    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
     if (lane == 0) mbar_init(s.bar, 1);
     __syncwarp();
     u32 phase = 0;
@@ -382,11 +466,54 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
             for (u32 j0 = 0; j0 < deg; j0 += 32) {
                 u32 nb = j0 == 0 ? e0 : e1;
                 if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
-                n = eval_merge(a, s, nb, n, phase, ndist, timeout);
+                n = eval_merge<P>(a, s, nb, n, phase, ndist, timeout);
             }
         }
         nexp_tot += hops;
-        if (a.mode == 0) {
+        if (a.mode == 0 && P != 0) {
+            // exact fp32 rerank of the best min(rerank * k, 64) live candidates
+            u64 *rk = reinterpret_cast<u64 *>(s.stage);
+            const int want = (int)min(a.rerank * a.k, 64u);
+            int c = 0;
+            for (int i0 = 0; i0 < n && c < want; i0 += 32) {
+                const int i = i0 + lane;
+                const bool ok = i < n && !ref_del(s.bref[i]);
+                const u32 m = __ballot_sync(FULL, ok);
+                const int pos = c + __popc(m & lanemask_lt());
+                if (ok && pos < want) rk[pos] = s.bkey[i];
+                c = min(want, c + __popc(m));
+            }
+            __syncwarp();
+            const int grp = lane >> 3, g = lane & 7;
+            for (int r0 = 0; r0 < c; r0 += 4) {
+                const int cc = min(r0 + grp, c - 1);
+                const u32 id = key_id(rk[cc]);
+                const float dist = canon_dist<8>(s.qv, d.x + (size_t)id * mp, (int)mp, (int)d.metric, g);
+                __syncwarp();
+                if (r0 + grp < c && g == 0) rk[cc] = mkkey(dist, id);
+                __syncwarp();
+            }
+            for (int i = c + lane; i < 64; i += 32) rk[i] = KEY_INF;
+            __syncwarp();
+            warp_sort_u64(rk, 64);
+            // equal keys (an id seen twice) are adjacent after the sort: keep one
+            u32 outc = 0;
+            for (int i0 = 0; i0 < 64; i0 += 32) {
+                const int i = i0 + lane;
+                const bool ok = rk[i] != KEY_INF && (i == 0 || rk[i] != rk[i - 1]);
+                const u32 m = __ballot_sync(FULL, ok);
+                const u32 pos = outc + __popc(m & lanemask_lt());
+                if (ok && pos < a.k) {
+                    a.out_ids[(size_t)qi * a.k + pos] = key_id(rk[i]);
+                    a.out_dist[(size_t)qi * a.k + pos] = key_rho(rk[i]);
+                }
+                outc += __popc(m);
+            }
+            for (u32 p = outc + lane; p < a.k; p += 32) {
+                a.out_ids[(size_t)qi * a.k + p] = NIL;
+                a.out_dist[(size_t)qi * a.k + p] = __int_as_float(0x7f800000);
+            }
+        } else if (a.mode == 0) {
             // first k beam entries whose sampled delta is 0
             u32 c = 0;
             for (int i0 = 0; i0 < n && c < a.k; i0 += 32) {
@@ -417,34 +544,49 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
 }
 
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
-    return 4 * search_warp_bytes(mp, L, stage_rows, seen_slots);
+    return 4 * search_warp_bytes(mp, L, stage_rows, seen_slots, mp * 4);
 }
 
-cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st) {
+cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec) {
     if (nq == 0 || d.n_entries == 0) return cudaSuccess;
-    SeedArgs a{d, q, nq, L, seed};
-    size_t smem = align_up((size_t)SEED_TILE * d.mp * 4, 16) + 8 * seed_warp_bytes(d.mp, L);
-    cudaError_t e = cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
+    const u32 rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
+    SeedArgs a{d, q, nq, L, seed, rowb};
+    const void *fn = prec == 1 ? (const void *)seed_kernel<1> : prec == 2 ? (const void *)seed_kernel<2>
+                                                                          : (const void *)seed_kernel<0>;
+    size_t smem = align_up((size_t)SEED_TILE * rowb, 16) + 8 * seed_warp_bytes(d.mp, L);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    seed_kernel<<<(nq + 7) / 8, 256, smem, st>>>(a);
+    const unsigned blocks = (nq + 7) / 8;
+    if (prec == 1) seed_kernel<1><<<blocks, 256, smem, st>>>(a);
+    else if (prec == 2) seed_kernel<2><<<blocks, 256, smem, st>>>(a);
+    else seed_kernel<0><<<blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
-                          const SearchTuning &tune, int num_sms, cudaStream_t st) {
+                          const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec, u32 rerank) {
     if (nq == 0) return cudaSuccess;
+    if (mode != 0) prec = 0;
+    if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
     SearchArgs a;
     a.d = d; a.q = q; a.seed = seed; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode; a.k = k;
     a.out_ids = out_ids; a.out_dist = out_dist; a.exp_keys = exp_keys; a.exp_count = exp_count;
     a.stage_rows = tune.stage_rows;
     a.seen_bits = tune.seen_bits;
     a.seen_slots = 1u << tune.seen_bits;
-    size_t smem = search_smem_bytes(d.mp, L, a.stage_rows, a.seen_slots);
-    cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
+    a.rerank = rerank;
+    // the rerank buffer (64 keys) lives in the stage
+    if (prec != 0 && (size_t)a.stage_rows * a.rowb < 64 * 8) a.stage_rows = (64 * 8 + a.rowb - 1) / a.rowb;
+    const void *fn = prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>
+                                                                            : (const void *)search_kernel<0>;
+    size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms);
@@ -452,7 +594,9 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    search_kernel<<<blocks, 128, smem, st>>>(a);
+    if (prec == 1) search_kernel<1><<<blocks, 128, smem, st>>>(a);
+    else if (prec == 2) search_kernel<2><<<blocks, 128, smem, st>>>(a);
+    else search_kernel<0><<<blocks, 128, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,9 @@
 // util.cu — scans, a stable LSD radix sort, segmenting, the pool recycle
 // step, ingest, entry-set selection, brute-force ground truth and graph
 // export.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -256,6 +259,40 @@ __global__ void ingest_kernel(float *x, u32 mp, const float *src, u32 dim, u64 n
     if (i >= n * mp) return;
     const u64 r = i / mp, c = i % mp;
     x[i] = c < dim ? src[r * dim + c] : 0.0f;
+}
+
+// Reduced-precision copies of rows [first, first + n), one warp per row:
+// bf16 by round-to-nearest-even; e4m3 codes of x / s with s = max|x| / 448
+// (s = 1 for a zero row), saturating, by CUDA's conversion intrinsic.
+__global__ void ingest_copies_kernel(Dev d, u64 first, u64 n) {
+    const u64 w = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const u64 row = first + w;
+    const float *xr = d.x + row * d.mp;
+    if (d.xb) {
+        __nv_bfloat16 *br = reinterpret_cast<__nv_bfloat16 *>(d.xb + row * d.mb);
+        for (u32 i = lane; i < d.mb; i += 32) br[i] = __float2bfloat16_rn(i < d.mp ? xr[i] : 0.0f);
+    }
+    if (d.x8) {
+        float amax = 0.0f;
+        for (u32 i = lane; i < d.dim; i += 32) amax = fmaxf(amax, fabsf(xr[i]));
+        for (int o = 16; o >= 1; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+        float sc = __fdiv_rn(amax, 448.0f);
+        if (!(sc > 0.0f)) sc = 1.0f;
+        unsigned char *cr = d.x8 + row * d.m8;
+        for (u32 i = lane; i < d.m8; i += 32) {
+            const float v = i < d.dim ? __fdiv_rn(xr[i], sc) : 0.0f;
+            cr[i] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+        }
+        if (lane == 0) d.x8s[row] = sc;
+    }
+}
+
+cudaError_t launch_ingest_copies(const Dev &d, u64 first, u64 n, cudaStream_t st) {
+    if (n == 0 || (!d.xb && !d.x8)) return cudaSuccess;
+    ingest_copies_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(d, first, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st) {
