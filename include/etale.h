@@ -185,9 +185,22 @@ etale_status etale_stats(etale_index *idx, etale_stats_t *out);
 /* Resolved configuration of an index.                                      */
 etale_status etale_get_config(const etale_index *idx, etale_config *out);
 
-/* One-line description of the last error on this index (or of the last
- * failed etale_create when idx is NULL).  Never NULL.                      */
+/* One-line description of the last failed call made by the calling thread
+ * (on any index, etale_create included); idx is ignored.  Never NULL.      */
 const char *etale_last_error(const etale_index *idx);
+
+/* Concurrent mode (off by default).  With it on, one thread may run query
+ * searches (etale_search / etale_search_static) on one stream while another
+ * thread runs update calls (insert, delete, reclaim) on another stream; the
+ * two overlap on the device.  Searches keep their own scratch, work queue
+ * and error word.  Slabs retired by an update call are not reused within it:
+ * they return to the free stack at the start of the NEXT update call, after
+ * that call's stream has waited for the last search issued so far, so no
+ * search can read a slab after its reuse (Lemma 1, Proposition 2).  Each
+ * update call therefore needs free slabs for all of its publications (large
+ * inserts may return ENOMEM; cut them).  Two searches, or two updates, must
+ * still not overlap.                                                        */
+etale_status etale_set_concurrent(etale_index *idx, int on);
 
 /* Kernel launches issued by this library so far (launch accounting).      */
 uint64_t etale_kernel_launches(const etale_index *idx);

@@ -48,7 +48,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_reclaim", "etale_search", "etale_ground_truth", "etale_export_graph",
            "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
            "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static",
-           "etale_set_search_precision", "etale_export_copies"]
+           "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
             "etale_search_static": ([P, P, U64, U32, U32, P, P, P], C.c_int),
             "etale_set_search_precision": ([P, C.c_int], C.c_int),
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
+            "etale_set_concurrent": ([P, C.c_int], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -198,6 +199,10 @@ class Index:
         self._check(self.lib.etale_search(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
                                           _ptr(dist), _stream(stream)))
         return ids, dist
+
+    def set_concurrent(self, on: bool = True):
+        """Let one search thread and one update thread overlap on the device."""
+        self._check(self.lib.etale_set_concurrent(self.h, int(on)))
 
     def set_search_precision(self, prec: str):
         """"fp32", "bf16" or "fp8" for later query searches."""

@@ -22,7 +22,9 @@ std::atomic<unsigned long long> g_kernel_launches{0};
 
 namespace {
 
-thread_local std::string g_create_error = "no error";
+// Message of the last failed call on this thread (any index), so that a
+// search thread and a writer thread never share one string.
+thread_local std::string t_last_error = "no error";
 
 struct DevBuf {
     void *p = nullptr;
@@ -89,13 +91,23 @@ struct etale_index {
     DevBuf del_ids, del_vals, del_ids2, del_vals2, del_ok, del_scan, dt, pair_key, pair_val, pair_key2, pair_val2,
         pair_K, pair_Kn, pair_flags, pair_scan, pair_seg, counts;
     DevBuf ex_del, ex_hs, ex_deg, ex_ids, ex_rho, seed;
+    // query-search scratch, separate from the writer's so that one search
+    // call and one update call can run at the same time (concurrent mode)
+    DevBuf s_stage, s_qpad, s_out_ids, s_out_dist, s_seed;
+    u64 *host_ctr_s = nullptr;        // pinned, search side
+    u64 *host_ctr_st = nullptr;       // pinned, etale_stats
+    cudaStream_t stat_stream = nullptr;
+    std::mutex mu;                    // guards search_ev and its validity
+    cudaEvent_t search_ev = nullptr;  // recorded after every query search
+    bool search_ev_valid = false;
+    bool concurrent = false;
     // host-side state
     u64 next_id = 0, live = 0, tombs = 0, reclaimed = 0;
-    u32 n_entries = 0;
+    std::atomic<u32> n_entries{0};
     u64 free_lb = 0;
     u64 device_bytes = 0;
     SearchTuning tune;
-    std::string err = "no error";
+
     // phase timing (opt-in)
     static constexpr int MAXREC = 2048;
     bool prof = false;
@@ -109,7 +121,7 @@ struct etale_index {
         Dev d;
         d.x = x; d.ref = ref; d.slab = slab; d.free_stack = free_stack; d.retired = retired; d.ctr = ctr;
         d.entries = entries; d.dim = dim; d.mp = mp; d.R = R; d.metric = metric; d.alpha2 = alpha2;
-        d.n_entries = n_entries; d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
+        d.n_entries = n_entries.load(std::memory_order_relaxed); d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
         d.gram = cfg.gram == 2 ? 1u : 0u;
         d.xb = xb; d.x8 = x8; d.x8s = x8s; d.mb = mb; d.m8 = m8;
         return d;
@@ -121,7 +133,7 @@ struct etale_index {
         va_start(ap, fmt);
         vsnprintf(buf, sizeof buf, fmt, ap);
         va_end(ap);
-        err = buf;
+        t_last_error = buf;
         return s;
     }
     etale_status cuda_fail(cudaError_t e, const char *where) {
@@ -200,6 +212,30 @@ etale_status check_device_errors(etale_index *idx, cudaStream_t st) {
     return ETALE_OK;
 }
 
+// Query-search counterpart of check_device_errors: its own pinned buffer and
+// error word, so that it never touches the writer's.
+etale_status check_search_errors(etale_index *idx, cudaStream_t st) {
+    CK(cudaMemcpyAsync(idx->host_ctr_s, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost, st), "read counters");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (idx->prof && !idx->concurrent) prof_flush(idx);
+    const u64 e = idx->host_ctr_s[C_ERR_S];
+    if (e) {
+        CK(cudaMemsetAsync(idx->ctr + C_ERR_S, 0, sizeof(u64), st), "clear error");
+        CK(cudaStreamSynchronize(st), "synchronize");
+        if (e & ERR_TIMEOUT) return idx->fail(ETALE_ETIMEOUT, "a bounded device wait gave up");
+        return idx->fail(ETALE_EINTERNAL, "device error bits 0x%llx", e);
+    }
+    return ETALE_OK;
+}
+
+// Concurrent mode: a writer call first waits (on its stream) for the last
+// query search issued so far, then returns the slabs retired by the previous
+// writer call to the free stack.  Any search that could still read one of
+// those slabs was issued before this call started (Proposition 2's separation
+// of searches from slab reuse, enforced with an event instead of a device
+// barrier).
+etale_status writer_begin(etale_index *idx, cudaStream_t st);
+
 // Make sure a phase that may pop `need` slabs cannot exhaust the pool.
 etale_status ensure_pool(etale_index *idx, u64 need, cudaStream_t st) {
     if (idx->free_lb >= need) {
@@ -216,7 +252,26 @@ etale_status ensure_pool(etale_index *idx, u64 need, cudaStream_t st) {
     return ETALE_OK;
 }
 
+etale_status recycle_now(etale_index *idx, cudaStream_t st) {
+    PhaseScope ps(idx, ETALE_PH_RECYCLE, st);
+    CK(launch_recycle(idx->dev(), st), "recycle");
+    g_kernel_launches++;
+    return ETALE_OK;
+}
+
+etale_status writer_begin(etale_index *idx, cudaStream_t st) {
+    if (!idx->concurrent) return ETALE_OK;
+    {
+        std::lock_guard<std::mutex> lk(idx->mu);
+        if (idx->search_ev_valid) CK(cudaStreamWaitEvent(st, idx->search_ev, 0), "wait for searches");
+    }
+    return recycle_now(idx, st);
+}
+
+// The recycle step between launches (Sec. 3.3).  In concurrent mode the
+// retired slabs stay retired until the next writer call (writer_begin).
 etale_status recycle(etale_index *idx, cudaStream_t st) {
+    if (idx->concurrent) return ETALE_OK;
     PhaseScope ps(idx, ETALE_PH_RECYCLE, st);
     CK(launch_recycle(idx->dev(), st), "recycle");
     g_kernel_launches++;
@@ -382,11 +437,11 @@ etale_status etale_config_default(etale_config *cfg) {
 
 etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, uint64_t capacity,
                           const etale_config *cfg_in, etale_index **out) {
-    if (!out) { g_create_error = "out is NULL"; return ETALE_EINVAL; }
+    if (!out) { t_last_error = "out is NULL"; return ETALE_EINVAL; }
     *out = nullptr;
     if (dim == 0 || degree == 0 || degree > (u32)MAX_R || capacity == 0 || capacity >= 0xFFFFFFFFull ||
         (metric != ETALE_L2 && metric != ETALE_IP)) {
-        g_create_error = "invalid dim, metric, degree (1..64) or capacity";
+        t_last_error = "invalid dim, metric, degree (1..64) or capacity";
         return ETALE_EINVAL;
     }
     etale_config cfg;
@@ -408,27 +463,27 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         if (cfg_in->rerank) cfg.rerank = cfg_in->rerank;
     }
     if (cfg.copies > 3) {
-        g_create_error = "copies is a bitmask of 1 (bf16) and 2 (fp8)";
+        t_last_error = "copies is a bitmask of 1 (bf16) and 2 (fp8)";
         return ETALE_EINVAL;
     }
     if (cfg.gram > 2) {
-        g_create_error = "gram must be 0..2";
+        t_last_error = "gram must be 0..2";
         return ETALE_EINVAL;
     }
     if (cfg.gram == 0) cfg.gram = cfg.mode == ETALE_MODE_LOCKFREE ? 2 : 1;
     if (cfg.stage_kb > 64) {
-        g_create_error = "stage_kb must be <= 64";
+        t_last_error = "stage_kb must be <= 64";
         return ETALE_EINVAL;
     }
     if (cfg.refine > 2 || cfg.mode > 1 || cfg.build_beam > 256) {
-        g_create_error = "refine must be 0..2, mode 0..1, build_beam <= 256";
+        t_last_error = "refine must be 0..2, mode 0..1, build_beam <= 256";
         return ETALE_EINVAL;
     }
     if (cfg.max_cand == 0) cfg.max_cand = 2 * cfg.build_beam;
     if (cfg.max_batch == 0) cfg.max_batch = capacity / 100 ? capacity / 100 : 1;
     if (cfg.pool_slabs == 0) cfg.pool_slabs = 2 * capacity + 4ull * (degree + 1) * cfg.max_batch;
     if (cfg.pool_slabs >= 0xFFFFFFFFull) {
-        g_create_error = "pool_slabs must be below 2^32 - 1";
+        t_last_error = "pool_slabs must be below 2^32 - 1";
         return ETALE_EINVAL;
     }
     etale_index *idx = new etale_index();
@@ -449,7 +504,11 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
               cudaMalloc(&idx->retired, pb) == cudaSuccess &&
               cudaMalloc(&idx->ctr, C_NCTR * sizeof(u64)) == cudaSuccess &&
               cudaMalloc(&idx->entries, (size_t)cfg.n_entry * 4) == cudaSuccess &&
-              cudaMallocHost(&idx->host_ctr, C_NCTR * sizeof(u64)) == cudaSuccess;
+              cudaMallocHost(&idx->host_ctr, C_NCTR * sizeof(u64)) == cudaSuccess &&
+              cudaMallocHost(&idx->host_ctr_s, C_NCTR * sizeof(u64)) == cudaSuccess &&
+              cudaMallocHost(&idx->host_ctr_st, C_NCTR * sizeof(u64)) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&idx->stat_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&idx->search_ev, cudaEventDisableTiming) == cudaSuccess;
     idx->mb = (idx->mp + 7) / 8 * 8;
     idx->m8 = (idx->mp + 15) / 16 * 16;
     if (ok && (cfg.copies & 1)) ok = cudaMalloc(&idx->xb, (size_t)capacity * idx->mb * 2) == cudaSuccess;
@@ -458,7 +517,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
              cudaMalloc(&idx->x8s, (size_t)capacity * 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        g_create_error = "device allocation failed";
+        t_last_error = "device allocation failed";
         etale_destroy(idx);
         return ETALE_ENOMEM;
     }
@@ -485,7 +544,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
     ok2 = ok2 && cudaMemcpy(idx->ctr, ctr.data(), C_NCTR * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
           cudaMemset(idx->x, 0, xb) == cudaSuccess;
     if (!ok2) {
-        g_create_error = std::string("device initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
+        t_last_error = std::string("device initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
         etale_destroy(idx);
         return ETALE_ECUDA;
     }
@@ -500,6 +559,10 @@ etale_status etale_destroy(etale_index *idx) {
     cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
     cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s);
     if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
+    if (idx->host_ctr_s) cudaFreeHost(idx->host_ctr_s);
+    if (idx->host_ctr_st) cudaFreeHost(idx->host_ctr_st);
+    if (idx->stat_stream) cudaStreamDestroy(idx->stat_stream);
+    if (idx->search_ev) cudaEventDestroy(idx->search_ev);
     for (cudaEvent_t e : idx->pev) cudaEventDestroy(e);
     DevBuf *bufs[] = {&idx->stage, &idx->qpad, &idx->out_ids, &idx->out_dist, &idx->exp_keys, &idx->exp_count,
                       &idx->F_id, &idx->F_rho, &idx->F_n, &idx->of_key, &idx->of_val, &idx->of_key2,
@@ -509,7 +572,8 @@ etale_status etale_destroy(etale_index *idx) {
                       &idx->del_ok, &idx->del_scan, &idx->dt, &idx->pair_key, &idx->pair_val, &idx->pair_key2,
                       &idx->pair_val2, &idx->pair_K, &idx->pair_Kn, &idx->pair_flags, &idx->pair_scan,
                       &idx->pair_seg, &idx->counts, &idx->ex_del, &idx->ex_hs, &idx->ex_deg, &idx->ex_ids,
-                      &idx->ex_rho, &idx->seed};
+                      &idx->ex_rho, &idx->seed, &idx->s_stage, &idx->s_qpad, &idx->s_out_ids, &idx->s_out_dist,
+                      &idx->s_seed};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     delete idx;
@@ -524,8 +588,10 @@ etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n, uint3
         return idx->fail(ETALE_ECAPACITY, "insert of %llu would exceed capacity %llu (next id %llu)",
                          (unsigned long long)n, (unsigned long long)idx->capacity, (unsigned long long)idx->next_id);
     cudaStream_t st = (cudaStream_t)stream;
+    etale_status s = writer_begin(idx, st);
+    if (s != ETALE_OK) return s;
     const void *src = nullptr;
-    etale_status s = StreamCopy::in(idx, idx->stage, vecs, (size_t)n * idx->dim * 4, &src, st);
+    s = StreamCopy::in(idx, idx->stage, vecs, (size_t)n * idx->dim * 4, &src, st);
     if (s != ETALE_OK) return s;
     const u64 first_all = idx->next_id;
     CK(launch_ingest(idx->x + first_all * idx->mp, idx->mp, (const float *)src, idx->dim, n, st), "ingest");
@@ -577,6 +643,10 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
               grow(idx->sort_scr, sort_scratch_elems((u32)std::max<u64>(slots, n)) * 4) &&
               grow(idx->scan_scr, scan_scratch_elems((u32)std::max<u64>(slots, n)) * 4);
     if (!ok) return idx->fail(ETALE_ENOMEM, "scratch allocation (delete batch of %llu)", (unsigned long long)n);
+    {
+        etale_status sb = writer_begin(idx, st);
+        if (sb != ETALE_OK) return sb;
+    }
     if (is_device_ptr(ids)) {
         CK(cudaMemcpyAsync(idx->del_ids.p, ids, n * 4, cudaMemcpyDeviceToDevice, st), "copy ids");
     } else {
@@ -644,10 +714,12 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
 etale_status etale_reclaim(etale_index *idx, void *stream) {
     if (!idx) return ETALE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
-    etale_status s = recompute_entries(idx, st);
+    etale_status s = writer_begin(idx, st);
+    if (s != ETALE_OK) return s;
+    s = recompute_entries(idx, st);
     if (s != ETALE_OK) return s;
     const u64 n = idx->next_id;
-    if (n == 0) return ETALE_OK;
+    if (n == 0) return check_device_errors(idx, st);
     if (!grow(idx->tomb_bits, ((n + 31) / 32) * 4)) return idx->fail(ETALE_ENOMEM, "scratch allocation (reclaim)");
     Dev d = idx->dev();
     s = ensure_pool(idx, idx->live, st);
@@ -685,43 +757,48 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
     if (nq > 0xFFFFFFFFull) return idx->fail(ETALE_EINVAL, "too many queries");
     cudaStream_t st = (cudaStream_t)stream;
     const void *src = nullptr;
-    etale_status s = StreamCopy::in(idx, idx->stage, queries, (size_t)nq * idx->dim * 4, &src, st);
+    etale_status s = StreamCopy::in(idx, idx->s_stage, queries, (size_t)nq * idx->dim * 4, &src, st);
     if (s != ETALE_OK) return s;
-    if (!grow(idx->qpad, (size_t)nq * idx->mp * 4)) return idx->fail(ETALE_ENOMEM, "query staging");
-    CK(launch_ingest(as<float>(idx->qpad), idx->mp, (const float *)src, idx->dim, nq, st), "query ingest");
+    if (!grow(idx->s_qpad, (size_t)nq * idx->mp * 4)) return idx->fail(ETALE_ENOMEM, "query staging");
+    float *qpad = as<float>(idx->s_qpad);
+    CK(launch_ingest(qpad, idx->mp, (const float *)src, idx->dim, nq, st), "query ingest");
     const bool dev_out = is_device_ptr(out_ids) && is_device_ptr(out_dists);
     u32 *oid = out_ids;
     float *od = out_dists;
     if (!dev_out) {
-        if (!grow(idx->out_ids, nq * k * 4) || !grow(idx->out_dist, nq * k * 4))
+        if (!grow(idx->s_out_ids, nq * k * 4) || !grow(idx->s_out_dist, nq * k * 4))
             return idx->fail(ETALE_ENOMEM, "output staging");
-        oid = as<u32>(idx->out_ids);
-        od = as<float>(idx->out_dist);
+        oid = as<u32>(idx->s_out_ids);
+        od = as<float>(idx->s_out_dist);
     }
     Dev d = idx->dev();
+    const bool prof = idx->prof && !idx->concurrent;
     if (exact) {
-        CK(launch_ground_truth(d, idx->next_id, as<float>(idx->qpad), (u32)nq, k, oid, od, idx->num_sms, st),
-           "ground truth");
+        CK(launch_ground_truth(d, idx->next_id, qpad, (u32)nq, k, oid, od, idx->num_sms, st), "ground truth");
     } else {
         const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
-        if (!grow(idx->seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
-        {
-            PhaseScope ps(idx, ETALE_PH_SEED, st);
-            CK(launch_seed(d, as<float>(idx->qpad), (u32)nq, L, as<u64>(idx->seed), st, idx->search_prec),
-               "query seed");
-        }
-        PhaseScope ps(idx, ETALE_PH_SEARCH_QUERY, st);
-        CK(launch_search(d, as<float>(idx->qpad), (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->seed),
-                         idx->tune, idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
+        if (!grow(idx->s_seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
+        if (prof) prof_begin(idx, ETALE_PH_SEED, st);
+        CK(launch_seed(d, qpad, (u32)nq, L, as<u64>(idx->s_seed), st, idx->search_prec), "query seed");
+        if (prof) prof_end(idx, st);
+        if (prof) prof_begin(idx, ETALE_PH_SEARCH_QUERY, st);
+        CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->s_seed), idx->tune,
+                         idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
            "search");
+        if (prof) prof_end(idx, st);
         g_kernel_launches++;
+        if (idx->concurrent) {
+            std::lock_guard<std::mutex> lk(idx->mu);
+            CK(cudaEventRecord(idx->search_ev, st), "record search event");
+            idx->search_ev_valid = true;
+        }
     }
     g_kernel_launches += 2;
     if (!dev_out) {
         CK(cudaMemcpyAsync(out_ids, oid, nq * k * 4, cudaMemcpyDeviceToHost, st), "copy ids out");
         CK(cudaMemcpyAsync(out_dists, od, nq * k * 4, cudaMemcpyDeviceToHost, st), "copy dists out");
     }
-    return check_device_errors(idx, st);
+    return check_search_errors(idx, st);
 }
 
 etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
@@ -767,10 +844,14 @@ etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n) {
 
 etale_status etale_stats(etale_index *idx, etale_stats_t *o) {
     if (!idx || !o) return ETALE_EINVAL;
-    cudaError_t e = cudaMemcpy(idx->host_ctr, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost);
+    // a private non-blocking stream: reading the counters never waits for,
+    // or orders against, the caller's streams
+    cudaError_t e = cudaMemcpyAsync(idx->host_ctr_st, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost,
+                                    idx->stat_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(idx->stat_stream);
     if (e != cudaSuccess) return idx->cuda_fail(e, "read counters");
     memset(o, 0, sizeof *o);
-    const u64 *c = idx->host_ctr;
+    const u64 *c = idx->host_ctr_st;
     o->live = idx->live;
     o->tombstones = idx->tombs;
     o->reclaimed = idx->reclaimed;
@@ -797,8 +878,12 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out) {
     return ETALE_OK;
 }
 
-const char *etale_last_error(const etale_index *idx) {
-    return idx ? idx->err.c_str() : g_create_error.c_str();
+const char *etale_last_error(const etale_index *) { return t_last_error.c_str(); }
+
+etale_status etale_set_concurrent(etale_index *idx, int on) {
+    if (!idx) return ETALE_EINVAL;
+    idx->concurrent = on != 0;
+    return ETALE_OK;
 }
 
 uint64_t etale_kernel_launches(const etale_index *) { return g_kernel_launches.load(); }
@@ -864,7 +949,12 @@ etale_status etale_search_static(etale_index *idx, const float *queries, uint64_
                      idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
        "search");
     g_kernel_launches += 3;
-    return check_device_errors(idx, st);
+    if (idx->concurrent) {
+        std::lock_guard<std::mutex> lk(idx->mu);
+        CK(cudaEventRecord(idx->search_ev, st), "record search event");
+        idx->search_ev_valid = true;
+    }
+    return check_search_errors(idx, st);
 }
 
 etale_status etale_set_search_precision(etale_index *idx, etale_precision p) {

@@ -42,6 +42,7 @@ enum : int {
     C_WORK2 = 10,
     C_COUNT_A = 11,    // scratch counts produced on the device
     C_COUNT_B = 12,
+    C_ERR_S = 13,      // error bits of query searches (kept apart from writers')
     C_NCTR = 16
 };
 

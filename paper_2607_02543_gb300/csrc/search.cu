@@ -34,6 +34,8 @@ struct SearchArgs {
     u32 *exp_count;
     u32 stage_rows, seen_slots, seen_bits;
     u32 rowb;            // bytes per gathered row (fp32, bf16 or fp8 copy)
+    u32 wq, err;         // work-queue counter and error word (query searches
+                         // use their own, so they can overlap a writer)
     u32 rerank;          // reduced precision: re-scored candidates (<= 64)
 };
 
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
     bool timeout = false;
     for (;;) {
         u32 qi = 0;
-        if (lane == 0) qi = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
+        if (lane == 0) qi = (u32)atomicAdd(&d.ctr[a.wq], 1ull);
         qi = __shfl_sync(FULL, qi, 0);
         if (qi >= a.nq) break;
         const float *qrow = a.q + (size_t)qi * mp;
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
     if (lane == 0) {
         atomicAdd(&d.ctr[C_EXPAND], nexp_tot);
         atomicAdd(&d.ctr[C_DIST], ndist);
-        if (timeout) atomicOr(&d.ctr[C_ERR], (u64)ERR_TIMEOUT);
+        if (timeout) atomicOr(&d.ctr[a.err], (u64)ERR_TIMEOUT);
     }
 }
 
@@ -578,6 +580,8 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.seen_slots = 1u << tune.seen_bits;
     a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
     a.rerank = rerank;
+    a.wq = mode == 0 ? C_WORK2 : C_WORK;
+    a.err = mode == 0 ? C_ERR_S : C_ERR;
     // the rerank buffer (64 keys) lives in the stage
     if (prec != 0 && (size_t)a.stage_rows * a.rowb < 64 * 8) a.stage_rows = (64 * 8 + a.rowb - 1) / a.rowb;
     const void *fn = prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>
@@ -592,7 +596,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     u32 blocks = (u32)(per_sm * num_sms);
     u32 need = (nq + 3) / 4;
     if (blocks > need) blocks = need;
-    e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
+    e = cudaMemsetAsync(d.ctr + a.wq, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
     if (prec == 1) search_kernel<1><<<blocks, 128, smem, st>>>(a);
     else if (prec == 2) search_kernel<2><<<blocks, 128, smem, st>>>(a);
