@@ -189,6 +189,44 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out);
  * (on any index, etale_create included); idx is ignored.  Never NULL.      */
 const char *etale_last_error(const etale_index *idx);
 
+/* ---- launch-shape tuning (Sec. 8(a) a13) --------------------------------- */
+typedef struct {
+    uint32_t stage_rows;  /* neighbour rows gathered per bulk-copy batch      */
+    uint32_t seen_bits;   /* log2 slots of the evaluated-id cache             */
+    float ms;             /* measured: seeding + search of the tuning batch   */
+} etale_tuning;
+
+/* Set the query-search launch shape (results never depend on it).          */
+etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits);
+
+/* Time seeding + BeamSearch of the given DEVICE query batch under each
+ * candidate launch shape (stage rows 8/16/32 x cache 2^8..2^11 slots), keep
+ * the fastest for this index, and report up to n_out tried shapes in out.
+ * Results do not depend on the launch shape.                               */
+etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
+                                   uint32_t beam, etale_tuning *out, uint32_t n_out, uint32_t *n_tried,
+                                   void *stream);
+
+/* ---- CUDA-graph query batches (Sec. 8(a) a13) ----------------------------- */
+typedef struct etale_search_graph etale_search_graph;
+
+/* Capture the query path (row padding, seeding, BeamSearch) into a CUDA
+ * graph bound to caller-owned DEVICE buffers: queries (nq_max x dim),
+ * out_ids / out_dists (nq_max x k) and nq_dev, one uint32 that holds the
+ * batch size of each launch (clamped to nq_max).  The kernels read the batch
+ * size and the entry-set size from device memory, so one graph serves every
+ * batch size and stays valid across later updates of the index.  The search
+ * precision and launch shape in force at creation are baked in.  The graph
+ * owns its scratch (allocated here, freed by destroy).                     */
+etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32_t k, uint32_t beam,
+                                       const float *queries, uint32_t *out_ids, float *out_dists,
+                                       const uint32_t *nq_dev, etale_search_graph **out);
+/* Enqueue one replay on `stream` (asynchronous, no host synchronisation).  */
+etale_status etale_search_graph_launch(etale_search_graph *g, void *stream);
+/* Synchronise `stream` and report device-side errors of earlier replays.    */
+etale_status etale_search_graph_check(etale_search_graph *g, void *stream);
+etale_status etale_search_graph_destroy(etale_search_graph *g);
+
 /* Concurrent mode (off by default).  With it on, one thread may run query
  * searches (etale_search / etale_search_static) on one stream while another
  * thread runs update calls (insert, delete, reclaim) on another stream; the

@@ -35,6 +35,10 @@ class Config(C.Structure):
                 ("copies", C.c_uint32), ("rerank", C.c_uint32), ("reserved", C.c_uint32 * 2)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("stage_rows", C.c_uint32), ("seen_bits", C.c_uint32), ("ms", C.c_float)]
+
+
 class Stats(C.Structure):
     _fields_ = [("live", C.c_uint64), ("tombstones", C.c_uint64), ("reclaimed", C.c_uint64),
                 ("next_id", C.c_uint64), ("capacity", C.c_uint64), ("pool_slabs", C.c_uint64),
@@ -48,7 +52,9 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_reclaim", "etale_search", "etale_ground_truth", "etale_export_graph",
            "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
            "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static",
-           "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent"]
+           "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent",
+           "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
+           "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
@@ -87,6 +93,12 @@ def load(path: str = LIB_PATH):
             "etale_set_search_precision": ([P, C.c_int], C.c_int),
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
             "etale_set_concurrent": ([P, C.c_int], C.c_int),
+            "etale_set_search_tuning": ([P, U32, U32], C.c_int),
+            "etale_autotune_search": ([P, P, U64, U32, U32, P, U32, C.POINTER(U32), P], C.c_int),
+            "etale_search_graph_create": ([P, U32, U32, U32, P, P, P, P, C.POINTER(P)], C.c_int),
+            "etale_search_graph_launch": ([P, P], C.c_int),
+            "etale_search_graph_check": ([P, P], C.c_int),
+            "etale_search_graph_destroy": ([P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -200,6 +212,25 @@ class Index:
                                           _ptr(dist), _stream(stream)))
         return ids, dist
 
+    def set_search_tuning(self, stage_rows: int, seen_bits: int):
+        self._check(self.lib.etale_set_search_tuning(self.h, stage_rows, seen_bits))
+
+    def autotune_search(self, queries, k: int, beam: int, stream=None):
+        """Time the launch shapes on a device query batch; keep the fastest.
+        Returns [(stage_rows, seen_bits, ms), ...] for the shapes tried."""
+        out = (Tuning * 32)()
+        n = C.c_uint32(0)
+        self._check(self.lib.etale_autotune_search(self.h, _ptr(queries), queries.shape[0], k, beam, out, 32,
+                                                   C.byref(n), _stream(stream)))
+        return [(out[i].stage_rows, out[i].seen_bits, out[i].ms) for i in range(n.value)]
+
+    def search_graph(self, queries, out_ids, out_dists, nq_dev, k: int, beam: int) -> "SearchGraph":
+        """Capture the query path for batches of up to queries.shape[0] into a CUDA graph."""
+        g = C.c_void_p()
+        self._check(self.lib.etale_search_graph_create(self.h, queries.shape[0], k, beam, _ptr(queries),
+                                                       _ptr(out_ids), _ptr(out_dists), _ptr(nq_dev), C.byref(g)))
+        return SearchGraph(self, g)
+
     def set_concurrent(self, on: bool = True):
         """Let one search thread and one update thread overlap on the device."""
         self._check(self.lib.etale_set_concurrent(self.h, int(on)))
@@ -278,3 +309,27 @@ class Index:
         cnt = np.zeros(n, np.uint64)
         self._check(self.lib.etale_get_profile(self.h, _ptr(ms), _ptr(cnt), n, int(reset)))
         return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+
+class SearchGraph:
+    """A captured query path (see etale_search_graph_create)."""
+
+    def __init__(self, index: Index, handle):
+        self.index, self.h = index, handle
+
+    def launch(self, stream=None):
+        self.index._check(self.index.lib.etale_search_graph_launch(self.h, _stream(stream)))
+
+    def check(self, stream=None):
+        self.index._check(self.index.lib.etale_search_graph_check(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.index.lib.etale_search_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,6 +83,7 @@ struct etale_index {
     float *x8s = nullptr;
     u32 mb = 0, m8 = 0;
     u32 search_prec = 0;
+    u32 *nent_dev = nullptr;        // |E| in device memory
     u64 *host_ctr = nullptr;   // pinned mirror
     // scratch
     DevBuf stage, qpad, out_ids, out_dist, exp_keys, exp_count, F_id, F_rho, F_n;
@@ -124,6 +125,7 @@ struct etale_index {
         d.n_entries = n_entries.load(std::memory_order_relaxed); d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
         d.gram = cfg.gram == 2 ? 1u : 0u;
         d.xb = xb; d.x8 = x8; d.x8s = x8s; d.mb = mb; d.m8 = m8;
+        d.nent_dev = nent_dev;
         return d;
     }
 
@@ -145,6 +147,11 @@ struct etale_index {
     do {                                                                    \
         cudaError_t _e = (expr);                                            \
         if (_e != cudaSuccess) return idx->cuda_fail(_e, where);            \
+    } while (0)
+#define CK2(ix, expr, where)                                                \
+    do {                                                                    \
+        cudaError_t _e = (expr);                                            \
+        if (_e != cudaSuccess) return (ix)->cuda_fail(_e, where);           \
     } while (0)
 
 namespace {
@@ -252,10 +259,32 @@ etale_status ensure_pool(etale_index *idx, u64 need, cudaStream_t st) {
     return ETALE_OK;
 }
 
+// Lock-free fold chunk: as many slots as the free pool covers at two slabs
+// each (one publication plus a retried one), at least one.  In concurrent
+// mode nothing is recycled mid-call, so the whole remainder must fit.
+etale_status lockfree_chunk(etale_index *idx, u64 remaining, u64 *chunk, cudaStream_t st);
+
 etale_status recycle_now(etale_index *idx, cudaStream_t st) {
     PhaseScope ps(idx, ETALE_PH_RECYCLE, st);
     CK(launch_recycle(idx->dev(), st), "recycle");
     g_kernel_launches++;
+    return ETALE_OK;
+}
+
+etale_status lockfree_chunk(etale_index *idx, u64 remaining, u64 *chunk, cudaStream_t st) {
+    u64 want = remaining * 2;
+    if (idx->free_lb < want) {
+        etale_status s = read_ctr(idx, st);
+        if (s != ETALE_OK) return s;
+        idx->free_lb = idx->host_ctr[C_FREE];
+    }
+    u64 c = std::min<u64>(remaining, idx->free_lb / 2);
+    if (idx->concurrent && c < remaining)
+        return idx->fail(ETALE_ENOMEM, "slab pool: %llu free, a concurrent-mode update may need %llu",
+                         (unsigned long long)idx->free_lb, (unsigned long long)want);
+    if (c == 0) return idx->fail(ETALE_ENOMEM, "slab pool exhausted (%llu free)", (unsigned long long)idx->free_lb);
+    idx->free_lb -= 2 * c;
+    *chunk = c;
     return ETALE_OK;
 }
 
@@ -282,6 +311,9 @@ etale_status recompute_entries(etale_index *idx, cudaStream_t st) {
     const u64 n = idx->next_id;
     const u32 S = (u32)(idx->live < idx->cfg.n_entry ? idx->live : idx->cfg.n_entry);
     idx->n_entries = S;
+    // the device copy of |E| (read by query kernels and captured graphs) is
+    // written on the writer's stream, in order with the entry-set update
+    CK(launch_set_u32(idx->nent_dev, S, st), "entry count");
     if (S == 0 || n == 0) return ETALE_OK;
     if (!grow(idx->live_flags, n * 4) || !grow(idx->live_rank, n * 4) ||
         !grow(idx->live_scan_scr, scan_scratch_elems((u32)n) * 4))
@@ -308,9 +340,29 @@ etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t 
     Offers of{as<u32>(idx->of_key), as<u32>(idx->of_val), as<u32>(idx->of_key2), as<u32>(idx->of_val2),
               as<u32>(idx->of_src), as<float>(idx->of_rho), nslots};
     const bool lockfree = idx->cfg.mode == ETALE_MODE_LOCKFREE;
+    u64 *seg_count = as<u64>(idx->counts) + 0;
+    if (lockfree) {
+        // every offer publishes on its own (a lost CAS retires one more slab):
+        // cut the slots into chunks the free pool covers, recycling between
+        for (u64 lo = 0; lo < nslots;) {
+            u64 chunk;
+            etale_status s = lockfree_chunk(idx, nslots - lo, &chunk, st);
+            if (s != ETALE_OK) return s;
+            {
+                PhaseScope ps(idx, ETALE_PH_OFFER_FOLD, st);
+                CK(launch_offer_fold(d, of, nullptr, seg_count, idx->cfg.cas_budget, idx->num_sms, st, (u32)lo,
+                                     (u32)(lo + chunk)),
+                   "offer fold");
+            }
+            g_kernel_launches++;
+            s = recycle(idx, st);
+            if (s != ETALE_OK) return s;
+            lo += chunk;
+        }
+        return ETALE_OK;
+    }
     etale_status s = ensure_pool(idx, std::min<u64>(nslots, targets), st);
     if (s != ETALE_OK) return s;
-    u64 *seg_count = as<u64>(idx->counts) + 0;
     if (!lockfree) {
         PhaseScope ps(idx, ETALE_PH_OFFER_SORT, st);
         SortScratch ss;
@@ -419,6 +471,14 @@ struct StreamCopy {
 
 }  // namespace
 
+struct etale_search_graph {
+    etale_index *idx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    float *qpad = nullptr;
+    u64 *seed = nullptr;
+};
+
 // ===========================================================================
 extern "C" {
 
@@ -508,7 +568,8 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
               cudaMallocHost(&idx->host_ctr_s, C_NCTR * sizeof(u64)) == cudaSuccess &&
               cudaMallocHost(&idx->host_ctr_st, C_NCTR * sizeof(u64)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&idx->stat_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&idx->search_ev, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&idx->search_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(&idx->nent_dev, 16) == cudaSuccess && cudaMemset(idx->nent_dev, 0, 16) == cudaSuccess;
     idx->mb = (idx->mp + 7) / 8 * 8;
     idx->m8 = (idx->mp + 15) / 16 * 16;
     if (ok && (cfg.copies & 1)) ok = cudaMalloc(&idx->xb, (size_t)capacity * idx->mb * 2) == cudaSuccess;
@@ -557,7 +618,7 @@ etale_status etale_destroy(etale_index *idx) {
     if (!idx) return ETALE_OK;
     cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
     cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
-    cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s);
+    cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s); cudaFree(idx->nent_dev);
     if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
     if (idx->host_ctr_s) cudaFreeHost(idx->host_ctr_s);
     if (idx->host_ctr_st) cudaFreeHost(idx->host_ctr_st);
@@ -682,9 +743,28 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
     g_kernel_launches += 2;
     prof_end(idx, st);
     const bool lockfree = idx->cfg.mode == ETALE_MODE_LOCKFREE;
-    etale_status s = ensure_pool(idx, std::min<u64>(slots, idx->live), st);
+    etale_status s = ETALE_OK;
+    if (lockfree) {
+        // one publication per (deleted, neighbour) pair: chunk as for offers
+        for (u64 lo = 0; lo < slots;) {
+            u64 chunk;
+            s = lockfree_chunk(idx, slots - lo, &chunk, st);
+            if (s != ETALE_OK) return s;
+            prof_begin(idx, ETALE_PH_REPAIR_FOLD, st);
+            CK(launch_repair_fold(d, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                                  as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), nullptr, seg_count, chunk,
+                                  idx->cfg.cas_budget, idx->num_sms, st, lo),
+               "repair fold");
+            g_kernel_launches++;
+            prof_end(idx, st);
+            s = recycle(idx, st);
+            if (s != ETALE_OK) return s;
+            lo += chunk;
+        }
+    }
+    if (!lockfree) s = ensure_pool(idx, std::min<u64>(slots, idx->live), st);
     if (s != ETALE_OK) return s;
-    prof_begin(idx, ETALE_PH_REPAIR_FOLD, st);
+    if (!lockfree) prof_begin(idx, ETALE_PH_REPAIR_FOLD, st);
     if (!lockfree) {
         CK(radix_sort_pairs(as<u32>(idx->pair_key), as<u32>(idx->pair_val), as<u32>(idx->pair_key2),
                             as<u32>(idx->pair_val2), (u32)slots, bits_for(idx->capacity), ss, st),
@@ -694,14 +774,16 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
            "pair segments");
         g_kernel_launches += 3 * ((bits_for(idx->capacity) + 7) / 8) * 2 + 4;
     }
-    CK(launch_repair_fold(d, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
-                          as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), as<u32>(idx->pair_seg), seg_count, slots,
-                          lockfree ? idx->cfg.cas_budget : 0, idx->num_sms, st),
-       "repair fold");
-    g_kernel_launches++;
-    prof_end(idx, st);
-    s = recycle(idx, st);
-    if (s != ETALE_OK) return s;
+    if (!lockfree) {
+        CK(launch_repair_fold(d, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                              as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), as<u32>(idx->pair_seg), seg_count, slots,
+                              0, idx->num_sms, st),
+           "repair fold");
+        g_kernel_launches++;
+        prof_end(idx, st);
+        s = recycle(idx, st);
+        if (s != ETALE_OK) return s;
+    }
     u64 k = 0;
     CK(cudaMemcpyAsync(&k, n_dt, sizeof k, cudaMemcpyDeviceToHost, st), "read count");
     s = check_device_errors(idx, st);   // synchronises
@@ -879,6 +961,152 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out) {
 }
 
 const char *etale_last_error(const etale_index *) { return t_last_error.c_str(); }
+
+etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits) {
+    if (!idx) return ETALE_EINVAL;
+    if (stage_rows < 1 || stage_rows > 32 || seen_bits < 6 || seen_bits > 14)
+        return idx->fail(ETALE_EINVAL, "stage_rows must be 1..32 and seen_bits 6..14");
+    idx->tune.stage_rows = stage_rows;
+    idx->tune.seen_bits = seen_bits;
+    return ETALE_OK;
+}
+
+etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
+                                   etale_tuning *out, uint32_t n_out, uint32_t *n_tried, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (n_tried) *n_tried = 0;
+    if (!queries || nq == 0 || k == 0 || !is_device_ptr(queries))
+        return idx->fail(ETALE_EINVAL, "autotune needs a non-empty DEVICE query batch");
+    const u32 L = beam > k ? beam : k;
+    if (L > 256 || nq > 0xFFFFFFFFull) return idx->fail(ETALE_EINVAL, "beam must be <= 256");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!grow(idx->s_qpad, (size_t)nq * idx->mp * 4) || !grow(idx->s_seed, (size_t)nq * L * 8) ||
+        !grow(idx->s_out_ids, nq * k * 4) || !grow(idx->s_out_dist, nq * k * 4))
+        return idx->fail(ETALE_ENOMEM, "autotune scratch");
+    float *qpad = as<float>(idx->s_qpad);
+    CK(launch_ingest(qpad, idx->mp, queries, idx->dim, nq, st), "query ingest");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const SearchTuning saved = idx->tune;
+    const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    float best = 1e30f;
+    SearchTuning best_t = saved;
+    u32 tried = 0;
+    const u32 rows[3] = {8, 16, 32}, bits[4] = {8, 9, 10, 11};
+    for (u32 a = 0; a < 3; a++)
+        for (u32 b = 0; b < 4; b++) {
+            SearchTuning t;
+            t.stage_rows = rows[a];
+            t.seen_bits = bits[b];
+            float ms_best = 1e30f;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; rep++) {   // first run warms up
+                Dev d = idx->dev();
+                cudaEventRecord(e0, st);
+                ok = launch_seed(d, qpad, (u32)nq, L, as<u64>(idx->s_seed), st, idx->search_prec) == cudaSuccess &&
+                     launch_search(d, qpad, (u32)nq, L, H, 0, k, as<u32>(idx->s_out_ids), as<float>(idx->s_out_dist),
+                                   nullptr, nullptr, as<u64>(idx->s_seed), t, idx->num_sms, st, idx->search_prec,
+                                   idx->cfg.rerank) == cudaSuccess;
+                cudaEventRecord(e1, st);
+                if (cudaStreamSynchronize(st) != cudaSuccess) ok = false;
+                float ms = 0.f;
+                if (ok && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) ms_best = std::min(ms_best, ms);
+            }
+            cudaGetLastError();   // a shape that does not fit is skipped
+            if (!ok) continue;
+            if (out && tried < n_out) out[tried] = etale_tuning{t.stage_rows, t.seen_bits, ms_best};
+            tried++;
+            if (ms_best < best) { best = ms_best; best_t = t; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g_kernel_launches += 1 + 2 * 3 * tried;
+    idx->tune = tried ? best_t : saved;
+    if (n_tried) *n_tried = tried;
+    return check_search_errors(idx, st);
+}
+
+etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32_t k, uint32_t beam,
+                                       const float *queries, uint32_t *out_ids, float *out_dists,
+                                       const uint32_t *nq_dev, etale_search_graph **out) {
+    if (!idx || !out) return ETALE_EINVAL;
+    *out = nullptr;
+    const u32 L = beam > k ? beam : k;
+    if (nq_max == 0 || k == 0 || L > 256 || !nq_dev)
+        return idx->fail(ETALE_EINVAL, "graph needs nq_max > 0, k > 0, beam <= 256 and nq_dev");
+    if (!is_device_ptr(queries) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists) || !is_device_ptr(nq_dev))
+        return idx->fail(ETALE_EINVAL, "graph buffers must be device pointers");
+    if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
+    etale_search_graph *g = new etale_search_graph();
+    g->idx = idx;
+    if (cudaMalloc(&g->qpad, (size_t)nq_max * idx->mp * 4) != cudaSuccess ||
+        cudaMalloc(&g->seed, (size_t)nq_max * L * 8) != cudaSuccess) {
+        cudaGetLastError();
+        etale_search_graph_destroy(g);
+        return idx->fail(ETALE_ENOMEM, "graph scratch");
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        etale_search_graph_destroy(g);
+        return idx->fail(ETALE_ECUDA, "capture stream");
+    }
+    const Dev d = idx->dev();
+    const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    auto enqueue = [&]() {
+        cudaError_t e = launch_ingest(g->qpad, idx->mp, queries, idx->dim, nq_max, cs, nq_dev);
+        if (e == cudaSuccess) e = launch_seed(d, g->qpad, nq_max, L, g->seed, cs, idx->search_prec, nq_dev);
+        if (e == cudaSuccess)
+            e = launch_search(d, g->qpad, nq_max, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, g->seed,
+                              idx->tune, idx->num_sms, cs, idx->search_prec, idx->cfg.rerank, nq_dev);
+        return e;
+    };
+    // one eager run sets the kernels' attributes outside the capture
+    cudaError_t e = enqueue();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue();
+        e = cudaStreamEndCapture(cs, &g->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        etale_search_graph_destroy(g);
+        return idx->cuda_fail(e, "graph capture");
+    }
+    *out = g;
+    return ETALE_OK;
+}
+
+etale_status etale_search_graph_launch(etale_search_graph *g, void *stream) {
+    if (!g) return ETALE_EINVAL;
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return g->idx->cuda_fail(e, "graph launch");
+    g_kernel_launches += 3;
+    if (g->idx->concurrent) {
+        std::lock_guard<std::mutex> lk(g->idx->mu);
+        CK2(g->idx, cudaEventRecord(g->idx->search_ev, (cudaStream_t)stream), "record search event");
+        g->idx->search_ev_valid = true;
+    }
+    return ETALE_OK;
+}
+
+etale_status etale_search_graph_check(etale_search_graph *g, void *stream) {
+    if (!g) return ETALE_EINVAL;
+    return check_search_errors(g->idx, (cudaStream_t)stream);
+}
+
+etale_status etale_search_graph_destroy(etale_search_graph *g) {
+    if (!g) return ETALE_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    cudaFree(g->qpad);
+    cudaFree(g->seed);
+    delete g;
+    return ETALE_OK;
+}
 
 etale_status etale_set_concurrent(etale_index *idx, int on) {
     if (!idx) return ETALE_EINVAL;

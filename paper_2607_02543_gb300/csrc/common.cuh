@@ -98,6 +98,8 @@ struct Dev {
     u32 *retired;      // P
     u64 *ctr;          // C_NCTR counters
     u32 *entries;      // n_entry
+    const u32 *nent_dev;  // current |E| in device memory (read by query kernels,
+                          // so a captured graph follows later updates)
     u32 dim, mp, R, metric;
     float alpha2;
     u32 n_entries;

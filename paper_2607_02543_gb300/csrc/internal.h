@@ -14,13 +14,14 @@ struct SearchTuning {
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
 // seed_kernel: top-L of the entry set per query into `seed` (nq x L); it
 // must precede the search launch that reads `seed`.
-cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec = 0);
+cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec = 0,
+                        const u32 *nq_dev = nullptr);
 // prec: 0 fp32, 1 bf16 copy, 2 fp8 copy (query mode only; the best
 // min(rerank * k, 64) live candidates are re-scored in canonical fp32).
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec = 0,
-                          u32 rerank = 4);
+                          u32 rerank = 4, const u32 *nq_dev = nullptr);
 
 // Offer lists: a payload index p names (src[p], rho[p]); key[p] is the target
 // id or `invalid` (= capacity) for an empty slot.
@@ -36,8 +37,10 @@ struct Offers {
 cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
                                 u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
                                 const Offers &of, int num_sms, cudaStream_t st);
+// lock-free (budget > 0): offer slots [lo, hi) only
 cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
-                              u32 lockfree_budget, int num_sms, cudaStream_t st);
+                              u32 lockfree_budget, int num_sms, cudaStream_t st, u32 lo = 0,
+                              u32 hi = 0xFFFFFFFFu);
 cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
                           int num_sms, cudaStream_t st);
 cudaError_t launch_tombstone(const Dev &d, const u32 *sorted_ids, u32 n, u64 next_id, u32 *ok_flags,
@@ -45,10 +48,11 @@ cudaError_t launch_tombstone(const Dev &d, const u32 *sorted_ids, u32 n, u64 nex
 cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
                             u32 *pair_val, uint2 *pair_K, u32 *pair_Kn, int num_sms, cudaStream_t st);
 // budget == 0: deterministic, one warp per segment of equal targets;
-// budget > 0: lock-free, one warp per pair slot (n_pairs slots).
+// budget > 0: lock-free, one warp per pair slot, slots [lo, lo + n_pairs).
 cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key, const u32 *pair_val,
                                const uint2 *pair_K, const u32 *pair_Kn, const u32 *seg_start,
-                               const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st);
+                               const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st,
+                               u64 lo = 0);
 cudaError_t launch_compact(const Dev &d, u64 next_id, const u32 *tomb_bits, cudaStream_t st);
 cudaError_t launch_reclaim_tombstones(const Dev &d, u64 next_id, cudaStream_t st);
 
@@ -79,7 +83,9 @@ cudaError_t make_segments(const u32 *key, u32 n, u32 invalid, u32 *flags, u32 *s
                           u32 *seg_start, u64 *seg_count, const ScanScratch &s, cudaStream_t st);
 
 cudaError_t launch_recycle(const Dev &d, cudaStream_t st);
-cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st);
+// n_dev (optional): row count read on the device, n is its cap.
+cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st,
+                          const u32 *n_dev = nullptr);
 cudaError_t launch_ingest_copies(const Dev &d, u64 first, u64 n, cudaStream_t st);
 cudaError_t launch_live_flags(const Dev &d, u64 next_id, u32 *flags, cudaStream_t st);
 cudaError_t launch_entries_select(const Dev &d, u64 next_id, const u32 *flags, const u32 *rank, u64 live,
@@ -92,5 +98,7 @@ cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 n
 cudaError_t launch_export(const Dev &d, u64 n, unsigned char *del, unsigned char *hs, unsigned char *deg,
                           u32 *ids, float *rho, cudaStream_t st);
 cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaStream_t st);
+// *p = v, stream-ordered (a kernel, so no host buffer must outlive the call)
+cudaError_t launch_set_u32(u32 *p, u32 v, cudaStream_t st);
 
 }  // namespace etale

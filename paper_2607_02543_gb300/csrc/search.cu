@@ -26,6 +26,7 @@ struct SearchArgs {
     Dev d;
     const float *q;      // query rows, stride mp floats, 16-byte aligned
     const u64 *seed;     // nq x L initial beams (top-L of the entry set), KEY_INF padded
+    const u32 *nq_dev;   // when set, the batch size is read here (CUDA graphs); nq is its cap
     u32 nq, L, max_hops, mode;   // mode 0: query, 1: insert
     u32 k;
     u32 *out_ids;
@@ -286,6 +287,7 @@ constexpr int SEED_TILE = 32;
 struct SeedArgs {
     Dev d;
     const float *q;
+    const u32 *nq_dev;   // when set, the batch size is read here; nq is its cap
     u32 nq, L;
     u64 *seed;
     u32 rowb;   // bytes per entry row in the tile (fp32 row or its copy)
@@ -347,12 +349,13 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     u64 *bk1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     u64 *nk = reinterpret_cast<u64 *>(p);
     const u32 qi = blockIdx.x * 8 + warp;
-    const bool active = qi < a.nq;
+    const u32 nq = a.nq_dev ? min(*a.nq_dev, a.nq) : a.nq;
+    const bool active = qi < nq;
     if (active)
         for (u32 i = lane * 4; i < mp; i += 128)
             *reinterpret_cast<float4 *>(qv + i) = *reinterpret_cast<const float4 *>(a.q + (size_t)qi * mp + i);
     const int grp = lane >> 3, g = lane & 7;
-    const u32 S = d.n_entries;
+    const u32 S = d.nent_dev ? *d.nent_dev : d.n_entries;
     int n = 0;
     for (u32 t0 = 0; t0 < S; t0 += SEED_TILE) {
         const int nt = (int)min((u32)SEED_TILE, S - t0);
@@ -399,11 +402,12 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
     u32 phase = 0;
     u64 nexp_tot = 0, ndist = 0;
     bool timeout = false;
+    const u32 nq = a.nq_dev ? min(*a.nq_dev, a.nq) : a.nq;
     for (;;) {
         u32 qi = 0;
         if (lane == 0) qi = (u32)atomicAdd(&d.ctr[a.wq], 1ull);
         qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= a.nq) break;
+        if (qi >= nq) break;
         const float *qrow = a.q + (size_t)qi * mp;
         for (u32 i = lane * 4; i < mp; i += 128)
             *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
@@ -411,7 +415,7 @@ __global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
         __syncwarp();
         // initial beam: the L nearest members of the entry set E, computed by
         // seed_kernel; the reference words are sampled here
-        const int n0 = (int)min(a.L, d.n_entries);
+        const int n0 = (int)min(a.L, d.nent_dev ? *d.nent_dev : d.n_entries);
         for (int i = lane; i < n0; i += 32) {
             const u64 k = a.seed[(size_t)qi * a.L + i];
             const u32 id = key_id(k);
@@ -549,11 +553,12 @@ size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
     return 4 * search_warp_bytes(mp, L, stage_rows, seen_slots, mp * 4);
 }
 
-cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec) {
-    if (nq == 0 || d.n_entries == 0) return cudaSuccess;
+cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec,
+                        const u32 *nq_dev) {
+    if (nq == 0 || (d.n_entries == 0 && !d.nent_dev)) return cudaSuccess;
     if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
     const u32 rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
-    SeedArgs a{d, q, nq, L, seed, rowb};
+    SeedArgs a{d, q, nq_dev, nq, L, seed, rowb};
     const void *fn = prec == 1 ? (const void *)seed_kernel<1> : prec == 2 ? (const void *)seed_kernel<2>
                                                                           : (const void *)seed_kernel<0>;
     size_t smem = align_up((size_t)SEED_TILE * rowb, 16) + 8 * seed_warp_bytes(d.mp, L);
@@ -568,12 +573,14 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
 
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
-                          const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec, u32 rerank) {
+                          const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec, u32 rerank,
+                          const u32 *nq_dev) {
     if (nq == 0) return cudaSuccess;
     if (mode != 0) prec = 0;
     if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
     SearchArgs a;
-    a.d = d; a.q = q; a.seed = seed; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode; a.k = k;
+    a.d = d; a.q = q; a.seed = seed; a.nq_dev = nq_dev; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode;
+    a.k = k;
     a.out_ids = out_ids; a.out_dist = out_dist; a.exp_keys = exp_keys; a.exp_count = exp_count;
     a.stage_rows = tune.stage_rows;
     a.seen_bits = tune.seen_bits;

@@ -484,6 +484,7 @@ struct FoldArgs {
     const u64 *seg_count;
     u32 budget;   // 0 = deterministic
     u32 np, ns, gram;
+    u32 lo, hi;   // lock-free: offer slots [lo, hi) of this launch
 };
 
 __host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
     u32 *idx = reinterpret_cast<u32 *>(p);
-    const u64 nwork = a.budget ? (u64)a.of.n : *a.seg_count;
+    const u64 nwork = a.budget ? (u64)(a.hi - a.lo) : *a.seg_count;
     for (;;) {
         u64 t = 0;
         if (lane == 0) t = atomicAdd(&d.ctr[C_WORK], 1ull);
@@ -534,6 +535,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
                 if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
+            t += a.lo;
             const u32 w = a.of.key[t];
             if (w >= (u32)d.capacity) continue;
             const u32 v = a.of.src[t];
@@ -559,9 +561,11 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
 }
 
 cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
-                              u32 budget, int num_sms, cudaStream_t st) {
+                              u32 budget, int num_sms, cudaStream_t st, u32 lo, u32 hi) {
     if (of.n == 0) return cudaSuccess;
-    FoldArgs a{d, of, seg_start, seg_count, budget, 0, 0, d.gram};
+    if (budget && hi > of.n) hi = of.n;
+    if (budget && lo >= hi) return cudaSuccess;
+    FoldArgs a{d, of, seg_start, seg_count, budget, 0, 0, d.gram, lo, budget ? hi : of.n};
     u32 np = 32;
     while (np < d.R + 1) np <<= 1;
     a.np = np;
@@ -575,7 +579,8 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, offer_fold_kernel, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    u32 blocks = (u32)(per_sm * num_sms), need = (of.n + W - 1) / W;
+    const u32 items = budget ? a.hi - a.lo : of.n;
+    u32 blocks = (u32)(per_sm * num_sms), need = (items + W - 1) / W;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
@@ -944,6 +949,7 @@ struct RepairFoldArgs {
     const u64 *seg_count;
     u64 n_pairs;
     u32 budget, np, ns, gram;
+    u64 lo;       // lock-free: pair slots [lo, lo + n_pairs) of this launch
 };
 
 __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
@@ -1017,6 +1023,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
                 if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
+            t += a.lo;
             const u32 w = a.pair_key[t];
             if (w >= (u32)d.capacity) continue;
             const u32 pv = a.pair_val[t];
@@ -1043,9 +1050,11 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
 
 cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key, const u32 *pair_val,
                                     const uint2 *pair_K, const u32 *pair_Kn, const u32 *seg_start,
-                                    const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st) {
+                                    const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st,
+                               u64 lo) {
     if (n_pairs == 0) return cudaSuccess;
-    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0, 0, d.gram};
+    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0, 0, d.gram,
+                     lo};
     u32 np = 32;
     while (np < 2 * d.R) np <<= 1;
     a.np = np;

@@ -254,8 +254,9 @@ cudaError_t launch_recycle(const Dev &d, cudaStream_t st) {
 }
 
 // Copy n rows of dim floats into rows of mp floats, zero padding.
-__global__ void ingest_kernel(float *x, u32 mp, const float *src, u32 dim, u64 n) {
+__global__ void ingest_kernel(float *x, u32 mp, const float *src, u32 dim, u64 n, const u32 *n_dev) {
     const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n_dev) n = min(n, (u64)*n_dev);
     if (i >= n * mp) return;
     const u64 r = i / mp, c = i % mp;
     x[i] = c < dim ? src[r * dim + c] : 0.0f;
@@ -295,10 +296,10 @@ cudaError_t launch_ingest_copies(const Dev &d, u64 first, u64 n, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st) {
+cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st, const u32 *n_dev) {
     if (n == 0) return cudaSuccess;
     const u64 tot = n * mp;
-    ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, mp, src, dim, n);
+    ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, mp, src, dim, n, n_dev);
     return cudaGetLastError();
 }
 
@@ -370,6 +371,13 @@ __global__ void fill_keys_kernel(u32 *key, u32 *val, u32 n, u32 invalid) {
     if (i >= n) return;
     key[i] = invalid;
     val[i] = i;
+}
+
+__global__ void set_u32_kernel(u32 *p, u32 v) { *p = v; }
+
+cudaError_t launch_set_u32(u32 *p, u32 v, cudaStream_t st) {
+    set_u32_kernel<<<1, 1, 0, st>>>(p, v);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaStream_t st) {

@@ -1,0 +1,67 @@
+"""Launch-shape tuning and CUDA-graph query batches (persistent-round row of
+the hot path): results must not depend on the launch shape, and one captured
+graph must answer every batch size exactly as etale_search does, also after
+the index has been updated."""
+import numpy as np
+import pytest
+
+from paper_2607_02543_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def index():
+    import torch
+    from paper_2607_02543_gb300 import Index, build
+    build.build()
+    w = W.scaled(W.SMALL, 6000, n_queries=1000, rounds=1)
+    plan = W.make_plan(w)
+    g = Index(w.dim, w.metric, w.degree, w.capacity + 1000, build_beam=48, mode="lockfree")
+    g.insert(plan.base)
+    g.reclaim()
+    return g, w, plan, torch.device("cuda", 0)
+
+
+def test_launch_shapes_do_not_change_results(index):
+    import torch
+    g, w, plan, dev = index
+    q = torch.from_numpy(plan.queries).to(dev)
+    ref = g.search(q, 10, 64)
+    for rows, bits in [(8, 8), (16, 9), (32, 11), (4, 12)]:
+        g.set_search_tuning(rows, bits)
+        ids, d = g.search(q, 10, 64)
+        assert torch.equal(ids, ref[0]) and torch.equal(d, ref[1]), (rows, bits)
+    tried = g.autotune_search(q, 10, 64)
+    assert len(tried) >= 6 and all(ms > 0 for *_, ms in tried)
+    ids, d = g.search(q, 10, 64)
+    assert torch.equal(ids, ref[0]) and torch.equal(d, ref[1])
+
+
+def test_one_graph_serves_every_batch_size(index):
+    import torch
+    g, w, plan, dev = index
+    nq_max, k, beam = 512, 10, 64
+    qbuf = torch.zeros((nq_max, w.dim), dtype=torch.float32, device=dev)
+    oid = torch.empty((nq_max, k), dtype=torch.int32, device=dev)
+    od = torch.empty((nq_max, k), dtype=torch.float32, device=dev)
+    nq = torch.zeros(1, dtype=torch.int32, device=dev)
+    graph = g.search_graph(qbuf, oid, od, nq, k, beam)
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(9)
+    for rnd in range(2):
+        for n in (1, 7, 300, 512):
+            sel = rng.choice(plan.queries.shape[0], n, replace=False)
+            qbuf[:n] = torch.from_numpy(plan.queries[sel]).to(dev)
+            nq.fill_(n)
+            torch.cuda.synchronize()
+            graph.launch(stream)
+            graph.check(stream)
+            ref_ids, ref_d = g.search(plan.queries[sel], k, beam)
+            assert (oid[:n].cpu().numpy().view(np.uint32) == ref_ids).all()
+            assert np.array_equal(od[:n].cpu().numpy(), ref_d)
+        # update the index (the entry set changes); the same graph follows
+        g.delete(np.arange(0, 6000, 5, dtype=np.uint32))
+        g.insert(W.Mixture(w).draw("inserts", 300))
+        g.reclaim()
+    graph.close()
