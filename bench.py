@@ -172,6 +172,16 @@ def config_dict(w, args):
                   "small index; no flush", "parallelism": f"replicas x{args.gpus}"}
 
 
+def reduce_max(vals, world: int, device) -> list:
+    """Element-wise maximum over ranks (identity on one rank)."""
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -329,10 +339,7 @@ def main():
                "d2h_bytes_per_step": int(w.n_insert * 4 + 8 + w.n_queries * w.k * 8),
                "qps": w.n_queries / (e2e_search * 1e-3)}
     # max over ranks
-    vals = torch.tensor([ms_round, ms_search], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_round, ms_search = float(vals[0]), float(vals[1])
+    ms_round, ms_search = reduce_max([ms_round, ms_search], world, dev)
     st = idx.stats()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

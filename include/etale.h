@@ -125,7 +125,9 @@ etale_status etale_destroy(etale_index *idx);
  * min(remaining, max(1, live), max_batch); each sub-batch is one round:
  * all members search the graph as it was before the sub-batch, prune, publish
  * their own slabs, then offer reverse edges.  ECAPACITY if next_id + n
- * exceeds capacity (index unchanged).                                      */
+ * exceeds capacity; ENOMEM if the free slab pool cannot hold one phase of
+ * the largest sub-batch, (R + 1) * min(n, max_batch) slabs; in both cases
+ * the index is unchanged.                                                   */
 etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n,
                           uint32_t *out_ids, void *stream);
 
@@ -226,6 +228,15 @@ etale_status etale_search_graph_launch(etale_search_graph *g, void *stream);
 /* Synchronise `stream` and report device-side errors of earlier replays.    */
 etale_status etale_search_graph_check(etale_search_graph *g, void *stream);
 etale_status etale_search_graph_destroy(etale_search_graph *g);
+
+/* Failure-detection self-test (diagnostic; the paper has no counterpart).
+ * Launches one warp whose mbarrier wait can never complete (it expects 16
+ * bytes that no copy delivers; no copy is issued), polled at most
+ * `poll_limit` times.  The wait gives up, the kernel records ETALE_ETIMEOUT
+ * in its status word and returns, and the call returns ETALE_ETIMEOUT with
+ * the CUDA context still usable.  Every bounded wait of the library ends
+ * the same way.  poll_limit must be 1..1e6.                                 */
+etale_status etale_selftest_bounded_wait(uint32_t poll_limit, void *stream);
 
 /* Concurrent mode (off by default).  With it on, one thread may run query
  * searches (etale_search / etale_search_static) on one stream while another

@@ -54,7 +54,8 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static",
            "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent",
            "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
-           "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy"]
+           "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
+           "etale_selftest_bounded_wait"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
@@ -99,12 +100,18 @@ def load(path: str = LIB_PATH):
             "etale_search_graph_launch": ([P, P], C.c_int),
             "etale_search_graph_check": ([P, P], C.c_int),
             "etale_search_graph_destroy": ([P], C.c_int),
+            "etale_selftest_bounded_wait": ([U32, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
             f.argtypes, f.restype = args, res
         _lib = lib
         return lib
+
+
+def selftest_bounded_wait(poll_limit: int = 1000, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status code (5 = ETIMEOUT)."""
+    return int(load().etale_selftest_bounded_wait(poll_limit, _stream(stream)))
 
 
 def _ptr(a):

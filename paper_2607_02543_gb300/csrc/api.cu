@@ -651,6 +651,14 @@ etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n, uint3
     cudaStream_t st = (cudaStream_t)stream;
     etale_status s = writer_begin(idx, st);
     if (s != ETALE_OK) return s;
+    {
+        // before any change: the largest phase of the largest sub-batch must
+        // fit the pool (each insert publishes at most 1 + R times per phase)
+        const u64 b = std::min<u64>(n, idx->cfg.max_batch);
+        s = ensure_pool(idx, b * (idx->R + 1), st);
+        if (s != ETALE_OK) return s;
+        idx->free_lb += b * (idx->R + 1);
+    }
     const void *src = nullptr;
     s = StreamCopy::in(idx, idx->stage, vecs, (size_t)n * idx->dim * 4, &src, st);
     if (s != ETALE_OK) return s;
@@ -1105,6 +1113,30 @@ etale_status etale_search_graph_destroy(etale_search_graph *g) {
     cudaFree(g->qpad);
     cudaFree(g->seed);
     delete g;
+    return ETALE_OK;
+}
+
+etale_status etale_selftest_bounded_wait(uint32_t poll_limit, void *stream) {
+    if (poll_limit < 1 || poll_limit > 1000000) {
+        t_last_error = "poll_limit must be 1..1e6";
+        return ETALE_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    u32 *status = nullptr, h = 0;
+    cudaError_t e = cudaMalloc(&status, 4);
+    if (e == cudaSuccess) e = launch_selftest_wait(poll_limit, status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (status) cudaFree(status);
+    if (e != cudaSuccess) {
+        t_last_error = std::string("selftest: ") + cudaGetErrorString(e);
+        return ETALE_ECUDA;
+    }
+    g_kernel_launches++;
+    if (h & ERR_TIMEOUT) {
+        t_last_error = "a bounded device wait gave up (self-test)";
+        return ETALE_ETIMEOUT;
+    }
     return ETALE_OK;
 }
 

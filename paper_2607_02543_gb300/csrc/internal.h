@@ -98,6 +98,7 @@ cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 n
 cudaError_t launch_export(const Dev &d, u64 n, unsigned char *del, unsigned char *hs, unsigned char *deg,
                           u32 *ids, float *rho, cudaStream_t st);
 cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaStream_t st);
+cudaError_t launch_selftest_wait(u32 limit, u32 *status, cudaStream_t st);
 // *p = v, stream-ordered (a kernel, so no host buffer must outlive the call)
 cudaError_t launch_set_u32(u32 *p, u32 v, cudaStream_t st);
 

@@ -375,6 +375,24 @@ __global__ void fill_keys_kernel(u32 *key, u32 *val, u32 n, u32 invalid) {
 
 __global__ void set_u32_kernel(u32 *p, u32 v) { *p = v; }
 
+// One warp waits on an mbarrier phase that needs 16 transaction bytes no
+// copy will deliver; the bounded wait gives up and the status is recorded.
+__global__ void selftest_wait_kernel(u32 limit, u32 *status) {
+    __shared__ __align__(8) u64 bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, 16);
+    }
+    __syncwarp();
+    const bool done = mbar_wait(&bar, 0, limit);
+    if (threadIdx.x == 0) *status = done ? 0u : (u32)ERR_TIMEOUT;
+}
+
+cudaError_t launch_selftest_wait(u32 limit, u32 *status, cudaStream_t st) {
+    selftest_wait_kernel<<<1, 32, 0, st>>>(limit, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_u32(u32 *p, u32 v, cudaStream_t st) {
     set_u32_kernel<<<1, 1, 0, st>>>(p, v);
     return cudaGetLastError();
