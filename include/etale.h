@@ -80,7 +80,10 @@ typedef struct {
     uint32_t rerank;      /* reduced-precision query search re-scores its
                              rerank * k best live candidates in exact fp32;
                              default 4, at most 64 / k candidates used      */
-    uint32_t reserved[2];
+    uint32_t gt;          /* etale_ground_truth: 0 default (tensor-core
+                             candidate pass with an exact certified rerank
+                             where it applies), 1 CUDA cores only            */
+    uint32_t reserved[1];
 } etale_config;
 
 typedef enum { ETALE_PREC_FP32 = 0, ETALE_PREC_BF16 = 1, ETALE_PREC_FP8 = 2 } etale_precision;
@@ -167,7 +170,12 @@ etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, u
                           uint32_t beam, uint32_t *out_ids, float *out_dists, void *stream);
 
 /* Exact k nearest live nodes by brute force (measurement support for
- * Recall@10, Sec. 5.2): canonical fp32 distances, ties by smaller id.       */
+ * Recall@10, Sec. 5.2): canonical fp32 distances, ties by smaller id.  k must
+ * be 1..32.  Unless cfg.gt = 1, a tensor-core pass (bf16 inputs, fp32
+ * accumulation; a hi/lo split when the data are not exact in bf16) keeps 32
+ * candidates per query, which are reranked with the canonical distance; a
+ * query whose result an a-priori error bound cannot certify is recomputed
+ * on CUDA cores, so the output never depends on the path taken.            */
 etale_status etale_ground_truth(etale_index *idx, const float *queries, uint64_t nq,
                                 uint32_t k, uint32_t *out_ids, float *out_dists, void *stream);
 
@@ -228,6 +236,11 @@ etale_status etale_search_graph_launch(etale_search_graph *g, void *stream);
 /* Synchronise `stream` and report device-side errors of earlier replays.    */
 etale_status etale_search_graph_check(etale_search_graph *g, void *stream);
 etale_status etale_search_graph_destroy(etale_search_graph *g);
+
+/* How the last etale_ground_truth call ran: *path 0 CUDA cores, 1 tensor
+ * cores on bf16-exact data, 2 tensor cores with the hi/lo split;
+ * *fallback_queries = queries recomputed on CUDA cores.  Diagnostic.        */
+etale_status etale_ground_truth_info(etale_index *idx, uint32_t *path, uint64_t *fallback_queries);
 
 /* Failure-detection self-test (diagnostic; the paper has no counterpart).
  * Launches one warp whose mbarrier wait can never complete (it expects 16

@@ -32,7 +32,8 @@ class Config(C.Structure):
                 ("max_cand", C.c_uint32), ("refine", C.c_uint32), ("max_batch", C.c_uint64),
                 ("pool_slabs", C.c_uint64), ("n_entry", C.c_uint32), ("mode", C.c_uint32),
                 ("cas_budget", C.c_uint32), ("stage_kb", C.c_uint32), ("gram", C.c_uint32),
-                ("copies", C.c_uint32), ("rerank", C.c_uint32), ("reserved", C.c_uint32 * 2)]
+                ("copies", C.c_uint32), ("rerank", C.c_uint32), ("gt", C.c_uint32),
+                ("reserved", C.c_uint32 * 1)]
 
 
 class Tuning(C.Structure):
@@ -55,7 +56,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent",
            "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
-           "etale_selftest_bounded_wait"]
+           "etale_selftest_bounded_wait", "etale_ground_truth_info"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
 
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
             "etale_search_graph_check": ([P, P], C.c_int),
             "etale_search_graph_destroy": ([P], C.c_int),
             "etale_selftest_bounded_wait": ([U32, P], C.c_int),
+            "etale_ground_truth_info": ([P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -140,7 +142,7 @@ class Index:
                  alpha: float = 0.0, max_hops: int = 0, max_cand: int = 0, refine: str = "default",
                  max_batch: int = 0, pool_slabs: int = 0, n_entry: int = 0, mode: str = "deterministic",
                  cas_budget: int = 0, stage_kb: int = 0, gram: str = "default", copies: tuple = (),
-                 rerank: int = 0):
+                 rerank: int = 0, gt: str = "default"):
         self.lib = load()
         cfg = Config()
         self.lib.etale_config_default(C.byref(cfg))
@@ -158,6 +160,7 @@ class Index:
             cfg.cas_budget = cas_budget
         cfg.stage_kb = stage_kb
         cfg.gram = {"default": 0, "canonical": 1, "tensor": 2}[gram]
+        cfg.gt = {"default": 0, "cuda_cores": 1}[gt]
         cfg.copies = (1 if "bf16" in copies else 0) | (2 if "fp8" in copies else 0)
         if rerank:
             cfg.rerank = rerank
@@ -272,6 +275,14 @@ class Index:
         self._check(self.lib.etale_ground_truth(self.h, _ptr(queries), queries.shape[0], k, _ptr(ids),
                                                 _ptr(dist), _stream(stream)))
         return ids, dist
+
+    def ground_truth_info(self) -> dict:
+        """How the last ground_truth call ran: path "cuda_cores", "tensor" or
+        "tensor_split", and the number of queries recomputed on CUDA cores."""
+        path = C.c_uint32()
+        fb = C.c_uint64()
+        self._check(self.lib.etale_ground_truth_info(self.h, C.byref(path), C.byref(fb)))
+        return {"path": ("cuda_cores", "tensor", "tensor_split")[path.value], "fallback_queries": fb.value}
 
     # --- introspection -----------------------------------------------------
     def export_graph(self, n: int | None = None):

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libetale.so")
-SOURCES = ["api.cu", "search.cu", "update.cu", "util.cu"]
+SOURCES = ["api.cu", "search.cu", "update.cu", "util.cu", "gt_tc.cu"]
 HEADERS = ["common.cuh", "internal.h", os.path.join("..", "..", "include", "etale.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

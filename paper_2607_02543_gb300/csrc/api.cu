@@ -95,6 +95,10 @@ struct etale_index {
     // query-search scratch, separate from the writer's so that one search
     // call and one update call can run at the same time (concurrent mode)
     DevBuf s_stage, s_qpad, s_out_ids, s_out_dist, s_seed;
+    // ground truth on tensor cores
+    DevBuf gt_A, gt_B, gt_xn, gt_qstat, gt_gstat, gt_thr, gt_fb, gt_lists;
+    u32 gt_path = 0;
+    u64 gt_fallbacks = 0;
     u64 *host_ctr_s = nullptr;        // pinned, search side
     u64 *host_ctr_st = nullptr;       // pinned, etale_stats
     cudaStream_t stat_stream = nullptr;
@@ -835,6 +839,59 @@ etale_status etale_reclaim(etale_index *idx, void *stream) {
     return s;
 }
 
+// Tensor-core candidate pass + certified exact rerank; queries it cannot
+// certify, and shapes it does not cover, run on the CUDA-core exact kernel.
+static etale_status ground_truth_run(etale_index *idx, const Dev &d, const float *qpad, u32 nq, u32 k, u32 *oid,
+                                     float *od, cudaStream_t st) {
+    idx->gt_path = 0;
+    idx->gt_fallbacks = 0;
+    GtTcPlan p = gt_tc_plan(idx->dim, idx->next_id, nq);
+    if (idx->cfg.gt == 1 || p.n_pad == 0) {
+        CK(launch_ground_truth(d, idx->next_id, qpad, nq, k, oid, od, idx->num_sms, st), "ground truth");
+        g_kernel_launches++;
+        return ETALE_OK;
+    }
+    if (!grow(idx->gt_A, p.bytes_A) || !grow(idx->gt_B, p.bytes_B) || !grow(idx->gt_xn, p.n_pad * 4) ||
+        !grow(idx->gt_qstat, (size_t)nq * 16) || !grow(idx->gt_gstat, 64) || !grow(idx->gt_thr, (size_t)nq * 4) ||
+        !grow(idx->gt_fb, (size_t)nq * 4))
+        return idx->fail(ETALE_ENOMEM, "ground-truth staging");
+    GtTcBufs b{};
+    b.A = idx->gt_A.p;
+    b.B = idx->gt_B.p;
+    b.xn = as<float>(idx->gt_xn);
+    b.qstat = as<float>(idx->gt_qstat);
+    b.gstat = as<u32>(idx->gt_gstat);
+    b.thr = as<u32>(idx->gt_thr);
+    b.fb = as<u32>(idx->gt_fb);
+    b.err = b.gstat + 5;
+    CK(launch_gt_tc_prep(d, idx->next_id, qpad, nq, p, b, st), "ground-truth copies");
+    g_kernel_launches += 2;
+    u32 h[8];
+    CK(cudaMemcpyAsync(h, b.gstat, sizeof h, cudaMemcpyDeviceToHost, st), "read split flag");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    gt_tc_configure(p, nq, h[3] != 0, idx->num_sms);
+    if (!p.usable) {
+        CK(launch_ground_truth(d, idx->next_id, qpad, nq, k, oid, od, idx->num_sms, st), "ground truth");
+        g_kernel_launches++;
+        return ETALE_OK;
+    }
+    if (!grow(idx->gt_lists, p.bytes_lists)) return idx->fail(ETALE_ENOMEM, "ground-truth candidate lists");
+    b.lists = as<u64>(idx->gt_lists);
+    CK(launch_gt_tc(d, qpad, nq, k, p, b, idx->next_id, oid, od, idx->num_sms, st), "ground truth (tensor)");
+    g_kernel_launches += 2;
+    CK(cudaMemcpyAsync(h, b.gstat, sizeof h, cudaMemcpyDeviceToHost, st), "read fallback count");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (h[5] & ERR_TIMEOUT) return idx->fail(ETALE_ETIMEOUT, "ground truth: a bounded device wait gave up");
+    idx->gt_path = p.split ? 2 : 1;
+    idx->gt_fallbacks = h[4];
+    if (h[4]) {
+        CK(launch_ground_truth(d, idx->next_id, qpad, h[4], k, oid, od, idx->num_sms, st, b.fb),
+           "ground truth (fallback)");
+        g_kernel_launches++;
+    }
+    return ETALE_OK;
+}
+
 static etale_status search_common(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
                                   uint32_t *out_ids, float *out_dists, void *stream, bool exact) {
     if (!idx) return ETALE_EINVAL;
@@ -864,7 +921,8 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
     Dev d = idx->dev();
     const bool prof = idx->prof && !idx->concurrent;
     if (exact) {
-        CK(launch_ground_truth(d, idx->next_id, qpad, (u32)nq, k, oid, od, idx->num_sms, st), "ground truth");
+        s = ground_truth_run(idx, d, qpad, (u32)nq, k, oid, od, st);
+        if (s != ETALE_OK) return s;
     } else {
         const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
         if (!grow(idx->s_seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
@@ -882,8 +940,9 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
             CK(cudaEventRecord(idx->search_ev, st), "record search event");
             idx->search_ev_valid = true;
         }
+        g_kernel_launches++;   // seed
     }
-    g_kernel_launches += 2;
+    g_kernel_launches++;       // query ingest
     if (!dev_out) {
         CK(cudaMemcpyAsync(out_ids, oid, nq * k * 4, cudaMemcpyDeviceToHost, st), "copy ids out");
         CK(cudaMemcpyAsync(out_dists, od, nq * k * 4, cudaMemcpyDeviceToHost, st), "copy dists out");
@@ -1113,6 +1172,13 @@ etale_status etale_search_graph_destroy(etale_search_graph *g) {
     cudaFree(g->qpad);
     cudaFree(g->seed);
     delete g;
+    return ETALE_OK;
+}
+
+etale_status etale_ground_truth_info(etale_index *idx, uint32_t *path, uint64_t *fallback_queries) {
+    if (!idx) return ETALE_EINVAL;
+    if (path) *path = idx->gt_path;
+    if (fallback_queries) *fallback_queries = idx->gt_fallbacks;
     return ETALE_OK;
 }
 

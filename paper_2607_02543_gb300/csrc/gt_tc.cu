@@ -1,0 +1,650 @@
+// Exact k nearest live nodes with a tensor-core candidate pass.
+//
+// Recall@10 (Sec. 5.2) needs the exact top-k over the live set; for the
+// 1M x 128 churn workload that is a 10k x 1M x 128 dense contraction per
+// round.  The contraction runs on the 5th-generation tensor cores:
+//
+//   1. gt_prep_rows / gt_prep_queries write bf16 copies of the live rows and
+//      the queries (x = hi + lo + e with hi, lo bf16; rows as [hi | lo | hi],
+//      queries as [hi | hi | lo], each segment padded to 64) and the norms an
+//      error bound needs.  When every lo is zero (data exactly
+//      representable in bf16, e.g. integers up to 256) only the first
+//      segment is used, otherwise all three (hi.hi + hi.lo + lo.hi).
+//   2. gt_tc_kernel: persistent CTAs; TMA (cp.async.bulk.tensor, 128-byte
+//      swizzle) streams 128-row boxes of the row copy through a shared
+//      memory ring while the query tile stays resident; one thread issues
+//      tcgen05.mma (M = N = 128, bf16 -> fp32) into a double-buffered TMEM
+//      accumulator; eight epilogue warps read it with tcgen05.ld and keep,
+//      per query and per chunk of rows, the 32 smallest approximate keys
+//      key = |x|^2 - 2 q.x (L2) or -q.x (IP), pruned by a per-query
+//      threshold shared through global memory.
+//   3. gt_merge_kernel: per query, the union of its chunk lists is cut to 32
+//      candidates, reranked with the canonical fp32 distance (the same
+//      definition the rest of the index uses), and certified: every item
+//      left out has an approximate key >= LB, and an a-priori bound E on
+//      |approximate - canonical| shows that no such item can beat the k-th
+//      reranked distance.  Queries that fail the certificate are recomputed
+//      by the CUDA-core exact kernel, so the result is always the exact
+//      top-k with canonical distances, ties by smaller id.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace etale {
+namespace {
+
+constexpr int TC_ROWS = 128;                      // MMA M (queries) and N (rows)
+constexpr int TC_KBOX = 64;                       // bf16 per 128-byte swizzle row
+constexpr u32 TC_BOX = TC_ROWS * TC_KBOX * 2;     // 16 KB per TMA box
+constexpr int TC_T = 32;                          // candidates per (query, chunk)
+constexpr int TC_MAX_STAGES = 12;
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;
+constexpr u32 ORD_INF = 0xFF800000u;              // f2ord(+inf)
+// kind::f16 instruction descriptor: fp32 accumulator (bits 4-5 = 1), A and B
+// bf16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24
+constexpr u32 TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(TC_ROWS >> 3) << 17) |
+                         ((u32)(TC_ROWS >> 4) << 24);
+
+struct TcArgs {
+    u32 nq, n_tiles, kblocks, n_msub, m_tiles, chunks, tiles_per_chunk, stages, tmem_cols;
+    float s;              // -2 (L2) or -1 (IP)
+    const float *xn;      // n_tiles * 128 key bases (+inf for dead rows and padding)
+    u32 *thr;             // nq ordered per-query thresholds
+    u64 *lists;           // nq x chunks x TC_T (ordered key << 32 | id), ascending
+    u32 *err;
+};
+
+// ---- PTX wrappers -----------------------------------------------------------
+__device__ __forceinline__ void mbar_arrive(u64 *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, u64 *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle
+// layout: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte
+// offset), descriptor version 1 (bit 46), swizzle mode 2 (bits 61-63).
+__device__ __forceinline__ u64 sw128_desc(u32 saddr) {
+    return (u64)((saddr & 0x3FFFFu) >> 4) | ((u64)1 << 16) | ((u64)(1024 >> 4) << 32) | ((u64)1 << 46) |
+           ((u64)2 << 61);
+}
+__device__ __forceinline__ void tc_mma(u32 d, u64 a, u64 b, u32 acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(u64 *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(u32 taddr, u32 (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Sorted (ascending) register list; requires k < lk[TC_T - 1].
+__device__ __forceinline__ void list_insert(float (&lk)[TC_T], u32 (&li)[TC_T], float k, u32 id) {
+    bool done = false;
+#pragma unroll
+    for (int j = TC_T - 1; j >= 0; --j) {
+        if (j > 0 && !done && k < lk[j - 1]) {
+            lk[j] = lk[j - 1];
+            li[j] = li[j - 1];
+        } else if (!done) {
+            lk[j] = k;
+            li[j] = id;
+            done = true;
+        }
+    }
+}
+
+// ---- candidate pass ---------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    extern __shared__ unsigned char tc_raw[];
+    __shared__ __align__(8) u64 full[TC_MAX_STAGES], empty[TC_MAX_STAGES];
+    __shared__ __align__(8) u64 a_full, a_empty, t_full[2], t_empty[2], drain;
+    __shared__ u32 tmem_base;
+    __shared__ volatile int abort_flag;
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = sm;
+    unsigned char *sB = sm + (size_t)a.n_msub * a.kblocks * TC_BOX;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const u32 items = a.m_tiles * a.chunks;
+
+    if (threadIdx.x == 0) {
+        for (u32 i = 0; i < a.stages; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&a_full, 1);
+        mbar_init(&a_empty, 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&t_full[b], 1);
+            mbar_init(&t_empty[b], 4 * a.n_msub);
+        }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const u32 tmem = tmem_base;
+
+    auto fail = [&]() {
+        abort_flag = 1;
+        atomicOr(a.err, ERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        // ---- producer: one thread issues every TMA load ----
+        if (lane == 0) {
+            u32 stage = 0, ph = 0, issued = 0, lastpar = 0, a_issued = 0, a_ph = 0;
+            bool first = true;
+            for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
+                const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
+                const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
+                if (!first) {
+                    if (!mbar_wait(&a_empty, a_ph, WAIT_LIMIT)) { fail(); break; }
+                    a_ph ^= 1;
+                }
+                first = false;
+                mbar_expect_tx(&a_full, a.n_msub * a.kblocks * TC_BOX);
+                for (u32 s = 0; s < a.n_msub; s++)
+                    for (u32 kb = 0; kb < a.kblocks; kb++)
+                        tma_load_2d(sA + (size_t)(s * a.kblocks + kb) * TC_BOX, &tmA, (int)(kb * TC_KBOX),
+                                    (int)((mt * a.n_msub + s) * TC_ROWS), &a_full);
+                a_issued++;
+                for (u32 t = t0; t < t1 && !abort_flag; t++) {
+                    for (u32 kb = 0; kb < a.kblocks; kb++) {
+                        if (!mbar_wait(&empty[stage], ph ^ 1, WAIT_LIMIT)) { fail(); break; }
+                        mbar_expect_tx(&full[stage], TC_BOX);
+                        tma_load_2d(sB + (size_t)stage * TC_BOX, &tmB, (int)(kb * TC_KBOX), (int)(t * TC_ROWS),
+                                    &full[stage]);
+                        issued |= 1u << stage;
+                        lastpar = (lastpar & ~(1u << stage)) | (ph << stage);
+                        if (++stage == a.stages) {
+                            stage = 0;
+                            ph ^= 1;
+                        }
+                    }
+                }
+            }
+            // every copy this thread issued has landed before the CTA exits
+            for (u32 i = 0; i < a.stages; i++)
+                if (issued >> i & 1) mbar_wait(&full[i], lastpar >> i & 1, WAIT_LIMIT);
+            if (a_issued) mbar_wait(&a_full, (a_issued - 1) & 1, WAIT_LIMIT);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: one thread ----
+        if (lane == 0) {
+            u32 stage = 0, ph = 0, a_ph = 0, tcount = 0;
+            for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
+                const u32 ch = it / a.m_tiles;
+                const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
+                if (!mbar_wait(&a_full, a_ph, WAIT_LIMIT)) { fail(); break; }
+                a_ph ^= 1;
+                tc_fence_after();
+                for (u32 t = t0; t < t1 && !abort_flag; t++, tcount++) {
+                    const u32 b = tcount & 1;
+                    if (!mbar_wait(&t_empty[b], ((tcount >> 1) & 1) ^ 1, WAIT_LIMIT)) { fail(); break; }
+                    tc_fence_after();
+                    bool ok = true;
+                    for (u32 kb = 0; kb < a.kblocks; kb++) {
+                        if (!mbar_wait(&full[stage], ph, WAIT_LIMIT)) { ok = false; break; }
+                        tc_fence_after();
+                        const u32 bb = smem_addr(sB + (size_t)stage * TC_BOX);
+#pragma unroll
+                        for (u32 k = 0; k < TC_KBOX / 16; k++) {
+                            const u64 bd = sw128_desc(bb + k * 32);
+                            for (u32 s = 0; s < a.n_msub; s++) {
+                                const u32 aa = smem_addr(sA + (size_t)(s * a.kblocks + kb) * TC_BOX) + k * 32;
+                                tc_mma(tmem + (b * a.n_msub + s) * TC_ROWS, sw128_desc(aa), bd, (kb | k) != 0);
+                            }
+                        }
+                        tc_commit(&empty[stage]);
+                        if (++stage == a.stages) {
+                            stage = 0;
+                            ph ^= 1;
+                        }
+                    }
+                    if (!ok) { fail(); break; }
+                    tc_commit(&t_full[b]);
+                }
+                tc_commit(&a_empty);
+            }
+            // all MMAs issued by this thread are complete before TMEM is freed
+            tc_commit(&drain);
+            mbar_wait(&drain, 0, WAIT_LIMIT);
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----
+        const int ew = warp - 2, ms = ew >> 2, quarter = warp & 3;
+        if ((u32)ms < a.n_msub) {
+            const int row = quarter * 32 + lane;
+            u32 tcount = 0;
+            for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
+                const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
+                const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
+                const u32 q = (mt * a.n_msub + ms) * TC_ROWS + row;
+                const bool valid = q < a.nq;
+                float lk[TC_T];
+                u32 li[TC_T];
+#pragma unroll
+                for (int j = 0; j < TC_T; j++) {
+                    lk[j] = __int_as_float(0x7f800000);
+                    li[j] = NIL;
+                }
+                float own_max = __int_as_float(0x7f800000), published = own_max;
+                bool ok = true;
+                for (u32 t = t0; t < t1; t++, tcount++) {
+                    const u32 b = tcount & 1;
+                    // every lane waits; the warp goes on together (tcgen05.ld is .sync.aligned)
+                    const bool got = !abort_flag && mbar_wait(&t_full[b], (tcount >> 1) & 1, WAIT_LIMIT);
+                    if (!__all_sync(FULL, got)) { ok = false; break; }
+                    tc_fence_after();
+                    const float thr_g = valid ? ord2f(*reinterpret_cast<volatile u32 *>(a.thr + q))
+                                              : __int_as_float(0xff800000);
+                    float thr = fminf(own_max, thr_g);
+                    const u32 tbase = tmem + ((u32)(quarter * 32) << 16) + (b * a.n_msub + ms) * TC_ROWS;
+#pragma unroll 1
+                    for (int c = 0; c < TC_ROWS / 32; c++) {
+                        u32 r[32];
+                        tmem_ld32(tbase + c * 32, r);
+                        const float4 *xn4 = reinterpret_cast<const float4 *>(a.xn + (size_t)t * TC_ROWS + c * 32);
+                        float kk[32];
+                        float mn = __int_as_float(0x7f800000);
+#pragma unroll
+                        for (int j4 = 0; j4 < 8; j4++) {
+                            const float4 v = __ldg(xn4 + j4);
+                            kk[4 * j4 + 0] = fmaf(a.s, __uint_as_float(r[4 * j4 + 0]), v.x);
+                            kk[4 * j4 + 1] = fmaf(a.s, __uint_as_float(r[4 * j4 + 1]), v.y);
+                            kk[4 * j4 + 2] = fmaf(a.s, __uint_as_float(r[4 * j4 + 2]), v.z);
+                            kk[4 * j4 + 3] = fmaf(a.s, __uint_as_float(r[4 * j4 + 3]), v.w);
+                            mn = fminf(fminf(mn, kk[4 * j4 + 0]), fminf(kk[4 * j4 + 1], kk[4 * j4 + 2]));
+                            mn = fminf(mn, kk[4 * j4 + 3]);
+                        }
+                        if (mn < thr) {
+                            const u32 id0 = t * TC_ROWS + c * 32;
+#pragma unroll
+                            for (int j = 0; j < 32; j++)
+                                if (kk[j] < thr) {
+                                    list_insert(lk, li, kk[j], id0 + j);
+                                    own_max = lk[TC_T - 1];
+                                    thr = fminf(own_max, thr_g);
+                                }
+                        }
+                        __syncwarp();
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&t_empty[b]);
+                    if (valid && own_max < published && own_max < thr_g) {
+                        atomicMin(a.thr + q, f2ord(own_max));
+                        published = own_max;
+                    }
+                }
+                if (!ok) {
+                    if (!abort_flag) fail();
+                    break;
+                }
+                if (valid) {
+                    u64 *dst = a.lists + ((size_t)q * a.chunks + ch) * TC_T;
+#pragma unroll
+                    for (int j = 0; j < TC_T; j++)
+                        dst[j] = li[j] == NIL ? KEY_INF : ((u64)f2ord(lk[j]) << 32 | li[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols)
+                     : "memory");
+    }
+}
+
+// ---- bf16 copies and norms ------------------------------------------------
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// gstat: [0] max |x|^2, [1] max |lo_x|, [2] max |e_x| (fp32 bits), [3] any lo != 0
+__global__ void gt_prep_rows(Dev d, u64 next_id, u32 n_pad, u32 kp1, u32 kb, __nv_bfloat16 *B, float *xn, u32 *gstat) {
+    const u32 c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (c >= n_pad) return;
+    bool live = false;
+    if (c < next_id) {
+        const u64 rf = d.ref[c];
+        live = !ref_del(rf) && ref_slab(rf) != NIL;
+    }
+    float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
+    bool anylo = false;
+    if (c < next_id) {
+        const float *xr = d.x + (size_t)c * d.mp;
+        __nv_bfloat16 *br = B + (size_t)c * kb;
+        for (u32 i = lane; i < kp1; i += 32) {
+            const float v = (live && i < d.dim) ? xr[i] : 0.0f;
+            const float hi = bf16_round(v);
+            const float lo = bf16_round(v - hi);
+            const float e = (v - hi) - lo;
+            br[i] = __float2bfloat16_rn(hi);
+            br[kp1 + i] = __float2bfloat16_rn(lo);
+            br[2 * kp1 + i] = __float2bfloat16_rn(hi);
+            sq = fmaf(v, v, sq);
+            lo2 = fmaf(lo, lo, lo2);
+            e2 = fmaf(e, e, e2);
+            anylo |= lo != 0.0f;
+        }
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        sq += __shfl_xor_sync(FULL, sq, h);
+        lo2 += __shfl_xor_sync(FULL, lo2, h);
+        e2 += __shfl_xor_sync(FULL, e2, h);
+    }
+    anylo = __any_sync(FULL, anylo);
+    if (lane == 0) {
+        xn[c] = live ? (d.metric == 0 ? sq : 0.0f) : __int_as_float(0x7f800000);
+        if (live) {
+            atomicMax(gstat + 0, __float_as_uint(sq));
+            atomicMax(gstat + 1, __float_as_uint(sqrtf(lo2)));
+            atomicMax(gstat + 2, __float_as_uint(sqrtf(e2)));
+            if (anylo) atomicOr(gstat + 3, 1u);
+        }
+    }
+}
+
+// qstat per query: |q|^2, |q|, |lo_q|, |e_q|
+__global__ void gt_prep_queries(const float *q, u32 mp, u32 dim, u32 nq, u32 kp1, u32 kb, __nv_bfloat16 *A,
+                                float *qstat, u32 *gstat, u32 *thr) {
+    const u32 r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (r >= nq) return;
+    const float *qr = q + (size_t)r * mp;
+    __nv_bfloat16 *ar = A + (size_t)r * kb;
+    float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
+    bool anylo = false;
+    for (u32 i = lane; i < kp1; i += 32) {
+        const float v = i < dim ? qr[i] : 0.0f;
+        const float hi = bf16_round(v);
+        const float lo = bf16_round(v - hi);
+        const float e = (v - hi) - lo;
+        ar[i] = __float2bfloat16_rn(hi);
+        ar[kp1 + i] = __float2bfloat16_rn(hi);
+        ar[2 * kp1 + i] = __float2bfloat16_rn(lo);
+        sq = fmaf(v, v, sq);
+        lo2 = fmaf(lo, lo, lo2);
+        e2 = fmaf(e, e, e2);
+        anylo |= lo != 0.0f;
+    }
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        sq += __shfl_xor_sync(FULL, sq, h);
+        lo2 += __shfl_xor_sync(FULL, lo2, h);
+        e2 += __shfl_xor_sync(FULL, e2, h);
+    }
+    anylo = __any_sync(FULL, anylo);
+    if (lane == 0) {
+        qstat[4 * (size_t)r + 0] = sq;
+        qstat[4 * (size_t)r + 1] = sqrtf(sq);
+        qstat[4 * (size_t)r + 2] = sqrtf(lo2);
+        qstat[4 * (size_t)r + 3] = sqrtf(e2);
+        thr[r] = ORD_INF;
+        if (anylo) atomicOr(gstat + 3, 1u);
+    }
+}
+
+// ---- merge, exact rerank, certificate --------------------------------------
+struct MergeArgs {
+    u32 nq, k, chunks, m, kprime, split;
+    u64 n_rows;           // ids at or above are not rows (never in a complete list)
+    const u32 *err;       // candidate pass error word: nonzero = lists incomplete
+    const float *q;       // nq x mp fp32
+    const u64 *lists;
+    const float *qstat;
+    const u32 *gstat;
+    u32 *out_ids;
+    float *out_dist;
+    u32 *fb;              // queries left to the exact CUDA-core kernel
+    u32 *fb_count;
+};
+
+__global__ void __launch_bounds__(256) gt_merge_kernel(Dev d, MergeArgs a) {
+    const u32 qi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (qi >= a.nq || *a.err) return;
+    u64 best = KEY_INF;          // sorted across lanes
+    u32 b1 = ORD_INF, b2 = ORD_INF;
+    for (u32 c = 0; c < a.chunks; c++) {
+        const u64 v = a.lists[((size_t)qi * a.chunks + c) * TC_T + lane];   // ascending
+        const u64 last = __shfl_sync(FULL, v, TC_T - 1);
+        if (last != KEY_INF) b1 = min(b1, (u32)(last >> 32));
+        const u64 rev = __shfl_sync(FULL, v, 31 - lane);
+        const u64 lo = best < rev ? best : rev;
+        u64 hi = best < rev ? rev : best;
+        // the larger half leaves the candidate set: remember its minimum
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+            const u64 o = __shfl_xor_sync(FULL, hi, h);
+            hi = o < hi ? o : hi;
+        }
+        if (hi != KEY_INF) b2 = min(b2, (u32)(hi >> 32));
+        best = warp_sort32(lo);
+    }
+    // exact rerank of the 32 candidates with the canonical distance
+    const float *qv = a.q + (size_t)qi * d.mp;
+    const int grp = lane >> 3, g = lane & 7;
+    u64 cand = KEY_INF;
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+        const u32 id = key_id(__shfl_sync(FULL, best, r0 + grp));
+        const u64 bk = __shfl_sync(FULL, best, r0 + grp);
+        float dd = 0.0f;
+        if (bk != KEY_INF && id < a.n_rows) dd = canon_dist<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
+        const u64 kk = bk != KEY_INF && id < a.n_rows ? mkkey(dd, id) : KEY_INF;
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const u64 v = __shfl_sync(FULL, kk, t * 8);
+            if (lane == r0 + t) cand = v;
+        }
+    }
+    cand = warp_sort32(cand);
+    const u32 lbo = min(b1, b2);
+    const u64 kth = __shfl_sync(FULL, cand, a.k - 1);
+    bool cert;
+    if (lbo == ORD_INF) {
+        cert = true;                                  // nothing was left out
+    } else if (kth == KEY_INF) {
+        cert = false;
+    } else {
+        const double u = 1.0 / 16777216.0, m = a.m, K = a.kprime;
+        const float *qs = a.qstat + 4 * (size_t)qi;
+        const double qn = qs[0], qa = (double)qs[1] * 1.01, loq = (double)qs[2] * 1.01, eq = (double)qs[3] * 1.01;
+        const double X2 = __uint_as_float(a.gstat[0]), X1 = sqrt(X2) * 1.01;
+        const double Lx = (double)__uint_as_float(a.gstat[1]) * 1.01, Ex = (double)__uint_as_float(a.gstat[2]) * 1.01;
+        const double dot_res = a.split ? loq * Lx + (qa + eq) * Ex + eq * (X1 + Ex) : 0.0;
+        const double dot_err = dot_res + (K + 2.0) * 2.0 * u * 1.03 * qa * X1;
+        const double LB = (double)ord2f(lbo);
+        double lb;
+        if (d.metric == 0) {
+            const double E = 2.0 * ((m + 2.0) * u * qn * 1.01 + (m + 2.0) * u * X2 + 2.0 * dot_err +
+                                    2.0 * u * (X2 + 2.1 * qa * X1));
+            const double y = qn + LB - E;
+            lb = y > 0.0 ? y * (1.0 - 2.0 * (m + 4.0) * u) : -1.0;
+        } else {
+            const double E = 2.0 * (dot_err + (m + 2.0) * u * qa * X1 + u * (1.0 + qa * X1));
+            lb = 1.0 + LB - E;
+        }
+        cert = (double)key_rho(kth) < lb;
+    }
+    if (cert) {
+        if (lane < (int)a.k) {
+            a.out_ids[(size_t)qi * a.k + lane] = cand == KEY_INF ? NIL : key_id(cand);
+            a.out_dist[(size_t)qi * a.k + lane] = cand == KEY_INF ? __int_as_float(0x7f800000) : key_rho(cand);
+        }
+    } else if (lane == 0) {
+        a.fb[atomicAdd(a.fb_count, 1u)] = qi;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool encode_bf16(CUtensorMap *m, const void *base, u64 rows, u32 cols) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {TC_KBOX, TC_ROWS};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+GtTcPlan gt_tc_plan(u32 dim, u64 next_id, u32 nq) {
+    GtTcPlan p{};
+    p.kp1 = (dim + TC_KBOX - 1) / TC_KBOX * TC_KBOX;
+    p.kb = 3 * p.kp1;
+    p.n_pad = (next_id + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
+    p.bytes_B = (size_t)next_id * p.kb * 2;
+    p.bytes_A = (size_t)nq * p.kb * 2;
+    return p;
+}
+
+cudaError_t launch_gt_tc_prep(const Dev &d, u64 next_id, const float *q, u32 nq, const GtTcPlan &p,
+                              const GtTcBufs &b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.gstat, 0, 8 * sizeof(u32), st);
+    if (e != cudaSuccess) return e;
+    if (p.n_pad) gt_prep_rows<<<(unsigned)((p.n_pad * 32 + 255) / 256), 256, 0, st>>>(
+        d, next_id, (u32)p.n_pad, p.kp1, p.kb, reinterpret_cast<__nv_bfloat16 *>(b.B), b.xn, b.gstat);
+    gt_prep_queries<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(
+        q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<__nv_bfloat16 *>(b.A), b.qstat, b.gstat, b.thr);
+    return cudaGetLastError();
+}
+
+cudaError_t gt_tc_configure(GtTcPlan &p, u32 nq, bool split, int num_sms) {
+    p.kprime = split ? p.kb : p.kp1;
+    p.split = split;
+    p.kblocks = p.kprime / TC_KBOX;
+    const u32 smem_max = 227 * 1024 - 1024 - 512;
+    p.n_msub = (2u * p.kblocks * TC_BOX + 2 * TC_BOX <= smem_max) && nq > TC_ROWS ? 2 : 1;
+    if ((u64)p.n_msub * p.kblocks * TC_BOX + 2 * TC_BOX > smem_max) {
+        p.usable = false;
+        return cudaSuccess;
+    }
+    p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - p.n_msub * p.kblocks * TC_BOX) / TC_BOX);
+    p.smem = p.n_msub * p.kblocks * TC_BOX + p.stages * TC_BOX + 1024;
+    p.n_tiles = (u32)(p.n_pad / TC_ROWS);
+    p.m_tiles = (nq + p.n_msub * TC_ROWS - 1) / (p.n_msub * TC_ROWS);
+    // chunks of rows: enough work items to fill every SM a few times over,
+    // with the fewest idle SMs in the last wave
+    u32 best_c = 1;
+    double best_eff = -1.0;
+    const u32 cmax = std::max<u32>(1, std::min<u32>(p.n_tiles, 256));
+    for (u32 c = 1; c <= cmax; c++) {
+        const u64 items = (u64)p.m_tiles * c;
+        const u64 waves = (items + num_sms - 1) / num_sms;
+        const double eff = (double)items / (double)(waves * num_sms);
+        const double score = eff - (items < 2ull * num_sms ? 0.5 : 0.0) - 0.002 * c;
+        if (score > best_eff) {
+            best_eff = score;
+            best_c = c;
+        }
+    }
+    p.chunks = best_c;
+    p.tiles_per_chunk = (p.n_tiles + p.chunks - 1) / p.chunks;
+    p.chunks = (p.n_tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+    p.tmem_cols = p.n_msub == 2 ? 512 : 256;
+    p.bytes_lists = (size_t)nq * p.chunks * TC_T * 8;
+    p.usable = p.n_tiles > 0;
+    return cudaSuccess;
+}
+
+cudaError_t launch_gt_tc(const Dev &d, const float *q, u32 nq, u32 k, const GtTcPlan &p, const GtTcBufs &b,
+                         u64 next_id, u32 *out_ids, float *out_dist, int num_sms, cudaStream_t st) {
+    CUtensorMap ta, tb;
+    if (!encode_bf16(&ta, b.A, nq, p.kb) || !encode_bf16(&tb, b.B, next_id, p.kb)) return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.nq = nq;
+    a.n_tiles = p.n_tiles;
+    a.kblocks = p.kblocks;
+    a.n_msub = p.n_msub;
+    a.m_tiles = p.m_tiles;
+    a.chunks = p.chunks;
+    a.tiles_per_chunk = p.tiles_per_chunk;
+    a.stages = p.stages;
+    a.tmem_cols = p.tmem_cols;
+    a.s = d.metric == 0 ? -2.0f : -1.0f;
+    a.xn = b.xn;
+    a.thr = b.thr;
+    a.lists = b.lists;
+    a.err = b.err;
+    cudaError_t e = cudaFuncSetAttribute(gt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    const u32 items = p.m_tiles * p.chunks;
+    const u32 grid = std::min<u32>(items, (u32)num_sms);
+    gt_tc_kernel<<<grid, TC_THREADS, p.smem, st>>>(ta, tb, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    MergeArgs m{};
+    m.nq = nq;
+    m.k = k;
+    m.chunks = p.chunks;
+    m.m = d.dim;
+    m.kprime = p.kprime;
+    m.split = p.split;
+    m.q = q;
+    m.lists = b.lists;
+    m.qstat = b.qstat;
+    m.gstat = b.gstat;
+    m.out_ids = out_ids;
+    m.out_dist = out_dist;
+    m.fb = b.fb;
+    m.fb_count = b.gstat + 4;
+    m.n_rows = next_id;
+    m.err = b.err;
+    gt_merge_kernel<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(d, m);
+    return cudaGetLastError();
+}
+
+}  // namespace etale

@@ -413,15 +413,16 @@ cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaS
 constexpr int GT_TILE = 32;
 
 __global__ void __launch_bounds__(256) gt_kernel(Dev d, u64 next_id, const float *q, u32 nq, u32 k, u32 *out_ids,
-                                                 float *out_dist) {
+                                                 float *out_dist, const u32 *qsel) {
     extern __shared__ __align__(16) float gsm[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const u32 mp = d.mp;
     float *rows = gsm;                               // GT_TILE x mp
     float *qv = gsm + GT_TILE * mp + warp * mp;      // 8 x mp
     __shared__ u64 rref[GT_TILE];
-    const u32 qi = blockIdx.x * 8 + warp;
-    const bool active = qi < nq;
+    const u32 slot = blockIdx.x * 8 + warp;
+    const bool active = slot < nq;
+    const u32 qi = active && qsel ? qsel[slot] : slot;
     if (active)
         for (u32 i = lane * 4; i < mp; i += 128)
             *reinterpret_cast<float4 *>(qv + i) = *reinterpret_cast<const float4 *>(q + (size_t)qi * mp + i);
@@ -466,13 +467,13 @@ __global__ void __launch_bounds__(256) gt_kernel(Dev d, u64 next_id, const float
 }
 
 cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 nq, u32 k, u32 *out_ids,
-                                float *out_dist, int num_sms, cudaStream_t st) {
+                                float *out_dist, int num_sms, cudaStream_t st, const u32 *qsel) {
     if (nq == 0) return cudaSuccess;
     if (k > 32) return cudaErrorInvalidValue;
     size_t smem = (size_t)(GT_TILE + 8) * d.mp * 4;
     cudaError_t e = cudaFuncSetAttribute(gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    gt_kernel<<<(nq + 7) / 8, 256, smem, st>>>(d, next_id, q, nq, k, out_ids, out_dist);
+    gt_kernel<<<(nq + 7) / 8, 256, smem, st>>>(d, next_id, q, nq, k, out_ids, out_dist, qsel);
     return cudaGetLastError();
 }
 
