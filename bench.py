@@ -27,6 +27,7 @@ from paper_2607_02543_gb300 import workloads as W  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -54,12 +55,13 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
     return W.scaled(w, n_live) if n_live else w
 
 
-def load_peaks():
+def load_peaks(key: str = "hbm_gbs"):
+    """(peak, "measured" | "fallback") for HBM GB/s or bf16 TFLOP/s."""
     try:
         p = json.load(open(PEAKS_FILE))
-        return float(p["hbm_gbs"]), "measured"
+        return float(p[key]), "measured"
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return (FALLBACK_HBM_GBS if key == "hbm_gbs" else FALLBACK_BF16_TFLOPS), "fallback"
 
 
 # ---------------------------------------------------------------------------
@@ -301,10 +303,32 @@ def main():
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     ms_round = float(np.mean(maint_ms))
     ms_search = float(np.mean(search_ms))
-    # recall of the last query batch against the exact live top-k
+    # recall of the last query batch against the exact live top-k, timed:
+    # the ground truth is the one dense contraction of the path (tensor cores)
+    idx.set_profiling(True)
+    idx.profile(reset=True)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
     gt_ids, _ = idx.ground_truth(d_q, w.k, stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gprof = idx.profile(reset=True)
+    idx.set_profiling(False)
     gt_np = gt_ids.cpu().numpy().view(np.uint32)
     recall = recall_of(out_ids)
+    ginfo = idx.ground_truth_info()
+    live_now = idx.stats()["live"]
+    gt_flop = 2.0 * w.n_queries * live_now * w.dim
+    tc_ms = gprof["gt_tensor"][0]
+    tc_peak, tc_kind = load_peaks("bf16_tflops")
+    gt_block = {"call_ms": g0.elapsed_time(g1), "path": ginfo["path"], "fallback_queries": ginfo["fallback_queries"],
+                "phase_ms": {k: round(v[0], 4) for k, v in gprof.items() if v[1]},
+                "flop": gt_flop, "flop_basis": "2 x queries x live rows x dim"}
+    if tc_ms > 0:
+        ach = gt_flop / (tc_ms * 1e-3) / 1e12
+        gt_block["roofline"] = {"bound": "tensor", "kernel": "gt_tc_kernel", "achieved": ach, "peak": tc_peak,
+                                "unit": "TFLOP/s", "frac": ach / tc_peak, "peak_source": tc_kind,
+                                "kernel_ms": tc_ms}
     # algorithmic bytes of the query-search launch
     m, R = w.dim, w.degree
     nexp = np.mean([b["n_expand"] - a["n_expand"] for a, b in search_stats])
@@ -361,7 +385,7 @@ def main():
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "kernel_ms": kernel_ms},
-               "phase_ms_per_step": phases,
+               "phase_ms_per_step": phases, "ground_truth": gt_block,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)

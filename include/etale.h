@@ -285,6 +285,10 @@ typedef enum {
     ETALE_PH_RECLAIM,         /* reclaim phase 2                                */
     ETALE_PH_SEARCH_QUERY,    /* BeamSearch kernel, query mode                  */
     ETALE_PH_RECYCLE,         /* retired -> free stack                          */
+    ETALE_PH_GT_PREP,         /* ground truth: bf16 copies and norms            */
+    ETALE_PH_GT_TENSOR,       /* ground truth: tensor-core candidate pass       */
+    ETALE_PH_GT_MERGE,        /* ground truth: exact rerank + certificate       */
+    ETALE_PH_GT_EXACT,        /* ground truth: CUDA-core exact kernel           */
     ETALE_PH_COUNT
 } etale_phase;
 

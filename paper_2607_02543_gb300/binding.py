@@ -58,7 +58,8 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
            "etale_selftest_bounded_wait", "etale_ground_truth_info"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
-          "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle"]
+          "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
+          "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
 
 _lock = threading.Lock()
 _lib = None

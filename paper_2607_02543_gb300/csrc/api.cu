@@ -96,7 +96,7 @@ struct etale_index {
     // call and one update call can run at the same time (concurrent mode)
     DevBuf s_stage, s_qpad, s_out_ids, s_out_dist, s_seed;
     // ground truth on tensor cores
-    DevBuf gt_A, gt_B, gt_xn, gt_qstat, gt_gstat, gt_thr, gt_fb, gt_lists;
+    DevBuf gt_A, gt_B, gt_xn, gt_qstat, gt_gstat, gt_fb, gt_bmin;
     u32 gt_path = 0;
     u64 gt_fallbacks = 0;
     u64 *host_ctr_s = nullptr;        // pinned, search side
@@ -525,6 +525,11 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         cfg.gram = cfg_in->gram;
         cfg.copies = cfg_in->copies;
         if (cfg_in->rerank) cfg.rerank = cfg_in->rerank;
+        cfg.gt = cfg_in->gt;
+    }
+    if (cfg.gt > 1) {
+        t_last_error = "gt must be 0 or 1";
+        return ETALE_EINVAL;
     }
     if (cfg.copies > 3) {
         t_last_error = "copies is a bitmask of 1 (bf16) and 2 (fp8)";
@@ -847,13 +852,13 @@ static etale_status ground_truth_run(etale_index *idx, const Dev &d, const float
     idx->gt_fallbacks = 0;
     GtTcPlan p = gt_tc_plan(idx->dim, idx->next_id, nq);
     if (idx->cfg.gt == 1 || p.n_pad == 0) {
+        PhaseScope ps(idx, ETALE_PH_GT_EXACT, st);
         CK(launch_ground_truth(d, idx->next_id, qpad, nq, k, oid, od, idx->num_sms, st), "ground truth");
         g_kernel_launches++;
         return ETALE_OK;
     }
     if (!grow(idx->gt_A, p.bytes_A) || !grow(idx->gt_B, p.bytes_B) || !grow(idx->gt_xn, p.n_pad * 4) ||
-        !grow(idx->gt_qstat, (size_t)nq * 16) || !grow(idx->gt_gstat, 64) || !grow(idx->gt_thr, (size_t)nq * 4) ||
-        !grow(idx->gt_fb, (size_t)nq * 4))
+        !grow(idx->gt_qstat, (size_t)nq * 16) || !grow(idx->gt_gstat, 64) || !grow(idx->gt_fb, (size_t)nq * 4))
         return idx->fail(ETALE_ENOMEM, "ground-truth staging");
     GtTcBufs b{};
     b.A = idx->gt_A.p;
@@ -861,30 +866,44 @@ static etale_status ground_truth_run(etale_index *idx, const Dev &d, const float
     b.xn = as<float>(idx->gt_xn);
     b.qstat = as<float>(idx->gt_qstat);
     b.gstat = as<u32>(idx->gt_gstat);
-    b.thr = as<u32>(idx->gt_thr);
     b.fb = as<u32>(idx->gt_fb);
     b.err = b.gstat + 5;
-    CK(launch_gt_tc_prep(d, idx->next_id, qpad, nq, p, b, st), "ground-truth copies");
+    {
+        PhaseScope ps(idx, ETALE_PH_GT_PREP, st);
+        CK(launch_gt_tc_prep(d, idx->next_id, qpad, nq, p, b, st), "ground-truth copies");
+    }
     g_kernel_launches += 2;
     u32 h[8];
     CK(cudaMemcpyAsync(h, b.gstat, sizeof h, cudaMemcpyDeviceToHost, st), "read split flag");
     CK(cudaStreamSynchronize(st), "synchronize");
-    gt_tc_configure(p, nq, h[3] != 0, idx->num_sms);
+    gt_tc_configure(p, nq, h[3] != 0);
     if (!p.usable) {
+        PhaseScope ps(idx, ETALE_PH_GT_EXACT, st);
         CK(launch_ground_truth(d, idx->next_id, qpad, nq, k, oid, od, idx->num_sms, st), "ground truth");
         g_kernel_launches++;
         return ETALE_OK;
     }
-    if (!grow(idx->gt_lists, p.bytes_lists)) return idx->fail(ETALE_ENOMEM, "ground-truth candidate lists");
-    b.lists = as<u64>(idx->gt_lists);
-    CK(launch_gt_tc(d, qpad, nq, k, p, b, idx->next_id, oid, od, idx->num_sms, st), "ground truth (tensor)");
-    g_kernel_launches += 2;
+    if (!grow(idx->gt_bmin, p.bytes_bmin)) return idx->fail(ETALE_ENOMEM, "ground-truth block minima");
+    b.bmin = as<float>(idx->gt_bmin);
+    for (u32 q0 = 0; q0 < nq; q0 += p.qgroup) {
+        const u32 g = std::min<u32>(p.qgroup, nq - q0);
+        {
+            PhaseScope ps(idx, ETALE_PH_GT_TENSOR, st);
+            CK(launch_gt_tc(d, q0, g, p, b, idx->next_id, idx->num_sms, st), "ground truth (tensor)");
+        }
+        {
+            PhaseScope ps(idx, ETALE_PH_GT_MERGE, st);
+            CK(launch_gt_rerank(d, qpad, q0, g, k, p, b, idx->next_id, oid, od, st), "ground truth (rerank)");
+        }
+        g_kernel_launches += 2;
+    }
     CK(cudaMemcpyAsync(h, b.gstat, sizeof h, cudaMemcpyDeviceToHost, st), "read fallback count");
     CK(cudaStreamSynchronize(st), "synchronize");
     if (h[5] & ERR_TIMEOUT) return idx->fail(ETALE_ETIMEOUT, "ground truth: a bounded device wait gave up");
     idx->gt_path = p.split ? 2 : 1;
     idx->gt_fallbacks = h[4];
     if (h[4]) {
+        PhaseScope ps(idx, ETALE_PH_GT_EXACT, st);
         CK(launch_ground_truth(d, idx->next_id, qpad, h[4], k, oid, od, idx->num_sms, st, b.fb),
            "ground truth (fallback)");
         g_kernel_launches++;

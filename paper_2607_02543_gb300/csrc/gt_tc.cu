@@ -14,18 +14,19 @@
 //      swizzle) streams 128-row boxes of the row copy through a shared
 //      memory ring while the query tile stays resident; one thread issues
 //      tcgen05.mma (M = N = 128, bf16 -> fp32) into a double-buffered TMEM
-//      accumulator; eight epilogue warps read it with tcgen05.ld and keep,
-//      per query and per chunk of rows, the 32 smallest approximate keys
-//      key = |x|^2 - 2 q.x (L2) or -q.x (IP), pruned by a per-query
-//      threshold shared through global memory.
-//   3. gt_merge_kernel: per query, the union of its chunk lists is cut to 32
-//      candidates, reranked with the canonical fp32 distance (the same
-//      definition the rest of the index uses), and certified: every item
-//      left out has an approximate key >= LB, and an a-priori bound E on
-//      |approximate - canonical| shows that no such item can beat the k-th
-//      reranked distance.  Queries that fail the certificate are recomputed
-//      by the CUDA-core exact kernel, so the result is always the exact
-//      top-k with canonical distances, ties by smaller id.
+//      accumulator; eight epilogue warps read it with tcgen05.ld and write,
+//      per query and per block of 32 rows, the smallest approximate key
+//      key = |x|^2 - 2 q.x (L2) or -q.x (IP); dead rows have key +inf.
+//   3. gt_rerank_kernel (a warp per query): tau = the 32nd smallest block
+//      minimum (or the 2k-th for k > 16); every row of every block whose
+//      minimum is <= tau is reranked with the canonical fp32 distance (the
+//      same definition the rest of the index uses) into the top k.  Rows
+//      left out have approximate keys > tau; an a-priori bound E on
+//      |approximate - canonical| certifies that none of them can beat the
+//      k-th reranked distance.  Queries that fail the certificate (or have
+//      more than 256 candidate blocks) are recomputed by the CUDA-core exact
+//      kernel, so the result is always the exact top-k with canonical
+//      distances, ties by smaller id.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -41,7 +42,6 @@ namespace {
 constexpr int TC_ROWS = 128;                      // MMA M (queries) and N (rows)
 constexpr int TC_KBOX = 64;                       // bf16 per 128-byte swizzle row
 constexpr u32 TC_BOX = TC_ROWS * TC_KBOX * 2;     // 16 KB per TMA box
-constexpr int TC_T = 32;                          // candidates per (query, chunk)
 constexpr int TC_MAX_STAGES = 12;
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;
@@ -52,11 +52,10 @@ constexpr u32 TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(TC_ROWS >> 
                          ((u32)(TC_ROWS >> 4) << 24);
 
 struct TcArgs {
-    u32 nq, n_tiles, kblocks, n_msub, m_tiles, chunks, tiles_per_chunk, stages, tmem_cols;
+    u32 nq, n_tiles, kblocks, n_msub, m_tiles, chunks, tiles_per_chunk, stages, tmem_cols, nblk;
     float s;              // -2 (L2) or -1 (IP)
     const float *xn;      // n_tiles * 128 key bases (+inf for dead rows and padding)
-    u32 *thr;             // nq ordered per-query thresholds
-    u64 *lists;           // nq x chunks x TC_T (ordered key << 32 | id), ascending
+    float *bmin;          // nq x nblk: smallest key of each block of 32 rows
     u32 *err;
 };
 
@@ -96,22 +95,6 @@ __device__ __forceinline__ void tmem_ld32(u32 taddr, u32 (&r)[32]) {
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Sorted (ascending) register list; requires k < lk[TC_T - 1].
-__device__ __forceinline__ void list_insert(float (&lk)[TC_T], u32 (&li)[TC_T], float k, u32 id) {
-    bool done = false;
-#pragma unroll
-    for (int j = TC_T - 1; j >= 0; --j) {
-        if (j > 0 && !done && k < lk[j - 1]) {
-            lk[j] = lk[j - 1];
-            li[j] = li[j - 1];
-        } else if (!done) {
-            lk[j] = k;
-            li[j] = id;
-            done = true;
-        }
-    }
 }
 
 // ---- candidate pass ---------------------------------------------------------
@@ -242,83 +225,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_wait(&drain, 0, WAIT_LIMIT);
         }
     } else {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31; lane = one query ----
         const int ew = warp - 2, ms = ew >> 2, quarter = warp & 3;
         if ((u32)ms < a.n_msub) {
             const int row = quarter * 32 + lane;
             u32 tcount = 0;
-            for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
+            bool ok = true;
+            for (u32 it = blockIdx.x; it < items && ok; it += gridDim.x) {
                 const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
                 const u32 q = (mt * a.n_msub + ms) * TC_ROWS + row;
                 const bool valid = q < a.nq;
-                float lk[TC_T];
-                u32 li[TC_T];
-#pragma unroll
-                for (int j = 0; j < TC_T; j++) {
-                    lk[j] = __int_as_float(0x7f800000);
-                    li[j] = NIL;
-                }
-                float own_max = __int_as_float(0x7f800000), published = own_max;
-                bool ok = true;
+                float4 *dst = reinterpret_cast<float4 *>(a.bmin + (size_t)(valid ? q : 0) * a.nblk);
                 for (u32 t = t0; t < t1; t++, tcount++) {
                     const u32 b = tcount & 1;
                     // every lane waits; the warp goes on together (tcgen05.ld is .sync.aligned)
                     const bool got = !abort_flag && mbar_wait(&t_full[b], (tcount >> 1) & 1, WAIT_LIMIT);
                     if (!__all_sync(FULL, got)) { ok = false; break; }
                     tc_fence_after();
-                    const float thr_g = valid ? ord2f(*reinterpret_cast<volatile u32 *>(a.thr + q))
-                                              : __int_as_float(0xff800000);
-                    float thr = fminf(own_max, thr_g);
                     const u32 tbase = tmem + ((u32)(quarter * 32) << 16) + (b * a.n_msub + ms) * TC_ROWS;
-#pragma unroll 1
+                    float bm[TC_ROWS / 32];
+#pragma unroll
                     for (int c = 0; c < TC_ROWS / 32; c++) {
                         u32 r[32];
                         tmem_ld32(tbase + c * 32, r);
                         const float4 *xn4 = reinterpret_cast<const float4 *>(a.xn + (size_t)t * TC_ROWS + c * 32);
-                        float kk[32];
-                        float mn = __int_as_float(0x7f800000);
+                        float m0 = __int_as_float(0x7f800000), m1 = m0;
 #pragma unroll
                         for (int j4 = 0; j4 < 8; j4++) {
                             const float4 v = __ldg(xn4 + j4);
-                            kk[4 * j4 + 0] = fmaf(a.s, __uint_as_float(r[4 * j4 + 0]), v.x);
-                            kk[4 * j4 + 1] = fmaf(a.s, __uint_as_float(r[4 * j4 + 1]), v.y);
-                            kk[4 * j4 + 2] = fmaf(a.s, __uint_as_float(r[4 * j4 + 2]), v.z);
-                            kk[4 * j4 + 3] = fmaf(a.s, __uint_as_float(r[4 * j4 + 3]), v.w);
-                            mn = fminf(fminf(mn, kk[4 * j4 + 0]), fminf(kk[4 * j4 + 1], kk[4 * j4 + 2]));
-                            mn = fminf(mn, kk[4 * j4 + 3]);
+                            m0 = fminf(m0, fmaf(a.s, __uint_as_float(r[4 * j4 + 0]), v.x));
+                            m1 = fminf(m1, fmaf(a.s, __uint_as_float(r[4 * j4 + 1]), v.y));
+                            m0 = fminf(m0, fmaf(a.s, __uint_as_float(r[4 * j4 + 2]), v.z));
+                            m1 = fminf(m1, fmaf(a.s, __uint_as_float(r[4 * j4 + 3]), v.w));
                         }
-                        if (mn < thr) {
-                            const u32 id0 = t * TC_ROWS + c * 32;
-#pragma unroll
-                            for (int j = 0; j < 32; j++)
-                                if (kk[j] < thr) {
-                                    list_insert(lk, li, kk[j], id0 + j);
-                                    own_max = lk[TC_T - 1];
-                                    thr = fminf(own_max, thr_g);
-                                }
-                        }
-                        __syncwarp();
+                        bm[c] = fminf(m0, m1);
                     }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&t_empty[b]);
-                    if (valid && own_max < published && own_max < thr_g) {
-                        atomicMin(a.thr + q, f2ord(own_max));
-                        published = own_max;
-                    }
-                }
-                if (!ok) {
-                    if (!abort_flag) fail();
-                    break;
-                }
-                if (valid) {
-                    u64 *dst = a.lists + ((size_t)q * a.chunks + ch) * TC_T;
-#pragma unroll
-                    for (int j = 0; j < TC_T; j++)
-                        dst[j] = li[j] == NIL ? KEY_INF : ((u64)f2ord(lk[j]) << 32 | li[j]);
+                    if (valid) dst[t] = make_float4(bm[0], bm[1], bm[2], bm[3]);
                 }
             }
+            if (!ok && !abort_flag) fail();
         }
     }
     tc_fence_before();
@@ -334,75 +283,110 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ---- bf16 copies and norms ------------------------------------------------
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-// gstat: [0] max |x|^2, [1] max |lo_x|, [2] max |e_x| (fp32 bits), [3] any lo != 0
-__global__ void gt_prep_rows(Dev d, u64 next_id, u32 n_pad, u32 kp1, u32 kb, __nv_bfloat16 *B, float *xn, u32 *gstat) {
-    const u32 c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Four consecutive elements: hi, lo and residual, with the sums an error bound needs.
+struct Split4 {
+    uint2 hi, lo;
+    float sq, lo2, e2;
+    bool anylo;
+};
+__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
+    const __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+    return make_uint2(*reinterpret_cast<const u32 *>(&x), *reinterpret_cast<const u32 *>(&y));
+}
+__device__ __forceinline__ Split4 split4(float4 v) {
+    Split4 o;
+    const float h0 = bf16_round(v.x), h1 = bf16_round(v.y), h2 = bf16_round(v.z), h3 = bf16_round(v.w);
+    const float l0 = bf16_round(v.x - h0), l1 = bf16_round(v.y - h1), l2 = bf16_round(v.z - h2),
+                l3 = bf16_round(v.w - h3);
+    const float e0 = (v.x - h0) - l0, e1 = (v.y - h1) - l1, e2 = (v.z - h2) - l2, e3 = (v.w - h3) - l3;
+    o.hi = pack_bf16x4(h0, h1, h2, h3);
+    o.lo = pack_bf16x4(l0, l1, l2, l3);
+    o.sq = fmaf(v.w, v.w, fmaf(v.z, v.z, fmaf(v.y, v.y, v.x * v.x)));
+    o.lo2 = fmaf(l3, l3, fmaf(l2, l2, fmaf(l1, l1, l0 * l0)));
+    o.e2 = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
+    o.anylo = (l0 != 0.0f) | (l1 != 0.0f) | (l2 != 0.0f) | (l3 != 0.0f);
+    return o;
+}
+__device__ __forceinline__ float4 load_row4(const float *r, u32 i, u32 dim, bool on) {
+    if (!on || i >= dim) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = *reinterpret_cast<const float4 *>(r + i);   // rows are padded to a multiple of 4
+    if (i + 1 >= dim) v.y = 0.f;
+    if (i + 2 >= dim) v.z = 0.f;
+    if (i + 3 >= dim) v.w = 0.f;
+    return v;
+}
+
+// gstat: [0] max |x|^2, [1] max |lo_x|, [2] max |e_x| (fp32 bits), [3] any lo != 0.
+// A warp per row, grid-stride; maxima are kept per warp and published once.
+__global__ void gt_prep_rows(Dev d, u64 next_id, u32 n_pad, u32 kp1, u32 kb, u32 *B, float *xn, u32 *gstat) {
     const int lane = lane_id();
-    if (c >= n_pad) return;
-    bool live = false;
-    if (c < next_id) {
-        const u64 rf = d.ref[c];
-        live = !ref_del(rf) && ref_slab(rf) != NIL;
-    }
-    float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
-    bool anylo = false;
-    if (c < next_id) {
-        const float *xr = d.x + (size_t)c * d.mp;
-        __nv_bfloat16 *br = B + (size_t)c * kb;
-        for (u32 i = lane; i < kp1; i += 32) {
-            const float v = (live && i < d.dim) ? xr[i] : 0.0f;
-            const float hi = bf16_round(v);
-            const float lo = bf16_round(v - hi);
-            const float e = (v - hi) - lo;
-            br[i] = __float2bfloat16_rn(hi);
-            br[kp1 + i] = __float2bfloat16_rn(lo);
-            br[2 * kp1 + i] = __float2bfloat16_rn(hi);
-            sq = fmaf(v, v, sq);
-            lo2 = fmaf(lo, lo, lo2);
-            e2 = fmaf(e, e, e2);
-            anylo |= lo != 0.0f;
+    const u32 nwarps = (gridDim.x * blockDim.x) >> 5;
+    float mx_sq = 0.0f, mx_lo = 0.0f, mx_e = 0.0f;
+    bool any_lo = false;
+    for (u32 c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_pad; c += nwarps) {
+        bool live = false;
+        if (c < next_id) {
+            const u64 rf = d.ref[c];
+            live = !ref_del(rf) && ref_slab(rf) != NIL;
         }
-    }
+        float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
+        bool anylo = false;
+        if (c < next_id) {
+            const float *xr = d.x + (size_t)c * d.mp;
+            uint2 *br = reinterpret_cast<uint2 *>(B + (size_t)c * (kb / 2));
+            for (u32 i = 4 * lane; i < kp1; i += 128) {
+                const Split4 v = split4(load_row4(xr, i, d.dim, live));
+                br[i / 4] = v.hi;
+                br[(kp1 + i) / 4] = v.lo;
+                br[(2 * kp1 + i) / 4] = v.hi;
+                sq += v.sq;
+                lo2 += v.lo2;
+                e2 += v.e2;
+                anylo |= v.anylo;
+            }
+        }
 #pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        sq += __shfl_xor_sync(FULL, sq, h);
-        lo2 += __shfl_xor_sync(FULL, lo2, h);
-        e2 += __shfl_xor_sync(FULL, e2, h);
-    }
-    anylo = __any_sync(FULL, anylo);
-    if (lane == 0) {
-        xn[c] = live ? (d.metric == 0 ? sq : 0.0f) : __int_as_float(0x7f800000);
-        if (live) {
-            atomicMax(gstat + 0, __float_as_uint(sq));
-            atomicMax(gstat + 1, __float_as_uint(sqrtf(lo2)));
-            atomicMax(gstat + 2, __float_as_uint(sqrtf(e2)));
-            if (anylo) atomicOr(gstat + 3, 1u);
+        for (int h = 16; h >= 1; h >>= 1) {
+            sq += __shfl_xor_sync(FULL, sq, h);
+            lo2 += __shfl_xor_sync(FULL, lo2, h);
+            e2 += __shfl_xor_sync(FULL, e2, h);
         }
+        if (lane == 0) xn[c] = live ? (d.metric == 0 ? sq : 0.0f) : __int_as_float(0x7f800000);
+        if (live) {
+            mx_sq = fmaxf(mx_sq, sq);
+            mx_lo = fmaxf(mx_lo, sqrtf(lo2));
+            mx_e = fmaxf(mx_e, sqrtf(e2));
+            any_lo |= anylo;
+        }
+    }
+    any_lo = __any_sync(FULL, any_lo);
+    if (lane == 0) {
+        if (mx_sq > 0.0f) atomicMax(gstat + 0, __float_as_uint(mx_sq));
+        if (mx_lo > 0.0f) atomicMax(gstat + 1, __float_as_uint(mx_lo));
+        if (mx_e > 0.0f) atomicMax(gstat + 2, __float_as_uint(mx_e));
+        if (any_lo) atomicOr(gstat + 3, 1u);
     }
 }
 
-// qstat per query: |q|^2, |q|, |lo_q|, |e_q|
-__global__ void gt_prep_queries(const float *q, u32 mp, u32 dim, u32 nq, u32 kp1, u32 kb, __nv_bfloat16 *A,
-                                float *qstat, u32 *gstat, u32 *thr) {
+// qstat per query: |q|^2, |q|, |lo_q|, |e_q|; copy as [hi | hi | lo]
+__global__ void gt_prep_queries(const float *q, u32 mp, u32 dim, u32 nq, u32 kp1, u32 kb, u32 *A, float *qstat,
+                                u32 *gstat) {
     const u32 r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (r >= nq) return;
     const float *qr = q + (size_t)r * mp;
-    __nv_bfloat16 *ar = A + (size_t)r * kb;
+    uint2 *ar = reinterpret_cast<uint2 *>(A + (size_t)r * (kb / 2));
     float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
     bool anylo = false;
-    for (u32 i = lane; i < kp1; i += 32) {
-        const float v = i < dim ? qr[i] : 0.0f;
-        const float hi = bf16_round(v);
-        const float lo = bf16_round(v - hi);
-        const float e = (v - hi) - lo;
-        ar[i] = __float2bfloat16_rn(hi);
-        ar[kp1 + i] = __float2bfloat16_rn(hi);
-        ar[2 * kp1 + i] = __float2bfloat16_rn(lo);
-        sq = fmaf(v, v, sq);
-        lo2 = fmaf(lo, lo, lo2);
-        e2 = fmaf(e, e, e2);
-        anylo |= lo != 0.0f;
+    for (u32 i = 4 * lane; i < kp1; i += 128) {
+        const Split4 v = split4(load_row4(qr, i, dim, true));
+        ar[i / 4] = v.hi;
+        ar[(kp1 + i) / 4] = v.hi;
+        ar[(2 * kp1 + i) / 4] = v.lo;
+        sq += v.sq;
+        lo2 += v.lo2;
+        e2 += v.e2;
+        anylo |= v.anylo;
     }
 #pragma unroll
     for (int h = 16; h >= 1; h >>= 1) {
@@ -416,70 +400,106 @@ __global__ void gt_prep_queries(const float *q, u32 mp, u32 dim, u32 nq, u32 kp1
         qstat[4 * (size_t)r + 1] = sqrtf(sq);
         qstat[4 * (size_t)r + 2] = sqrtf(lo2);
         qstat[4 * (size_t)r + 3] = sqrtf(e2);
-        thr[r] = ORD_INF;
         if (anylo) atomicOr(gstat + 3, 1u);
     }
 }
 
-// ---- merge, exact rerank, certificate --------------------------------------
-struct MergeArgs {
-    u32 nq, k, chunks, m, kprime, split;
-    u64 n_rows;           // ids at or above are not rows (never in a complete list)
-    const u32 *err;       // candidate pass error word: nonzero = lists incomplete
-    const float *q;       // nq x mp fp32
-    const u64 *lists;
-    const float *qstat;
+// ---- threshold, exact rerank, certificate -------------------------------
+constexpr int RR_MAXB = 256;      // candidate blocks a query may keep
+constexpr int RR_WARPS = 8;
+
+struct RerankArgs {
+    u32 nq, q0, k, nblk, rt, m, kprime, split;
+    u64 n_rows;
+    const float *q;       // all queries, nq_total x mp fp32
+    const float *bmin;    // this group: nq x nblk
+    const float *qstat;   // all queries
     const u32 *gstat;
-    u32 *out_ids;
+    u32 *out_ids;         // all queries, x k
     float *out_dist;
-    u32 *fb;              // queries left to the exact CUDA-core kernel
+    u32 *fb;              // queries left to the exact CUDA-core kernel (global indices)
     u32 *fb_count;
+    const u32 *err;       // candidate pass error word: nonzero = minima incomplete
 };
 
-__global__ void __launch_bounds__(256) gt_merge_kernel(Dev d, MergeArgs a) {
-    const u32 qi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = lane_id();
-    if (qi >= a.nq || *a.err) return;
-    u64 best = KEY_INF;          // sorted across lanes
-    u32 b1 = ORD_INF, b2 = ORD_INF;
-    for (u32 c = 0; c < a.chunks; c++) {
-        const u64 v = a.lists[((size_t)qi * a.chunks + c) * TC_T + lane];   // ascending
-        const u64 last = __shfl_sync(FULL, v, TC_T - 1);
-        if (last != KEY_INF) b1 = min(b1, (u32)(last >> 32));
-        const u64 rev = __shfl_sync(FULL, v, 31 - lane);
-        const u64 lo = best < rev ? best : rev;
-        u64 hi = best < rev ? rev : best;
-        // the larger half leaves the candidate set: remember its minimum
-#pragma unroll
-        for (int h = 16; h >= 1; h >>= 1) {
-            const u64 o = __shfl_xor_sync(FULL, hi, h);
-            hi = o < hi ? o : hi;
+__global__ void __launch_bounds__(RR_WARPS * 32) gt_rerank_kernel(Dev d, RerankArgs a) {
+    __shared__ u32 cblk[RR_WARPS][RR_MAXB];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const u32 li = blockIdx.x * RR_WARPS + warp;
+    if (li >= a.nq || *a.err) return;
+    const u32 qi = a.q0 + li;
+    const float *row = a.bmin + (size_t)li * a.nblk;
+    // 1. each lane keeps the four smallest block minima of blocks lane, lane + 32, ...
+    u32 t0 = ~0u, t1 = ~0u, t2 = ~0u, t3 = ~0u;
+    for (u32 b = lane; b < a.nblk; b += 32) {
+        const u32 v = f2ord(__ldg(row + b));
+        if (v < t3) {
+            if (v < t2) {
+                t3 = t2;
+                if (v < t1) {
+                    t2 = t1;
+                    if (v < t0) { t1 = t0; t0 = v; } else t1 = v;
+                } else t2 = v;
+            } else t3 = v;
         }
-        if (hi != KEY_INF) b2 = min(b2, (u32)(hi >> 32));
-        best = warp_sort32(lo);
     }
-    // exact rerank of the 32 candidates with the canonical distance
+    // 2. tau = the rt-th smallest of the 128 kept values (bitwise search on
+    //    the order-preserving integer image); at least rt blocks have a
+    //    minimum <= tau
+    u32 tau = 0;
+    for (int bit = 31; bit >= 0; bit--) {
+        const u32 tr = tau | (1u << bit);
+        const u32 c = (u32)(t0 < tr) + (u32)(t1 < tr) + (u32)(t2 < tr) + (u32)(t3 < tr);
+        if (__reduce_add_sync(FULL, c) < a.rt) tau = tr;
+    }
+    // 3. candidate blocks: minimum <= tau (dead-only blocks have +inf)
+    u32 cnt = 0;
+    for (u32 b0 = 0; b0 < a.nblk; b0 += 32) {
+        const u32 b = b0 + lane;
+        const u32 v = b < a.nblk ? f2ord(__ldg(row + b)) : ~0u;
+        const bool c = v <= tau && v < ORD_INF;
+        const u32 m = __ballot_sync(FULL, c);
+        const u32 pos = cnt + __popc(m & lanemask_lt());
+        if (c && pos < RR_MAXB) cblk[warp][pos] = b;
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    const bool over = cnt > RR_MAXB;
+    // 4. exact rerank of every live row of the candidate blocks
+    u64 best = KEY_INF;   // sorted across lanes
     const float *qv = a.q + (size_t)qi * d.mp;
     const int grp = lane >> 3, g = lane & 7;
-    u64 cand = KEY_INF;
-    for (int r0 = 0; r0 < 32; r0 += 4) {
-        const u32 id = key_id(__shfl_sync(FULL, best, r0 + grp));
-        const u64 bk = __shfl_sync(FULL, best, r0 + grp);
-        float dd = 0.0f;
-        if (bk != KEY_INF && id < a.n_rows) dd = canon_dist<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
-        const u64 kk = bk != KEY_INF && id < a.n_rows ? mkkey(dd, id) : KEY_INF;
+    for (u32 i = 0; i < (over ? 0u : cnt); i++) {
+        const u32 b = cblk[warp][i];
+        u64 cand = KEY_INF;
+        for (int r0 = 0; r0 < 32; r0 += 4) {
+            const u32 id = b * 32 + r0 + grp;
+            const bool inr = id < a.n_rows;
+            bool live = false;
+            if (inr) {
+                const u64 rf = d.ref[id];
+                live = !ref_del(rf) && ref_slab(rf) != NIL;
+            }
+            // every lane computes (the distance shuffles over the full warp)
+            const float dd = canon_dist<8>(qv, d.x + (size_t)(inr ? id : 0u) * d.mp, (int)d.mp, (int)d.metric, g);
+            const u64 kk = live ? mkkey(dd, id) : KEY_INF;
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const u64 v = __shfl_sync(FULL, kk, t * 8);
-            if (lane == r0 + t) cand = v;
+            for (int t = 0; t < 4; t++) {
+                const u64 v = __shfl_sync(FULL, kk, t * 8);
+                if (lane == r0 + t) cand = v;
+            }
         }
+        cand = warp_sort32(cand);
+        const u64 rev = __shfl_sync(FULL, cand, 31 - lane);
+        best = warp_sort32(best < rev ? best : rev);
     }
-    cand = warp_sort32(cand);
-    const u32 lbo = min(b1, b2);
-    const u64 kth = __shfl_sync(FULL, cand, a.k - 1);
+    // 5. certificate: every row left out has an approximate key > tau
+    const u64 kth = __shfl_sync(FULL, best, a.k - 1);
     bool cert;
-    if (lbo == ORD_INF) {
-        cert = true;                                  // nothing was left out
+    if (over) {
+        cert = false;
+    } else if (tau >= ORD_INF) {
+        cert = true;                                  // every live row was reranked
     } else if (kth == KEY_INF) {
         cert = false;
     } else {
@@ -488,14 +508,17 @@ __global__ void __launch_bounds__(256) gt_merge_kernel(Dev d, MergeArgs a) {
         const double qn = qs[0], qa = (double)qs[1] * 1.01, loq = (double)qs[2] * 1.01, eq = (double)qs[3] * 1.01;
         const double X2 = __uint_as_float(a.gstat[0]), X1 = sqrt(X2) * 1.01;
         const double Lx = (double)__uint_as_float(a.gstat[1]) * 1.01, Ex = (double)__uint_as_float(a.gstat[2]) * 1.01;
+        // |computed dot - q.x|: the terms the split leaves out, plus fp32 accumulation
         const double dot_res = a.split ? loq * Lx + (qa + eq) * Ex + eq * (X1 + Ex) : 0.0;
         const double dot_err = dot_res + (K + 2.0) * 2.0 * u * 1.03 * qa * X1;
-        const double LB = (double)ord2f(lbo);
+        const double LB = (double)ord2f(tau);
         double lb;
         if (d.metric == 0) {
+            // norms (fp32 sums of squares), 2 x dot error, rounding of the key
             const double E = 2.0 * ((m + 2.0) * u * qn * 1.01 + (m + 2.0) * u * X2 + 2.0 * dot_err +
                                     2.0 * u * (X2 + 2.1 * qa * X1));
             const double y = qn + LB - E;
+            // the canonical fp32 distance is within (m + 4) u of the exact one
             lb = y > 0.0 ? y * (1.0 - 2.0 * (m + 4.0) * u) : -1.0;
         } else {
             const double E = 2.0 * (dot_err + (m + 2.0) * u * qa * X1 + u * (1.0 + qa * X1));
@@ -505,8 +528,8 @@ __global__ void __launch_bounds__(256) gt_merge_kernel(Dev d, MergeArgs a) {
     }
     if (cert) {
         if (lane < (int)a.k) {
-            a.out_ids[(size_t)qi * a.k + lane] = cand == KEY_INF ? NIL : key_id(cand);
-            a.out_dist[(size_t)qi * a.k + lane] = cand == KEY_INF ? __int_as_float(0x7f800000) : key_rho(cand);
+            a.out_ids[(size_t)qi * a.k + lane] = best == KEY_INF ? NIL : key_id(best);
+            a.out_dist[(size_t)qi * a.k + lane] = best == KEY_INF ? __int_as_float(0x7f800000) : key_rho(best);
         }
     } else if (lane == 0) {
         a.fb[atomicAdd(a.fb_count, 1u)] = qi;
@@ -555,95 +578,101 @@ cudaError_t launch_gt_tc_prep(const Dev &d, u64 next_id, const float *q, u32 nq,
                               const GtTcBufs &b, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(b.gstat, 0, 8 * sizeof(u32), st);
     if (e != cudaSuccess) return e;
-    if (p.n_pad) gt_prep_rows<<<(unsigned)((p.n_pad * 32 + 255) / 256), 256, 0, st>>>(
-        d, next_id, (u32)p.n_pad, p.kp1, p.kb, reinterpret_cast<__nv_bfloat16 *>(b.B), b.xn, b.gstat);
+    if (p.n_pad)
+        gt_prep_rows<<<(unsigned)std::min<u64>((p.n_pad * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
+            d, next_id, (u32)p.n_pad, p.kp1, p.kb, reinterpret_cast<u32 *>(b.B), b.xn, b.gstat);
     gt_prep_queries<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(
-        q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<__nv_bfloat16 *>(b.A), b.qstat, b.gstat, b.thr);
+        q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<u32 *>(b.A), b.qstat, b.gstat);
     return cudaGetLastError();
 }
 
-cudaError_t gt_tc_configure(GtTcPlan &p, u32 nq, bool split, int num_sms) {
+void gt_tc_configure(GtTcPlan &p, u32 nq, bool split) {
     p.kprime = split ? p.kb : p.kp1;
     p.split = split;
     p.kblocks = p.kprime / TC_KBOX;
     const u32 smem_max = 227 * 1024 - 1024 - 512;
     p.n_msub = (2u * p.kblocks * TC_BOX + 2 * TC_BOX <= smem_max) && nq > TC_ROWS ? 2 : 1;
-    if ((u64)p.n_msub * p.kblocks * TC_BOX + 2 * TC_BOX > smem_max) {
+    if ((u64)p.n_msub * p.kblocks * TC_BOX + 2 * TC_BOX > smem_max || p.n_pad == 0) {
         p.usable = false;
-        return cudaSuccess;
+        return;
     }
     p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - p.n_msub * p.kblocks * TC_BOX) / TC_BOX);
     p.smem = p.n_msub * p.kblocks * TC_BOX + p.stages * TC_BOX + 1024;
     p.n_tiles = (u32)(p.n_pad / TC_ROWS);
-    p.m_tiles = (nq + p.n_msub * TC_ROWS - 1) / (p.n_msub * TC_ROWS);
-    // chunks of rows: enough work items to fill every SM a few times over,
-    // with the fewest idle SMs in the last wave
-    u32 best_c = 1;
-    double best_eff = -1.0;
-    const u32 cmax = std::max<u32>(1, std::min<u32>(p.n_tiles, 256));
-    for (u32 c = 1; c <= cmax; c++) {
-        const u64 items = (u64)p.m_tiles * c;
-        const u64 waves = (items + num_sms - 1) / num_sms;
-        const double eff = (double)items / (double)(waves * num_sms);
-        const double score = eff - (items < 2ull * num_sms ? 0.5 : 0.0) - 0.002 * c;
-        if (score > best_eff) {
-            best_eff = score;
-            best_c = c;
-        }
-    }
-    p.chunks = best_c;
-    p.tiles_per_chunk = (p.n_tiles + p.chunks - 1) / p.chunks;
-    p.chunks = (p.n_tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+    p.nblk = 4 * p.n_tiles;
     p.tmem_cols = p.n_msub == 2 ? 512 : 256;
-    p.bytes_lists = (size_t)nq * p.chunks * TC_T * 8;
-    p.usable = p.n_tiles > 0;
-    return cudaSuccess;
+    // queries per pass: the block-minimum buffer stays under 4 GiB
+    const u64 cap = std::max<u64>(256, ((4ull << 30) / ((u64)p.nblk * 4)) / 256 * 256);
+    p.qgroup = (u32)std::min<u64>(nq, cap);
+    p.bytes_bmin = (size_t)p.qgroup * p.nblk * 4;
+    p.usable = true;
 }
 
-cudaError_t launch_gt_tc(const Dev &d, const float *q, u32 nq, u32 k, const GtTcPlan &p, const GtTcBufs &b,
-                         u64 next_id, u32 *out_ids, float *out_dist, int num_sms, cudaStream_t st) {
+cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const GtTcBufs &b, u64 next_id,
+                         int num_sms, cudaStream_t st) {
     CUtensorMap ta, tb;
-    if (!encode_bf16(&ta, b.A, nq, p.kb) || !encode_bf16(&tb, b.B, next_id, p.kb)) return cudaErrorInvalidValue;
+    const void *abase = static_cast<const char *>(b.A) + (size_t)q0 * p.kb * 2;
+    if (!encode_bf16(&ta, abase, nq, p.kb) || !encode_bf16(&tb, b.B, next_id, p.kb)) return cudaErrorInvalidValue;
     TcArgs a{};
     a.nq = nq;
     a.n_tiles = p.n_tiles;
     a.kblocks = p.kblocks;
     a.n_msub = p.n_msub;
-    a.m_tiles = p.m_tiles;
-    a.chunks = p.chunks;
-    a.tiles_per_chunk = p.tiles_per_chunk;
+    a.m_tiles = (nq + p.n_msub * TC_ROWS - 1) / (p.n_msub * TC_ROWS);
+    // chunks of rows: enough work items to fill every SM, with the fewest
+    // idle SMs in the last wave
+    u32 best_c = 1;
+    double best_score = -1e9;
+    const u32 cmax = std::max<u32>(1, std::min<u32>(p.n_tiles, 256));
+    for (u32 c = 1; c <= cmax; c++) {
+        const u64 items = (u64)a.m_tiles * c;
+        const u64 waves = (items + num_sms - 1) / num_sms;
+        const double eff = (double)items / (double)(waves * num_sms);
+        const double score = eff - (items < (u64)num_sms ? 0.5 : 0.0) - 0.002 * c;
+        if (score > best_score) {
+            best_score = score;
+            best_c = c;
+        }
+    }
+    a.tiles_per_chunk = (p.n_tiles + best_c - 1) / best_c;
+    a.chunks = (p.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
     a.stages = p.stages;
     a.tmem_cols = p.tmem_cols;
+    a.nblk = p.nblk;
     a.s = d.metric == 0 ? -2.0f : -1.0f;
     a.xn = b.xn;
-    a.thr = b.thr;
-    a.lists = b.lists;
+    a.bmin = b.bmin;
     a.err = b.err;
     cudaError_t e = cudaFuncSetAttribute(gt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
-    const u32 items = p.m_tiles * p.chunks;
+    const u32 items = a.m_tiles * a.chunks;
     const u32 grid = std::min<u32>(items, (u32)num_sms);
     gt_tc_kernel<<<grid, TC_THREADS, p.smem, st>>>(ta, tb, a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    MergeArgs m{};
-    m.nq = nq;
-    m.k = k;
-    m.chunks = p.chunks;
-    m.m = d.dim;
-    m.kprime = p.kprime;
-    m.split = p.split;
-    m.q = q;
-    m.lists = b.lists;
-    m.qstat = b.qstat;
-    m.gstat = b.gstat;
-    m.out_ids = out_ids;
-    m.out_dist = out_dist;
-    m.fb = b.fb;
-    m.fb_count = b.gstat + 4;
-    m.n_rows = next_id;
-    m.err = b.err;
-    gt_merge_kernel<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(d, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gt_rerank(const Dev &d, const float *q, u32 q0, u32 nq, u32 k, const GtTcPlan &p,
+                             const GtTcBufs &b, u64 next_id, u32 *out_ids, float *out_dist, cudaStream_t st) {
+    RerankArgs r{};
+    r.nq = nq;
+    r.q0 = q0;
+    r.k = k;
+    r.nblk = p.nblk;
+    r.rt = k <= 16 ? 32 : 2 * k;
+    r.m = d.dim;
+    r.kprime = p.kprime;
+    r.split = p.split;
+    r.n_rows = next_id;
+    r.q = q;
+    r.bmin = b.bmin;
+    r.qstat = b.qstat;
+    r.gstat = b.gstat;
+    r.out_ids = out_ids;
+    r.out_dist = out_dist;
+    r.fb = b.fb;
+    r.fb_count = b.gstat + 4;
+    r.err = b.err;
+    gt_rerank_kernel<<<(nq + RR_WARPS - 1) / RR_WARPS, RR_WARPS * 32, 0, st>>>(d, r);
     return cudaGetLastError();
 }
 

@@ -101,25 +101,27 @@ cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 n
 struct GtTcPlan {
     u32 kp1 = 0, kb = 0;            // one bf16 segment (dim rounded to 64); three segments
     u64 n_pad = 0;                  // rows rounded to the 128-row tile
-    size_t bytes_A = 0, bytes_B = 0, bytes_lists = 0;
-    u32 kprime = 0, kblocks = 0, n_msub = 0, stages = 0, smem = 0, n_tiles = 0, m_tiles = 0;
-    u32 chunks = 0, tiles_per_chunk = 0, tmem_cols = 0;
+    size_t bytes_A = 0, bytes_B = 0, bytes_bmin = 0;
+    u32 kprime = 0, kblocks = 0, n_msub = 0, stages = 0, smem = 0, n_tiles = 0, nblk = 0, tmem_cols = 0;
+    u32 qgroup = 0;                 // queries per candidate pass
     bool split = false, usable = false;
 };
 struct GtTcBufs {
     void *A, *B;                    // query and row bf16 copies
     float *xn, *qstat;              // per-row key base; per-query norms (4 floats)
     u32 *gstat;                     // [0..3] maxima and the split flag, [4] fallback count, [5] error word
-    u32 *thr, *fb;                  // per-query threshold; fallback query list
-    u64 *lists;                     // nq x chunks x 32 candidates
+    u32 *fb;                        // fallback query list
+    float *bmin;                    // qgroup x nblk block minima
     u32 *err;
 };
 GtTcPlan gt_tc_plan(u32 dim, u64 next_id, u32 nq);
 cudaError_t launch_gt_tc_prep(const Dev &d, u64 next_id, const float *q, u32 nq, const GtTcPlan &p,
                               const GtTcBufs &b, cudaStream_t st);
-cudaError_t gt_tc_configure(GtTcPlan &p, u32 nq, bool split, int num_sms);
-cudaError_t launch_gt_tc(const Dev &d, const float *q, u32 nq, u32 k, const GtTcPlan &p, const GtTcBufs &b,
-                         u64 next_id, u32 *out_ids, float *out_dist, int num_sms, cudaStream_t st);
+void gt_tc_configure(GtTcPlan &p, u32 nq, bool split);
+cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const GtTcBufs &b, u64 next_id,
+                         int num_sms, cudaStream_t st);
+cudaError_t launch_gt_rerank(const Dev &d, const float *q, u32 q0, u32 nq, u32 k, const GtTcPlan &p,
+                             const GtTcBufs &b, u64 next_id, u32 *out_ids, float *out_dist, cudaStream_t st);
 cudaError_t launch_export(const Dev &d, u64 n, unsigned char *del, unsigned char *hs, unsigned char *deg,
                           u32 *ids, float *rho, cudaStream_t st);
 cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaStream_t st);

@@ -44,7 +44,8 @@ def test_tensor_ground_truth_matches_exact(oracle_mod, wname, n, k, path):
     assert info["path"] == path
     np.testing.assert_array_equal(ti, ci)
     np.testing.assert_array_equal(td.view(np.uint32), cd.view(np.uint32))
-    assert info["fallback_queries"] <= len(plan.queries) // 10, info
+    if k <= 16:   # with k = 32 = the candidate count there is no margin to certify
+        assert info["fallback_queries"] <= len(plan.queries) // 10, info
     # the oracle ranks in fp64: equal ids up to fp32 ties, close distances
     o = oracle_mod.Oracle(base.dim, base.metric, base.degree, n + 10, build_beam=16)
     o.insert(plan.base)
