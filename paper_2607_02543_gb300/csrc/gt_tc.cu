@@ -11,9 +11,9 @@
 //      representable in bf16, e.g. integers up to 256) only the first
 //      segment is used, otherwise all three (hi.hi + hi.lo + lo.hi).
 //   2. gt_tc_kernel: persistent CTAs; TMA (cp.async.bulk.tensor, 128-byte
-//      swizzle) streams 128-row boxes of the row copy through a shared
+//      swizzle) streams 256-row boxes of the row copy through a shared
 //      memory ring while the query tile stays resident; one thread issues
-//      tcgen05.mma (M = N = 128, bf16 -> fp32) into a double-buffered TMEM
+//      tcgen05.mma (M = 128, N = 256, bf16 -> fp32) into a double-buffered TMEM
 //      accumulator; eight epilogue warps read it with tcgen05.ld and write,
 //      per query and per block of 32 rows, the smallest approximate key
 //      key = |x|^2 - 2 q.x (L2) or -q.x (IP); dead rows have key +inf.
@@ -39,20 +39,29 @@
 namespace etale {
 namespace {
 
-constexpr int TC_ROWS = 128;                      // MMA M (queries) and N (rows)
+constexpr int TC_ROWS = 128;                      // MMA M: queries per query sub-tile
+constexpr int TC_ACC = 256;                       // TMEM columns per accumulator buffer
 constexpr int TC_KBOX = 64;                       // bf16 per 128-byte swizzle row
-constexpr u32 TC_BOX = TC_ROWS * TC_KBOX * 2;     // 16 KB per TMA box
+constexpr u32 TC_BOX = TC_ROWS * TC_KBOX * 2;     // 16 KB per 128-row TMA box
+// Tile shapes: one query sub-tile (M = 128) against 256 rows, or two
+// (M = 2 x 128) against 128 rows; both fill a 256-column accumulator.  The
+// first reads 96 B of operands from shared memory per MMA cycle instead of
+// 128 B (the SM's shared-memory bandwidth), the second half as many rows
+// from L2 per query.  On the 1M x 128 workload (10k queries) the first ran
+// the candidate pass in 3.5 ms, the second in 4.1 ms, so the plan takes the
+// first; the kernel keeps both.
 constexpr int TC_MAX_STAGES = 12;
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;
 constexpr u32 ORD_INF = 0xFF800000u;              // f2ord(+inf)
 // kind::f16 instruction descriptor: fp32 accumulator (bits 4-5 = 1), A and B
 // bf16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24
-constexpr u32 TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(TC_ROWS >> 3) << 17) |
-                         ((u32)(TC_ROWS >> 4) << 24);
+__host__ __device__ constexpr u32 tc_idesc(u32 n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((u32)(TC_ROWS >> 4) << 24);
+}
 
 struct TcArgs {
-    u32 nq, n_tiles, kblocks, n_msub, m_tiles, chunks, tiles_per_chunk, stages, tmem_cols, nblk;
+    u32 nq, n_tiles, kblocks, n_msub, bn, m_tiles, chunks, tiles_per_chunk, stages, nblk;
     float s;              // -2 (L2) or -1 (IP)
     const float *xn;      // n_tiles * 128 key bases (+inf for dead rows and padding)
     float *bmin;          // nq x nblk: smallest key of each block of 32 rows
@@ -78,11 +87,11 @@ __device__ __forceinline__ u64 sw128_desc(u32 saddr) {
     return (u64)((saddr & 0x3FFFFu) >> 4) | ((u64)1 << 16) | ((u64)(1024 >> 4) << 32) | ((u64)1 << 46) |
            ((u64)2 << 61);
 }
-__device__ __forceinline__ void tc_mma(u32 d, u64 a, u64 b, u32 acc) {
+__device__ __forceinline__ void tc_mma(u32 d, u64 a, u64 b, u32 idesc, u32 acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void tc_commit(u64 *bar) {
@@ -90,12 +99,13 @@ __device__ __forceinline__ void tc_commit(u64 *bar) {
                      smem_addr(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(u32 taddr, u32 (&r)[32]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+// 64 consecutive TMEM columns of this warp's 32 lanes; completes at tmem_wait().
+__device__ __forceinline__ void tmem_ld64(u32 taddr, u32 *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
                  : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- candidate pass ---------------------------------------------------------
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -103,6 +113,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ unsigned char tc_raw[];
     __shared__ __align__(8) u64 full[TC_MAX_STAGES], empty[TC_MAX_STAGES];
     __shared__ __align__(8) u64 a_full, a_empty, t_full[2], t_empty[2], drain;
+    __shared__ __align__(16) float xs[2][TC_ACC];    // key bases of the tile in TMEM buffer b
     __shared__ u32 tmem_base;
     __shared__ volatile int abort_flag;
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
@@ -110,6 +121,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *sB = sm + (size_t)a.n_msub * a.kblocks * TC_BOX;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const u32 items = a.m_tiles * a.chunks;
+    const u32 bbox = a.bn * TC_KBOX * 2;            // bytes of one row box
 
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < a.stages; i++) {
@@ -119,8 +131,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_init(&a_full, 1);
         mbar_init(&a_empty, 1);
         for (int b = 0; b < 2; b++) {
-            mbar_init(&t_full[b], 1);
-            mbar_init(&t_empty[b], 4 * a.n_msub);
+            mbar_init(&t_full[b], 2);   // the MMA commit + the key-base copy
+            mbar_init(&t_empty[b], TC_EPI_WARPS);
         }
         mbar_init(&drain, 1);
         abort_flag = 0;
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                     "r"(a.tmem_cols)
+                     "r"(2 * TC_ACC)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -165,8 +177,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (u32 t = t0; t < t1 && !abort_flag; t++) {
                     for (u32 kb = 0; kb < a.kblocks; kb++) {
                         if (!mbar_wait(&empty[stage], ph ^ 1, WAIT_LIMIT)) { fail(); break; }
-                        mbar_expect_tx(&full[stage], TC_BOX);
-                        tma_load_2d(sB + (size_t)stage * TC_BOX, &tmB, (int)(kb * TC_KBOX), (int)(t * TC_ROWS),
+                        mbar_expect_tx(&full[stage], bbox);
+                        tma_load_2d(sB + (size_t)stage * bbox, &tmB, (int)(kb * TC_KBOX), (int)(t * a.bn),
                                     &full[stage]);
                         issued |= 1u << stage;
                         lastpar = (lastpar & ~(1u << stage)) | (ph << stage);
@@ -196,17 +208,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const u32 b = tcount & 1;
                     if (!mbar_wait(&t_empty[b], ((tcount >> 1) & 1) ^ 1, WAIT_LIMIT)) { fail(); break; }
                     tc_fence_after();
+                    // the tile's key bases travel with the accumulator: same barrier
+                    mbar_expect_tx(&t_full[b], a.bn * 4);
+                    bulk_g2s(xs[b], a.xn + (size_t)t * a.bn, a.bn * 4, &t_full[b]);
                     bool ok = true;
                     for (u32 kb = 0; kb < a.kblocks; kb++) {
                         if (!mbar_wait(&full[stage], ph, WAIT_LIMIT)) { ok = false; break; }
                         tc_fence_after();
-                        const u32 bb = smem_addr(sB + (size_t)stage * TC_BOX);
+                        const u32 bb = smem_addr(sB + (size_t)stage * bbox);
+                        const u32 idesc = tc_idesc(a.bn);
 #pragma unroll
                         for (u32 k = 0; k < TC_KBOX / 16; k++) {
                             const u64 bd = sw128_desc(bb + k * 32);
                             for (u32 s = 0; s < a.n_msub; s++) {
                                 const u32 aa = smem_addr(sA + (size_t)(s * a.kblocks + kb) * TC_BOX) + k * 32;
-                                tc_mma(tmem + (b * a.n_msub + s) * TC_ROWS, sw128_desc(aa), bd, (kb | k) != 0);
+                                tc_mma(tmem + b * TC_ACC + s * TC_ROWS, sw128_desc(aa), bd, idesc, (kb | k) != 0);
                             }
                         }
                         tc_commit(&empty[stage]);
@@ -215,19 +231,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             ph ^= 1;
                         }
                     }
-                    if (!ok) { fail(); break; }
                     tc_commit(&t_full[b]);
+                    if (!ok) {
+                        tcount++;   // this tile's key-base copy is in flight too
+                        fail();
+                        break;
+                    }
                 }
                 tc_commit(&a_empty);
             }
-            // all MMAs issued by this thread are complete before TMEM is freed
+            // all MMAs and key-base copies issued by this thread are complete
+            // before TMEM and shared memory are released
             tc_commit(&drain);
             mbar_wait(&drain, 0, WAIT_LIMIT);
+            for (u32 b = 0; b < 2 && b < tcount; b++) {
+                const u32 uses = (tcount - b + 1) / 2;     // tiles that used buffer b
+                mbar_wait(&t_full[b], (uses - 1) & 1, WAIT_LIMIT);
+            }
         }
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31; lane = one query ----
-        const int ew = warp - 2, ms = ew >> 2, quarter = warp & 3;
-        if ((u32)ms < a.n_msub) {
+        // group g of four warps: query sub-tile g (two sub-tiles) or row half g (one)
+        const int ew = warp - 2, grp = ew >> 2, quarter = warp & 3;
+        const int ms = a.n_msub == 2 ? grp : 0, half = a.n_msub == 2 ? 0 : grp;
+        {
             const int row = quarter * 32 + lane;
             u32 tcount = 0;
             bool ok = true;
@@ -243,28 +270,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const bool got = !abort_flag && mbar_wait(&t_full[b], (tcount >> 1) & 1, WAIT_LIMIT);
                     if (!__all_sync(FULL, got)) { ok = false; break; }
                     tc_fence_after();
-                    const u32 tbase = tmem + ((u32)(quarter * 32) << 16) + (b * a.n_msub + ms) * TC_ROWS;
+                    const u32 tbase = tmem + ((u32)(quarter * 32) << 16) + b * TC_ACC + grp * TC_ROWS;
                     float bm[TC_ROWS / 32];
+                    {
+                        u32 r[TC_ROWS];
+                        tmem_ld64(tbase, r);
+                        tmem_ld64(tbase + 64, r + 64);
+                        tmem_wait();
+                        const float4 *x4 = reinterpret_cast<const float4 *>(xs[b] + half * TC_ROWS);
 #pragma unroll
-                    for (int c = 0; c < TC_ROWS / 32; c++) {
-                        u32 r[32];
-                        tmem_ld32(tbase + c * 32, r);
-                        const float4 *xn4 = reinterpret_cast<const float4 *>(a.xn + (size_t)t * TC_ROWS + c * 32);
-                        float m0 = __int_as_float(0x7f800000), m1 = m0;
+                        for (int c = 0; c < TC_ROWS / 32; c++) {
+                            float m0 = __int_as_float(0x7f800000), m1 = m0;
 #pragma unroll
-                        for (int j4 = 0; j4 < 8; j4++) {
-                            const float4 v = __ldg(xn4 + j4);
-                            m0 = fminf(m0, fmaf(a.s, __uint_as_float(r[4 * j4 + 0]), v.x));
-                            m1 = fminf(m1, fmaf(a.s, __uint_as_float(r[4 * j4 + 1]), v.y));
-                            m0 = fminf(m0, fmaf(a.s, __uint_as_float(r[4 * j4 + 2]), v.z));
-                            m1 = fminf(m1, fmaf(a.s, __uint_as_float(r[4 * j4 + 3]), v.w));
+                            for (int j4 = 0; j4 < 8; j4++) {
+                                const float4 v = x4[c * 8 + j4];
+                                const u32 *rr = r + c * 32 + 4 * j4;
+                                m0 = fminf(m0, fmaf(a.s, __uint_as_float(rr[0]), v.x));
+                                m1 = fminf(m1, fmaf(a.s, __uint_as_float(rr[1]), v.y));
+                                m0 = fminf(m0, fmaf(a.s, __uint_as_float(rr[2]), v.z));
+                                m1 = fminf(m1, fmaf(a.s, __uint_as_float(rr[3]), v.w));
+                            }
+                            bm[c] = fminf(m0, m1);
                         }
-                        bm[c] = fminf(m0, m1);
                     }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&t_empty[b]);
-                    if (valid) dst[t] = make_float4(bm[0], bm[1], bm[2], bm[3]);
+                    if (valid) dst[t * (a.bn / TC_ROWS) + half] = make_float4(bm[0], bm[1], bm[2], bm[3]);
                 }
             }
             if (!ok && !abort_flag) fail();
@@ -275,7 +307,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_ACC)
                      : "memory");
     }
 }
@@ -550,12 +582,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode_bf16(CUtensorMap *m, const void *base, u64 rows, u32 cols) {
+bool encode_bf16(CUtensorMap *m, const void *base, u64 rows, u32 cols, u32 box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {TC_KBOX, TC_ROWS};
+    cuuint32_t box[2] = {TC_KBOX, box_rows};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -568,7 +600,7 @@ GtTcPlan gt_tc_plan(u32 dim, u64 next_id, u32 nq) {
     GtTcPlan p{};
     p.kp1 = (dim + TC_KBOX - 1) / TC_KBOX * TC_KBOX;
     p.kb = 3 * p.kp1;
-    p.n_pad = (next_id + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
+    p.n_pad = (next_id + TC_ACC - 1) / TC_ACC * TC_ACC;
     p.bytes_B = (size_t)next_id * p.kb * 2;
     p.bytes_A = (size_t)nq * p.kb * 2;
     return p;
@@ -590,17 +622,18 @@ void gt_tc_configure(GtTcPlan &p, u32 nq, bool split) {
     p.kprime = split ? p.kb : p.kp1;
     p.split = split;
     p.kblocks = p.kprime / TC_KBOX;
-    const u32 smem_max = 227 * 1024 - 1024 - 512;
-    p.n_msub = (2u * p.kblocks * TC_BOX + 2 * TC_BOX <= smem_max) && nq > TC_ROWS ? 2 : 1;
-    if ((u64)p.n_msub * p.kblocks * TC_BOX + 2 * TC_BOX > smem_max || p.n_pad == 0) {
+    const u32 smem_max = 227 * 1024 - 1024 - 4096;   // alignment slack, static shared memory
+    p.n_msub = 1;
+    p.bn = TC_ACC / p.n_msub;
+    const u32 bbox = p.bn * TC_KBOX * 2;
+    if ((u64)p.n_msub * p.kblocks * TC_BOX + 2ull * bbox > smem_max || p.n_pad == 0) {
         p.usable = false;
         return;
     }
-    p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - p.n_msub * p.kblocks * TC_BOX) / TC_BOX);
-    p.smem = p.n_msub * p.kblocks * TC_BOX + p.stages * TC_BOX + 1024;
-    p.n_tiles = (u32)(p.n_pad / TC_ROWS);
-    p.nblk = 4 * p.n_tiles;
-    p.tmem_cols = p.n_msub == 2 ? 512 : 256;
+    p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - p.n_msub * p.kblocks * TC_BOX) / bbox);
+    p.smem = p.n_msub * p.kblocks * TC_BOX + p.stages * bbox + 1024;
+    p.n_tiles = (u32)(p.n_pad / p.bn);
+    p.nblk = (u32)(p.n_pad / 32);
     // queries per pass: the block-minimum buffer stays under 4 GiB
     const u64 cap = std::max<u64>(256, ((4ull << 30) / ((u64)p.nblk * 4)) / 256 * 256);
     p.qgroup = (u32)std::min<u64>(nq, cap);
@@ -612,12 +645,14 @@ cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const 
                          int num_sms, cudaStream_t st) {
     CUtensorMap ta, tb;
     const void *abase = static_cast<const char *>(b.A) + (size_t)q0 * p.kb * 2;
-    if (!encode_bf16(&ta, abase, nq, p.kb) || !encode_bf16(&tb, b.B, next_id, p.kb)) return cudaErrorInvalidValue;
+    if (!encode_bf16(&ta, abase, nq, p.kb, TC_ROWS) || !encode_bf16(&tb, b.B, next_id, p.kb, p.bn))
+        return cudaErrorInvalidValue;
     TcArgs a{};
     a.nq = nq;
     a.n_tiles = p.n_tiles;
     a.kblocks = p.kblocks;
     a.n_msub = p.n_msub;
+    a.bn = p.bn;
     a.m_tiles = (nq + p.n_msub * TC_ROWS - 1) / (p.n_msub * TC_ROWS);
     // chunks of rows: enough work items to fill every SM, with the fewest
     // idle SMs in the last wave
@@ -637,7 +672,6 @@ cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const 
     a.tiles_per_chunk = (p.n_tiles + best_c - 1) / best_c;
     a.chunks = (p.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
     a.stages = p.stages;
-    a.tmem_cols = p.tmem_cols;
     a.nblk = p.nblk;
     a.s = d.metric == 0 ? -2.0f : -1.0f;
     a.xn = b.xn;

@@ -100,9 +100,9 @@ cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 n
 // Tensor-core ground truth (gt_tc.cu).
 struct GtTcPlan {
     u32 kp1 = 0, kb = 0;            // one bf16 segment (dim rounded to 64); three segments
-    u64 n_pad = 0;                  // rows rounded to the 128-row tile
+    u64 n_pad = 0;                  // rows rounded to 256
     size_t bytes_A = 0, bytes_B = 0, bytes_bmin = 0;
-    u32 kprime = 0, kblocks = 0, n_msub = 0, stages = 0, smem = 0, n_tiles = 0, nblk = 0, tmem_cols = 0;
+    u32 kprime = 0, kblocks = 0, n_msub = 0, bn = 0, stages = 0, smem = 0, n_tiles = 0, nblk = 0;
     u32 qgroup = 0;                 // queries per candidate pass
     bool split = false, usable = false;
 };
