@@ -83,7 +83,11 @@ typedef struct {
     uint32_t gt;          /* etale_ground_truth: 0 default (tensor-core
                              candidate pass with an exact certified rerank
                              where it applies), 1 CUDA cores only            */
-    uint32_t reserved[1];
+    uint32_t seed;        /* entry-set seeding of fp32 BeamSearches: 0 default
+                             (tensor-core candidate pass with an exact
+                             certified rerank, same seeds as the CUDA-core
+                             kernel; not in concurrent mode, captured
+                             graphs or reduced precision), 1 CUDA cores only */
 } etale_config;
 
 typedef enum { ETALE_PREC_FP32 = 0, ETALE_PREC_BF16 = 1, ETALE_PREC_FP8 = 2 } etale_precision;

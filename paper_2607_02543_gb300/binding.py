@@ -33,7 +33,7 @@ class Config(C.Structure):
                 ("pool_slabs", C.c_uint64), ("n_entry", C.c_uint32), ("mode", C.c_uint32),
                 ("cas_budget", C.c_uint32), ("stage_kb", C.c_uint32), ("gram", C.c_uint32),
                 ("copies", C.c_uint32), ("rerank", C.c_uint32), ("gt", C.c_uint32),
-                ("reserved", C.c_uint32 * 1)]
+                ("seed", C.c_uint32)]
 
 
 class Tuning(C.Structure):
@@ -143,7 +143,7 @@ class Index:
                  alpha: float = 0.0, max_hops: int = 0, max_cand: int = 0, refine: str = "default",
                  max_batch: int = 0, pool_slabs: int = 0, n_entry: int = 0, mode: str = "deterministic",
                  cas_budget: int = 0, stage_kb: int = 0, gram: str = "default", copies: tuple = (),
-                 rerank: int = 0, gt: str = "default"):
+                 rerank: int = 0, gt: str = "default", seed: str = "default"):
         self.lib = load()
         cfg = Config()
         self.lib.etale_config_default(C.byref(cfg))
@@ -162,6 +162,7 @@ class Index:
         cfg.stage_kb = stage_kb
         cfg.gram = {"default": 0, "canonical": 1, "tensor": 2}[gram]
         cfg.gt = {"default": 0, "cuda_cores": 1}[gt]
+        cfg.seed = {"default": 0, "cuda_cores": 1}[seed]
         cfg.copies = (1 if "bf16" in copies else 0) | (2 if "fp8" in copies else 0)
         if rerank:
             cfg.rerank = rerank

@@ -99,6 +99,9 @@ struct etale_index {
     DevBuf gt_A, gt_B, gt_xn, gt_qstat, gt_gstat, gt_fb, gt_bmin;
     u32 gt_path = 0;
     u64 gt_fallbacks = 0;
+    // seeding on tensor cores
+    DevBuf sd_E, sd_en, sd_estat, sd_A, sd_qstat, sd_keys, sd_fb, sd_ctr;
+    bool seed_tc = false;   // configured and the shapes fit
     u64 *host_ctr_s = nullptr;        // pinned, search side
     u64 *host_ctr_st = nullptr;       // pinned, etale_stats
     cudaStream_t stat_stream = nullptr;
@@ -122,6 +125,18 @@ struct etale_index {
     double pms[ETALE_PH_COUNT] = {0};
     u64 pcnt[ETALE_PH_COUNT] = {0};
 
+    SeedTcBufs seed_bufs() const {
+        SeedTcBufs b{};
+        b.E = sd_E.p;
+        b.A = sd_A.p;
+        b.en = static_cast<float *>(sd_en.p);
+        b.qstat = static_cast<float *>(sd_qstat.p);
+        b.keys = static_cast<float *>(sd_keys.p);
+        b.estat = static_cast<u32 *>(sd_estat.p);
+        b.fb = static_cast<u32 *>(sd_fb.p);
+        b.ctr = static_cast<u32 *>(sd_ctr.p);
+        return b;
+    }
     Dev dev() const {
         Dev d;
         d.x = x; d.ref = ref; d.slab = slab; d.free_stack = free_stack; d.retired = retired; d.ctr = ctr;
@@ -331,6 +346,13 @@ etale_status recompute_entries(etale_index *idx, cudaStream_t st) {
     CK(launch_entries_select(d, n, as<u32>(idx->live_flags), as<u32>(idx->live_rank), idx->live, S, st),
        "entries select");
     g_kernel_launches += 3;
+    if (idx->seed_tc) {
+        const SeedTcPlan p = seed_tc_plan(idx->dim, S, 0);
+        if (!grow(idx->sd_E, p.bytes_E) || !grow(idx->sd_en, (size_t)p.s_pad * 4) || !grow(idx->sd_estat, 64))
+            return idx->fail(ETALE_ENOMEM, "entry-set copy");
+        CK(launch_seed_tc_entries(d, S, p, idx->seed_bufs(), st), "entry-set copy");
+        g_kernel_launches++;
+    }
     return ETALE_OK;
 }
 
@@ -403,6 +425,26 @@ etale_status size_batch_scratch(etale_index *idx, u64 b) {
     return ok ? ETALE_OK : idx->fail(ETALE_ENOMEM, "scratch allocation (insert batch of %llu)", (unsigned long long)b);
 }
 
+// Seeds of nq BeamSearches (top-L of the entry set): tensor cores with a
+// certified exact rerank when they apply, else the CUDA-core kernel; both
+// give the same seeds.  Returns the launches made.
+static etale_status seed_batch(etale_index *idx, const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, u32 prec,
+                               cudaStream_t st) {
+    const u32 S = idx->n_entries;
+    if (prec == 0 && idx->seed_tc && !idx->concurrent && S > 0 && nq >= 32) {
+        const SeedTcPlan p = seed_tc_plan(idx->dim, S, nq);
+        if (!grow(idx->sd_A, p.bytes_A) || !grow(idx->sd_qstat, (size_t)nq * 16) ||
+            !grow(idx->sd_keys, p.bytes_keys) || !grow(idx->sd_fb, (size_t)nq * 4) || !grow(idx->sd_ctr, 64))
+            return idx->fail(ETALE_ENOMEM, "seed staging");
+        CK(launch_seed_tc(d, q, nq, S, L, seed, p, idx->seed_bufs(), idx->num_sms, st), "seed (tensor)");
+        g_kernel_launches += 4;
+        return ETALE_OK;
+    }
+    CK(launch_seed(d, q, nq, L, seed, st, prec), "seed");
+    g_kernel_launches++;
+    return ETALE_OK;
+}
+
 etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st) {
     Dev d = idx->dev();
     const u32 L = idx->cfg.build_beam;
@@ -415,7 +457,8 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     if (!grow(idx->seed, (size_t)b * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
     {
         PhaseScope ps(idx, ETALE_PH_SEED, st);
-        CK(launch_seed(d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed), st), "insert seed");
+        etale_status s0 = seed_batch(idx, d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed), 0, st);
+        if (s0 != ETALE_OK) return s0;
     }
     {
         PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
@@ -424,7 +467,7 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
                          idx->num_sms, st),
            "insert search");
     }
-    g_kernel_launches += 2;
+    g_kernel_launches += 1;
     // 2. forward edges, own slab, offers
     etale_status s = ensure_pool(idx, b, st);
     if (s != ETALE_OK) return s;
@@ -526,9 +569,10 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         cfg.copies = cfg_in->copies;
         if (cfg_in->rerank) cfg.rerank = cfg_in->rerank;
         cfg.gt = cfg_in->gt;
+        cfg.seed = cfg_in->seed;
     }
-    if (cfg.gt > 1) {
-        t_last_error = "gt must be 0 or 1";
+    if (cfg.gt > 1 || cfg.seed > 1) {
+        t_last_error = "gt and seed must be 0 or 1";
         return ETALE_EINVAL;
     }
     if (cfg.copies > 3) {
@@ -557,6 +601,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
     }
     etale_index *idx = new etale_index();
     idx->cfg = cfg;
+    idx->seed_tc = cfg.seed == 0 && seed_tc_plan(dim, cfg.n_entry, 0).usable;
     idx->dim = dim;
     idx->mp = (dim + 3) / 4 * 4;
     idx->R = degree;
@@ -946,8 +991,9 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
         const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
         if (!grow(idx->s_seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
         if (prof) prof_begin(idx, ETALE_PH_SEED, st);
-        CK(launch_seed(d, qpad, (u32)nq, L, as<u64>(idx->s_seed), st, idx->search_prec), "query seed");
+        s = seed_batch(idx, d, qpad, (u32)nq, L, as<u64>(idx->s_seed), idx->search_prec, st);
         if (prof) prof_end(idx, st);
+        if (s != ETALE_OK) return s;
         if (prof) prof_begin(idx, ETALE_PH_SEARCH_QUERY, st);
         CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->s_seed), idx->tune,
                          idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
@@ -959,7 +1005,6 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
             CK(cudaEventRecord(idx->search_ev, st), "record search event");
             idx->search_ev_valid = true;
         }
-        g_kernel_launches++;   // seed
     }
     g_kernel_launches++;       // query ingest
     if (!dev_out) {

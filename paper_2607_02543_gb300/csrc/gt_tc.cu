@@ -61,10 +61,12 @@ __host__ __device__ constexpr u32 tc_idesc(u32 n) {
 }
 
 struct TcArgs {
-    u32 nq, n_tiles, kblocks, n_msub, bn, m_tiles, chunks, tiles_per_chunk, stages, nblk;
+    u32 nq, n_tiles, kblocks, n_msub, bn, m_tiles, chunks, tiles_per_chunk, stages;
+    u32 all_keys;         // 0: smallest key per block of 32 rows; 1: every key
+    u32 ld;               // row length of the output (blocks or keys)
     float s;              // -2 (L2) or -1 (IP)
-    const float *xn;      // n_tiles * 128 key bases (+inf for dead rows and padding)
-    float *bmin;          // nq x nblk: smallest key of each block of 32 rows
+    const float *xn;      // n_tiles * bn key bases (+inf for dead rows and padding)
+    float *out;           // nq x ld
     u32 *err;
 };
 
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
                 const u32 q = (mt * a.n_msub + ms) * TC_ROWS + row;
                 const bool valid = q < a.nq;
-                float4 *dst = reinterpret_cast<float4 *>(a.bmin + (size_t)(valid ? q : 0) * a.nblk);
+                float4 *dst = reinterpret_cast<float4 *>(a.out + (size_t)(valid ? q : 0) * a.ld);
                 for (u32 t = t0; t < t1; t++, tcount++) {
                     const u32 b = tcount & 1;
                     // every lane waits; the warp goes on together (tcgen05.ld is .sync.aligned)
@@ -272,6 +274,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     const u32 tbase = tmem + ((u32)(quarter * 32) << 16) + b * TC_ACC + grp * TC_ROWS;
                     float bm[TC_ROWS / 32];
+                    if (a.all_keys) {
+                        u32 r[TC_ROWS];
+                        tmem_ld64(tbase, r);
+                        tmem_ld64(tbase + 64, r + 64);
+                        tmem_wait();
+                        const float4 *x4 = reinterpret_cast<const float4 *>(xs[b] + half * TC_ROWS);
+                        float4 *o4 = dst + (size_t)(t * a.bn + half * TC_ROWS) / 4;
+#pragma unroll
+                        for (int j4 = 0; j4 < TC_ROWS / 4; j4++) {
+                            const float4 v = x4[j4];
+                            const u32 *rr = r + 4 * j4;
+                            const float4 kv = make_float4(fmaf(a.s, __uint_as_float(rr[0]), v.x),
+                                                          fmaf(a.s, __uint_as_float(rr[1]), v.y),
+                                                          fmaf(a.s, __uint_as_float(rr[2]), v.z),
+                                                          fmaf(a.s, __uint_as_float(rr[3]), v.w));
+                            if (valid) o4[j4] = kv;
+                        }
+                        // TMEM and the key bases of buffer b are refilled after this
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&t_empty[b]);
+                        continue;
+                    }
                     {
                         u32 r[TC_ROWS];
                         tmem_ld64(tbase, r);
@@ -350,21 +375,25 @@ __device__ __forceinline__ float4 load_row4(const float *r, u32 i, u32 dim, bool
 
 // gstat: [0] max |x|^2, [1] max |lo_x|, [2] max |e_x| (fp32 bits), [3] any lo != 0.
 // A warp per row, grid-stride; maxima are kept per warp and published once.
-__global__ void gt_prep_rows(Dev d, u64 next_id, u32 n_pad, u32 kp1, u32 kb, u32 *B, float *xn, u32 *gstat) {
+// ids (optional): row c is node ids[c]; check_live: rows of deleted or
+// never-inserted nodes get key base +inf and a zero copy.
+__global__ void gt_prep_rows(Dev d, const u32 *ids, u64 next_id, u32 n_pad, bool check_live, u32 kp1, u32 kb, u32 *B,
+                             float *xn, u32 *gstat) {
     const int lane = lane_id();
     const u32 nwarps = (gridDim.x * blockDim.x) >> 5;
     float mx_sq = 0.0f, mx_lo = 0.0f, mx_e = 0.0f;
     bool any_lo = false;
     for (u32 c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_pad; c += nwarps) {
-        bool live = false;
-        if (c < next_id) {
-            const u64 rf = d.ref[c];
+        const u32 id = c < next_id ? (ids ? ids[c] : c) : 0u;
+        bool live = c < next_id;
+        if (live && check_live) {
+            const u64 rf = d.ref[id];
             live = !ref_del(rf) && ref_slab(rf) != NIL;
         }
         float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
         bool anylo = false;
         if (c < next_id) {
-            const float *xr = d.x + (size_t)c * d.mp;
+            const float *xr = d.x + (size_t)id * d.mp;
             uint2 *br = reinterpret_cast<uint2 *>(B + (size_t)c * (kb / 2));
             for (u32 i = 4 * lane; i < kp1; i += 128) {
                 const Split4 v = split4(load_row4(xr, i, d.dim, live));
@@ -434,6 +463,31 @@ __global__ void gt_prep_queries(const float *q, u32 mp, u32 dim, u32 nq, u32 kp1
         qstat[4 * (size_t)r + 3] = sqrtf(e2);
         if (anylo) atomicOr(gstat + 3, 1u);
     }
+}
+
+// ---- the certificate ----------------------------------------------------------
+// Lower bound on the canonical fp32 distance of every row whose approximate
+// key exceeds LB.  qs: |q|^2, |q|, |lo_q|, |e_q| of the query; gs: max |x|^2,
+// max |lo_x|, max |e_x| over the rows (fp32 bits).  K = contracted length.
+__device__ double key_lower_bound(int metric, double m, double K, bool split, const float *qs, const u32 *gs,
+                                  double LB) {
+    const double u = 1.0 / 16777216.0;
+    const double qn = qs[0], qa = (double)qs[1] * 1.01, loq = (double)qs[2] * 1.01, eq = (double)qs[3] * 1.01;
+    const double X2 = __uint_as_float(gs[0]), X1 = sqrt(X2) * 1.01;
+    const double Lx = (double)__uint_as_float(gs[1]) * 1.01, Ex = (double)__uint_as_float(gs[2]) * 1.01;
+    // |computed dot - q.x|: the terms the split leaves out, plus fp32 accumulation
+    const double dot_res = split ? loq * Lx + (qa + eq) * Ex + eq * (X1 + Ex) : 0.0;
+    const double dot_err = dot_res + (K + 2.0) * 2.0 * u * 1.03 * qa * X1;
+    if (metric == 0) {
+        // norms (fp32 sums of squares), 2 x dot error, rounding of the key
+        const double E = 2.0 * ((m + 2.0) * u * qn * 1.01 + (m + 2.0) * u * X2 + 2.0 * dot_err +
+                                2.0 * u * (X2 + 2.1 * qa * X1));
+        const double y = qn + LB - E;
+        // the canonical fp32 distance is within (m + 4) u of the exact one
+        return y > 0.0 ? y * (1.0 - 2.0 * (m + 4.0) * u) : -1.0;
+    }
+    const double E = 2.0 * (dot_err + (m + 2.0) * u * qa * X1 + u * (1.0 + qa * X1));
+    return 1.0 + LB - E;
 }
 
 // ---- threshold, exact rerank, certificate -------------------------------
@@ -535,27 +589,8 @@ __global__ void __launch_bounds__(RR_WARPS * 32) gt_rerank_kernel(Dev d, RerankA
     } else if (kth == KEY_INF) {
         cert = false;
     } else {
-        const double u = 1.0 / 16777216.0, m = a.m, K = a.kprime;
-        const float *qs = a.qstat + 4 * (size_t)qi;
-        const double qn = qs[0], qa = (double)qs[1] * 1.01, loq = (double)qs[2] * 1.01, eq = (double)qs[3] * 1.01;
-        const double X2 = __uint_as_float(a.gstat[0]), X1 = sqrt(X2) * 1.01;
-        const double Lx = (double)__uint_as_float(a.gstat[1]) * 1.01, Ex = (double)__uint_as_float(a.gstat[2]) * 1.01;
-        // |computed dot - q.x|: the terms the split leaves out, plus fp32 accumulation
-        const double dot_res = a.split ? loq * Lx + (qa + eq) * Ex + eq * (X1 + Ex) : 0.0;
-        const double dot_err = dot_res + (K + 2.0) * 2.0 * u * 1.03 * qa * X1;
-        const double LB = (double)ord2f(tau);
-        double lb;
-        if (d.metric == 0) {
-            // norms (fp32 sums of squares), 2 x dot error, rounding of the key
-            const double E = 2.0 * ((m + 2.0) * u * qn * 1.01 + (m + 2.0) * u * X2 + 2.0 * dot_err +
-                                    2.0 * u * (X2 + 2.1 * qa * X1));
-            const double y = qn + LB - E;
-            // the canonical fp32 distance is within (m + 4) u of the exact one
-            lb = y > 0.0 ? y * (1.0 - 2.0 * (m + 4.0) * u) : -1.0;
-        } else {
-            const double E = 2.0 * (dot_err + (m + 2.0) * u * qa * X1 + u * (1.0 + qa * X1));
-            lb = 1.0 + LB - E;
-        }
+        const double lb = key_lower_bound((int)d.metric, a.m, a.kprime, a.split != 0, a.qstat + 4 * (size_t)qi,
+                                          a.gstat, (double)ord2f(tau));
         cert = (double)key_rho(kth) < lb;
     }
     if (cert) {
@@ -565,6 +600,81 @@ __global__ void __launch_bounds__(RR_WARPS * 32) gt_rerank_kernel(Dev d, RerankA
         }
     } else if (lane == 0) {
         a.fb[atomicAdd(a.fb_count, 1u)] = qi;
+    }
+}
+
+// ---- seeding: exact top-L of the entry set ---------------------------------
+constexpr int SS_CAP = 512;       // candidates a query may keep
+constexpr int SS_WARPS = 4;
+
+struct SeedSelArgs {
+    u32 nq, L, S, ld, want, m, kprime;
+    const float *q;       // nq x mp fp32
+    const float *keys;    // nq x ld approximate keys (entry order)
+    const float *qstat;
+    const u32 *estat;     // maxima over the entry rows
+    u64 *seed;            // nq x L
+    u32 *fb;              // queries left to the CUDA-core seed kernel
+    u32 *ctr;             // [0] their count, [1] error word of the candidate pass
+};
+
+// A warp per query: tau = the want-th smallest approximate key; every entry
+// with key <= tau is scored with the canonical distance, the scores are
+// sorted, and the first L are the seeds if the certificate shows that no
+// entry left out can beat the L-th.
+__global__ void __launch_bounds__(SS_WARPS * 32) seed_select_kernel(Dev d, SeedSelArgs a) {
+    __shared__ u32 cidx[SS_WARPS][SS_CAP];
+    __shared__ u64 ckey[SS_WARPS][SS_CAP];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const u32 qi = blockIdx.x * SS_WARPS + warp;
+    if (qi >= a.nq || a.ctr[1]) return;
+    const float *row = a.keys + (size_t)qi * a.ld;
+    u32 tau = ~0u;                                   // all entries when S <= want
+    if (a.S > a.want) {
+        tau = 0;
+        for (int bit = 31; bit >= 0; bit--) {
+            const u32 tr = tau | (1u << bit);
+            u32 c = 0;
+            for (u32 e = lane; e < a.S; e += 32) c += (u32)(f2ord(row[e]) < tr);
+            if (__reduce_add_sync(FULL, c) < a.want) tau = tr;
+        }
+    }
+    u32 cnt = 0;
+    for (u32 e0 = 0; e0 < a.S; e0 += 32) {
+        const u32 e = e0 + lane;
+        const bool c = e < a.S && f2ord(row[e]) <= tau;
+        const u32 m = __ballot_sync(FULL, c);
+        const u32 pos = cnt + __popc(m & lanemask_lt());
+        if (c && pos < SS_CAP) cidx[warp][pos] = e;
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    bool cert = false;
+    if (cnt <= SS_CAP) {
+        const float *qv = a.q + (size_t)qi * d.mp;
+        const int grp = lane >> 3, g = lane & 7;
+        for (u32 r0 = 0; r0 < cnt; r0 += 4) {
+            const u32 i = r0 + grp;
+            const u32 id = d.entries[cidx[warp][i < cnt ? i : cnt - 1]];
+            const float dd = canon_dist<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
+            if (i < cnt && g == 0) ckey[warp][i] = mkkey(dd, id);
+        }
+        const int np = next_pow2((int)cnt);
+        for (int i = (int)cnt + lane; i < np; i += 32) ckey[warp][i] = KEY_INF;
+        __syncwarp();
+        warp_sort_u64(ckey[warp], np);
+        if (tau == ~0u) {
+            cert = true;                               // every entry was scored
+        } else if (cnt >= a.L) {
+            const double lb = key_lower_bound((int)d.metric, a.m, a.kprime, true, a.qstat + 4 * (size_t)qi, a.estat,
+                                              (double)ord2f(tau));
+            cert = (double)key_rho(ckey[warp][a.L - 1]) < lb;
+        }
+    }
+    if (cert) {
+        for (u32 i = lane; i < a.L; i += 32) a.seed[(size_t)qi * a.L + i] = i < cnt ? ckey[warp][i] : KEY_INF;
+    } else if (lane == 0) {
+        a.fb[atomicAdd(a.ctr, 1u)] = qi;
     }
 }
 
@@ -612,7 +722,7 @@ cudaError_t launch_gt_tc_prep(const Dev &d, u64 next_id, const float *q, u32 nq,
     if (e != cudaSuccess) return e;
     if (p.n_pad)
         gt_prep_rows<<<(unsigned)std::min<u64>((p.n_pad * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
-            d, next_id, (u32)p.n_pad, p.kp1, p.kb, reinterpret_cast<u32 *>(b.B), b.xn, b.gstat);
+            d, nullptr, next_id, (u32)p.n_pad, true, p.kp1, p.kb, reinterpret_cast<u32 *>(b.B), b.xn, b.gstat);
     gt_prep_queries<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(
         q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<u32 *>(b.A), b.qstat, b.gstat);
     return cudaGetLastError();
@@ -672,10 +782,11 @@ cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const 
     a.tiles_per_chunk = (p.n_tiles + best_c - 1) / best_c;
     a.chunks = (p.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
     a.stages = p.stages;
-    a.nblk = p.nblk;
+    a.all_keys = 0;
+    a.ld = p.nblk;
     a.s = d.metric == 0 ? -2.0f : -1.0f;
     a.xn = b.xn;
-    a.bmin = b.bmin;
+    a.out = b.bmin;
     a.err = b.err;
     cudaError_t e = cudaFuncSetAttribute(gt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return e;
@@ -708,6 +819,98 @@ cudaError_t launch_gt_rerank(const Dev &d, const float *q, u32 q0, u32 nq, u32 k
     r.err = b.err;
     gt_rerank_kernel<<<(nq + RR_WARPS - 1) / RR_WARPS, RR_WARPS * 32, 0, st>>>(d, r);
     return cudaGetLastError();
+}
+
+// ---- seeding on tensor cores ----------------------------------------------
+SeedTcPlan seed_tc_plan(u32 dim, u32 n_entry, u32 nq) {
+    SeedTcPlan p{};
+    p.kp1 = (dim + TC_KBOX - 1) / TC_KBOX * TC_KBOX;
+    p.kb = 3 * p.kp1;
+    p.s_pad = (n_entry + TC_ACC - 1) / TC_ACC * TC_ACC;
+    const u32 smem_max = 227 * 1024 - 1024 - 4096;
+    const u32 bbox = TC_ACC * TC_KBOX * 2;
+    const u32 abytes = (p.kb / TC_KBOX) * TC_BOX;
+    p.usable = abytes + 2 * bbox <= smem_max && n_entry > 0;
+    p.stages = p.usable ? std::min<u32>(TC_MAX_STAGES, (smem_max - abytes) / bbox) : 0;
+    p.smem = abytes + p.stages * bbox + 1024;
+    p.bytes_E = (size_t)n_entry * p.kb * 2;
+    p.bytes_A = (size_t)nq * p.kb * 2;
+    p.bytes_keys = (size_t)nq * p.s_pad * 4;
+    return p;
+}
+
+cudaError_t launch_seed_tc_entries(const Dev &d, u32 S, const SeedTcPlan &p, const SeedTcBufs &b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.estat, 0, 8 * sizeof(u32), st);
+    if (e != cudaSuccess || p.s_pad == 0) return e;
+    gt_prep_rows<<<(unsigned)std::min<u64>(((u64)p.s_pad * 32 + 255) / 256, 152 * 16), 256, 0, st>>>(
+        d, d.entries, S, p.s_pad, false, p.kp1, p.kb, reinterpret_cast<u32 *>(b.E), b.en, b.estat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u64 *seed, const SeedTcPlan &p,
+                           const SeedTcBufs &b, int num_sms, cudaStream_t st) {
+    if (nq == 0 || S == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(b.ctr, 0, 8 * sizeof(u32), st);
+    if (e != cudaSuccess) return e;
+    gt_prep_queries<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(
+        q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<u32 *>(b.A), b.qstat, b.ctr + 4);
+    CUtensorMap ta, tb;
+    if (!encode_bf16(&ta, b.A, nq, p.kb, TC_ROWS) || !encode_bf16(&tb, b.E, S, p.kb, TC_ACC))
+        return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.nq = nq;
+    a.n_tiles = p.s_pad / TC_ACC;
+    a.kblocks = p.kb / TC_KBOX;
+    a.n_msub = 1;
+    a.bn = TC_ACC;
+    a.m_tiles = (nq + TC_ROWS - 1) / TC_ROWS;
+    u32 best_c = 1;
+    double best_score = -1e9;
+    for (u32 c = 1; c <= a.n_tiles; c++) {
+        const u64 items = (u64)a.m_tiles * c;
+        const u64 waves = (items + num_sms - 1) / num_sms;
+        const double score = (double)items / (double)(waves * num_sms) - 0.02 * c;
+        if (score > best_score) {
+            best_score = score;
+            best_c = c;
+        }
+    }
+    a.tiles_per_chunk = (a.n_tiles + best_c - 1) / best_c;
+    a.chunks = (a.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
+    a.stages = p.stages;
+    a.all_keys = 1;
+    a.ld = p.s_pad;
+    a.s = d.metric == 0 ? -2.0f : -1.0f;
+    a.xn = b.en;
+    a.out = b.keys;
+    a.err = b.ctr + 1;
+    e = cudaFuncSetAttribute(gt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    const u32 items = a.m_tiles * a.chunks;
+    gt_tc_kernel<<<std::min<u32>(items, (u32)num_sms), TC_THREADS, p.smem, st>>>(ta, tb, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    SeedSelArgs r{};
+    r.nq = nq;
+    r.L = L;
+    r.S = S;
+    r.ld = p.s_pad;
+    r.want = L + 32;
+    r.m = d.dim;
+    r.kprime = p.kb;
+    r.q = q;
+    r.keys = b.keys;
+    r.qstat = b.qstat;
+    r.estat = b.estat;
+    r.seed = seed;
+    r.fb = b.fb;
+    r.ctr = b.ctr;
+    seed_select_kernel<<<(nq + SS_WARPS - 1) / SS_WARPS, SS_WARPS * 32, 0, st>>>(d, r);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // queries the certificate did not cover: the exact CUDA-core seed, with
+    // the count read on the device
+    return launch_seed(d, q, nq, L, seed, st, 0, b.ctr, b.fb);
 }
 
 }  // namespace etale

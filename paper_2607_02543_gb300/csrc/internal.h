@@ -14,8 +14,10 @@ struct SearchTuning {
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
 // seed_kernel: top-L of the entry set per query into `seed` (nq x L); it
 // must precede the search launch that reads `seed`.
+// qsel (optional): the batch is the queries qsel[0 .. n) (n = *nq_dev), each
+// written to its own row of `seed`.
 cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec = 0,
-                        const u32 *nq_dev = nullptr);
+                        const u32 *nq_dev = nullptr, const u32 *qsel = nullptr);
 // prec: 0 fp32, 1 bf16 copy, 2 fp8 copy (query mode only; the best
 // min(rerank * k, 64) live candidates are re-scored in canonical fp32).
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
@@ -114,6 +116,24 @@ struct GtTcBufs {
     float *bmin;                    // qgroup x nblk block minima
     u32 *err;
 };
+struct SeedTcPlan {
+    u32 kp1 = 0, kb = 0, s_pad = 0, stages = 0, smem = 0;
+    size_t bytes_E = 0, bytes_A = 0, bytes_keys = 0;
+    bool usable = false;
+};
+struct SeedTcBufs {
+    void *E, *A;                    // entry and query bf16 copies ([hi | lo | hi], [hi | hi | lo])
+    float *en, *qstat, *keys;       // entry key bases; query norms; nq x s_pad approximate keys
+    u32 *estat;                     // maxima over the entry rows (8 words)
+    u32 *fb;                        // queries left to the CUDA-core seed
+    u32 *ctr;                       // [0] their count, [1] error word, [4..] query flag scratch
+};
+SeedTcPlan seed_tc_plan(u32 dim, u32 n_entry, u32 nq);
+// After the entry set changes: its bf16 copy, key bases and maxima.
+cudaError_t launch_seed_tc_entries(const Dev &d, u32 S, const SeedTcPlan &p, const SeedTcBufs &b, cudaStream_t st);
+// Exact top-L of the S entries for each query (same result as launch_seed with fp32 rows).
+cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u64 *seed, const SeedTcPlan &p,
+                           const SeedTcBufs &b, int num_sms, cudaStream_t st);
 GtTcPlan gt_tc_plan(u32 dim, u64 next_id, u32 nq);
 cudaError_t launch_gt_tc_prep(const Dev &d, u64 next_id, const float *q, u32 nq, const GtTcPlan &p,
                               const GtTcBufs &b, cudaStream_t st);

@@ -291,6 +291,7 @@ struct SeedArgs {
     u32 nq, L;
     u64 *seed;
     u32 rowb;   // bytes per entry row in the tile (fp32 row or its copy)
+    const u32 *qsel;     // optional: slot i computes query qsel[i]
 };
 
 __host__ __device__ inline size_t seed_warp_bytes(u32 mp, u32 L) {
@@ -348,9 +349,11 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     u64 *bk0 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     u64 *bk1 = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     u64 *nk = reinterpret_cast<u64 *>(p);
-    const u32 qi = blockIdx.x * 8 + warp;
     const u32 nq = a.nq_dev ? min(*a.nq_dev, a.nq) : a.nq;
-    const bool active = qi < nq;
+    if (blockIdx.x * 8 >= nq) return;   // block-uniform: no tile work for an empty block
+    const u32 slot = blockIdx.x * 8 + warp;
+    const bool active = slot < nq;
+    const u32 qi = active && a.qsel ? a.qsel[slot] : slot;
     if (active)
         for (u32 i = lane * 4; i < mp; i += 128)
             *reinterpret_cast<float4 *>(qv + i) = *reinterpret_cast<const float4 *>(a.q + (size_t)qi * mp + i);
@@ -554,11 +557,11 @@ size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
 }
 
 cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec,
-                        const u32 *nq_dev) {
+                        const u32 *nq_dev, const u32 *qsel) {
     if (nq == 0 || (d.n_entries == 0 && !d.nent_dev)) return cudaSuccess;
     if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
     const u32 rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
-    SeedArgs a{d, q, nq_dev, nq, L, seed, rowb};
+    SeedArgs a{d, q, nq_dev, nq, L, seed, rowb, qsel};
     const void *fn = prec == 1 ? (const void *)seed_kernel<1> : prec == 2 ? (const void *)seed_kernel<2>
                                                                           : (const void *)seed_kernel<0>;
     size_t smem = align_up((size_t)SEED_TILE * rowb, 16) + 8 * seed_warp_bytes(d.mp, L);
