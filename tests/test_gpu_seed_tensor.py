@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2607_02543_gb300 import workloads as W
-from pair import graphs_equal
+from tests.pair import graphs_equal
 
 pytestmark = pytest.mark.gpu
 
