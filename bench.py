@@ -308,9 +308,13 @@ def main():
     idx.set_profiling(True)
     idx.profile(reset=True)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("ground_truth")
     g0.record(stream)
     gt_ids, _ = idx.ground_truth(d_q, w.k, stream)
     g1.record(stream)
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     gprof = idx.profile(reset=True)
     idx.set_profiling(False)
