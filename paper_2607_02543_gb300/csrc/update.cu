@@ -59,11 +59,10 @@ __device__ __forceinline__ void stage_done(const Dev &d, const Stage &st) {
 }
 
 // Warps per block (<= 4) such that a block's shared memory stays <= 200 KB.
-inline int warps_for(size_t per_warp) {
-    int w = 4;
-    while (w > 1 && (size_t)w * per_warp > 200 * 1024) w >>= 1;
-    return w;
-}
+// Warps per block of the persistent update kernels: one.  Their shared memory
+// is per warp (up to ~20 KB with the Gram tile), so one-warp blocks pack the
+// SM by the warp instead of by four (11 warps instead of 8 at 19 KB).
+inline int warps_for(size_t) { return 1; }
 
 // Rows that fit a per-warp stage of `budget` bytes, capped at `want`.
 inline u32 stage_cap(u32 mp, u32 want, u32 budget) {
@@ -122,80 +121,79 @@ __device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
     return r;
 }
 
-// Writes the n x n Gram into T (fp32, row stride GRAM_N) and the diagonal into
-// nrm.  T and the bf16 rows share `buf`.
+// Writes the upper triangle (j >= i, in 16 x 8 tiles) of the n x n Gram into
+// T (fp32, row stride GRAM_N) and the diagonal into nrm.  T and the bf16 rows
+// share `buf`: the Gram is built in 16-row stripes, and stripe mt's table rows
+// (bytes [4096 mt, 4096 (mt + 1))) never reach a staged row a later stripe
+// reads (row r >= 16 (mt + 1) starts at byte 272 r).  A stripe only needs the
+// columns j >= 16 mt, because the prune reads T[head][j] for j > head.
 __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, float *&T, float *&nrm) {
     const int lane = lane_id();
     __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(buf);
     T = reinterpret_cast<float *>(buf);
     nrm = reinterpret_cast<float *>(buf + (size_t)GRAM_N * GRAM_RS * 2);
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
-    float acc[4][8][4];
-#pragma unroll
-    for (int a = 0; a < 4; a++)
+    const int nkb = ((int)d.mp + 127) >> 7;
+    const u32 xs = smem_addr(X);
+    for (int mt = 0; mt < nm; mt++) {
+        float acc[8][4];
 #pragma unroll
         for (int b = 0; b < 8; b++)
 #pragma unroll
-            for (int c = 0; c < 4; c++) acc[a][b][c] = 0.f;
-    const u32 xs = smem_addr(X);
-    for (int k0 = 0; k0 < (int)d.mp; k0 += 128) {
-        // stage columns [k0, k0 + 128) of every candidate row as bf16 (zero pad)
-        __syncwarp();
-        const int col = k0 + 4 * lane;                   // 32 lanes x float4 = 128 columns
-        for (int r0 = 0; r0 < nm * 16; r0 += 16) {
-            float4 v[16];                                // 16 row loads in flight per lane
+            for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
+        for (int kb = 0; kb < nkb; kb++) {
+            if (nkb > 1 || mt == 0) {
+                // stage columns [128 kb, 128 kb + 128) of rows [16 mt, 16 nm) as bf16 (zero pad)
+                __syncwarp();
+                const int col = 128 * kb + 4 * lane;     // 32 lanes x float4 = 128 columns
+                for (int r0 = 16 * mt; r0 < nm * 16; r0 += 8) {
+                    float4 v[8];                         // 8 row loads in flight per lane
 #pragma unroll
-            for (int t = 0; t < 16; t++) {
-                const int r = r0 + t;
-                v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < n && col < (int)d.mp)
-                    v[t] = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
+                    for (int t = 0; t < 8; t++) {
+                        const int r = r0 + t;
+                        v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < n && col < (int)d.mp)
+                            v[t] = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; t++) {
+                        const uint2 pk = make_uint2(pack_bf16(v[t].x, v[t].y), pack_bf16(v[t].z, v[t].w));
+                        *reinterpret_cast<uint2 *>(X + (size_t)(r0 + t) * GRAM_RS + 4 * lane) = pk;
+                    }
+                }
+                __syncwarp();
             }
 #pragma unroll
-            for (int t = 0; t < 16; t++) {
-                const uint2 pk = make_uint2(pack_bf16(v[t].x, v[t].y), pack_bf16(v[t].z, v[t].w));
-                *reinterpret_cast<uint2 *>(X + (size_t)(r0 + t) * GRAM_RS + 4 * lane) = pk;
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int ks = 0; ks < 8; ks++) {
-#pragma unroll
-            for (int mt = 0; mt < 4; mt++) {
-                if (mt >= nm) break;
+            for (int ks = 0; ks < 8; ks++) {
                 u32 a0, a1, a2, a3;
                 const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
                 const int ac = 16 * ks + 8 * (lane >> 4);
                 ldsm_x4(a0, a1, a2, a3, xs + (u32)((ar * GRAM_RS + ac) * 2));
 #pragma unroll
                 for (int nt = 0; nt < 8; nt += 2) {
-                    if (nt >= nn) break;
+                    if (nt < 2 * mt || nt >= nn) continue;
                     u32 b0, b1, b2, b3;
                     const int br = 8 * nt + (lane & 7) + 8 * (lane >> 4);
                     const int bc = 16 * ks + 8 * ((lane >> 3) & 1);
                     ldsm_x4(b0, b1, b2, b3, xs + (u32)((br * GRAM_RS + bc) * 2));
-                    mma_bf16_16816(acc[mt][nt], a0, a1, a2, a3, b0, b1);
-                    mma_bf16_16816(acc[mt][nt + 1], a0, a1, a2, a3, b2, b3);
+                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b1);
+                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b2, b3);
                 }
             }
         }
-    }
-    __syncwarp();
-    // write the accumulators over the staged rows
-#pragma unroll
-    for (int mt = 0; mt < 4; mt++) {
-        if (mt >= nm) break;
+        __syncwarp();
+        // this stripe's table rows, over staged rows no later stripe reads
 #pragma unroll
         for (int nt = 0; nt < 8; nt++) {
-            if (nt >= nn) break;
+            if (nt < 2 * mt || nt >= nn) continue;
             const int r = 16 * mt + (lane >> 2), c = 8 * nt + 2 * (lane & 3);
-            T[r * GRAM_N + c] = acc[mt][nt][0];
-            T[r * GRAM_N + c + 1] = acc[mt][nt][1];
-            T[(r + 8) * GRAM_N + c] = acc[mt][nt][2];
-            T[(r + 8) * GRAM_N + c + 1] = acc[mt][nt][3];
+            T[r * GRAM_N + c] = acc[nt][0];
+            T[r * GRAM_N + c + 1] = acc[nt][1];
+            T[(r + 8) * GRAM_N + c] = acc[nt][2];
+            T[(r + 8) * GRAM_N + c + 1] = acc[nt][3];
         }
+        __syncwarp();
     }
-    __syncwarp();
     for (int i = lane; i < n; i += 32) nrm[i] = T[i * GRAM_N + i];
     __syncwarp();
 }
