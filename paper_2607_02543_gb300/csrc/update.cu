@@ -27,7 +27,8 @@ struct Stage {
     u64 *bar;        // this warp's mbarrier
     u32 phase;
     bool timeout;
-    char *gram;      // GRAM_BYTES for the tensor-core Gram path (nullptr: canonical path)
+    char *gram;      // gram_bytes(gram_rows) for the tensor-core Gram path (nullptr: canonical path)
+    int gram_rows;   // candidates the Gram buffer holds (a multiple of 16, <= GRAM_N)
 };
 
 // Tensor-core Gram tile: up to 64 candidates, K staged 128 columns at a time
@@ -35,13 +36,20 @@ struct Stage {
 // 64 x 64 fp32 result reuses the same bytes.
 constexpr int GRAM_N = 64;
 constexpr int GRAM_RS = 136;
-constexpr size_t GRAM_BYTES = (size_t)GRAM_N * GRAM_RS * 2 + GRAM_N * 4;   // rows (or table) + norms
+// Shared-memory bytes of a Gram buffer for `rows` candidates: the bf16 rows
+// (or the table over them) and the norms; 0 rows = no buffer.
+__host__ __device__ inline size_t gram_bytes(u32 rows) {
+    return rows ? (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15) + (((size_t)rows * 4 + 15) & ~(size_t)15) : 0;
+}
+// Gram rows for a kernel whose prunes see at most max_n candidates (0: the
+// Gram path is off or cannot hold them).
+inline u32 gram_rows_for(u32 on, u32 max_n) { return on && max_n <= (u32)GRAM_N ? (max_n + 15) / 16 * 16 : 0; }
 
 // Shared-memory bytes for a stage of ns rows plus its mbarrier.
 __host__ __device__ inline size_t stage_bytes(u32 ns, u32 mp) { return al16((size_t)ns * mp * 4) + 16; }
 
 // Carve a stage at p (16-byte aligned) and initialise the warp's mbarrier.
-__device__ __forceinline__ Stage stage_init(char *p, u32 ns, u32 mp, char *gram = nullptr) {
+__device__ __forceinline__ Stage stage_init(char *p, u32 ns, u32 mp, char *gram = nullptr, u32 gram_rows = 0) {
     Stage st;
     st.rows = ns ? reinterpret_cast<float *>(p) : nullptr;
     st.ns_cap = (int)ns;
@@ -49,6 +57,7 @@ __device__ __forceinline__ Stage stage_init(char *p, u32 ns, u32 mp, char *gram 
     st.phase = 0;
     st.timeout = false;
     st.gram = gram;
+    st.gram_rows = (int)gram_rows;
     if (lane_id() == 0) mbar_init(st.bar, 1);
     __syncwarp();
     return st;
@@ -127,11 +136,11 @@ __device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
 // (bytes [4096 mt, 4096 (mt + 1))) never reach a staged row a later stripe
 // reads (row r >= 16 (mt + 1) starts at byte 272 r).  A stripe only needs the
 // columns j >= 16 mt, because the prune reads T[head][j] for j > head.
-__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, float *&T, float *&nrm) {
+__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, float *&T, float *&nrm) {
     const int lane = lane_id();
     __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(buf);
     T = reinterpret_cast<float *>(buf);
-    nrm = reinterpret_cast<float *>(buf + (size_t)GRAM_N * GRAM_RS * 2);
+    nrm = reinterpret_cast<float *>(buf + (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15));
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
     const int nkb = ((int)d.mp + 127) >> 7;
     const u32 xs = smem_addr(X);
@@ -203,7 +212,7 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
                                float *out_rho, Stage &st) {
     const int lane = lane_id();
     float *T, *nrm;
-    warp_gram(d, ck, n, st.gram, T, nrm);
+    warp_gram(d, ck, n, st.gram, st.gram_rows, T, nrm);
     for (int i = lane; i < n; i += 32) alive[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1 : 0;
     __syncwarp();
     int nout = 0, start = 0;
@@ -244,7 +253,7 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
 // ---------------------------------------------------------------------------
 __device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx, u32 *out_id,
                           float *out_rho, Stage &st) {
-    if (st.gram && n <= GRAM_N) return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
+    if (st.gram && n <= st.gram_rows) return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
     const int lane = lane_id();
     const int grp = lane >> 3, g = lane & 7;
     const int ns = st.rows ? min(n, st.ns_cap) : 0;
@@ -390,7 +399,7 @@ struct PruneInsArgs {
 
 __host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
     return stage_bytes(ns, mp) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4) +
-           (gram ? al16(GRAM_BYTES) : 0);
+           gram_bytes(gram);
 }
 
 __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
@@ -400,8 +409,8 @@ __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
     const u32 R = d.R;
     char *p = smem + warp * prune_ins_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    if (a.gram) p += al16(GRAM_BYTES);
-    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += gram_bytes(a.gram);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     p += stage_bytes(a.ns, d.mp);
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
@@ -447,7 +456,7 @@ cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_k
                                 const Offers &of, int num_sms, cudaStream_t st) {
     if (b == 0) return cudaSuccess;
     // the Gram tile covers the prune only when every candidate fits in it
-    const u32 gram = d.gram && max_cand <= (u32)GRAM_N ? 1u : 0u;
+    const u32 gram = gram_rows_for(d.gram, max_cand);
     PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, 0, gram, F_id, F_rho, F_n, of};
     u32 np = 32;
     while (np < max_hops) np <<= 1;
@@ -487,7 +496,7 @@ struct FoldArgs {
 
 __host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
     return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + (gram ? al16(GRAM_BYTES) : 0);
+           al16((size_t)np * 4) + gram_bytes(gram);
 }
 
 __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
@@ -497,8 +506,8 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
     const u32 R = d.R;
     char *p = smem + warp * fold_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    if (a.gram) p += al16(GRAM_BYTES);
-    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += gram_bytes(a.gram);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     p += stage_bytes(a.ns, d.mp);
     const size_t lb = al16((size_t)R * 4 + 4);
     u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
@@ -563,7 +572,7 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     if (of.n == 0) return cudaSuccess;
     if (budget && hi > of.n) hi = of.n;
     if (budget && lo >= hi) return cudaSuccess;
-    FoldArgs a{d, of, seg_start, seg_count, budget, 0, 0, d.gram, lo, budget ? hi : of.n};
+    FoldArgs a{d, of, seg_start, seg_count, budget, 0, 0, gram_rows_for(d.gram, d.R + 1), lo, budget ? hi : of.n};
     u32 np = 32;
     while (np < d.R + 1) np <<= 1;
     a.np = np;
@@ -600,7 +609,7 @@ struct RefineArgs {
 
 __host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 ns, u32 mp, u32 gram) {
     return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + al16((size_t)cap * 4) + (gram ? al16(GRAM_BYTES) : 0);
+           al16((size_t)np * 4) + al16((size_t)cap * 4) + gram_bytes(gram);
 }
 
 __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
@@ -610,8 +619,8 @@ __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
     const u32 R = d.R;
     char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    if (a.gram) p += al16(GRAM_BYTES);
-    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += gram_bytes(a.gram);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     p += stage_bytes(a.ns, d.mp);
     u32 *nid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *nrho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
@@ -733,7 +742,7 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     u32 np = 32;
     while (np < cap + d.R) np <<= 1;
     a.np = np;
-    a.gram = d.gram;
+    a.gram = d.gram ? (u32)GRAM_N : 0u;
     a.ns = d.gram ? 0 : stage_cap(d.mp, max_cand, d.stage_bytes);
     const size_t wb = refine_warp_bytes(np, cap, d.R, a.ns, d.mp, a.gram);
     const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
@@ -802,7 +811,7 @@ __host__ __device__ inline u32 repk_np(u32 R) {
 __host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp, u32 gram) {
     const u32 np = repk_np(R);
     return stage_bytes(ns, mp) + 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)np * 8) +
-           al16(np) + (gram ? al16(GRAM_BYTES) : 0);
+           al16(np) + gram_bytes(gram);
 }
 
 __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
@@ -812,8 +821,8 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
     const u32 R = d.R;
     char *p = smem + warp * repk_warp_bytes(R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    if (a.gram) p += al16(GRAM_BYTES);
-    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += gram_bytes(a.gram);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     p += stage_bytes(a.ns, d.mp);
     u32 *bid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     u32 *bdel = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
@@ -952,7 +961,7 @@ struct RepairFoldArgs {
 
 __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
     return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + (gram ? al16(GRAM_BYTES) : 0);
+           al16((size_t)np * 4) + gram_bytes(gram);
 }
 
 __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
@@ -985,8 +994,8 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
     const u32 R = d.R;
     char *p = smem + warp * repf_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    if (a.gram) p += al16(GRAM_BYTES);
-    Stage st = stage_init(p, a.ns, d.mp, gbuf);
+    p += gram_bytes(a.gram);
+    Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     p += stage_bytes(a.ns, d.mp);
     const size_t lb = al16((size_t)R * 4 + 4);
     u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
@@ -1051,8 +1060,8 @@ cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key,
                                     const u64 *seg_count, u64 n_pairs, u32 budget, int num_sms, cudaStream_t st,
                                u64 lo) {
     if (n_pairs == 0) return cudaSuccess;
-    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0, 0, d.gram,
-                     lo};
+    RepairFoldArgs a{d, dt, pair_key, pair_val, pair_K, pair_Kn, seg_start, seg_count, n_pairs, budget, 0, 0,
+                     gram_rows_for(d.gram, 2 * d.R - 1), lo};
     u32 np = 32;
     while (np < 2 * d.R) np <<= 1;
     a.np = np;
