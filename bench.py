@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--max-cand", type=int, default=64,
                     help="RobustPrune candidates kept; 64 fits the tensor-core Gram tile (library default: 2 * build beam)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default BeamSearch launch shape")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
@@ -262,6 +263,13 @@ def main():
                 beam = b
                 break
     args.search_beam = beam
+    # launch shape of the BeamSearch kernel (inserts and queries), tuned on
+    # this index before any timed work (the library's own autotuner)
+    tuning = None
+    if not args.no_autotune:
+        tried = idx.autotune_search(d_q, w.k, beam, stream)
+        best = min(tried, key=lambda t: t[2])
+        tuning = {"stage_rows": best[0], "seen_bits": best[1], "tried": [list(t) for t in tried]}
     for r in range(args.warmup):
         round_dev(r)
         idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
@@ -389,7 +397,7 @@ def main():
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "kernel_ms": kernel_ms},
-               "phase_ms_per_step": phases, "ground_truth": gt_block,
+               "phase_ms_per_step": phases, "ground_truth": gt_block, "search_tuning": tuning,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)

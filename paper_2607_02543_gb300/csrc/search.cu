@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, 4) search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
