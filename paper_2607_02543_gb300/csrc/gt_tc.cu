@@ -631,12 +631,37 @@ __global__ void __launch_bounds__(SS_WARPS * 32) seed_select_kernel(Dev d, SeedS
     const float *row = a.keys + (size_t)qi * a.ld;
     u32 tau = ~0u;                                   // all entries when S <= want
     if (a.S > a.want) {
-        tau = 0;
+        // a threshold from every 8th key (16 per lane), kept when the count
+        // of keys at or below it lands in [want, SS_CAP]; else the exact
+        // want-th smallest key by a bitwise search over all keys
+        u32 smp[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const u32 e = 8u * (lane + 32u * j);
+            smp[j] = e < a.S ? f2ord(row[e]) : ~0u;
+        }
+        const u32 rs = a.want / 8 + 8;
+        u32 t0 = 0;
         for (int bit = 31; bit >= 0; bit--) {
-            const u32 tr = tau | (1u << bit);
+            const u32 tr = t0 | (1u << bit);
             u32 c = 0;
-            for (u32 e = lane; e < a.S; e += 32) c += (u32)(f2ord(row[e]) < tr);
-            if (__reduce_add_sync(FULL, c) < a.want) tau = tr;
+#pragma unroll
+            for (int j = 0; j < 16; j++) c += (u32)(smp[j] < tr);
+            if (__reduce_add_sync(FULL, c) < rs) t0 = tr;
+        }
+        u32 c = 0;
+        for (u32 e = lane; e < a.S; e += 32) c += (u32)(f2ord(row[e]) <= t0);
+        c = __reduce_add_sync(FULL, c);
+        if (t0 != ~0u && c >= a.want && c <= (u32)SS_CAP) {
+            tau = t0;
+        } else {
+            tau = 0;
+            for (int bit = 31; bit >= 0; bit--) {
+                const u32 tr = tau | (1u << bit);
+                u32 c2 = 0;
+                for (u32 e = lane; e < a.S; e += 32) c2 += (u32)(f2ord(row[e]) < tr);
+                if (__reduce_add_sync(FULL, c2) < a.want) tau = tr;
+            }
         }
     }
     u32 cnt = 0;

@@ -810,8 +810,8 @@ __host__ __device__ inline u32 repk_np(u32 R) {
 
 __host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp, u32 gram) {
     const u32 np = repk_np(R);
-    return stage_bytes(ns, mp) + 3 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)np * 8) +
-           al16(np) + gram_bytes(gram);
+    return stage_bytes(ns, mp) + 2 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)32 * np) +
+           gram_bytes(gram);
 }
 
 __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
@@ -826,11 +826,9 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
     p += stage_bytes(a.ns, d.mp);
     u32 *bid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     u32 *bdel = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
-    u32 *cj = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *M = reinterpret_cast<float *>(p); p += al16((size_t)R * R * 4);
     const int npk = (int)repk_np(R);
-    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)npk * 8);
-    unsigned char *alive = reinterpret_cast<unsigned char *>(p);
+    unsigned char *ord = reinterpret_cast<unsigned char *>(p) + lane * npk;   // this lane's sorted candidates
     const int grp = lane >> 3, g = lane & 7;
     const u64 nd = *a.n_dt;
     const u32 invalid = (u32)d.capacity;
@@ -867,56 +865,47 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
             }
         }
         __syncwarp();
-        for (int ja = 0; ja < (int)R; ja++) {
+        // K(u, a) for every a in B, one lane per a: the candidates b != a, live,
+        // in ascending (d(a, b), b), then the greedy RobustPrune on the table
+        for (int ja = lane; ja < (int)R; ja += 32) {
             const size_t slot = (size_t)i * R + ja;
             if (ja >= nb || bdel[ja]) {
-                if (lane == 0) { a.pair_key[slot] = invalid; a.pair_val[slot] = (u32)slot; a.pair_Kn[slot] = 0; }
+                a.pair_key[slot] = invalid;
+                a.pair_val[slot] = (u32)slot;
+                a.pair_Kn[slot] = 0;
                 continue;
             }
-            // candidates b in B, b != a, live; key (d(a, b), b), payload index jb
-            for (int t = lane; t < npk; t += 32) {
-                u64 k = KEY_INF;
-                if (t < nb && t != ja && !bdel[t]) k = mkkey(M[ja * R + t], bid[t]);
-                keys[t] = k;
-            }
-            __syncwarp();
-            warp_sort_u64(keys, npk);
+            // rank of each candidate among the candidates (keys are distinct: ids differ);
+            // M is symmetric, and M[t][ja] keeps the lanes on distinct banks
             int nc = 0;
-            for (int t0 = 0; t0 < npk; t0 += 32) nc += __popc(__ballot_sync(FULL, keys[t0 + lane] != KEY_INF));
-            // table index of each sorted candidate
-            for (int t = lane; t < nc; t += 32) {
-                const u32 id = key_id(keys[t]);
-                u32 jb = 0;
-                for (int q = 0; q < nb; q++) if (bid[q] == id) jb = (u32)q;
-                cj[t] = jb;
-                alive[t] = 1;
+            for (int t = 0; t < nb; t++) {
+                if (t == ja || bdel[t]) continue;
+                const u64 kt = mkkey(M[t * R + ja], bid[t]);
+                int rank = 0;
+                for (int t2 = 0; t2 < nb; t2++)
+                    if (t2 != ja && !bdel[t2] && mkkey(M[t2 * R + ja], bid[t2]) < kt) rank++;
+                ord[rank] = (unsigned char)t;
+                nc++;
             }
-            __syncwarp();
-            int nk = 0, start = 0;
-            while (nk < (int)R) {
-                int head = -1;
-                for (int t0 = start; t0 < nc; t0 += 32) {
-                    int t = t0 + lane;
-                    u32 m = __ballot_sync(FULL, t < nc && alive[t]);
-                    if (m) { head = t0 + __ffs(m) - 1; break; }
-                }
-                if (head < 0) break;
-                if (lane == 0) {
-                    const u64 hk = keys[head];
-                    a.pair_K[slot * R + nk] = make_uint2(key_id(hk), __float_as_uint(key_rho(hk)));
-                }
+            u64 alive = nc >= 64 ? ~0ull : ((1ull << nc) - 1);
+            int nk = 0;
+            for (int h = 0; h < nc && nk < (int)R; h++) {
+                if (!(alive >> h & 1)) continue;
+                const int hj = ord[h];
+                const float hr = M[hj * R + ja];
+                a.pair_K[slot * R + nk] = make_uint2(bid[hj], __float_as_uint(hr));
                 nk++;
-                if (nk == (int)R) break;
-                const u32 hj = cj[head];
-                for (int t = head + 1 + lane; t < nc; t += 32) {
-                    if (alive[t] && __fmul_rn(d.alpha2, M[hj * R + cj[t]]) <= key_rho(keys[t])) alive[t] = 0;
+                for (int t2 = h + 1; t2 < nc; t2++) {
+                    if (!(alive >> t2 & 1)) continue;
+                    const int tj = ord[t2];
+                    if (__fmul_rn(d.alpha2, M[hj * R + tj]) <= M[tj * R + ja]) alive &= ~(1ull << t2);
                 }
-                __syncwarp();
-                start = head + 1;
             }
-            if (lane == 0) { a.pair_key[slot] = bid[ja]; a.pair_val[slot] = (u32)slot; a.pair_Kn[slot] = (u32)nk; }
-            __syncwarp();
+            a.pair_key[slot] = bid[ja];
+            a.pair_val[slot] = (u32)slot;
+            a.pair_Kn[slot] = (u32)nk;
         }
+        __syncwarp();
     }
     stage_done(d, st);
 }
