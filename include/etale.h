@@ -73,7 +73,9 @@ typedef struct {
                              lock-free mode, canonical fp32 in deterministic
                              mode), 1 canonical fp32, 2 tensor-core Gram
                              tile (bf16 inputs, fp32 accumulation; exact for
-                             integer-valued data of magnitude <= 256)       */
+                             integer-valued data of magnitude <= 256).  The
+                             Gram tile stages its rows from the BF16 copy,
+                             so gram = 2 also keeps that copy (copies bit 0) */
     uint32_t copies;      /* reduced-precision search copies kept beside the
                              fp32 rows: bit 0 BF16, bit 1 FP8-E4M3 with a
                              per-vector scale max|x| / 448; default none    */

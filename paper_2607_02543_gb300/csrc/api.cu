@@ -584,6 +584,8 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         return ETALE_EINVAL;
     }
     if (cfg.gram == 0) cfg.gram = cfg.mode == ETALE_MODE_LOCKFREE ? 2 : 1;
+    // the Gram tiles stage their rows from the bf16 copy
+    if (cfg.gram == 2) cfg.copies |= 1u;
     if (cfg.stage_kb > 64) {
         t_last_error = "stage_kb must be <= 64";
         return ETALE_EINVAL;

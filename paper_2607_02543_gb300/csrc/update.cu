@@ -136,7 +136,7 @@ __device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
 // (bytes [4096 mt, 4096 (mt + 1))) never reach a staged row a later stripe
 // reads (row r >= 16 (mt + 1) starts at byte 272 r).  A stripe only needs the
 // columns j >= 16 mt, because the prune reads T[head][j] for j > head.
-__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, float *&T, float *&nrm) {
+__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float *&nrm) {
     const int lane = lane_id();
     __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(buf);
     T = reinterpret_cast<float *>(buf);
@@ -151,7 +151,34 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
         for (int kb = 0; kb < nkb; kb++) {
-            if (nkb > 1 || mt == 0) {
+            if ((nkb > 1 || mt == 0) && d.xb) {
+                // rows from the bf16 copy (the same round-to-nearest-even values):
+                // one bulk copy per row, all in flight on the stage's mbarrier;
+                // columns past the row and rows past n are zeroed
+                const int r_lo = 16 * mt, r_hi = nm * 16;
+                const int cols = min(128, (int)d.mb - 128 * kb);
+                __syncwarp();
+                if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const int zr0 = cols < 128 ? r_lo : max(r_lo, min(n, r_hi));   // first row with zeros
+                for (int z = lane; z < (r_hi - zr0) * 64; z += 32) {
+                    const int r = zr0 + (z >> 6), c = (z & 63) * 2;
+                    if (r >= n || c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS + c) = 0u;
+                }
+                const int nr = max(0, min(n, r_hi) - r_lo);
+                if (lane == 0 && nr > 0) mbar_expect_tx(st.bar, (u32)(nr * cols * 2));
+                __syncwarp();
+                for (int r = r_lo + lane; r < r_lo + nr; r += 32)
+                    bulk_g2s(X + (size_t)r * GRAM_RS, d.xb + (size_t)key_id(ck[r]) * d.mb + 128 * kb, (u32)cols * 2,
+                             st.bar);
+                if (nr > 0) {
+                    if (!mbar_wait(st.bar, st.phase, WAIT_LIMIT)) {
+                        st.timeout = true;
+                        mbar_wait(st.bar, st.phase, WAIT_LIMIT);   // let copies in flight land
+                    }
+                    st.phase ^= 1u;
+                }
+                __syncwarp();
+            } else if (nkb > 1 || mt == 0) {
                 // stage columns [128 kb, 128 kb + 128) of rows [16 mt, 16 nm) as bf16 (zero pad)
                 __syncwarp();
                 const int col = 128 * kb + 4 * lane;     // 32 lanes x float4 = 128 columns
@@ -207,38 +234,56 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
     __syncwarp();
 }
 
-// RobustPrune on a Gram table: same rule and order as warp_prune.
+// RobustPrune on a Gram table: same rule and order as warp_prune.  First,
+// lane h (and h + 32) builds the mask of later candidates j that candidate h
+// would drop (alpha^2 * d(h, j) <= rho(j)), reading the table in a
+// lane-rotated column order so that the lanes hit distinct banks.  The greedy
+// pass is then a warp-uniform walk over a 64-bit alive mask: take the first
+// alive candidate, clear the ones it drops.
 __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *out_id,
                                float *out_rho, Stage &st) {
+    (void)alive;
     const int lane = lane_id();
     float *T, *nrm;
-    warp_gram(d, ck, n, st.gram, st.gram_rows, T, nrm);
-    for (int i = lane; i < n; i += 32) alive[i] = (i == 0 || ck[i] != ck[i - 1]) ? 1 : 0;
-    __syncwarp();
-    int nout = 0, start = 0;
-    const int R = (int)d.R;
-    while (nout < R) {
-        int head = -1;
-        for (int i0 = start; i0 < n; i0 += 32) {
-            int i = i0 + lane;
-            u32 m = __ballot_sync(FULL, i < n && alive[i]);
-            if (m) { head = i0 + __ffs(m) - 1; break; }
-        }
-        if (head < 0) break;
-        const u64 hk = ck[head];
-        if (lane == 0) { out_id[nout] = key_id(hk); out_rho[nout] = key_rho(hk); }
-        nout++;
-        if (nout == R) break;
-        const float nh = nrm[head];
-        for (int j = head + 1 + lane; j < n; j += 32) {
-            if (!alive[j]) continue;
-            const float g = T[head * GRAM_N + j];
+    warp_gram(d, ck, n, st.gram, st.gram_rows, st, T, nrm);
+    u64 dom[2] = {0ull, 0ull};
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+        const int h = lane + 32 * hh;
+        if (h >= n - 1) continue;
+        const float nh = nrm[h];
+        const float *Th = T + h * GRAM_N;
+        u64 m = 0ull;
+        for (int k = 0; k < 64; k++) {
+            const int j = (k + lane) & 63;
+            if (j <= h || j >= n) continue;
+            const float g = Th[j];
             // (n_h - g) + (n_j - g): every intermediate stays as small as the result
             const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
-            if (__fmul_rn(d.alpha2, dd) <= key_rho(ck[j])) alive[j] = 0;
+            if (__fmul_rn(d.alpha2, dd) <= key_rho(ck[j])) m |= 1ull << j;
         }
-        __syncwarp();
-        start = head + 1;
+        dom[hh] = m;
+    }
+    // equal adjacent keys collapse to one
+    u64 live = 0ull;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const u32 b = __ballot_sync(FULL, i < n && (i == 0 || ck[i] != ck[i - 1]));
+        live |= (u64)b << i0;
+    }
+    int nout = 0;
+    const int R = (int)d.R;
+    while (nout < R && live) {
+        const int head = __ffsll((long long)live) - 1;
+        live &= live - 1;
+        if (lane == 0) {
+            const u64 hk = ck[head];
+            out_id[nout] = key_id(hk);
+            out_rho[nout] = key_rho(hk);
+        }
+        nout++;
+        const u64 dl = __shfl_sync(FULL, dom[0], head & 31), dh = __shfl_sync(FULL, dom[1], head & 31);
+        live &= ~(head < 32 ? dl : dh);
     }
     __syncwarp();
     return nout;
