@@ -1126,7 +1126,7 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
     float best = 1e30f;
     SearchTuning best_t = saved;
     u32 tried = 0;
-    const u32 rows[3] = {8, 16, 32}, bits[4] = {8, 9, 10, 11};
+    const u32 rows[3] = {4, 8, 16}, bits[4] = {7, 8, 9, 10};
     for (u32 a = 0; a < 3; a++)
         for (u32 b = 0; b < 4; b++) {
             SearchTuning t;
