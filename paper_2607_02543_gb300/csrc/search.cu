@@ -108,6 +108,43 @@ __device__ __forceinline__ float qdist(const float *__restrict__ q, const void *
     return metric == 0 ? s : __fsub_rn(1.0f, s);
 }
 
+// canon_dist<8> for rows of at most 128 floats with this lane's four query
+// float4 (elements 4 (g + 8 t) .. + 3, t = 0..3; zero past the row) held in
+// registers: the same operations in the same order.
+__device__ __forceinline__ float canon_dist_q8(const float4 (&qr)[4], const float *__restrict__ b, int mp, int metric,
+                                               int g) {
+    float p[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int i = 4 * (g + 8 * t);
+        float acc = 0.0f;
+        if (i < mp) {
+            const float4 u = qr[t];
+            const float4 v = *reinterpret_cast<const float4 *>(b + i);
+            if (metric == 0) {
+                float d0 = __fsub_rn(u.x, v.x), d1 = __fsub_rn(u.y, v.y);
+                float d2 = __fsub_rn(u.z, v.z), d3 = __fsub_rn(u.w, v.w);
+                acc = __fmaf_rn(d0, d0, acc);
+                acc = __fmaf_rn(d1, d1, acc);
+                acc = __fmaf_rn(d2, d2, acc);
+                acc = __fmaf_rn(d3, d3, acc);
+            } else {
+                acc = __fmaf_rn(u.x, v.x, acc);
+                acc = __fmaf_rn(u.y, v.y, acc);
+                acc = __fmaf_rn(u.z, v.z, acc);
+                acc = __fmaf_rn(u.w, v.w, acc);
+            }
+        }
+        p[t] = acc;
+    }
+    p[0] = __fadd_rn(p[0], p[2]);
+    p[1] = __fadd_rn(p[1], p[3]);
+    float s = __fadd_rn(p[0], p[1]);
+#pragma unroll
+    for (int h = 4; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
+    return metric == 0 ? s : __fsub_rn(1.0f, s);
+}
+
 struct WarpSmem {
     float *qv;       // mp
     float *stage;    // stage_rows x mp
@@ -167,8 +204,9 @@ __device__ __forceinline__ int lower_bound(const u64 *a, int n, u64 key) {
 
 // Merge the candidate keys held one per lane (KEY_INF = none) into the beam
 // in place.  Only keys that can enter the beam take part; entries before the
-// first insertion point do not move.  Returns the new beam size.
-__device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L) {
+// first insertion point do not move, so `lo` (every entry before it is
+// expanded) drops to that point at most.  Returns the new beam size.
+__device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L, int &lo) {
     const int lane = lane_id();
     const u64 *bk = s.bkey;
     // drop keys that cannot enter a full beam, and keys already in the beam
@@ -193,6 +231,7 @@ __device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L) {
     // the first insertion point is the lower bound of the smallest new key
     int p0 = (key != KEY_INF && rank == 0) ? lb : 0x7fffffff;
     for (int o = 16; o >= 1; o >>= 1) p0 = min(p0, __shfl_xor_sync(FULL, p0, o));
+    lo = min(lo, p0);
     __syncwarp();
     // move entries [p0, n) down, last chunk first so no unread entry is overwritten
     const int nmove = n - p0;
@@ -225,7 +264,7 @@ __device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L) {
 // into the beam.  Returns the new beam size.  `phase` tracks the mbarrier.
 template <int P>
 __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u32 &phase, u64 &ndist,
-                          bool &timeout) {
+                          bool &timeout, int &lo, const float4 (&qr)[4]) {
     const Dev &d = a.d;
     const int lane = lane_id();
     const u32 mp = d.mp;
@@ -264,7 +303,12 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
         for (int r0 = 0; r0 < nb; r0 += 4) {
             const int c = r0 + grp;
             const int cc = c < nb ? c : nb - 1;   // idle groups recompute a valid row
-            float dist = qdist<P>(s.qv, stage + (size_t)cc * rowb, P == 2 ? scl[cc] : 1.0f, (int)mp, (int)d.metric, g);
+            float dist;
+            if (P == 0 && mp <= 128)
+                dist = canon_dist_q8(qr, reinterpret_cast<const float *>(stage + (size_t)cc * rowb), (int)mp,
+                                     (int)d.metric, g);
+            else
+                dist = qdist<P>(s.qv, stage + (size_t)cc * rowb, P == 2 ? scl[cc] : 1.0f, (int)mp, (int)d.metric, g);
             if (c < nb && g == 0) s.ckey[b0 + c] = mkkey(dist, s.cid[b0 + c]);
         }
         __syncwarp();
@@ -273,7 +317,7 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
     const u64 key = lane < cnt ? s.ckey[lane] : KEY_INF;
     const u64 ref = lane < cnt ? s.cref[lane] : 0;
     if (lane < cnt) s.seen[seen_slot(key_id(key), a.seen_bits)] = key_id(key);
-    return merge_beam(s, key, ref, n, (int)a.L);
+    return merge_beam(s, key, ref, n, (int)a.L, lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -416,6 +460,12 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
             *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
         for (u32 i = lane; i < a.seen_slots; i += 32) s.seen[i] = NIL;
         __syncwarp();
+        float4 qr[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const u32 i = 4u * ((lane & 7) + 8 * t);
+            qr[t] = i < mp ? *reinterpret_cast<const float4 *>(s.qv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         // initial beam: the L nearest members of the entry set E, computed by
         // seed_kernel; the reference words are sampled here
         const int n0 = (int)min(a.L, d.nent_dev ? *d.nent_dev : d.n_entries);
@@ -432,15 +482,17 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
         u32 hops = 0, nexp = 0;
         // slab entries of the predicted next expansion, loaded ahead of use
         u32 pf_id = NIL, pf0 = NIL, pf1 = NIL;
+        int lo = 0;   // every beam entry before lo is expanded
         for (;;) {
             int first = -1;
-            for (int i0 = 0; i0 < n; i0 += 32) {
+            for (int i0 = lo; i0 < n; i0 += 32) {
                 int i = i0 + lane;
                 u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
                 if (m) { first = i0 + __ffs(m) - 1; break; }
             }
             if (first < 0 || hops >= a.max_hops) break;
             hops++;
+            lo = first + 1;
             const u64 r = s.bref[first];
             const u64 bkey = s.bkey[first];
             const u32 fid = key_id(bkey);
@@ -475,7 +527,7 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
             for (u32 j0 = 0; j0 < deg; j0 += 32) {
                 u32 nb = j0 == 0 ? e0 : e1;
                 if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
-                n = eval_merge<P>(a, s, nb, n, phase, ndist, timeout);
+                n = eval_merge<P>(a, s, nb, n, phase, ndist, timeout, lo, qr);
             }
         }
         nexp_tot += hops;
