@@ -154,15 +154,19 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
             if ((nkb > 1 || mt == 0) && d.xb) {
                 // rows from the bf16 copy (the same round-to-nearest-even values):
                 // one bulk copy per row, all in flight on the stage's mbarrier;
-                // columns past the row and rows past n are zeroed
+                // columns past the row are zeroed.  Rows past n stay as they
+                // are: an entry (i, j) of the table reads rows i and j only,
+                // and no entry with i or j >= n is read.
                 const int r_lo = 16 * mt, r_hi = nm * 16;
                 const int cols = min(128, (int)d.mb - 128 * kb);
                 __syncwarp();
                 if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const int zr0 = cols < 128 ? r_lo : max(r_lo, min(n, r_hi));   // first row with zeros
-                for (int z = lane; z < (r_hi - zr0) * 64; z += 32) {
-                    const int r = zr0 + (z >> 6), c = (z & 63) * 2;
-                    if (r >= n || c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS + c) = 0u;
+                if (cols < 128) {
+                    const int rz = min(n, r_hi);
+                    for (int z = lane; z < (rz - r_lo) * 64; z += 32) {
+                        const int r = r_lo + (z >> 6), c = (z & 63) * 2;
+                        if (c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS + c) = 0u;
+                    }
                 }
                 const int nr = max(0, min(n, r_hi) - r_lo);
                 if (lane == 0 && nr > 0) mbar_expect_tx(st.bar, (u32)(nr * cols * 2));
@@ -254,9 +258,11 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
         const float nh = nrm[h];
         const float *Th = T + h * GRAM_N;
         u64 m = 0ull;
-        for (int k = 0; k < 64; k++) {
-            const int j = (k + lane) & 63;
-            if (j <= h || j >= n) continue;
+        const int l0 = lane % n;
+        for (int k = 0; k < n; k++) {
+            int j = k + l0;                          // rotated by lane: distinct banks
+            if (j >= n) j -= n;
+            if (j <= h) continue;
             const float g = Th[j];
             // (n_h - g) + (n_j - g): every intermediate stays as small as the result
             const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
@@ -407,19 +413,26 @@ __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, flo
         __syncwarp();
         return n + 1;
     }
-    for (int i = lane; i < np; i += 32) {
+    // the list is sorted by (rho, id) and holds no v: the candidates in order
+    // are its live entries with v placed at its rank
+    int nl = 0, below = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
         u64 k = KEY_INF;
+        bool live = false;
         if (i < n) {
-            if (!ref_del(ld_ref(d, ids[i]))) k = mkkey(rho[i], ids[i]);
-        } else if (i == n) {
-            k = kv;
+            k = mkkey(rho[i], ids[i]);
+            live = !ref_del(ld_ref(d, ids[i]));
         }
-        keys[i] = k;
+        const u32 lm = __ballot_sync(FULL, live);
+        const int pos = nl + __popc(lm & lanemask_lt()) + (k > kv ? 1 : 0);
+        if (live) keys[pos] = k;
+        below += __popc(__ballot_sync(FULL, live && k < kv));
+        nl += __popc(lm);
     }
+    if (lane == 0) keys[below] = kv;
     __syncwarp();
-    warp_sort_u64(keys, np);
-    int cn = 0;
-    for (int i0 = 0; i0 < np; i0 += 32) cn += __popc(__ballot_sync(FULL, keys[i0 + lane] != KEY_INF));
+    const int cn = nl + 1;
     int nout = warp_prune(d, keys, cn, alive, idx, oid, orho, st);
     for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
     __syncwarp();
