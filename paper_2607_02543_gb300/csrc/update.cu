@@ -1007,27 +1007,56 @@ struct RepairFoldArgs {
 };
 
 __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
-    return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) +
+    return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + 3 * al16((size_t)np * 8) + al16(np) +
            al16((size_t)np * 4) + gram_bytes(gram);
 }
 
 __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
-                            unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho, Stage &st) {
+                            u64 *ka, u64 *kb, unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho,
+                            Stage &st) {
     const int lane = lane_id();
-    for (int i = lane; i < np; i += 32) {
-        u64 k = KEY_INF;
-        if (i < n) {
-            if (lid[i] != u && !ref_del(ld_ref(d, lid[i]))) k = mkkey(lrho[i], lid[i]);
-        } else if (i < n + nk) {
-            const uint2 e = K[i - n];
-            if (!ref_del(ld_ref(d, e.x))) k = mkkey(__uint_as_float(e.y), e.x);
-        }
-        keys[i] = k;
+    // The list (minus u and deleted nodes) and K(u, a) (minus deleted nodes)
+    // are each sorted by (rho, id); compact both, then place every key at its
+    // rank in the union: a list key after the K keys below it, a K key after
+    // the list keys at or below it (an id in both has equal keys: adjacent).
+    int na = 0, nb = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool v = i < n && lid[i] != u && !ref_del(ld_ref(d, lid[i]));
+        const u32 m = __ballot_sync(FULL, v);
+        if (v) ka[na + __popc(m & lanemask_lt())] = mkkey(lrho[i], lid[i]);
+        na += __popc(m);
+    }
+    for (int j0 = 0; j0 < nk; j0 += 32) {
+        const int j = j0 + lane;
+        uint2 e = make_uint2(0u, 0u);
+        if (j < nk) e = K[j];
+        const bool v = j < nk && !ref_del(ld_ref(d, e.x));
+        const u32 m = __ballot_sync(FULL, v);
+        if (v) kb[nb + __popc(m & lanemask_lt())] = mkkey(__uint_as_float(e.y), e.x);
+        nb += __popc(m);
     }
     __syncwarp();
-    warp_sort_u64(keys, np);
-    int cn = 0;
-    for (int i0 = 0; i0 < np; i0 += 32) cn += __popc(__ballot_sync(FULL, keys[i0 + lane] != KEY_INF));
+    for (int i = lane; i < na; i += 32) {
+        const u64 k = ka[i];
+        int lo = 0, hi = nb;                         // K keys < k
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (kb[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        keys[i + lo] = k;
+    }
+    for (int j = lane; j < nb; j += 32) {
+        const u64 k = kb[j];
+        int lo = 0, hi = na;                         // list keys <= k
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ka[mid] <= k) lo = mid + 1; else hi = mid;
+        }
+        keys[j + lo] = k;
+    }
+    __syncwarp();
+    const int cn = na + nb;
     const int nout = warp_prune(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
@@ -1052,6 +1081,8 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
     u32 *tid = reinterpret_cast<u32 *>(p); p += lb;
     float *trho = reinterpret_cast<float *>(p); p += lb;
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    u64 *ka = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    u64 *kb = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
     u32 *idx = reinterpret_cast<u32 *>(p);
     const u64 nwork = a.budget ? a.n_pairs : *a.seg_count;
@@ -1071,7 +1102,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
             for (u32 q = lo; q < hi; q++) {
                 const u32 pv = a.pair_val[q];
                 n = repair_apply(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
-                                 alive, idx, (int)a.np, tid, trho, st);
+                                 ka, kb, alive, idx, (int)a.np, tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
                 if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
@@ -1088,7 +1119,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
                 const int n = repair_apply(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
-                                           (int)a.pair_Kn[pv], keys, alive, idx, (int)a.np, tid, trho, st);
+                                           (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, w, lid, lrho, n, snap);
                 u64 err = 0;
