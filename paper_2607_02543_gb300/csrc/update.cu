@@ -915,11 +915,14 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
         };
         for (int x = 0; x < nb; x++) {
             const float *xr = brow(x);
-            for (int y0 = x + 1; y0 < nb; y0 += 4) {
-                const int y = y0 + grp;
-                const int yy = y < nb ? y : nb - 1;
-                float dd = canon_dist<8>(xr, brow(yy), (int)d.mp, (int)d.metric, g);
+            // two independent rounds of four pairs per trip: their row loads overlap
+            for (int y0 = x + 1; y0 < nb; y0 += 8) {
+                const int y = y0 + grp, y2 = y + 4;
+                const int yy = y < nb ? y : nb - 1, yy2 = y2 < nb ? y2 : nb - 1;
+                const float dd = canon_dist<8>(xr, brow(yy), (int)d.mp, (int)d.metric, g);
+                const float dd2 = canon_dist<8>(xr, brow(yy2), (int)d.mp, (int)d.metric, g);
                 if (y < nb && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
+                if (y2 < nb && g == 0) { M[x * R + y2] = dd2; M[y2 * R + x] = dd2; }
             }
         }
         __syncwarp();
