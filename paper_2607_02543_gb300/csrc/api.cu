@@ -144,6 +144,9 @@ struct etale_index {
         d.n_entries = n_entries.load(std::memory_order_relaxed); d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
         d.gram = cfg.gram == 2 ? 1u : 0u;
         d.xb = xb; d.x8 = x8; d.x8s = x8s; d.mb = mb; d.m8 = m8;
+        // warps pop 8 free slabs at a time when the free pool covers every
+        // resident warp's batch many times over (else one, as Algorithm 1)
+        d.slab_batch = free_lb >= (u64)num_sms * 64 * 8 * 2 ? 8u : 1u;
         d.nent_dev = nent_dev;
         return d;
     }

@@ -111,6 +111,7 @@ struct Dev {
     unsigned char *x8;   // C x m8 e4m3 codes (nullptr if not kept)
     float *x8s;          // C per-vector scales
     u32 mb, m8;          // row strides in elements (16-byte rows)
+    u32 slab_batch;      // free slabs a warp pops at once (1..32; see WarpSlabs)
 };
 
 // ---- canonical distance ------------------------------------------------------
@@ -217,18 +218,75 @@ __device__ __forceinline__ int next_pow2(int n) {
 // Inside one launch the free stack is only popped and the retired stack only
 // pushed, each through one atomic counter; the host-ordered recycle kernel
 // moves retired entries back between launches.
-__device__ __forceinline__ u32 alloc_slab(const Dev &d) {
-    u64 i = atomicAdd(&d.ctr[C_POP], 1ull);
-    u64 nfree = d.ctr[C_FREE];
-    if (i >= nfree) {
-        atomicOr(&d.ctr[C_ERR], (u64)ERR_NOMEM);
-        return NIL;
-    }
-    return d.free_stack[nfree - 1 - i];
-}
 __device__ __forceinline__ void retire_slab(const Dev &d, u32 s) {
     u64 j = atomicAdd(&d.ctr[C_RET], 1ull);
     d.retired[j] = s;
+}
+
+// Per-warp batches of slab pops and retirements (lane j holds entry j of
+// each batch).  A warp pops d.slab_batch free slabs with one atomic and pushes
+// its retirements 32 at a time; before the kernel ends, ws_finish pushes the
+// popped slabs it did not use onto the retired stack, so the recycle step
+// between launches (Lemma 1) returns them.  No slab is reused inside the
+// launch that retired it, as before.  The host sets slab_batch to 1 when the
+// free pool is too small for every resident warp to hold a batch.
+struct WarpSlabs {
+    u32 pop_slab, ret_slab;
+    int npop, nret;      // warp-uniform
+    u64 npub, nretry;    // counted on every lane, added once
+};
+__device__ __forceinline__ void ws_init(WarpSlabs &w) {
+    w.pop_slab = NIL;
+    w.ret_slab = NIL;
+    w.npop = w.nret = 0;
+    w.npub = w.nretry = 0;
+}
+__device__ __forceinline__ u32 ws_pop(const Dev &d, WarpSlabs &w) {
+    const int lane = threadIdx.x & 31;
+    if (w.npop == 0) {
+        const u32 K = d.slab_batch < 1 ? 1u : (d.slab_batch > 32 ? 32u : d.slab_batch);
+        u64 i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&d.ctr[C_POP], (u64)K);
+        i0 = __shfl_sync(0xffffffffu, i0, 0);
+        const u64 nfree = d.ctr[C_FREE];
+        const bool ok = (u32)lane < K && i0 + lane < nfree;
+        w.pop_slab = ok ? d.free_stack[nfree - 1 - (i0 + lane)] : NIL;
+        w.npop = __popc(__ballot_sync(0xffffffffu, ok));
+        if (w.npop == 0) {
+            if (lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_NOMEM);
+            return NIL;
+        }
+    }
+    w.npop--;
+    return __shfl_sync(0xffffffffu, w.pop_slab, w.npop);
+}
+__device__ __forceinline__ void ws_flush(const Dev &d, WarpSlabs &w) {
+    const int lane = threadIdx.x & 31;
+    if (w.nret == 0) return;
+    u64 j0 = 0;
+    if (lane == 0) j0 = atomicAdd(&d.ctr[C_RET], (u64)w.nret);
+    j0 = __shfl_sync(0xffffffffu, j0, 0);
+    if (lane < w.nret) d.retired[j0 + lane] = w.ret_slab;
+    w.nret = 0;
+}
+__device__ __forceinline__ void ws_retire(const Dev &d, WarpSlabs &w, u32 s) {
+    if ((threadIdx.x & 31) == (u32)w.nret) w.ret_slab = s;
+    if (++w.nret == 32) ws_flush(d, w);
+}
+__device__ __forceinline__ void ws_finish(const Dev &d, WarpSlabs &w) {
+    const int lane = threadIdx.x & 31;
+    ws_flush(d, w);
+    if (w.npop > 0) {
+        u64 j0 = 0;
+        if (lane == 0) j0 = atomicAdd(&d.ctr[C_RET], (u64)w.npop);
+        j0 = __shfl_sync(0xffffffffu, j0, 0);
+        if (lane < w.npop) d.retired[j0 + lane] = w.pop_slab;
+        w.npop = 0;
+    }
+    if (lane == 0) {
+        if (w.npub) atomicAdd(&d.ctr[C_PUBLISH], w.npub);
+        if (w.nretry) atomicAdd(&d.ctr[C_CAS_RETRY], w.nretry);
+    }
 }
 
 // Warp-cooperative Publish(u, N) (Algorithm 1).  All 32 lanes call it with
@@ -237,12 +295,10 @@ __device__ __forceinline__ void retire_slab(const Dev &d, u32 s) {
 // installs <delta of snap, n, fresh slab> only if r(u) still equals snap;
 // returns true on success.  On a lost CAS the fresh slab is retired and false
 // is returned (the caller retries or drops the update).
-__device__ __forceinline__ bool warp_publish(const Dev &d, u32 u, const u32 *ids, const float *rho,
-                                             int n, u64 snap) {
+__device__ __forceinline__ bool warp_publish(const Dev &d, WarpSlabs &ws, u32 u, const u32 *ids,
+                                             const float *rho, int n, u64 snap) {
     const int lane = lane_id();
-    u32 s2 = 0;
-    if (lane == 0) s2 = alloc_slab(d);
-    s2 = __shfl_sync(FULL, s2, 0);
+    const u32 s2 = ws_pop(d, ws);
     if (s2 == NIL) return false;
     uint2 *dst = d.slab + (u64)s2 * d.R;
     for (int j = lane; j < n; j += 32) dst[j] = make_uint2(ids[j], __float_as_uint(rho[j]));
@@ -250,18 +306,17 @@ __device__ __forceinline__ bool warp_publish(const Dev &d, u32 u, const u32 *ids
     __syncwarp();
     int ok = 0;
     if (lane == 0) {
-        u64 nw = ref_pack(ref_del(snap), (u32)n, s2);   // carry the deletion flag
-        u64 old = atomicCAS(&d.ref[u], snap, nw);
-        if (old == snap) {
-            ok = 1;
-            if (ref_slab(snap) != NIL) retire_slab(d, ref_slab(snap));
-            atomicAdd(&d.ctr[C_PUBLISH], 1ull);
-        } else {
-            retire_slab(d, s2);
-            atomicAdd(&d.ctr[C_CAS_RETRY], 1ull);
-        }
+        const u64 nw = ref_pack(ref_del(snap), (u32)n, s2);   // carry the deletion flag
+        ok = atomicCAS(&d.ref[u], snap, nw) == snap;
     }
     ok = __shfl_sync(FULL, ok, 0);
+    if (ok) {
+        if (ref_slab(snap) != NIL) ws_retire(d, ws, ref_slab(snap));
+        ws.npub++;
+    } else {
+        ws_retire(d, ws, s2);
+        ws.nretry++;
+    }
     return ok != 0;
 }
 

@@ -469,6 +469,8 @@ __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
     char *gbuf = a.gram ? p : nullptr;
     p += gram_bytes(a.gram);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
+    WarpSlabs ws;
+    ws_init(ws);
     p += stage_bytes(a.ns, d.mp);
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
         snap = __shfl_sync(FULL, snap, 0);
-        if (!warp_publish(d, v, oid, orho, nout, snap) && lane == 0)
+        if (!warp_publish(d, ws, v, oid, orho, nout, snap) && lane == 0)
             atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         const u32 invalid = (u32)d.capacity;
         for (u32 j = lane; j < R; j += 32) {
@@ -506,6 +508,7 @@ __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
         if (lane == 0) a.F_n[t] = (u32)nout;
         __syncwarp();
     }
+    ws_finish(d, ws);
     stage_done(d, st);
 }
 
@@ -566,6 +569,8 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
     char *gbuf = a.gram ? p : nullptr;
     p += gram_bytes(a.gram);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
+    WarpSlabs ws;
+    ws_init(ws);
     p += stage_bytes(a.ns, d.mp);
     const size_t lb = al16((size_t)R * 4 + 4);
     u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
@@ -597,7 +602,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
                                 tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
-                if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+                if (!warp_publish(d, ws, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
             t += a.lo;
@@ -613,7 +618,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
                 __syncwarp();
                 const int n = apply_offer(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
-                done = warp_publish(d, w, lid, lrho, n, snap);
+                done = warp_publish(d, ws, w, lid, lrho, n, snap);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
                 if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
@@ -622,6 +627,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
         }
         __syncwarp();
     }
+    ws_finish(d, ws);
     stage_done(d, st);
 }
 
@@ -679,6 +685,8 @@ __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
     char *gbuf = a.gram ? p : nullptr;
     p += gram_bytes(a.gram);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
+    WarpSlabs ws;
+    ws_init(ws);
     p += stage_bytes(a.ns, d.mp);
     u32 *nid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *nrho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
@@ -769,7 +777,7 @@ __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
         const int n = min(nc, (int)a.max_cand);
         const int nout = warp_prune(d, buf, n, alive, idx, oid, orho, st);
         if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
-            if (!warp_publish(d, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+            if (!warp_publish(d, ws, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         }
         const u32 invalid = (u32)d.capacity;
         for (u32 j = lane; j < R; j += 32) {
@@ -786,6 +794,7 @@ __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
         }
         __syncwarp();
     }
+    ws_finish(d, ws);
     stage_done(d, st);
 }
 
@@ -1075,6 +1084,8 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
     char *gbuf = a.gram ? p : nullptr;
     p += gram_bytes(a.gram);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
+    WarpSlabs ws;
+    ws_init(ws);
     p += stage_bytes(a.ns, d.mp);
     const size_t lb = al16((size_t)R * 4 + 4);
     u32 *lid = reinterpret_cast<u32 *>(p); p += lb;
@@ -1108,7 +1119,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
                                  ka, kb, alive, idx, (int)a.np, tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
-                if (!warp_publish(d, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+                if (!warp_publish(d, ws, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
             t += a.lo;
@@ -1124,7 +1135,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
                 const int n = repair_apply(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
                                            (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
-                done = warp_publish(d, w, lid, lrho, n, snap);
+                done = warp_publish(d, ws, w, lid, lrho, n, snap);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
                 if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
@@ -1133,6 +1144,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
         }
         __syncwarp();
     }
+    ws_finish(d, ws);
     stage_done(d, st);
 }
 
@@ -1179,6 +1191,8 @@ __global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const 
     const u64 myid = base + lane;
     const u64 myref = myid < next_id ? ld_ref(d, (u32)myid) : ref_pack(1, 0, NIL);
     const u32 R = d.R;
+    WarpSlabs ws;
+    ws_init(ws);
     for (int t = 0; t < 32; t++) {
         const u64 r = __shfl_sync(FULL, myref, t);
         if (ref_del(r) || ref_slab(r) == NIL) continue;
@@ -1210,10 +1224,11 @@ __global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const 
         __syncwarp();
         // a lost CAS here means another writer touched the node during the
         // reclaim launch, which the launch discipline forbids
-        if (!warp_publish(d, (u32)(base + t), sid[warp], srho[warp], nk, r) && lane == 0)
+        if (!warp_publish(d, ws, (u32)(base + t), sid[warp], srho[warp], nk, r) && lane == 0)
             atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         __syncwarp();
     }
+    ws_finish(d, ws);
 }
 
 cudaError_t launch_compact(const Dev &d, u64 next_id, const u32 *tomb_bits, cudaStream_t st) {
