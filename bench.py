@@ -36,7 +36,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="etale", choices=["etale", "reference"])
-    ap.add_argument("--workload", default="int256-1m-d128", choices=["int256-1m-d128", "gauss64-10k-d128"])
+    ap.add_argument("--workload", default="int256-1m-d128",
+                    choices=["int256-1m-d128", "gauss64-10k-d128", "unit768-1m-ip"])
     ap.add_argument("--mode", default="lockfree", choices=["lockfree", "deterministic"])
     ap.add_argument("--search-beam", type=int, default=0,
                     help="EF_SEARCH; default: the smallest of 64..256 reaching Recall@10 >= 0.95")
@@ -51,8 +52,13 @@ def parse():
     return ap.parse_args()
 
 
+WORKLOADS = {"int256-1m-d128": W.SIFT_LIKE_1M, "gauss64-10k-d128": W.SMALL, "unit768-1m-ip": W.UNIT768_1M}
+# workloads that keep reduced-precision search copies (reported per precision)
+PRECISION_WORKLOADS = {"unit768-1m-ip"}
+
+
 def workload(name: str, n_live: int = 0) -> W.Workload:
-    w = W.SIFT_LIKE_1M if name == "int256-1m-d128" else W.SMALL
+    w = WORKLOADS[name]
     return W.scaled(w, n_live) if n_live else w
 
 
@@ -175,6 +181,62 @@ def config_dict(w, args):
                   "small index; no flush", "parallelism": f"replicas x{args.gpus}"}
 
 
+def precision_sweep(idx, d_q, gt_np, plan, w, stream, out_ids, out_d) -> dict:
+    """Per search precision (fp32, bf16, fp8 + exact fp32 rerank): the smallest
+    beam of 64..256 reaching Recall@10 >= 0.95, the query batch time at that
+    beam (CUDA events, best of 3), and the largest relative error of the
+    returned distances against fp64 on 200 sampled queries."""
+    import torch
+    out = {}
+    sample = np.arange(0, len(plan.queries), max(1, len(plan.queries) // 200))
+    Q64 = plan.queries.astype(np.float64)
+    for prec in ("fp32", "bf16", "fp8"):
+        idx.set_search_precision(prec)
+        chosen, rec = None, 0.0
+        for b in (64, 96, 128, 160, 192, 256):
+            idx.search(d_q, w.k, b, stream, out=(out_ids, out_d))
+            got = out_ids.cpu().numpy().view(np.uint32)
+            rec = float(np.mean([len(set(a.tolist()) & set(g.tolist())) / w.k for a, g in zip(got, gt_np)]))
+            chosen = b
+            if rec >= 0.95:
+                break
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            idx.search(d_q, w.k, chosen, stream, out=(out_ids, out_d))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        ids = out_ids.cpu().numpy().view(np.uint32)
+        dist = out_d.cpu().numpy()
+        err = 0.0
+        X = idx_rows(idx, plan, w)
+        for t in sample:
+            for j in range(w.k):
+                if ids[t, j] == 0xFFFFFFFF:
+                    continue
+                x = X(int(ids[t, j]))
+                ex = 1.0 - float(Q64[t] @ x) if w.metric == "ip" else float(((Q64[t] - x) ** 2).sum())
+                err = max(err, abs(float(dist[t, j]) - ex) / max(abs(ex), 1e-12))
+        out[prec] = {"beam": chosen, "recall_at_10": rec, "ms_per_batch": best,
+                     "qps": len(plan.queries) / (best * 1e-3), "max_rel_dist_err_vs_fp64": err}
+    idx.set_search_precision("fp32")
+    return out
+
+
+def idx_rows(idx, plan, w):
+    """Row of an id in fp64, from the plan's base and insert batches (ids are
+    handed out in that order)."""
+    chunks = [plan.base] + list(plan.inserts)
+    starts = np.cumsum([0] + [len(c) for c in chunks])
+
+    def row(i):
+        c = int(np.searchsorted(starts, i, side="right") - 1)
+        return chunks[c][i - starts[c]].astype(np.float64)
+    return row
+
+
 def reduce_max(vals, world: int, device) -> list:
     """Element-wise maximum over ranks (identity on one rank)."""
     import torch
@@ -210,8 +272,9 @@ def main():
     wr = W.dataclasses.replace(w, rounds=total_rounds)
     plan = W.make_plan(wr)
     n_entry = args.n_entry
+    precisions = args.workload in PRECISION_WORKLOADS
     idx = Index(w.dim, w.metric, w.degree, wr.capacity, build_beam=w.build_beam, mode=args.mode,
-                n_entry=n_entry, max_cand=args.max_cand)
+                n_entry=n_entry, max_cand=args.max_cand, copies=("bf16", "fp8") if precisions else ())
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
@@ -329,6 +392,9 @@ def main():
     gt_np = gt_ids.cpu().numpy().view(np.uint32)
     recall = recall_of(out_ids)
     ginfo = idx.ground_truth_info()
+    prec_block = None
+    if precisions:
+        prec_block = precision_sweep(idx, d_q, gt_np, plan, w, stream, out_ids, out_d)
     live_now = idx.stats()["live"]
     gt_flop = 2.0 * w.n_queries * live_now * w.dim
     tc_ms = gprof["gt_tensor"][0]
@@ -398,6 +464,7 @@ def main():
                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "kernel_ms": kernel_ms},
                "phase_ms_per_step": phases, "ground_truth": gt_block, "search_tuning": tuning,
+               "precision": prec_block,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)

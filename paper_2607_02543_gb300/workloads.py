@@ -60,6 +60,15 @@ SIFT_LIKE_1M = Workload("int256-1m-d128", 1_000_000, 128, "l2", 32, 128, 20,
                         10_000, 10_000, 10_000, 10, 64, 256, "int")
 
 
+# 1,000,000 x 768 unit vectors (text-embedding shape), inner product, degree 64,
+# 1,024 centres, 10 rounds of 1% churn; kept with BF16 and FP8 search copies.
+UNIT768_1M = Workload("unit768-1m-ip", 1_000_000, 768, "ip", 64, 128, 10,
+                      10_000, 10_000, 10_000, 10, 64, 1024, "unit")
+# 10,000,000 x 96 Gaussian mixture (1,000 centres), the served configuration.
+GAUSS96_10M = Workload("gauss96-10m-d96", 10_000_000, 96, "l2", 32, 64, 1,
+                       0, 0, 1_000, 10, 64, 1000, "gauss")
+
+
 def scaled(w: Workload, n_base: int, churn_frac: float = 0.01,
            n_queries: int | None = None, rounds: int | None = None) -> Workload:
     """The same mixture family at another size (tests and bounded samples)."""
