@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving run on the 10M x 96 mixture: Poisson queries with interleaved updates")
+    ap.add_argument("--qps-target", type=float, default=50_000.0, help="serving: query arrival rate (1/s)")
+    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     return ap.parse_args()
 
 
@@ -247,9 +251,99 @@ def reduce_max(vals, world: int, device) -> list:
     return [float(x) for x in t.tolist()]
 
 
+def run_serve(args):
+    """Serving run (continuous batching, queries and updates overlapping on
+    two streams): Poisson query arrivals at --qps-target, insert and delete
+    requests of U{1..4096} vectors totalling 5% of the live set per minute,
+    BF16 search copies with the exact fp32 rerank.  Reports query and update
+    latency percentiles, throughput, Recall@10 of a fixed anchor query set
+    before and after the run, and the index's device bytes over time."""
+    import torch
+    from paper_2607_02543_gb300 import Index, build as B
+    from paper_2607_02543_gb300.serve import Request, Server, poisson_stream
+    B.build()
+    base_w = W.GAUSS96_10M
+    n = args.n_live or base_w.n_base
+    w = W.dataclasses.replace(base_w, name=base_w.name if n == base_w.n_base else f"{base_w.name}@{n}", n_base=n)
+    mix = W.Mixture(w)
+    churn_per_s = 0.05 * n / 60.0
+    n_upd_vec = int(churn_per_s * args.duration * 1.2) + 4096
+    X = mix.draw("base", n)
+    fresh = mix.draw("inserts", n_upd_vec)
+    anchors = mix.draw("queries", w.n_queries)
+    rng = np.random.default_rng(w.seed)
+    qarr = poisson_stream(rng, args.qps_target, args.duration)
+    qrows = mix.draw("stream", len(qarr))
+    dev = torch.device("cuda", 0)
+    idx = Index(w.dim, w.metric, w.degree, n + n_upd_vec + 10, build_beam=w.build_beam, mode="lockfree",
+                n_entry=args.n_entry, max_cand=args.max_cand, copies=("bf16",))
+    t0 = time.perf_counter()
+    idx.insert(torch.from_numpy(X).to(dev))
+    idx.reclaim()
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    idx.set_search_precision("bf16")
+    d_a = torch.from_numpy(anchors).to(dev)
+
+    def anchor_recall(beam):
+        gt, _ = idx.ground_truth(d_a, w.k)
+        ids, _ = idx.search(d_a, w.k, beam)
+        g, r = gt.cpu().numpy().view(np.uint32), ids.cpu().numpy().view(np.uint32)
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w.k for a, b in zip(r, g)]))
+
+    beam, rec0 = 256, 0.0
+    for b in (32, 48, 64, 96, 128, 192, 256):
+        rec0 = anchor_recall(b)
+        if rec0 >= 0.95:
+            beam = b
+            break
+    reqs = [Request(float(t), "query", qrows[i]) for i, t in enumerate(qarr)]
+    live = np.arange(n, dtype=np.uint32)
+    rng.shuffle(live)
+    t_u, off_i, off_d = 0.0, 0, 0
+    while True:
+        size = int(rng.integers(1, 4097))
+        t_u += size / churn_per_s * float(rng.exponential(1.0))
+        if t_u >= args.duration:
+            break
+        if rng.random() < 0.5 and off_i + size <= len(fresh):
+            reqs.append(Request(t_u, "insert", fresh[off_i:off_i + size]))
+            off_i += size
+        elif off_d + size <= len(live):
+            reqs.append(Request(t_u, "delete", live[off_d:off_d + size]))
+            off_d += size
+    reqs.sort(key=lambda r: r.t)
+    streams = (torch.cuda.Stream(), torch.cuda.Stream())
+    srv = Server(idx, k=w.k, beam=beam, streams=streams)
+    out = srv.run(reqs)
+    idx.reclaim()
+    torch.cuda.synchronize()
+    rec1 = anchor_recall(beam)
+    st = idx.stats()
+    R = w.degree
+    row_bytes = w.dim * 4 + ((w.dim + 7) // 8 * 8) * 2 + 8        # fp32 row, bf16 copy, reference word
+    bytes_over_time = [{"t": round(e["t"], 3), "live": e["live"],
+                        "bytes": e["live"] * row_bytes + e["used_slabs"] * 8 * R} for e in srv.stats_over_time]
+    res = {"metric": "p99 query latency, Poisson queries with 5%/min churn", "value": out["queries"]["p99_ms"],
+           "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "bf16 search + f32 rerank",
+           "data": "synthetic",
+           "config": {"workload": w.name, "n_live": n, "dim": w.dim, "degree": R, "build_beam": w.build_beam,
+                      "query_rate_per_s": args.qps_target, "duration_s": args.duration,
+                      "update_vectors_per_s": churn_per_s, "search_beam": beam, "k": w.k},
+           "queries": out["queries"], "updates": out["updates"], "query_throughput": out["query_throughput"],
+           "update_vectors_per_s": out["update_vectors_per_s"], "query_batches": out["query_batches"],
+           "update_batches": out["update_batches"], "deferred": out["deferred"], "reclaims": out["reclaims"],
+           "recall_at_10_anchor": {"before": rec0, "after": rec1}, "build_s": build_s,
+           "index_bytes_over_time": bytes_over_time[:: max(1, len(bytes_over_time) // 20)],
+           "stats": {k2: st[k2] for k2 in ("live", "used_slabs", "n_dropped", "n_publish")}}
+    print(json.dumps(res), flush=True)
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.serve:
+        return run_serve(args)
     w = workload(args.workload, args.n_live)
     if args.impl == "reference":
         return run_reference(args, w)

@@ -17,7 +17,7 @@ import math
 
 import numpy as np
 
-STREAMS = ("centers", "base", "inserts", "deletes", "queries", "assign")
+STREAMS = ("centers", "base", "inserts", "deletes", "queries", "assign", "stream")   # appended only: earlier streams keep their seeds
 
 
 def _streams(seed: int) -> dict[str, np.random.Generator]:
