@@ -39,11 +39,15 @@ constexpr int GRAM_RS = 136;
 // Shared-memory bytes of a Gram buffer for `rows` candidates: the bf16 rows
 // (or the table over them) and the norms; 0 rows = no buffer.
 __host__ __device__ inline size_t gram_bytes(u32 rows) {
-    return rows ? (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15) + (((size_t)rows * 4 + 15) & ~(size_t)15) : 0;
+    if (!rows) return 0;
+    const size_t b = (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15) + (((size_t)rows * 4 + 15) & ~(size_t)15);
+    return rows > (u32)GRAM_N ? b + (size_t)rows * 16 : b;   // domination masks of the large path
 }
+constexpr int GRAM_NL = 128;   // candidates of the large (mask) path
 // Gram rows for a kernel whose prunes see at most max_n candidates (0: the
-// Gram path is off or cannot hold them).
-inline u32 gram_rows_for(u32 on, u32 max_n) { return on && max_n <= (u32)GRAM_N ? (max_n + 15) / 16 * 16 : 0; }
+// Gram path is off or cannot hold them).  Above GRAM_N rows the kernel runs
+// the large path (warp_prune_masks).
+inline u32 gram_rows_for(u32 on, u32 max_n) { return on && max_n <= (u32)GRAM_NL ? (max_n + 15) / 16 * 16 : 0; }
 
 // Shared-memory bytes for a stage of ns rows plus its mbarrier.
 __host__ __device__ inline size_t stage_bytes(u32 ns, u32 mp) { return al16((size_t)ns * mp * 4) + 16; }
@@ -294,6 +298,160 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
     __syncwarp();
     return nout;
 }
+// RobustPrune on the tensor-core Gram for up to GRAM_NL candidates, with no
+// table in shared memory: the Gram is built in 16-row stripes, last stripe
+// first, so that by the time a stripe is converted the norms of every column
+// it reads are known (this stripe's diagonal, or a later stripe's).  Each
+// accumulator entry (i, j), j > i, becomes bit j of row i's domination mask
+// (alpha^2 * d(i, j) <= rho(j)); the four lanes of a quad hold the columns of
+// a row and OR their bits.  The greedy pass is the register walk of
+// warp_prune_gram over 128-bit masks.  Same distances as warp_prune_gram:
+// squared L2 as (G_ii - G_ij) + (G_jj - G_ij), inner product as 1 - G_ij.
+__device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id, float *out_rho, Stage &st) {
+    constexpr int NT = GRAM_NL / 8;
+    const int lane = lane_id();
+    const int rows = st.gram_rows;
+    __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(st.gram);
+    char *tail = st.gram + (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15);
+    float *nrm = reinterpret_cast<float *>(tail);
+    u64 *dom = reinterpret_cast<u64 *>(tail + (((size_t)rows * 4 + 15) & ~(size_t)15));
+    const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
+    const int nkb = ((int)d.mp + 127) >> 7;
+    const u32 xs = smem_addr(X);
+    for (int mt = nm - 1; mt >= 0; mt--) {
+        float acc[NT][4];
+#pragma unroll
+        for (int b = 0; b < NT; b++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
+        for (int kb = 0; kb < nkb; kb++) {
+            if (nkb > 1 || mt == nm - 1) {
+                // rows [r_lo, n) of columns [128 kb, 128 kb + 128): all rows once
+                // when one block covers the row, else those of this stripe on
+                const int r_lo = nkb > 1 ? 16 * mt : 0;
+                __syncwarp();
+                if (d.xb) {
+                    const int cols = min(128, (int)d.mb - 128 * kb);
+                    if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (cols < 128)
+                        for (int z = lane; z < (n - r_lo) * 64; z += 32) {
+                            const int r = r_lo + (z >> 6), c = (z & 63) * 2;
+                            if (c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS + c) = 0u;
+                        }
+                    const int nr = n - r_lo;
+                    if (lane == 0 && nr > 0) mbar_expect_tx(st.bar, (u32)(nr * cols * 2));
+                    __syncwarp();
+                    for (int r = r_lo + lane; r < n; r += 32)
+                        bulk_g2s(X + (size_t)r * GRAM_RS, d.xb + (size_t)key_id(ck[r]) * d.mb + 128 * kb,
+                                 (u32)cols * 2, st.bar);
+                    if (nr > 0) {
+                        if (!mbar_wait(st.bar, st.phase, WAIT_LIMIT)) {
+                            st.timeout = true;
+                            mbar_wait(st.bar, st.phase, WAIT_LIMIT);   // let copies in flight land
+                        }
+                        st.phase ^= 1u;
+                    }
+                } else {
+                    const int col = 128 * kb + 4 * lane;
+                    for (int r = r_lo; r < n; r++) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (col < (int)d.mp)
+                            v = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
+                        *reinterpret_cast<uint2 *>(X + (size_t)r * GRAM_RS + 4 * lane) =
+                            make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+                    }
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int ks = 0; ks < 8; ks++) {
+                u32 a0, a1, a2, a3;
+                const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                const int ac = 16 * ks + 8 * (lane >> 4);
+                ldsm_x4(a0, a1, a2, a3, xs + (u32)((ar * GRAM_RS + ac) * 2));
+#pragma unroll
+                for (int nt = 0; nt < NT; nt += 2) {
+                    if (nt < 2 * mt || nt >= nn) continue;
+                    u32 b0, b1, b2, b3;
+                    const int br = 8 * nt + (lane & 7) + 8 * (lane >> 4);
+                    const int bc = 16 * ks + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(b0, b1, b2, b3, xs + (u32)((br * GRAM_RS + bc) * 2));
+                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b1);
+                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+        // this stripe's diagonal: entry (r, r) sits in tile 2 mt (rows r0) or 2 mt + 1 (rows r0 + 8)
+        const int r0 = 16 * mt + (lane >> 2), r1 = r0 + 8, cq = 2 * (lane & 3);
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) {
+            if (nt == 2 * mt) {
+                if (cq == (lane >> 2) && r0 < n) nrm[r0] = acc[nt][0];
+                if (cq + 1 == (lane >> 2) && r0 < n) nrm[r0] = acc[nt][1];
+            }
+            if (nt == 2 * mt + 1) {
+                if (cq == (lane >> 2) && r1 < n) nrm[r1] = acc[nt][2];
+                if (cq + 1 == (lane >> 2) && r1 < n) nrm[r1] = acc[nt][3];
+            }
+        }
+        __syncwarp();
+        const float n0 = r0 < n ? nrm[r0] : 0.f, n1 = r1 < n ? nrm[r1] : 0.f;
+        u64 m0l = 0, m0h = 0, m1l = 0, m1h = 0;
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) {
+            if (nt < 2 * mt || nt >= nn) continue;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int r = e < 2 ? r0 : r1, c = 8 * nt + cq + (e & 1);
+                if (c <= r || c >= n || r >= n) continue;
+                const float g = acc[nt][e];
+                const float nr_ = e < 2 ? n0 : n1;
+                const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nr_, g), __fsub_rn(nrm[c], g)) : __fsub_rn(1.0f, g);
+                if (__fmul_rn(d.alpha2, dd) <= key_rho(ck[c])) {
+                    const u64 bit = 1ull << (c & 63);
+                    if (e < 2) { if (c < 64) m0l |= bit; else m0h |= bit; }
+                    else { if (c < 64) m1l |= bit; else m1h |= bit; }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+            m0l |= __shfl_xor_sync(FULL, m0l, o);
+            m0h |= __shfl_xor_sync(FULL, m0h, o);
+            m1l |= __shfl_xor_sync(FULL, m1l, o);
+            m1h |= __shfl_xor_sync(FULL, m1h, o);
+        }
+        if ((lane & 3) == 0) {
+            if (r0 < n) { dom[2 * r0] = m0l; dom[2 * r0 + 1] = m0h; }
+            if (r1 < n) { dom[2 * r1] = m1l; dom[2 * r1 + 1] = m1h; }
+        }
+        __syncwarp();
+    }
+    // equal adjacent keys collapse to one
+    u64 lo = 0, hi = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const u64 b = __ballot_sync(FULL, i < n && (i == 0 || ck[i] != ck[i - 1]));
+        if (i0 < 64) lo |= b << i0; else hi |= b << (i0 - 64);
+    }
+    int nout = 0;
+    const int R = (int)d.R;
+    while (nout < R && (lo | hi)) {
+        const int head = lo ? __ffsll((long long)lo) - 1 : 64 + __ffsll((long long)hi) - 1;
+        if (head < 64) lo &= lo - 1; else hi &= hi - 1;
+        if (lane == 0) {
+            const u64 hk = ck[head];
+            out_id[nout] = key_id(hk);
+            out_rho[nout] = key_rho(hk);
+        }
+        nout++;
+        lo &= ~dom[2 * head];
+        hi &= ~dom[2 * head + 1];
+    }
+    __syncwarp();
+    return nout;
+}
+
 // ---------------------------------------------------------------------------
 // RobustPrune over n candidates whose keys ck[0..n) are sorted ascending
 // (rho = distance to the owner).  Equal adjacent keys collapse to one.  The
@@ -302,9 +460,14 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
 // distances, 8 lanes per distance, rows taken from the stage when staged.
 // Scratch: alive[n], idx[n].
 // ---------------------------------------------------------------------------
+// LG: the kernel's Gram buffer holds more than GRAM_N rows (the large path).
+template <bool LG>
 __device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx, u32 *out_id,
                           float *out_rho, Stage &st) {
-    if (st.gram && n <= st.gram_rows) return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
+    if (st.gram && n <= st.gram_rows) {
+        if constexpr (LG) return warp_prune_masks(d, ck, n, out_id, out_rho, st);
+        else return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
+    }
     const int lane = lane_id();
     const int grp = lane >> 3, g = lane & 7;
     const int ns = st.rows ? min(n, st.ns_cap) : 0;
@@ -391,6 +554,7 @@ __device__ __forceinline__ bool warp_contains(const u32 *ids, int n, u32 v) {
 // a present id is a no-op; below R the entry is inserted in (rho, id) order;
 // at R the list is RobustPrune(list + v) about the owner (tombstones drop).
 // Scratch: keys[np], alive[np], idx[np] with np >= R + 1 (power of two).
+template <bool LG>
 __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, float vr, u64 *keys,
                            unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho, Stage &st) {
     const int lane = lane_id();
@@ -433,7 +597,7 @@ __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, flo
     if (lane == 0) keys[below] = kv;
     __syncwarp();
     const int cn = nl + 1;
-    int nout = warp_prune(d, keys, cn, alive, idx, oid, orho, st);
+    int nout = warp_prune<LG>(d, keys, cn, alive, idx, oid, orho, st);
     for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
     __syncwarp();
     return nout;
@@ -460,6 +624,7 @@ __host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u3
            gram_bytes(gram);
 }
 
+template <bool LG>
 __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -487,7 +652,7 @@ __global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
         __syncwarp();
         warp_sort_u64(keys, (int)a.np);
         const int n = (int)min(cnt, a.max_cand);
-        const int nout = warp_prune(d, keys, n, alive, idx, oid, orho, st);
+        const int nout = warp_prune<LG>(d, keys, n, alive, idx, oid, orho, st);
         const u32 v = a.first + t;
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
@@ -526,17 +691,20 @@ cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_k
     const size_t wb = prune_ins_warp_bytes(np, d.R, a.ns, d.mp, gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(prune_insert_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)prune_insert_kernel<true> : (const void *)prune_insert_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, prune_insert_kernel, 32 * W, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, a.gram > (u32)GRAM_N ? (const void *)prune_insert_kernel<true> : (const void *)prune_insert_kernel<false>, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms), need = (b + W - 1) / W;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    prune_insert_kernel<<<blocks, 32 * W, smem, st>>>(a);
+    if (a.gram > (u32)GRAM_N) prune_insert_kernel<true><<<blocks, 32 * W, smem, st>>>(a);
+    else prune_insert_kernel<false><<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -560,6 +728,7 @@ __host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp,
            al16((size_t)np * 4) + gram_bytes(gram);
 }
 
+template <bool LG>
 __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -598,7 +767,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
             int n = n0;
             for (u32 q = lo; q < hi; q++) {
                 const u32 pi = a.of.val[q];
-                n = apply_offer(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
+                n = apply_offer<LG>(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
                                 tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
@@ -616,7 +785,7 @@ __global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
-                const int n = apply_offer(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
+                const int n = apply_offer<LG>(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, ws, w, lid, lrho, n, snap);
                 u64 err = 0;
@@ -644,10 +813,12 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     const size_t wb = fold_warp_bytes(np, d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(offer_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)offer_fold_kernel<true> : (const void *)offer_fold_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, offer_fold_kernel, 32 * W, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, a.gram > (u32)GRAM_N ? (const void *)offer_fold_kernel<true> : (const void *)offer_fold_kernel<false>, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const u32 items = budget ? a.hi - a.lo : of.n;
@@ -655,7 +826,8 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    offer_fold_kernel<<<blocks, 32 * W, smem, st>>>(a);
+    if (a.gram > (u32)GRAM_N) offer_fold_kernel<true><<<blocks, 32 * W, smem, st>>>(a);
+    else offer_fold_kernel<false><<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -676,6 +848,7 @@ __host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 
            al16((size_t)np * 4) + al16((size_t)cap * 4) + gram_bytes(gram);
 }
 
+template <bool LG>
 __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -775,7 +948,7 @@ __global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
         __syncwarp();
         warp_sort_u64(buf, np3);
         const int n = min(nc, (int)a.max_cand);
-        const int nout = warp_prune(d, buf, n, alive, idx, oid, orho, st);
+        const int nout = warp_prune<LG>(d, buf, n, alive, idx, oid, orho, st);
         if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
             if (!warp_publish(d, ws, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         }
@@ -809,22 +982,25 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     u32 np = 32;
     while (np < cap + d.R) np <<= 1;
     a.np = np;
-    a.gram = d.gram ? (u32)GRAM_N : 0u;
+    a.gram = d.gram ? (d.R > 32 ? (u32)GRAM_NL : (u32)GRAM_N) : 0u;
     a.ns = d.gram ? 0 : stage_cap(d.mp, max_cand, d.stage_bytes);
     const size_t wb = refine_warp_bytes(np, cap, d.R, a.ns, d.mp, a.gram);
     const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
     size_t smem = warps * wb;
-    cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)refine_kernel<true> : (const void *)refine_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_kernel, 32 * warps, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, a.gram > (u32)GRAM_N ? (const void *)refine_kernel<true> : (const void *)refine_kernel<false>, 32 * warps, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms), need = (b + warps - 1) / warps;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    refine_kernel<<<blocks, 32 * warps, smem, st>>>(a);
+    if (a.gram > (u32)GRAM_N) refine_kernel<true><<<blocks, 32 * warps, smem, st>>>(a);
+    else refine_kernel<false><<<blocks, 32 * warps, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1023,6 +1199,7 @@ __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp,
            al16((size_t)np * 4) + gram_bytes(gram);
 }
 
+template <bool LG>
 __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
                             u64 *ka, u64 *kb, unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho,
                             Stage &st) {
@@ -1069,12 +1246,13 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     }
     __syncwarp();
     const int cn = na + nb;
-    const int nout = warp_prune(d, keys, cn, alive, idx, tid, trho, st);
+    const int nout = warp_prune<LG>(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
     return nout;
 }
 
+template <bool LG>
 __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -1115,7 +1293,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
             int n = n0;
             for (u32 q = lo; q < hi; q++) {
                 const u32 pv = a.pair_val[q];
-                n = repair_apply(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
+                n = repair_apply<LG>(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
                                  ka, kb, alive, idx, (int)a.np, tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
@@ -1132,7 +1310,7 @@ __global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
-                const int n = repair_apply(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
+                const int n = repair_apply<LG>(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
                                            (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st);
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, ws, w, lid, lrho, n, snap);
@@ -1162,10 +1340,12 @@ cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key,
     const size_t wb = repf_warp_bytes(np, d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(repair_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)repair_fold_kernel<true> : (const void *)repair_fold_kernel<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_fold_kernel, 32 * W, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, a.gram > (u32)GRAM_N ? (const void *)repair_fold_kernel<true> : (const void *)repair_fold_kernel<false>, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u64 need = (n_pairs + W - 1) / W;
@@ -1173,7 +1353,8 @@ cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key,
     if ((u64)blocks > need) blocks = (u32)need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    repair_fold_kernel<<<blocks, 32 * W, smem, st>>>(a);
+    if (a.gram > (u32)GRAM_N) repair_fold_kernel<true><<<blocks, 32 * W, smem, st>>>(a);
+    else repair_fold_kernel<false><<<blocks, 32 * W, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -73,6 +73,10 @@ CASES = [
     # is exact, so the result must still match the oracle bit for bit
     (128, "l2", 32, "int", 1500, 96, {"gram": "tensor"}),
     (200, "l2", 24, "int", 800, 48, {"gram": "tensor"}),   # two K chunks of 128, ragged
+    # more than 64 candidates: the mask path (repairs of R = 64 see up to 127,
+    # offers 65; R = 48 repairs see up to 95 over two K chunks)
+    (128, "l2", 64, "int", 1500, 96, {"gram": "tensor"}),
+    (200, "l2", 48, "int", 900, 64, {"gram": "tensor"}),
     # rows staged in shared memory by bulk copies (canonical arithmetic)
     (128, "l2", 32, "gauss", 1200, 64, {"stage_kb": 24}),
 ]
