@@ -53,6 +53,9 @@ def parse():
                     help="serving run on the 10M x 96 mixture: Poisson queries with interleaved updates")
     ap.add_argument("--qps-target", type=float, default=50_000.0, help="serving: query arrival rate (1/s)")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--experiment", default="", choices=["", "reclaim_interval", "deletion_stress",
+                                                         "concurrent_latency"],
+                    help="one of the measurements in paper_2607_02543_gb300/experiments.py (a JSON line)")
     return ap.parse_args()
 
 
@@ -353,6 +356,14 @@ def main():
     args = parse()
     if args.serve:
         return run_serve(args)
+    if args.experiment:
+        from paper_2607_02543_gb300 import build as B, experiments as X
+        B.build()
+        w = workload(args.workload, args.n_live)
+        fn = {"reclaim_interval": X.run_reclaim_interval, "deletion_stress": X.run_deletion_stress,
+              "concurrent_latency": X.run_concurrent_latency}[args.experiment]
+        print(json.dumps(fn(w)), flush=True)
+        return
     w = workload(args.workload, args.n_live)
     if args.impl == "reference":
         return run_reference(args, w)
