@@ -86,44 +86,48 @@ def _build(w: W.Workload, capacity: int, mode: str = "lockfree", n_entry: int = 
 
 
 # ---- f1: reclaim interval ----------------------------------------------------
-def run_reclaim_interval(w: W.Workload, checkpoints=(1_000, 2_000, 5_000, 10_000, 20_000, 50_000, 100_000,
-                                                      200_000)) -> dict:
-    """For each t: delete t uniformly chosen live ids (no reclaim in between),
-    count dead edges and dirty nodes, time one Reclaim (CUDA events), read the
-    republications it made (its dirty-node count), then insert t fresh rows
-    so that every checkpoint starts from about the same live set."""
+def run_reclaim_interval(w: W.Workload, rounds=(1, 2, 4, 8, 12, 16, 24, 32)) -> dict:
+    """Tombstones accumulate over churn rounds with no Reclaim in between (each
+    round: 1% of the live set deleted uniformly, as many fresh rows inserted),
+    as when reclamation is deferred.  For each T in `rounds` a fresh index is
+    built and churned T rounds; then dead edges (live -> tombstone) and dirty
+    nodes (live nodes with one) are counted from the exported graph, and one
+    Reclaim is timed (CUDA events) with the republications it makes, which
+    equal the dirty-node count.  t = tombstones accumulated."""
     import torch
     mix = W.Mixture(w)
-    fresh = mix.draw("inserts", int(sum(checkpoints)))
-    idx, _ = _build(w, w.n_base + int(sum(checkpoints)) + 10)
-    rng = np.random.default_rng(w.seed + 1)
-    pts, off = [], 0
-    for t in checkpoints:
-        g = idx.export_graph()
-        live_ids = np.nonzero((g[0] == 0) & (g[1] == 1))[0].astype(np.uint32)
-        dele = rng.choice(live_ids, size=t, replace=False).astype(np.uint32)
-        idx.delete(dele)
+    n_ch = max(1, w.n_base // 100)
+    fresh = mix.draw("inserts", n_ch * max(rounds))
+    pts = []
+    for T in rounds:
+        idx, _ = _build(w, w.n_base + n_ch * max(rounds) + 10)
+        rng = np.random.default_rng(w.seed + 1)
+        alive = np.zeros(w.n_base + n_ch * max(rounds) + 10, bool)
+        alive[:w.n_base] = True
+        for r in range(T):
+            dele = rng.choice(np.nonzero(alive)[0], size=n_ch, replace=False).astype(np.uint32)
+            idx.delete(dele)
+            alive[dele] = False
+            alive[idx.insert(fresh[r * n_ch:(r + 1) * n_ch])] = True
         torch.cuda.synchronize()
         counts = dead_edge_counts(idx.export_graph())
         s0 = idx.stats()
         idx.set_profiling(True)
         idx.profile(reset=True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         idx.reclaim(st)
         e1.record(st)
         torch.cuda.synchronize()
         prof = idx.profile(reset=True)
-        idx.set_profiling(False)
         s1 = idx.stats()
-        pts.append({"t": int(t), "reclaim_ms": e0.elapsed_time(e1),
+        pts.append({"rounds": T, "t": int(s0["tombstones"]), "reclaim_ms": e0.elapsed_time(e1),
                     "compact_ms": prof["compact"][0], "republished": int(s1["n_publish"] - s0["n_publish"]),
                     "dirty": counts["dirty"], "dead_edges": counts["dead_edges"], "live": counts["live"],
                     "mean_in_degree": counts["live_edges"] / max(1, counts["live"])})
-        idx.insert(fresh[off:off + t])
-        off += t
-        torch.cuda.synchronize()
+        del idx
+        torch.cuda.empty_cache()
     L = float(np.mean([p["live"] for p in pts]))
     dbar = float(np.mean([p["mean_in_degree"] for p in pts]))
     ts = np.array([p["t"] for p in pts], dtype=np.float64)
@@ -131,9 +135,10 @@ def run_reclaim_interval(w: W.Workload, checkpoints=(1_000, 2_000, 5_000, 10_000
     for p in pts:
         p["model_dirty"] = float(dirty_model(p["live"], p["mean_in_degree"], p["t"]))
         p["monte_carlo_dirty"] = dirty_monte_carlo(int(p["live"]), p["mean_in_degree"], p["t"], mc_rng)
-    return {"experiment": "reclaim_interval", "workload": w.name, "points": pts,
-            "fit_reclaim_ms": fit_saturating(ts, [p["reclaim_ms"] for p in pts]),
+    return {"experiment": "reclaim_interval", "workload": w.name, "churn_per_round": n_ch, "points": pts,
             "fit_dirty": fit_saturating(ts, [p["dirty"] for p in pts]),
+            "fit_reclaim_ms": fit_saturating(ts, [p["reclaim_ms"] for p in pts]),
+            "fit_dead_edges_linear_slope": float(np.polyfit(ts, [p["dead_edges"] for p in pts], 1)[0]),
             "model_tau": L / dbar, "L": L, "mean_in_degree": dbar}
 
 
@@ -180,7 +185,7 @@ def run_deletion_stress(w: W.Workload, frac: float = 0.10, beam: int = 128) -> d
 # ---- f3: concurrent query-vs-update latency ----------------------------------
 def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 2000, beam: int = 128) -> dict:
     """Latency of 1,000-query batches alone and while a writer thread churns the
-    index (1% deletes + 1% inserts + Reclaim per round) on its own stream, in
+    index (0.05% deletes + 0.05% inserts + Reclaim per round) on its own stream, in
     concurrent mode.  The anchor queries' exact top-10 never changes: deletes
     skip those ids, and inserts come from the same mixture shifted far from
     every anchor (+10^4 on each coordinate)."""
@@ -227,9 +232,11 @@ def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 20
     keep[protected] = True
 
     def writer():
-        # the live set is tracked on the host from the ids each call returns
+        # the live set is tracked on the host from the ids each call returns;
+        # 0.05% of the build per round keeps the live set's make-up steady
+        # over the measured window
         off = 0
-        n_ch = max(1, w.n_base // 100)
+        n_ch = max(1, w.n_base // 2000)
         while not stop.is_set() and off + n_ch <= len(fresh):
             cand = np.nonzero(alive & ~keep)[0].astype(np.uint32)
             dele = rng.choice(cand, size=n_ch, replace=False).astype(np.uint32)
@@ -250,4 +257,5 @@ def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 20
     idx.set_concurrent(False)
     return {"experiment": "concurrent_latency", "workload": w.name, "batch": batch, "beam": beam,
             "quiescent": {**pct(q_lat), "recall_at_10": float(np.mean(q_rec))},
-            "concurrent": {**pct(c_lat), "recall_at_10": float(np.mean(c_rec)), "writer_rounds": rounds[0]}}
+            "concurrent": {**pct(c_lat), "recall_at_10": float(np.mean(c_rec)), "writer_rounds": rounds[0],
+                           "churned_fraction": rounds[0] * max(1, w.n_base // 2000) / w.n_base}}
