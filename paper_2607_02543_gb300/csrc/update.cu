@@ -1053,7 +1053,7 @@ __host__ __device__ inline u32 repk_np(u32 R) {
 
 __host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp, u32 gram) {
     const u32 np = repk_np(R);
-    return stage_bytes(ns, mp) + 2 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)32 * np) +
+    return stage_bytes(ns, mp) + 2 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)32 * np + 32) +
            gram_bytes(gram);
 }
 
@@ -1112,7 +1112,34 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
         }
         __syncwarp();
         // K(u, a) for every a in B, one lane per a: the candidates b != a, live,
-        // in ascending (d(a, b), b), then the greedy RobustPrune on the table
+        // in ascending (d(a, b), b), then the greedy RobustPrune on the table.
+        // Orders: with |B| <= 32 the warp sorts each a's candidates in
+        // registers (the id replaced by its rank among B's ids: the same
+        // order, and the rank leads back to the table index); above that each
+        // lane ranks its own candidates by counting.
+        u32 liveB = 0;
+        for (int t0 = 0; t0 < nb; t0 += 32) {
+            const u32 m = __ballot_sync(FULL, t0 + lane < nb && !bdel[t0 + lane]);
+            if (t0 == 0) liveB = m;
+        }
+        const bool sorted_by_warp = nb <= 32;
+        if (sorted_by_warp) {
+            int idr = 0;
+            if (lane < nb)
+                for (int t2 = 0; t2 < nb; t2++) idr += bid[t2] < bid[lane];
+            unsigned char *inv = reinterpret_cast<unsigned char *>(ord) - lane * npk + 32 * npk;   // after the orders
+            if (lane < nb) inv[idr] = (unsigned char)lane;
+            __syncwarp();
+            for (int ja = 0; ja < nb; ja++) {
+                if (!(liveB >> ja & 1)) continue;
+                const bool v = lane < nb && lane != ja && (liveB >> lane & 1);
+                u64 k = v ? ((u64)f2ord(M[lane * R + ja]) << 32) | (u32)idr : KEY_INF;
+                k = warp_sort32(k);
+                unsigned char *oa = reinterpret_cast<unsigned char *>(ord) - lane * npk + ja * npk;
+                if (k != KEY_INF) oa[lane] = inv[(u32)k];
+            }
+            __syncwarp();
+        }
         for (int ja = lane; ja < (int)R; ja += 32) {
             const size_t slot = (size_t)i * R + ja;
             if (ja >= nb || bdel[ja]) {
@@ -1121,17 +1148,21 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
                 a.pair_Kn[slot] = 0;
                 continue;
             }
-            // rank of each candidate among the candidates (keys are distinct: ids differ);
-            // M is symmetric, and M[t][ja] keeps the lanes on distinct banks
             int nc = 0;
-            for (int t = 0; t < nb; t++) {
-                if (t == ja || bdel[t]) continue;
-                const u64 kt = mkkey(M[t * R + ja], bid[t]);
-                int rank = 0;
-                for (int t2 = 0; t2 < nb; t2++)
-                    if (t2 != ja && !bdel[t2] && mkkey(M[t2 * R + ja], bid[t2]) < kt) rank++;
-                ord[rank] = (unsigned char)t;
-                nc++;
+            if (sorted_by_warp) {
+                nc = __popc(liveB & ~(1u << ja));
+            } else {
+                // rank of each candidate among the candidates (keys are distinct: ids
+                // differ); M is symmetric, and M[t][ja] keeps the lanes on distinct banks
+                for (int t = 0; t < nb; t++) {
+                    if (t == ja || bdel[t]) continue;
+                    const u64 kt = mkkey(M[t * R + ja], bid[t]);
+                    int rank = 0;
+                    for (int t2 = 0; t2 < nb; t2++)
+                        if (t2 != ja && !bdel[t2] && mkkey(M[t2 * R + ja], bid[t2]) < kt) rank++;
+                    ord[rank] = (unsigned char)t;
+                    nc++;
+                }
             }
             u64 alive = nc >= 64 ? ~0ull : ((1ull << nc) - 1);
             int nk = 0;
