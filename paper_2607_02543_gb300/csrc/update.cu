@@ -307,8 +307,8 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
 // a row and OR their bits.  The greedy pass is the register walk of
 // warp_prune_gram over 128-bit masks.  Same distances as warp_prune_gram:
 // squared L2 as (G_ii - G_ij) + (G_jj - G_ij), inner product as 1 - G_ij.
+template <int NT>   // tiles of 8 columns: 8 (n <= 64) or 16 (n <= 128)
 __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id, float *out_rho, Stage &st) {
-    constexpr int NT = GRAM_NL / 8;
     const int lane = lane_id();
     const int rows = st.gram_rows;
     __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(st.gram);
@@ -383,35 +383,35 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
         }
         // this stripe's diagonal: entry (r, r) sits in tile 2 mt (rows r0) or 2 mt + 1 (rows r0 + 8)
         const int r0 = 16 * mt + (lane >> 2), r1 = r0 + 8, cq = 2 * (lane & 3);
+        {
+            float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-        for (int nt = 0; nt < NT; nt++) {
-            if (nt == 2 * mt) {
-                if (cq == (lane >> 2) && r0 < n) nrm[r0] = acc[nt][0];
-                if (cq + 1 == (lane >> 2) && r0 < n) nrm[r0] = acc[nt][1];
+            for (int nt = 0; nt < NT; nt++) {
+                if (nt == 2 * mt) d0 = cq == (lane >> 2) ? acc[nt][0] : acc[nt][1];
+                if (nt == 2 * mt + 1) d1 = cq == (lane >> 2) ? acc[nt][2] : acc[nt][3];
             }
-            if (nt == 2 * mt + 1) {
-                if (cq == (lane >> 2) && r1 < n) nrm[r1] = acc[nt][2];
-                if (cq + 1 == (lane >> 2) && r1 < n) nrm[r1] = acc[nt][3];
-            }
+            const bool own = cq == (lane >> 2) || cq + 1 == (lane >> 2);
+            if (own && r0 < n) nrm[r0] = d0;
+            if (own && r1 < n) nrm[r1] = d1;
         }
         __syncwarp();
         const float n0 = r0 < n ? nrm[r0] : 0.f, n1 = r1 < n ? nrm[r1] : 0.f;
         u64 m0l = 0, m0h = 0, m1l = 0, m1h = 0;
 #pragma unroll
         for (int nt = 0; nt < NT; nt++) {
-            if (nt < 2 * mt || nt >= nn) continue;
+            const bool tile = nt >= 2 * mt && nt < nn;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const int r = e < 2 ? r0 : r1, c = 8 * nt + cq + (e & 1);
-                if (c <= r || c >= n || r >= n) continue;
+                const bool ok = tile && c > r && c < n;   // c < n implies r < n
+                const int cc = ok ? c : 0;
                 const float g = acc[nt][e];
                 const float nr_ = e < 2 ? n0 : n1;
-                const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nr_, g), __fsub_rn(nrm[c], g)) : __fsub_rn(1.0f, g);
-                if (__fmul_rn(d.alpha2, dd) <= key_rho(ck[c])) {
-                    const u64 bit = 1ull << (c & 63);
-                    if (e < 2) { if (c < 64) m0l |= bit; else m0h |= bit; }
-                    else { if (c < 64) m1l |= bit; else m1h |= bit; }
-                }
+                const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nr_, g), __fsub_rn(nrm[cc], g)) : __fsub_rn(1.0f, g);
+                const bool hit = ok && __fmul_rn(d.alpha2, dd) <= key_rho(ck[cc]);
+                const u64 bit = hit ? 1ull << (c & 63) : 0ull;
+                if (e < 2) { if (8 * nt < 64) m0l |= bit; else m0h |= bit; }
+                else { if (8 * nt < 64) m1l |= bit; else m1h |= bit; }
             }
         }
 #pragma unroll
@@ -465,7 +465,7 @@ template <bool LG>
 __device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx, u32 *out_id,
                           float *out_rho, Stage &st) {
     if (st.gram && n <= st.gram_rows) {
-        if constexpr (LG) return warp_prune_masks(d, ck, n, out_id, out_rho, st);
+        if constexpr (LG) return warp_prune_masks<GRAM_NL / 8>(d, ck, n, out_id, out_rho, st);
         else return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
     }
     const int lane = lane_id();
@@ -624,8 +624,10 @@ __host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u3
            gram_bytes(gram);
 }
 
+// one-warp blocks (the launch uses 32 threads); the small-path instantiation
+// is held to 12 resident warps per SM (at most 170 registers a thread)
 template <bool LG>
-__global__ void __launch_bounds__(128, 1) prune_insert_kernel(PruneInsArgs a) {
+__global__ void __launch_bounds__(32, LG ? 1 : 12) prune_insert_kernel(PruneInsArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -728,8 +730,10 @@ __host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp,
            al16((size_t)np * 4) + gram_bytes(gram);
 }
 
+// one-warp blocks (the launch uses 32 threads); the small-path instantiation
+// is held to 12 resident warps per SM (at most 170 registers a thread)
 template <bool LG>
-__global__ void __launch_bounds__(128, 1) offer_fold_kernel(FoldArgs a) {
+__global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -849,7 +853,7 @@ __host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 
 }
 
 template <bool LG>
-__global__ void __launch_bounds__(64, 1) refine_kernel(RefineArgs a) {
+__global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -1283,8 +1287,10 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     return nout;
 }
 
+// one-warp blocks (the launch uses 32 threads); the small-path instantiation
+// is held to 12 resident warps per SM (at most 170 registers a thread)
 template <bool LG>
-__global__ void __launch_bounds__(128, 1) repair_fold_kernel(RepairFoldArgs a) {
+__global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
