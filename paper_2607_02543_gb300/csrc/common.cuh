@@ -43,6 +43,7 @@ enum : int {
     C_COUNT_A = 11,    // scratch counts produced on the device
     C_COUNT_B = 12,
     C_ERR_S = 13,      // error bits of query searches (kept apart from writers')
+    C_RECYCLED = 14,   // blocks of the recycle launch that have finished copying
     C_NCTR = 16
 };
 

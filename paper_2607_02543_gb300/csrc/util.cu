@@ -229,8 +229,12 @@ cudaError_t make_segments(const u32 *key, u32 n, u32 invalid, u32 *flags, u32 *s
 // ---------------------------------------------------------------------------
 // Host-ordered recycle between launches: retired stack -> free stack.
 // ---------------------------------------------------------------------------
+// Every block reads the stack counters, copies its share of the retired
+// stack onto the free stack, and counts itself done; the last block to finish
+// (all others have read the counters by then) installs the new counts.
 __global__ void __launch_bounds__(1024) recycle_kernel(Dev d) {
-    __shared__ u64 sh[3];
+    __shared__ u64 sh[2];
+    __shared__ bool last;
     if (threadIdx.x == 0) {
         const u64 nfree = d.ctr[C_FREE];
         const u64 pops = d.ctr[C_POP] < nfree ? d.ctr[C_POP] : nfree;
@@ -239,17 +243,23 @@ __global__ void __launch_bounds__(1024) recycle_kernel(Dev d) {
     }
     __syncthreads();
     const u64 base = sh[0], nret = sh[1];
-    for (u64 i = threadIdx.x; i < nret; i += 1024) d.free_stack[base + i] = d.retired[i];
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nret; i += (u64)gridDim.x * blockDim.x)
+        d.free_stack[base + i] = d.retired[i];
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) last = atomicAdd(&d.ctr[C_RECYCLED], 1ull) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
         d.ctr[C_FREE] = base + nret;
         d.ctr[C_POP] = 0;
         d.ctr[C_RET] = 0;
+        d.ctr[C_RECYCLED] = 0;
     }
 }
 
 cudaError_t launch_recycle(const Dev &d, cudaStream_t st) {
-    recycle_kernel<<<1, 1024, 0, st>>>(d);
+    recycle_kernel<<<64, 1024, 0, st>>>(d);
     return cudaGetLastError();
 }
 
