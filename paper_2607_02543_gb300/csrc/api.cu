@@ -91,7 +91,7 @@ struct etale_index {
     DevBuf live_flags, live_rank, live_scan_scr, tomb_bits;
     DevBuf del_ids, del_vals, del_ids2, del_vals2, del_ok, del_scan, dt, pair_key, pair_val, pair_key2, pair_val2,
         pair_K, pair_Kn, pair_flags, pair_scan, pair_seg, counts;
-    DevBuf ex_del, ex_hs, ex_deg, ex_ids, ex_rho, seed;
+    DevBuf ex_del, ex_hs, ex_deg, ex_ids, ex_rho, seed, refine_spill;
     // query-search scratch, separate from the writer's so that one search
     // call and one update call can run at the same time (concurrent mode)
     DevBuf s_stage, s_qpad, s_out_ids, s_out_dist, s_seed;
@@ -493,7 +493,11 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
         if (s != ETALE_OK) return s;
         {
             PhaseScope ps(idx, ETALE_PH_REFINE, st);
-            CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st), "refine");
+            const size_t sb = refine_spill_bytes(d, idx->cfg.max_cand, idx->num_sms);
+            if (!grow(idx->refine_spill, sb)) return idx->fail(ETALE_ENOMEM, "refine spill lists");
+            CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st,
+                             static_cast<char *>(idx->refine_spill.p), sb),
+               "refine");
         }
         g_kernel_launches++;
         s = recycle(idx, st);

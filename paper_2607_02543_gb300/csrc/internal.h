@@ -43,8 +43,11 @@ cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_k
 cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
                               u32 lockfree_budget, int num_sms, cudaStream_t st, u32 lo = 0,
                               u32 hi = 0xFFFFFFFFu);
+// spill: per resident warp, candidate lists for members with many peers
+// (refine_spill_bytes bytes).
+size_t refine_spill_bytes(const Dev &d, u32 max_cand, int num_sms);
 cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
-                          int num_sms, cudaStream_t st);
+                          int num_sms, cudaStream_t st, char *spill, size_t spill_bytes);
 cudaError_t launch_tombstone(const Dev &d, const u32 *sorted_ids, u32 n, u64 next_id, u32 *ok_flags,
                              cudaStream_t st);
 cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,

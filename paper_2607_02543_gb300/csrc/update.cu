@@ -844,12 +844,19 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
 struct RefineArgs {
     Dev d;
     u32 first, b, mode, max_cand, cap, np, ns, gram;
+    u32 cap_s, np_s;   // the shared-memory lists (most members); cap, np: the full ones
+    char *spill;       // per warp, lists for cap raw ids (a member with more)
+    u64 spill_warp;    // bytes of one warp's spill lists
     Offers of;
 };
 
+// Bytes of one warp's candidate lists for `cap` raw two-hop ids.
+__host__ __device__ inline size_t refine_list_bytes(u32 np, u32 cap) {
+    return al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + al16((size_t)cap * 4);
+}
+
 __host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 ns, u32 mp, u32 gram) {
-    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + al16((size_t)cap * 4) + gram_bytes(gram);
+    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + refine_list_bytes(np, cap) + gram_bytes(gram);
 }
 
 template <bool LG>
@@ -858,7 +865,7 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
-    char *p = smem + warp * refine_warp_bytes(a.np, a.cap, R, a.ns, d.mp, a.gram);
+    char *p = smem + warp * refine_warp_bytes(a.np_s, a.cap_s, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
     p += gram_bytes(a.gram);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
@@ -869,10 +876,17 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
     float *nrho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
     u32 *oid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *orho = reinterpret_cast<float *>(p); p += al16((size_t)R * 4);
-    u64 *buf = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
-    unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
-    u32 *idx = reinterpret_cast<u32 *>(p); p += al16((size_t)a.np * 4);
-    u32 *uid = reinterpret_cast<u32 *>(p);
+    // lists: in shared memory for up to cap_s raw ids, else this warp's spill
+    auto carve_lists = [](char *q, u32 np) {
+        struct L { u64 *buf; unsigned char *alive; u32 *idx, *uid; } l;
+        l.buf = reinterpret_cast<u64 *>(q); q += al16((size_t)np * 8);
+        l.alive = reinterpret_cast<unsigned char *>(q); q += al16(np);
+        l.idx = reinterpret_cast<u32 *>(q); q += al16((size_t)np * 4);
+        l.uid = reinterpret_cast<u32 *>(q);
+        return l;
+    };
+    const auto ls = carve_lists(p, a.np_s);
+    const auto lg = carve_lists(a.spill + (blockIdx.x * (blockDim.x >> 5) + warp) * a.spill_warp, a.np);
     const int grp = lane >> 3, g = lane & 7;
     for (;;) {
         u32 t = 0;
@@ -883,9 +897,17 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
         u64 snap;
         const int dv = load_list(d, v, nid, nrho, snap);
         // 1. raw two-hop ids (v, members of N(v), and for mode 2 non-members
-        //    of the sub-batch excluded), kept as u64 for the sort
+        //    of the sub-batch excluded), kept as u64 for the sort; a member
+        //    with more than cap_s of them is collected again into the spill
+        u64 *buf = ls.buf;
+        unsigned char *alive = ls.alive;
+        u32 *idx = ls.idx, *uid = ls.uid;
+        u32 cap = a.cap_s;
         int nraw = 0;
         bool overflow = false;
+    collect:
+        nraw = 0;
+        overflow = false;
         for (int i = 0; i < dv; i++) {
             const u64 rw = ld_ref(d, nid[i]);
             const u32 s = ref_slab(rw);
@@ -901,13 +923,21 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
                 u32 m = __ballot_sync(FULL, ok);
                 int pos = nraw + __popc(m & lanemask_lt());
                 if (ok) {
-                    if (pos < (int)a.cap) buf[pos] = y;
+                    if (pos < (int)cap) buf[pos] = y;
                     else overflow = true;
                 }
                 nraw += __popc(m);
             }
         }
         if (__any_sync(FULL, overflow)) {
+            if (buf == ls.buf) {
+                buf = lg.buf;
+                alive = lg.alive;
+                idx = lg.idx;
+                uid = lg.uid;
+                cap = a.cap;
+                goto collect;
+            }
             if (lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_OVERFLOW);
             nraw = min(nraw, (int)a.cap);
         }
@@ -975,20 +1005,38 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
     stage_done(d, st);
 }
 
-cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
-                          int num_sms, cudaStream_t st) {
-    if (b == 0) return cudaSuccess;
-    RefineArgs a;
-    a.d = d; a.first = first; a.b = b; a.mode = mode; a.max_cand = max_cand; a.of = of;
+// Launch shape of the refine kernel (shared by launch_refine and the spill size).
+static void refine_shape(const Dev &d, u32 max_cand, RefineArgs &a) {
     u32 cap = d.R * d.R;
     if (cap > 4096) cap = 4096;
     a.cap = cap;
     u32 np = 32;
     while (np < cap + d.R) np <<= 1;
     a.np = np;
+    a.cap_s = cap < 192u ? cap : 192u;
+    u32 nps = 32;
+    while (nps < a.cap_s + d.R) nps <<= 1;
+    a.np_s = nps;
     a.gram = d.gram ? (d.R > 32 ? (u32)GRAM_NL : (u32)GRAM_N) : 0u;
     a.ns = d.gram ? 0 : stage_cap(d.mp, max_cand, d.stage_bytes);
-    const size_t wb = refine_warp_bytes(np, cap, d.R, a.ns, d.mp, a.gram);
+    a.spill_warp = refine_list_bytes(np, cap);
+}
+
+size_t refine_spill_bytes(const Dev &d, u32 max_cand, int num_sms) {
+    RefineArgs a{};
+    refine_shape(d, max_cand, a);
+    // every warp an SM can hold (2,048 threads)
+    return (size_t)num_sms * 64 * a.spill_warp;
+}
+
+cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand, const Offers &of,
+                          int num_sms, cudaStream_t st, char *spill, size_t spill_bytes) {
+    if (b == 0) return cudaSuccess;
+    RefineArgs a;
+    a.d = d; a.first = first; a.b = b; a.mode = mode; a.max_cand = max_cand; a.of = of;
+    refine_shape(d, max_cand, a);
+    a.spill = spill;
+    const size_t wb = refine_warp_bytes(a.np_s, a.cap_s, d.R, a.ns, d.mp, a.gram);
     const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
     size_t smem = warps * wb;
     cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)refine_kernel<true> : (const void *)refine_kernel<false>,
@@ -1001,6 +1049,7 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms), need = (b + warps - 1) / warps;
     if (blocks > need) blocks = need;
+    if ((size_t)blocks * warps * a.spill_warp > spill_bytes) return cudaErrorInvalidValue;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
     if (a.gram > (u32)GRAM_N) refine_kernel<true><<<blocks, 32 * warps, smem, st>>>(a);
