@@ -69,6 +69,23 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
     return W.scaled(w, n_live) if n_live else w
 
 
+# DRAM bytes of one query-mode BeamSearch launch on the 1M x 128 workload, from
+# the ncu capture in profiles/search_kernel_int256-1m-d128_dram.md; valid only
+# for the search.cu revision it was taken on (first 16 hex digits of SHA-256).
+SEARCH_DRAM_BYTES = {"int256-1m-d128": (10_487_631_616 + 1_352_192, "05c5e56e501c5f7d")}
+
+
+def search_traffic(workload_name: str):
+    """DRAM bytes per query-mode search launch if measured for this source, else None."""
+    import hashlib
+    entry = SEARCH_DRAM_BYTES.get(workload_name)
+    if entry is None:
+        return None
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2607_02543_gb300", "csrc", "search.cu")
+    rev = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return entry[0] if rev == entry[1] else None
+
+
 def load_peaks(key: str = "hbm_gbs"):
     """(peak, "measured" | "fallback") for HBM GB/s or bf16 TFLOP/s."""
     try:
@@ -574,7 +591,7 @@ def main():
                "recall_at_10": recall, "beam_sweep": sweep, "qps": world * w.n_queries / (ms_search * 1e-3),
                "search_ms_per_10k": ms_search, "build_s": build_s,
                "roofline": {"bound": "hbm", "kernel": "search_kernel (query mode)", "achieved": achieved,
-                            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": search_traffic(w.name),
                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "kernel_ms": kernel_ms},
                "phase_ms_per_step": phases, "ground_truth": gt_block, "search_tuning": tuning,
