@@ -32,15 +32,18 @@ struct Stage {
 };
 
 // Tensor-core Gram tile: up to 64 candidates, K staged 128 columns at a time
-// as bf16 rows of GRAM_RS elements (16-byte pad: conflict-free ldmatrix); the
-// 64 x 64 fp32 result reuses the same bytes.
+// as bf16 rows of 256 bytes with no pad; the 16-byte chunk c of row r sits at
+// chunk c ^ (r & 7), so the eight rows an ldmatrix phase reads at one column
+// fall in eight distinct bank groups.  The 64 x 64 fp32 result (row stride
+// GRAM_N floats, also 256 bytes) reuses the same bytes.
 constexpr int GRAM_N = 64;
-constexpr int GRAM_RS = 136;
+constexpr int GRAM_RB = 256;   // bytes per staged row (128 bf16 columns)
+__host__ __device__ inline u32 gram_xoff(int r, int chunk) { return (u32)(r * GRAM_RB + ((chunk ^ (r & 7)) << 4)); }
 // Shared-memory bytes of a Gram buffer for `rows` candidates: the bf16 rows
 // (or the table over them) and the norms; 0 rows = no buffer.
 __host__ __device__ inline size_t gram_bytes(u32 rows) {
     if (!rows) return 0;
-    const size_t b = (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15) + (((size_t)rows * 4 + 15) & ~(size_t)15);
+    const size_t b = (size_t)rows * GRAM_RB + (((size_t)rows * 4 + 15) & ~(size_t)15);
     return rows > (u32)GRAM_N ? b + (size_t)rows * 16 : b;   // domination masks of the large path
 }
 constexpr int GRAM_NL = 128;   // candidates of the large (mask) path
@@ -48,6 +51,10 @@ constexpr int GRAM_NL = 128;   // candidates of the large (mask) path
 // Gram path is off or cannot hold them).  Above GRAM_N rows the kernel runs
 // the large path (warp_prune_masks).
 inline u32 gram_rows_for(u32 on, u32 max_n) { return on && max_n <= (u32)GRAM_NL ? (max_n + 15) / 16 * 16 : 0; }
+// Scratch that is dead whenever the Gram buffer is live (list compaction before
+// a prune, the canonical prune's arrays, a prune's output, written after its
+// last read of the buffer) lives inside the Gram buffer's row bytes if it fits.
+__host__ __device__ inline bool gram_alias(u32 gram, size_t scratch) { return gram && scratch <= (size_t)gram * GRAM_RB; }
 
 // Shared-memory bytes for a stage of ns rows plus its mbarrier.
 __host__ __device__ inline size_t stage_bytes(u32 ns, u32 mp) { return al16((size_t)ns * mp * 4) + 16; }
@@ -134,20 +141,69 @@ __device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
     return r;
 }
 
+// ldmatrix row addresses in the swizzled tile: lane l reads (row, chunk
+// 2 ks + (l >> 4)) with row & 7 = l & 7, so the chunk's byte offset in its row
+// is (32 ks) ^ c0 with c0 = 16 ((l >> 4) ^ (l & 7)), shared by every row.
+__device__ __forceinline__ u32 gram_c0(int lane) { return (u32)(((lane >> 4) ^ (lane & 7)) << 4); }
+
+__device__ __forceinline__ void cp_async16(u32 dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage columns [128 kb, 128 kb + 128) of candidate rows [r_lo, r_hi) into the
+// swizzled tile at xs, a lane per row and a 16-byte copy per chunk; chunks past
+// the row's end are zeroed.  From the bf16 copy when there is one (the same
+// round-to-nearest-even values), else converted from the fp32 rows.
+__device__ __forceinline__ void gram_stage_rows(const Dev &d, const u64 *ck, int r_lo, int r_hi, int kb, u32 xs) {
+    __syncwarp();   // earlier reads of these bytes are done
+    const int lane = lane_id();
+    const int cols = min(128, (int)d.mb - 128 * kb);   // d.mb is a multiple of 8
+    const int nch = cols >> 3;
+    for (int r = r_lo + lane; r < r_hi; r += 32) {
+        const u32 id = key_id(ck[r]);
+        if (d.xb) {
+            const auto *src = d.xb + (size_t)id * d.mb + 128 * kb;
+#pragma unroll 4
+            for (int c = 0; c < 16; c++) {
+                if (c < nch) cp_async16(xs + gram_xoff(r, c), src + 8 * c);
+                else asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(xs + gram_xoff(r, c)), "r"(0u) : "memory");
+            }
+        } else {
+            const float *src = d.x + (size_t)id * d.mp + 128 * kb;
+            const int pc = min(128, (int)d.mp - 128 * kb) >> 2;   // float4 columns (d.mp is a multiple of 4)
+#pragma unroll 1
+            for (int c = 0; c < 16; c++) {
+                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                if (2 * c < pc) v0 = *reinterpret_cast<const float4 *>(src + 8 * c);
+                if (2 * c + 1 < pc) v1 = *reinterpret_cast<const float4 *>(src + 8 * c + 4);
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(xs + gram_xoff(r, c)),
+                             "r"(pack_bf16(v0.x, v0.y)), "r"(pack_bf16(v0.z, v0.w)), "r"(pack_bf16(v1.x, v1.y)),
+                             "r"(pack_bf16(v1.z, v1.w))
+                             : "memory");
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
 // Writes the upper triangle (j >= i, in 16 x 8 tiles) of the n x n Gram into
 // T (fp32, row stride GRAM_N) and the diagonal into nrm.  T and the bf16 rows
 // share `buf`: the Gram is built in 16-row stripes, and stripe mt's table rows
-// (bytes [4096 mt, 4096 (mt + 1))) never reach a staged row a later stripe
-// reads (row r >= 16 (mt + 1) starts at byte 272 r).  A stripe only needs the
-// columns j >= 16 mt, because the prune reads T[head][j] for j > head.
+// (bytes [4096 mt, 4096 (mt + 1))) are the staged rows of that same stripe,
+// which no later stripe reads (it reads rows >= 16 (mt + 1)).  A stripe only
+// needs the columns j >= 16 mt, because the prune reads T[head][j] for j > head.
+// Rows past n hold whatever the buffer held: an entry (i, j) reads rows i and j
+// only, and no entry with i or j >= n is read.
 __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float *&nrm) {
+    (void)st;
     const int lane = lane_id();
-    __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(buf);
     T = reinterpret_cast<float *>(buf);
-    nrm = reinterpret_cast<float *>(buf + (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15));
+    nrm = reinterpret_cast<float *>(buf + (size_t)rows * GRAM_RB);
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
     const int nkb = ((int)d.mp + 127) >> 7;
-    const u32 xs = smem_addr(X);
+    const u32 xs = smem_addr(buf), c0 = gram_c0(lane);
     for (int mt = 0; mt < nm; mt++) {
         float acc[8][4];
 #pragma unroll
@@ -155,86 +211,35 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
         for (int kb = 0; kb < nkb; kb++) {
-            if ((nkb > 1 || mt == 0) && d.xb) {
-                // rows from the bf16 copy (the same round-to-nearest-even values):
-                // one bulk copy per row, all in flight on the stage's mbarrier;
-                // columns past the row are zeroed.  Rows past n stay as they
-                // are: an entry (i, j) of the table reads rows i and j only,
-                // and no entry with i or j >= n is read.
-                const int r_lo = 16 * mt, r_hi = nm * 16;
-                const int cols = min(128, (int)d.mb - 128 * kb);
-                __syncwarp();
-                if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (cols < 128) {
-                    const int rz = min(n, r_hi);
-                    for (int z = lane; z < (rz - r_lo) * 64; z += 32) {
-                        const int r = r_lo + (z >> 6), c = (z & 63) * 2;
-                        if (c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS + c) = 0u;
-                    }
-                }
-                const int nr = max(0, min(n, r_hi) - r_lo);
-                if (lane == 0 && nr > 0) mbar_expect_tx(st.bar, (u32)(nr * cols * 2));
-                __syncwarp();
-                for (int r = r_lo + lane; r < r_lo + nr; r += 32)
-                    bulk_g2s(X + (size_t)r * GRAM_RS, d.xb + (size_t)key_id(ck[r]) * d.mb + 128 * kb, (u32)cols * 2,
-                             st.bar);
-                if (nr > 0) {
-                    if (!mbar_wait(st.bar, st.phase, WAIT_LIMIT)) {
-                        st.timeout = true;
-                        mbar_wait(st.bar, st.phase, WAIT_LIMIT);   // let copies in flight land
-                    }
-                    st.phase ^= 1u;
-                }
-                __syncwarp();
-            } else if (nkb > 1 || mt == 0) {
-                // stage columns [128 kb, 128 kb + 128) of rows [16 mt, 16 nm) as bf16 (zero pad)
-                __syncwarp();
-                const int col = 128 * kb + 4 * lane;     // 32 lanes x float4 = 128 columns
-                for (int r0 = 16 * mt; r0 < nm * 16; r0 += 8) {
-                    float4 v[8];                         // 8 row loads in flight per lane
-#pragma unroll
-                    for (int t = 0; t < 8; t++) {
-                        const int r = r0 + t;
-                        v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (r < n && col < (int)d.mp)
-                            v[t] = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
-                    }
-#pragma unroll
-                    for (int t = 0; t < 8; t++) {
-                        const uint2 pk = make_uint2(pack_bf16(v[t].x, v[t].y), pack_bf16(v[t].z, v[t].w));
-                        *reinterpret_cast<uint2 *>(X + (size_t)(r0 + t) * GRAM_RS + 4 * lane) = pk;
-                    }
-                }
-                __syncwarp();
-            }
+            // rows [16 mt, n) of this column block: all rows once when one
+            // block covers the row, else this stripe's and later ones per block
+            if (nkb > 1 || mt == 0) gram_stage_rows(d, ck, 16 * mt, n, kb, xs);
 #pragma unroll
             for (int ks = 0; ks < 8; ks++) {
                 u32 a0, a1, a2, a3;
+                const u32 ko = (u32)(32 * ks) ^ c0;
                 const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
-                const int ac = 16 * ks + 8 * (lane >> 4);
-                ldsm_x4(a0, a1, a2, a3, xs + (u32)((ar * GRAM_RS + ac) * 2));
+                ldsm_x4(a0, a1, a2, a3, xs + (u32)ar * GRAM_RB + ko);
 #pragma unroll
                 for (int nt = 0; nt < 8; nt += 2) {
                     if (nt < 2 * mt || nt >= nn) continue;
+                    // matrices: (nt, k 0-7), (nt + 1, k 0-7), (nt, k 8-15), (nt + 1, k 8-15)
                     u32 b0, b1, b2, b3;
-                    const int br = 8 * nt + (lane & 7) + 8 * (lane >> 4);
-                    const int bc = 16 * ks + 8 * ((lane >> 3) & 1);
-                    ldsm_x4(b0, b1, b2, b3, xs + (u32)((br * GRAM_RS + bc) * 2));
-                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b1);
-                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b2, b3);
+                    const int br = 8 * nt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(b0, b1, b2, b3, xs + (u32)br * GRAM_RB + ko);
+                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b2);
+                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b1, b3);
                 }
             }
         }
         __syncwarp();
-        // this stripe's table rows, over staged rows no later stripe reads
+        // this stripe's table rows, over this stripe's staged rows
 #pragma unroll
         for (int nt = 0; nt < 8; nt++) {
             if (nt < 2 * mt || nt >= nn) continue;
             const int r = 16 * mt + (lane >> 2), c = 8 * nt + 2 * (lane & 3);
-            T[r * GRAM_N + c] = acc[nt][0];
-            T[r * GRAM_N + c + 1] = acc[nt][1];
-            T[(r + 8) * GRAM_N + c] = acc[nt][2];
-            T[(r + 8) * GRAM_N + c + 1] = acc[nt][3];
+            *reinterpret_cast<float2 *>(T + r * GRAM_N + c) = make_float2(acc[nt][0], acc[nt][1]);
+            *reinterpret_cast<float2 *>(T + (r + 8) * GRAM_N + c) = make_float2(acc[nt][2], acc[nt][3]);
         }
         __syncwarp();
     }
@@ -242,38 +247,43 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
     __syncwarp();
 }
 
-// RobustPrune on a Gram table: same rule and order as warp_prune.  First,
-// lane h (and h + 32) builds the mask of later candidates j that candidate h
-// would drop (alpha^2 * d(h, j) <= rho(j)), reading the table in a
-// lane-rotated column order so that the lanes hit distinct banks.  The greedy
-// pass is then a warp-uniform walk over a 64-bit alive mask: take the first
-// alive candidate, clear the ones it drops.
+// RobustPrune on a Gram table: same rule and order as warp_prune.  First the
+// domination masks: row i's mask holds the later candidates j > i that i would
+// drop (alpha^2 * d(i, j) <= rho(j)).  Lane l builds the mask of row l
+// (columns l + 1 .. n - 1, ascending) and, when n - 2 - l >= 32, of row
+// n - 2 - l (columns n - 1 down to n - 1 - l), so that every lane walks at
+// most n columns; within a step the lanes of each row set read distinct banks
+// (the table's row stride is 64 floats).  The greedy pass is then a
+// warp-uniform walk over a 64-bit alive mask: take the first alive candidate,
+// clear the ones it drops.
 __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *out_id,
                                float *out_rho, Stage &st) {
     (void)alive;
     const int lane = lane_id();
     float *T, *nrm;
     warp_gram(d, ck, n, st.gram, st.gram_rows, st, T, nrm);
-    u64 dom[2] = {0ull, 0ull};
-#pragma unroll
-    for (int hh = 0; hh < 2; hh++) {
-        const int h = lane + 32 * hh;
-        if (h >= n - 1) continue;
-        const float nh = nrm[h];
-        const float *Th = T + h * GRAM_N;
-        u64 m = 0ull;
-        const int l0 = lane % n;
-        for (int k = 0; k < n; k++) {
-            int j = k + l0;                          // rotated by lane: distinct banks
-            if (j >= n) j -= n;
-            if (j <= h) continue;
-            const float g = Th[j];
-            // (n_h - g) + (n_j - g): every intermediate stays as small as the result
-            const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
-            if (__fmul_rn(d.alpha2, dd) <= key_rho(ck[j])) m |= 1ull << j;
-        }
-        dom[hh] = m;
+    const int ra = lane, rb = n - 2 - lane;
+    const int len_a = ra < n - 1 ? n - 1 - ra : 0;
+    const int len_b = rb >= 32 ? lane + 1 : 0;        // rb >= 32 implies ra < n - 1
+    const int tot = len_a + len_b;                     // <= n
+    const float *Ta = T + min(ra, n - 1) * GRAM_N, *Tb = T + max(rb, 0) * GRAM_N;
+    const float na = nrm[min(ra, n - 1)], nb = nrm[max(rb, 0)];
+    const u32 *rk = reinterpret_cast<const u32 *>(ck) + 1;   // high word of key j: ord(rho_j)
+    u64 dom_a = 0ull, dom_b = 0ull;
+#pragma unroll 4
+    for (int k = 0; k < n; k++) {
+        const bool ia = k < len_a, ib = !ia && k < tot;
+        const int j = ia ? ra + 1 + k : (ib ? 2 * n - 2 - k - lane : 0);
+        const float g = (ia ? Ta : (ib ? Tb : T))[j];   // idle lanes: one shared address
+        const float nh = ia ? na : nb;
+        // (n_h - g) + (n_j - g): every intermediate stays as small as the result
+        const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
+        const bool hit = __fmul_rn(d.alpha2, dd) <= ord2f(rk[2 * j]);
+        const u64 bit = 1ull << j;
+        if (ia && hit) dom_a |= bit;
+        if (ib && hit) dom_b |= bit;
     }
+    __syncwarp();   // the table is read; the output may reuse its bytes
     // equal adjacent keys collapse to one
     u64 live = 0ull;
     for (int i0 = 0; i0 < n; i0 += 32) {
@@ -292,8 +302,11 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
             out_rho[nout] = key_rho(hk);
         }
         nout++;
-        const u64 dl = __shfl_sync(FULL, dom[0], head & 31), dh = __shfl_sync(FULL, dom[1], head & 31);
-        live &= ~(head < 32 ? dl : dh);
+        // row head: lane head's first mask, or lane n - 2 - head's second (the last row has none)
+        const bool first = head < 32;
+        u64 m = __shfl_sync(FULL, first ? dom_a : dom_b, (first ? head : n - 2 - head) & 31);
+        if (head >= n - 1) m = 0ull;
+        live &= ~m;
     }
     __syncwarp();
     return nout;
@@ -311,13 +324,12 @@ template <int NT>   // tiles of 8 columns: 8 (n <= 64) or 16 (n <= 128)
 __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id, float *out_rho, Stage &st) {
     const int lane = lane_id();
     const int rows = st.gram_rows;
-    __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(st.gram);
-    char *tail = st.gram + (((size_t)rows * GRAM_RS * 2 + 15) & ~(size_t)15);
+    char *tail = st.gram + (size_t)rows * GRAM_RB;
     float *nrm = reinterpret_cast<float *>(tail);
     u64 *dom = reinterpret_cast<u64 *>(tail + (((size_t)rows * 4 + 15) & ~(size_t)15));
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
     const int nkb = ((int)d.mp + 127) >> 7;
-    const u32 xs = smem_addr(X);
+    const u32 xs = smem_addr(st.gram), c0 = gram_c0(lane);
     for (int mt = nm - 1; mt >= 0; mt--) {
         float acc[NT][4];
 #pragma unroll
@@ -325,59 +337,24 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
         for (int kb = 0; kb < nkb; kb++) {
-            if (nkb > 1 || mt == nm - 1) {
-                // rows [r_lo, n) of columns [128 kb, 128 kb + 128): all rows once
-                // when one block covers the row, else those of this stripe on
-                const int r_lo = nkb > 1 ? 16 * mt : 0;
-                __syncwarp();
-                if (d.xb) {
-                    const int cols = min(128, (int)d.mb - 128 * kb);
-                    if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (cols < 128)
-                        for (int z = lane; z < (n - r_lo) * 64; z += 32) {
-                            const int r = r_lo + (z >> 6), c = (z & 63) * 2;
-                            if (c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS + c) = 0u;
-                        }
-                    const int nr = n - r_lo;
-                    if (lane == 0 && nr > 0) mbar_expect_tx(st.bar, (u32)(nr * cols * 2));
-                    __syncwarp();
-                    for (int r = r_lo + lane; r < n; r += 32)
-                        bulk_g2s(X + (size_t)r * GRAM_RS, d.xb + (size_t)key_id(ck[r]) * d.mb + 128 * kb,
-                                 (u32)cols * 2, st.bar);
-                    if (nr > 0) {
-                        if (!mbar_wait(st.bar, st.phase, WAIT_LIMIT)) {
-                            st.timeout = true;
-                            mbar_wait(st.bar, st.phase, WAIT_LIMIT);   // let copies in flight land
-                        }
-                        st.phase ^= 1u;
-                    }
-                } else {
-                    const int col = 128 * kb + 4 * lane;
-                    for (int r = r_lo; r < n; r++) {
-                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (col < (int)d.mp)
-                            v = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
-                        *reinterpret_cast<uint2 *>(X + (size_t)r * GRAM_RS + 4 * lane) =
-                            make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
-                    }
-                }
-                __syncwarp();
-            }
+            // rows [r_lo, n) of columns [128 kb, 128 kb + 128): all rows once
+            // when one block covers the row, else those of this stripe on
+            if (nkb > 1 || mt == nm - 1) gram_stage_rows(d, ck, nkb > 1 ? 16 * mt : 0, n, kb, xs);
 #pragma unroll
             for (int ks = 0; ks < 8; ks++) {
                 u32 a0, a1, a2, a3;
+                const u32 ko = (u32)(32 * ks) ^ c0;
                 const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
-                const int ac = 16 * ks + 8 * (lane >> 4);
-                ldsm_x4(a0, a1, a2, a3, xs + (u32)((ar * GRAM_RS + ac) * 2));
+                ldsm_x4(a0, a1, a2, a3, xs + (u32)ar * GRAM_RB + ko);
 #pragma unroll
                 for (int nt = 0; nt < NT; nt += 2) {
                     if (nt < 2 * mt || nt >= nn) continue;
+                    // matrices: (nt, k 0-7), (nt + 1, k 0-7), (nt, k 8-15), (nt + 1, k 8-15)
                     u32 b0, b1, b2, b3;
-                    const int br = 8 * nt + (lane & 7) + 8 * (lane >> 4);
-                    const int bc = 16 * ks + 8 * ((lane >> 3) & 1);
-                    ldsm_x4(b0, b1, b2, b3, xs + (u32)((br * GRAM_RS + bc) * 2));
-                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b1);
-                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b2, b3);
+                    const int br = 8 * nt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(b0, b1, b2, b3, xs + (u32)br * GRAM_RB + ko);
+                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b2);
+                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b1, b3);
                 }
             }
         }
@@ -619,9 +596,12 @@ struct PruneInsArgs {
     Offers of;
 };
 
+__host__ __device__ inline size_t prune_ins_scratch(u32 np, u32 R) {
+    return al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4);
+}
 __host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
-    return stage_bytes(ns, mp) + al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4) + 2 * al16((size_t)R * 4) +
-           gram_bytes(gram);
+    const size_t sc = prune_ins_scratch(np, R);
+    return stage_bytes(ns, mp) + al16((size_t)np * 8) + (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram);
 }
 
 // one-warp blocks (the launch uses 32 threads); the small-path instantiation
@@ -640,15 +620,17 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) prune_insert_kernel(PruneInsA
     ws_init(ws);
     p += stage_bytes(a.ns, d.mp);
     u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    if (gram_alias(a.gram, prune_ins_scratch(a.np, R))) p = gbuf;
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
     u32 *idx = reinterpret_cast<u32 *>(p); p += al16((size_t)a.np * 4);
     u32 *oid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
     float *orho = reinterpret_cast<float *>(p);
+    u32 t_next = 0;   // the next item's claim, in flight while this one runs
+    if (lane == 0) t_next = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
     for (;;) {
-        u32 t = 0;
-        if (lane == 0) t = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
-        t = __shfl_sync(FULL, t, 0);
+        const u32 t = __shfl_sync(FULL, t_next, 0);
         if (t >= a.b) break;
+        if (lane == 0) t_next = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
         const u32 cnt = a.exp_count[t];
         for (u32 i = lane; i < a.np; i += 32) keys[i] = i < cnt ? a.exp_keys[(size_t)t * a.max_hops + i] : KEY_INF;
         __syncwarp();
@@ -725,9 +707,14 @@ struct FoldArgs {
     u32 lo, hi;   // lock-free: offer slots [lo, hi) of this launch
 };
 
+__host__ __device__ inline size_t fold_scratch(u32 np, u32 R) {
+    return 2 * al16((size_t)R * 4 + 4) + al16(np) + al16((size_t)np * 4);
+}
+// keys: a prune sees at most R + 1 candidates
 __host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
-    return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + gram_bytes(gram);
+    const size_t sc = fold_scratch(np, R);
+    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4 + 4) + al16((size_t)(R + 1) * 8) +
+           (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram);
 }
 
 // one-warp blocks (the launch uses 32 threads); the small-path instantiation
@@ -750,17 +737,19 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a)
     float *lrho = reinterpret_cast<float *>(p); p += lb;
     u32 *oid0 = reinterpret_cast<u32 *>(p); p += lb;
     float *orho0 = reinterpret_cast<float *>(p); p += lb;
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)(R + 1) * 8);
+    if (gram_alias(a.gram, fold_scratch(a.np, R))) p = gbuf;
     u32 *tid = reinterpret_cast<u32 *>(p); p += lb;
     float *trho = reinterpret_cast<float *>(p); p += lb;
-    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
     u32 *idx = reinterpret_cast<u32 *>(p);
     const u64 nwork = a.budget ? (u64)(a.hi - a.lo) : *a.seg_count;
+    u64 t_next = 0;   // the next item's claim, in flight while this one runs
+    if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
     for (;;) {
-        u64 t = 0;
-        if (lane == 0) t = atomicAdd(&d.ctr[C_WORK], 1ull);
-        t = __shfl_sync(FULL, t, 0);
+        u64 t = __shfl_sync(FULL, t_next, 0);
         if (t >= nwork) break;
+        if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
         if (a.budget == 0) {
             const u32 lo = a.seg_start[t], hi = a.seg_start[t + 1];
             const u32 w = a.of.key[lo];
@@ -888,11 +877,12 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
     const auto ls = carve_lists(p, a.np_s);
     const auto lg = carve_lists(a.spill + (blockIdx.x * (blockDim.x >> 5) + warp) * a.spill_warp, a.np);
     const int grp = lane >> 3, g = lane & 7;
+    u32 t_next = 0;   // the next item's claim, in flight while this one runs
+    if (lane == 0) t_next = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
     for (;;) {
-        u32 t = 0;
-        if (lane == 0) t = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
-        t = __shfl_sync(FULL, t, 0);
+        const u32 t = __shfl_sync(FULL, t_next, 0);
         if (t >= a.b) break;
+        if (lane == 0) t_next = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
         const u32 v = a.first + t;
         u64 snap;
         const int dv = load_list(d, v, nid, nrho, snap);
@@ -1128,11 +1118,12 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
     const int grp = lane >> 3, g = lane & 7;
     const u64 nd = *a.n_dt;
     const u32 invalid = (u32)d.capacity;
+    u64 i_next = 0;   // the next item's claim, in flight while this one runs
+    if (lane == 0) i_next = atomicAdd(&d.ctr[C_WORK], 1ull);
     for (;;) {
-        u64 i = 0;
-        if (lane == 0) i = atomicAdd(&d.ctr[C_WORK], 1ull);
-        i = __shfl_sync(FULL, i, 0);
+        const u64 i = __shfl_sync(FULL, i_next, 0);
         if (i >= nd) break;
+        if (lane == 0) i_next = atomicAdd(&d.ctr[C_WORK], 1ull);
         const u32 u = a.dt[i];
         u64 r = 0;
         if (lane == 0) r = ld_ref(d, u);
@@ -1278,9 +1269,13 @@ struct RepairFoldArgs {
     u64 lo;       // lock-free: pair slots [lo, lo + n_pairs) of this launch
 };
 
+__host__ __device__ inline size_t repf_scratch(u32 np, u32 R) {
+    return 2 * al16((size_t)R * 4 + 4) + 2 * al16((size_t)np * 8) + al16(np) + al16((size_t)np * 4);
+}
 __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
-    return stage_bytes(ns, mp) + 6 * al16((size_t)R * 4 + 4) + 3 * al16((size_t)np * 8) + al16(np) +
-           al16((size_t)np * 4) + gram_bytes(gram);
+    const size_t sc = repf_scratch(np, R);
+    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) +
+           (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram);
 }
 
 template <bool LG>
@@ -1356,19 +1351,21 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFold
     float *lrho = reinterpret_cast<float *>(p); p += lb;
     u32 *oid0 = reinterpret_cast<u32 *>(p); p += lb;
     float *orho0 = reinterpret_cast<float *>(p); p += lb;
+    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
+    if (gram_alias(a.gram, repf_scratch(a.np, R))) p = gbuf;
     u32 *tid = reinterpret_cast<u32 *>(p); p += lb;
     float *trho = reinterpret_cast<float *>(p); p += lb;
-    u64 *keys = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     u64 *ka = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     u64 *kb = reinterpret_cast<u64 *>(p); p += al16((size_t)a.np * 8);
     unsigned char *alive = reinterpret_cast<unsigned char *>(p); p += al16(a.np);
     u32 *idx = reinterpret_cast<u32 *>(p);
     const u64 nwork = a.budget ? a.n_pairs : *a.seg_count;
+    u64 t_next = 0;   // the next item's claim, in flight while this one runs
+    if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
     for (;;) {
-        u64 t = 0;
-        if (lane == 0) t = atomicAdd(&d.ctr[C_WORK], 1ull);
-        t = __shfl_sync(FULL, t, 0);
+        u64 t = __shfl_sync(FULL, t_next, 0);
         if (t >= nwork) break;
+        if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
         if (a.budget == 0) {
             const u32 lo = a.seg_start[t], hi = a.seg_start[t + 1];
             const u32 w = a.pair_key[lo];
