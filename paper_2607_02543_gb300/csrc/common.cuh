@@ -209,6 +209,27 @@ __device__ __forceinline__ u64 warp_sort32(u64 v) {
     return v;
 }
 
+// Four independent warp_sort32 networks interleaved: the same result as four
+// calls, with their shuffles in flight together.
+__device__ __forceinline__ void warp_sort32x4(u64 (&v)[4]) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const bool take_lo = ((lane & j) == 0) == ((lane & k) == 0);
+            u64 o[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) o[q] = __shfl_xor_sync(FULL, v[q], j);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const u64 lo = v[q] < o[q] ? v[q] : o[q], hi = v[q] < o[q] ? o[q] : v[q];
+                v[q] = take_lo ? lo : hi;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int next_pow2(int n) {
     int p = 32;
     while (p < n) p <<= 1;

@@ -188,8 +188,15 @@ __device__ __forceinline__ void gram_stage_rows(const Dev &d, const u64 *ck, int
     __syncwarp();
 }
 
+// Column swizzle of the Gram table: entry (r, c) sits at column c ^ gram_tsw(r),
+// so the eight rows of an accumulator fragment store to four bank groups
+// (two wavefronts instead of eight), while a walk along rows (lane h reading
+// (h, h + 1 + k)) still hits 32 distinct banks.
+__device__ __forceinline__ int gram_tsw(int r) { return (r & 3) << 3; }
+
 // Writes the upper triangle (j >= i, in 16 x 8 tiles) of the n x n Gram into
-// T (fp32, row stride GRAM_N) and the diagonal into nrm.  T and the bf16 rows
+// T (fp32, row stride GRAM_N, columns swizzled by gram_tsw) and the diagonal
+// into nrm.  T and the bf16 rows
 // share `buf`: the Gram is built in 16-row stripes, and stripe mt's table rows
 // (bytes [4096 mt, 4096 (mt + 1))) are the staged rows of that same stripe,
 // which no later stripe reads (it reads rows >= 16 (mt + 1)).  A stripe only
@@ -233,57 +240,67 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
             }
         }
         __syncwarp();
-        // this stripe's table rows, over this stripe's staged rows
+        // this stripe's table rows, over this stripe's staged rows (rows r and
+        // r + 8 share the column swizzle)
 #pragma unroll
         for (int nt = 0; nt < 8; nt++) {
             if (nt < 2 * mt || nt >= nn) continue;
-            const int r = 16 * mt + (lane >> 2), c = 8 * nt + 2 * (lane & 3);
+            const int r = 16 * mt + (lane >> 2), c = (8 * nt + 2 * (lane & 3)) ^ gram_tsw(r);
             *reinterpret_cast<float2 *>(T + r * GRAM_N + c) = make_float2(acc[nt][0], acc[nt][1]);
             *reinterpret_cast<float2 *>(T + (r + 8) * GRAM_N + c) = make_float2(acc[nt][2], acc[nt][3]);
         }
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) nrm[i] = T[i * GRAM_N + i];
+    for (int i = lane; i < n; i += 32) nrm[i] = T[i * GRAM_N + (i ^ gram_tsw(i))];
     __syncwarp();
 }
 
 // RobustPrune on a Gram table: same rule and order as warp_prune.  First the
 // domination masks: row i's mask holds the later candidates j > i that i would
-// drop (alpha^2 * d(i, j) <= rho(j)).  Lane l builds the mask of row l
-// (columns l + 1 .. n - 1, ascending) and, when n - 2 - l >= 32, of row
-// n - 2 - l (columns n - 1 down to n - 1 - l), so that every lane walks at
-// most n columns; within a step the lanes of each row set read distinct banks
-// (the table's row stride is 64 floats).  The greedy pass is then a
-// warp-uniform walk over a 64-bit alive mask: take the first alive candidate,
-// clear the ones it drops.
+// drop (alpha^2 * d(i, j) <= rho(j)).  Lane l builds the mask of row l and,
+// when n - 2 - l >= 32, of row n - 2 - l, walking each row's columns upward
+// (lane l reads column row + 1 + k in step k: distinct banks).  The masks go
+// to the last 512 bytes of the Gram buffer (the table is read by then); the
+// greedy pass is a warp-uniform walk over a 64-bit alive mask (take the first
+// alive candidate, clear the ones it drops), and the kept candidates are
+// written out afterwards, a lane per candidate.
 __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *out_id,
                                float *out_rho, Stage &st) {
     (void)alive;
     const int lane = lane_id();
     float *T, *nrm;
     warp_gram(d, ck, n, st.gram, st.gram_rows, st, T, nrm);
-    const int ra = lane, rb = n - 2 - lane;
-    const int len_a = ra < n - 1 ? n - 1 - ra : 0;
-    const int len_b = rb >= 32 ? lane + 1 : 0;        // rb >= 32 implies ra < n - 1
-    const int tot = len_a + len_b;                     // <= n
-    const float *Ta = T + min(ra, n - 1) * GRAM_N, *Tb = T + max(rb, 0) * GRAM_N;
-    const float na = nrm[min(ra, n - 1)], nb = nrm[max(rb, 0)];
     const u32 *rk = reinterpret_cast<const u32 *>(ck) + 1;   // high word of key j: ord(rho_j)
+    const float alpha2 = d.alpha2;
+    const bool l2 = d.metric == 0;
+    // (n_h - g) + (n_j - g): every intermediate stays as small as the result
+    auto hit = [&](float nh, float g, int j) {
+        const float dd = l2 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
+        return __fmul_rn(alpha2, dd) <= ord2f(rk[2 * j]);
+    };
     u64 dom_a = 0ull, dom_b = 0ull;
+    const int ra = lane, rb = n - 2 - lane;
+    if (ra < n - 1) {
+        const float *Ta = T + ra * GRAM_N;
+        const float na = nrm[ra];
+        const int sw = gram_tsw(ra);
 #pragma unroll 4
-    for (int k = 0; k < n; k++) {
-        const bool ia = k < len_a, ib = !ia && k < tot;
-        const int j = ia ? ra + 1 + k : (ib ? 2 * n - 2 - k - lane : 0);
-        const float g = (ia ? Ta : (ib ? Tb : T))[j];   // idle lanes: one shared address
-        const float nh = ia ? na : nb;
-        // (n_h - g) + (n_j - g): every intermediate stays as small as the result
-        const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
-        const bool hit = __fmul_rn(d.alpha2, dd) <= ord2f(rk[2 * j]);
-        const u64 bit = 1ull << j;
-        if (ia && hit) dom_a |= bit;
-        if (ib && hit) dom_b |= bit;
+        for (int j = ra + 1; j < n; j++)
+            if (hit(na, Ta[j ^ sw], j)) dom_a |= 1ull << j;
     }
-    __syncwarp();   // the table is read; the output may reuse its bytes
+    if (rb >= 32) {
+        const float *Tb = T + rb * GRAM_N;
+        const float nb = nrm[rb];
+        const int sw = gram_tsw(rb);
+#pragma unroll 4
+        for (int j = rb + 1; j < n; j++)
+            if (hit(nb, Tb[j ^ sw], j)) dom_b |= 1ull << j;
+    }
+    __syncwarp();   // the table is read: its last bytes take the masks
+    u64 *dsm = reinterpret_cast<u64 *>(st.gram + (size_t)st.gram_rows * GRAM_RB - GRAM_N * 8);
+    if (ra < n) dsm[ra] = dom_a;
+    if (rb >= 32) dsm[rb] = dom_b;
+    if (lane == 0 && n - 1 >= 32) dsm[n - 1] = 0ull;   // the last row drops nothing
     // equal adjacent keys collapse to one
     u64 live = 0ull;
     for (int i0 = 0; i0 < n; i0 += 32) {
@@ -291,22 +308,25 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
         const u32 b = __ballot_sync(FULL, i < n && (i == 0 || ck[i] != ck[i - 1]));
         live |= (u64)b << i0;
     }
+    __syncwarp();
+    u64 kept = 0ull;
     int nout = 0;
     const int R = (int)d.R;
     while (nout < R && live) {
+        const u64 low = live & (0ull - live);
         const int head = __ffsll((long long)live) - 1;
-        live &= live - 1;
-        if (lane == 0) {
-            const u64 hk = ck[head];
-            out_id[nout] = key_id(hk);
-            out_rho[nout] = key_rho(hk);
-        }
+        kept |= low;
         nout++;
-        // row head: lane head's first mask, or lane n - 2 - head's second (the last row has none)
-        const bool first = head < 32;
-        u64 m = __shfl_sync(FULL, first ? dom_a : dom_b, (first ? head : n - 2 - head) & 31);
-        if (head >= n - 1) m = 0ull;
-        live &= ~m;
+        live = (live ^ low) & ~dsm[head];
+    }
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        if (i < n && (kept >> i & 1)) {
+            const int pos = __popcll(kept & ((1ull << i) - 1));
+            const u64 hk = ck[i];
+            out_id[pos] = key_id(hk);
+            out_rho[pos] = key_rho(hk);
+        }
     }
     __syncwarp();
     return nout;
@@ -746,8 +766,11 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a)
     const u64 nwork = a.budget ? (u64)(a.hi - a.lo) : *a.seg_count;
     u64 t_next = 0;   // the next item's claim, in flight while this one runs
     if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
+    u64 pf_t = ~0ull;   // lock-free: the item whose words pf_w, pf_v, pf_vr hold
+    u32 pf_w = 0, pf_v = 0;
+    float pf_vr = 0.f;
     for (;;) {
-        u64 t = __shfl_sync(FULL, t_next, 0);
+        const u64 t = __shfl_sync(FULL, t_next, 0);
         if (t >= nwork) break;
         if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
         if (a.budget == 0) {
@@ -767,11 +790,10 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a)
                 if (!warp_publish(d, ws, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
-            t += a.lo;
-            const u32 w = a.of.key[t];
+            u32 w = pf_w, v = pf_v;
+            float vr = pf_vr;
+            if (t != pf_t) { w = a.of.key[t + a.lo]; v = a.of.src[t + a.lo]; vr = a.of.rho[t + a.lo]; }
             if (w >= (u32)d.capacity) continue;
-            const u32 v = a.of.src[t];
-            const float vr = a.of.rho[t];
             bool done = false;
             for (u32 att = 0; att < a.budget && !done; att++) {
                 u64 snap;
@@ -779,6 +801,10 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a)
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
                 const int n = apply_offer<LG>(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
+                if (att == 0) {                      // the next offer's words, in flight while this one publishes
+                    pf_t = __shfl_sync(FULL, t_next, 0);
+                    if (pf_t < nwork) { pf_w = a.of.key[pf_t + a.lo]; pf_v = a.of.src[pf_t + a.lo]; pf_vr = a.of.rho[pf_t + a.lo]; }
+                }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, ws, w, lid, lrho, n, snap);
                 u64 err = 0;
@@ -1142,17 +1168,25 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
         auto brow = [&](int i) -> const float * {
             return i < nsb ? st.rows + (size_t)i * d.mp : d.x + (size_t)bid[i] * d.mp;
         };
-        for (int x = 0; x < nb; x++) {
-            const float *xr = brow(x);
-            // two independent rounds of four pairs per trip: their row loads overlap
-            for (int y0 = x + 1; y0 < nb; y0 += 8) {
-                const int y = y0 + grp, y2 = y + 4;
-                const int yy = y < nb ? y : nb - 1, yy2 = y2 < nb ? y2 : nb - 1;
-                const float dd = canon_dist<8>(xr, brow(yy), (int)d.mp, (int)d.metric, g);
-                const float dd2 = canon_dist<8>(xr, brow(yy2), (int)d.mp, (int)d.metric, g);
-                if (y < nb && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
-                if (y2 < nb && g == 0) { M[x * R + y2] = dd2; M[y2 * R + x] = dd2; }
-            }
+        // the pairs x < y in one sequence (index y (y - 1) / 2 + x), eight per
+        // trip in two independent rounds of four: their row loads overlap
+        const int npair = nb * (nb - 1) / 2;
+        auto pair_of = [](int q, int &x, int &y) {
+            int yy = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)q)) * 0.5f);
+            if (yy * (yy - 1) / 2 > q) yy--;
+            if ((yy + 1) * yy / 2 <= q) yy++;
+            y = yy;
+            x = q - yy * (yy - 1) / 2;
+        };
+        for (int q0 = 0; q0 < npair; q0 += 8) {
+            const int q = q0 + grp, q2 = q + 4;
+            int x, y, x2, y2;
+            pair_of(q < npair ? q : npair - 1, x, y);
+            pair_of(q2 < npair ? q2 : npair - 1, x2, y2);
+            const float dd = canon_dist<8>(brow(x), brow(y), (int)d.mp, (int)d.metric, g);
+            const float dd2 = canon_dist<8>(brow(x2), brow(y2), (int)d.mp, (int)d.metric, g);
+            if (q < npair && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
+            if (q2 < npair && g == 0) { M[x2 * R + y2] = dd2; M[y2 * R + x2] = dd2; }
         }
         __syncwarp();
         // K(u, a) for every a in B, one lane per a: the candidates b != a, live,
@@ -1174,13 +1208,20 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
             unsigned char *inv = reinterpret_cast<unsigned char *>(ord) - lane * npk + 32 * npk;   // after the orders
             if (lane < nb) inv[idr] = (unsigned char)lane;
             __syncwarp();
-            for (int ja = 0; ja < nb; ja++) {
-                if (!(liveB >> ja & 1)) continue;
-                const bool v = lane < nb && lane != ja && (liveB >> lane & 1);
-                u64 k = v ? ((u64)f2ord(M[lane * R + ja]) << 32) | (u32)idr : KEY_INF;
-                k = warp_sort32(k);
-                unsigned char *oa = reinterpret_cast<unsigned char *>(ord) - lane * npk + ja * npk;
-                if (k != KEY_INF) oa[lane] = inv[(u32)k];
+            for (int ja0 = 0; ja0 < nb; ja0 += 4) {
+                u64 k[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int ja = ja0 + c;
+                    const bool v = ja < nb && (liveB >> ja & 1) && lane < nb && lane != ja && (liveB >> lane & 1);
+                    k[c] = v ? ((u64)f2ord(M[ja * R + lane]) << 32) | (u32)idr : KEY_INF;   // M is symmetric
+                }
+                warp_sort32x4(k);
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    unsigned char *oa = reinterpret_cast<unsigned char *>(ord) - lane * npk + (ja0 + c) * npk;
+                    if (k[c] != KEY_INF) oa[lane] = inv[(u32)k[c]];
+                }
             }
             __syncwarp();
         }
@@ -1208,8 +1249,8 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
                     nc++;
                 }
             }
-            u64 alive = nc >= 64 ? ~0ull : ((1ull << nc) - 1);
             int nk = 0;
+            u64 alive = nc >= 64 ? ~0ull : ((1ull << nc) - 1);
             for (int h = 0; h < nc && nk < (int)R; h++) {
                 if (!(alive >> h & 1)) continue;
                 const int hj = ord[h];
@@ -1285,9 +1326,12 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     const int lane = lane_id();
     // The list (minus u and deleted nodes) and K(u, a) (minus deleted nodes)
     // are each sorted by (rho, id); compact both, then place every key at its
-    // rank in the union: a list key after the K keys below it, a K key after
-    // the list keys at or below it (an id in both has equal keys: adjacent).
+    // rank in the union: a K key after the list keys below it, a list key after
+    // the K keys below it.  An id in both has equal keys and would collapse in
+    // the prune; its K copy is dropped here (same result, fewer Gram rows).
     int na = 0, nb = 0;
+    uint2 e0 = make_uint2(0u, 0u);                   // K's first 32 entries, in flight with the list's words
+    if (lane < nk) e0 = K[lane];
     for (int i0 = 0; i0 < n; i0 += 32) {
         const int i = i0 + lane;
         const bool v = i < n && lid[i] != u && !ref_del(ld_ref(d, lid[i]));
@@ -1297,34 +1341,46 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     }
     for (int j0 = 0; j0 < nk; j0 += 32) {
         const int j = j0 + lane;
-        uint2 e = make_uint2(0u, 0u);
-        if (j < nk) e = K[j];
+        uint2 e = e0;
+        if (j0 > 0 && j < nk) e = K[j];
         const bool v = j < nk && !ref_del(ld_ref(d, e.x));
         const u32 m = __ballot_sync(FULL, v);
         if (v) kb[nb + __popc(m & lanemask_lt())] = mkkey(__uint_as_float(e.y), e.x);
         nb += __popc(m);
     }
     __syncwarp();
+    int nb2 = 0;                                     // K keys not in the list, compacted in place
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        u64 k = 0;
+        int lo = 0;
+        bool keep = false;
+        if (j < nb) {
+            k = kb[j];
+            int hi = na;                             // list keys <= k
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (ka[mid] <= k) lo = mid + 1; else hi = mid;
+            }
+            keep = lo == 0 || ka[lo - 1] != k;
+        }
+        const u32 m = __ballot_sync(FULL, keep);
+        const int jj = nb2 + __popc(m & lanemask_lt());
+        if (keep) { kb[jj] = k; keys[jj + lo] = k; }
+        nb2 += __popc(m);
+    }
+    __syncwarp();
     for (int i = lane; i < na; i += 32) {
         const u64 k = ka[i];
-        int lo = 0, hi = nb;                         // K keys < k
+        int lo = 0, hi = nb2;                        // kept K keys < k
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (kb[mid] < k) lo = mid + 1; else hi = mid;
         }
         keys[i + lo] = k;
     }
-    for (int j = lane; j < nb; j += 32) {
-        const u64 k = kb[j];
-        int lo = 0, hi = na;                         // list keys <= k
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (ka[mid] <= k) lo = mid + 1; else hi = mid;
-        }
-        keys[j + lo] = k;
-    }
     __syncwarp();
-    const int cn = na + nb;
+    const int cn = na + nb2;
     const int nout = warp_prune<LG>(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
@@ -1362,8 +1418,10 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFold
     const u64 nwork = a.budget ? a.n_pairs : *a.seg_count;
     u64 t_next = 0;   // the next item's claim, in flight while this one runs
     if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
+    u64 pf_t = ~0ull;   // lock-free: the item whose words pf_w, pf_pv hold
+    u32 pf_w = 0, pf_pv = 0;
     for (;;) {
-        u64 t = __shfl_sync(FULL, t_next, 0);
+        const u64 t = __shfl_sync(FULL, t_next, 0);
         if (t >= nwork) break;
         if (lane == 0) t_next = atomicAdd(&d.ctr[C_WORK], 1ull);
         if (a.budget == 0) {
@@ -1383,10 +1441,9 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFold
                 if (!warp_publish(d, ws, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
-            t += a.lo;
-            const u32 w = a.pair_key[t];
+            u32 w = pf_w, pv = pf_pv;
+            if (t != pf_t) { w = a.pair_key[t + a.lo]; pv = a.pair_val[t + a.lo]; }
             if (w >= (u32)d.capacity) continue;
-            const u32 pv = a.pair_val[t];
             bool done = false;
             for (u32 att = 0; att < a.budget && !done; att++) {
                 u64 snap;
@@ -1395,6 +1452,10 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFold
                 __syncwarp();
                 const int n = repair_apply<LG>(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
                                            (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st);
+                if (att == 0) {                      // the next pair's words, in flight while this one publishes
+                    pf_t = __shfl_sync(FULL, t_next, 0);
+                    if (pf_t < nwork) { pf_w = a.pair_key[pf_t + a.lo]; pf_pv = a.pair_val[pf_t + a.lo]; }
+                }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
                 done = warp_publish(d, ws, w, lid, lrho, n, snap);
                 u64 err = 0;
