@@ -40,10 +40,11 @@ constexpr int GRAM_N = 64;
 constexpr int GRAM_RB = 256;   // bytes per staged row (128 bf16 columns)
 __host__ __device__ inline u32 gram_xoff(int r, int chunk) { return (u32)(r * GRAM_RB + ((chunk ^ (r & 7)) << 4)); }
 // Shared-memory bytes of a Gram buffer for `rows` candidates: the bf16 rows
-// (or the table over them) and the norms; 0 rows = no buffer.
+// (or the table over them) and a (norm, rho) pair per candidate; 0 rows = no
+// buffer.  rows is a multiple of 16.
 __host__ __device__ inline size_t gram_bytes(u32 rows) {
     if (!rows) return 0;
-    const size_t b = (size_t)rows * GRAM_RB + (((size_t)rows * 4 + 15) & ~(size_t)15);
+    const size_t b = (size_t)rows * GRAM_RB + (size_t)rows * 8;
     return rows > (u32)GRAM_N ? b + (size_t)rows * 16 : b;   // domination masks of the large path
 }
 constexpr int GRAM_NL = 128;   // candidates of the large (mask) path
@@ -196,18 +197,18 @@ __device__ __forceinline__ int gram_tsw(int r) { return (r & 3) << 3; }
 
 // Writes the upper triangle (j >= i, in 16 x 8 tiles) of the n x n Gram into
 // T (fp32, row stride GRAM_N, columns swizzled by gram_tsw) and the diagonal
-// into nrm.  T and the bf16 rows
+// into nr2[i].x, with rho_i (the candidate's key distance) in nr2[i].y.  T and the bf16 rows
 // share `buf`: the Gram is built in 16-row stripes, and stripe mt's table rows
 // (bytes [4096 mt, 4096 (mt + 1))) are the staged rows of that same stripe,
 // which no later stripe reads (it reads rows >= 16 (mt + 1)).  A stripe only
 // needs the columns j >= 16 mt, because the prune reads T[head][j] for j > head.
 // Rows past n hold whatever the buffer held: an entry (i, j) reads rows i and j
 // only, and no entry with i or j >= n is read.
-__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float *&nrm) {
+__device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float2 *&nr2) {
     (void)st;
     const int lane = lane_id();
     T = reinterpret_cast<float *>(buf);
-    nrm = reinterpret_cast<float *>(buf + (size_t)rows * GRAM_RB);
+    nr2 = reinterpret_cast<float2 *>(buf + (size_t)rows * GRAM_RB);
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
     const int nkb = ((int)d.mp + 127) >> 7;
     const u32 xs = smem_addr(buf), c0 = gram_c0(lane);
@@ -251,7 +252,7 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
         }
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) nrm[i] = T[i * GRAM_N + (i ^ gram_tsw(i))];
+    for (int i = lane; i < n; i += 32) nr2[i] = make_float2(T[i * GRAM_N + (i ^ gram_tsw(i))], key_rho(ck[i]));
     __syncwarp();
 }
 
@@ -268,21 +269,22 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
                                float *out_rho, Stage &st) {
     (void)alive;
     const int lane = lane_id();
-    float *T, *nrm;
-    warp_gram(d, ck, n, st.gram, st.gram_rows, st, T, nrm);
-    const u32 *rk = reinterpret_cast<const u32 *>(ck) + 1;   // high word of key j: ord(rho_j)
+    float *T;
+    float2 *nr2;
+    warp_gram(d, ck, n, st.gram, st.gram_rows, st, T, nr2);
     const float alpha2 = d.alpha2;
     const bool l2 = d.metric == 0;
     // (n_h - g) + (n_j - g): every intermediate stays as small as the result
     auto hit = [&](float nh, float g, int j) {
-        const float dd = l2 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(nrm[j], g)) : __fsub_rn(1.0f, g);
-        return __fmul_rn(alpha2, dd) <= ord2f(rk[2 * j]);
+        const float2 v = nr2[j];
+        const float dd = l2 ? __fadd_rn(__fsub_rn(nh, g), __fsub_rn(v.x, g)) : __fsub_rn(1.0f, g);
+        return __fmul_rn(alpha2, dd) <= v.y;
     };
     u64 dom_a = 0ull, dom_b = 0ull;
     const int ra = lane, rb = n - 2 - lane;
     if (ra < n - 1) {
         const float *Ta = T + ra * GRAM_N;
-        const float na = nrm[ra];
+        const float na = nr2[ra].x;
         const int sw = gram_tsw(ra);
 #pragma unroll 4
         for (int j = ra + 1; j < n; j++)
@@ -290,7 +292,7 @@ __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char
     }
     if (rb >= 32) {
         const float *Tb = T + rb * GRAM_N;
-        const float nb = nrm[rb];
+        const float nb = nr2[rb].x;
         const int sw = gram_tsw(rb);
 #pragma unroll 4
         for (int j = rb + 1; j < n; j++)
@@ -345,8 +347,8 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
     const int lane = lane_id();
     const int rows = st.gram_rows;
     char *tail = st.gram + (size_t)rows * GRAM_RB;
-    float *nrm = reinterpret_cast<float *>(tail);
-    u64 *dom = reinterpret_cast<u64 *>(tail + (((size_t)rows * 4 + 15) & ~(size_t)15));
+    float2 *nr2 = reinterpret_cast<float2 *>(tail);   // .x: the norms (.y unused here)
+    u64 *dom = reinterpret_cast<u64 *>(tail + (size_t)rows * 8);
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
     const int nkb = ((int)d.mp + 127) >> 7;
     const u32 xs = smem_addr(st.gram), c0 = gram_c0(lane);
@@ -388,11 +390,11 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
                 if (nt == 2 * mt + 1) d1 = cq == (lane >> 2) ? acc[nt][2] : acc[nt][3];
             }
             const bool own = cq == (lane >> 2) || cq + 1 == (lane >> 2);
-            if (own && r0 < n) nrm[r0] = d0;
-            if (own && r1 < n) nrm[r1] = d1;
+            if (own && r0 < n) nr2[r0].x = d0;
+            if (own && r1 < n) nr2[r1].x = d1;
         }
         __syncwarp();
-        const float n0 = r0 < n ? nrm[r0] : 0.f, n1 = r1 < n ? nrm[r1] : 0.f;
+        const float n0 = r0 < n ? nr2[r0].x : 0.f, n1 = r1 < n ? nr2[r1].x : 0.f;
         u64 m0l = 0, m0h = 0, m1l = 0, m1h = 0;
 #pragma unroll
         for (int nt = 0; nt < NT; nt++) {
@@ -404,7 +406,7 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
                 const int cc = ok ? c : 0;
                 const float g = acc[nt][e];
                 const float nr_ = e < 2 ? n0 : n1;
-                const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nr_, g), __fsub_rn(nrm[cc], g)) : __fsub_rn(1.0f, g);
+                const float dd = d.metric == 0 ? __fadd_rn(__fsub_rn(nr_, g), __fsub_rn(nr2[cc].x, g)) : __fsub_rn(1.0f, g);
                 const bool hit = ok && __fmul_rn(d.alpha2, dd) <= key_rho(ck[cc]);
                 const u64 bit = hit ? 1ull << (c & 63) : 0ull;
                 if (e < 2) { if (8 * nt < 64) m0l |= bit; else m0h |= bit; }
@@ -1275,7 +1277,9 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
 cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
                             u32 *pair_val, uint2 *pair_K, u32 *pair_Kn, int num_sms, cudaStream_t st) {
     if (max_n == 0) return cudaSuccess;
-    RepairKArgs a{d, dt, n_dt, max_n, stage_cap(d.mp, d.R, d.stage_bytes), 0u, pair_key, pair_val, pair_K, pair_Kn};
+    // B's rows are read about |B| times each: stage up to 16 KB of them
+    const u32 budget = d.stage_bytes > (16u << 10) ? d.stage_bytes : (16u << 10);
+    RepairKArgs a{d, dt, n_dt, max_n, stage_cap(d.mp, d.R, budget), 0u, pair_key, pair_val, pair_K, pair_Kn};
     const size_t wb = repk_warp_bytes(d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
