@@ -165,6 +165,52 @@ __device__ __forceinline__ float canon_dist(const float *__restrict__ a, const f
     return metric == 0 ? s : __fsub_rn(1.0f, s);
 }
 
+// canon_dist<8> for rows of at most 128 floats, in two steps so that several
+// rows' loads can be in flight: canon_row_q8 loads this lane's four row float4
+// (elements 4 (g + 8 t) .. + 3, t = 0..3; zero past the row), canon_dist_q8v
+// reduces them against the query's four float4 held in registers, with the
+// same operations in the same order as canon_dist<8>.
+__device__ __forceinline__ void canon_row_q8(const float *__restrict__ b, int mp, int g, float4 (&v)[4]) {
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int i = 4 * (g + 8 * t);
+        v[t] = i < mp ? *reinterpret_cast<const float4 *>(b + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ float canon_dist_q8v(const float4 (&qr)[4], const float4 (&v)[4], int mp, int metric,
+                                                int g) {
+    float p[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const int i = 4 * (g + 8 * t);
+        float acc = 0.0f;
+        if (i < mp) {
+            const float4 u = qr[t];
+            if (metric == 0) {
+                float d0 = __fsub_rn(u.x, v[t].x), d1 = __fsub_rn(u.y, v[t].y);
+                float d2 = __fsub_rn(u.z, v[t].z), d3 = __fsub_rn(u.w, v[t].w);
+                acc = __fmaf_rn(d0, d0, acc);
+                acc = __fmaf_rn(d1, d1, acc);
+                acc = __fmaf_rn(d2, d2, acc);
+                acc = __fmaf_rn(d3, d3, acc);
+            } else {
+                acc = __fmaf_rn(u.x, v[t].x, acc);
+                acc = __fmaf_rn(u.y, v[t].y, acc);
+                acc = __fmaf_rn(u.z, v[t].z, acc);
+                acc = __fmaf_rn(u.w, v[t].w, acc);
+            }
+        }
+        p[t] = acc;
+    }
+    p[0] = __fadd_rn(p[0], p[2]);
+    p[1] = __fadd_rn(p[1], p[3]);
+    float s = __fadd_rn(p[0], p[1]);
+#pragma unroll
+    for (int h = 4; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
+    return metric == 0 ? s : __fsub_rn(1.0f, s);
+}
+
 // ---- small warp helpers -------------------------------------------------------
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ u32 lanemask_lt() {

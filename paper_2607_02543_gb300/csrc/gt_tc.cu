@@ -632,8 +632,8 @@ __global__ void __launch_bounds__(SS_WARPS * 32) seed_select_kernel(Dev d, SeedS
     u32 tau = ~0u;                                   // all entries when S <= want
     if (a.S > a.want) {
         // a threshold from every 8th key (16 per lane), kept when the count
-        // of keys at or below it lands in [want, SS_CAP]; else the exact
-        // want-th smallest key by a bitwise search over all keys
+        // of keys at or below it lands in [want, SS_CAP]; else (below) the
+        // exact want-th smallest key by a bitwise search over all keys
         u32 smp[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -649,40 +649,73 @@ __global__ void __launch_bounds__(SS_WARPS * 32) seed_select_kernel(Dev d, SeedS
             for (int j = 0; j < 16; j++) c += (u32)(smp[j] < tr);
             if (__reduce_add_sync(FULL, c) < rs) t0 = tr;
         }
-        u32 c = 0;
-        for (u32 e = lane; e < a.S; e += 32) c += (u32)(f2ord(row[e]) <= t0);
-        c = __reduce_add_sync(FULL, c);
-        if (t0 != ~0u && c >= a.want && c <= (u32)SS_CAP) {
-            tau = t0;
-        } else {
-            tau = 0;
-            for (int bit = 31; bit >= 0; bit--) {
-                const u32 tr = tau | (1u << bit);
-                u32 c2 = 0;
-                for (u32 e = lane; e < a.S; e += 32) c2 += (u32)(f2ord(row[e]) < tr);
-                if (__reduce_add_sync(FULL, c2) < a.want) tau = tr;
-            }
-        }
+        tau = t0;
     }
-    u32 cnt = 0;
-    for (u32 e0 = 0; e0 < a.S; e0 += 32) {
-        const u32 e = e0 + lane;
-        const bool c = e < a.S && f2ord(row[e]) <= tau;
-        const u32 m = __ballot_sync(FULL, c);
-        const u32 pos = cnt + __popc(m & lanemask_lt());
-        if (c && pos < SS_CAP) cidx[warp][pos] = e;
-        cnt += __popc(m);
+    // entries with key <= tau, collected and counted in one pass
+    auto collect = [&](u32 t) {
+        u32 n = 0;
+        for (u32 e0 = 0; e0 < a.S; e0 += 32) {
+            const u32 e = e0 + lane;
+            const bool c = e < a.S && f2ord(row[e]) <= t;
+            const u32 m = __ballot_sync(FULL, c);
+            const u32 pos = n + __popc(m & lanemask_lt());
+            if (c && pos < SS_CAP) cidx[warp][pos] = e;
+            n += __popc(m);
+        }
+        return n;
+    };
+    u32 cnt = collect(tau);
+    if (a.S > a.want && (tau == ~0u || cnt < a.want || cnt > (u32)SS_CAP)) {
+        // the sampled threshold missed: the exact want-th smallest key
+        tau = 0;
+        for (int bit = 31; bit >= 0; bit--) {
+            const u32 tr = tau | (1u << bit);
+            u32 c2 = 0;
+            for (u32 e = lane; e < a.S; e += 32) c2 += (u32)(f2ord(row[e]) < tr);
+            if (__reduce_add_sync(FULL, c2) < a.want) tau = tr;
+        }
+        __syncwarp();
+        cnt = collect(tau);
     }
     __syncwarp();
     bool cert = false;
     if (cnt <= SS_CAP) {
         const float *qv = a.q + (size_t)qi * d.mp;
         const int grp = lane >> 3, g = lane & 7;
-        for (u32 r0 = 0; r0 < cnt; r0 += 4) {
-            const u32 i = r0 + grp;
-            const u32 id = d.entries[cidx[warp][i < cnt ? i : cnt - 1]];
-            const float dd = canon_dist<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
-            if (i < cnt && g == 0) ckey[warp][i] = mkkey(dd, id);
+        if (d.mp <= 128) {
+            // the query's elements in registers; four rows per group in flight
+            float4 qr[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int i = 4 * (g + 8 * t);
+                qr[t] = i < (int)d.mp ? *reinterpret_cast<const float4 *>(qv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            for (u32 r0 = 0; r0 < cnt; r0 += 16) {
+                u32 id[4];
+                float dd[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const u32 i = r0 + grp + 4 * u;
+                    id[u] = d.entries[cidx[warp][i < cnt ? i : cnt - 1]];
+                }
+                float4 v[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) canon_row_q8(d.x + (size_t)id[u] * d.mp, (int)d.mp, g, v[u]);
+#pragma unroll
+                for (int u = 0; u < 4; u++) dd[u] = canon_dist_q8v(qr, v[u], (int)d.mp, (int)d.metric, g);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const u32 i = r0 + grp + 4 * u;
+                    if (i < cnt && g == 0) ckey[warp][i] = mkkey(dd[u], id[u]);
+                }
+            }
+        } else {
+            for (u32 r0 = 0; r0 < cnt; r0 += 4) {
+                const u32 i = r0 + grp;
+                const u32 id = d.entries[cidx[warp][i < cnt ? i : cnt - 1]];
+                const float dd = canon_dist<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
+                if (i < cnt && g == 0) ckey[warp][i] = mkkey(dd, id);
+            }
         }
         const int np = next_pow2((int)cnt);
         for (int i = (int)cnt + lane; i < np; i += 32) ckey[warp][i] = KEY_INF;
