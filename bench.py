@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
+    ap.add_argument("--varbatch", action="store_true",
+                    help="uneven-batch run on the 1M x 960 non-negative mixture: 30 rounds of variable "
+                         "insert/delete batches and graph-launched query batches")
     ap.add_argument("--serve", action="store_true",
                     help="serving run on the 10M x 96 mixture: Poisson queries with interleaved updates")
     ap.add_argument("--qps-target", type=float, default=50_000.0, help="serving: query arrival rate (1/s)")
@@ -368,9 +371,157 @@ def run_serve(args):
     print(json.dumps(res), flush=True)
 
 
+def run_varbatch(args):
+    """Uneven batches on the 1M x 960 non-negative mixture, degree 32: per
+    round a delete batch of U[0, 2% of live] ids, an insert batch of
+    log-uniform [64, 65,536] fresh vectors, Reclaim, then a query batch of
+    log-uniform [1, 16,384] queries through one captured query graph (batch
+    size read from device memory).  The BeamSearch launch shape is tuned by
+    the library's autotuner and EF_SEARCH is the smallest beam reaching
+    Recall@10 >= 0.95 on 1,000 anchor queries.  Reports ms per round against
+    the batch sizes, QPS, Recall@10 of the anchors after the run, and the
+    query batches' algorithmic bytes per second against the measured HBM peak."""
+    import torch
+    from paper_2607_02543_gb300 import Index, build as B
+    B.build()
+    w = W.GIST_LIKE_1M
+    n = args.n_live or w.n_base
+    if n != w.n_base:
+        w = W.dataclasses.replace(w, name=f"{w.name}@{n}", n_base=n)
+    mix = W.Mixture(w)
+    rng = W._streams(w.seed)["batches"]
+    rounds = args.steps if args.steps != 5 else w.rounds
+    n_ins = W.random_batch_sizes(rng, rounds, 64, 65_536)
+    n_q = W.random_batch_sizes(rng, rounds, 1, 16_384)
+    capacity = n + int(n_ins.sum()) + 16
+    X = mix.draw("base", n)
+    fresh = mix.draw("inserts", int(n_ins.sum()))
+    pool = mix.draw("queries", w.n_queries)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    idx = Index(w.dim, w.metric, w.degree, capacity, build_beam=w.build_beam, mode="lockfree",
+                n_entry=args.n_entry, max_cand=args.max_cand)
+    t0 = time.perf_counter()
+    idx.insert(torch.from_numpy(X).to(dev), stream)
+    idx.reclaim(stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del X
+    d_pool = torch.from_numpy(pool).to(dev)
+    d_anchor = d_pool[:1000].contiguous()
+    gt_np = None
+
+    def anchor_recall(beam):
+        # the anchors' exact neighbours in the current live set
+        ids, _ = idx.search(d_anchor, w.k, beam, stream)
+        got = ids.cpu().numpy().view(np.uint32)
+        return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w.k for a, b in zip(got, gt_np)]))
+
+    def refresh_gt():
+        nonlocal gt_np
+        gt_a, _ = idx.ground_truth(d_anchor, w.k, stream)
+        gt_np = gt_a.cpu().numpy().view(np.uint32)
+
+    refresh_gt()
+    beam, sweep = 256, []
+    for b in (64, 96, 128, 160, 192, 256):
+        rec = anchor_recall(b)
+        sweep.append([b, rec])
+        if rec >= 0.95:
+            beam = b
+            break
+    tried = idx.autotune_search(d_pool[:4096].contiguous(), w.k, beam, stream)
+    best = min(tried, key=lambda t: t[2])
+    nq_max = w.n_queries
+    qbuf = torch.zeros((nq_max, w.dim), dtype=torch.float32, device=dev)
+    oid = torch.empty((nq_max, w.k), dtype=torch.int32, device=dev)
+    od = torch.empty((nq_max, w.k), dtype=torch.float32, device=dev)
+    nq_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+    graph = idx.search_graph(qbuf, oid, od, nq_dev, w.k, beam)
+    alive = np.zeros(capacity, bool)
+    alive[:n] = True
+    next_id, off = n, 0
+    del_rng = W._streams(w.seed)["deletes"]
+    sel_rng = np.random.default_rng(w.seed)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    R, m = w.degree, w.dim
+    rows = []
+    idx.set_profiling(True)
+    idx.profile(reset=True)
+    for r in range(rounds):
+        live_ids = np.nonzero(alive)[0].astype(np.uint32)
+        nd = int(del_rng.integers(0, int(0.02 * live_ids.size) + 1))
+        dl = W.choose_deletes(del_rng, live_ids, nd)
+        alive[dl] = False
+        ni, nq = int(n_ins[r]), int(n_q[r])
+        d_del = torch.from_numpy(dl.astype(np.int32)).to(dev)
+        d_ins = torch.from_numpy(fresh[off:off + ni]).to(dev)
+        off += ni
+        alive[next_id:next_id + ni] = True
+        next_id += ni
+        sel = torch.from_numpy(sel_rng.choice(nq_max, nq, replace=False)).to(dev)
+        qbuf[:nq] = d_pool[sel]
+        nq_dev.fill_(nq)
+        torch.cuda.synchronize()
+        s0 = idx.stats()
+        ev[0].record(stream)
+        if nd:
+            idx.delete(d_del, stream)
+        idx.insert(d_ins, stream)
+        idx.reclaim(stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        s1 = idx.stats()
+        ev[2].record(stream)
+        graph.launch(stream)
+        ev[3].record(stream)
+        graph.check(stream)
+        torch.cuda.synchronize()
+        s2 = idx.stats()
+        qms = ev[2].elapsed_time(ev[3])
+        alg = (s2["n_expand"] - s1["n_expand"]) * 8 * R + (s2["n_dist"] - s1["n_dist"]) * (4 * m + 8) + \
+            nq * (4 * m + 8 * w.k)
+        rows.append({"round": r, "deletes": nd, "inserts": ni, "update_ms": ev[0].elapsed_time(ev[1]),
+                     "queries": nq, "query_ms": qms, "query_alg_gbs": alg / (qms * 1e-3) / 1e9,
+                     "publishes": s1["n_publish"] - s0["n_publish"]})
+    graph.close()
+    phases = {k2: round(v[0], 2) for k2, v in idx.profile(reset=True).items() if v[1]}
+    idx.set_profiling(False)
+    refresh_gt()
+    rec_after = anchor_recall(beam)
+    st = idx.stats()
+    peak, peak_kind = load_peaks("hbm_gbs")
+    upd = np.array([x["update_ms"] for x in rows])
+    qtot = sum(x["queries"] for x in rows)
+    qms_tot = sum(x["query_ms"] for x in rows)
+    big = [x for x in rows if x["queries"] >= 4096]
+    best_q = max(big, key=lambda x: x["query_alg_gbs"]) if big else None
+    ins = np.array([x["inserts"] for x in rows], dtype=np.float64)
+    res = {"metric": "ms per churn round, uneven batches (1M x 960)", "value": float(upd.mean()), "unit": "ms",
+           "n_gpus": 1, "steps": rounds, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": w.name, "n_live": n, "dim": m, "degree": R, "build_beam": w.build_beam,
+                      "mode": "lockfree", "insert_batch": "log-uniform [64, 65536]",
+                      "delete_batch": "uniform [0, 2% of live]", "query_batch": "log-uniform [1, 16384]",
+                      "search_beam": beam, "k": w.k, "query_path": "one captured CUDA graph, batch size in device memory"},
+           "us_per_inserted_vector": float(1e3 * upd.sum() / max(1.0, ins.sum())),
+           "qps": qtot / (qms_tot * 1e-3), "recall_at_10_anchor": {"before": sweep[-1][1], "after": rec_after},
+           "beam_sweep": sweep, "search_tuning": {"stage_rows": best[0], "seen_bits": best[1]},
+           "phase_ms_total": phases,
+           "query_roofline": None if best_q is None else {
+               "bound": "hbm", "kernel": "captured query graph (seeding + search_kernel)",
+               "achieved": best_q["query_alg_gbs"], "peak": peak, "unit": "GB/s",
+               "frac": best_q["query_alg_gbs"] / peak, "peak_source": peak_kind,
+               "basis": "algorithmic bytes of the batch / graph time, largest-throughput batch of >= 4096 queries"},
+           "rounds": [{k2: (round(v, 3) if isinstance(v, float) else v) for k2, v in x.items()} for x in rows],
+           "build_s": build_s, "stats": {k2: st[k2] for k2 in ("live", "used_slabs", "n_dropped", "n_publish")}}
+    print(json.dumps(res), flush=True)
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.varbatch:
+        return run_varbatch(args)
     if args.serve:
         return run_serve(args)
     if args.experiment:

@@ -216,7 +216,8 @@ typedef struct {
 etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits);
 
 /* Time seeding + BeamSearch of the given DEVICE query batch under each
- * candidate launch shape (stage rows 4/8/16 x cache 2^7..2^10 slots), keep
+ * candidate launch shape (stage rows 2/4/8/16 x cache 2^7..2^10 slots; shapes
+ * whose shared memory does not fit the device are skipped), keep
  * the fastest for this index, and report up to n_out tried shapes in out.
  * Results do not depend on the launch shape.                               */
 etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,

@@ -67,7 +67,7 @@ u32 bits_for(u64 v) {
 }  // namespace
 
 struct etale_index {
-    int device = 0, num_sms = 0;
+    int device = 0, num_sms = 0, smem_optin = 0;
     etale_config cfg{};
     u32 dim = 0, mp = 0, R = 0, metric = 0;
     u64 capacity = 0, pool = 0;
@@ -428,6 +428,14 @@ etale_status size_batch_scratch(etale_index *idx, u64 b) {
     return ok ? ETALE_OK : idx->fail(ETALE_ENOMEM, "scratch allocation (insert batch of %llu)", (unsigned long long)b);
 }
 
+// The BeamSearch launch shape with its row stage shrunk until a block's shared
+// memory fits the device (long rows); results do not depend on the stage.
+SearchTuning fit_tuning(const etale_index *idx, u32 L, SearchTuning t) {
+    while (t.stage_rows > 1 && search_smem_bytes(idx->mp, L, t.stage_rows, 1u << t.seen_bits) > (size_t)idx->smem_optin)
+        t.stage_rows >>= 1;
+    return t;
+}
+
 // Seeds of nq BeamSearches (top-L of the entry set): tensor cores with a
 // certified exact rerank when they apply, else the CUDA-core kernel; both
 // give the same seeds.  Returns the launches made.
@@ -466,7 +474,7 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     {
         PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
         CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr,
-                         as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), idx->tune,
+                         as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, L, idx->tune),
                          idx->num_sms, st),
            "insert search");
     }
@@ -620,6 +628,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
     idx->alpha2 = cfg.alpha * cfg.alpha;
     cudaGetDevice(&idx->device);
     cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device);
+    cudaDeviceGetAttribute(&idx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device);
     const size_t xb = (size_t)capacity * idx->mp * 4, rb = (size_t)capacity * 8;
     const size_t sb = (size_t)idx->pool * degree * 8, pb = (size_t)idx->pool * 4;
     bool ok = cudaMalloc(&idx->x, xb) == cudaSuccess && cudaMalloc(&idx->ref, rb) == cudaSuccess &&
@@ -1004,7 +1013,7 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
         if (prof) prof_end(idx, st);
         if (s != ETALE_OK) return s;
         if (prof) prof_begin(idx, ETALE_PH_SEARCH_QUERY, st);
-        CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->s_seed), idx->tune,
+        CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->s_seed), fit_tuning(idx, L, idx->tune),
                          idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
            "search");
         if (prof) prof_end(idx, st);
@@ -1133,12 +1142,13 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
     float best = 1e30f;
     SearchTuning best_t = saved;
     u32 tried = 0;
-    const u32 rows[3] = {4, 8, 16}, bits[4] = {7, 8, 9, 10};
-    for (u32 a = 0; a < 3; a++)
+    const u32 rows[4] = {2, 4, 8, 16}, bits[4] = {7, 8, 9, 10};
+    for (u32 a = 0; a < 4; a++)
         for (u32 b = 0; b < 4; b++) {
             SearchTuning t;
             t.stage_rows = rows[a];
             t.seen_bits = bits[b];
+            if (fit_tuning(idx, L, t).stage_rows != t.stage_rows) continue;   // does not fit: not a shape
             float ms_best = 1e30f;
             bool ok = true;
             for (int rep = 0; rep < 3 && ok; rep++) {   // first run warms up
@@ -1198,7 +1208,7 @@ etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32
         if (e == cudaSuccess) e = launch_seed(d, g->qpad, nq_max, L, g->seed, cs, idx->search_prec, nq_dev);
         if (e == cudaSuccess)
             e = launch_search(d, g->qpad, nq_max, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, g->seed,
-                              idx->tune, idx->num_sms, cs, idx->search_prec, idx->cfg.rerank, nq_dev);
+                              fit_tuning(idx, L, idx->tune), idx->num_sms, cs, idx->search_prec, idx->cfg.rerank, nq_dev);
         return e;
     };
     // one eager run sets the kernels' attributes outside the capture
@@ -1344,7 +1354,7 @@ etale_status etale_search_static(etale_index *idx, const float *queries, uint64_
     CK(launch_seed(d, qpad, (u32)nq, L, seed, st, idx->search_prec), "query seed");
     const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
     if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
-    CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, seed, idx->tune,
+    CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, seed, fit_tuning(idx, L, idx->tune),
                      idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
        "search");
     g_kernel_launches += 3;

@@ -17,7 +17,7 @@ import math
 
 import numpy as np
 
-STREAMS = ("centers", "base", "inserts", "deletes", "queries", "assign", "stream")   # appended only: earlier streams keep their seeds
+STREAMS = ("centers", "base", "inserts", "deletes", "queries", "assign", "stream", "batches")   # appended only: earlier streams keep their seeds
 
 
 def _streams(seed: int) -> dict[str, np.random.Generator]:
@@ -64,6 +64,11 @@ SIFT_LIKE_1M = Workload("int256-1m-d128", 1_000_000, 128, "l2", 32, 128, 20,
 # 1,024 centres, 10 rounds of 1% churn; kept with BF16 and FP8 search copies.
 UNIT768_1M = Workload("unit768-1m-ip", 1_000_000, 768, "ip", 64, 128, 10,
                       10_000, 10_000, 10_000, 10, 64, 1024, "unit")
+# 1,000,000 x 960 non-negative mixture (512 centres, GIST-like), degree 32;
+# 30 rounds of uneven batches (sizes drawn per round, see random_batch_sizes):
+# n_delete and n_insert are 0 here, the run draws them.
+GIST_LIKE_1M = Workload("absgauss960-1m-d960", 1_000_000, 960, "l2", 32, 128, 30, 0, 0,
+                        16_384, 10, 128, 512, "absgauss")
 # 10,000,000 x 96 Gaussian mixture (1,000 centres), the served configuration.
 GAUSS96_10M = Workload("gauss96-10m-d96", 10_000_000, 96, "l2", 32, 64, 1,
                        0, 0, 1_000, 10, 64, 1000, "gauss")
@@ -87,6 +92,8 @@ class Mixture:
                   clamped to [0, 255] (an integer-valued, SIFT-shaped set).
     kind "unit":  centres uniform on the unit sphere, points =
                   normalise(centre + 0.3 N(0, I/m)).
+    kind "absgauss": centres ~ |N(0, 10^2 I)|, points = |centre + N(0, I)|
+                  (non-negative, GIST-shaped).
     """
 
     def __init__(self, w: Workload):
@@ -96,6 +103,8 @@ class Mixture:
         gc = self.g["centers"]
         if w.kind == "gauss":
             self.centers = gc.normal(0.0, 10.0, size=(k, m))
+        elif w.kind == "absgauss":
+            self.centers = np.abs(gc.normal(0.0, 10.0, size=(k, m)))
         elif w.kind == "int":
             self.centers = gc.uniform(0.0, 255.0, size=(k, m))
         elif w.kind == "unit":
@@ -115,6 +124,8 @@ class Mixture:
             c = self.centers[lab]
             if w.kind == "gauss":
                 p = c + noise
+            elif w.kind == "absgauss":
+                p = np.abs(c + noise)
             elif w.kind == "int":
                 p = np.clip(np.rint(c + 20.0 * noise), 0.0, 255.0)
             else:
