@@ -27,7 +27,7 @@ struct Stage {
     u64 *bar;        // this warp's mbarrier
     u32 phase;
     bool timeout;
-    char *gram;      // gram_bytes(gram_rows) for the tensor-core Gram path (nullptr: canonical path)
+    char *gram;      // gram_bytes(gram_rows, mp) for the tensor-core Gram path (nullptr: canonical path)
     int gram_rows;   // candidates the Gram buffer holds (a multiple of 16, <= GRAM_N)
 };
 
@@ -39,18 +39,32 @@ struct Stage {
 constexpr int GRAM_N = 64;
 constexpr int GRAM_RB = 256;   // bytes per staged row (128 bf16 columns)
 __host__ __device__ inline u32 gram_xoff(int r, int chunk) { return (u32)(r * GRAM_RB + ((chunk ^ (r & 7)) << 4)); }
-// Shared-memory bytes of a Gram buffer for `rows` candidates: the bf16 rows
-// (or the table over them) and a (norm, rho) pair per candidate; 0 rows = no
-// buffer.  rows is a multiple of 16.
-__host__ __device__ inline size_t gram_bytes(u32 rows) {
-    if (!rows) return 0;
+// Byte offset, in a Gram buffer for `rows` candidates, of the partial sums
+// that rows longer than one 128-column block keep between blocks: after the
+// bf16 rows (or the table over them), a (norm, rho) pair per candidate and
+// the large path's domination masks.  rows is a multiple of 16.
+__host__ __device__ inline size_t gram_part_off(u32 rows) {
     const size_t b = (size_t)rows * GRAM_RB + (size_t)rows * 8;
-    return rows > (u32)GRAM_N ? b + (size_t)rows * 16 : b;   // domination masks of the large path
+    return rows > (u32)GRAM_N ? b + (size_t)rows * 16 : b;
 }
+// Shared-memory bytes of a Gram buffer for `rows` candidates of mp columns;
+// 0 rows = no buffer.  With more than one column block, a small-path buffer
+// (rows <= GRAM_N) also holds one accumulator fragment (32 lanes x 16 bytes)
+// per upper-triangle tile: nm (nm + 1) tiles for nm = rows / 16 stripes.
+__host__ __device__ inline size_t gram_bytes(u32 rows, u32 mp) {
+    if (!rows) return 0;
+    const size_t nm = rows / 16;
+    return gram_part_off(rows) + (mp > 128 && rows <= (u32)GRAM_N ? nm * (nm + 1) * 512 : 0);
+}
+// First tile slot of stripe mt among the partial sums (stripe mt holds the
+// tiles nt = 2 mt .. 2 nmr - 1, nmr = rows / 16).
+__device__ __forceinline__ int gram_part_slot(int mt, int nmr) { return mt * (2 * nmr + 1 - mt); }
 constexpr int GRAM_NL = 128;   // candidates of the large (mask) path
 // Gram rows for a kernel whose prunes see at most max_n candidates (0: the
 // Gram path is off or cannot hold them).  Above GRAM_N rows the kernel runs
 // the large path (warp_prune_masks).
+// The Gram variant (see warp_prune) of a kernel whose buffer holds gram_rows rows of mp columns.
+inline int gram_variant(u32 gram_rows, u32 mp) { return gram_rows > (u32)GRAM_N ? 1 : (gram_rows && mp > 128 ? 2 : 0); }
 inline u32 gram_rows_for(u32 on, u32 max_n) { return on && max_n <= (u32)GRAM_NL ? (max_n + 15) / 16 * 16 : 0; }
 // Scratch that is dead whenever the Gram buffer is live (list compaction before
 // a prune, the canonical prune's arrays, a prune's output, written after its
@@ -197,63 +211,138 @@ __device__ __forceinline__ int gram_tsw(int r) { return (r & 3) << 3; }
 
 // Writes the upper triangle (j >= i, in 16 x 8 tiles) of the n x n Gram into
 // T (fp32, row stride GRAM_N, columns swizzled by gram_tsw) and the diagonal
-// into nr2[i].x, with rho_i (the candidate's key distance) in nr2[i].y.  T and the bf16 rows
-// share `buf`: the Gram is built in 16-row stripes, and stripe mt's table rows
-// (bytes [4096 mt, 4096 (mt + 1))) are the staged rows of that same stripe,
-// which no later stripe reads (it reads rows >= 16 (mt + 1)).  A stripe only
-// needs the columns j >= 16 mt, because the prune reads T[head][j] for j > head.
-// Rows past n hold whatever the buffer held: an entry (i, j) reads rows i and j
+// into nr2[i].x, with rho_i (the candidate's key distance) in nr2[i].y.
+// Column blocks of 128 go outermost: each block of every row is staged once,
+// and with more than one block each stripe adds its products for the block
+// to the buffer's partial sums (fp32; exact for the integer-valued data the
+// tile is exact for).  T and the bf16 rows share `buf`: in the last block the stripes go
+// in ascending order, and stripe mt's table rows (bytes [4096 mt,
+// 4096 (mt + 1))) are the staged rows of that same stripe, which no later
+// stripe reads (it reads rows >= 16 (mt + 1)).  A stripe only needs the
+// columns j >= 16 mt, because the prune reads T[head][j] for j > head.  Rows
+// past n hold whatever the buffer held: an entry (i, j) reads rows i and j
 // only, and no entry with i or j >= n is read.
+template <bool MB>   // rows span more than one 128-column block
 __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float2 *&nr2) {
-    (void)st;
-    const int lane = lane_id();
-    T = reinterpret_cast<float *>(buf);
-    nr2 = reinterpret_cast<float2 *>(buf + (size_t)rows * GRAM_RB);
-    const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
-    const int nkb = ((int)d.mp + 127) >> 7;
-    const u32 xs = smem_addr(buf), c0 = gram_c0(lane);
-    for (int mt = 0; mt < nm; mt++) {
-        float acc[8][4];
+    if constexpr (!MB) {
+        (void)st;
+        const int lane = lane_id();
+        T = reinterpret_cast<float *>(buf);
+        nr2 = reinterpret_cast<float2 *>(buf + (size_t)rows * GRAM_RB);
+        const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
+        const int nkb = ((int)d.mp + 127) >> 7;
+        const u32 xs = smem_addr(buf), c0 = gram_c0(lane);
+        for (int mt = 0; mt < nm; mt++) {
+            float acc[8][4];
 #pragma unroll
-        for (int b = 0; b < 8; b++)
+            for (int b = 0; b < 8; b++)
 #pragma unroll
-            for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
-        for (int kb = 0; kb < nkb; kb++) {
-            // rows [16 mt, n) of this column block: all rows once when one
-            // block covers the row, else this stripe's and later ones per block
-            if (nkb > 1 || mt == 0) gram_stage_rows(d, ck, 16 * mt, n, kb, xs);
+                for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
+            for (int kb = 0; kb < nkb; kb++) {
+                // rows [16 mt, n) of this column block: all rows once when one
+                // block covers the row, else this stripe's and later ones per block
+                if (nkb > 1 || mt == 0) gram_stage_rows(d, ck, 16 * mt, n, kb, xs);
 #pragma unroll
-            for (int ks = 0; ks < 8; ks++) {
-                u32 a0, a1, a2, a3;
-                const u32 ko = (u32)(32 * ks) ^ c0;
-                const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
-                ldsm_x4(a0, a1, a2, a3, xs + (u32)ar * GRAM_RB + ko);
+                for (int ks = 0; ks < 8; ks++) {
+                    u32 a0, a1, a2, a3;
+                    const u32 ko = (u32)(32 * ks) ^ c0;
+                    const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(a0, a1, a2, a3, xs + (u32)ar * GRAM_RB + ko);
 #pragma unroll
-                for (int nt = 0; nt < 8; nt += 2) {
-                    if (nt < 2 * mt || nt >= nn) continue;
-                    // matrices: (nt, k 0-7), (nt + 1, k 0-7), (nt, k 8-15), (nt + 1, k 8-15)
-                    u32 b0, b1, b2, b3;
-                    const int br = 8 * nt + (lane & 7) + 8 * ((lane >> 3) & 1);
-                    ldsm_x4(b0, b1, b2, b3, xs + (u32)br * GRAM_RB + ko);
-                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b2);
-                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b1, b3);
+                    for (int nt = 0; nt < 8; nt += 2) {
+                        if (nt < 2 * mt || nt >= nn) continue;
+                        // matrices: (nt, k 0-7), (nt + 1, k 0-7), (nt, k 8-15), (nt + 1, k 8-15)
+                        u32 b0, b1, b2, b3;
+                        const int br = 8 * nt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                        ldsm_x4(b0, b1, b2, b3, xs + (u32)br * GRAM_RB + ko);
+                        mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b2);
+                        mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b1, b3);
+                    }
                 }
             }
-        }
-        __syncwarp();
-        // this stripe's table rows, over this stripe's staged rows (rows r and
-        // r + 8 share the column swizzle)
+            __syncwarp();
+            // this stripe's table rows, over this stripe's staged rows (rows r and
+            // r + 8 share the column swizzle)
 #pragma unroll
-        for (int nt = 0; nt < 8; nt++) {
-            if (nt < 2 * mt || nt >= nn) continue;
-            const int r = 16 * mt + (lane >> 2), c = (8 * nt + 2 * (lane & 3)) ^ gram_tsw(r);
-            *reinterpret_cast<float2 *>(T + r * GRAM_N + c) = make_float2(acc[nt][0], acc[nt][1]);
-            *reinterpret_cast<float2 *>(T + (r + 8) * GRAM_N + c) = make_float2(acc[nt][2], acc[nt][3]);
+            for (int nt = 0; nt < 8; nt++) {
+                if (nt < 2 * mt || nt >= nn) continue;
+                const int r = 16 * mt + (lane >> 2), c = (8 * nt + 2 * (lane & 3)) ^ gram_tsw(r);
+                *reinterpret_cast<float2 *>(T + r * GRAM_N + c) = make_float2(acc[nt][0], acc[nt][1]);
+                *reinterpret_cast<float2 *>(T + (r + 8) * GRAM_N + c) = make_float2(acc[nt][2], acc[nt][3]);
+            }
+            __syncwarp();
         }
+        for (int i = lane; i < n; i += 32) nr2[i] = make_float2(T[i * GRAM_N + (i ^ gram_tsw(i))], key_rho(ck[i]));
+        __syncwarp();
+    } else {
+        (void)st;
+        const int lane = lane_id();
+        T = reinterpret_cast<float *>(buf);
+        nr2 = reinterpret_cast<float2 *>(buf + (size_t)rows * GRAM_RB);
+        float4 *part = reinterpret_cast<float4 *>(buf + gram_part_off((u32)rows));
+        const int nm = (n + 15) >> 4, nn = (n + 7) >> 3, nmr = rows >> 4;
+        const int nkb = MB ? ((int)d.mp + 127) >> 7 : 1;
+        const u32 xs = smem_addr(buf), c0 = gram_c0(lane);
+        for (int kb = 0; kb < nkb; kb++) {
+            gram_stage_rows(d, ck, 0, n, kb, xs);
+            const bool last = kb == nkb - 1;
+            for (int mt = 0; mt < nm; mt++) {
+                const int slot = gram_part_slot(mt, nmr) - 2 * mt;
+                float acc[8][4];
+#pragma unroll
+                for (int b = 0; b < 8; b++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
+#pragma unroll
+                for (int ks = 0; ks < 8; ks++) {
+                    u32 a0, a1, a2, a3;
+                    const u32 ko = (u32)(32 * ks) ^ c0;
+                    const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(a0, a1, a2, a3, xs + (u32)ar * GRAM_RB + ko);
+#pragma unroll
+                    for (int nt = 0; nt < 8; nt += 2) {
+                        if (nt < 2 * mt || nt >= nn) continue;
+                        // matrices: (nt, k 0-7), (nt + 1, k 0-7), (nt, k 8-15), (nt + 1, k 8-15)
+                        u32 b0, b1, b2, b3;
+                        const int br = 8 * nt + (lane & 7) + 8 * ((lane >> 3) & 1);
+                        ldsm_x4(b0, b1, b2, b3, xs + (u32)br * GRAM_RB + ko);
+                        mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b2);
+                        mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b1, b3);
+                    }
+                }
+                if constexpr (MB) {
+                    // this block's products join the earlier blocks' sums
+#pragma unroll
+                    for (int nt = 0; nt < 8; nt++) {
+                        if (nt < 2 * mt || nt >= nn) continue;
+                        float4 *pp = part + (size_t)(slot + nt) * 32 + lane;
+                        if (kb > 0) {
+                            const float4 v = *pp;
+                            acc[nt][0] = __fadd_rn(v.x, acc[nt][0]);
+                            acc[nt][1] = __fadd_rn(v.y, acc[nt][1]);
+                            acc[nt][2] = __fadd_rn(v.z, acc[nt][2]);
+                            acc[nt][3] = __fadd_rn(v.w, acc[nt][3]);
+                        }
+                        if (!last) *pp = make_float4(acc[nt][0], acc[nt][1], acc[nt][2], acc[nt][3]);
+                    }
+                    if (!last) continue;
+                }
+                __syncwarp();
+                // this stripe's table rows, over this stripe's staged rows (rows r and
+                // r + 8 share the column swizzle)
+#pragma unroll
+                for (int nt = 0; nt < 8; nt++) {
+                    if (nt < 2 * mt || nt >= nn) continue;
+                    const int r = 16 * mt + (lane >> 2), c = (8 * nt + 2 * (lane & 3)) ^ gram_tsw(r);
+                    *reinterpret_cast<float2 *>(T + r * GRAM_N + c) = make_float2(acc[nt][0], acc[nt][1]);
+                    *reinterpret_cast<float2 *>(T + (r + 8) * GRAM_N + c) = make_float2(acc[nt][2], acc[nt][3]);
+                }
+                __syncwarp();
+            }
+        }
+        for (int i = lane; i < n; i += 32) nr2[i] = make_float2(T[i * GRAM_N + (i ^ gram_tsw(i))], key_rho(ck[i]));
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) nr2[i] = make_float2(T[i * GRAM_N + (i ^ gram_tsw(i))], key_rho(ck[i]));
-    __syncwarp();
 }
 
 // RobustPrune on a Gram table: same rule and order as warp_prune.  First the
@@ -265,13 +354,14 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
 // greedy pass is a warp-uniform walk over a 64-bit alive mask (take the first
 // alive candidate, clear the ones it drops), and the kept candidates are
 // written out afterwards, a lane per candidate.
+template <bool MB>
 __device__ int warp_prune_gram(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *out_id,
                                float *out_rho, Stage &st) {
     (void)alive;
     const int lane = lane_id();
     float *T;
     float2 *nr2;
-    warp_gram(d, ck, n, st.gram, st.gram_rows, st, T, nr2);
+    warp_gram<MB>(d, ck, n, st.gram, st.gram_rows, st, T, nr2);
     const float alpha2 = d.alpha2;
     const bool l2 = d.metric == 0;
     // (n_h - g) + (n_j - g): every intermediate stays as small as the result
@@ -459,13 +549,16 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
 // distances, 8 lanes per distance, rows taken from the stage when staged.
 // Scratch: alive[n], idx[n].
 // ---------------------------------------------------------------------------
-// LG: the kernel's Gram buffer holds more than GRAM_N rows (the large path).
-template <bool LG>
+// GV, the Gram variant of a kernel: 0, a buffer of at most GRAM_N rows with
+// rows of one 128-column block; 1, more than GRAM_N rows (the large path,
+// which restages each block per stripe); 2, at most GRAM_N rows spanning
+// several blocks (partial sums kept between blocks).
+template <int GV>
 __device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *alive, u32 *idx, u32 *out_id,
                           float *out_rho, Stage &st) {
     if (st.gram && n <= st.gram_rows) {
-        if constexpr (LG) return warp_prune_masks<GRAM_NL / 8>(d, ck, n, out_id, out_rho, st);
-        else return warp_prune_gram(d, ck, n, alive, out_id, out_rho, st);
+        if constexpr (GV == 1) return warp_prune_masks<GRAM_NL / 8>(d, ck, n, out_id, out_rho, st);
+        else return warp_prune_gram<GV == 2>(d, ck, n, alive, out_id, out_rho, st);
     }
     const int lane = lane_id();
     const int grp = lane >> 3, g = lane & 7;
@@ -553,7 +646,7 @@ __device__ __forceinline__ bool warp_contains(const u32 *ids, int n, u32 v) {
 // a present id is a no-op; below R the entry is inserted in (rho, id) order;
 // at R the list is RobustPrune(list + v) about the owner (tombstones drop).
 // Scratch: keys[np], alive[np], idx[np] with np >= R + 1 (power of two).
-template <bool LG>
+template <int GV>
 __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, float vr, u64 *keys,
                            unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho, Stage &st) {
     const int lane = lane_id();
@@ -596,7 +689,7 @@ __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, flo
     if (lane == 0) keys[below] = kv;
     __syncwarp();
     const int cn = nl + 1;
-    int nout = warp_prune<LG>(d, keys, cn, alive, idx, oid, orho, st);
+    int nout = warp_prune<GV>(d, keys, cn, alive, idx, oid, orho, st);
     for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
     __syncwarp();
     return nout;
@@ -623,20 +716,20 @@ __host__ __device__ inline size_t prune_ins_scratch(u32 np, u32 R) {
 }
 __host__ __device__ inline size_t prune_ins_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
     const size_t sc = prune_ins_scratch(np, R);
-    return stage_bytes(ns, mp) + al16((size_t)np * 8) + (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram);
+    return stage_bytes(ns, mp) + al16((size_t)np * 8) + (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram, mp);
 }
 
 // one-warp blocks (the launch uses 32 threads); the small-path instantiation
 // is held to 12 resident warps per SM (at most 170 registers a thread)
-template <bool LG>
-__global__ void __launch_bounds__(32, LG ? 1 : 12) prune_insert_kernel(PruneInsArgs a) {
+template <int GV>
+__global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(PruneInsArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
     char *p = smem + warp * prune_ins_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    p += gram_bytes(a.gram);
+    p += gram_bytes(a.gram, d.mp);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     WarpSlabs ws;
     ws_init(ws);
@@ -658,7 +751,7 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) prune_insert_kernel(PruneInsA
         __syncwarp();
         warp_sort_u64(keys, (int)a.np);
         const int n = (int)min(cnt, a.max_cand);
-        const int nout = warp_prune<LG>(d, keys, n, alive, idx, oid, orho, st);
+        const int nout = warp_prune<GV>(d, keys, n, alive, idx, oid, orho, st);
         const u32 v = a.first + t;
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
@@ -697,20 +790,22 @@ cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_k
     const size_t wb = prune_ins_warp_bytes(np, d.R, a.ns, d.mp, gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)prune_insert_kernel<true> : (const void *)prune_insert_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *fns[3] = {(const void *)prune_insert_kernel<0>, (const void *)prune_insert_kernel<1>, (const void *)prune_insert_kernel<2>};
+    const void *fn = fns[gram_variant(a.gram, d.mp)];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, a.gram > (u32)GRAM_N ? (const void *)prune_insert_kernel<true> : (const void *)prune_insert_kernel<false>, 32 * W, smem);
+        &per_sm, fn, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms), need = (b + W - 1) / W;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    if (a.gram > (u32)GRAM_N) prune_insert_kernel<true><<<blocks, 32 * W, smem, st>>>(a);
-    else prune_insert_kernel<false><<<blocks, 32 * W, smem, st>>>(a);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(blocks), dim3(32 * W), args, smem, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -736,20 +831,20 @@ __host__ __device__ inline size_t fold_scratch(u32 np, u32 R) {
 __host__ __device__ inline size_t fold_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
     const size_t sc = fold_scratch(np, R);
     return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4 + 4) + al16((size_t)(R + 1) * 8) +
-           (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram);
+           (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram, mp);
 }
 
 // one-warp blocks (the launch uses 32 threads); the small-path instantiation
 // is held to 12 resident warps per SM (at most 170 registers a thread)
-template <bool LG>
-__global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a) {
+template <int GV>
+__global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
     char *p = smem + warp * fold_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    p += gram_bytes(a.gram);
+    p += gram_bytes(a.gram, d.mp);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     WarpSlabs ws;
     ws_init(ws);
@@ -785,7 +880,7 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a)
             int n = n0;
             for (u32 q = lo; q < hi; q++) {
                 const u32 pi = a.of.val[q];
-                n = apply_offer<LG>(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
+                n = apply_offer<GV>(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
                                 tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
@@ -802,7 +897,7 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) offer_fold_kernel(FoldArgs a)
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
-                const int n = apply_offer<LG>(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
+                const int n = apply_offer<GV>(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
                 if (att == 0) {                      // the next offer's words, in flight while this one publishes
                     pf_t = __shfl_sync(FULL, t_next, 0);
                     if (pf_t < nwork) { pf_w = a.of.key[pf_t + a.lo]; pf_v = a.of.src[pf_t + a.lo]; pf_vr = a.of.rho[pf_t + a.lo]; }
@@ -834,12 +929,13 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     const size_t wb = fold_warp_bytes(np, d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)offer_fold_kernel<true> : (const void *)offer_fold_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *fns[3] = {(const void *)offer_fold_kernel<0>, (const void *)offer_fold_kernel<1>, (const void *)offer_fold_kernel<2>};
+    const void *fn = fns[gram_variant(a.gram, d.mp)];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, a.gram > (u32)GRAM_N ? (const void *)offer_fold_kernel<true> : (const void *)offer_fold_kernel<false>, 32 * W, smem);
+        &per_sm, fn, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const u32 items = budget ? a.hi - a.lo : of.n;
@@ -847,8 +943,9 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    if (a.gram > (u32)GRAM_N) offer_fold_kernel<true><<<blocks, 32 * W, smem, st>>>(a);
-    else offer_fold_kernel<false><<<blocks, 32 * W, smem, st>>>(a);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(blocks), dim3(32 * W), args, smem, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -873,18 +970,18 @@ __host__ __device__ inline size_t refine_list_bytes(u32 np, u32 cap) {
 }
 
 __host__ __device__ inline size_t refine_warp_bytes(u32 np, u32 cap, u32 R, u32 ns, u32 mp, u32 gram) {
-    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + refine_list_bytes(np, cap) + gram_bytes(gram);
+    return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4) + refine_list_bytes(np, cap) + gram_bytes(gram, mp);
 }
 
-template <bool LG>
-__global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
+template <int GV>
+__global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
     char *p = smem + warp * refine_warp_bytes(a.np_s, a.cap_s, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    p += gram_bytes(a.gram);
+    p += gram_bytes(a.gram, d.mp);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     WarpSlabs ws;
     ws_init(ws);
@@ -1000,7 +1097,7 @@ __global__ void __launch_bounds__(64, LG ? 1 : 6) refine_kernel(RefineArgs a) {
         __syncwarp();
         warp_sort_u64(buf, np3);
         const int n = min(nc, (int)a.max_cand);
-        const int nout = warp_prune<LG>(d, buf, n, alive, idx, oid, orho, st);
+        const int nout = warp_prune<GV>(d, buf, n, alive, idx, oid, orho, st);
         if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
             if (!warp_publish(d, ws, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         }
@@ -1057,12 +1154,13 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     const size_t wb = refine_warp_bytes(a.np_s, a.cap_s, d.R, a.ns, d.mp, a.gram);
     const int warps = 2 * wb <= 200 * 1024 ? 2 : 1;
     size_t smem = warps * wb;
-    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)refine_kernel<true> : (const void *)refine_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *fns[3] = {(const void *)refine_kernel<0>, (const void *)refine_kernel<1>, (const void *)refine_kernel<2>};
+    const void *fn = fns[gram_variant(a.gram, d.mp)];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, a.gram > (u32)GRAM_N ? (const void *)refine_kernel<true> : (const void *)refine_kernel<false>, 32 * warps, smem);
+        &per_sm, fn, 32 * warps, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms), need = (b + warps - 1) / warps;
@@ -1070,8 +1168,9 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     if ((size_t)blocks * warps * a.spill_warp > spill_bytes) return cudaErrorInvalidValue;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    if (a.gram > (u32)GRAM_N) refine_kernel<true><<<blocks, 32 * warps, smem, st>>>(a);
-    else refine_kernel<false><<<blocks, 32 * warps, smem, st>>>(a);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(blocks), dim3(32 * warps), args, smem, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1125,7 +1224,7 @@ __host__ __device__ inline u32 repk_np(u32 R) {
 __host__ __device__ inline size_t repk_warp_bytes(u32 R, u32 ns, u32 mp, u32 gram) {
     const u32 np = repk_np(R);
     return stage_bytes(ns, mp) + 2 * al16((size_t)R * 4) + al16((size_t)R * R * 4) + al16((size_t)32 * np + 32) +
-           gram_bytes(gram);
+           gram_bytes(gram, mp);
 }
 
 __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
@@ -1135,7 +1234,7 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
     const u32 R = d.R;
     char *p = smem + warp * repk_warp_bytes(R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    p += gram_bytes(a.gram);
+    p += gram_bytes(a.gram, d.mp);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     p += stage_bytes(a.ns, d.mp);
     u32 *bid = reinterpret_cast<u32 *>(p); p += al16((size_t)R * 4);
@@ -1320,10 +1419,10 @@ __host__ __device__ inline size_t repf_scratch(u32 np, u32 R) {
 __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp, u32 gram) {
     const size_t sc = repf_scratch(np, R);
     return stage_bytes(ns, mp) + 4 * al16((size_t)R * 4 + 4) + al16((size_t)np * 8) +
-           (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram);
+           (gram_alias(gram, sc) ? 0 : sc) + gram_bytes(gram, mp);
 }
 
-template <bool LG>
+template <int GV>
 __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
                             u64 *ka, u64 *kb, unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho,
                             Stage &st) {
@@ -1385,7 +1484,7 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     }
     __syncwarp();
     const int cn = na + nb2;
-    const int nout = warp_prune<LG>(d, keys, cn, alive, idx, tid, trho, st);
+    const int nout = warp_prune<GV>(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
     return nout;
@@ -1393,15 +1492,15 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
 
 // one-warp blocks (the launch uses 32 threads); the small-path instantiation
 // is held to 12 resident warps per SM (at most 170 registers a thread)
-template <bool LG>
-__global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFoldArgs a) {
+template <int GV>
+__global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(RepairFoldArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 R = d.R;
     char *p = smem + warp * repf_warp_bytes(a.np, R, a.ns, d.mp, a.gram);
     char *gbuf = a.gram ? p : nullptr;
-    p += gram_bytes(a.gram);
+    p += gram_bytes(a.gram, d.mp);
     Stage st = stage_init(p, a.ns, d.mp, gbuf, a.gram);
     WarpSlabs ws;
     ws_init(ws);
@@ -1438,7 +1537,7 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFold
             int n = n0;
             for (u32 q = lo; q < hi; q++) {
                 const u32 pv = a.pair_val[q];
-                n = repair_apply<LG>(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
+                n = repair_apply<GV>(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
                                  ka, kb, alive, idx, (int)a.np, tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
@@ -1454,7 +1553,7 @@ __global__ void __launch_bounds__(32, LG ? 1 : 12) repair_fold_kernel(RepairFold
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
-                const int n = repair_apply<LG>(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
+                const int n = repair_apply<GV>(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
                                            (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st);
                 if (att == 0) {                      // the next pair's words, in flight while this one publishes
                     pf_t = __shfl_sync(FULL, t_next, 0);
@@ -1488,12 +1587,13 @@ cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key,
     const size_t wb = repf_warp_bytes(np, d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(a.gram > (u32)GRAM_N ? (const void *)repair_fold_kernel<true> : (const void *)repair_fold_kernel<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *fns[3] = {(const void *)repair_fold_kernel<0>, (const void *)repair_fold_kernel<1>, (const void *)repair_fold_kernel<2>};
+    const void *fn = fns[gram_variant(a.gram, d.mp)];
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, a.gram > (u32)GRAM_N ? (const void *)repair_fold_kernel<true> : (const void *)repair_fold_kernel<false>, 32 * W, smem);
+        &per_sm, fn, 32 * W, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u64 need = (n_pairs + W - 1) / W;
@@ -1501,8 +1601,9 @@ cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key,
     if ((u64)blocks > need) blocks = (u32)need;
     e = cudaMemsetAsync(d.ctr + C_WORK, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    if (a.gram > (u32)GRAM_N) repair_fold_kernel<true><<<blocks, 32 * W, smem, st>>>(a);
-    else repair_fold_kernel<false><<<blocks, 32 * W, smem, st>>>(a);
+    void *args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(blocks), dim3(32 * W), args, smem, st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
