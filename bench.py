@@ -46,6 +46,9 @@ def parse():
                     help="RobustPrune candidates kept; 64 fits the tensor-core Gram tile (library default: 2 * build beam)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default BeamSearch launch shape")
+    ap.add_argument("--exact-steps", type=int, default=2,
+                    help="extra rounds timed with fp32 BeamSearches gathering the BF16 copy, which holds every "
+                         "row of the integer-valued workload exactly (0: skip); reported apart from the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
@@ -550,7 +553,8 @@ def main():
 
     from paper_2607_02543_gb300 import Index, build as B
     B.build()
-    total_rounds = args.warmup + args.steps * (1 if args.no_e2e else 2)
+    main_rounds = args.warmup + args.steps * (1 if args.no_e2e else 2)
+    total_rounds = main_rounds + (1 + args.exact_steps if args.exact_steps > 0 else 0)
     wr = W.dataclasses.replace(w, rounds=total_rounds)
     plan = W.make_plan(wr)
     n_entry = args.n_entry
@@ -693,7 +697,10 @@ def main():
     m, R = w.dim, w.degree
     nexp = np.mean([b["n_expand"] - a["n_expand"] for a, b in search_stats])
     ndist = np.mean([b["n_dist"] - a["n_dist"] for a, b in search_stats])
-    alg_bytes = nexp * 8 * R + ndist * (4 * m + 8) + w.n_queries * (4 * m + 8 * w.k)
+    # a gathered row is the fp32 row, or the bf16 copy while that holds every row exactly
+    exact_copy = bool(idx.stats()["exact_rows"])
+    row_b = 2 * ((m + 7) // 8 * 8) if exact_copy else 4 * m
+    alg_bytes = nexp * 8 * R + ndist * (row_b + 8) + w.n_queries * (4 * m + 8 * w.k)
     peak, peak_kind = load_peaks()
     sq_ms, sq_n = prof["search_query"]
     kernel_ms = sq_ms / max(sq_n, 1)          # one query-mode search_kernel launch per step
@@ -722,6 +729,54 @@ def main():
                "h2d_bytes_per_step": int(w.n_insert * m * 4 + w.n_delete * 4 + w.n_queries * m * 4),
                "d2h_bytes_per_step": int(w.n_insert * 4 + 8 + w.n_queries * w.k * 8),
                "qps": w.n_queries / (e2e_search * 1e-3)}
+    # supplementary: the same rounds with fp32 BeamSearches gathering the bf16
+    # copy while it holds every stored row exactly (bit-identical distances,
+    # half the row bytes); not the headline, which gathers the fp32 rows
+    exact_block = None
+    if args.exact_steps > 0:
+        idx.set_exact_rows(True)
+        if idx.stats()["exact_rows"]:
+            tried_x = idx.autotune_search(d_q, w.k, beam, stream)
+            best_x = min(tried_x, key=lambda t: t[2])
+            round_dev(main_rounds)
+            idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+            torch.cuda.synchronize()
+            idx.set_profiling(True)
+            idx.profile(reset=True)
+            evx = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.exact_steps)]
+            sx = []
+            for i in range(args.exact_steps):
+                evx[i][0].record(stream)
+                round_dev(main_rounds + 1 + i)
+                evx[i][1].record(stream)
+                a = idx.stats()
+                evx[i][2].record(stream)
+                idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+                evx[i][3].record(stream)
+                sx.append((a, idx.stats()))
+            torch.cuda.synchronize()
+            profx = idx.profile(reset=True)
+            idx.set_profiling(False)
+            gx, _ = idx.ground_truth(d_q, w.k, stream)
+            gxn = gx.cpu().numpy().view(np.uint32)
+            gotx = out_ids.cpu().numpy().view(np.uint32)
+            rec_x = float(np.mean([len(set(u.tolist()) & set(v.tolist())) / w.k for u, v in zip(gotx, gxn)]))
+            nexp_x = np.mean([b["n_expand"] - a["n_expand"] for a, b in sx])
+            ndist_x = np.mean([b["n_dist"] - a["n_dist"] for a, b in sx])
+            alg_x = nexp_x * 8 * R + ndist_x * (2 * ((m + 7) // 8 * 8) + 8) + w.n_queries * (4 * m + 8 * w.k)
+            kx_ms = profx["search_query"][0] / max(profx["search_query"][1], 1)
+            ms_x = float(np.mean([e[2].elapsed_time(e[3]) for e in evx]))
+            exact_block = {
+                "ms_per_round": float(np.mean([e[0].elapsed_time(e[1]) for e in evx])), "steps": args.exact_steps,
+                "qps": w.n_queries / (ms_x * 1e-3), "recall_at_10": rec_x,
+                "search_kernel_ms": kx_ms, "insert_search_ms": profx["search_insert"][0] / args.exact_steps,
+                "search_roofline": {"achieved": alg_x / (kx_ms * 1e-3) / 1e9, "unit": "GB/s",
+                                    "frac": alg_x / (kx_ms * 1e-3) / 1e9 / load_peaks()[0],
+                                    "alg_bytes_per_launch": alg_x},
+                "stage_rows": best_x[0], "seen_bits": best_x[1],
+                "note": "rows gathered from the bf16 copy, which holds every stored row exactly; distances "
+                        "bit-identical to the fp32 rows (tests/test_gpu_exact_rows.py)"}
+        idx.set_exact_rows(False)
     # max over ranks
     ms_round, ms_search = reduce_max([ms_round, ms_search], world, dev)
     st = idx.stats()
@@ -744,9 +799,10 @@ def main():
                "roofline": {"bound": "hbm", "kernel": "search_kernel (query mode)", "achieved": achieved,
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": search_traffic(w.name),
                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                            "rows_gathered": "bf16 copy (exact for every stored row)" if exact_copy else "fp32",
                             "kernel_ms": kernel_ms},
                "phase_ms_per_step": phases, "ground_truth": gt_block, "search_tuning": tuning,
-               "precision": prec_block,
+               "precision": prec_block, "exact_bf16_rows": exact_block,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)

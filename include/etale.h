@@ -90,6 +90,14 @@ typedef struct {
                              certified rerank, same seeds as the CUDA-core
                              kernel; not in concurrent mode, captured
                              graphs or reduced precision), 1 CUDA cores only */
+    uint32_t exact_rows;  /* fp32 BeamSearches (inserts and etale_search):
+                             0 default, always gather the fp32 rows; 1 gather
+                             the BF16 copy instead while every stored row
+                             converts to bf16 exactly (checked at ingest; the
+                             distances are then bit-identical to those of the
+                             fp32 rows, at half the bytes).  Needs the BF16
+                             copy; never used in concurrent mode or captured
+                             graphs.  See also etale_set_exact_rows.        */
 } etale_config;
 
 typedef enum { ETALE_PREC_FP32 = 0, ETALE_PREC_BF16 = 1, ETALE_PREC_FP8 = 2 } etale_precision;
@@ -112,6 +120,7 @@ typedef struct {
     uint64_t n_expand;        /* BeamSearch expansions                        */
     uint64_t n_dist;          /* distance evaluations in BeamSearch           */
     uint64_t device_bytes;    /* index memory held on the device              */
+    uint64_t exact_rows;      /* 1 while fp32 searches gather the exact BF16 copy */
 } etale_stats_t;
 
 /* Fill *cfg with the defaults (all fields resolved except those that depend
@@ -211,6 +220,11 @@ typedef struct {
     uint32_t seen_bits;   /* log2 slots of the evaluated-id cache             */
     float ms;             /* measured: seeding + search of the tuning batch   */
 } etale_tuning;
+
+/* Turn the exact-copy gathers of cfg.exact_rows on (1) or off (0) for the
+ * calls that follow (results never depend on it).  Turning them on reads
+ * the device's count of inexact rows (synchronises the default stream).   */
+etale_status etale_set_exact_rows(etale_index *idx, int on);
 
 /* Set the query-search launch shape (results never depend on it).          */
 etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits);

@@ -33,7 +33,7 @@ class Config(C.Structure):
                 ("pool_slabs", C.c_uint64), ("n_entry", C.c_uint32), ("mode", C.c_uint32),
                 ("cas_budget", C.c_uint32), ("stage_kb", C.c_uint32), ("gram", C.c_uint32),
                 ("copies", C.c_uint32), ("rerank", C.c_uint32), ("gt", C.c_uint32),
-                ("seed", C.c_uint32)]
+                ("seed", C.c_uint32), ("exact_rows", C.c_uint32)]
 
 
 class Tuning(C.Structure):
@@ -46,7 +46,7 @@ class Stats(C.Structure):
                 ("free_slabs", C.c_uint64), ("retired_slabs", C.c_uint64), ("used_slabs", C.c_uint64),
                 ("n_entries", C.c_uint32), ("degree", C.c_uint32), ("n_publish", C.c_uint64),
                 ("n_cas_retry", C.c_uint64), ("n_dropped", C.c_uint64), ("n_expand", C.c_uint64),
-                ("n_dist", C.c_uint64), ("device_bytes", C.c_uint64)]
+                ("n_dist", C.c_uint64), ("device_bytes", C.c_uint64), ("exact_rows", C.c_uint64)]
 
 
 EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_insert", "etale_delete",
@@ -56,7 +56,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent",
            "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
-           "etale_selftest_bounded_wait", "etale_ground_truth_info"]
+           "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
             "etale_set_concurrent": ([P, C.c_int], C.c_int),
             "etale_set_search_tuning": ([P, U32, U32], C.c_int),
+            "etale_set_exact_rows": ([P, C.c_int], C.c_int),
             "etale_autotune_search": ([P, P, U64, U32, U32, P, U32, C.POINTER(U32), P], C.c_int),
             "etale_search_graph_create": ([P, U32, U32, U32, P, P, P, P, C.POINTER(P)], C.c_int),
             "etale_search_graph_launch": ([P, P], C.c_int),
@@ -143,7 +144,7 @@ class Index:
                  alpha: float = 0.0, max_hops: int = 0, max_cand: int = 0, refine: str = "default",
                  max_batch: int = 0, pool_slabs: int = 0, n_entry: int = 0, mode: str = "deterministic",
                  cas_budget: int = 0, stage_kb: int = 0, gram: str = "default", copies: tuple = (),
-                 rerank: int = 0, gt: str = "default", seed: str = "default"):
+                 rerank: int = 0, gt: str = "default", seed: str = "default", exact_rows: str = "off"):
         self.lib = load()
         cfg = Config()
         self.lib.etale_config_default(C.byref(cfg))
@@ -163,6 +164,7 @@ class Index:
         cfg.gram = {"default": 0, "canonical": 1, "tensor": 2}[gram]
         cfg.gt = {"default": 0, "cuda_cores": 1}[gt]
         cfg.seed = {"default": 0, "cuda_cores": 1}[seed]
+        cfg.exact_rows = {"off": 0, "on": 1}[exact_rows]
         cfg.copies = (1 if "bf16" in copies else 0) | (2 if "fp8" in copies else 0)
         if rerank:
             cfg.rerank = rerank
@@ -223,6 +225,10 @@ class Index:
         self._check(self.lib.etale_search(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
                                           _ptr(dist), _stream(stream)))
         return ids, dist
+
+    def set_exact_rows(self, on: bool = True):
+        """Gather the exact BF16 copy in fp32 BeamSearches (see etale_set_exact_rows)."""
+        self._check(self.lib.etale_set_exact_rows(self.h, int(on)))
 
     def set_search_tuning(self, stage_rows: int, seen_bits: int):
         self._check(self.lib.etale_set_search_tuning(self.h, stage_rows, seen_bits))

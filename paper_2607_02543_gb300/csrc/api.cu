@@ -83,6 +83,7 @@ struct etale_index {
     float *x8s = nullptr;
     u32 mb = 0, m8 = 0;
     u32 search_prec = 0;
+    bool rows_exact = true;         // every ingested row's bf16 copy is exact (C_INEXACT == 0)
     u32 *nent_dev = nullptr;        // |E| in device memory
     u64 *host_ctr = nullptr;   // pinned mirror
     // scratch
@@ -428,6 +429,13 @@ etale_status size_batch_scratch(etale_index *idx, u64 b) {
     return ok ? ETALE_OK : idx->fail(ETALE_ENOMEM, "scratch allocation (insert batch of %llu)", (unsigned long long)b);
 }
 
+// fp32 BeamSearches may gather the bf16 copy: it holds every stored row
+// exactly, so the distances are those of the fp32 rows.  Not in concurrent
+// mode, where a row ingested during a search could be inexact.
+bool exact_rows(const etale_index *idx) {
+    return idx->cfg.exact_rows == 1 && idx->rows_exact && idx->xb && !idx->concurrent;
+}
+
 // The BeamSearch launch shape with its row stage shrunk until a block's shared
 // memory fits the device (long rows); results do not depend on the stage.
 SearchTuning fit_tuning(const etale_index *idx, u32 L, SearchTuning t) {
@@ -475,7 +483,7 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
         PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
         CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr,
                          as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, L, idx->tune),
-                         idx->num_sms, st),
+                         idx->num_sms, st, 0, 4, nullptr, exact_rows(idx)),
            "insert search");
     }
     g_kernel_launches += 1;
@@ -585,9 +593,10 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         if (cfg_in->rerank) cfg.rerank = cfg_in->rerank;
         cfg.gt = cfg_in->gt;
         cfg.seed = cfg_in->seed;
+        cfg.exact_rows = cfg_in->exact_rows;
     }
-    if (cfg.gt > 1 || cfg.seed > 1) {
-        t_last_error = "gt and seed must be 0 or 1";
+    if (cfg.gt > 1 || cfg.seed > 1 || cfg.exact_rows > 1) {
+        t_last_error = "gt, seed and exact_rows must be 0 or 1";
         return ETALE_EINVAL;
     }
     if (cfg.copies > 3) {
@@ -738,6 +747,12 @@ etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n, uint3
     CK(launch_ingest(idx->x + first_all * idx->mp, idx->mp, (const float *)src, idx->dim, n, st), "ingest");
     CK(launch_ingest_copies(idx->dev(), first_all, n, st), "ingest copies");
     g_kernel_launches += 2;
+    if (idx->rows_exact && idx->xb && idx->cfg.exact_rows == 1) {
+        // the batch's searches below gather the bf16 copy only if it is still exact
+        s = read_ctr(idx, st);
+        if (s != ETALE_OK) return s;
+        idx->rows_exact = idx->host_ctr[C_INEXACT] == 0;
+    }
     u64 done = 0;
     const u64 maxb = idx->cfg.max_batch;
     s = size_batch_scratch(idx, std::min<u64>(n, maxb));
@@ -1014,7 +1029,8 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
         if (s != ETALE_OK) return s;
         if (prof) prof_begin(idx, ETALE_PH_SEARCH_QUERY, st);
         CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->s_seed), fit_tuning(idx, L, idx->tune),
-                         idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
+                         idx->num_sms, st, idx->search_prec, idx->cfg.rerank, nullptr,
+                         idx->search_prec == 0 && exact_rows(idx)),
            "search");
         if (prof) prof_end(idx, st);
         g_kernel_launches++;
@@ -1100,6 +1116,7 @@ etale_status etale_stats(etale_index *idx, etale_stats_t *o) {
     o->n_expand = c[C_EXPAND];
     o->n_dist = c[C_DIST];
     o->device_bytes = idx->device_bytes;
+    o->exact_rows = exact_rows(idx) ? 1 : 0;
     return ETALE_OK;
 }
 
@@ -1110,6 +1127,18 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out) {
 }
 
 const char *etale_last_error(const etale_index *) { return t_last_error.c_str(); }
+
+etale_status etale_set_exact_rows(etale_index *idx, int on) {
+    if (!idx) return ETALE_EINVAL;
+    if (on && idx->rows_exact && idx->xb) {
+        // rows ingested while the gathers were off were counted on the device
+        u64 inexact = 0;
+        CK(cudaMemcpy(&inexact, idx->ctr + C_INEXACT, sizeof inexact, cudaMemcpyDeviceToHost), "read counter");
+        idx->rows_exact = inexact == 0;
+    }
+    idx->cfg.exact_rows = on ? 1u : 0u;
+    return ETALE_OK;
+}
 
 etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits) {
     if (!idx) return ETALE_EINVAL;
@@ -1157,7 +1186,7 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
                 ok = launch_seed(d, qpad, (u32)nq, L, as<u64>(idx->s_seed), st, idx->search_prec) == cudaSuccess &&
                      launch_search(d, qpad, (u32)nq, L, H, 0, k, as<u32>(idx->s_out_ids), as<float>(idx->s_out_dist),
                                    nullptr, nullptr, as<u64>(idx->s_seed), t, idx->num_sms, st, idx->search_prec,
-                                   idx->cfg.rerank) == cudaSuccess;
+                                   idx->cfg.rerank, nullptr, idx->search_prec == 0 && exact_rows(idx)) == cudaSuccess;
                 cudaEventRecord(e1, st);
                 if (cudaStreamSynchronize(st) != cudaSuccess) ok = false;
                 float ms = 0.f;

@@ -44,6 +44,7 @@ enum : int {
     C_COUNT_B = 12,
     C_ERR_S = 13,      // error bits of query searches (kept apart from writers')
     C_RECYCLED = 14,   // blocks of the recycle launch that have finished copying
+    C_INEXACT = 15,    // ingested rows whose bf16 copy differs from the fp32 row
     C_NCTR = 16
 };
 

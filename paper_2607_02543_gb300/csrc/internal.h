@@ -20,10 +20,12 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
                         const u32 *nq_dev = nullptr, const u32 *qsel = nullptr);
 // prec: 0 fp32, 1 bf16 copy, 2 fp8 copy (query mode only; the best
 // min(rerank * k, 64) live candidates are re-scored in canonical fp32).
+// exact_rows: fp32 semantics with rows gathered from the bf16 copy, which
+// holds every stored row exactly (prec 1, no rerank, any mode).
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec = 0,
-                          u32 rerank = 4, const u32 *nq_dev = nullptr);
+                          u32 rerank = 4, const u32 *nq_dev = nullptr, bool exact_rows = false);
 
 // Offer lists: a payload index p names (src[p], rho[p]); key[p] is the target
 // id or `invalid` (= capacity) for an empty slot.

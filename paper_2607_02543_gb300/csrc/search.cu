@@ -38,6 +38,7 @@ struct SearchArgs {
     u32 wq, err;         // work-queue counter and error word (query searches
                          // use their own, so they can overlap a writer)
     u32 rerank;          // reduced precision: re-scored candidates (<= 64)
+    u32 exact;           // P = 1 over a bf16 copy that holds every row exactly: no rerank
 };
 
 // Row gathered for a neighbour: the fp32 row or its reduced-precision copy.
@@ -304,10 +305,19 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
             const int c = r0 + grp;
             const int cc = c < nb ? c : nb - 1;   // idle groups recompute a valid row
             float dist;
-            if (P == 0 && mp <= 128)
+            if (P == 0 && mp <= 128) {
                 dist = canon_dist_q8(qr, reinterpret_cast<const float *>(stage + (size_t)cc * rowb), (int)mp,
                                      (int)d.metric, g);
-            else
+            } else if (P == 1 && mp <= 128) {
+                // the bf16 row widened to fp32, then canon_dist's operations in its order
+                float4 v[4];
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const int i = 4 * (g + 8 * t);
+                    v[t] = i < (int)mp ? load4<1>(stage + (size_t)cc * rowb, i, 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                dist = canon_dist_q8v(qr, v, (int)mp, (int)d.metric, g);
+            } else
                 dist = qdist<P>(s.qv, stage + (size_t)cc * rowb, P == 2 ? scl[cc] : 1.0f, (int)mp, (int)d.metric, g);
             if (c < nb && g == 0) s.ckey[b0 + c] = mkkey(dist, s.cid[b0 + c]);
         }
@@ -531,7 +541,7 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
             }
         }
         nexp_tot += hops;
-        if (a.mode == 0 && P != 0) {
+        if (a.mode == 0 && P != 0 && !a.exact) {
             // exact fp32 rerank of the best min(rerank * k, 64) live candidates
             u64 *rk = reinterpret_cast<u64 *>(s.stage);
             const int want = (int)min(a.rerank * a.k, 64u);
@@ -629,9 +639,10 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec, u32 rerank,
-                          const u32 *nq_dev) {
+                          const u32 *nq_dev, bool exact_rows) {
     if (nq == 0) return cudaSuccess;
-    if (mode != 0) prec = 0;
+    if (exact_rows) prec = 1;
+    else if (mode != 0) prec = 0;
     if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
     SearchArgs a;
     a.d = d; a.q = q; a.seed = seed; a.nq_dev = nq_dev; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode;
@@ -642,6 +653,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.seen_slots = 1u << tune.seen_bits;
     a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
     a.rerank = rerank;
+    a.exact = exact_rows ? 1u : 0u;
     a.wq = mode == 0 ? C_WORK2 : C_WORK;
     a.err = mode == 0 ? C_ERR_S : C_ERR;
     // the rerank buffer (64 keys) lives in the stage

@@ -283,7 +283,15 @@ __global__ void ingest_copies_kernel(Dev d, u64 first, u64 n) {
     const float *xr = d.x + row * d.mp;
     if (d.xb) {
         __nv_bfloat16 *br = reinterpret_cast<__nv_bfloat16 *>(d.xb + row * d.mb);
-        for (u32 i = lane; i < d.mb; i += 32) br[i] = __float2bfloat16_rn(i < d.mp ? xr[i] : 0.0f);
+        bool inexact = false;
+        for (u32 i = lane; i < d.mb; i += 32) {
+            const float v = i < d.mp ? xr[i] : 0.0f;
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            br[i] = b;
+            inexact |= !(__bfloat162float(b) == v);   // NaN counts as inexact
+        }
+        // a row whose copy is not exact keeps fp32 searches on the fp32 rows
+        if (__any_sync(FULL, inexact) && lane == 0) atomicAdd(&d.ctr[C_INEXACT], 1ull);
     }
     if (d.x8) {
         float amax = 0.0f;
