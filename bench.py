@@ -78,7 +78,7 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
 # DRAM bytes of one query-mode BeamSearch launch on the 1M x 128 workload, from
 # the ncu capture in profiles/search_kernel_int256-1m-d128_dram.md; valid only
 # for the search.cu revision it was taken on (first 16 hex digits of SHA-256).
-SEARCH_DRAM_BYTES = {"int256-1m-d128": (10_487_631_616 + 1_352_192, "05c5e56e501c5f7d")}
+SEARCH_DRAM_BYTES = {"int256-1m-d128": (10_486_715_904 + 1_275_904, "b7a690c3dfe366f4")}
 
 
 def search_traffic(workload_name: str):
