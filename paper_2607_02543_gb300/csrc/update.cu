@@ -38,13 +38,18 @@ struct Stage {
 // GRAM_N floats, also 256 bytes) reuses the same bytes.
 constexpr int GRAM_N = 64;
 constexpr int GRAM_RB = 256;   // bytes per staged row (128 bf16 columns)
+// The large path (more than GRAM_N rows) keeps rows of GRAM_RS_LG bf16 (a
+// 16-byte pad: conflict-free ldmatrix without a swizzle), so that a whole
+// row block lands with one bulk copy per row.
+constexpr int GRAM_RS_LG = 136;
+__host__ __device__ inline size_t gram_rowb(u32 rows) { return rows > (u32)GRAM_N ? (size_t)GRAM_RS_LG * 2 : GRAM_RB; }
 __host__ __device__ inline u32 gram_xoff(int r, int chunk) { return (u32)(r * GRAM_RB + ((chunk ^ (r & 7)) << 4)); }
 // Byte offset, in a Gram buffer for `rows` candidates, of the partial sums
 // that rows longer than one 128-column block keep between blocks: after the
 // bf16 rows (or the table over them), a (norm, rho) pair per candidate and
 // the large path's domination masks.  rows is a multiple of 16.
 __host__ __device__ inline size_t gram_part_off(u32 rows) {
-    const size_t b = (size_t)rows * GRAM_RB + (size_t)rows * 8;
+    const size_t b = (size_t)rows * gram_rowb(rows) + (size_t)rows * 8;
     return rows > (u32)GRAM_N ? b + (size_t)rows * 16 : b;
 }
 // Shared-memory bytes of a Gram buffer for `rows` candidates of mp columns;
@@ -436,12 +441,13 @@ template <int NT>   // tiles of 8 columns: 8 (n <= 64) or 16 (n <= 128)
 __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id, float *out_rho, Stage &st) {
     const int lane = lane_id();
     const int rows = st.gram_rows;
-    char *tail = st.gram + (size_t)rows * GRAM_RB;
+    __nv_bfloat16 *X = reinterpret_cast<__nv_bfloat16 *>(st.gram);
+    char *tail = st.gram + (size_t)rows * GRAM_RS_LG * 2;
     float2 *nr2 = reinterpret_cast<float2 *>(tail);   // .x: the norms (.y unused here)
     u64 *dom = reinterpret_cast<u64 *>(tail + (size_t)rows * 8);
     const int nm = (n + 15) >> 4, nn = (n + 7) >> 3;
     const int nkb = ((int)d.mp + 127) >> 7;
-    const u32 xs = smem_addr(st.gram), c0 = gram_c0(lane);
+    const u32 xs = smem_addr(X);
     for (int mt = nm - 1; mt >= 0; mt--) {
         float acc[NT][4];
 #pragma unroll
@@ -449,24 +455,59 @@ __device__ int warp_prune_masks(const Dev &d, const u64 *ck, int n, u32 *out_id,
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[b][c] = 0.f;
         for (int kb = 0; kb < nkb; kb++) {
-            // rows [r_lo, n) of columns [128 kb, 128 kb + 128): all rows once
-            // when one block covers the row, else those of this stripe on
-            if (nkb > 1 || mt == nm - 1) gram_stage_rows(d, ck, nkb > 1 ? 16 * mt : 0, n, kb, xs);
+            if (nkb > 1 || mt == nm - 1) {
+                // rows [r_lo, n) of columns [128 kb, 128 kb + 128): all rows once
+                // when one block covers the row, else those of this stripe on
+                const int r_lo = nkb > 1 ? 16 * mt : 0;
+                __syncwarp();
+                if (d.xb) {
+                    const int cols = min(128, (int)d.mb - 128 * kb);
+                    if (lane == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (cols < 128)
+                        for (int z = lane; z < (n - r_lo) * 64; z += 32) {
+                            const int r = r_lo + (z >> 6), c = (z & 63) * 2;
+                            if (c >= cols) *reinterpret_cast<u32 *>(X + (size_t)r * GRAM_RS_LG + c) = 0u;
+                        }
+                    const int nr = n - r_lo;
+                    if (lane == 0 && nr > 0) mbar_expect_tx(st.bar, (u32)(nr * cols * 2));
+                    __syncwarp();
+                    for (int r = r_lo + lane; r < n; r += 32)
+                        bulk_g2s(X + (size_t)r * GRAM_RS_LG, d.xb + (size_t)key_id(ck[r]) * d.mb + 128 * kb,
+                                 (u32)cols * 2, st.bar);
+                    if (nr > 0) {
+                        if (!mbar_wait(st.bar, st.phase, WAIT_LIMIT)) {
+                            st.timeout = true;
+                            mbar_wait(st.bar, st.phase, WAIT_LIMIT);   // let copies in flight land
+                        }
+                        st.phase ^= 1u;
+                    }
+                } else {
+                    const int col = 128 * kb + 4 * lane;
+                    for (int r = r_lo; r < n; r++) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (col < (int)d.mp)
+                            v = *reinterpret_cast<const float4 *>(d.x + (size_t)key_id(ck[r]) * d.mp + col);
+                        *reinterpret_cast<uint2 *>(X + (size_t)r * GRAM_RS_LG + 4 * lane) =
+                            make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+                    }
+                }
+                __syncwarp();
+            }
 #pragma unroll
             for (int ks = 0; ks < 8; ks++) {
                 u32 a0, a1, a2, a3;
-                const u32 ko = (u32)(32 * ks) ^ c0;
                 const int ar = 16 * mt + (lane & 7) + 8 * ((lane >> 3) & 1);
-                ldsm_x4(a0, a1, a2, a3, xs + (u32)ar * GRAM_RB + ko);
+                const int ac = 16 * ks + 8 * (lane >> 4);
+                ldsm_x4(a0, a1, a2, a3, xs + (u32)((ar * GRAM_RS_LG + ac) * 2));
 #pragma unroll
                 for (int nt = 0; nt < NT; nt += 2) {
                     if (nt < 2 * mt || nt >= nn) continue;
-                    // matrices: (nt, k 0-7), (nt + 1, k 0-7), (nt, k 8-15), (nt + 1, k 8-15)
                     u32 b0, b1, b2, b3;
-                    const int br = 8 * nt + (lane & 7) + 8 * ((lane >> 3) & 1);
-                    ldsm_x4(b0, b1, b2, b3, xs + (u32)br * GRAM_RB + ko);
-                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b2);
-                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b1, b3);
+                    const int br = 8 * nt + (lane & 7) + 8 * (lane >> 4);
+                    const int bc = 16 * ks + 8 * ((lane >> 3) & 1);
+                    ldsm_x4(b0, b1, b2, b3, xs + (u32)((br * GRAM_RS_LG + bc) * 2));
+                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, b0, b1);
+                    mma_bf16_16816(acc[nt + 1], a0, a1, a2, a3, b2, b3);
                 }
             }
         }
