@@ -28,7 +28,7 @@ struct Stage {
     u32 phase;
     bool timeout;
     char *gram;      // gram_bytes(gram_rows, mp) for the tensor-core Gram path (nullptr: canonical path)
-    int gram_rows;   // candidates the Gram buffer holds (a multiple of 16, <= GRAM_N)
+    int gram_rows;   // candidates the Gram buffer holds (a multiple of 16, <= GRAM_NL)
 };
 
 // Tensor-core Gram tile: up to 64 candidates, K staged 128 columns at a time
@@ -65,11 +65,11 @@ __host__ __device__ inline size_t gram_bytes(u32 rows, u32 mp) {
 // tiles nt = 2 mt .. 2 nmr - 1, nmr = rows / 16).
 __device__ __forceinline__ int gram_part_slot(int mt, int nmr) { return mt * (2 * nmr + 1 - mt); }
 constexpr int GRAM_NL = 128;   // candidates of the large (mask) path
+// The Gram variant (see warp_prune) of a kernel whose buffer holds gram_rows rows of mp columns.
+inline int gram_variant(u32 gram_rows, u32 mp) { return gram_rows > (u32)GRAM_N ? 1 : (gram_rows && mp > 128 ? 2 : 0); }
 // Gram rows for a kernel whose prunes see at most max_n candidates (0: the
 // Gram path is off or cannot hold them).  Above GRAM_N rows the kernel runs
 // the large path (warp_prune_masks).
-// The Gram variant (see warp_prune) of a kernel whose buffer holds gram_rows rows of mp columns.
-inline int gram_variant(u32 gram_rows, u32 mp) { return gram_rows > (u32)GRAM_N ? 1 : (gram_rows && mp > 128 ? 2 : 0); }
 inline u32 gram_rows_for(u32 on, u32 max_n) { return on && max_n <= (u32)GRAM_NL ? (max_n + 15) / 16 * 16 : 0; }
 // Scratch that is dead whenever the Gram buffer is live (list compaction before
 // a prune, the canonical prune's arrays, a prune's output, written after its
@@ -217,16 +217,17 @@ __device__ __forceinline__ int gram_tsw(int r) { return (r & 3) << 3; }
 // Writes the upper triangle (j >= i, in 16 x 8 tiles) of the n x n Gram into
 // T (fp32, row stride GRAM_N, columns swizzled by gram_tsw) and the diagonal
 // into nr2[i].x, with rho_i (the candidate's key distance) in nr2[i].y.
-// Column blocks of 128 go outermost: each block of every row is staged once,
-// and with more than one block each stripe adds its products for the block
-// to the buffer's partial sums (fp32; exact for the integer-valued data the
-// tile is exact for).  T and the bf16 rows share `buf`: in the last block the stripes go
-// in ascending order, and stripe mt's table rows (bytes [4096 mt,
-// 4096 (mt + 1))) are the staged rows of that same stripe, which no later
-// stripe reads (it reads rows >= 16 (mt + 1)).  A stripe only needs the
-// columns j >= 16 mt, because the prune reads T[head][j] for j > head.  Rows
-// past n hold whatever the buffer held: an entry (i, j) reads rows i and j
-// only, and no entry with i or j >= n is read.
+// Rows of one 128-column block (MB false) are staged once, then the stripes
+// run in ascending order.  With several blocks (MB true) the blocks go
+// outermost: each block of every row is staged once, and each stripe adds
+// its products for the block to the buffer's partial sums (fp32; exact for
+// the integer-valued data the tile is exact for).  T and the bf16 rows share
+// `buf`: in the (last) block the stripes go in ascending order, and stripe
+// mt's table rows (bytes [4096 mt, 4096 (mt + 1))) are the staged rows of
+// that same stripe, which no later stripe reads (it reads rows >= 16 (mt + 1)).
+// A stripe only needs the columns j >= 16 mt, because the prune reads
+// T[head][j] for j > head.  Rows past n hold whatever the buffer held: an
+// entry (i, j) reads rows i and j only, and no entry with i or j >= n is read.
 template <bool MB>   // rows span more than one 128-column block
 __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float2 *&nr2) {
     if constexpr (!MB) {
