@@ -205,7 +205,8 @@ def run_reference(args, w):
 def config_dict(w, args):
     return {"workload": w.name, "n_live": w.n_base, "dim": w.dim, "metric": w.metric, "degree": w.degree,
             "build_beam": w.build_beam, "churn_per_round": [w.n_delete, w.n_insert],
-            "queries_per_step": w.n_queries, "k": w.k, "search_beam": args.search_beam or w.search_beam,
+            "queries_per_step": w.n_queries, "k": w.k,
+            "search_beam": args.search_beam if args.search_beam_fixed else "smallest of 64..256 with Recall@10 >= 0.95",
             "mode": args.mode, "n_entry": args.n_entry, "max_cand": args.max_cand or 2 * w.build_beam,
             "l2": "working set (index > 600 MB) larger than L2; no flush" if w.n_base >= 1_000_000 else
                   "small index; no flush", "parallelism": f"replicas x{args.gpus}"}
@@ -523,6 +524,7 @@ def run_varbatch(args):
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
+    args.search_beam_fixed = bool(args.search_beam)   # else chosen by the recall sweep (reported apart)
     if args.varbatch:
         return run_varbatch(args)
     if args.serve:
@@ -794,7 +796,8 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic", "config": config_dict(w, args),
-               "recall_at_10": recall, "beam_sweep": sweep, "qps": world * w.n_queries / (ms_search * 1e-3),
+               "recall_at_10": recall, "search_beam": beam, "beam_sweep": sweep,
+               "qps": world * w.n_queries / (ms_search * 1e-3),
                "search_ms_per_10k": ms_search, "build_s": build_s,
                "roofline": {"bound": "hbm", "kernel": "search_kernel (query mode)", "achieved": achieved,
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": search_traffic(w.name),
