@@ -50,13 +50,17 @@ enum : int {
 
 // ---- reference word r(u) = <delta, d, s>: bit 63 delta, bits 48..55 d,
 //      bits 0..31 s (NIL = no slab).  Same packing as the paper's single
-//      64-bit word; the bit positions are this library's choice.
+//      64-bit word; the bit positions are this library's choice.  Bit 56 (P)
+//      is a hint of this library's own: set when the list was written by a
+//      RobustPrune (or is such a list with entries removed), so that no entry
+//      is dropped by an earlier one; a plain insertion clears it.
 __host__ __device__ __forceinline__ u64 ref_pack(u32 del, u32 d, u32 s) {
     return ((u64)(del & 1u) << 63) | ((u64)(d & 0xFFu) << 48) | (u64)s;
 }
 __host__ __device__ __forceinline__ u32 ref_del(u64 r) { return (u32)(r >> 63); }
 __host__ __device__ __forceinline__ u32 ref_deg(u64 r) { return (u32)(r >> 48) & 0xFFu; }
 __host__ __device__ __forceinline__ u32 ref_slab(u64 r) { return (u32)r; }
+__host__ __device__ __forceinline__ u32 ref_pruned(u64 r) { return (u32)(r >> 56) & 1u; }
 
 // ---- (rho, id) total order: fp32 bits mapped to an unsigned order ---------
 __host__ __device__ __forceinline__ u32 fbits(float f) {
@@ -364,8 +368,9 @@ __device__ __forceinline__ void ws_finish(const Dev &d, WarpSlabs &w) {
 // installs <delta of snap, n, fresh slab> only if r(u) still equals snap;
 // returns true on success.  On a lost CAS the fresh slab is retired and false
 // is returned (the caller retries or drops the update).
+// pruned: the new list's P bit (see ref_pruned).
 __device__ __forceinline__ bool warp_publish(const Dev &d, WarpSlabs &ws, u32 u, const u32 *ids,
-                                             const float *rho, int n, u64 snap) {
+                                             const float *rho, int n, u64 snap, bool pruned) {
     const int lane = lane_id();
     const u32 s2 = ws_pop(d, ws);
     if (s2 == NIL) return false;
@@ -375,7 +380,7 @@ __device__ __forceinline__ bool warp_publish(const Dev &d, WarpSlabs &ws, u32 u,
     __syncwarp();
     int ok = 0;
     if (lane == 0) {
-        const u64 nw = ref_pack(ref_del(snap), (u32)n, s2);   // carry the deletion flag
+        const u64 nw = ref_pack(ref_del(snap), (u32)n, s2) | ((u64)(pruned ? 1u : 0u) << 56);   // carry the deletion flag
         ok = atomicCAS(&d.ref[u], snap, nw) == snap;
     }
     ok = __shfl_sync(FULL, ok, 0);

@@ -689,12 +689,15 @@ __device__ __forceinline__ bool warp_contains(const u32 *ids, int n, u32 v) {
 // at R the list is RobustPrune(list + v) about the owner (tombstones drop).
 // Scratch: keys[np], alive[np], idx[np] with np >= R + 1 (power of two).
 template <int GV>
+// pruned: in, whether the list is a RobustPrune output (no entry dropped by
+// an earlier one, see ref_pruned); out, the same for the returned list.
 __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, float vr, u64 *keys,
-                           unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho, Stage &st) {
+                           unsigned char *alive, u32 *idx, int np, u32 *oid, float *orho, Stage &st, bool &pruned) {
     const int lane = lane_id();
     if (warp_contains(ids, n, v)) return n;
     const u64 kv = mkkey(vr, v);
     if (n < (int)d.R) {
+        pruned = false;   // a plain insertion: v is not checked against the entries
         int pos = 0;
         for (int j0 = 0; j0 < n; j0 += 32) {
             int j = j0 + lane;
@@ -728,12 +731,16 @@ __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, flo
         below += __popc(__ballot_sync(FULL, live && k < kv));
         nl += __popc(lm);
     }
+    // A full list of live entries that no earlier entry drops, with v after
+    // all of them: the prune keeps the R entries in order and stops before v.
+    if (pruned && nl == n && below == nl) return n;
     if (lane == 0) keys[below] = kv;
     __syncwarp();
     const int cn = nl + 1;
     int nout = warp_prune<GV>(d, keys, cn, alive, idx, oid, orho, st);
     for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
     __syncwarp();
+    pruned = true;
     return nout;
 }
 
@@ -798,7 +805,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(Prun
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
         snap = __shfl_sync(FULL, snap, 0);
-        if (!warp_publish(d, ws, v, oid, orho, nout, snap) && lane == 0)
+        if (!warp_publish(d, ws, v, oid, orho, nout, snap, true) && lane == 0)
             atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         const u32 invalid = (u32)d.capacity;
         for (u32 j = lane; j < R; j += 32) {
@@ -920,13 +927,15 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
             for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
             __syncwarp();
             int n = n0;
+            bool pruned = ref_pruned(snap) != 0;
             for (u32 q = lo; q < hi; q++) {
                 const u32 pi = a.of.val[q];
                 n = apply_offer<GV>(d, lid, lrho, n, a.of.src[pi], a.of.rho[pi], keys, alive, idx, (int)a.np,
-                                tid, trho, st);
+                                tid, trho, st, pruned);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
-                if (!warp_publish(d, ws, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+                if (!warp_publish(d, ws, w, lid, lrho, n, snap, pruned) && lane == 0)
+                    atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
             u32 w = pf_w, v = pf_v;
@@ -939,13 +948,15 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
-                const int n = apply_offer<GV>(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st);
+                bool pruned = ref_pruned(snap) != 0;
+                const int n = apply_offer<GV>(d, lid, lrho, n0, v, vr, keys, alive, idx, (int)a.np, tid, trho, st,
+                                              pruned);
                 if (att == 0) {                      // the next offer's words, in flight while this one publishes
                     pf_t = __shfl_sync(FULL, t_next, 0);
                     if (pf_t < nwork) { pf_w = a.of.key[pf_t + a.lo]; pf_v = a.of.src[pf_t + a.lo]; pf_vr = a.of.rho[pf_t + a.lo]; }
                 }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
-                done = warp_publish(d, ws, w, lid, lrho, n, snap);
+                done = warp_publish(d, ws, w, lid, lrho, n, snap, pruned);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
                 if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
@@ -1141,7 +1152,7 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         const int n = min(nc, (int)a.max_cand);
         const int nout = warp_prune<GV>(d, buf, n, alive, idx, oid, orho, st);
         if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
-            if (!warp_publish(d, ws, v, oid, orho, nout, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+            if (!warp_publish(d, ws, v, oid, orho, nout, snap, true) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         }
         const u32 invalid = (u32)d.capacity;
         for (u32 j = lane; j < R; j += 32) {
@@ -1583,7 +1594,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
                                  ka, kb, alive, idx, (int)a.np, tid, trho, st);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
-                if (!warp_publish(d, ws, w, lid, lrho, n, snap) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+                if (!warp_publish(d, ws, w, lid, lrho, n, snap, true) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
             u32 w = pf_w, pv = pf_pv;
@@ -1602,7 +1613,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
                     if (pf_t < nwork) { pf_w = a.pair_key[pf_t + a.lo]; pf_pv = a.pair_val[pf_t + a.lo]; }
                 }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
-                done = warp_publish(d, ws, w, lid, lrho, n, snap);
+                done = warp_publish(d, ws, w, lid, lrho, n, snap, true);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
                 if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
@@ -1696,7 +1707,7 @@ __global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const 
         __syncwarp();
         // a lost CAS here means another writer touched the node during the
         // reclaim launch, which the launch discipline forbids
-        if (!warp_publish(d, ws, (u32)(base + t), sid[warp], srho[warp], nk, r) && lane == 0)
+        if (!warp_publish(d, ws, (u32)(base + t), sid[warp], srho[warp], nk, r, ref_pruned(r) != 0) && lane == 0)
             atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         __syncwarp();
     }
