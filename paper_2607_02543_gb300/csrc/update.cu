@@ -1476,9 +1476,11 @@ __host__ __device__ inline size_t repf_warp_bytes(u32 np, u32 R, u32 ns, u32 mp,
 }
 
 template <int GV>
+// pruned: in, whether the list is a RobustPrune output (see ref_pruned);
+// out, the same for the returned list.
 __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, const uint2 *K, int nk, u64 *keys,
                             u64 *ka, u64 *kb, unsigned char *alive, u32 *idx, int np, u32 *tid, float *trho,
-                            Stage &st) {
+                            Stage &st, bool &pruned) {
     const int lane = lane_id();
     // The list (minus u and deleted nodes) and K(u, a) (minus deleted nodes)
     // are each sorted by (rho, id); compact both, then place every key at its
@@ -1506,6 +1508,7 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     }
     __syncwarp();
     int nb2 = 0;                                     // K keys not in the list, compacted in place
+    bool early = false;                              // a kept K key sorts before the list's last key
     for (int j0 = 0; j0 < nb; j0 += 32) {
         const int j = j0 + lane;
         u64 k = 0;
@@ -1524,8 +1527,13 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
         const int jj = nb2 + __popc(m & lanemask_lt());
         if (keep) { kb[jj] = k; keys[jj + lo] = k; }
         nb2 += __popc(m);
+        early |= __ballot_sync(FULL, keep && lo < na) != 0;
     }
     __syncwarp();
+    // The list is full, live, without u, and no entry drops a later one; every
+    // K key left sorts after it: the prune keeps the R entries in order and
+    // stops before the first K key.
+    if (pruned && na == n && n == (int)d.R && !early) return n;
     for (int i = lane; i < na; i += 32) {
         const u64 k = ka[i];
         int lo = 0, hi = nb2;                        // kept K keys < k
@@ -1540,6 +1548,7 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     const int nout = warp_prune<GV>(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
+    pruned = true;
     return nout;
 }
 
@@ -1588,13 +1597,15 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
             for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
             __syncwarp();
             int n = n0;
+            bool pruned = ref_pruned(snap) != 0;
             for (u32 q = lo; q < hi; q++) {
                 const u32 pv = a.pair_val[q];
                 n = repair_apply<GV>(d, lid, lrho, n, a.dt[pv / R], a.pair_K + (size_t)pv * R, (int)a.pair_Kn[pv], keys,
-                                 ka, kb, alive, idx, (int)a.np, tid, trho, st);
+                                 ka, kb, alive, idx, (int)a.np, tid, trho, st, pruned);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
-                if (!warp_publish(d, ws, w, lid, lrho, n, snap, true) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+                if (!warp_publish(d, ws, w, lid, lrho, n, snap, pruned) && lane == 0)
+                    atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
         } else {
             u32 w = pf_w, pv = pf_pv;
@@ -1606,14 +1617,16 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
                 const int n0 = load_list(d, w, lid, lrho, snap);
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
+                bool pruned = ref_pruned(snap) != 0;
                 const int n = repair_apply<GV>(d, lid, lrho, n0, a.dt[pv / R], a.pair_K + (size_t)pv * R,
-                                           (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st);
+                                           (int)a.pair_Kn[pv], keys, ka, kb, alive, idx, (int)a.np, tid, trho, st,
+                                           pruned);
                 if (att == 0) {                      // the next pair's words, in flight while this one publishes
                     pf_t = __shfl_sync(FULL, t_next, 0);
                     if (pf_t < nwork) { pf_w = a.pair_key[pf_t + a.lo]; pf_pv = a.pair_val[pf_t + a.lo]; }
                 }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
-                done = warp_publish(d, ws, w, lid, lrho, n, snap, true);
+                done = warp_publish(d, ws, w, lid, lrho, n, snap, pruned);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
                 if (!done && (__shfl_sync(FULL, err, 0) & ERR_NOMEM)) break;
