@@ -1144,15 +1144,32 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
             if (ok) buf[nc + __popc(m & lanemask_lt())] = mkkey(nrho[j], nid[j]);
             nc += __popc(m);
         }
-        int np3 = 32;
-        while (np3 < nc) np3 <<= 1;
-        for (int i = nc + lane; i < np3; i += 32) buf[i] = KEY_INF;
-        __syncwarp();
-        warp_sort_u64(buf, np3);
-        const int n = min(nc, (int)a.max_cand);
-        const int nout = warp_prune<GV>(d, buf, n, alive, idx, oid, orho, st);
-        if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
-            if (!warp_publish(d, ws, v, oid, orho, nout, snap, true) && lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+        // The re-selection cannot change a pruned list of live entries (see
+        // ref_pruned) when no peer was found, or when the list is full and
+        // every peer sorts after it: the prune keeps the list in order.
+        bool same = false;
+        if (ref_pruned(snap) && nc - nu == dv) {
+            const u64 last = dv ? mkkey(nrho[dv - 1], nid[dv - 1]) : 0ull;
+            bool early = false;
+            for (int i = lane; i < nu; i += 32) early |= buf[i] < last;
+            same = nu == 0 || (dv == (int)R && !__any_sync(FULL, early));
+        }
+        int nout = dv;
+        if (same) {
+            for (int j = lane; j < dv; j += 32) { oid[j] = nid[j]; orho[j] = nrho[j]; }
+            __syncwarp();
+        } else {
+            int np3 = 32;
+            while (np3 < nc) np3 <<= 1;
+            for (int i = nc + lane; i < np3; i += 32) buf[i] = KEY_INF;
+            __syncwarp();
+            warp_sort_u64(buf, np3);
+            const int n = min(nc, (int)a.max_cand);
+            nout = warp_prune<GV>(d, buf, n, alive, idx, oid, orho, st);
+            if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
+                if (!warp_publish(d, ws, v, oid, orho, nout, snap, true) && lane == 0)
+                    atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
+            }
         }
         const u32 invalid = (u32)d.capacity;
         for (u32 j = lane; j < R; j += 32) {
