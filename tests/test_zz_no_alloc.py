@@ -29,7 +29,7 @@ def test_static_search_matches_search_twice():
     batches = [(q_all, 10, 64), (q_all[100:400].contiguous(), 7, 48)]
     expected = [g.search(q, k, beam) for q, k, beam in batches]
     # The first call on a device looks up the fixed array (once per device).
-    # That call, and torch's first comparison kernels, may make the driver
+    # That call, and torch's first comparison kernels, may make the CUDA driver
     # load code and module memory lazily; both happen before measuring.
     ids, dist = g.search_static(*batches[0])
     assert torch.equal(ids, expected[0][0]) and torch.equal(dist, expected[0][1])
