@@ -356,7 +356,7 @@ __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int row
 // drop (alpha^2 * d(i, j) <= rho(j)).  Lane l builds the mask of row l and,
 // when n - 2 - l >= 32, of row n - 2 - l, walking each row's columns upward
 // (lane l reads column row + 1 + k in step k: distinct banks).  The masks go
-// to the last 512 bytes of the Gram buffer (the table is read by then); the
+// to the last 512 bytes of the buffer's row area (the table is read by then); the
 // greedy pass is a warp-uniform walk over a 64-bit alive mask (take the first
 // alive candidate, clear the ones it drops), and the kept candidates are
 // written out afterwards, a lane per candidate.
