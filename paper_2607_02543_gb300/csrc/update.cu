@@ -230,6 +230,9 @@ __device__ __forceinline__ int gram_tsw(int r) { return (r & 3) << 3; }
 // entry (i, j) reads rows i and j only, and no entry with i or j >= n is read.
 template <bool MB>   // rows span more than one 128-column block
 __device__ void warp_gram(const Dev &d, const u64 *ck, int n, char *buf, int rows, Stage &st, float *&T, float2 *&nr2) {
+    // The single-block form keeps its own loop nest: written as the
+    // multi-block one with one block, it costs the 128-d kernels 10 to 20
+    // registers and with them resident warps.
     if constexpr (!MB) {
         (void)st;
         const int lane = lane_id();
