@@ -134,7 +134,9 @@ etale_status etale_config_default(etale_config *cfg);
 etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree,
                           uint64_t capacity, const etale_config *cfg, etale_index **out);
 
-/* Free every device and host resource of the index.  NULL is a no-op.       */
+/* Free every device and host resource of the index (the three maps of
+ * Definition 1 and the two-stack slab pool of Sec. 3.3, plus scratch).  NULL
+ * is a no-op.                                                              */
 etale_status etale_destroy(etale_index *idx);
 
 /* Insert n vectors (row-major n x dim fp32) as fresh nodes (Algorithm 2 with
@@ -205,6 +207,12 @@ etale_status etale_export_graph(etale_index *idx, uint64_t n, uint8_t *deleted,
  * receives its size.                                                       */
 etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n);
 
+/* Counters of the index.  live / tombstones / reclaimed classify the
+ * reference words of Definition 1 (delta and s); used_slabs is the resident
+ * slab count of Sec. 4.4, which equals live right after etale_reclaim
+ * (Proposition 3) and live + tombstones between reclaims; free_slabs and
+ * retired_slabs are the two stacks of Sec. 3.3.  Reads the device counters
+ * on a private stream (never waits for the caller's streams).              */
 etale_status etale_stats(etale_index *idx, etale_stats_t *out);
 
 /* Resolved configuration of an index.                                      */
@@ -214,7 +222,7 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out);
  * (on any index, etale_create included); idx is ignored.  Never NULL.      */
 const char *etale_last_error(const etale_index *idx);
 
-/* ---- launch-shape tuning (Sec. 8(a) a13) --------------------------------- */
+/* ---- launch-shape tuning (deployment support; the paper has none) -------- */
 typedef struct {
     uint32_t stage_rows;  /* neighbour rows gathered per bulk-copy batch      */
     uint32_t seen_bits;   /* log2 slots of the evaluated-id cache             */
@@ -238,7 +246,7 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
                                    uint32_t beam, etale_tuning *out, uint32_t n_out, uint32_t *n_tried,
                                    void *stream);
 
-/* ---- CUDA-graph query batches (Sec. 8(a) a13) ----------------------------- */
+/* ---- CUDA-graph query batches (deployment support; the paper has none) -- */
 typedef struct etale_search_graph etale_search_graph;
 
 /* Capture the query path (row padding, seeding, BeamSearch) into a CUDA
@@ -322,19 +330,20 @@ etale_status etale_get_profile(etale_index *idx, double *ms, uint64_t *count, ui
 /* Query search that allocates nothing (the paper has no counterpart: this is
  * a deployment variant of etale_search).
  *
- * For callers that must not allocate device memory while they run: code
- * inside CUDA stream capture, where cudaMalloc would break the capture, and
- * serving threads with a fixed memory budget or an allocator that may not be
- * entered from their context.  etale_search may grow staging buffers on
- * demand; this variant never calls cudaMalloc, cudaFree or any allocating
- * routine.  Its scratch (padded query rows and the seeded beams) lives in a
- * file-scope device array of ETALE_STATIC_SCRATCH_BYTES that every GPU
- * loading the library holds until the process exits.
+ * For callers that cannot call cudaMalloc while they run: a serving thread
+ * held to a device-memory budget fixed at start-up, or a library hosted
+ * inside another framework whose memory manager owns the device and must not
+ * be bypassed or re-entered from that context.  etale_search may grow
+ * staging buffers on demand; this variant never calls cudaMalloc, cudaFree or
+ * any allocating routine.  Its scratch (padded query rows and the seeded
+ * beams) lives in a file-scope device array of ETALE_STATIC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.
  *
  * queries, out_ids and out_dists must be DEVICE pointers (host buffers would
  * need staging); results equal etale_search's for the same arguments.
  * nq * (4 * round_up(dim, 4) + 8 * max(beam, k)) must not exceed
- * ETALE_STATIC_SCRATCH_BYTES, else ETALE_EINVAL with a message.
+ * ETALE_STATIC_SCRATCH_BYTES, else ETALE_EINVAL with a message; every
+ * argument is checked before anything is launched.
  *
  * The first call on a device looks up the array's device address (set-up
  * once per device, with that device current); make that first call before

@@ -1366,6 +1366,13 @@ etale_status etale_search_static(etale_index *idx, const float *queries, uint64_
         return idx->fail(ETALE_EINVAL, "etale_search_static takes device pointers only");
     const u32 L = beam > k ? beam : k;
     if (L > 256) return idx->fail(ETALE_EINVAL, "beam must be <= 256");
+    if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
+    // Bound nq by a division first, so that the byte count below cannot wrap
+    // (each query needs at least 4 * mp + 8 * L >= 12 bytes).
+    const u64 per_query = 4ull * idx->mp + 8ull * L;
+    if (nq > (u64)ETALE_STATIC_SCRATCH_BYTES / per_query)
+        return idx->fail(ETALE_EINVAL, "etale_search_static: %llu queries need %llu bytes of scratch each, above the %u-byte limit",
+                         (unsigned long long)nq, (unsigned long long)per_query, (unsigned)ETALE_STATIC_SCRATCH_BYTES);
     const size_t qbytes = ((size_t)nq * idx->mp * 4 + 255) / 256 * 256;
     const size_t need = qbytes + (size_t)nq * L * 8;
     if (need > ETALE_STATIC_SCRATCH_BYTES)
@@ -1382,7 +1389,6 @@ etale_status etale_search_static(etale_index *idx, const float *queries, uint64_
     CK(launch_ingest(qpad, idx->mp, queries, idx->dim, nq, st), "query ingest");
     CK(launch_seed(d, qpad, (u32)nq, L, seed, st, idx->search_prec), "query seed");
     const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
-    if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
     CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, seed, fit_tuning(idx, L, idx->tune),
                      idx->num_sms, st, idx->search_prec, idx->cfg.rerank),
        "search");

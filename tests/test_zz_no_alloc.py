@@ -1,18 +1,28 @@
 """etale_search_static: the query search that allocates no device memory.
 
-Some callers cannot allocate while they run: code recording a CUDA graph
-(a cudaMalloc would break the capture) or a serving thread held to a fixed
-device-memory budget.  The variant keeps its scratch in a fixed array inside
-the library instead of growing buffers on demand.  It must return exactly
-what etale_search returns for the same arguments, call after call, and leave
-the device's free memory untouched.
+Some callers cannot call cudaMalloc while they run: a serving thread held to a
+device-memory budget fixed at start-up, or a library hosted inside another
+framework whose memory manager owns the device.  The variant keeps its scratch
+in a fixed array inside the library instead of growing buffers on demand.  It
+must return exactly what etale_search returns for the same arguments, call
+after call, and leave the device's free memory untouched.  Sizes beyond the
+fixed array are refused before anything is launched.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
 from paper_2607_02543_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+
+def _same(g, batches, expected):
+    for (q, k, beam), (ref_ids, ref_d) in zip(batches, expected):
+        ids, dist = g.search_static(q, k, beam)
+        assert np.array_equal(ids.cpu().numpy(), ref_ids.cpu().numpy())
+        assert np.array_equal(dist.cpu().numpy().view(np.uint32), ref_d.cpu().numpy().view(np.uint32))
 
 
 def test_static_search_matches_search_twice():
@@ -46,6 +56,50 @@ def test_static_search_matches_search_twice():
     big = torch.zeros((20000, w.dim), dtype=torch.float32, device=dev)
     with pytest.raises(EtaleError, match="scratch"):
         g.search_static(big, 10, 64)
+    # a query count whose byte total would wrap a 64-bit size is refused by
+    # the argument checks, before any launch reads the (small) buffers
+    lib = g.lib
+    tiny_ids = torch.empty((1, 10), dtype=torch.int32, device=dev)
+    tiny_d = torch.empty((1, 10), dtype=torch.float32, device=dev)
+    st = lib.etale_search_static(g.h, C.c_void_p(q_all.data_ptr()), C.c_uint64(1 << 62), 10, 64,
+                                 C.c_void_p(tiny_ids.data_ptr()), C.c_void_p(tiny_d.data_ptr()), None)
+    assert st == 1   # ETALE_EINVAL
+    assert "scratch" in lib.etale_last_error(g.h).decode()
     # host buffers are refused: they would need staging
     with pytest.raises(EtaleError, match="device pointers"):
         g.search_static(plan.queries[:4], 10, 64)
+    # the results still match after the refusals
+    _same(g, batches, expected)
+
+
+def test_static_search_reduced_precision_and_exact_rows():
+    """The static path seeds on CUDA cores and reads fp32 rows; etale_search
+    may seed on tensor cores and gather the exact BF16 copy.  Both choices are
+    result-preserving, so the two entry points must still agree: under BF16
+    search precision, and with exact-copy gathers on integer-valued data."""
+    import torch
+    from paper_2607_02543_gb300 import Index, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    # BF16 search precision (reduced-precision beam, exact fp32 rerank)
+    w = W.scaled(W.SMALL, 3000, n_queries=400)
+    plan = W.make_plan(w)
+    g = Index(w.dim, w.metric, w.degree, w.capacity, build_beam=32, copies=("bf16",))
+    g.insert(torch.from_numpy(plan.base).to(dev))
+    g.set_search_precision("bf16")
+    q = torch.from_numpy(plan.queries).to(dev)
+    batches = [(q, 10, 64), (q[:64].contiguous(), 5, 32)]
+    expected = [g.search(*b) for b in batches]
+    _same(g, batches, expected)
+    _same(g, batches, expected)
+    # exact-copy gathers on integer-valued data, nq >= 32 (tensor-core seeds)
+    wi = W.scaled(W.SIFT_LIKE_1M, 3000, n_queries=256)
+    pi = W.make_plan(wi)
+    gi = Index(wi.dim, wi.metric, wi.degree, wi.capacity, build_beam=32, copies=("bf16",), exact_rows="on")
+    gi.insert(torch.from_numpy(pi.base).to(dev))
+    assert gi.stats()["exact_rows"] == 1
+    qi = torch.from_numpy(pi.queries).to(dev)
+    batches = [(qi, 10, 64), (qi[:40].contiguous(), 10, 96)]
+    expected = [gi.search(*b) for b in batches]
+    _same(gi, batches, expected)
+    _same(gi, batches, expected)
