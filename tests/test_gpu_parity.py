@@ -18,6 +18,8 @@ from tests.pair import make_pair, graphs_equal, churn_round
 pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "line5_hand.json")
+GOLD_REFINE = os.path.join(os.path.dirname(__file__), "golden", "refine_peers_hand.json")
+GOLD_REPAIR = os.path.join(os.path.dirname(__file__), "golden", "repair_two_deletions_hand.json")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -61,6 +63,60 @@ def test_hand_derived_line(oracle_mod):
     assert rid[0].tolist() == gold["query_result"][0]
     assert rd[0].tolist() == [float(x) for x in gold["query_result"][1]]
 
+
+
+def _gpu_lists(g, expect):
+    de, hs, dg, ids, rho = g.export_graph()
+    for u, (nb, rr) in expect.items():
+        u = int(u)
+        assert hs[u], u
+        assert ids[u, :dg[u]].tolist() == nb, (u, ids[u, :dg[u]].tolist(), nb)
+        assert rho[u, :dg[u]].tolist() == [float(x) for x in rr], (u, rho[u, :dg[u]].tolist(), rr)
+    return de
+
+
+@pytest.mark.parametrize("gram", ["default", "tensor"])
+def test_hand_derived_refine_pass(gram):
+    """Refine pass on one sub-batch of three mutually invisible inserts; the
+    expected lists are the hand derivation in tests/test_oracle_protocol.py."""
+    from paper_2607_02543_gb300 import Index
+    gold = json.load(open(GOLD_REFINE))
+    nb, nt = len(gold["base_x"]), len(gold["batch_x"])
+    X = np.zeros((nb + nt, gold["dim"]), np.float32)
+    X[:, 0] = gold["base_x"] + gold["batch_x"]
+    g = Index(gold["dim"], "l2", gold["degree"], 100, build_beam=gold["build_beam"], alpha=gold["alpha"],
+              refine="peers", max_batch=gold["max_batch"], n_entry=gold["n_entry"], gram=gram)
+    for i in range(nb):
+        assert g.insert(X[i:i + 1]).tolist() == [i]
+    _gpu_lists(g, gold["after_base"])
+    assert g.insert(X[nb:]).tolist() == list(range(nb, nb + nt))
+    _gpu_lists(g, gold["after_batch"])
+
+
+@pytest.mark.parametrize("gram", ["default", "tensor"])
+def test_hand_derived_two_deletions(gram):
+    """Two deletions sharing a live out-neighbour with a full list: the repair
+    folds in ascending deleted id; expected values derived by hand."""
+    from paper_2607_02543_gb300 import Index
+    gold = json.load(open(GOLD_REPAIR))
+    n = len(gold["points_x"])
+    X = np.zeros((n, gold["dim"]), np.float32)
+    X[:, 0] = gold["points_x"]
+    g = Index(gold["dim"], "l2", gold["degree"], 100, build_beam=gold["build_beam"], alpha=gold["alpha"],
+              refine="off", max_batch=gold["max_batch"], n_entry=gold["n_entry"], gram=gram)
+    assert g.insert(X).tolist() == list(range(n))
+    _gpu_lists(g, gold["after_inserts"])
+    assert g.delete(np.array(gold["delete"], np.uint32)) == 2
+    de = _gpu_lists(g, gold["after_delete"])
+    assert de.tolist() == gold["deleted_flags_after_delete"]
+    g.reclaim()
+    s = g.stats()
+    assert s["live"] == gold["after_reclaim_live"] and s["used_slabs"] == gold["after_reclaim_used_slabs"]
+    q = np.zeros((1, gold["dim"]), np.float32)
+    q[0, 0] = gold["query_x"]
+    rid, rd = g.search(q, gold["k"], gold["beam"])
+    assert rid[0].tolist() == gold["query_result"][0]
+    assert rd[0].tolist() == [float(x) for x in gold["query_result"][1]]
 
 CASES = [
     # (dim, metric, degree, kind, n_base, build_beam, gpu options)

@@ -97,6 +97,160 @@ def test_hand_derived_line(oracle_mod):
     assert rd[0].tolist() == [float(x) for x in g["query_result"][1]]
 
 
+# ---------------------------------------------------------------------------
+# Hand derivation 2: the refine pass (Sec. 3.4.1, reading "batch peers found
+# within two hops"), tests/golden/refine_peers_hand.json.
+# R = 3, alpha = 1.5 (alpha^2 = 2.25), E = {smallest live id}, beam 8.
+# Points x: id0 19, id1 2, id2 6 (one per sub-batch), then ids 3, 4, 5 at
+# x = 26, 21, 3 as ONE sub-batch (live = 3, max_batch = 3).
+# Squared distances: d01 289, d02 169, d03 49, d04 4, d05 256, d12 16,
+# d13 576, d14 361, d15 1, d23 400, d24 225, d25 9, d34 25, d35 529, d45 324.
+# p' is dropped by the head p* when 2.25 * d(p*, p') <= d(p, p').
+#
+# id0: empty graph -> N(0) = [].
+# id1: beam [0(289)] -> C = {0} -> F = [0(289)]; offer 0 <- 1: [1(289)].
+# id2: beam [0(169)]; expand 0 -> 1: 16.  C = 1(16), 0(169).  Keep 1;
+#      0: 2.25*289 = 650.25 <= 169? no; keep 0.  F = [1(16), 0(169)].
+#      Offers below R: N(0) = [2(169), 1(289)], N(1) = [2(16), 0(289)].
+# Batch phase 1 (each member searches the 3-node graph; all 3 are expanded):
+#   v3 (26): C = 0(49), 2(400), 1(576).  Keep 0; 2: 2.25*169 = 380.25 <= 400
+#            -> dropped; 1: 650.25 <= 576? no; keep 1.  F3 = [0(49), 1(576)].
+#   v4 (21): C = 0(4), 2(225), 1(361).  Keep 0; 2: 380.25 <= 225? no; 1:
+#            650.25 <= 361? no; keep 2; 1: 2.25*16 = 36 <= 361 -> dropped.
+#            F4 = [0(4), 2(225)].
+#   v5 (3):  C = 1(1), 2(9), 0(256).  Keep 1; 2: 36 <= 9? no; 0: 650.25 <=
+#            256? no; keep 2; 0: 380.25 <= 256? no; keep 0 (R).
+#            F5 = [1(1), 2(9), 0(256)].
+# Phase 3, offers by target in ascending source:
+#   0 <- 3(49): below R -> [3(49), 2(169), 1(289)].
+#   0 <- 4(4): full, prune {4(4), 3(49), 2(169), 1(289)}: keep 4; 3: 2.25*25
+#            = 56.25 <= 49? no; 2: 506.25 <= 169? no; 1: 812.25 <= 289? no;
+#            keep 3; keep 2 (R) -> [4(4), 3(49), 2(169)].
+#   0 <- 5(256): prune {4, 3, 2, 5(256)}: 4, 3, 2 kept as before (5: 2.25*324
+#            = 729 > 256, 2.25*529 > 256), R reached -> unchanged.
+#   1 <- 3(576): below R -> [2(16), 0(289), 3(576)].
+#   1 <- 5(1): prune {5(1), 2(16), 0(289), 3(576)}: keep 5; 2: 2.25*9 =
+#            20.25 <= 16? no; 0: 576 <= 289? no; 3: 1190.25 <= 576? no; keep 2;
+#            0: 380.25 <= 289? no; keep 0 (R) -> [5(1), 2(16), 0(289)].
+#   2 <- 4(225): below R -> [1(16), 0(169), 4(225)].
+#   2 <- 5(9): prune {5(9), 1(16), 0(169), 4(225)}: keep 5; 1: 2.25*1 <= 16
+#            -> dropped; 0: 576 <= 169? no; 4: 729 <= 225? no; keep 0; 4:
+#            2.25*4 = 9 <= 225 -> dropped -> [5(9), 0(169)] (below R).
+# Phase 4, refine on the graph phase 3 left; two-hop ids admitted only if
+# they are batch peers (3, 4, 5):
+#   v3: N(3) = [0(49), 1(576)]; via N(0) peer 4 (25); via N(1) peer 5 (529).
+#       Prune 4(25), 0(49), 5(529), 1(576): keep 4; 0: 2.25*4 = 9 <= 49 ->
+#       dropped; 5: 729 <= 529? no; 1: 812.25 <= 576? no; keep 5; 1: 2.25*1
+#       <= 576 -> dropped.  F'3 = [4(25), 5(529)]: publish; gained 4 and 5.
+#   v4: N(4) = [0(4), 2(225)]; via N(0) peer 3 (25); via N(2) peer 5 (324).
+#       Prune 0(4), 3(25), 2(225), 5(324): keep 0; 3: 110.25 <= 25? no; 2:
+#       380.25 <= 225? no; 5: 576 <= 324? no; keep 3; keep 2 (R).
+#       F'4 = [0(4), 3(25), 2(225)]: publish; gained 3 only.  (2 is kept,
+#       not gained: N(2) = [5, 0] lacks 4 and is below R, so re-offering
+#       every edge of F'4 would wrongly add 4 to N(2).)
+#   v5: N(5) = [1, 2, 0]; via N(0) peers 4 (324) and 3 (529).  Prune 1(1),
+#       2(9), 0(256), 4(324), 3(529): 1, 2, 0 kept as in phase 1 (4: 812.25,
+#       506.25 > 324; 3: 1296, 900 > 529) -> unchanged, no publish, no offer.
+#   Offers 3 <- 4 and 4 <- 3: already present, no-op.  5 <- 3(529): prune
+#       {1, 2, 0, 3}: 1, 2, 0 kept (R) -> unchanged.
+# Publishes: 1 + 2 + 3 (base) + 3 own + 3 targets + 2 refined = 14.
+# (Admitting non-peer two-hop ids would give v3 the base node 2 and
+# F'3 = [4(25), 2(400)]; refining on the pre-offer graph finds no peers.)
+# ---------------------------------------------------------------------------
+GOLD_REFINE = os.path.join(os.path.dirname(__file__), "golden", "refine_peers_hand.json")
+
+
+def test_hand_derived_refine_pass(oracle_mod):
+    g = json.load(open(GOLD_REFINE))
+    nb, nt = len(g["base_x"]), len(g["batch_x"])
+    X = np.zeros((nb + nt, g["dim"]), np.float32)
+    X[:, 0] = g["base_x"] + g["batch_x"]
+    o = oracle_mod.Oracle(g["dim"], "l2", g["degree"], 100, build_beam=g["build_beam"],
+                          alpha=g["alpha"], refine=g["refine"], max_batch=g["max_batch"],
+                          n_entry=g["n_entry"])
+    for i in range(nb):
+        assert o.insert(X[i:i + 1]).tolist() == [i]
+    _check_lists(o, g["after_base"])
+    assert o.insert(X[nb:]).tolist() == list(range(nb, nb + nt))
+    _check_lists(o, g["after_batch"])
+    assert o.stats()["n_publish"] == g["n_publish"]
+
+
+# ---------------------------------------------------------------------------
+# Hand derivation 3: two deletions sharing a live out-neighbour whose list is
+# at capacity (Algorithm 3), tests/golden/repair_two_deletions_hand.json.
+# R = 2, alpha = 2 (alpha^2 = 4), E = {smallest live id}, refine off, one
+# node per sub-batch.  Points x = 11, 16, 21, 6, 20, 18 (ids 0..5).
+# Squared distances: d01 25, d02 100, d03 25, d04 81, d05 49, d12 25, d13 100,
+# d14 16, d15 4, d23 225, d24 1, d25 9, d34 196, d35 144, d45 4.
+# p' is dropped by the head p* when 4 * d(p*, p') <= d(p, p').
+#
+# id0: N(0) = [].
+# id1: F = [0(25)]; offer: N(0) = [1(25)].
+# id2: beam [0(100)] -> 1(25).  C = 1(25), 0(100): keep 1; 0: 4*25 = 100 <=
+#      100 -> dropped.  F = [1(25)]; offer: N(1) = [0(25), 2(25)] (tie by id).
+# id3: beam [0(25)] -> 1(100) -> 2(225).  C = 0(25), 1(100), 2(225): keep 0;
+#      1: 100 <= 100 -> dropped; 2: 400 <= 225? no; keep 2.  F = [0(25),
+#      2(225)].  Offers below R: N(0) = [1(25), 3(25)], N(2) = [1(25), 3(225)].
+# id4: beam from 0(81): 1(16), 3(196), then via 1: 2(1).  C = 2(1), 1(16),
+#      0(81), 3(196): keep 2; 1: 100 <= 16? no; 0: 400 <= 81? no; 3: 900 <=
+#      196? no; keep 1.  F = [2(1), 1(16)].
+#      1 <- 4(16): prune {4(16), 0(25), 2(25)}: keep 4; 0: 324 <= 25? no; 2:
+#      4*1 <= 25 -> dropped; keep 0 -> [4(16), 0(25)].
+#      2 <- 4(1): prune {4(1), 1(25), 3(225)}: keep 4; 1: 64 <= 25? no; 3: 784
+#      <= 225? no; keep 1 -> [4(1), 1(25)].
+# id5: C = 1(4), 4(4), 2(9), 0(49), 3(144): keep 1; 4: 64 <= 4? no; 2: 100 <=
+#      9? no; 0: 100 <= 49? no; 3: 400 <= 144? no; keep 4.  F = [1(4), 4(4)].
+#      1 <- 5(4): prune {5(4), 4(16), 0(25)}: keep 5; 4: 4*4 = 16 <= 16 ->
+#      dropped; 0: 196 <= 25? no; keep 0 -> [5(4), 0(25)].
+#      4 <- 5(4): prune {2(1), 5(4), 1(16)}: keep 2; 5: 36 <= 4? no; keep 5
+#      -> [2(1), 5(4)].
+# Delete {4, 3} (sorted: 3, 4); both tombstoned first.  a = 2 is a live
+# out-neighbour of both (N(3) = [0, 2], N(4) = [2, 5]) and N(2) = [4(1),
+# 1(25)] is full.
+#   K(3, 0) = prune_0({2(100)}) = [2(100)];  K(3, 2) = prune_2({0(100)}) = [0(100)].
+#   K(4, 2) = prune_2({5(9)}) = [5(9)];      K(4, 5) = prune_5({2(9)}) = [2(9)].
+#   a = 0: prune {1(25), 2(100)}: keep 1; 2: 4*25 = 100 <= 100 -> dropped.
+#          N(0) = [1(25)].
+#   a = 2, u = 3 first: prune ({4(1), 1(25)} u {0(100)}); 4 is a tombstone ->
+#          removed; keep 1; 0: 100 <= 100 -> dropped -> [1(25)].
+#          then u = 4: prune ({1(25)} u {5(9)}): keep 5; 1: 4*4 = 16 <= 25 ->
+#          dropped -> [5(9)].  N(2) = [5(9)], one publish.
+#          (One prune over the union {1(25), 0(100), 5(9)}, or the two folds
+#          in descending u, both keep 0 as well: [5(9), 0(100)].)
+#   a = 5: prune {1(4), 2(9)}: keep 1; 2: 100 <= 9? no -> [1(4), 2(9)].
+# Publishes: 14 while inserting + 3 repairs = 17.
+# Reclaim: E = {0}; no live list names 3 or 4; both slabs freed; used = 4.
+# Query x = 19, k = 2, beam 8: 0(64) -> 1(9) -> 5(1) -> 2(4).  Result
+# [5(1), 2(4)].
+# ---------------------------------------------------------------------------
+GOLD_REPAIR = os.path.join(os.path.dirname(__file__), "golden", "repair_two_deletions_hand.json")
+
+
+def test_hand_derived_two_deletions(oracle_mod):
+    g = json.load(open(GOLD_REPAIR))
+    n = len(g["points_x"])
+    X = np.zeros((n, g["dim"]), np.float32)
+    X[:, 0] = g["points_x"]
+    o = oracle_mod.Oracle(g["dim"], "l2", g["degree"], 100, build_beam=g["build_beam"],
+                          alpha=g["alpha"], refine=g["refine"], max_batch=g["max_batch"],
+                          n_entry=g["n_entry"])
+    assert o.insert(X).tolist() == list(range(n))
+    _check_lists(o, g["after_inserts"])
+    assert o.delete(g["delete"]) == 2
+    _check_lists(o, g["after_delete"])
+    assert [o.node(u)[0] for u in range(n)] == g["deleted_flags_after_delete"]
+    assert o.stats()["n_publish"] == g["n_publish_after_delete"]
+    o.reclaim()
+    s = o.stats()
+    assert s["live"] == g["after_reclaim_live"] and s["used_slabs"] == g["after_reclaim_used_slabs"]
+    q = np.zeros((1, g["dim"]), np.float32)
+    q[0, 0] = g["query_x"]
+    rid, rd = o.search(q, g["k"], g["beam"])
+    assert rid[0].tolist() == g["query_result"][0]
+    assert rd[0].tolist() == [float(x) for x in g["query_result"][1]]
+
+
 def _small_index(oracle_mod, n, refine=2, seed_shift=0, **kw):
     w = W.scaled(W.SMALL, n, n_queries=200)
     p = W.make_plan(w)
