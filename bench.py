@@ -50,6 +50,10 @@ def parse():
                     help="extra rounds timed with fp32 BeamSearches gathering the BF16 copy, which holds every "
                          "row of the integer-valued workload exactly (0: skip); reported apart from the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--cpu-ops", type=int, default=1000,
+                    help="cpu_baseline: deletes and inserts the oracle runs on the full graph (scaled to the round)")
+    ap.add_argument("--ref-ops", type=int, default=250,
+                    help="--impl reference: deletes and inserts per step on the full graph (scaled to the round)")
     ap.add_argument("--n-live", type=int, default=0, help="scale the workload to this many live vectors")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed region with an NVTX range 'timed'")
     ap.add_argument("--varbatch", action="store_true",
@@ -148,56 +152,103 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # the CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(w: W.Workload, n_sample: int, ops: int, n_entry: int, rounds: int = 1, max_cand: int = 0):
-    """Build the oracle on n_sample points of the workload's mixture (untimed),
-    then time `rounds` batches of `ops` deletes + `ops` inserts + reclaim.
-    Per-operation costs are scaled to the workload's round (n_delete deletes,
-    n_insert inserts; reclaim scaled linearly in the live count)."""
+def host_cpu() -> dict:
+    """Host CPU model and core count (lscpu), recorded beside the oracle timing."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "logical_cpus": os.cpu_count()}
+
+
+def oracle_knobs(w: W.Workload, args) -> dict:
+    return dict(build_beam=w.build_beam, refine=2, n_entry=args.n_entry, max_cand=args.max_cand)
+
+
+def oracle_rounds(snap: str, w: W.Workload, args, plan, n_ops: int, rounds: int, first_round: int,
+                  first_new_id: int):
+    """Time the oracle (one host core, as it stands) on the graph in the
+    snapshot file: per round, n_ops uniformly chosen live ids deleted, n_ops of
+    the round's fresh vectors inserted, then one Reclaim.  The per-operation
+    times of deletes and inserts are scaled to the workload's round (n_delete +
+    n_insert); the Reclaim (a scan of every list plus the compaction of the
+    sample's dirty nodes) is counted as timed.  Returns per-round ms and the
+    parts of the last round."""
     import oracle
-    ws = W.scaled(w, n_sample, n_queries=16, rounds=rounds)
-    ws = W.dataclasses.replace(ws, n_delete=ops, n_insert=ops)
-    p = W.make_plan(ws)
-    o = oracle.Oracle(w.dim, w.metric, w.degree, ws.capacity, build_beam=w.build_beam, refine=2,
-                      n_entry=n_entry, max_cand=max_cand)
-    o.insert(p.base)
-    o.reclaim()
-    alive = np.zeros(ws.capacity, bool)
-    alive[:n_sample] = True
-    per_round = []
+    t = time.perf_counter()
+    o = oracle.Oracle.load(snap, **oracle_knobs(w, args))
+    load_s = time.perf_counter() - t
+    de, hs = o.dump()[:2]
+    live = set(np.nonzero((de == 0) & (hs == 1))[0].tolist())
+    rng = np.random.default_rng(first_round)
+    per, parts = [], {}
+    next_id = first_new_id
     for r in range(rounds):
-        dele = W.choose_deletes(p.delete_rng, np.nonzero(alive)[0].astype(np.uint32), ops)
+        ids = np.fromiter(sorted(live), np.uint32)
+        dele = W.choose_deletes(rng, ids, n_ops)
+        ins = plan.inserts[(first_round + r) % len(plan.inserts)][:n_ops]
         t0 = time.perf_counter()
         o.delete(dele)
         t1 = time.perf_counter()
-        ids = o.insert(p.inserts[r])
+        new = o.insert(ins)
         t2 = time.perf_counter()
         o.reclaim()
         t3 = time.perf_counter()
-        alive[dele] = False
-        alive[ids] = True
-        t_del, t_ins, t_rec = (t1 - t0) / ops, (t2 - t1) / ops, (t3 - t2)
-        est = (w.n_delete * t_del + w.n_insert * t_ins + t_rec * (w.n_base / n_sample)) * 1e3
-        per_round.append(est)
-    return per_round, {"n_sample": n_sample, "ops": ops}
+        live.difference_update(dele.tolist())
+        live.update(new.tolist())
+        next_id += n_ops
+        est = ((t1 - t0) / n_ops * w.n_delete + (t2 - t1) / n_ops * w.n_insert + (t3 - t2)) * 1e3
+        per.append(est)
+        parts = {"delete_ms_per_op": (t1 - t0) / n_ops * 1e3, "insert_ms_per_op": (t2 - t1) / n_ops * 1e3,
+                 "reclaim_ms": (t3 - t2) * 1e3}
+    return per, {"load_s": load_s, "parts": parts, "n_live_start": len(live)}
+
+
+def oracle_sample_text(w, n_ops, rounds):
+    return (f"oracle (C, one host core) loaded from a snapshot of the GPU-built {w.n_base:,}-node graph "
+            f"(etale_save / orc_load, untimed); {rounds} round(s) of {n_ops} deletes + {n_ops} inserts + one "
+            f"Reclaim on it, delete and insert times scaled per operation to {w.n_delete} + {w.n_insert}, "
+            f"Reclaim as timed; no result of the oracle is compared here")
+
+
+def gpu_build_snapshot(w: W.Workload, args, plan, path: str):
+    """Build the workload's graph with the library (as the GPU arm does) and
+    save it; setup only, outside every timed region."""
+    import torch
+    from paper_2607_02543_gb300 import Index, build as B
+    B.build()
+    idx = Index(w.dim, w.metric, w.degree, w.capacity, build_beam=w.build_beam, mode=args.mode,
+                n_entry=args.n_entry, max_cand=args.max_cand)
+    idx.insert(torch.from_numpy(plan.base).cuda())
+    idx.reclaim()
+    idx.save(path)
+    idx.close()
+    torch.cuda.empty_cache()
 
 
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_entry = args.n_entry
-    per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry,
-                              rounds=args.warmup + args.steps, max_cand=args.max_cand)
+    n_ops = args.ref_ops
+    plan = W.make_plan(W.dataclasses.replace(w, rounds=args.warmup + args.steps))
+    with tempfile.TemporaryDirectory() as tmp:
+        snap = os.path.join(tmp, "graph.snap")
+        gpu_build_snapshot(w, args, plan, snap)
+        per, info = oracle_rounds(snap, w, args, plan, n_ops, args.warmup + args.steps, 0, w.n_base)
     timed = per[args.warmup:]
     v = float(np.mean(timed))
-    sample = (f"oracle built on {info['n_sample']} points of the same mixture (untimed); each step times "
-              f"{info['ops']} deletes + {info['ops']} inserts + reclaim, scaled per operation to "
-              f"{w.n_delete} + {w.n_insert} and reclaim linearly to {w.n_base} live")
+    cpu = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "host": host_cpu(),
+           "sample": oracle_sample_text(w, n_ops, args.steps), "parts": info["parts"]}
     out = {"impl": "reference", "metric": "ms per 1% churn round", "value": v, "unit": "ms",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic", "config": config_dict(w, args),
-           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+           "data": "synthetic", "config": config_dict(w, args), "cpu_baseline": cpu,
            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -625,6 +676,11 @@ def main():
         round_dev(r)
         idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
     torch.cuda.synchronize()
+    # the graph the timed rounds start from, for the oracle's timing (setup)
+    snap_dir = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        snap_dir = tempfile.TemporaryDirectory()
+        idx.save(os.path.join(snap_dir.name, "graph.snap"), stream)
     barrier()
     clocks = Clocks(local)
     clocks.start()
@@ -783,14 +839,14 @@ def main():
     ms_round, ms_search = reduce_max([ms_round, ms_search], world, dev)
     st = idx.stats()
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        per, info = oracle_sample(w, 3000 if w.n_base > 10_000 else 2000, 40, n_entry, rounds=1,
-                                  max_cand=args.max_cand)
-        cpu = {"value": float(np.mean(per)), "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"oracle on {info['n_sample']} points of the same mixture, one batch of "
-                         f"{info['ops']} deletes + {info['ops']} inserts + reclaim timed on one host core, "
-                         f"scaled per operation to {w.n_delete} + {w.n_insert} and reclaim linearly to "
-                         f"{w.n_base} live"}
+    if snap_dir is not None:
+        idx.close()                      # the oracle's timing runs alone on the host
+        per, info = oracle_rounds(os.path.join(snap_dir.name, "graph.snap"), w, args, plan, args.cpu_ops, 1,
+                                  args.warmup, w.n_base + args.warmup * w.n_insert)
+        snap_dir.cleanup()
+        cpu = {"value": float(np.mean(per)), "unit": "ms", "cores": 1, "kind": "oracle", "host": host_cpu(),
+               "sample": oracle_sample_text(w, args.cpu_ops, 1), "parts": info["parts"],
+               "load_s": info["load_s"]}
     if rank == 0:
         out = {"metric": "ms per 1% churn round", "value": ms_round, "unit": "ms", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),

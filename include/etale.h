@@ -121,6 +121,8 @@ typedef struct {
     uint64_t n_dist;          /* distance evaluations in BeamSearch           */
     uint64_t device_bytes;    /* index memory held on the device              */
     uint64_t exact_rows;      /* 1 while fp32 searches gather the exact BF16 copy */
+    uint32_t dim;             /* m                                            */
+    uint32_t metric;          /* etale_metric                                 */
 } etale_stats_t;
 
 /* Fill *cfg with the defaults (all fields resolved except those that depend
@@ -221,6 +223,42 @@ etale_status etale_get_config(const etale_index *idx, etale_config *out);
 /* One-line description of the last failed call made by the calling thread
  * (on any index, etale_create included); idx is ignored.  Never NULL.      */
 const char *etale_last_error(const etale_index *idx);
+
+/* ---- snapshots ---------------------------------------------------------- */
+/* Save the index state (Definition 1: vectors, reference words, the slab
+ * map, plus the entry set and configuration) to the file `path`, so that
+ * etale_load (or any reader of the format below) can rebuild the same
+ * logical graph.  Waits for `stream` first; synchronous.  The file holds no
+ * slab numbers: a loaded index lays its slabs out afresh, so its resident
+ * slab count is the number of ids with a slab.
+ *
+ * Format (version 1, little-endian, no padding):
+ *   char  magic[8] = "ETALESN1"
+ *   u32   version = 1, dim, metric (0 L2, 1 IP), degree R
+ *   u64   capacity, next_id
+ *   u32   n_entries, n_cfg (= 17)
+ *   u64   cfg[n_cfg]: build_beam, alpha (fp32 bits), max_hops, max_cand,
+ *         refine, max_batch, pool_slabs, n_entry, mode, cas_budget,
+ *         stage_kb, gram, copies, rerank, gt, seed, exact_rows
+ *   f32   x[next_id][dim]
+ *   u8    flags[next_id]: bit 0 delta, bit 1 has a slab, bit 2 the list was
+ *         written by a RobustPrune (a hint of this library; 0 is always
+ *         valid and changes no result)
+ *   u8    deg[next_id] (0 when there is no slab)
+ *   then, for each id with a slab in ascending id, deg entries {u32 id;
+ *         f32 rho} in slab order
+ *   u32   entries[n_entries]
+ * EINVAL if the file cannot be written.                                    */
+etale_status etale_save(etale_index *idx, const char *path, void *stream);
+
+/* Create an index from a file written by etale_save (or in its format).
+ * cfg NULL takes the saved configuration; otherwise cfg's fields apply as in
+ * etale_create.  capacity 0 keeps the saved capacity; it must be >= the
+ * saved next_id.  The reduced-precision copies are recomputed from the
+ * vectors.  EINVAL for a malformed or inconsistent file (an id beyond
+ * next_id, a degree above R, a list on an id without a slab); ENOMEM if the
+ * pool cannot hold the saved lists.                                        */
+etale_status etale_load(const char *path, const etale_config *cfg, uint64_t capacity, etale_index **out);
 
 /* ---- launch-shape tuning (deployment support; the paper has none) -------- */
 typedef struct {

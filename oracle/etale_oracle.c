@@ -39,6 +39,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -769,6 +770,72 @@ void orc_dump(const orc *o, uint8_t *del, uint8_t *has_slab, uint8_t *deg, uint3
         const entry *e = o->slab + (uint64_t)ref_slab(r) * R;
         for (uint32_t i = 0; i < d; i++) { ids[u * R + i] = e[i].id; rho[u * R + i] = e[i].rho; }
     }
+}
+
+/* ---- snapshot reader ------------------------------------------------------
+ * Rebuilds the state of Definition 1 from a snapshot file (the format written
+ * by the library's etale_save, read here by this file's own code).  cfg gives
+ * the maintenance knobs; dim, metric and degree come from the file and
+ * cfg->capacity (0: the saved capacity) must cover the saved next_id.  The
+ * k-th id with a slab gets slab k; the free stack holds the remaining slabs.
+ * The entry set is the saved one.  Used for timing on large graphs and for
+ * round-trip tests; returns NULL on a malformed file.                       */
+static int rd(FILE *f, void *p, size_t sz, size_t n) { return fread(p, sz, n, f) == n; }
+
+orc *orc_load(const char *path, const orc_config *cfg) {
+    FILE *f = fopen(path, "rb");
+    if (!f) return NULL;
+    char magic[8];
+    uint32_t h[4], hb[2];
+    uint64_t cap_n[2], cw[64];
+    orc *o = NULL;
+    uint8_t *fl = NULL, *dg = NULL;
+    if (!rd(f, magic, 1, 8) || memcmp(magic, "ETALESN1", 8) != 0 || !rd(f, h, 4, 4) || h[0] != 1 ||
+        !rd(f, cap_n, 8, 2) || !rd(f, hb, 4, 2) || hb[1] > 64 || !rd(f, cw, 8, hb[1]))
+        goto bad;
+    {
+        orc_config c = *cfg;
+        c.dim = h[1]; c.metric = h[2]; c.degree = h[3];
+        if (c.capacity == 0) c.capacity = cap_n[0];
+        uint64_t n = cap_n[1];
+        uint32_t R = c.degree, ne = hb[0];
+        if (n > c.capacity) goto bad;
+        o = orc_create(&c);
+        if (!o || ne > o->c.n_entry) goto bad;
+        if (n && !rd(f, o->x, sizeof(float), n * c.dim)) goto bad;
+        fl = malloc(n ? n : 1); dg = malloc(n ? n : 1);
+        if (n && (!rd(f, fl, 1, n) || !rd(f, dg, 1, n))) goto bad;
+        uint64_t k = 0, live = 0;
+        for (uint64_t u = 0; u < n; u++) {
+            uint32_t del = fl[u] & 1u, hs = (fl[u] >> 1) & 1u;
+            if (dg[u] > R || (!hs && dg[u])) goto bad;
+            if (!hs) { o->ref[u] = pack(del, 0, ORC_NIL); continue; }
+            if (k >= o->c.pool_slabs) goto bad;
+            entry *e = o->slab + k * R;
+            for (uint32_t j = 0; j < dg[u]; j++) {
+                if (!rd(f, &e[j].id, 4, 1) || !rd(f, &e[j].rho, 4, 1) || e[j].id >= n) goto bad;
+            }
+            o->ref[u] = pack(del, dg[u], (uint32_t)k);
+            k++;
+            live += !del;
+        }
+        /* free stack: every slab not taken above */
+        o->nfree = 0;
+        for (uint64_t i = o->c.pool_slabs; i-- > k;) o->fst[o->nfree++] = (uint32_t)i;
+        if (ne && !rd(f, o->ent, 4, ne)) goto bad;
+        for (uint32_t i = 0; i < ne; i++) if (o->ent[i] >= n) goto bad;
+        o->n_ent = ne;
+        o->next_id = n;
+        o->live = live;
+    }
+    free(fl); free(dg);
+    fclose(f);
+    return o;
+bad:
+    free(fl); free(dg);
+    orc_destroy(o);
+    fclose(f);
+    return NULL;
 }
 
 void orc_get_stats(const orc *o, orc_stats *s) {

@@ -80,6 +80,8 @@ def _load():
         lib.orc_effective_config.argtypes = [P, C.POINTER(_Config)]
         lib.orc_entries.restype = C.c_uint32
         lib.orc_entries.argtypes = [P, P]
+        lib.orc_load.restype = P
+        lib.orc_load.argtypes = [C.c_char_p, C.POINTER(_Config)]
         _lib = lib
         return lib
 
@@ -128,6 +130,25 @@ class Oracle:
             raise ValueError("orc_create rejected the configuration")
         self.dim, self.degree, self.capacity = dim, degree, capacity
         self.metric = metric
+
+    @classmethod
+    def load(cls, path: str, capacity: int = 0, *, build_beam: int = 64, alpha: float = 1.2,
+             max_hops: int = 0, max_cand: int = 0, refine: int = 1, max_batch: int = 0,
+             pool_slabs: int = 0, n_entry: int = 0) -> "Oracle":
+        """orc_load: an oracle index rebuilt from a snapshot file (dim, metric and
+        degree from the file; the maintenance knobs from the arguments)."""
+        lib = _load()
+        cfg = _Config(0, 0, 0, capacity, build_beam, alpha, max_hops, max_cand, refine, max_batch,
+                      pool_slabs, n_entry)
+        h = lib.orc_load(os.fsencode(path), C.byref(cfg))
+        if not h:
+            raise ValueError(f"orc_load could not read {path}")
+        self = cls.__new__(cls)
+        self.lib, self.h = lib, h
+        c = self.config()
+        self.dim, self.degree, self.capacity = c["dim"], c["degree"], c["capacity"]
+        self.metric = "l2" if c["metric"] == 0 else "ip"
+        return self
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -46,7 +46,8 @@ class Stats(C.Structure):
                 ("free_slabs", C.c_uint64), ("retired_slabs", C.c_uint64), ("used_slabs", C.c_uint64),
                 ("n_entries", C.c_uint32), ("degree", C.c_uint32), ("n_publish", C.c_uint64),
                 ("n_cas_retry", C.c_uint64), ("n_dropped", C.c_uint64), ("n_expand", C.c_uint64),
-                ("n_dist", C.c_uint64), ("device_bytes", C.c_uint64), ("exact_rows", C.c_uint64)]
+                ("n_dist", C.c_uint64), ("device_bytes", C.c_uint64), ("exact_rows", C.c_uint64),
+                ("dim", C.c_uint32), ("metric", C.c_uint32)]
 
 
 EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_insert", "etale_delete",
@@ -56,7 +57,8 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent",
            "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
-           "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows"]
+           "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
+           "etale_load"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -105,6 +107,8 @@ def load(path: str = LIB_PATH):
             "etale_search_graph_destroy": ([P], C.c_int),
             "etale_selftest_bounded_wait": ([U32, P], C.c_int),
             "etale_ground_truth_info": ([P, P, P], C.c_int),
+            "etale_save": ([P, C.c_char_p, P], C.c_int),
+            "etale_load": ([C.c_char_p, C.POINTER(Config), U64, C.POINTER(P)], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -189,6 +193,27 @@ class Index:
             self.close()
         except Exception:
             pass
+
+    # --- snapshots -----------------------------------------------------------
+    def save(self, path: str, stream=None):
+        """etale_save: write the index state to `path` (format in include/etale.h)."""
+        self._check(self.lib.etale_save(self.h, os.fsencode(path), _stream(stream)))
+
+    @classmethod
+    def load(cls, path: str, capacity: int = 0) -> "Index":
+        """etale_load with the saved configuration; capacity 0 keeps the saved one."""
+        lib = load()
+        h = C.c_void_p()
+        st = lib.etale_load(os.fsencode(path), None, capacity, C.byref(h))
+        if st:
+            raise EtaleError(st, lib.etale_last_error(None).decode())
+        self = cls.__new__(cls)
+        self.lib, self.h = lib, h
+        s = Stats()
+        self._check(lib.etale_stats(h, C.byref(s)))
+        self.dim, self.degree, self.capacity = s.dim, s.degree, s.capacity
+        self.metric = "l2" if s.metric == 0 else "ip"
+        return self
 
     # --- updates -----------------------------------------------------------
     def insert(self, vecs, stream=None):
@@ -359,3 +384,24 @@ class SearchGraph:
             self.close()
         except Exception:
             pass
+
+    # --- snapshots -----------------------------------------------------------
+    def save(self, path: str, stream=None):
+        """etale_save: write the index state to `path` (format in include/etale.h)."""
+        self._check(self.lib.etale_save(self.h, os.fsencode(path), _stream(stream)))
+
+    @classmethod
+    def load(cls, path: str, capacity: int = 0) -> "Index":
+        """etale_load with the saved configuration; capacity 0 keeps the saved one."""
+        lib = load()
+        h = C.c_void_p()
+        st = lib.etale_load(os.fsencode(path), None, capacity, C.byref(h))
+        if st:
+            raise EtaleError(st, lib.etale_last_error(None).decode())
+        self = cls.__new__(cls)
+        self.lib, self.h = lib, h
+        s = Stats()
+        self._check(lib.etale_stats(h, C.byref(s)))
+        self.dim, self.degree, self.capacity = s.dim, s.degree, s.capacity
+        self.metric = "l2" if s.metric == 0 else "ip"
+        return self

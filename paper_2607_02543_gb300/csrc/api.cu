@@ -1117,6 +1117,8 @@ etale_status etale_stats(etale_index *idx, etale_stats_t *o) {
     o->n_dist = c[C_DIST];
     o->device_bytes = idx->device_bytes;
     o->exact_rows = exact_rows(idx) ? 1 : 0;
+    o->dim = idx->dim;
+    o->metric = idx->metric;
     return ETALE_OK;
 }
 
@@ -1399,6 +1401,233 @@ etale_status etale_search_static(etale_index *idx, const float *queries, uint64_
         idx->search_ev_valid = true;
     }
     return check_search_errors(idx, st);
+}
+
+// ---------------------------------------------------------------------------
+// Snapshots (format in include/etale.h).  Chunked by ids so that host memory
+// stays bounded at 10M-row indexes.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char SNAP_MAGIC[8] = {'E', 'T', 'A', 'L', 'E', 'S', 'N', '1'};
+constexpr u32 SNAP_NCFG = 17;
+constexpr u64 SNAP_CHUNK = 1ull << 18;
+
+void cfg_to_words(const etale_config &c, u64 *w) {
+    u32 ab;
+    memcpy(&ab, &c.alpha, 4);
+    const u64 v[SNAP_NCFG] = {c.build_beam, ab, c.max_hops, c.max_cand, c.refine, c.max_batch, c.pool_slabs,
+                              c.n_entry, c.mode, c.cas_budget, c.stage_kb, c.gram, c.copies, c.rerank,
+                              c.gt, c.seed, c.exact_rows};
+    memcpy(w, v, sizeof v);
+}
+void words_to_cfg(const u64 *w, etale_config &c) {
+    memset(&c, 0, sizeof c);
+    u32 ab = (u32)w[1];
+    c.build_beam = (u32)w[0]; memcpy(&c.alpha, &ab, 4); c.max_hops = (u32)w[2]; c.max_cand = (u32)w[3];
+    c.refine = (u32)w[4]; c.max_batch = w[5]; c.pool_slabs = w[6]; c.n_entry = (u32)w[7]; c.mode = (u32)w[8];
+    c.cas_budget = (u32)w[9]; c.stage_kb = (u32)w[10]; c.gram = (u32)w[11]; c.copies = (u32)w[12];
+    c.rerank = (u32)w[13]; c.gt = (u32)w[14]; c.seed = (u32)w[15]; c.exact_rows = (u32)w[16];
+}
+
+struct File {
+    FILE *f = nullptr;
+    ~File() { if (f) fclose(f); }
+};
+}  // namespace
+
+etale_status etale_save(etale_index *idx, const char *path, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (!path) return idx->fail(ETALE_EINVAL, "path is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st), "synchronize");
+    File f;
+    f.f = fopen(path, "wb");
+    if (!f.f) return idx->fail(ETALE_EINVAL, "cannot open %s for writing", path);
+    const u64 n = idx->next_id, R = idx->R;
+    const u32 ne = idx->n_entries;
+    bool ok = fwrite(SNAP_MAGIC, 1, 8, f.f) == 8;
+    const u32 h32[4] = {1u, idx->dim, idx->metric, idx->R};
+    const u64 h64[2] = {idx->capacity, n};
+    const u32 h32b[2] = {ne, SNAP_NCFG};
+    u64 cw[SNAP_NCFG];
+    cfg_to_words(idx->cfg, cw);
+    ok = ok && fwrite(h32, 4, 4, f.f) == 4 && fwrite(h64, 8, 2, f.f) == 2 && fwrite(h32b, 4, 2, f.f) == 2 &&
+         fwrite(cw, 8, SNAP_NCFG, f.f) == SNAP_NCFG;
+    // vectors, unpadded
+    std::vector<float> xh;
+    for (u64 lo = 0; lo < n && ok; lo += SNAP_CHUNK) {
+        const u64 c = std::min(SNAP_CHUNK, n - lo);
+        xh.resize(c * idx->dim);
+        CK(cudaMemcpy2D(xh.data(), (size_t)idx->dim * 4, idx->x + lo * idx->mp, (size_t)idx->mp * 4,
+                        (size_t)idx->dim * 4, c, cudaMemcpyDeviceToHost),
+           "save vectors");
+        ok = fwrite(xh.data(), 4, c * idx->dim, f.f) == c * idx->dim;
+    }
+    // flags and degrees from the reference words; lists from the export kernel
+    std::vector<u64> refh(n);
+    if (n) CK(cudaMemcpy(refh.data(), idx->ref, n * 8, cudaMemcpyDeviceToHost), "save references");
+    std::vector<unsigned char> fl(n), dg(n);
+    for (u64 u = 0; u < n; u++) {
+        const u64 r = refh[u];
+        const bool hs = ref_slab(r) != NIL;
+        fl[u] = (unsigned char)(ref_del(r) | (hs ? 2u : 0u) | (hs && ref_pruned(r) ? 4u : 0u));
+        dg[u] = hs ? (unsigned char)ref_deg(r) : 0;
+    }
+    ok = ok && fwrite(fl.data(), 1, n, f.f) == n && fwrite(dg.data(), 1, n, f.f) == n;
+    if (n && ok) {
+        const u64 c0 = std::min(SNAP_CHUNK, n);
+        if (!grow(idx->ex_del, c0) || !grow(idx->ex_hs, c0) || !grow(idx->ex_deg, c0) ||
+            !grow(idx->ex_ids, c0 * R * 4) || !grow(idx->ex_rho, c0 * R * 4))
+            return idx->fail(ETALE_ENOMEM, "save staging");
+        std::vector<u32> ids(c0 * R);
+        std::vector<float> rho(c0 * R);
+        std::vector<uint2> out;
+        for (u64 lo = 0; lo < n && ok; lo += SNAP_CHUNK) {
+            const u64 c = std::min(SNAP_CHUNK, n - lo);
+            Dev d = idx->dev();
+            d.ref = idx->ref + lo;   // the export kernel reads ids [0, c) of this view
+            CK(launch_export(d, c, as<unsigned char>(idx->ex_del), as<unsigned char>(idx->ex_hs),
+                             as<unsigned char>(idx->ex_deg), as<u32>(idx->ex_ids), as<float>(idx->ex_rho), st),
+               "save export");
+            g_kernel_launches++;
+            CK(cudaMemcpyAsync(ids.data(), idx->ex_ids.p, c * R * 4, cudaMemcpyDeviceToHost, st), "save lists");
+            CK(cudaMemcpyAsync(rho.data(), idx->ex_rho.p, c * R * 4, cudaMemcpyDeviceToHost, st), "save lists");
+            CK(cudaStreamSynchronize(st), "synchronize");
+            out.clear();
+            for (u64 i = 0; i < c; i++)
+                for (u32 j = 0; j < dg[lo + i]; j++) {
+                    uint2 e;
+                    e.x = ids[i * R + j];
+                    memcpy(&e.y, &rho[i * R + j], 4);
+                    out.push_back(e);
+                }
+            ok = fwrite(out.data(), 8, out.size(), f.f) == out.size();
+        }
+    }
+    if (ne && ok) {
+        std::vector<u32> eh(ne);
+        CK(cudaMemcpy(eh.data(), idx->entries, (size_t)ne * 4, cudaMemcpyDeviceToHost), "save entries");
+        ok = fwrite(eh.data(), 4, ne, f.f) == ne;
+    }
+    ok = ok && fflush(f.f) == 0;
+    if (!ok) return idx->fail(ETALE_EINVAL, "write to %s failed", path);
+    return ETALE_OK;
+}
+
+etale_status etale_load(const char *path, const etale_config *cfg_in, uint64_t capacity, etale_index **out) {
+    if (!out) { t_last_error = "out is NULL"; return ETALE_EINVAL; }
+    *out = nullptr;
+    auto bad = [](const char *m) { t_last_error = m; return ETALE_EINVAL; };
+    if (!path) return bad("path is NULL");
+    File f;
+    f.f = fopen(path, "rb");
+    if (!f.f) return bad("cannot open the snapshot file");
+    char magic[8];
+    u32 h32[4], h32b[2];
+    u64 h64[2], cw[SNAP_NCFG];
+    if (fread(magic, 1, 8, f.f) != 8 || memcmp(magic, SNAP_MAGIC, 8) != 0) return bad("not an ETALE snapshot (magic)");
+    if (fread(h32, 4, 4, f.f) != 4 || h32[0] != 1u) return bad("unsupported snapshot version");
+    if (fread(h64, 8, 2, f.f) != 2 || fread(h32b, 4, 2, f.f) != 2 || h32b[1] != SNAP_NCFG ||
+        fread(cw, 8, SNAP_NCFG, f.f) != SNAP_NCFG)
+        return bad("truncated snapshot header");
+    const u32 dim = h32[1], metric = h32[2], R = h32[3];
+    const u64 n = h64[1];
+    const u32 ne = h32b[0];
+    if (capacity == 0) capacity = h64[0];
+    if (n > capacity) return bad("capacity below the saved next_id");
+    etale_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else words_to_cfg(cw, cfg);
+    etale_index *idx = nullptr;
+    etale_status s = etale_create(dim, (etale_metric)metric, R, capacity, &cfg, &idx);
+    if (s != ETALE_OK) return s;
+    auto fail = [&](etale_status e, const char *m) {
+        t_last_error = m;
+        etale_destroy(idx);
+        return e;
+    };
+    if (ne > idx->cfg.n_entry) return fail(ETALE_EINVAL, "saved entry set larger than n_entry");
+    std::vector<float> xh;
+    for (u64 lo = 0; lo < n; lo += SNAP_CHUNK) {
+        const u64 c = std::min(SNAP_CHUNK, n - lo);
+        xh.resize(c * dim);
+        if (fread(xh.data(), 4, c * dim, f.f) != c * dim) return fail(ETALE_EINVAL, "truncated vectors");
+        if (cudaMemcpy2D(idx->x + lo * idx->mp, (size_t)idx->mp * 4, xh.data(), (size_t)dim * 4, (size_t)dim * 4, c,
+                         cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(ETALE_ECUDA, "load vectors");
+    }
+    std::vector<unsigned char> fl(n), dg(n);
+    if (fread(fl.data(), 1, n, f.f) != n || fread(dg.data(), 1, n, f.f) != n) return fail(ETALE_EINVAL, "truncated flags");
+    u64 used = 0, live = 0, tombs = 0, reclaimed = 0;
+    for (u64 u = 0; u < n; u++) {
+        const bool del = fl[u] & 1u, hs = (fl[u] >> 1) & 1u;
+        if (fl[u] > 7u || dg[u] > R || (!hs && dg[u] != 0)) return fail(ETALE_EINVAL, "inconsistent flags or degree");
+        used += hs;
+        if (hs && !del) live++;
+        else if (hs) tombs++;
+        else if (del) reclaimed++;
+    }
+    if (used > idx->pool) return fail(ETALE_ENOMEM, "slab pool smaller than the saved lists");
+    // slabs in ascending id order: the k-th id with a slab gets slab k; the free
+    // stack as etale_create laid it out (slab P - 1 - i at position i) then holds
+    // exactly the slabs >= used below its top
+    std::vector<u64> refh(n);
+    std::vector<uint2> slabh;
+    u64 k = 0, kflush = 0;
+    for (u64 u = 0; u < n; u++) {
+        const bool del = fl[u] & 1u, hs = (fl[u] >> 1) & 1u;
+        if (!hs) { refh[u] = ref_pack(del, 0, NIL); continue; }
+        const size_t at = slabh.size();
+        slabh.resize(at + R, make_uint2(NIL, 0u));
+        if (dg[u] && fread(slabh.data() + at, 8, dg[u], f.f) != dg[u]) return fail(ETALE_EINVAL, "truncated lists");
+        for (u32 j = 0; j < dg[u]; j++)
+            if (slabh[at + j].x >= n) return fail(ETALE_EINVAL, "a list names an id beyond next_id");
+        refh[u] = ref_pack(del, dg[u], (u32)k) | ((u64)((fl[u] >> 2) & 1u) << 56);
+        k++;
+        if (slabh.size() >= SNAP_CHUNK * R || u + 1 == n) {
+            if (cudaMemcpy(idx->slab + kflush * R, slabh.data(), slabh.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(ETALE_ECUDA, "load slabs");
+            kflush = k;
+            slabh.clear();
+        }
+    }
+    if (!slabh.empty() &&
+        cudaMemcpy(idx->slab + kflush * R, slabh.data(), slabh.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(ETALE_ECUDA, "load slabs");
+    std::vector<u32> eh(ne);
+    if (ne && fread(eh.data(), 4, ne, f.f) != ne) return fail(ETALE_EINVAL, "truncated entry set");
+    for (u32 e : eh)
+        if (e >= n) return fail(ETALE_EINVAL, "an entry id beyond next_id");
+    const u64 free_n = idx->pool - used;
+    if ((n && cudaMemcpy(idx->ref, refh.data(), n * 8, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(idx->ctr + C_FREE, &free_n, 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (ne && cudaMemcpy(idx->entries, eh.data(), (size_t)ne * 4, cudaMemcpyHostToDevice) != cudaSuccess))
+        return fail(ETALE_ECUDA, "load references");
+    idx->next_id = n;
+    idx->live = live;
+    idx->tombs = tombs;
+    idx->reclaimed = reclaimed;
+    idx->free_lb = free_n;
+    idx->n_entries = ne;
+    cudaStream_t st = nullptr;
+    if (launch_set_u32(idx->nent_dev, ne, st) != cudaSuccess ||
+        launch_ingest_copies(idx->dev(), 0, n, st) != cudaSuccess)
+        return fail(ETALE_ECUDA, "load copies");
+    g_kernel_launches += 2;
+    if (idx->seed_tc && ne) {
+        const SeedTcPlan p = seed_tc_plan(idx->dim, ne, 0);
+        if (!grow(idx->sd_E, p.bytes_E) || !grow(idx->sd_en, (size_t)p.s_pad * 4) || !grow(idx->sd_estat, 64))
+            return fail(ETALE_ENOMEM, "entry-set copy");
+        if (launch_seed_tc_entries(idx->dev(), ne, p, idx->seed_bufs(), st) != cudaSuccess)
+            return fail(ETALE_ECUDA, "entry-set copy");
+        g_kernel_launches++;
+    }
+    u64 inexact = 0;
+    if (cudaMemcpy(&inexact, idx->ctr + C_INEXACT, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ETALE_ECUDA, "load synchronise");
+    idx->rows_exact = inexact == 0;
+    *out = idx;
+    return ETALE_OK;
 }
 
 etale_status etale_set_search_precision(etale_index *idx, etale_precision p) {
