@@ -188,6 +188,24 @@ etale_status etale_export_copies(etale_index *idx, uint64_t first, uint64_t n, u
 etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
                           uint32_t beam, uint32_t *out_ids, float *out_dists, void *stream);
 
+/* Evaluation count of a query batch (diagnostic; measurement support for
+ * the algorithmic bytes of BeamSearch, Sec. 3.4.1).  Runs the query search
+ * of etale_search once on DEVICE or host queries with a per-query log of the
+ * ids whose distance it computed during expansions, and reports:
+ *   *n_eval   distance evaluations made by the kernel (its visited set is a
+ *             lossy cache, so an id may be evaluated more than once);
+ *   *n_unique distinct ids evaluated per query, summed, not counting each
+ *             query's initial beam (the seeds): the evaluations of an exact
+ *             visited set.  With an entry set no larger than the beam, this
+ *             is the distance count of a sequential BeamSearch minus |E| per
+ *             query;
+ *   *n_expand expansions.
+ * Allocates nq * max_hops * R * 4 bytes of log for the call; max_hops * R
+ * must be <= 32768.  Results are not returned.                            */
+etale_status etale_search_eval_count(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
+                                     uint32_t beam, uint64_t *n_eval, uint64_t *n_unique,
+                                     uint64_t *n_expand, void *stream);
+
 /* Exact k nearest live nodes by brute force (measurement support for
  * Recall@10, Sec. 5.2): canonical fp32 distances, ties by smaller id.  k must
  * be 1..32.  Unless cfg.gt = 1, a tensor-core pass (bf16 inputs, fp32

@@ -58,7 +58,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
            "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
-           "etale_load"]
+           "etale_load", "etale_search_eval_count"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH):
             "etale_selftest_bounded_wait": ([U32, P], C.c_int),
             "etale_ground_truth_info": ([P, P, P], C.c_int),
             "etale_save": ([P, C.c_char_p, P], C.c_int),
+            "etale_search_eval_count": ([P, P, U64, U32, U32, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64), P],
+                                        C.c_int),
             "etale_load": ([C.c_char_p, C.POINTER(Config), U64, C.POINTER(P)], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -300,6 +302,15 @@ class Index:
         self._check(self.lib.etale_search_static(self.h, _ptr(queries), queries.shape[0], k, beam, _ptr(ids),
                                                  _ptr(dist), _stream(stream)))
         return ids, dist
+
+    def eval_count(self, queries, k: int, beam: int, stream=None) -> dict:
+        """etale_search_eval_count: evaluations, distinct non-seed ids, expansions."""
+        if not _is_cuda(queries):
+            queries = np.ascontiguousarray(queries, dtype=np.float32)
+        ne, nu, nx = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        self._check(self.lib.etale_search_eval_count(self.h, _ptr(queries), queries.shape[0], k, beam, C.byref(ne),
+                                                     C.byref(nu), C.byref(nx), _stream(stream)))
+        return {"n_eval": ne.value, "n_unique": nu.value, "n_expand": nx.value}
 
     def ground_truth(self, queries, k: int, stream=None):
         if not _is_cuda(queries):

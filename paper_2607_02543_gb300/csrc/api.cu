@@ -1053,6 +1053,59 @@ etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, u
     return search_common(idx, queries, nq, k, beam, out_ids, out_dists, stream, false);
 }
 
+etale_status etale_search_eval_count(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
+                                     uint64_t *n_eval, uint64_t *n_unique, uint64_t *n_expand, void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    if (!queries || !n_eval || !n_unique || !n_expand || k == 0 || nq == 0)
+        return idx->fail(ETALE_EINVAL, "null argument, k == 0 or nq == 0");
+    const u32 L = beam > k ? beam : k;
+    if (L > 256 || nq > 0xFFFFFFFFull) return idx->fail(ETALE_EINVAL, "beam must be <= 256");
+    if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
+    const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    const u64 cap = (u64)H * idx->R;   // no search evaluates more (one slab per expansion)
+    if (cap > (1u << 15) || eval_unique_smem((u32)cap, L) > (size_t)idx->smem_optin)
+        return idx->fail(ETALE_EINVAL, "evaluation log of %llu ids per query is above 32768",
+                         (unsigned long long)cap);
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *src = nullptr;
+    etale_status s = StreamCopy::in(idx, idx->s_stage, queries, (size_t)nq * idx->dim * 4, &src, st);
+    if (s != ETALE_OK) return s;
+    float *qpad = nullptr;
+    u64 *seed = nullptr, *cnt = nullptr;
+    u32 *elog = nullptr, *elog_n = nullptr, *oid = nullptr;
+    float *od = nullptr;
+    cudaError_t e = cudaMalloc(&qpad, (size_t)nq * idx->mp * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&seed, (size_t)nq * L * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&elog, (size_t)nq * cap * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&elog_n, (size_t)nq * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&oid, (size_t)nq * k * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&od, (size_t)nq * k * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, 4 * 8);
+    u64 h[4] = {0, 0, 0, 0}, e0 = 0, e1 = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 4 * 8, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&e0, idx->ctr + C_EXPAND, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = launch_ingest(qpad, idx->mp, (const float *)src, idx->dim, nq, st);
+    Dev d = idx->dev();
+    if (e == cudaSuccess) e = launch_seed(d, qpad, (u32)nq, L, seed, st, idx->search_prec);
+    if (e == cudaSuccess)
+        e = launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, seed, fit_tuning(idx, L, idx->tune),
+                          idx->num_sms, st, idx->search_prec, idx->cfg.rerank, nullptr,
+                          idx->search_prec == 0 && exact_rows(idx), elog, elog_n, (u32)cap);
+    const u32 n0 = std::min<u32>(L, idx->n_entries);
+    if (e == cudaSuccess) e = launch_eval_unique(elog, elog_n, (u32)cap, seed, L, n0, (u32)nq, cnt, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cnt, 4 * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&e1, idx->ctr + C_EXPAND, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    g_kernel_launches += 4;
+    cudaFree(qpad); cudaFree(seed); cudaFree(elog); cudaFree(elog_n); cudaFree(oid); cudaFree(od); cudaFree(cnt);
+    if (e != cudaSuccess) return idx->cuda_fail(e, "evaluation count");
+    if (h[2]) return idx->fail(ETALE_EINTERNAL, "evaluation log overflowed");
+    *n_eval = h[0];
+    *n_unique = h[1];
+    *n_expand = e1 - e0;
+    return check_search_errors(idx, st);
+}
+
 etale_status etale_ground_truth(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t *out_ids,
                                 float *out_dists, void *stream) {
     return search_common(idx, queries, nq, k, 0, out_ids, out_dists, stream, true);

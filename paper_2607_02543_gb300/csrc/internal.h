@@ -25,7 +25,14 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec = 0,
-                          u32 rerank = 4, const u32 *nq_dev = nullptr, bool exact_rows = false);
+                          u32 rerank = 4, const u32 *nq_dev = nullptr, bool exact_rows = false,
+                          u32 *elog = nullptr, u32 *elog_n = nullptr, u32 elog_cap = 0);
+// Diagnostic: distinct ids each query evaluated (its log, elog_cap slots per
+// query, from a launch_search with elog set), not counting its n0 seeds;
+// out[0] += evaluations, out[1] += distinct non-seed ids, out[2] += overflows.
+size_t eval_unique_smem(u32 cap, u32 L);
+cudaError_t launch_eval_unique(const u32 *elog, const u32 *elog_n, u32 cap, const u64 *seed, u32 L, u32 n0, u32 nq,
+                               u64 *out, cudaStream_t st);
 
 // Offer lists: a payload index p names (src[p], rho[p]); key[p] is the target
 // id or `invalid` (= capacity) for an empty slot.

@@ -39,6 +39,9 @@ struct SearchArgs {
                          // use their own, so they can overlap a writer)
     u32 rerank;          // reduced precision: re-scored candidates (<= 64)
     u32 exact;           // P = 1 over a bf16 copy that holds every row exactly: no rerank
+    u32 *elog;           // diagnostic (LOG kernels): per query, the ids evaluated during
+    u32 *elog_n;         //   expansions in order (elog_cap slots) and their count
+    u32 elog_cap;
 };
 
 // Row gathered for a neighbour: the fp32 row or its reduced-precision copy.
@@ -263,9 +266,9 @@ __device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L, int &lo) 
 
 // Evaluate the candidate ids held one per lane (NIL = none) and merge them
 // into the beam.  Returns the new beam size.  `phase` tracks the mbarrier.
-template <int P>
+template <int P, bool LOG>
 __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u32 &phase, u64 &ndist,
-                          bool &timeout, int &lo, const float4 (&qr)[4]) {
+                          bool &timeout, int &lo, const float4 (&qr)[4], u32 *qlog, u32 &qcnt) {
     const Dev &d = a.d;
     const int lane = lane_id();
     const u32 mp = d.mp;
@@ -324,6 +327,10 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
         __syncwarp();
     }
     ndist += cnt;
+    if (LOG) {
+        if (lane < cnt && qcnt + lane < a.elog_cap) qlog[qcnt + lane] = s.cid[lane];
+        qcnt += cnt;
+    }
     const u64 key = lane < cnt ? s.ckey[lane] : KEY_INF;
     const u64 ref = lane < cnt ? s.cref[lane] : 0;
     if (lane < cnt) s.seen[seen_slot(key_id(key), a.seen_bits)] = key_id(key);
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     }
 }
 
-template <int P>
+template <int P, bool LOG = false>
 __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -490,6 +497,8 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
         int n = n0;
         __syncwarp();
         u32 hops = 0, nexp = 0;
+        u32 qcnt = 0;
+        u32 *qlog = LOG ? a.elog + (size_t)qi * a.elog_cap : nullptr;
         // slab entries of the predicted next expansion, loaded ahead of use
         u32 pf_id = NIL, pf0 = NIL, pf1 = NIL;
         int lo = 0;   // every beam entry before lo is expanded
@@ -537,10 +546,11 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
             for (u32 j0 = 0; j0 < deg; j0 += 32) {
                 u32 nb = j0 == 0 ? e0 : e1;
                 if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
-                n = eval_merge<P>(a, s, nb, n, phase, ndist, timeout, lo, qr);
+                n = eval_merge<P, LOG>(a, s, nb, n, phase, ndist, timeout, lo, qr, qlog, qcnt);
             }
         }
         nexp_tot += hops;
+        if (LOG && lane == 0) a.elog_n[qi] = qcnt;
         if (a.mode == 0 && P != 0 && !a.exact) {
             // exact fp32 rerank of the best min(rerank * k, 64) live candidates
             u64 *rk = reinterpret_cast<u64 *>(s.stage);
@@ -639,7 +649,7 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec, u32 rerank,
-                          const u32 *nq_dev, bool exact_rows) {
+                          const u32 *nq_dev, bool exact_rows, u32 *elog, u32 *elog_n, u32 elog_cap) {
     if (nq == 0) return cudaSuccess;
     if (exact_rows) prec = 1;
     else if (mode != 0) prec = 0;
@@ -656,10 +666,16 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.exact = exact_rows ? 1u : 0u;
     a.wq = mode == 0 ? C_WORK2 : C_WORK;
     a.err = mode == 0 ? C_ERR_S : C_ERR;
+    a.elog = elog;
+    a.elog_n = elog_n;
+    a.elog_cap = elog_cap;
+    const bool log = elog != nullptr;
     // the rerank buffer (64 keys) lives in the stage
     if (prec != 0 && (size_t)a.stage_rows * a.rowb < 64 * 8) a.stage_rows = (64 * 8 + a.rowb - 1) / a.rowb;
-    const void *fn = prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>
-                                                                            : (const void *)search_kernel<0>;
+    const void *fn = log ? (prec == 1 ? (const void *)search_kernel<1, true> : prec == 2 ? (const void *)search_kernel<2, true>
+                                                                                      : (const void *)search_kernel<0, true>)
+                         : (prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>
+                                                                                   : (const void *)search_kernel<0>);
     size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -672,9 +688,87 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + a.wq, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    if (prec == 1) search_kernel<1><<<blocks, 128, smem, st>>>(a);
+    if (log) {
+        if (prec == 1) search_kernel<1, true><<<blocks, 128, smem, st>>>(a);
+        else if (prec == 2) search_kernel<2, true><<<blocks, 128, smem, st>>>(a);
+        else search_kernel<0, true><<<blocks, 128, smem, st>>>(a);
+    } else if (prec == 1) search_kernel<1><<<blocks, 128, smem, st>>>(a);
     else if (prec == 2) search_kernel<2><<<blocks, 128, smem, st>>>(a);
     else search_kernel<0><<<blocks, 128, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Evaluation count (diagnostic): for each query, the number of distinct ids
+// its BeamSearch evaluated during expansions, not counting the ids of its
+// initial beam (the seeds).  That is the size of the exact visited set of
+// the search minus the seeds: the evaluations the method itself makes,
+// whatever the kernel's lossy cache re-evaluates.  One block per query sorts
+// the query's log (bitonic, in shared memory) and the seed ids, then counts.
+// ---------------------------------------------------------------------------
+__device__ void block_bitonic_u32(u32 *v, u32 n) {   // n a power of two
+    for (u32 k = 2; k <= n; k <<= 1)
+        for (u32 j = k >> 1; j > 0; j >>= 1) {
+            for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+                const u32 l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const u32 x = v[i], y = v[l];
+                    if ((x > y) == up) { v[i] = y; v[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(512) eval_unique_kernel(const u32 *elog, const u32 *elog_n, u32 cap,
+                                                          const u64 *seed, u32 L, u32 n0, u64 *out) {
+    extern __shared__ u32 eu[];
+    const u32 qi = blockIdx.x;
+    const u32 cnt = elog_n[qi], n = min(cnt, cap);
+    u32 np = 1;
+    while (np < n) np <<= 1;
+    u32 ns = 1;
+    while (ns < n0) ns <<= 1;
+    u32 *v = eu, *sd = eu + np;
+    for (u32 i = threadIdx.x; i < np; i += blockDim.x) v[i] = i < n ? elog[(size_t)qi * cap + i] : NIL;
+    for (u32 i = threadIdx.x; i < ns; i += blockDim.x) sd[i] = i < n0 ? key_id(seed[(size_t)qi * L + i]) : NIL;
+    __syncthreads();
+    block_bitonic_u32(v, np);
+    block_bitonic_u32(sd, ns);
+    u32 uniq = 0;
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+        const u32 id = v[i];
+        if (id == NIL || (i > 0 && v[i - 1] == id)) continue;
+        u32 lo = 0, hi = ns;   // is id a seed?
+        while (lo < hi) {
+            const u32 mid = (lo + hi) >> 1;
+            if (sd[mid] < id) lo = mid + 1; else hi = mid;
+        }
+        uniq += !(lo < ns && sd[lo] == id);
+    }
+    for (int o = 16; o >= 1; o >>= 1) uniq += __shfl_xor_sync(FULL, uniq, o);
+    if ((threadIdx.x & 31) == 0 && uniq) atomicAdd(&out[1], (u64)uniq);
+    if (threadIdx.x == 0) {
+        atomicAdd(&out[0], (u64)cnt);
+        if (cnt > cap) atomicAdd(&out[2], 1ull);   // log overflow (cannot happen when cap = max_hops * R)
+    }
+}
+
+size_t eval_unique_smem(u32 cap, u32 L) {
+    u32 np = 1, ns = 1;
+    while (np < cap) np <<= 1;
+    while (ns < L) ns <<= 1;
+    return (size_t)(np + ns) * 4;
+}
+
+cudaError_t launch_eval_unique(const u32 *elog, const u32 *elog_n, u32 cap, const u64 *seed, u32 L, u32 n0, u32 nq,
+                               u64 *out, cudaStream_t st) {
+    if (nq == 0) return cudaSuccess;
+    const size_t smem = eval_unique_smem(cap, L);
+    cudaError_t e = cudaFuncSetAttribute(eval_unique_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    eval_unique_kernel<<<nq, 512, smem, st>>>(elog, elog_n, cap, seed, L, n0, out);
     return cudaGetLastError();
 }
 

@@ -183,21 +183,22 @@ def run_deletion_stress(w: W.Workload, frac: float = 0.10, beam: int = 128) -> d
 
 
 # ---- f3: concurrent query-vs-update latency ----------------------------------
-def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 2000, beam: int = 128) -> dict:
+def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 2000, beam: int = 128,
+                           extra: int = 4_000_000, n_fresh: int = 2_000_000) -> dict:
     """Latency of 1,000-query batches alone and while a writer thread churns the
     index (0.05% deletes + 0.05% inserts + Reclaim per round) on its own stream, in
     concurrent mode.  The anchor queries' exact top-10 never changes: deletes
     skip those ids, and inserts come from the same mixture shifted far from
     every anchor (+10^4 on each coordinate)."""
     import torch
-    idx, plan = _build(w, w.n_base + 4_000_000)
+    idx, plan = _build(w, w.n_base + extra)
     anchors = plan.queries[:batch]
     d_a = torch.from_numpy(anchors).cuda()
     gt, _ = idx.ground_truth(d_a, w.k)
     gt_np = gt.cpu().numpy().view(np.uint32)
     protected = np.unique(gt_np)
     mix = W.Mixture(w)
-    fresh = (mix.draw("inserts", 2_000_000) + 1.0e4).astype(np.float32)
+    fresh = (mix.draw("inserts", n_fresh) + 1.0e4).astype(np.float32)
     qs, us = torch.cuda.Stream(), torch.cuda.Stream()
 
     def batches(n):
@@ -226,7 +227,7 @@ def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 20
     stop = threading.Event()
     rounds = [0]
     rng = np.random.default_rng(w.seed + 3)
-    alive = np.zeros(w.n_base + 4_000_000, bool)
+    alive = np.zeros(w.n_base + extra, bool)
     alive[:w.n_base] = True
     keep = np.zeros_like(alive)
     keep[protected] = True
