@@ -846,7 +846,7 @@ cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const 
     a.xn = b.xn;
     a.out = b.bmin;
     a.err = b.err;
-    cudaError_t e = cudaFuncSetAttribute(gt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    cudaError_t e = smem_at_least((const void *)gt_tc_kernel, p.smem);
     if (e != cudaSuccess) return e;
     const u32 items = a.m_tiles * a.chunks;
     const u32 grid = std::min<u32>(items, (u32)num_sms);
@@ -942,7 +942,7 @@ cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u
     a.xn = b.en;
     a.out = b.keys;
     a.err = b.ctr + 1;
-    e = cudaFuncSetAttribute(gt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    e = smem_at_least((const void *)gt_tc_kernel, p.smem);
     if (e != cudaSuccess) return e;
     const u32 items = a.m_tiles * a.chunks;
     gt_tc_kernel<<<std::min<u32>(items, (u32)num_sms), TC_THREADS, p.smem, st>>>(ta, tb, a);

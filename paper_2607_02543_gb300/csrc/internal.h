@@ -10,6 +10,12 @@ struct SearchTuning {
     u32 seen_bits = 9;     // log2 of the evaluated-id cache slots
 };
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// limit is process-wide per kernel and only ever raised (under a lock), so a
+// thread launching with less never lowers it under another thread that has
+// just raised it for a larger launch.
+cudaError_t smem_at_least(const void *fn, size_t bytes);
+
 // search.cu
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
 // seed_kernel: top-L of the entry set per query into `seed` (nq x L); it

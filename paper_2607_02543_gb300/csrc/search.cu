@@ -637,7 +637,7 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
     const void *fn = prec == 1 ? (const void *)seed_kernel<1> : prec == 2 ? (const void *)seed_kernel<2>
                                                                           : (const void *)seed_kernel<0>;
     size_t smem = align_up((size_t)SEED_TILE * rowb, 16) + 8 * seed_warp_bytes(d.mp, L);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (nq + 7) / 8;
     if (prec == 1) seed_kernel<1><<<blocks, 256, smem, st>>>(a);
@@ -677,7 +677,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
                          : (prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>
                                                                                    : (const void *)search_kernel<0>);
     size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, smem);
@@ -766,7 +766,7 @@ cudaError_t launch_eval_unique(const u32 *elog, const u32 *elog_n, u32 cap, cons
                                u64 *out, cudaStream_t st) {
     if (nq == 0) return cudaSuccess;
     const size_t smem = eval_unique_smem(cap, L);
-    cudaError_t e = cudaFuncSetAttribute(eval_unique_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)eval_unique_kernel, smem);
     if (e != cudaSuccess) return e;
     eval_unique_kernel<<<nq, 512, smem, st>>>(elog, elog_n, cap, seed, L, n0, out);
     return cudaGetLastError();

@@ -844,7 +844,7 @@ cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_k
     size_t smem = W * wb;
     const void *fns[3] = {(const void *)prune_insert_kernel<0>, (const void *)prune_insert_kernel<1>, (const void *)prune_insert_kernel<2>};
     const void *fn = fns[gram_variant(a.gram, d.mp)];
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -987,7 +987,7 @@ cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_sta
     size_t smem = W * wb;
     const void *fns[3] = {(const void *)offer_fold_kernel<0>, (const void *)offer_fold_kernel<1>, (const void *)offer_fold_kernel<2>};
     const void *fn = fns[gram_variant(a.gram, d.mp)];
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1229,7 +1229,7 @@ cudaError_t launch_refine(const Dev &d, u32 first, u32 b, u32 mode, u32 max_cand
     size_t smem = warps * wb;
     const void *fns[3] = {(const void *)refine_kernel<0>, (const void *)refine_kernel<1>, (const void *)refine_kernel<2>};
     const void *fn = fns[gram_variant(a.gram, d.mp)];
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1455,7 +1455,7 @@ cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 ma
     const size_t wb = repk_warp_bytes(d.R, a.ns, d.mp, a.gram);
     const int W = warps_for(wb);
     size_t smem = W * wb;
-    cudaError_t e = cudaFuncSetAttribute(repair_k_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)repair_k_kernel, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_k_kernel, 32 * W, smem);
@@ -1675,7 +1675,7 @@ cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key,
     size_t smem = W * wb;
     const void *fns[3] = {(const void *)repair_fold_kernel<0>, (const void *)repair_fold_kernel<1>, (const void *)repair_fold_kernel<2>};
     const void *fn = fns[gram_variant(a.gram, d.mp)];
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -4,6 +4,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -258,6 +261,17 @@ __global__ void __launch_bounds__(1024) recycle_kernel(Dev d) {
     }
 }
 
+cudaError_t smem_at_least(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, size_t> set;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = set[fn];
+    if (bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 cudaError_t launch_recycle(const Dev &d, cudaStream_t st) {
     recycle_kernel<<<64, 1024, 0, st>>>(d);
     return cudaGetLastError();
@@ -489,7 +503,7 @@ cudaError_t launch_ground_truth(const Dev &d, u64 next_id, const float *q, u32 n
     if (nq == 0) return cudaSuccess;
     if (k > 32) return cudaErrorInvalidValue;
     size_t smem = (size_t)(GT_TILE + 8) * d.mp * 4;
-    cudaError_t e = cudaFuncSetAttribute(gt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least((const void *)gt_kernel, smem);
     if (e != cudaSuccess) return e;
     gt_kernel<<<(nq + 7) / 8, 256, smem, st>>>(d, next_id, q, nq, k, out_ids, out_dist, qsel);
     return cudaGetLastError();

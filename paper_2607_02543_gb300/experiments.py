@@ -232,7 +232,16 @@ def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 20
     keep = np.zeros_like(alive)
     keep[protected] = True
 
+    errors = []
+
     def writer():
+        try:
+            write_rounds()
+        except Exception as e:   # surfaced after join: a failed writer fails the run
+            errors.append(e)
+            stop.set()
+
+    def write_rounds():
         # the live set is tracked on the host from the ids each call returns;
         # 0.05% of the build per round keeps the live set's make-up steady
         # over the measured window
@@ -256,6 +265,8 @@ def run_concurrent_latency(w: W.Workload, batch: int = 1000, n_batches: int = 20
     stop.set()
     th.join()
     idx.set_concurrent(False)
+    if errors:
+        raise errors[0]
     return {"experiment": "concurrent_latency", "workload": w.name, "batch": batch, "beam": beam,
             "quiescent": {**pct(q_lat), "recall_at_10": float(np.mean(q_rec))},
             "concurrent": {**pct(c_lat), "recall_at_10": float(np.mean(c_rec)), "writer_rounds": rounds[0],
