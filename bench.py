@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--exact-steps", type=int, default=2,
                     help="extra rounds timed with fp32 BeamSearches gathering the BF16 copy, which holds every "
                          "row of the integer-valued workload exactly (0: skip); reported apart from the headline")
+    ap.add_argument("--graph-steps", type=int, default=5,
+                    help="extra rounds replayed from a recorded round graph (0: skip); reported apart")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-ops", type=int, default=2000,
                     help="cpu_baseline: deletes and inserts the oracle runs on the full graph (scaled to the round)")
@@ -607,7 +609,9 @@ def main():
     from paper_2607_02543_gb300 import Index, build as B
     B.build()
     main_rounds = args.warmup + args.steps * (1 if args.no_e2e else 2)
-    total_rounds = main_rounds + (1 + args.exact_steps if args.exact_steps > 0 else 0)
+    exact_rounds = 1 + args.exact_steps if args.exact_steps > 0 else 0
+    graph_rounds = 2 * (1 + args.graph_steps) if args.graph_steps > 0 else 0
+    total_rounds = main_rounds + exact_rounds + graph_rounds
     wr = W.dataclasses.replace(w, rounds=total_rounds)
     plan = W.make_plan(wr)
     n_entry = args.n_entry
@@ -844,6 +848,41 @@ def main():
                 "note": "rows gathered from the bf16 copy, which holds every stored row exactly; distances "
                         "bit-identical to the fp32 rows (tests/test_gpu_exact_rows.py)"}
         idx.set_exact_rows(False)
+    # the same rounds recorded once as a CUDA graph (etale_round_graph_*) and
+    # replayed with one launch each: round only (as `value`), then round +
+    # the query batch (as ms_per_step).  Each timed step includes the copy of
+    # its delete ids and rows into the recorded buffers.
+    graph_block = None
+    if args.graph_steps > 0:
+        r0 = main_rounds + exact_rounds
+        g_del = torch.empty((w.n_delete,), dtype=torch.int32, device=dev)
+        g_ins = torch.empty((w.n_insert, w.dim), dtype=torch.float32, device=dev)
+        graph_block = {"steps": args.graph_steps}
+        for name, with_q in (("round", False), ("round_and_queries", True)):
+            rgraph = idx.round_graph(g_del, g_ins, d_q if with_q else None, (out_ids, out_d) if with_q else None,
+                                     k=w.k, beam=beam)
+            evg = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(2)) for _ in range(1 + args.graph_steps)]
+            l0g = idx.kernel_launches()
+            for i in range(1 + args.graph_steps):      # the first replay is a warm-up
+                evg[i][0].record(stream)
+                g_del.copy_(d_del[r0], non_blocking=True)
+                g_ins.copy_(d_ins[r0], non_blocking=True)
+                rgraph.launch(stream)
+                evg[i][1].record(stream)
+                r0 += 1
+            rgraph.sync()
+            ms_g = [e[0].elapsed_time(e[1]) for e in evg[1:]]
+            graph_block[name + "_ms"] = float(np.mean(ms_g))
+            graph_block[name + "_launches_per_step"] = (idx.kernel_launches() - l0g) / (1 + args.graph_steps)
+            if with_q:
+                gtg, _ = idx.ground_truth(d_q, w.k, stream)
+                graph_block["recall_at_10"] = float(np.mean([
+                    len(set(u.tolist()) & set(v.tolist())) / w.k
+                    for u, v in zip(out_ids.cpu().numpy().view(np.uint32), gtg.cpu().numpy().view(np.uint32))]))
+                graph_block["qps"] = w.n_queries / ((graph_block["round_and_queries_ms"] - graph_block["round_ms"]) * 1e-3)
+            rgraph.close()
+        st_g = idx.stats()
+        graph_block["used_slabs_eq_live"] = st_g["used_slabs"] == st_g["live"]
     # max over ranks
     ms_round, ms_search = reduce_max([ms_round, ms_search], world, dev)
     st = idx.stats()
@@ -875,7 +914,7 @@ def main():
                             "rows_gathered": "bf16 copy (exact for every stored row)" if exact_copy else "fp32",
                             "kernel_ms": kernel_ms},
                "phase_ms_per_step": phases, "ground_truth": gt_block, "search_tuning": tuning,
-               "precision": prec_block, "exact_bf16_rows": exact_block,
+               "precision": prec_block, "exact_bf16_rows": exact_block, "round_graph": graph_block,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)

@@ -232,7 +232,8 @@ etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n);
  * slab count of Sec. 4.4, which equals live right after etale_reclaim
  * (Proposition 3) and live + tombstones between reclaims; free_slabs and
  * retired_slabs are the two stacks of Sec. 3.3.  Reads the device counters
- * on a private stream (never waits for the caller's streams).              */
+ * on a private stream (never waits for the caller's streams, except for the
+ * last round-graph launch when one ran since the counts were read).        */
 etale_status etale_stats(etale_index *idx, etale_stats_t *out);
 
 /* Resolved configuration of an index.                                      */
@@ -321,6 +322,52 @@ etale_status etale_search_graph_launch(etale_search_graph *g, void *stream);
 /* Synchronise `stream` and report device-side errors of earlier replays.    */
 etale_status etale_search_graph_check(etale_search_graph *g, void *stream);
 etale_status etale_search_graph_destroy(etale_search_graph *g);
+
+/* ---- recorded churn rounds (deployment support; the paper has none) ---- */
+/* One churn round recorded as a CUDA graph and replayed with one launch: a
+ * delete batch with repair (Algorithm 3), one insert sub-batch with its
+ * reverse offers and refine pass (Algorithm 2), a Reclaim (Algorithm 4) and,
+ * if nq > 0, a query batch, in the order and with the results of the eager
+ * calls etale_delete, etale_insert, etale_reclaim and etale_search.  Each
+ * recorded kernel is still its own launch, run after the previous one has
+ * terminated, with the recycle step between publishing launches
+ * (Definition 2, Lemma 1).  The kernels read next_id, the first new id, the
+ * live count and |E| from device memory, so the host neither reads nor waits
+ * between or within replays.
+ *
+ * Buffers (DEVICE, caller-owned, read at every launch, rewritten by the
+ * caller between launches in stream order):
+ *   del_ids    n_del ids to delete; ETALE_NIL entries, ids never inserted
+ *              and ids already deleted are no-ops (as in etale_delete);
+ *   ins_vecs   n_ins x dim rows, inserted as ids [next_id, next_id + n_ins);
+ *   queries    nq x dim rows; out_ids / out_dists nq x k (as etale_search,
+ *              fp32 or the search precision in force at recording).
+ * n_del, n_ins or nq may be 0.
+ *
+ * Conditions, checked at recording and at every launch (EINVAL, ECAPACITY
+ * or ENOMEM; nothing is launched): not in concurrent mode; the insert is
+ * one sub-batch (n_ins <= max_batch and <= the live count once the deletes
+ * are made); the ids left cover n_ins; the slab pool covers a round.  With
+ * tensor-core seeding the live count must also stay >= n_entry.  The host's
+ * counts (live, tombstones, |E|, free slabs) are read back by
+ * etale_round_graph_sync, or by the next call that needs them (any eager
+ * call on the index waits for the last replay first).
+ *
+ * The graph records the addresses of index scratch buffers: while it
+ * lives, an eager call that would need one of them larger fails with
+ * ENOMEM.  Destroy every round graph before etale_destroy (which refuses
+ * otherwise).                                                              */
+typedef struct etale_round_graph etale_round_graph;
+etale_status etale_round_graph_create(etale_index *idx, uint32_t n_del, const uint32_t *del_ids, uint32_t n_ins,
+                                      const float *ins_vecs, uint32_t nq, uint32_t k, uint32_t beam,
+                                      const float *queries, uint32_t *out_ids, float *out_dists,
+                                      etale_round_graph **out);
+/* Enqueue one round on `stream` (asynchronous; no host synchronisation).   */
+etale_status etale_round_graph_launch(etale_round_graph *g, void *stream);
+/* Wait for the last launch, read the index's counts back, and report
+ * device-side errors of the replays since the last sync.                   */
+etale_status etale_round_graph_sync(etale_round_graph *g);
+etale_status etale_round_graph_destroy(etale_round_graph *g);
 
 /* How the last etale_ground_truth call ran: *path 0 CUDA cores, 1 tensor
  * cores on bf16-exact data, 2 tensor cores with the hi/lo split;

@@ -58,7 +58,8 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
            "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
-           "etale_load", "etale_search_eval_count"]
+           "etale_load", "etale_search_eval_count", "etale_round_graph_create",
+           "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -108,6 +109,10 @@ def load(path: str = LIB_PATH):
             "etale_selftest_bounded_wait": ([U32, P], C.c_int),
             "etale_ground_truth_info": ([P, P, P], C.c_int),
             "etale_save": ([P, C.c_char_p, P], C.c_int),
+            "etale_round_graph_create": ([P, U32, P, U32, P, U32, U32, U32, P, P, P, C.POINTER(P)], C.c_int),
+            "etale_round_graph_launch": ([P, P], C.c_int),
+            "etale_round_graph_sync": ([P], C.c_int),
+            "etale_round_graph_destroy": ([P], C.c_int),
             "etale_search_eval_count": ([P, P, U64, U32, U32, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64), P],
                                         C.c_int),
             "etale_load": ([C.c_char_p, C.POINTER(Config), U64, C.POINTER(P)], C.c_int),
@@ -276,6 +281,20 @@ class Index:
                                                        _ptr(out_ids), _ptr(out_dists), _ptr(nq_dev), C.byref(g)))
         return SearchGraph(self, g)
 
+    def round_graph(self, del_ids, ins_vecs, queries=None, out=None, k: int = 10, beam: int = 64) -> "RoundGraph":
+        """Record one churn round over DEVICE tensors: del_ids (int32/uint32, n_del),
+        ins_vecs (n_ins x dim), optional queries with out = (ids, dists)."""
+        nul = C.c_void_p(None)
+        nd = 0 if del_ids is None else del_ids.shape[0]
+        ni = 0 if ins_vecs is None else ins_vecs.shape[0]
+        nq = 0 if queries is None else queries.shape[0]
+        oi, od = out if out is not None else (None, None)
+        g = C.c_void_p()
+        self._check(self.lib.etale_round_graph_create(
+            self.h, nd, _ptr(del_ids) if nd else nul, ni, _ptr(ins_vecs) if ni else nul, nq, k, beam,
+            _ptr(queries) if nq else nul, _ptr(oi) if nq else nul, _ptr(od) if nq else nul, C.byref(g)))
+        return RoundGraph(self, g, (del_ids, ins_vecs, queries, oi, od))
+
     def set_concurrent(self, on: bool = True):
         """Let one search thread and one update thread overlap on the device."""
         self._check(self.lib.etale_set_concurrent(self.h, int(on)))
@@ -396,23 +415,26 @@ class SearchGraph:
         except Exception:
             pass
 
-    # --- snapshots -----------------------------------------------------------
-    def save(self, path: str, stream=None):
-        """etale_save: write the index state to `path` (format in include/etale.h)."""
-        self._check(self.lib.etale_save(self.h, os.fsencode(path), _stream(stream)))
 
-    @classmethod
-    def load(cls, path: str, capacity: int = 0) -> "Index":
-        """etale_load with the saved configuration; capacity 0 keeps the saved one."""
-        lib = load()
-        h = C.c_void_p()
-        st = lib.etale_load(os.fsencode(path), None, capacity, C.byref(h))
-        if st:
-            raise EtaleError(st, lib.etale_last_error(None).decode())
-        self = cls.__new__(cls)
-        self.lib, self.h = lib, h
-        s = Stats()
-        self._check(lib.etale_stats(h, C.byref(s)))
-        self.dim, self.degree, self.capacity = s.dim, s.degree, s.capacity
-        self.metric = "l2" if s.metric == 0 else "ip"
-        return self
+class RoundGraph:
+    """A recorded churn round (see etale_round_graph_create)."""
+
+    def __init__(self, index: Index, handle, buffers):
+        self.index, self.h, self._buffers = index, handle, buffers
+
+    def launch(self, stream=None):
+        self.index._check(self.index.lib.etale_round_graph_launch(self.h, _stream(stream)))
+
+    def sync(self):
+        self.index._check(self.index.lib.etale_round_graph_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.index.lib.etale_round_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

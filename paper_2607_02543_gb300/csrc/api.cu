@@ -2,7 +2,9 @@
 // orchestration and the host side of the epoch discipline.  Each phase is a
 // separate launch on the caller's stream and every phase that publishes is
 // followed by the recycle launch (Sec. 3.3, Lemma 1, Definition 2).
+#include <algorithm>
 #include <atomic>
+#include <initializer_list>
 #include <mutex>
 #include <cstdarg>
 #include <cstdio>
@@ -29,10 +31,13 @@ thread_local std::string t_last_error = "no error";
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    int pins = 0;   // round graphs that recorded this buffer's address
 };
 
+// A buffer a round graph recorded is never reallocated while the graph lives.
 bool grow(DevBuf &b, size_t bytes) {
     if (b.bytes >= bytes) return true;
+    if (b.pins) return false;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -85,6 +90,10 @@ struct etale_index {
     u32 search_prec = 0;
     bool rows_exact = true;         // every ingested row's bf16 copy is exact (C_INEXACT == 0)
     u32 *nent_dev = nullptr;        // |E| in device memory
+    u64 *rs = nullptr;              // round state (RS_* words) of recorded rounds
+    int round_graphs = 0;           // live round graphs
+    bool graph_pending = false;     // a round graph ran since the host state was read
+    cudaEvent_t graph_ev = nullptr; // recorded after the last round-graph launch
     u64 *host_ctr = nullptr;   // pinned mirror
     // scratch
     DevBuf stage, qpad, out_ids, out_dist, exp_keys, exp_count, F_id, F_rho, F_n;
@@ -149,6 +158,7 @@ struct etale_index {
         // resident warp's batch many times over (else one, as Algorithm 1)
         d.slab_batch = free_lb >= (u64)num_sms * 64 * 8 * 2 ? 8u : 1u;
         d.nent_dev = nent_dev;
+        d.rs = nullptr;
         return d;
     }
 
@@ -238,6 +248,35 @@ etale_status check_device_errors(etale_index *idx, cudaStream_t st) {
         if (e & ERR_CAS) return idx->fail(ETALE_EINTERNAL, "a publication lost a CAS that had no competitor");
         if (e & ERR_OVERFLOW) return idx->fail(ETALE_EINTERNAL, "a candidate list overflowed its bound");
         return idx->fail(ETALE_EINTERNAL, "device error bits 0x%llx", e);
+    }
+    return ETALE_OK;
+}
+
+// After round-graph launches the device holds the live count, the deletions
+// made and the entry-set size; read them back before a call that uses the
+// host's copies (waits for the last launch).
+etale_status settle(etale_index *idx) {
+    if (!idx->graph_pending) return ETALE_OK;
+    CK(cudaEventSynchronize(idx->graph_ev), "wait for the round graph");
+    u64 rs[RS_N];
+    u32 nent = 0;
+    CK(cudaMemcpy(rs, idx->rs, sizeof rs, cudaMemcpyDeviceToHost), "read round state");
+    CK(cudaMemcpy(&nent, idx->nent_dev, 4, cudaMemcpyDeviceToHost), "read entry count");
+    CK(cudaMemcpy(idx->host_ctr, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost), "read counters");
+    CK(cudaMemset(idx->rs + RS_DELETED, 0, sizeof(u64)), "reset round state");
+    idx->graph_pending = false;
+    idx->live = rs[RS_LIVE];
+    idx->reclaimed += idx->tombs + rs[RS_DELETED];
+    idx->tombs = 0;
+    idx->n_entries = nent;
+    idx->free_lb = idx->host_ctr[C_FREE];
+    const u64 e = idx->host_ctr[C_ERR] | idx->host_ctr[C_ERR_S];
+    if (e) {
+        CK(cudaMemset(idx->ctr + C_ERR, 0, sizeof(u64)), "clear error");
+        CK(cudaMemset(idx->ctr + C_ERR_S, 0, sizeof(u64)), "clear error");
+        if (e & ERR_TIMEOUT) return idx->fail(ETALE_ETIMEOUT, "round graph: a bounded device wait gave up");
+        if (e & ERR_NOMEM) return idx->fail(ETALE_ENOMEM, "round graph: slab pool exhausted during a launch");
+        return idx->fail(ETALE_EINTERNAL, "round graph: device error bits 0x%llx", e);
     }
     return ETALE_OK;
 }
@@ -414,6 +453,19 @@ etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t 
     }
     g_kernel_launches++;
     return recycle(idx, st);
+}
+
+bool size_delete_scratch(etale_index *idx, u64 n) {
+    const u64 R = idx->R, slots = n * R;
+    return grow(idx->del_ids, n * 4) && grow(idx->del_vals, n * 4) && grow(idx->del_ids2, n * 4) &&
+           grow(idx->del_vals2, n * 4) && grow(idx->del_ok, n * 4) && grow(idx->del_scan, n * 4) &&
+           grow(idx->dt, n * 4) && grow(idx->pair_key, slots * 4) && grow(idx->pair_val, slots * 4) &&
+           grow(idx->pair_key2, slots * 4) && grow(idx->pair_val2, slots * 4) &&
+           grow(idx->pair_K, slots * R * 8) && grow(idx->pair_Kn, slots * 4) &&
+           grow(idx->pair_flags, slots * 4) && grow(idx->pair_scan, slots * 4) &&
+           grow(idx->pair_seg, (slots + 1) * 4) && grow(idx->counts, 64) &&
+           grow(idx->sort_scr, sort_scratch_elems((u32)std::max<u64>(slots, n)) * 4) &&
+           grow(idx->scan_scr, scan_scratch_elems((u32)std::max<u64>(slots, n)) * 4);
 }
 
 etale_status size_batch_scratch(etale_index *idx, u64 b) {
@@ -650,7 +702,10 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
               cudaMallocHost(&idx->host_ctr_st, C_NCTR * sizeof(u64)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&idx->stat_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&idx->search_ev, cudaEventDisableTiming) == cudaSuccess &&
-              cudaMalloc(&idx->nent_dev, 16) == cudaSuccess && cudaMemset(idx->nent_dev, 0, 16) == cudaSuccess;
+              cudaMalloc(&idx->nent_dev, 16) == cudaSuccess && cudaMemset(idx->nent_dev, 0, 16) == cudaSuccess &&
+              cudaMalloc(&idx->rs, RS_N * sizeof(u64)) == cudaSuccess &&
+              cudaMemset(idx->rs, 0, RS_N * sizeof(u64)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&idx->graph_ev, cudaEventDisableTiming) == cudaSuccess;
     idx->mb = (idx->mp + 7) / 8 * 8;
     idx->m8 = (idx->mp + 15) / 16 * 16;
     if (ok && (cfg.copies & 1)) ok = cudaMalloc(&idx->xb, (size_t)capacity * idx->mb * 2) == cudaSuccess;
@@ -697,9 +752,14 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
 
 etale_status etale_destroy(etale_index *idx) {
     if (!idx) return ETALE_OK;
+    if (idx->round_graphs) {
+        t_last_error = "destroy the index's round graphs first";
+        return ETALE_EINVAL;
+    }
     cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
     cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
-    cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s); cudaFree(idx->nent_dev);
+    cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s); cudaFree(idx->nent_dev); cudaFree(idx->rs);
+    if (idx->graph_ev) cudaEventDestroy(idx->graph_ev);
     if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
     if (idx->host_ctr_s) cudaFreeHost(idx->host_ctr_s);
     if (idx->host_ctr_st) cudaFreeHost(idx->host_ctr_st);
@@ -724,6 +784,10 @@ etale_status etale_destroy(etale_index *idx) {
 
 etale_status etale_insert(etale_index *idx, const float *vecs, uint64_t n, uint32_t *out_ids, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (n == 0) return ETALE_OK;
     if (!vecs) return idx->fail(ETALE_EINVAL, "vecs is NULL");
     if (idx->next_id + n > idx->capacity)
@@ -787,18 +851,14 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
     if (!ids) return idx->fail(ETALE_EINVAL, "ids is NULL");
     if (n > 0x7FFFFFFFull / MAX_R) return idx->fail(ETALE_EINVAL, "delete batch too large");
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        etale_status s0 = settle(idx);
+        if (s0 != ETALE_OK) return s0;
+    }
     const u32 R = idx->R;
     const u64 slots = n * R;
-    bool ok = grow(idx->del_ids, n * 4) && grow(idx->del_vals, n * 4) && grow(idx->del_ids2, n * 4) &&
-              grow(idx->del_vals2, n * 4) && grow(idx->del_ok, n * 4) && grow(idx->del_scan, n * 4) &&
-              grow(idx->dt, n * 4) && grow(idx->pair_key, slots * 4) && grow(idx->pair_val, slots * 4) &&
-              grow(idx->pair_key2, slots * 4) && grow(idx->pair_val2, slots * 4) &&
-              grow(idx->pair_K, slots * R * 8) && grow(idx->pair_Kn, slots * 4) &&
-              grow(idx->pair_flags, slots * 4) && grow(idx->pair_scan, slots * 4) &&
-              grow(idx->pair_seg, (slots + 1) * 4) && grow(idx->counts, 64) &&
-              grow(idx->sort_scr, sort_scratch_elems((u32)std::max<u64>(slots, n)) * 4) &&
-              grow(idx->scan_scr, scan_scratch_elems((u32)std::max<u64>(slots, n)) * 4);
-    if (!ok) return idx->fail(ETALE_ENOMEM, "scratch allocation (delete batch of %llu)", (unsigned long long)n);
+    if (!size_delete_scratch(idx, n))
+        return idx->fail(ETALE_ENOMEM, "scratch allocation (delete batch of %llu)", (unsigned long long)n);
     {
         etale_status sb = writer_begin(idx, st);
         if (sb != ETALE_OK) return sb;
@@ -890,6 +950,10 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
 
 etale_status etale_reclaim(etale_index *idx, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     etale_status s = writer_begin(idx, st);
     if (s != ETALE_OK) return s;
@@ -992,6 +1056,10 @@ static etale_status ground_truth_run(etale_index *idx, const Dev &d, const float
 static etale_status search_common(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
                                   uint32_t *out_ids, float *out_dists, void *stream, bool exact) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (nq == 0) return ETALE_OK;
     if (!queries || !out_ids || !out_dists || k == 0) return idx->fail(ETALE_EINVAL, "null buffer or k == 0");
     if (exact && k > 32) return idx->fail(ETALE_EINVAL, "ground truth supports k <= 32");
@@ -1056,6 +1124,10 @@ etale_status etale_search(etale_index *idx, const float *queries, uint64_t nq, u
 etale_status etale_search_eval_count(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
                                      uint64_t *n_eval, uint64_t *n_unique, uint64_t *n_expand, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (!queries || !n_eval || !n_unique || !n_expand || k == 0 || nq == 0)
         return idx->fail(ETALE_EINVAL, "null argument, k == 0 or nq == 0");
     const u32 L = beam > k ? beam : k;
@@ -1114,6 +1186,10 @@ etale_status etale_ground_truth(etale_index *idx, const float *queries, uint64_t
 etale_status etale_export_graph(etale_index *idx, uint64_t n, uint8_t *deleted, uint8_t *has_slab, uint8_t *degree,
                                 uint32_t *nbr_ids, float *nbr_rho, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (n > idx->next_id) return idx->fail(ETALE_EINVAL, "n exceeds next_id");
     if (n == 0) return ETALE_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1136,6 +1212,10 @@ etale_status etale_export_graph(etale_index *idx, uint64_t n, uint8_t *deleted, 
 
 etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n) {
     if (!idx || !out || !n) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     *n = idx->n_entries;
     if (idx->n_entries == 0) return ETALE_OK;
     cudaError_t e = cudaMemcpy(out, idx->entries, (size_t)idx->n_entries * 4, cudaMemcpyDefault);
@@ -1144,6 +1224,10 @@ etale_status etale_get_entries(etale_index *idx, uint32_t *out, uint32_t *n) {
 
 etale_status etale_stats(etale_index *idx, etale_stats_t *o) {
     if (!idx || !o) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     // a private non-blocking stream: reading the counters never waits for,
     // or orders against, the caller's streams
     cudaError_t e = cudaMemcpyAsync(idx->host_ctr_st, idx->ctr, C_NCTR * sizeof(u64), cudaMemcpyDeviceToHost,
@@ -1207,6 +1291,10 @@ etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint
 etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
                                    etale_tuning *out, uint32_t n_out, uint32_t *n_tried, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (n_tried) *n_tried = 0;
     if (!queries || nq == 0 || k == 0 || !is_device_ptr(queries))
         return idx->fail(ETALE_EINVAL, "autotune needs a non-empty DEVICE query batch");
@@ -1265,6 +1353,10 @@ etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32
                                        const float *queries, uint32_t *out_ids, float *out_dists,
                                        const uint32_t *nq_dev, etale_search_graph **out) {
     if (!idx || !out) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     *out = nullptr;
     const u32 L = beam > k ? beam : k;
     if (nq_max == 0 || k == 0 || L > 256 || !nq_dev)
@@ -1342,6 +1434,344 @@ etale_status etale_search_graph_destroy(etale_search_graph *g) {
     return ETALE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Round graphs: one churn round (delete with repair, insert with refine,
+// reclaim, and optionally a query batch) recorded once as a CUDA graph and
+// replayed with one launch.  Sizes that change from round to round (next_id,
+// the first new id, the live count, |E|) are read by the kernels from the
+// index's device round state; the host never reads or waits in between.
+// ---------------------------------------------------------------------------
+struct etale_round_graph {
+    etale_index *idx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    u32 n_del = 0, n_ins = 0, nq = 0, k = 0, L = 0;
+    const u32 *del_ids = nullptr;
+    const float *ins = nullptr, *queries = nullptr;
+    u32 *out_ids = nullptr;
+    float *out_dists = nullptr;
+    float *ins_q = nullptr, *q_pad = nullptr;   // padded rows, fixed addresses
+    u64 *q_seed = nullptr;
+    bool seed_tc = false;
+    u64 kernels = 0;                             // kernel nodes per replay
+    u64 live_lb = 0;                             // host lower bound of the live count
+    std::vector<DevBuf *> pinned;
+};
+
+namespace {
+
+// Entry set from the device's live count (a recorded round).
+cudaError_t rg_entries(etale_index *idx, etale_round_graph *g, const Dev &dg, cudaStream_t st) {
+    const u64 cap = idx->capacity;
+    ScanScratch ss;
+    scan_scratch_carve(ss, as<u32>(idx->live_scan_scr), (u32)cap);
+    cudaError_t e = launch_live_flags(dg, cap, as<u32>(idx->live_flags), st);
+    if (e == cudaSuccess) e = exclusive_scan(as<u32>(idx->live_flags), as<u32>(idx->live_rank), (u32)cap, ss, st);
+    if (e == cudaSuccess)
+        e = launch_entries_select(dg, cap, as<u32>(idx->live_flags), as<u32>(idx->live_rank), 0, idx->cfg.n_entry, st);
+    if (e == cudaSuccess && g->seed_tc) {
+        const SeedTcPlan p = seed_tc_plan(idx->dim, idx->cfg.n_entry, 0);
+        e = launch_seed_tc_entries(dg, idx->cfg.n_entry, p, idx->seed_bufs(), st);
+    }
+    return e;
+}
+
+cudaError_t rg_seed(etale_index *idx, etale_round_graph *g, const Dev &dg, const float *q, u32 nq, u32 L, u64 *seed,
+                    cudaStream_t st, u32 prec = 0) {
+    if (prec) return launch_seed(dg, q, nq, L, seed, st, prec);
+    if (g->seed_tc && nq >= 32) {
+        const SeedTcPlan p = seed_tc_plan(idx->dim, idx->cfg.n_entry, nq);
+        return launch_seed_tc(dg, q, nq, idx->cfg.n_entry, L, seed, p, idx->seed_bufs(), idx->num_sms, st);
+    }
+    return launch_seed(dg, q, nq, L, seed, st, 0);
+}
+
+cudaError_t rg_offers(etale_index *idx, const Dev &dg, u32 nslots, cudaStream_t st) {
+    Offers of{as<u32>(idx->of_key), as<u32>(idx->of_val), as<u32>(idx->of_key2), as<u32>(idx->of_val2),
+              as<u32>(idx->of_src), as<float>(idx->of_rho), nslots};
+    u64 *seg_count = as<u64>(idx->counts) + 0;
+    cudaError_t e = cudaSuccess;
+    if (idx->cfg.mode == ETALE_MODE_LOCKFREE) {
+        e = launch_offer_fold(dg, of, nullptr, seg_count, idx->cfg.cas_budget, idx->num_sms, st, 0, nslots);
+    } else {
+        SortScratch ss;
+        sort_scratch_carve(ss, as<u32>(idx->sort_scr), nslots);
+        ScanScratch sc;
+        scan_scratch_carve(sc, as<u32>(idx->scan_scr), nslots);
+        e = radix_sort_pairs(of.key, of.val, of.key_alt, of.val_alt, nslots, bits_for(idx->capacity), ss, st);
+        if (e == cudaSuccess)
+            e = make_segments(of.key, nslots, (u32)idx->capacity, as<u32>(idx->seg_flags), as<u32>(idx->seg_scan),
+                              as<u32>(idx->seg_start), seg_count, sc, st);
+        if (e == cudaSuccess)
+            e = launch_offer_fold(dg, of, as<u32>(idx->seg_start), seg_count, 0, idx->num_sms, st);
+    }
+    if (e == cudaSuccess) e = launch_recycle(dg, st);
+    return e;
+}
+
+// The phase sequence of one round, as the eager calls run it for a delete
+// batch of n_del ids (NIL entries are no-ops), one insert sub-batch of n_ins
+// rows and a Reclaim, then the query batch.
+cudaError_t rg_enqueue(etale_index *idx, etale_round_graph *g, cudaStream_t st) {
+    Dev dg = idx->dev();
+    dg.rs = idx->rs;
+    const u32 R = idx->R;
+    const u64 cap = idx->capacity;
+    cudaError_t e = cudaSuccess;
+    if (g->n_del) {
+        const u32 n = g->n_del, slots = n * R;
+        SortScratch ss;
+        sort_scratch_carve(ss, as<u32>(idx->sort_scr), std::max(slots, n));
+        ScanScratch sc;
+        scan_scratch_carve(sc, as<u32>(idx->scan_scr), std::max(slots, n));
+        u64 *n_dt = as<u64>(idx->counts) + 1, *seg_count = as<u64>(idx->counts) + 2;
+        const u32 invalid = (u32)cap;
+        e = cudaMemcpyAsync(idx->del_ids.p, g->del_ids, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = launch_fill_offer_keys(as<u32>(idx->del_vals2), as<u32>(idx->del_vals), n, 0, st);
+        if (e == cudaSuccess)
+            e = radix_sort_pairs(as<u32>(idx->del_ids), as<u32>(idx->del_vals), as<u32>(idx->del_ids2),
+                                 as<u32>(idx->del_vals2), n, 32, ss, st);
+        if (e == cudaSuccess) e = launch_tombstone(dg, as<u32>(idx->del_ids), n, cap, as<u32>(idx->del_ok), st);
+        if (e == cudaSuccess) e = exclusive_scan(as<u32>(idx->del_ok), as<u32>(idx->del_scan), n, sc, st);
+        if (e == cudaSuccess)
+            e = launch_compact_ok(as<u32>(idx->del_ids), as<u32>(idx->del_ok), as<u32>(idx->del_scan), n,
+                                  as<u32>(idx->dt), n_dt, st);
+        if (e == cudaSuccess) e = launch_round_add(idx->rs, RS_DELETED, n_dt, st);
+        if (e == cudaSuccess) e = launch_fill_offer_keys(as<u32>(idx->pair_key), as<u32>(idx->pair_val), slots, invalid, st);
+        if (e == cudaSuccess)
+            e = launch_repair_k(dg, as<u32>(idx->dt), n_dt, n, as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                                as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), idx->num_sms, st);
+        if (idx->cfg.mode == ETALE_MODE_LOCKFREE) {
+            if (e == cudaSuccess)
+                e = launch_repair_fold(dg, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                                       as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), nullptr, seg_count, slots,
+                                       idx->cfg.cas_budget, idx->num_sms, st, 0);
+        } else {
+            if (e == cudaSuccess)
+                e = radix_sort_pairs(as<u32>(idx->pair_key), as<u32>(idx->pair_val), as<u32>(idx->pair_key2),
+                                     as<u32>(idx->pair_val2), slots, bits_for(cap), ss, st);
+            if (e == cudaSuccess)
+                e = make_segments(as<u32>(idx->pair_key), slots, invalid, as<u32>(idx->pair_flags),
+                                  as<u32>(idx->pair_scan), as<u32>(idx->pair_seg), seg_count, sc, st);
+            if (e == cudaSuccess)
+                e = launch_repair_fold(dg, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
+                                       as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), as<u32>(idx->pair_seg),
+                                       seg_count, slots, 0, idx->num_sms, st);
+        }
+        if (e == cudaSuccess) e = launch_recycle(dg, st);
+    }
+    if (g->n_ins && e == cudaSuccess) {
+        const u32 b = g->n_ins, Lb = idx->cfg.build_beam;
+        const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * Lb;
+        Offers of{as<u32>(idx->of_key), as<u32>(idx->of_val), as<u32>(idx->of_key2), as<u32>(idx->of_val2),
+                  as<u32>(idx->of_src), as<float>(idx->of_rho), b * R};
+        e = launch_round_advance(idx->rs, b, st);
+        if (e == cudaSuccess) e = launch_ingest(idx->x, idx->mp, g->ins, idx->dim, b, st, nullptr, idx->rs + RS_FIRST);
+        if (e == cudaSuccess) e = launch_ingest(g->ins_q, idx->mp, g->ins, idx->dim, b, st);
+        if (e == cudaSuccess) e = launch_ingest_copies(dg, 0, b, st);
+        if (e == cudaSuccess) e = rg_seed(idx, g, dg, g->ins_q, b, Lb, as<u64>(idx->seed), st);
+        if (e == cudaSuccess)
+            e = launch_search(dg, g->ins_q, b, Lb, H, 1, 0, nullptr, nullptr, as<u64>(idx->exp_keys),
+                              as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, Lb, idx->tune), idx->num_sms,
+                              st, 0, 4, nullptr, false);
+        if (e == cudaSuccess)
+            e = launch_prune_insert(dg, 0, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
+                                    as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st);
+        if (e == cudaSuccess) e = launch_recycle(dg, st);
+        if (e == cudaSuccess) e = rg_offers(idx, dg, b * R, st);
+        const u32 rmode = idx->cfg.refine == 1 ? 0 : idx->cfg.refine;
+        if (rmode && e == cudaSuccess) {
+            const size_t sb = refine_spill_bytes(dg, idx->cfg.max_cand, idx->num_sms);
+            e = launch_refine(dg, 0, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st,
+                              static_cast<char *>(idx->refine_spill.p), sb);
+            if (e == cudaSuccess) e = launch_recycle(dg, st);
+            if (e == cudaSuccess) e = rg_offers(idx, dg, b * R, st);
+        }
+        if (e == cudaSuccess) e = rg_entries(idx, g, dg, st);
+    }
+    // Reclaim: entry set first, then compaction and phase 2
+    if (e == cudaSuccess) e = rg_entries(idx, g, dg, st);
+    if (e == cudaSuccess) e = launch_tomb_bits(dg, cap, as<u32>(idx->tomb_bits), st);
+    if (e == cudaSuccess) e = launch_compact(dg, cap, as<u32>(idx->tomb_bits), st);
+    if (e == cudaSuccess) e = launch_recycle(dg, st);
+    if (e == cudaSuccess) e = launch_reclaim_tombstones(dg, cap, st);
+    if (e == cudaSuccess) e = launch_recycle(dg, st);
+    if (g->nq && e == cudaSuccess) {
+        const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * g->L;
+        e = launch_ingest(g->q_pad, idx->mp, g->queries, idx->dim, g->nq, st);
+        if (e == cudaSuccess) e = rg_seed(idx, g, dg, g->q_pad, g->nq, g->L, g->q_seed, st, idx->search_prec);
+        if (e == cudaSuccess)
+            e = launch_search(dg, g->q_pad, g->nq, g->L, H, 0, g->k, g->out_ids, g->out_dists, nullptr, nullptr,
+                              g->q_seed, fit_tuning(idx, g->L, idx->tune), idx->num_sms, st, idx->search_prec,
+                              idx->cfg.rerank, nullptr, false);
+    }
+    return e;
+}
+
+// Conditions under which a replay equals the eager calls: one insert
+// sub-batch (n_ins <= live, <= max_batch), an entry set at its full size
+// when seeding on tensor cores, ids left, and a pool that covers the round.
+etale_status rg_check(etale_index *idx, etale_round_graph *g) {
+    const u64 live_ins = g->live_lb > g->n_del ? g->live_lb - g->n_del : 0;   // live when the insert runs
+    if (g->n_ins && (live_ins < g->n_ins || g->n_ins > idx->cfg.max_batch))
+        return idx->fail(ETALE_EINVAL, "round graph: the insert would not be one sub-batch (live may be %llu)",
+                         (unsigned long long)live_ins);
+    if (g->seed_tc && live_ins < idx->cfg.n_entry)
+        return idx->fail(ETALE_EINVAL, "round graph: the live set may fall below n_entry; record a new graph");
+    if (idx->next_id + g->n_ins > idx->capacity) return idx->fail(ETALE_ECAPACITY, "round graph: id budget exhausted");
+    // at a call boundary every id holds at most one slab and nothing is
+    // retired; a phase pops at most two slabs per publication it attempts
+    // (lock-free retries are rare; the device flags an empty pool) and the
+    // compaction at most one per live node
+    const u64 nid = idx->next_id + g->n_ins;
+    const u64 need = nid + std::max<u64>({2ull * g->n_del * idx->R, 2ull * g->n_ins * (idx->R + 1), nid});
+    if (idx->pool < need)
+        return idx->fail(ETALE_ENOMEM, "round graph: the slab pool may not cover a round");
+    return ETALE_OK;
+}
+
+}  // namespace
+
+etale_status etale_round_graph_create(etale_index *idx, uint32_t n_del, const uint32_t *del_ids, uint32_t n_ins,
+                                      const float *ins_vecs, uint32_t nq, uint32_t k, uint32_t beam,
+                                      const float *queries, uint32_t *out_ids, float *out_dists,
+                                      etale_round_graph **out) {
+    if (!idx || !out) return ETALE_EINVAL;
+    *out = nullptr;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
+    if (idx->concurrent) return idx->fail(ETALE_EINVAL, "round graphs are not available in concurrent mode");
+    if ((n_del && !is_device_ptr(del_ids)) || (n_ins && !is_device_ptr(ins_vecs)) ||
+        (nq && (!is_device_ptr(queries) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))))
+        return idx->fail(ETALE_EINVAL, "round graph buffers must be device pointers");
+    const u32 L = beam > k ? beam : k;
+    if (nq && (k == 0 || L > 256)) return idx->fail(ETALE_EINVAL, "round graph queries need k > 0 and beam <= 256");
+    if (nq && idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
+    if ((u64)n_del * idx->R > 0x7FFFFFFFull || (u64)n_ins * idx->R > 0x7FFFFFFFull)
+        return idx->fail(ETALE_EINVAL, "round graph batch too large");
+    etale_round_graph *g = new etale_round_graph();
+    g->idx = idx;
+    g->n_del = n_del; g->n_ins = n_ins; g->nq = nq; g->k = k; g->L = L;
+    g->del_ids = del_ids; g->ins = ins_vecs; g->queries = queries; g->out_ids = out_ids; g->out_dists = out_dists;
+    g->live_lb = idx->live;
+    g->seed_tc = idx->seed_tc && idx->live >= (u64)idx->cfg.n_entry + n_del;
+    auto bail = [&](etale_status s) {
+        etale_round_graph_destroy(g);
+        return s;
+    };
+    etale_status s = rg_check(idx, g);
+    if (s != ETALE_OK) return bail(s);
+    // every buffer the recording names is sized now and then pinned
+    const u32 R = idx->R, Lb = idx->cfg.build_beam;
+    const u64 cap = idx->capacity, mx = std::max<u64>({(u64)n_ins, (u64)nq, 1});
+    const u64 nslot = std::max<u64>({(u64)n_del * R, (u64)n_ins * R, (u64)n_del, 1});
+    const SeedTcPlan pe = seed_tc_plan(idx->dim, idx->cfg.n_entry, 0), pq = seed_tc_plan(idx->dim, idx->cfg.n_entry, (u32)mx);
+    Dev d0 = idx->dev();
+    bool ok = size_delete_scratch(idx, std::max<u32>(n_del, 1)) && size_batch_scratch(idx, std::max<u32>(n_ins, 1)) == ETALE_OK &&
+              grow(idx->sort_scr, sort_scratch_elems((u32)nslot) * 4) && grow(idx->scan_scr, scan_scratch_elems((u32)nslot) * 4) &&
+              grow(idx->seed, (size_t)std::max<u32>(n_ins, 1) * Lb * 8) &&
+              grow(idx->refine_spill, refine_spill_bytes(d0, idx->cfg.max_cand, idx->num_sms)) &&
+              grow(idx->live_flags, cap * 4) && grow(idx->live_rank, cap * 4) &&
+              grow(idx->live_scan_scr, scan_scratch_elems((u32)cap) * 4) && grow(idx->tomb_bits, ((cap + 31) / 32) * 4);
+    if (ok && g->seed_tc)
+        ok = grow(idx->sd_E, pe.bytes_E) && grow(idx->sd_en, (size_t)pe.s_pad * 4) && grow(idx->sd_estat, 64) &&
+             grow(idx->sd_A, pq.bytes_A) && grow(idx->sd_qstat, (size_t)mx * 16) && grow(idx->sd_keys, pq.bytes_keys) &&
+             grow(idx->sd_fb, (size_t)mx * 4) && grow(idx->sd_ctr, 64);
+    if (!ok) return bail(idx->fail(ETALE_ENOMEM, "round graph scratch"));
+    if ((n_ins && cudaMalloc(&g->ins_q, (size_t)n_ins * idx->mp * 4) != cudaSuccess) ||
+        (nq && (cudaMalloc(&g->q_pad, (size_t)nq * idx->mp * 4) != cudaSuccess ||
+                cudaMalloc(&g->q_seed, (size_t)nq * L * 8) != cudaSuccess))) {
+        cudaGetLastError();
+        return bail(idx->fail(ETALE_ENOMEM, "round graph buffers"));
+    }
+    // pin every index buffer the recording names
+    DevBuf *pins[] = {&idx->del_ids, &idx->del_vals, &idx->del_ids2, &idx->del_vals2, &idx->del_ok, &idx->del_scan,
+                      &idx->dt, &idx->pair_key, &idx->pair_val, &idx->pair_key2, &idx->pair_val2, &idx->pair_K,
+                      &idx->pair_Kn, &idx->pair_flags, &idx->pair_scan, &idx->pair_seg, &idx->counts,
+                      &idx->sort_scr, &idx->scan_scr, &idx->exp_keys, &idx->exp_count, &idx->F_id, &idx->F_rho,
+                      &idx->F_n, &idx->of_key, &idx->of_val, &idx->of_key2, &idx->of_val2, &idx->of_src,
+                      &idx->of_rho, &idx->seg_flags, &idx->seg_scan, &idx->seg_start, &idx->seed,
+                      &idx->refine_spill, &idx->live_flags, &idx->live_rank, &idx->live_scan_scr, &idx->tomb_bits,
+                      &idx->sd_E, &idx->sd_en, &idx->sd_estat, &idx->sd_A, &idx->sd_qstat, &idx->sd_keys,
+                      &idx->sd_fb, &idx->sd_ctr};
+    for (DevBuf *p : pins) {
+        p->pins++;
+        g->pinned.push_back(p);
+    }
+    idx->round_graphs++;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return bail(idx->fail(ETALE_ECUDA, "capture stream"));
+    const bool prof = idx->prof;
+    idx->prof = false;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = rg_enqueue(idx, g, cs);
+        e = cudaStreamEndCapture(cs, &g->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    idx->prof = prof;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(g->graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g->graph, nodes.data(), &nn);
+        for (size_t i = 0; e == cudaSuccess && i < nn; i++) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) g->kernels++;
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(idx->cuda_fail(e, "round graph capture"));
+    }
+    *out = g;
+    return ETALE_OK;
+}
+
+etale_status etale_round_graph_launch(etale_round_graph *g, void *stream) {
+    if (!g) return ETALE_EINVAL;
+    etale_index *idx = g->idx;
+    if (!idx->graph_pending) g->live_lb = idx->live;
+    etale_status s = rg_check(idx, g);
+    if (s != ETALE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_round_set(idx->rs, idx->next_id, st), "round state");
+    CK(cudaGraphLaunch(g->exec, st), "round graph launch");
+    CK(cudaEventRecord(idx->graph_ev, st), "round graph event");
+    g_kernel_launches += g->kernels + 1;
+    idx->next_id += g->n_ins;
+    idx->graph_pending = true;
+    g->live_lb = g->live_lb + g->n_ins - std::min<u64>(g->live_lb, g->n_del);
+    return ETALE_OK;
+}
+
+etale_status etale_round_graph_sync(etale_round_graph *g) {
+    if (!g) return ETALE_EINVAL;
+    etale_status s = settle(g->idx);
+    g->live_lb = g->idx->live;
+    return s;
+}
+
+etale_status etale_round_graph_destroy(etale_round_graph *g) {
+    if (!g) return ETALE_OK;
+    if (g->idx) {
+        if (g->idx->graph_pending) settle(g->idx);
+        for (DevBuf *p : g->pinned) p->pins--;
+        if (!g->pinned.empty()) g->idx->round_graphs--;
+    }
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    cudaFree(g->ins_q);
+    cudaFree(g->q_pad);
+    cudaFree(g->q_seed);
+    delete g;
+    return ETALE_OK;
+}
+
 etale_status etale_ground_truth_info(etale_index *idx, uint32_t *path, uint64_t *fallback_queries) {
     if (!idx) return ETALE_EINVAL;
     if (path) *path = idx->gt_path;
@@ -1415,6 +1845,10 @@ cudaError_t static_scratch(void **out) {
 etale_status etale_search_static(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
                                  uint32_t *out_ids, float *out_dists, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (nq == 0) return ETALE_OK;
     if (!queries || !out_ids || !out_dists || k == 0) return idx->fail(ETALE_EINVAL, "null buffer or k == 0");
     if (!is_device_ptr(queries) || !is_device_ptr(out_ids) || !is_device_ptr(out_dists))
@@ -1490,6 +1924,10 @@ struct File {
 
 etale_status etale_save(etale_index *idx, const char *path, void *stream) {
     if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
     if (!path) return idx->fail(ETALE_EINVAL, "path is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaStreamSynchronize(st), "synchronize");

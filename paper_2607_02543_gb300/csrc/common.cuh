@@ -118,7 +118,23 @@ struct Dev {
     float *x8s;          // C per-vector scales
     u32 mb, m8;          // row strides in elements (16-byte rows)
     u32 slab_batch;      // free slabs a warp pops at once (1..32; see WarpSlabs)
+    // Round state in device memory (RS_* words), set only for launches recorded
+    // into a round graph: kernels then take next_id and the first id of the
+    // current insert from here instead of from their arguments, so that one
+    // recorded round stays valid as the index grows.  nullptr otherwise.
+    u64 *rs;
 };
+
+enum : int {
+    RS_NEXT = 0,      // ids handed out so far
+    RS_FIRST = 1,     // first id of the insert being run
+    RS_LIVE = 2,      // live count at the last entry-set recomputation
+    RS_DELETED = 3,   // ids tombstoned since the host last read the state
+    RS_N = 8
+};
+// next_id for a kernel whose argument (a grid bound) may exceed it.
+__device__ __forceinline__ u64 dev_next_id(const Dev &d, u64 arg) { return d.rs ? min(arg, d.rs[RS_NEXT]) : arg; }
+__device__ __forceinline__ u32 dev_first(const Dev &d, u32 arg) { return d.rs ? (u32)d.rs[RS_FIRST] : arg; }
 
 // ---- canonical distance ------------------------------------------------------
 // Element i belongs to partial j = (i mod 128) / 4.  Each partial is a fused

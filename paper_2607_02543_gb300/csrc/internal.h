@@ -104,8 +104,9 @@ cudaError_t make_segments(const u32 *key, u32 n, u32 invalid, u32 *flags, u32 *s
 
 cudaError_t launch_recycle(const Dev &d, cudaStream_t st);
 // n_dev (optional): row count read on the device, n is its cap.
+// row0 (optional): the destination's first row, read on the device.
 cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st,
-                          const u32 *n_dev = nullptr);
+                          const u32 *n_dev = nullptr, const u64 *row0 = nullptr);
 cudaError_t launch_ingest_copies(const Dev &d, u64 first, u64 n, cudaStream_t st);
 cudaError_t launch_live_flags(const Dev &d, u64 next_id, u32 *flags, cudaStream_t st);
 cudaError_t launch_entries_select(const Dev &d, u64 next_id, const u32 *flags, const u32 *rank, u64 live,
@@ -166,5 +167,10 @@ cudaError_t launch_fill_offer_keys(u32 *key, u32 *val, u32 n, u32 invalid, cudaS
 cudaError_t launch_selftest_wait(u32 limit, u32 *status, cudaStream_t st);
 // *p = v, stream-ordered (a kernel, so no host buffer must outlive the call)
 cudaError_t launch_set_u32(u32 *p, u32 v, cudaStream_t st);
+// Round state (RS_* words): the insert takes ids [next, next + n); rs[word]
+// += *v; next = first = next_id.
+cudaError_t launch_round_advance(u64 *rs, u32 n, cudaStream_t st);
+cudaError_t launch_round_add(u64 *rs, int word, const u64 *v, cudaStream_t st);
+cudaError_t launch_round_set(u64 *rs, u64 next_id, cudaStream_t st);
 
 }  // namespace etale

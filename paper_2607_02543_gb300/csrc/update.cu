@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(Prun
         warp_sort_u64(keys, (int)a.np);
         const int n = (int)min(cnt, a.max_cand);
         const int nout = warp_prune<GV>(d, keys, n, alive, idx, oid, orho, st);
-        const u32 v = a.first + t;
+        const u32 v = dev_first(d, a.first) + t;
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
         snap = __shfl_sync(FULL, snap, 0);
@@ -1064,7 +1064,7 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         const u32 t = __shfl_sync(FULL, t_next, 0);
         if (t >= a.b) break;
         if (lane == 0) t_next = (u32)atomicAdd(&d.ctr[C_WORK], 1ull);
-        const u32 v = a.first + t;
+        const u32 v = dev_first(d, a.first) + t;
         u64 snap;
         const int dv = load_list(d, v, nid, nrho, snap);
         // 1. raw two-hop ids (v, members of N(v), and for mode 2 non-members
@@ -1087,7 +1087,7 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
                 u32 y = NIL;
                 if (j0 + lane < dw) y = d.slab[(size_t)s * R + j0 + lane].x;
                 bool ok = y != NIL && y != v;
-                if (ok && a.mode == 2) ok = y >= a.first && y < a.first + a.b;
+                if (ok && a.mode == 2) ok = y >= dev_first(d, a.first) && y < dev_first(d, a.first) + a.b;
                 if (ok) {
                     for (int k = 0; k < dv; k++) ok &= nid[k] != y;
                 }
@@ -1256,7 +1256,7 @@ __global__ void tombstone_kernel(Dev d, const u32 *ids, u32 n, u64 next_id, u32 
     if (i >= n) return;
     const u32 u = ids[i];
     u32 res = 0;
-    if ((i == 0 || ids[i - 1] != u) && (u64)u < next_id) {
+    if ((i == 0 || ids[i - 1] != u) && (u64)u < dev_next_id(d, next_id)) {
         for (int att = 0; att < 64; att++) {
             const u64 r = ld_ref(d, u);
             if (ref_del(r) || ref_slab(r) == NIL) break;
@@ -1703,6 +1703,7 @@ __global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const 
     __shared__ float srho[8][MAX_R];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const u64 base = ((u64)blockIdx.x * 8 + warp) * 32;
+    next_id = dev_next_id(d, next_id);
     if (base >= next_id) return;
     const u64 myid = base + lane;
     const u64 myref = myid < next_id ? ld_ref(d, (u32)myid) : ref_pack(1, 0, NIL);
@@ -1757,7 +1758,7 @@ cudaError_t launch_compact(const Dev &d, u64 next_id, const u32 *tomb_bits, cuda
 // Reclaim phase 2: CAS <1,d,s> -> <1,0,NIL> and retire s.
 __global__ void reclaim_tomb_kernel(Dev d, u64 next_id) {
     const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= next_id) return;
+    if (u >= dev_next_id(d, next_id)) return;
     const u64 r = ld_ref(d, (u32)u);
     if (!ref_del(r) || ref_slab(r) == NIL) return;
     if (atomicCAS(&d.ref[u], r, ref_pack(1, 0, NIL)) == r) retire_slab(d, ref_slab(r));

@@ -278,9 +278,11 @@ cudaError_t launch_recycle(const Dev &d, cudaStream_t st) {
 }
 
 // Copy n rows of dim floats into rows of mp floats, zero padding.
-__global__ void ingest_kernel(float *x, u32 mp, const float *src, u32 dim, u64 n, const u32 *n_dev) {
+__global__ void ingest_kernel(float *x, u32 mp, const float *src, u32 dim, u64 n, const u32 *n_dev,
+                              const u64 *row0) {
     const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (n_dev) n = min(n, (u64)*n_dev);
+    if (row0) x += *row0 * mp;
     if (i >= n * mp) return;
     const u64 r = i / mp, c = i % mp;
     x[i] = c < dim ? src[r * dim + c] : 0.0f;
@@ -293,7 +295,7 @@ __global__ void ingest_copies_kernel(Dev d, u64 first, u64 n) {
     const u64 w = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= n) return;
-    const u64 row = first + w;
+    const u64 row = dev_first(d, (u32)first) + w;
     const float *xr = d.x + row * d.mp;
     if (d.xb) {
         __nv_bfloat16 *br = reinterpret_cast<__nv_bfloat16 *>(d.xb + row * d.mb);
@@ -328,10 +330,11 @@ cudaError_t launch_ingest_copies(const Dev &d, u64 first, u64 n, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st, const u32 *n_dev) {
+cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cudaStream_t st, const u32 *n_dev,
+                          const u64 *row0) {
     if (n == 0) return cudaSuccess;
     const u64 tot = n * mp;
-    ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, mp, src, dim, n, n_dev);
+    ingest_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, mp, src, dim, n, n_dev, row0);
     return cudaGetLastError();
 }
 
@@ -341,6 +344,7 @@ cudaError_t launch_ingest(float *x, u32 mp, const float *src, u32 dim, u64 n, cu
 __global__ void live_flags_kernel(Dev d, u64 next_id, u32 *flags) {
     const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= next_id) return;
+    if (u >= dev_next_id(d, next_id)) { flags[u] = 0u; return; }
     const u64 r = d.ref[u];
     flags[u] = (!ref_del(r) && ref_slab(r) != NIL) ? 1u : 0u;
 }
@@ -351,8 +355,20 @@ cudaError_t launch_live_flags(const Dev &d, u64 next_id, u32 *flags, cudaStream_
     return cudaGetLastError();
 }
 
+// With d.rs set, L is the live total read from the scan (n = next_id rank
+// slots, the last one included) and S = min(S, L); the kernel also publishes
+// |E| and the live count to the device words (a recorded round).
 __global__ void entries_select_kernel(Dev d, u64 next_id, const u32 *flags, const u32 *rank, u64 L, u32 S) {
     const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d.rs) {
+        L = (u64)rank[next_id - 1] + flags[next_id - 1];
+        S = (u32)min((u64)S, L);
+        if (u == 0) {
+            *const_cast<u32 *>(d.nent_dev) = S;
+            d.rs[RS_LIVE] = L;
+        }
+        if (S == 0) return;
+    }
     if (u >= next_id || !flags[u]) return;
     const u64 r = rank[u];
     const u64 j = (r * S + L - 1) / L;        // smallest j with j * L / S >= r
@@ -361,7 +377,7 @@ __global__ void entries_select_kernel(Dev d, u64 next_id, const u32 *flags, cons
 
 cudaError_t launch_entries_select(const Dev &d, u64 next_id, const u32 *flags, const u32 *rank, u64 live, u32 S,
                                   cudaStream_t st) {
-    if (next_id == 0 || S == 0) return cudaSuccess;
+    if (next_id == 0 || (S == 0 && !d.rs)) return cudaSuccess;
     entries_select_kernel<<<(unsigned)((next_id + 255) / 256), 256, 0, st>>>(d, next_id, flags, rank, live, S);
     return cudaGetLastError();
 }
@@ -371,7 +387,7 @@ __global__ void tomb_bits_kernel(Dev d, u64 next_id, u32 *bits) {
     const u64 u = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     const u64 nw = (next_id + 31) / 32;
     if (u >= nw * 32) return;
-    const bool del = u < next_id && ref_del(d.ref[u]);
+    const bool del = u < dev_next_id(d, next_id) && ref_del(d.ref[u]);
     const u32 m = __ballot_sync(FULL, del);
     if ((threadIdx.x & 31) == 0) bits[u >> 5] = m;
 }
@@ -407,6 +423,17 @@ __global__ void fill_keys_kernel(u32 *key, u32 *val, u32 n, u32 invalid) {
 
 __global__ void set_u32_kernel(u32 *p, u32 v) { *p = v; }
 
+// A recorded round: the insert takes ids [next_id, next_id + n).
+__global__ void round_advance_kernel(u64 *rs, u32 n) {
+    rs[RS_FIRST] = rs[RS_NEXT];
+    rs[RS_NEXT] += n;
+}
+__global__ void round_add_kernel(u64 *rs, int word, const u64 *v) { rs[word] += *v; }
+__global__ void round_set_kernel(u64 *rs, u64 next_id) {
+    rs[RS_NEXT] = next_id;
+    rs[RS_FIRST] = next_id;
+}
+
 // One warp waits on an mbarrier phase that needs 16 transaction bytes no
 // copy will deliver; the bounded wait gives up and the status is recorded.
 __global__ void selftest_wait_kernel(u32 limit, u32 *status) {
@@ -422,6 +449,19 @@ __global__ void selftest_wait_kernel(u32 limit, u32 *status) {
 
 cudaError_t launch_selftest_wait(u32 limit, u32 *status, cudaStream_t st) {
     selftest_wait_kernel<<<1, 32, 0, st>>>(limit, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_advance(u64 *rs, u32 n, cudaStream_t st) {
+    round_advance_kernel<<<1, 1, 0, st>>>(rs, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_round_add(u64 *rs, int word, const u64 *v, cudaStream_t st) {
+    round_add_kernel<<<1, 1, 0, st>>>(rs, word, v);
+    return cudaGetLastError();
+}
+cudaError_t launch_round_set(u64 *rs, u64 next_id, cudaStream_t st) {
+    round_set_kernel<<<1, 1, 0, st>>>(rs, next_id);
     return cudaGetLastError();
 }
 
