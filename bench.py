@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--graph-steps", type=int, default=5,
                     help="extra rounds replayed from a recorded round graph (0: skip); reported apart")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--forms", default="fp32,bf16,fp8",
+                    help="precision forms of the 1M x 768 inner-product block ('' to skip)")
+    ap.add_argument("--forms-rounds", type=int, default=5, help="timed 1%% churn rounds per precision form")
+    ap.add_argument("--forms-only", action="store_true", help="run only the precision-form block")
     ap.add_argument("--cpu-ops", type=int, default=2000,
                     help="cpu_baseline: deletes and inserts the oracle runs on the full graph (scaled to the round)")
     ap.add_argument("--ref-ops", type=int, default=250,
@@ -307,6 +311,133 @@ def precision_sweep(idx, d_q, gt_np, plan, w, stream, out_ids, out_d) -> dict:
                      "qps": len(plan.queries) / (best * 1e-3), "max_rel_dist_err_vs_fp64": err}
     idx.set_search_precision("fp32")
     return out
+
+
+def precision_forms(args, stream, forms=("fp32", "bf16", "fp8")) -> dict:
+    """The 1M x 768 unit-vector workload (inner product, degree 64, 1% churn)
+    in each precision form: an index built and maintained with that precision
+    (FP32: canonical fp32 everywhere; BF16 / FP8: RobustPrune domination tests
+    on the bf16 tensor-core Gram tile, insert BeamSearch on the copy with the
+    candidates re-scored in fp32) and queried in it (exact fp32 rerank).  Per form: build time, ms per 1% churn round (CUDA
+    events, mean of `rounds`), then the cheapest (beam, rerank) reaching
+    Recall@10 >= 0.95 against the exact top-10 of the live set, its QPS, and
+    the largest relative error of returned distances against fp64 on 200
+    sampled queries."""
+    import torch
+    from paper_2607_02543_gb300 import Index
+    w = W.UNIT768_1M if not args.n_live else W.scaled(W.UNIT768_1M, args.n_live)
+    rounds = args.forms_rounds
+    wr = W.dataclasses.replace(w, rounds=1 + rounds)
+    plan = W.make_plan(wr)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_base = torch.from_numpy(plan.base).to(dev)
+    d_q = torch.from_numpy(plan.queries).to(dev)
+    d_ins = [torch.from_numpy(x).to(dev) for x in plan.inserts]
+    out_ids = torch.empty((w.n_queries, w.k), dtype=torch.int32, device=dev)
+    out_d = torch.empty((w.n_queries, w.k), dtype=torch.float32, device=dev)
+    sample = np.arange(0, w.n_queries, max(1, w.n_queries // 200))
+    Q64 = plan.queries.astype(np.float64)
+    X = idx_rows(None, plan, wr)
+    res = {"workload": w.name, "rounds": rounds, "forms": {}}
+    for form in forms:
+        # plain FP32: every distance of the path in canonical fp32 (CUDA-core
+        # RobustPrunes); BF16 / FP8: prunes on the bf16 tensor-core Gram tile
+        # and searches on the reduced copy (fp32 re-score of the candidates,
+        # fp32 rerank of the results)
+        idx = Index(w.dim, w.metric, w.degree, wr.capacity, build_beam=w.build_beam, mode=args.mode,
+                    n_entry=args.n_entry, max_cand=args.max_cand, copies=("bf16", "fp8"),
+                    gram="canonical" if form == "fp32" else "tensor")
+        idx.set_insert_precision(form)
+        idx.set_search_precision(form)
+        t0 = time.perf_counter()
+        idx.insert(d_base, stream)
+        idx.reclaim(stream)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        rng = np.random.default_rng(w.seed + 5)
+        alive = np.zeros(wr.capacity, bool)
+        alive[:w.n_base] = True
+        nxt = w.n_base
+        ms = []
+        idx.set_profiling(True)
+        for r in range(1 + rounds):               # the first round is a warm-up
+            if r == 1:
+                idx.profile(reset=True)
+            dele = W.choose_deletes(rng, np.nonzero(alive)[0].astype(np.uint32), w.n_delete)
+            d_del = torch.from_numpy(dele.view(np.int32)).to(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            idx.delete(d_del, stream)
+            idx.insert(d_ins[r], stream)
+            idx.reclaim(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ms.append(e0.elapsed_time(e1))
+            alive[dele] = False
+            alive[nxt:nxt + w.n_insert] = True
+            nxt += w.n_insert
+        phases = {k: round(v[0] / rounds, 3) for k, v in idx.profile(reset=True).items() if v[1]}
+        idx.set_profiling(False)
+        gt, _ = idx.ground_truth(d_q, w.k, stream)
+        gt_np = gt.cpu().numpy().view(np.uint32)
+
+        def recall():
+            got = out_ids.cpu().numpy().view(np.uint32)
+            return float(np.mean([len(set(a.tolist()) & set(g.tolist())) / w.k for a, g in zip(got, gt_np)]))
+
+        def timed(b):
+            best = 1e30
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                idx.search(d_q, w.k, b, stream, out=(out_ids, out_d))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            return best
+
+        sweep, chosen = [], None
+        for rr in ((1,) if form == "fp32" else (4, 8, 25)):
+            idx.set_rerank(rr)
+            for b in (64, 96, 128, 160, 192, 256):
+                idx.search(d_q, w.k, b, stream, out=(out_ids, out_d))
+                rec = recall()
+                if rec >= 0.95:
+                    t = timed(b)
+                    sweep.append([b, rr, rec, t])
+                    if chosen is None or t < chosen[3]:
+                        chosen = [b, rr, rec, t]
+                    break
+                sweep.append([b, rr, rec, None])
+        if chosen is None:                          # report the best reached
+            b, rr, rec, _ = max(sweep, key=lambda x: x[2])
+            idx.set_rerank(rr)
+            chosen = [b, rr, rec, timed(b)]
+        idx.set_rerank(chosen[1])
+        idx.search(d_q, w.k, chosen[0], stream, out=(out_ids, out_d))
+        ids, dist = out_ids.cpu().numpy().view(np.uint32), out_d.cpu().numpy()
+        err = 0.0
+        for t in sample:
+            for j in range(w.k):
+                if ids[t, j] == 0xFFFFFFFF:
+                    continue
+                ex = 1.0 - float(Q64[t] @ X(int(ids[t, j])))
+                err = max(err, abs(float(dist[t, j]) - ex) / max(abs(ex), 1e-12))
+        res["forms"][form] = {"build_s": build_s, "ms_per_round": float(np.mean(ms)), "phase_ms": phases,
+                              "beam": chosen[0],
+                              "rerank": chosen[1], "recall_at_10": chosen[2], "ms_per_10k_queries": chosen[3],
+                              "qps": w.n_queries / (chosen[3] * 1e-3), "max_rel_dist_err_vs_fp64": err,
+                              "sweep": sweep}
+        idx.close()
+        torch.cuda.empty_cache()
+    f = res["forms"]
+    if "fp32" in f:
+        for form in forms[1:]:
+            if form in f:
+                f[form]["vs_fp32"] = {"round_speedup": f["fp32"]["ms_per_round"] / f[form]["ms_per_round"],
+                                      "qps_ratio": f[form]["qps"] / f["fp32"]["qps"]}
+    return res
 
 
 def idx_rows(idx, plan, w):
@@ -594,6 +725,13 @@ def main():
     if args.impl == "reference":
         return run_reference(args, w)
     import torch
+    if args.forms_only:
+        from paper_2607_02543_gb300 import build as B
+        B.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(precision_forms(args, torch.cuda.current_stream(),
+                                         tuple(f for f in args.forms.split(",") if f))), flush=True)
+        return
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -895,6 +1033,13 @@ def main():
         cpu = {"value": float(np.mean(per)), "unit": "ms", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": oracle_sample_text(w, args.cpu_ops, 1), "parts": info["parts"],
                "load_s": info["load_s"]}
+    # the reduced-precision forms on the 1M x 768 inner-product workload (their
+    # own indexes, after the headline index is released)
+    if rank == 0 and world == 1 and args.forms and args.workload == "int256-1m-d128":
+        if snap_dir is None:
+            idx.close()
+        torch.cuda.empty_cache()
+        prec_block = precision_forms(args, stream, tuple(f for f in args.forms.split(",") if f))
     if rank == 0:
         out = {"metric": "ms per 1% churn round", "value": ms_round, "unit": "ms", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),

@@ -80,8 +80,8 @@ typedef struct {
                              fp32 rows: bit 0 BF16, bit 1 FP8-E4M3 with a
                              per-vector scale max|x| / 448; default none    */
     uint32_t rerank;      /* reduced-precision query search re-scores its
-                             rerank * k best live candidates in exact fp32;
-                             default 4, at most 64 / k candidates used      */
+                             rerank * k best live candidates in exact fp32
+                             (at most the beam); default 4                 */
     uint32_t gt;          /* etale_ground_truth: 0 default (tensor-core
                              candidate pass with an exact certified rerank
                              where it applies), 1 CUDA cores only            */
@@ -173,6 +173,19 @@ etale_status etale_reclaim(etale_index *idx, void *stream);
  * with the canonical fp32 distance before the k results are chosen, so
  * returned distances are exact fp32.  EINVAL if the copy is not kept.       */
 etale_status etale_set_search_precision(etale_index *idx, etale_precision p);
+
+/* Distance precision of the BeamSearch of inserts (Algorithm 2; the
+ * candidate set C_v): FP32 (default) or a copy kept by `copies`.  With BF16
+ * or FP8 the search is scored on the reduced rows, and the nearest max_cand
+ * expanded nodes are re-scored with the canonical fp32 distance and
+ * re-sorted before RobustPrune, so every stored rho is exact fp32; only the
+ * choice of candidates depends on the precision.  Seeding of these searches
+ * runs in the same precision (CUDA cores).  EINVAL if the copy is not kept.
+ * Recorded rounds use the precision in force when they are recorded.       */
+etale_status etale_set_insert_precision(etale_index *idx, etale_precision p);
+
+/* Set cfg.rerank for later reduced-precision query searches (1..256).     */
+etale_status etale_set_rerank(etale_index *idx, uint32_t rerank);
 
 /* Copy the reduced-precision codes of ids [first, first + n) to HOST
  * buffers (either may be NULL): bf16 as uint16 bits, n x dim; fp8 as bytes,

@@ -59,7 +59,8 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
            "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
            "etale_load", "etale_search_eval_count", "etale_round_graph_create",
-           "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy"]
+           "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy",
+           "etale_set_insert_precision", "etale_set_rerank"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -97,6 +98,8 @@ def load(path: str = LIB_PATH):
             "etale_get_profile": ([P, P, P, U32, C.c_int], C.c_int),
             "etale_search_static": ([P, P, U64, U32, U32, P, P, P], C.c_int),
             "etale_set_search_precision": ([P, C.c_int], C.c_int),
+            "etale_set_insert_precision": ([P, C.c_int], C.c_int),
+            "etale_set_rerank": ([P, U32], C.c_int),
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
             "etale_set_concurrent": ([P, C.c_int], C.c_int),
             "etale_set_search_tuning": ([P, U32, U32], C.c_int),
@@ -298,6 +301,14 @@ class Index:
     def set_concurrent(self, on: bool = True):
         """Let one search thread and one update thread overlap on the device."""
         self._check(self.lib.etale_set_concurrent(self.h, int(on)))
+
+    def set_insert_precision(self, prec: str):
+        """"fp32", "bf16" or "fp8" for the BeamSearch of later inserts (rho stays exact fp32)."""
+        self._check(self.lib.etale_set_insert_precision(self.h, {"fp32": 0, "bf16": 1, "fp8": 2}[prec]))
+
+    def set_rerank(self, rerank: int):
+        """Candidates re-scored in fp32 by reduced-precision queries: rerank * k (at most the beam)."""
+        self._check(self.lib.etale_set_rerank(self.h, rerank))
 
     def set_search_precision(self, prec: str):
         """"fp32", "bf16" or "fp8" for later query searches."""

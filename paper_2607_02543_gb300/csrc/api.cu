@@ -88,6 +88,7 @@ struct etale_index {
     float *x8s = nullptr;
     u32 mb = 0, m8 = 0;
     u32 search_prec = 0;
+    u32 insert_prec = 0;            // precision of the insert BeamSearch gathers
     bool rows_exact = true;         // every ingested row's bf16 copy is exact (C_INEXACT == 0)
     u32 *nent_dev = nullptr;        // |E| in device memory
     u64 *rs = nullptr;              // round state (RS_* words) of recorded rounds
@@ -528,14 +529,15 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     if (!grow(idx->seed, (size_t)b * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
     {
         PhaseScope ps(idx, ETALE_PH_SEED, st);
-        etale_status s0 = seed_batch(idx, d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed), 0, st);
+        etale_status s0 = seed_batch(idx, d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed),
+                                     idx->insert_prec, st);
         if (s0 != ETALE_OK) return s0;
     }
     {
         PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
         CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr,
                          as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, L, idx->tune),
-                         idx->num_sms, st, 0, 4, nullptr, exact_rows(idx)),
+                         idx->num_sms, st, idx->insert_prec, 4, nullptr, idx->insert_prec == 0 && exact_rows(idx)),
            "insert search");
     }
     g_kernel_launches += 1;
@@ -545,7 +547,8 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     {
         PhaseScope ps(idx, ETALE_PH_PRUNE, st);
         CK(launch_prune_insert(d, first, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
-                               as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st),
+                               as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st,
+                               idx->insert_prec != 0),
            "prune insert");
     }
     g_kernel_launches++;
@@ -1569,14 +1572,15 @@ cudaError_t rg_enqueue(etale_index *idx, etale_round_graph *g, cudaStream_t st) 
         if (e == cudaSuccess) e = launch_ingest(idx->x, idx->mp, g->ins, idx->dim, b, st, nullptr, idx->rs + RS_FIRST);
         if (e == cudaSuccess) e = launch_ingest(g->ins_q, idx->mp, g->ins, idx->dim, b, st);
         if (e == cudaSuccess) e = launch_ingest_copies(dg, 0, b, st);
-        if (e == cudaSuccess) e = rg_seed(idx, g, dg, g->ins_q, b, Lb, as<u64>(idx->seed), st);
+        if (e == cudaSuccess) e = rg_seed(idx, g, dg, g->ins_q, b, Lb, as<u64>(idx->seed), st, idx->insert_prec);
         if (e == cudaSuccess)
             e = launch_search(dg, g->ins_q, b, Lb, H, 1, 0, nullptr, nullptr, as<u64>(idx->exp_keys),
                               as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, Lb, idx->tune), idx->num_sms,
-                              st, 0, 4, nullptr, false);
+                              st, idx->insert_prec, 4, nullptr, false);
         if (e == cudaSuccess)
             e = launch_prune_insert(dg, 0, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
-                                    as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st);
+                                    as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st,
+                                    idx->insert_prec != 0);
         if (e == cudaSuccess) e = launch_recycle(dg, st);
         if (e == cudaSuccess) e = rg_offers(idx, dg, b * R, st);
         const u32 rmode = idx->cfg.refine == 1 ? 0 : idx->cfg.refine;
@@ -2118,6 +2122,22 @@ etale_status etale_load(const char *path, const etale_config *cfg_in, uint64_t c
         return fail(ETALE_ECUDA, "load synchronise");
     idx->rows_exact = inexact == 0;
     *out = idx;
+    return ETALE_OK;
+}
+
+etale_status etale_set_rerank(etale_index *idx, uint32_t rerank) {
+    if (!idx) return ETALE_EINVAL;
+    if (rerank == 0 || rerank > 256) return idx->fail(ETALE_EINVAL, "rerank must be 1..256");
+    idx->cfg.rerank = rerank;
+    return ETALE_OK;
+}
+
+etale_status etale_set_insert_precision(etale_index *idx, etale_precision p) {
+    if (!idx) return ETALE_EINVAL;
+    if (p == ETALE_PREC_BF16 && !idx->xb) return idx->fail(ETALE_EINVAL, "no bf16 copy kept (config.copies bit 0)");
+    if (p == ETALE_PREC_FP8 && !idx->x8) return idx->fail(ETALE_EINVAL, "no fp8 copy kept (config.copies bit 1)");
+    if ((u32)p > 2) return idx->fail(ETALE_EINVAL, "unknown precision");
+    idx->insert_prec = (u32)p;
     return ETALE_OK;
 }
 

@@ -25,7 +25,7 @@ size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
 cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec = 0,
                         const u32 *nq_dev = nullptr, const u32 *qsel = nullptr);
 // prec: 0 fp32, 1 bf16 copy, 2 fp8 copy (query mode only; the best
-// min(rerank * k, 64) live candidates are re-scored in canonical fp32).
+// min(rerank * k, L) live candidates are re-scored in canonical fp32).
 // exact_rows: fp32 semantics with rows gathered from the bf16 copy, which
 // holds every stored row exactly (prec 1, no rerank, any mode).
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
@@ -51,9 +51,11 @@ struct Offers {
 };
 
 // update.cu
+// rescore: the keys come from a reduced-precision search; the kept candidates
+// are re-scored with the canonical fp32 distance before RobustPrune.
 cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
                                 u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
-                                const Offers &of, int num_sms, cudaStream_t st);
+                                const Offers &of, int num_sms, cudaStream_t st, bool rescore = false);
 // lock-free (budget > 0): offer slots [lo, hi) only
 cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
                               u32 lockfree_budget, int num_sms, cudaStream_t st, u32 lo = 0,

@@ -14,6 +14,8 @@
 // once the beam is full its worst key only decreases, so an id that left the
 // beam or was refused is refused again (its key is the same), and an id still
 // in the beam is recognised in the merge by its equal key and dropped.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -552,9 +554,11 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
         nexp_tot += hops;
         if (LOG && lane == 0) a.elog_n[qi] = qcnt;
         if (a.mode == 0 && P != 0 && !a.exact) {
-            // exact fp32 rerank of the best min(rerank * k, 64) live candidates
+            // exact fp32 rerank of the best min(rerank * k, L) live candidates
             u64 *rk = reinterpret_cast<u64 *>(s.stage);
-            const int want = (int)min(a.rerank * a.k, 64u);
+            const int want = (int)min(a.rerank * a.k, a.L);
+            int rn = 64;
+            while (rn < want) rn <<= 1;
             int c = 0;
             for (int i0 = 0; i0 < n && c < want; i0 += 32) {
                 const int i = i0 + lane;
@@ -574,12 +578,12 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
                 if (r0 + grp < c && g == 0) rk[cc] = mkkey(dist, id);
                 __syncwarp();
             }
-            for (int i = c + lane; i < 64; i += 32) rk[i] = KEY_INF;
+            for (int i = c + lane; i < rn; i += 32) rk[i] = KEY_INF;
             __syncwarp();
-            warp_sort_u64(rk, 64);
+            warp_sort_u64(rk, rn);
             // equal keys (an id seen twice) are adjacent after the sort: keep one
             u32 outc = 0;
-            for (int i0 = 0; i0 < 64; i0 += 32) {
+            for (int i0 = 0; i0 < rn; i0 += 32) {
                 const int i = i0 + lane;
                 const bool ok = rk[i] != KEY_INF && (i == 0 || rk[i] != rk[i - 1]);
                 const u32 m = __ballot_sync(FULL, ok);
@@ -652,7 +656,6 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
                           const u32 *nq_dev, bool exact_rows, u32 *elog, u32 *elog_n, u32 elog_cap) {
     if (nq == 0) return cudaSuccess;
     if (exact_rows) prec = 1;
-    else if (mode != 0) prec = 0;
     if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
     SearchArgs a;
     a.d = d; a.q = q; a.seed = seed; a.nq_dev = nq_dev; a.nq = nq; a.L = L; a.max_hops = max_hops; a.mode = mode;
@@ -670,8 +673,13 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.elog_n = elog_n;
     a.elog_cap = elog_cap;
     const bool log = elog != nullptr;
-    // the rerank buffer (64 keys) lives in the stage
-    if (prec != 0 && (size_t)a.stage_rows * a.rowb < 64 * 8) a.stage_rows = (64 * 8 + a.rowb - 1) / a.rowb;
+    // the rerank buffer (up to the beam, rounded up to a power of two >= 64
+    // keys) lives in the stage
+    if (prec != 0 && mode == 0) {
+        size_t rn = 64;
+        while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
+        if ((size_t)a.stage_rows * a.rowb < rn * 8) a.stage_rows = (u32)((rn * 8 + a.rowb - 1) / a.rowb);
+    }
     const void *fn = log ? (prec == 1 ? (const void *)search_kernel<1, true> : prec == 2 ? (const void *)search_kernel<2, true>
                                                                                       : (const void *)search_kernel<0, true>)
                          : (prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>

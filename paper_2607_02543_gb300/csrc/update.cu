@@ -757,6 +757,7 @@ struct PruneInsArgs {
     const u64 *exp_keys;
     const u32 *exp_count;
     u32 max_hops, max_cand, np, ns, gram;
+    u32 rescore;   // the search ran on a reduced-precision copy: rescore in fp32
     u32 *F_id;
     float *F_rho;
     u32 *F_n;
@@ -803,8 +804,26 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(Prun
         __syncwarp();
         warp_sort_u64(keys, (int)a.np);
         const int n = (int)min(cnt, a.max_cand);
-        const int nout = warp_prune<GV>(d, keys, n, alive, idx, oid, orho, st);
         const u32 v = dev_first(d, a.first) + t;
+        if (a.rescore) {
+            // the nearest max_cand by the search's reduced-precision distance,
+            // re-scored with the canonical fp32 distance to v and re-sorted,
+            // so that RobustPrune and every stored rho see exact distances
+            const float *xv = d.x + (size_t)v * d.mp;
+            const int grp = lane >> 3, g = lane & 7;
+            for (int r0 = 0; r0 < n; r0 += 4) {
+                const int c = min(r0 + grp, n - 1);
+                const u32 id = key_id(keys[c]);
+                const float dist = canon_dist<8>(xv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
+                __syncwarp();
+                if (r0 + grp < n && g == 0) keys[c] = mkkey(dist, id);
+                __syncwarp();
+            }
+            for (u32 i = n + lane; i < a.np; i += 32) keys[i] = KEY_INF;
+            __syncwarp();
+            warp_sort_u64(keys, (int)a.np);
+        }
+        const int nout = warp_prune<GV>(d, keys, n, alive, idx, oid, orho, st);
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
         snap = __shfl_sync(FULL, snap, 0);
@@ -830,11 +849,12 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(Prun
 
 cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
                                 u32 max_hops, u32 max_cand, u32 *F_id, float *F_rho, u32 *F_n,
-                                const Offers &of, int num_sms, cudaStream_t st) {
+                                const Offers &of, int num_sms, cudaStream_t st, bool rescore) {
     if (b == 0) return cudaSuccess;
     // the Gram tile covers the prune only when every candidate fits in it
     const u32 gram = gram_rows_for(d.gram, max_cand);
-    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, 0, gram, F_id, F_rho, F_n, of};
+    PruneInsArgs a{d, first, b, exp_keys, exp_count, max_hops, max_cand, 0, 0, gram, rescore ? 1u : 0u,
+                   F_id, F_rho, F_n, of};
     u32 np = 32;
     while (np < max_hops) np <<= 1;
     a.np = np;
