@@ -297,6 +297,7 @@ typedef struct {
     uint32_t stage_rows;  /* neighbour rows gathered per bulk-copy batch      */
     uint32_t seen_bits;   /* log2 slots of the evaluated-id cache             */
     float ms;             /* measured: seeding + search of the tuning batch   */
+    uint32_t warps_per_block; /* queries in flight per thread block: 2, 4, 8 */
 } etale_tuning;
 
 /* Turn the exact-copy gathers of cfg.exact_rows on (1) or off (0) for the
@@ -304,17 +305,30 @@ typedef struct {
  * the device's count of inexact rows (synchronises the default stream).   */
 etale_status etale_set_exact_rows(etale_index *idx, int on);
 
-/* Set the query-search launch shape (results never depend on it).          */
-etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits);
+/* Set the BeamSearch launch shape (results never depend on it);
+ * warps_per_block 0 keeps the current value.                               */
+etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits,
+                                     uint32_t warps_per_block);
 
 /* Time seeding + BeamSearch of the given DEVICE query batch under each
- * candidate launch shape (stage rows 2/4/8/16 x cache 2^7..2^10 slots; shapes
- * whose shared memory does not fit the device are skipped), keep
- * the fastest for this index, and report up to n_out tried shapes in out.
- * Results do not depend on the launch shape.                               */
+ * candidate launch shape (stage rows 2/4/8/16 x cache 2^7..2^10 slots x
+ * 2/4/8 warps per block; shapes whose shared memory does not fit the device
+ * are skipped), keep the fastest for this index, and report up to n_out
+ * tried shapes in out.  Results do not depend on the launch shape.         */
 etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
                                    uint32_t beam, etale_tuning *out, uint32_t n_out, uint32_t *n_tried,
                                    void *stream);
+
+/* The search beam (EF_SEARCH, Sec. 5.6) for a recall target, then the launch
+ * shape at that beam: computes the exact top-k of the DEVICE query batch
+ * (etale_ground_truth, k <= 32), searches with each beam of `beams`
+ * (ascending, <= 256) until Recall@k reaches `target`, writes the beam taken
+ * to *chosen (the last one if none reaches it) and each tried beam's recall
+ * to recalls[i] (may be NULL; -1 for beams not tried), then runs
+ * etale_autotune_search at *chosen.                                         */
+etale_status etale_autotune_beam(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, float target,
+                                 const uint32_t *beams, uint32_t n_beams, float *recalls, uint32_t *chosen,
+                                 void *stream);
 
 /* ---- CUDA-graph query batches (deployment support; the paper has none) -- */
 typedef struct etale_search_graph etale_search_graph;

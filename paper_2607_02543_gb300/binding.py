@@ -37,7 +37,8 @@ class Config(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("stage_rows", C.c_uint32), ("seen_bits", C.c_uint32), ("ms", C.c_float)]
+    _fields_ = [("stage_rows", C.c_uint32), ("seen_bits", C.c_uint32), ("ms", C.c_float),
+                ("warps_per_block", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -60,7 +61,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
            "etale_load", "etale_search_eval_count", "etale_round_graph_create",
            "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy",
-           "etale_set_insert_precision", "etale_set_rerank"]
+           "etale_set_insert_precision", "etale_set_rerank", "etale_autotune_beam"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -100,9 +101,10 @@ def load(path: str = LIB_PATH):
             "etale_set_search_precision": ([P, C.c_int], C.c_int),
             "etale_set_insert_precision": ([P, C.c_int], C.c_int),
             "etale_set_rerank": ([P, U32], C.c_int),
+            "etale_autotune_beam": ([P, P, U64, U32, C.c_float, P, U32, P, C.POINTER(U32), P], C.c_int),
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
             "etale_set_concurrent": ([P, C.c_int], C.c_int),
-            "etale_set_search_tuning": ([P, U32, U32], C.c_int),
+            "etale_set_search_tuning": ([P, U32, U32, U32], C.c_int),
             "etale_set_exact_rows": ([P, C.c_int], C.c_int),
             "etale_autotune_search": ([P, P, U64, U32, U32, P, U32, C.POINTER(U32), P], C.c_int),
             "etale_search_graph_create": ([P, U32, U32, U32, P, P, P, P, C.POINTER(P)], C.c_int),
@@ -265,17 +267,27 @@ class Index:
         """Gather the exact BF16 copy in fp32 BeamSearches (see etale_set_exact_rows)."""
         self._check(self.lib.etale_set_exact_rows(self.h, int(on)))
 
-    def set_search_tuning(self, stage_rows: int, seen_bits: int):
-        self._check(self.lib.etale_set_search_tuning(self.h, stage_rows, seen_bits))
+    def set_search_tuning(self, stage_rows: int, seen_bits: int, warps_per_block: int = 0):
+        self._check(self.lib.etale_set_search_tuning(self.h, stage_rows, seen_bits, warps_per_block))
 
     def autotune_search(self, queries, k: int, beam: int, stream=None):
         """Time the launch shapes on a device query batch; keep the fastest.
-        Returns [(stage_rows, seen_bits, ms), ...] for the shapes tried."""
-        out = (Tuning * 32)()
+        Returns [(stage_rows, seen_bits, ms, warps_per_block), ...] for the shapes tried."""
+        out = (Tuning * 64)()
         n = C.c_uint32(0)
-        self._check(self.lib.etale_autotune_search(self.h, _ptr(queries), queries.shape[0], k, beam, out, 32,
+        self._check(self.lib.etale_autotune_search(self.h, _ptr(queries), queries.shape[0], k, beam, out, 64,
                                                    C.byref(n), _stream(stream)))
-        return [(out[i].stage_rows, out[i].seen_bits, out[i].ms) for i in range(n.value)]
+        return [(out[i].stage_rows, out[i].seen_bits, out[i].ms, out[i].warps_per_block) for i in range(n.value)]
+
+    def autotune_beam(self, queries, k: int, target: float, beams=(64, 96, 112, 128, 144, 160, 192, 256),
+                      stream=None):
+        """etale_autotune_beam: (beam taken, [(beam, recall), ...] tried)."""
+        b = np.ascontiguousarray(beams, dtype=np.uint32)
+        rec = np.empty(b.size, np.float32)
+        ch = C.c_uint32(0)
+        self._check(self.lib.etale_autotune_beam(self.h, _ptr(queries), queries.shape[0], k, C.c_float(target),
+                                                 _ptr(b), b.size, _ptr(rec), C.byref(ch), _stream(stream)))
+        return ch.value, [(int(x), float(r)) for x, r in zip(b, rec) if r >= 0]
 
     def search_graph(self, queries, out_ids, out_dists, nq_dev, k: int, beam: int) -> "SearchGraph":
         """Capture the query path for batches of up to queries.shape[0] into a CUDA graph."""

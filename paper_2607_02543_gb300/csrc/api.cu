@@ -492,7 +492,8 @@ bool exact_rows(const etale_index *idx) {
 // The BeamSearch launch shape with its row stage shrunk until a block's shared
 // memory fits the device (long rows); results do not depend on the stage.
 SearchTuning fit_tuning(const etale_index *idx, u32 L, SearchTuning t) {
-    while (t.stage_rows > 1 && search_smem_bytes(idx->mp, L, t.stage_rows, 1u << t.seen_bits) > (size_t)idx->smem_optin)
+    while (t.stage_rows > 1 &&
+           search_smem_bytes(idx->mp, L, t.stage_rows, 1u << t.seen_bits, t.warps_per_block) > (size_t)idx->smem_optin)
         t.stage_rows >>= 1;
     return t;
 }
@@ -1282,12 +1283,16 @@ etale_status etale_set_exact_rows(etale_index *idx, int on) {
     return ETALE_OK;
 }
 
-etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits) {
+etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits,
+                                     uint32_t warps_per_block) {
     if (!idx) return ETALE_EINVAL;
     if (stage_rows < 1 || stage_rows > 32 || seen_bits < 6 || seen_bits > 14)
         return idx->fail(ETALE_EINVAL, "stage_rows must be 1..32 and seen_bits 6..14");
+    if (warps_per_block && warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8)
+        return idx->fail(ETALE_EINVAL, "warps_per_block must be 2, 4 or 8 (0 keeps it)");
     idx->tune.stage_rows = stage_rows;
     idx->tune.seen_bits = seen_bits;
+    if (warps_per_block) idx->tune.warps_per_block = warps_per_block;
     return ETALE_OK;
 }
 
@@ -1317,12 +1322,14 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
     float best = 1e30f;
     SearchTuning best_t = saved;
     u32 tried = 0;
-    const u32 rows[4] = {2, 4, 8, 16}, bits[4] = {7, 8, 9, 10};
+    const u32 rows[4] = {2, 4, 8, 16}, bits[4] = {7, 8, 9, 10}, wpbs[3] = {2, 4, 8};
+    for (u32 c = 0; c < 3; c++)
     for (u32 a = 0; a < 4; a++)
         for (u32 b = 0; b < 4; b++) {
             SearchTuning t;
             t.stage_rows = rows[a];
             t.seen_bits = bits[b];
+            t.warps_per_block = wpbs[c];
             if (fit_tuning(idx, L, t).stage_rows != t.stage_rows) continue;   // does not fit: not a shape
             float ms_best = 1e30f;
             bool ok = true;
@@ -1340,7 +1347,7 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
             }
             cudaGetLastError();   // a shape that does not fit is skipped
             if (!ok) continue;
-            if (out && tried < n_out) out[tried] = etale_tuning{t.stage_rows, t.seen_bits, ms_best};
+            if (out && tried < n_out) out[tried] = etale_tuning{t.stage_rows, t.seen_bits, ms_best, t.warps_per_block};
             tried++;
             if (ms_best < best) { best = ms_best; best_t = t; }
         }
@@ -1350,6 +1357,64 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
     idx->tune = tried ? best_t : saved;
     if (n_tried) *n_tried = tried;
     return check_search_errors(idx, st);
+}
+
+etale_status etale_autotune_beam(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, float target,
+                                 const uint32_t *beams, uint32_t n_beams, float *recalls, uint32_t *chosen,
+                                 void *stream) {
+    if (!idx) return ETALE_EINVAL;
+    {
+        etale_status s_ = settle(idx);
+        if (s_ != ETALE_OK) return s_;
+    }
+    if (!queries || !is_device_ptr(queries) || nq == 0 || nq > 0xFFFFFFFFull || k == 0 || k > 32 || !beams ||
+        n_beams == 0 || !chosen)
+        return idx->fail(ETALE_EINVAL, "autotune_beam needs a DEVICE query batch, k in 1..32 and beams");
+    for (u32 i = 0; i < n_beams; i++)
+        if (beams[i] > 256 || (i && beams[i] <= beams[i - 1]))
+            return idx->fail(ETALE_EINVAL, "beams must ascend and stay <= 256");
+    const size_t nk = (size_t)nq * k;
+    u32 *gid = nullptr, *sid = nullptr;
+    float *gd = nullptr, *sd = nullptr;
+    if (cudaMalloc(&gid, nk * 4) != cudaSuccess || cudaMalloc(&sid, nk * 4) != cudaSuccess ||
+        cudaMalloc(&gd, nk * 4) != cudaSuccess || cudaMalloc(&sd, nk * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(gid); cudaFree(sid); cudaFree(gd); cudaFree(sd);
+        return idx->fail(ETALE_ENOMEM, "autotune_beam buffers");
+    }
+    std::vector<u32> gh(nk), sh(nk);
+    etale_status s = search_common(idx, queries, nq, k, 0, gid, gd, stream, true);   // exact top-k
+    if (s == ETALE_OK && cudaMemcpy(gh.data(), gid, nk * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = idx->fail(ETALE_ECUDA, "autotune_beam copy");
+    for (u32 i = 0; i < n_beams; i++) recalls ? (void)(recalls[i] = -1.0f) : (void)0;
+    u32 pick = beams[n_beams - 1];
+    for (u32 i = 0; i < n_beams && s == ETALE_OK; i++) {
+        s = search_common(idx, queries, nq, k, beams[i], sid, sd, stream, false);
+        if (s != ETALE_OK) break;
+        if (cudaMemcpy(sh.data(), sid, nk * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            s = idx->fail(ETALE_ECUDA, "autotune_beam copy");
+            break;
+        }
+        u64 hit = 0;
+        for (u64 q = 0; q < nq; q++) {
+            const u32 *a = sh.data() + q * k, *b = gh.data() + q * k;
+            for (u32 x = 0; x < k; x++) {
+                if (a[x] == NIL) continue;
+                for (u32 y = 0; y < k; y++)
+                    if (a[x] == b[y]) { hit++; break; }
+            }
+        }
+        const float rec = (float)((double)hit / (double)nk);
+        if (recalls) recalls[i] = rec;
+        if (rec >= target) {
+            pick = beams[i];
+            break;
+        }
+    }
+    cudaFree(gid); cudaFree(sid); cudaFree(gd); cudaFree(sd);
+    if (s != ETALE_OK) return s;
+    *chosen = pick;
+    return etale_autotune_search(idx, queries, nq, k, pick, nullptr, 0, nullptr, stream);
 }
 
 etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32_t k, uint32_t beam,

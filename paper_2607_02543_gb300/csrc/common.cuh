@@ -321,17 +321,24 @@ __device__ __forceinline__ void retire_slab(const Dev &d, u32 s) {
 // free pool is too small for every resident warp to hold a batch.
 struct WarpSlabs {
     u32 pop_slab, ret_slab;
+    u32 spare;           // warp-uniform: a slab written for a lost CAS, never linked
     int npop, nret;      // warp-uniform
     u64 npub, nretry;    // counted on every lane, added once
 };
 __device__ __forceinline__ void ws_init(WarpSlabs &w) {
     w.pop_slab = NIL;
     w.ret_slab = NIL;
+    w.spare = NIL;
     w.npop = w.nret = 0;
     w.npub = w.nretry = 0;
 }
 __device__ __forceinline__ u32 ws_pop(const Dev &d, WarpSlabs &w) {
     const int lane = threadIdx.x & 31;
+    if (w.spare != NIL) {   // reuse the slab of a lost CAS: no reader can hold it
+        const u32 s = w.spare;
+        w.spare = NIL;
+        return s;
+    }
     if (w.npop == 0) {
         const u32 K = d.slab_batch < 1 ? 1u : (d.slab_batch > 32 ? 32u : d.slab_batch);
         u64 i0 = 0;
@@ -364,6 +371,10 @@ __device__ __forceinline__ void ws_retire(const Dev &d, WarpSlabs &w, u32 s) {
 }
 __device__ __forceinline__ void ws_finish(const Dev &d, WarpSlabs &w) {
     const int lane = threadIdx.x & 31;
+    if (w.spare != NIL) {
+        ws_retire(d, w, w.spare);
+        w.spare = NIL;
+    }
     ws_flush(d, w);
     if (w.npop > 0) {
         u64 j0 = 0;
@@ -382,8 +393,12 @@ __device__ __forceinline__ void ws_finish(const Dev &d, WarpSlabs &w) {
 // the same arguments; ids/rho hold the n <= R entries (shared memory) and
 // `snap` is the reference word the caller read before building N.  The CAS
 // installs <delta of snap, n, fresh slab> only if r(u) still equals snap;
-// returns true on success.  On a lost CAS the fresh slab is retired and false
-// is returned (the caller retries or drops the update).
+// returns true on success.  On a lost CAS false is returned (the caller
+// retries or drops the update) and the fresh slab, which was never linked
+// into any reference and so cannot be read by anyone else, is kept as the
+// warp's spare: the next publication writes into it instead of popping, so
+// retries under contention do not drain the pool.  A spare left at the end of
+// a launch is retired.
 // pruned: the new list's P bit (see ref_pruned).
 __device__ __forceinline__ bool warp_publish(const Dev &d, WarpSlabs &ws, u32 u, const u32 *ids,
                                              const float *rho, int n, u64 snap, bool pruned) {
@@ -404,7 +419,7 @@ __device__ __forceinline__ bool warp_publish(const Dev &d, WarpSlabs &ws, u32 u,
         if (ref_slab(snap) != NIL) ws_retire(d, ws, ref_slab(snap));
         ws.npub++;
     } else {
-        ws_retire(d, ws, s2);
+        ws.spare = s2;
         ws.nretry++;
     }
     return ok != 0;

@@ -6,8 +6,9 @@
 namespace etale {
 
 struct SearchTuning {
-    u32 stage_rows = 16;   // rows gathered per bulk-copy batch
-    u32 seen_bits = 9;     // log2 of the evaluated-id cache slots
+    u32 stage_rows = 16;       // rows gathered per bulk-copy batch
+    u32 seen_bits = 9;         // log2 of the evaluated-id cache slots
+    u32 warps_per_block = 4;   // queries in flight per block: 2, 4 or 8
 };
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The
@@ -17,7 +18,7 @@ struct SearchTuning {
 cudaError_t smem_at_least(const void *fn, size_t bytes);
 
 // search.cu
-size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots);
+size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 wpb);
 // seed_kernel: top-L of the entry set per query into `seed` (nq x L); it
 // must precede the search launch that reads `seed`.
 // qsel (optional): the batch is the queries qsel[0 .. n) (n = *nq_dev), each

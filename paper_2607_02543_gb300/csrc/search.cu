@@ -455,8 +455,9 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     }
 }
 
-template <int P, bool LOG = false>
-__global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
+// WPB warps (queries in flight) per block; about 24 resident warps per SM.
+template <int P, bool LOG = false, int WPB = 4>
+__global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -628,8 +629,8 @@ __global__ void __launch_bounds__(128, 6) search_kernel(SearchArgs a) {
     }
 }
 
-size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots) {
-    return 4 * search_warp_bytes(mp, L, stage_rows, seen_slots, mp * 4);
+size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 wpb) {
+    return (size_t)wpb * search_warp_bytes(mp, L, stage_rows, seen_slots, mp * 4);
 }
 
 cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec,
@@ -673,6 +674,8 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.elog_n = elog_n;
     a.elog_cap = elog_cap;
     const bool log = elog != nullptr;
+    const u32 wpb = log ? 4u : tune.warps_per_block;
+    if (wpb != 2 && wpb != 4 && wpb != 8) return cudaErrorInvalidValue;
     // the rerank buffer (up to the beam, rounded up to a power of two >= 64
     // keys) lives in the stage
     if (prec != 0 && mode == 0) {
@@ -680,29 +683,25 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
         while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
         if ((size_t)a.stage_rows * a.rowb < rn * 8) a.stage_rows = (u32)((rn * 8 + a.rowb - 1) / a.rowb);
     }
-    const void *fn = log ? (prec == 1 ? (const void *)search_kernel<1, true> : prec == 2 ? (const void *)search_kernel<2, true>
-                                                                                      : (const void *)search_kernel<0, true>)
-                         : (prec == 1 ? (const void *)search_kernel<1> : prec == 2 ? (const void *)search_kernel<2>
-                                                                                   : (const void *)search_kernel<0>);
-    size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
+    using K = void (*)(SearchArgs);
+    K fn = nullptr;
+    if (log) fn = prec == 1 ? search_kernel<1, true> : prec == 2 ? search_kernel<2, true> : search_kernel<0, true>;
+    else if (wpb == 2) fn = prec == 1 ? search_kernel<1, false, 2> : prec == 2 ? search_kernel<2, false, 2> : search_kernel<0, false, 2>;
+    else if (wpb == 8) fn = prec == 1 ? search_kernel<1, false, 8> : prec == 2 ? search_kernel<2, false, 8> : search_kernel<0, false, 8>;
+    else fn = prec == 1 ? search_kernel<1> : prec == 2 ? search_kernel<2> : search_kernel<0>;
+    size_t smem = (size_t)wpb * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
     cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 32 * wpb, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     u32 blocks = (u32)(per_sm * num_sms);
-    u32 need = (nq + 3) / 4;
+    u32 need = (nq + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
     e = cudaMemsetAsync(d.ctr + a.wq, 0, sizeof(u64), st);
     if (e != cudaSuccess) return e;
-    if (log) {
-        if (prec == 1) search_kernel<1, true><<<blocks, 128, smem, st>>>(a);
-        else if (prec == 2) search_kernel<2, true><<<blocks, 128, smem, st>>>(a);
-        else search_kernel<0, true><<<blocks, 128, smem, st>>>(a);
-    } else if (prec == 1) search_kernel<1><<<blocks, 128, smem, st>>>(a);
-    else if (prec == 2) search_kernel<2><<<blocks, 128, smem, st>>>(a);
-    else search_kernel<0><<<blocks, 128, smem, st>>>(a);
+    fn<<<blocks, 32 * wpb, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -28,12 +28,13 @@ def test_launch_shapes_do_not_change_results(index):
     g, w, plan, dev = index
     q = torch.from_numpy(plan.queries).to(dev)
     ref = g.search(q, 10, 64)
-    for rows, bits in [(8, 8), (16, 9), (32, 11), (4, 12)]:
-        g.set_search_tuning(rows, bits)
+    for rows, bits, wpb in [(8, 8, 4), (16, 9, 2), (32, 11, 8), (4, 12, 2), (8, 8, 8)]:
+        g.set_search_tuning(rows, bits, wpb)
         ids, d = g.search(q, 10, 64)
-        assert torch.equal(ids, ref[0]) and torch.equal(d, ref[1]), (rows, bits)
+        assert torch.equal(ids, ref[0]) and torch.equal(d, ref[1]), (rows, bits, wpb)
     tried = g.autotune_search(q, 10, 64)
-    assert len(tried) >= 6 and all(ms > 0 for *_, ms in tried)
+    assert len(tried) >= 6 and all(t[2] > 0 for t in tried)
+    assert {t[3] for t in tried} == {2, 4, 8}
     ids, d = g.search(q, 10, 64)
     assert torch.equal(ids, ref[0]) and torch.equal(d, ref[1])
 
@@ -65,3 +66,26 @@ def test_one_graph_serves_every_batch_size(index):
         g.insert(W.Mixture(w).draw("inserts", 300))
         g.reclaim()
     graph.close()
+
+
+def test_autotune_beam_picks_smallest_beam_for_target(index):
+    import torch
+    g, w, plan, dev = index
+    q = torch.from_numpy(plan.queries).to(dev)
+    beams = (16, 24, 32, 48, 64, 96)
+    chosen, tried = g.autotune_beam(q, 10, 0.97, beams)
+    gt, _ = g.ground_truth(q, 10)
+    gt = gt.cpu().numpy().view(np.uint32)
+
+    def recall(b):
+        ids, _ = g.search(q, 10, b)
+        got = ids.cpu().numpy().view(np.uint32)
+        return float(np.mean([len(set(a.tolist()) & set(c.tolist())) / 10 for a, c in zip(got, gt)]))
+
+    assert [b for b, _ in tried] == list(beams[:len(tried)])
+    for b, r in tried:
+        assert abs(r - recall(b)) < 1e-6, (b, r)
+    if tried[-1][1] >= 0.97:
+        assert chosen == tried[-1][0] and all(r < 0.97 for _, r in tried[:-1])
+    else:
+        assert chosen == beams[-1] and len(tried) == len(beams)
