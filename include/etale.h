@@ -396,6 +396,55 @@ etale_status etale_round_graph_launch(etale_round_graph *g, void *stream);
 etale_status etale_round_graph_sync(etale_round_graph *g);
 etale_status etale_round_graph_destroy(etale_round_graph *g);
 
+/* ---- serving ring (deployment support; the paper's two-stream serving,
+ *      Sec. 5.5, with requests admitted while a launch runs) ------------- */
+/* A ring of `slots` query slots in pinned, host-mapped memory.  The host
+ * writes query rows into slots (row stride round_up(dim, 4) floats, the
+ * padding left at zero) and publishes the number of tickets submitted;
+ * ticket t uses slot t % slots.  Each etale_ring_launch enqueues one bounded
+ * persistent search launch on `stream`: its warps take submitted tickets in
+ * order as they become free, including tickets published while the launch
+ * runs, seed each query from the entry set (the same seeds as etale_search),
+ * run the query BeamSearch (k, beam and precision as etale_search) and write
+ * the k results into the slot's host-mapped rows, then done[slot] = t + 1 and
+ * served_by[slot] = the launch's sequence number.  A launch stops taking
+ * tickets after max_us microseconds or when the ring is closed, and ends
+ * once its warps finish the queries they hold; the caller keeps one launch
+ * in flight to serve continuously.  Slabs are recycled only between
+ * launches (in concurrent mode the launch counts as a query search for
+ * writer calls), so a query never reads a reused slab (Lemma 1).
+ * Flow control is the caller's: ticket t may be written only once
+ * done[t % slots] == t - slots + 1 (or the slot is unused).  Results equal
+ * etale_search's for the same query, k and beam.                           */
+typedef struct etale_ring etale_ring;
+etale_status etale_ring_create(etale_index *idx, uint32_t slots, uint32_t k, uint32_t beam, etale_ring **out);
+/* Host views: rows (slots x row_stride floats), ids / dists (slots x k),
+ * done (slots), served_by (slots).  Any pointer may be NULL.               */
+etale_status etale_ring_buffers(etale_ring *r, float **rows, uint32_t *row_stride, uint32_t **ids, float **dists,
+                                uint64_t **done, uint32_t **served_by);
+/* Make tickets [0, tail) visible to launches (a release store; rows first). */
+etale_status etale_ring_publish(etale_ring *r, uint64_t tail);
+etale_status etale_ring_close(etale_ring *r, int closed);
+/* blocks: thread blocks of 4 warps (0 = 2 per SM); *seq (may be NULL)
+ * receives the launch's sequence number.                                   */
+etale_status etale_ring_launch(etale_ring *r, uint32_t max_us, uint32_t blocks, uint32_t *seq, void *stream);
+/* Serve n queries (HOST rows, n x dim) arriving at arrival_s[i] seconds from
+ * the call's start (ascending): native threads submit each query into the
+ * ring at its arrival time (waiting for a free slot), keep one launch of at
+ * most max_us microseconds in flight on `stream`, and collect completions.
+ * issued_s[i] (may be NULL) receives when query i was written into a slot,
+ * completion_s[i] when its results were seen on the host; out_ids /
+ * out_dists (n x k, may be NULL) the results; *mid_launch (may be NULL) the
+ * number of queries taken by a launch issued before they were submitted;
+ * *launches (may be NULL) the launches made.  Runs without the caller (for
+ * example, another thread may run update calls on another stream meanwhile,
+ * in concurrent mode).                                                     */
+etale_status etale_ring_serve(etale_ring *r, const float *queries, const double *arrival_s, uint64_t n,
+                              uint32_t max_us, uint32_t blocks, double *issued_s, double *completion_s,
+                              uint32_t *out_ids, float *out_dists, uint64_t *mid_launch, uint32_t *launches,
+                              void *stream);
+etale_status etale_ring_destroy(etale_ring *r);
+
 /* How the last etale_ground_truth call ran: *path 0 CUDA cores, 1 tensor
  * cores on bf16-exact data, 2 tensor cores with the hi/lo split;
  * *fallback_queries = queries recomputed on CUDA cores.  Diagnostic.        */

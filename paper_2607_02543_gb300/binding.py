@@ -61,7 +61,8 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
            "etale_load", "etale_search_eval_count", "etale_round_graph_create",
            "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy",
-           "etale_set_insert_precision", "etale_set_rerank", "etale_autotune_beam"]
+           "etale_set_insert_precision", "etale_set_rerank", "etale_autotune_beam", "etale_ring_create",
+           "etale_ring_buffers", "etale_ring_publish", "etale_ring_close", "etale_ring_launch", "etale_ring_destroy", "etale_ring_serve"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -101,6 +102,14 @@ def load(path: str = LIB_PATH):
             "etale_set_search_precision": ([P, C.c_int], C.c_int),
             "etale_set_insert_precision": ([P, C.c_int], C.c_int),
             "etale_set_rerank": ([P, U32], C.c_int),
+            "etale_ring_create": ([P, U32, U32, U32, C.POINTER(P)], C.c_int),
+            "etale_ring_buffers": ([P, C.POINTER(P), C.POINTER(U32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                    C.POINTER(P)], C.c_int),
+            "etale_ring_publish": ([P, U64], C.c_int),
+            "etale_ring_close": ([P, C.c_int], C.c_int),
+            "etale_ring_launch": ([P, U32, U32, C.POINTER(U32), P], C.c_int),
+            "etale_ring_destroy": ([P], C.c_int),
+            "etale_ring_serve": ([P, P, P, U64, U32, U32, P, P, P, P, C.POINTER(U64), C.POINTER(U32), P], C.c_int),
             "etale_autotune_beam": ([P, P, U64, U32, C.c_float, P, U32, P, C.POINTER(U32), P], C.c_int),
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
             "etale_set_concurrent": ([P, C.c_int], C.c_int),
@@ -454,6 +463,69 @@ class RoundGraph:
     def close(self):
         if getattr(self, "h", None):
             self.index.lib.etale_round_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ring:
+    """A serving ring (see etale_ring_create): numpy views of the host-mapped
+    slots, submission and launches."""
+
+    def __init__(self, index: Index, slots: int, k: int, beam: int):
+        self.index, self.slots, self.k = index, slots, k
+        h = C.c_void_p()
+        index._check(index.lib.etale_ring_create(index.h, slots, k, beam, C.byref(h)))
+        self.h = h
+        rows, ids, dists, done, served = (C.c_void_p() for _ in range(5))
+        stride = C.c_uint32()
+        index._check(index.lib.etale_ring_buffers(h, C.byref(rows), C.byref(stride), C.byref(ids), C.byref(dists),
+                                                  C.byref(done), C.byref(served)))
+        self.stride = stride.value
+
+        def view(p, dtype, shape):
+            n = int(np.prod(shape))
+            buf = (C.c_byte * (n * np.dtype(dtype).itemsize)).from_address(p.value)
+            return np.frombuffer(buf, dtype=dtype).reshape(shape)
+        self.rows = view(rows, np.float32, (slots, self.stride))
+        self.ids = view(ids, np.uint32, (slots, k))
+        self.dists = view(dists, np.float32, (slots, k))
+        self.done = view(done, np.uint64, (slots,))
+        self.served_by = view(served, np.uint32, (slots,))
+
+    def publish(self, tail: int):
+        self.index._check(self.index.lib.etale_ring_publish(self.h, tail))
+
+    def close_ring(self, closed: bool = True):
+        self.index._check(self.index.lib.etale_ring_close(self.h, int(closed)))
+
+    def launch(self, max_us: int = 2000, blocks: int = 0, stream=None) -> int:
+        seq = C.c_uint32()
+        self.index._check(self.index.lib.etale_ring_launch(self.h, max_us, blocks, C.byref(seq), _stream(stream)))
+        return seq.value
+
+    def serve(self, queries: np.ndarray, arrival_s: np.ndarray, max_us: int = 2000, blocks: int = 0,
+              stream=None) -> dict:
+        """etale_ring_serve: queries (host, n x dim) arriving at arrival_s (ascending seconds)."""
+        q = np.ascontiguousarray(queries, dtype=np.float32)
+        a = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        n = q.shape[0]
+        issued, done = np.empty(n, np.float64), np.empty(n, np.float64)
+        ids, dists = np.empty((n, self.k), np.uint32), np.empty((n, self.k), np.float32)
+        mid, nl = C.c_uint64(), C.c_uint32()
+        self.index._check(self.index.lib.etale_ring_serve(self.h, _ptr(q), _ptr(a), n, max_us, blocks, _ptr(issued),
+                                                          _ptr(done), _ptr(ids), _ptr(dists), C.byref(mid),
+                                                          C.byref(nl), _stream(stream)))
+        return {"issued": issued, "done": done, "ids": ids, "dists": dists, "mid_launch": mid.value,
+                "launches": nl.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.index.lib.etale_ring_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -4,6 +4,8 @@
 // followed by the recycle launch (Sec. 3.3, Lemma 1, Definition 2).
 #include <algorithm>
 #include <atomic>
+#include <thread>
+#include <chrono>
 #include <initializer_list>
 #include <mutex>
 #include <cstdarg>
@@ -1838,6 +1840,224 @@ etale_status etale_round_graph_destroy(etale_round_graph *g) {
     cudaFree(g->q_pad);
     cudaFree(g->q_seed);
     delete g;
+    return ETALE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving ring (see launch_ring_search): slots of query rows and results in
+// pinned, mapped host memory, so that the host submits and collects without
+// copies and a running launch sees new submissions.
+// ---------------------------------------------------------------------------
+struct etale_ring {
+    etale_index *idx = nullptr;
+    u32 slots = 0, k = 0, L = 0, seq = 0;
+    void *host = nullptr;                 // one mapped allocation
+    float *rows = nullptr;                // slots x mp
+    u32 *ids = nullptr, *served_by = nullptr;
+    float *dists = nullptr;
+    u64 *done = nullptr, *ctl = nullptr;  // ctl[0] tail, ctl[1] closed
+    float *d_rows = nullptr;
+    u32 *d_ids = nullptr, *d_served = nullptr;
+    float *d_dists = nullptr;
+    u64 *d_done = nullptr, *d_ctl = nullptr;
+    u64 *head = nullptr, *seed = nullptr; // device memory
+    u64 tickets = 0;                      // tickets published so far (etale_ring_serve)
+};
+
+etale_status etale_ring_create(etale_index *idx, uint32_t slots, uint32_t k, uint32_t beam, etale_ring **out) {
+    if (!idx || !out) return ETALE_EINVAL;
+    *out = nullptr;
+    const u32 L = beam > k ? beam : k;
+    if (slots == 0 || slots > (1u << 24) || k == 0 || L > 256)
+        return idx->fail(ETALE_EINVAL, "ring needs 1..2^24 slots, k > 0 and beam <= 256");
+    if (idx->search_prec && k > 64) return idx->fail(ETALE_EINVAL, "reduced-precision search needs k <= 64");
+    etale_ring *r = new etale_ring();
+    r->idx = idx; r->slots = slots; r->k = k; r->L = L;
+    const size_t b_rows = (size_t)slots * idx->mp * 4, b_ids = (size_t)slots * k * 4, b_served = (size_t)slots * 4;
+    const size_t o_ids = (b_rows + 255) / 256 * 256, o_dists = o_ids + (b_ids + 255) / 256 * 256;
+    const size_t o_done = o_dists + (b_ids + 255) / 256 * 256, o_served = o_done + ((size_t)slots * 8 + 255) / 256 * 256;
+    const size_t o_ctl = o_served + (b_served + 255) / 256 * 256, total = o_ctl + 256;
+    char *d = nullptr;
+    bool ok = cudaHostAlloc(&r->host, total, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer((void **)&d, r->host, 0) == cudaSuccess &&
+              cudaMalloc(&r->head, 8) == cudaSuccess && cudaMemset(r->head, 0, 8) == cudaSuccess &&
+              cudaMalloc(&r->seed, (size_t)slots * L * 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        etale_ring_destroy(r);
+        return idx->fail(ETALE_ENOMEM, "ring allocation");
+    }
+    memset(r->host, 0, total);
+    char *h = static_cast<char *>(r->host);
+    r->rows = reinterpret_cast<float *>(h); r->d_rows = reinterpret_cast<float *>(d);
+    r->ids = reinterpret_cast<u32 *>(h + o_ids); r->d_ids = reinterpret_cast<u32 *>(d + o_ids);
+    r->dists = reinterpret_cast<float *>(h + o_dists); r->d_dists = reinterpret_cast<float *>(d + o_dists);
+    r->done = reinterpret_cast<u64 *>(h + o_done); r->d_done = reinterpret_cast<u64 *>(d + o_done);
+    r->served_by = reinterpret_cast<u32 *>(h + o_served); r->d_served = reinterpret_cast<u32 *>(d + o_served);
+    r->ctl = reinterpret_cast<u64 *>(h + o_ctl); r->d_ctl = reinterpret_cast<u64 *>(d + o_ctl);
+    *out = r;
+    return ETALE_OK;
+}
+
+etale_status etale_ring_buffers(etale_ring *r, float **rows, uint32_t *row_stride, uint32_t **ids, float **dists,
+                                uint64_t **done, uint32_t **served_by) {
+    if (!r) return ETALE_EINVAL;
+    if (rows) *rows = r->rows;
+    if (row_stride) *row_stride = r->idx->mp;
+    if (ids) *ids = r->ids;
+    if (dists) *dists = r->dists;
+    if (done) *done = reinterpret_cast<uint64_t *>(r->done);
+    if (served_by) *served_by = r->served_by;
+    return ETALE_OK;
+}
+
+etale_status etale_ring_publish(etale_ring *r, uint64_t tail) {
+    if (!r) return ETALE_EINVAL;
+    __atomic_store_n(&r->ctl[0], tail, __ATOMIC_RELEASE);
+    return ETALE_OK;
+}
+
+etale_status etale_ring_close(etale_ring *r, int closed) {
+    if (!r) return ETALE_EINVAL;
+    __atomic_store_n(&r->ctl[1], (u64)(closed != 0), __ATOMIC_RELEASE);
+    return ETALE_OK;
+}
+
+etale_status etale_ring_launch(etale_ring *r, uint32_t max_us, uint32_t blocks, uint32_t *seq, void *stream) {
+    if (!r) return ETALE_EINVAL;
+    etale_index *idx = r->idx;
+    if (max_us == 0 || max_us > 1000000) return idx->fail(ETALE_EINVAL, "max_us must be 1..1e6");
+    if (blocks == 0) blocks = (u32)idx->num_sms * 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * r->L;
+    Dev d = idx->dev();
+    const u32 sq = ++r->seq;
+    CK(launch_ring_search(d, r->d_rows, r->slots, r->L, H, r->k, r->d_ids, r->d_dists, r->seed,
+                          fit_tuning(idx, r->L, idx->tune), blocks, st, idx->search_prec, idx->cfg.rerank, r->head,
+                          r->d_ctl, r->d_ctl + 1, r->d_done, r->d_served, sq, (u64)max_us * 1000ull),
+       "ring launch");
+    g_kernel_launches++;
+    if (seq) *seq = sq;
+    if (idx->concurrent) {
+        std::lock_guard<std::mutex> lk(idx->mu);
+        CK(cudaEventRecord(idx->search_ev, st), "record search event");
+        idx->search_ev_valid = true;
+    }
+    return ETALE_OK;
+}
+
+etale_status etale_ring_serve(etale_ring *r, const float *queries, const double *arrival_s, uint64_t n,
+                             uint32_t max_us, uint32_t blocks, double *issued_s, double *completion_s,
+                             uint32_t *out_ids, float *out_dists, uint64_t *mid_launch, uint32_t *launches,
+                             void *stream) {
+    if (!r || (n && (!queries || !arrival_s || !completion_s))) return ETALE_EINVAL;
+    etale_index *idx = r->idx;
+    if (max_us == 0 || max_us > 1000000) return idx->fail(ETALE_EINVAL, "max_us must be 1..1e6");
+    for (u64 i = 1; i < n; i++)
+        if (arrival_s[i] < arrival_s[i - 1]) return idx->fail(ETALE_EINVAL, "arrivals must ascend");
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    const u64 base = r->tickets, S = r->slots, K = r->k, dim = idx->dim, mp = idx->mp;
+    std::vector<std::atomic<unsigned char>> collected(n);
+    for (auto &c : collected) c.store(0);
+    std::vector<double> issue_of_seq;         // host issue time of each launch of this call
+    std::mutex seq_mu;
+    std::atomic<bool> finished{false};
+    std::atomic<u64> mids{0};
+    std::atomic<u32> nlaunch{0};
+    std::atomic<int> launch_err{0};
+    const u32 seq0 = r->seq + 1;
+    std::vector<double> issued_local(issued_s ? 0 : n);
+    double *iss = issued_s ? issued_s : issued_local.data();
+    __atomic_store_n(&r->ctl[1], 0ull, __ATOMIC_RELEASE);
+    // one bounded launch always in flight
+    std::thread launcher([&]() {
+        cudaStream_t st = (cudaStream_t)stream;
+        while (!finished.load()) {
+            uint32_t sq = 0;
+            {
+                std::lock_guard<std::mutex> lk(seq_mu);
+                issue_of_seq.push_back(now_s());
+            }
+            if (etale_ring_launch(r, max_us, blocks, &sq, stream) != ETALE_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+                launch_err.store(1);
+                finished.store(true);
+                break;
+            }
+            nlaunch++;
+        }
+    });
+    // completions, in any order; results copied out before a slot is reused
+    std::thread collector([&]() {
+        u64 nxt = 0;
+        std::vector<unsigned char> seen(n, 0);
+        while (nxt < n && !launch_err.load()) {
+            bool any = false;
+            const u64 hi = std::min<u64>(n, nxt + S);
+            for (u64 i = nxt; i < hi; i++) {
+                if (seen[i]) continue;
+                const u64 t = base + i, slot = t % S;
+                if (__atomic_load_n(&r->done[slot], __ATOMIC_ACQUIRE) != t + 1) continue;
+                completion_s[i] = now_s();
+                if (out_ids) memcpy(out_ids + i * K, r->ids + slot * K, K * 4);
+                if (out_dists) memcpy(out_dists + i * K, r->dists + slot * K, K * 4);
+                const u32 sq = __atomic_load_n(&r->served_by[slot], __ATOMIC_RELAXED);
+                {
+                    std::lock_guard<std::mutex> lk(seq_mu);
+                    if (sq >= seq0 && sq - seq0 < issue_of_seq.size() && issue_of_seq[sq - seq0] < iss[i]) mids++;
+                }
+                seen[i] = 1;
+                collected[i].store(1, std::memory_order_release);
+                any = true;
+            }
+            while (nxt < n && seen[nxt]) nxt++;
+            if (!any) std::this_thread::sleep_for(std::chrono::microseconds(10));
+        }
+    });
+    // submissions at their arrival times; a slot is rewritten only after its
+    // previous query's results were collected
+    u64 i = 0;
+    while (i < n && !launch_err.load()) {
+        const double now = now_s();
+        if (arrival_s[i] > now) {
+            const double wait = arrival_s[i] - now;
+            if (wait > 50e-6) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait - 20e-6, 1e-3)));
+            continue;
+        }
+        u64 j = i;
+        while (j < n && arrival_s[j] <= now) {
+            if (j >= S && !collected[j - S].load(std::memory_order_acquire)) break;
+            const u64 slot = (base + j) % S;
+            memcpy(r->rows + slot * mp, queries + j * dim, dim * 4);
+            iss[j] = now_s();
+            j++;
+        }
+        if (j > i) {
+            __atomic_store_n(&r->ctl[0], base + j, __ATOMIC_RELEASE);
+            i = j;
+        } else {
+            std::this_thread::sleep_for(std::chrono::microseconds(10));
+        }
+    }
+    collector.join();
+    finished.store(true);
+    __atomic_store_n(&r->ctl[1], 1ull, __ATOMIC_RELEASE);   // the launch in flight ends now
+    launcher.join();
+    __atomic_store_n(&r->ctl[1], 0ull, __ATOMIC_RELEASE);
+    r->tickets = base + n;
+    if (mid_launch) *mid_launch = mids.load();
+    if (launches) *launches = nlaunch.load();
+    if (launch_err.load()) return idx->fail(ETALE_ECUDA, "ring launch failed during serving");
+    return check_search_errors(idx, (cudaStream_t)stream);
+}
+
+etale_status etale_ring_destroy(etale_ring *r) {
+    if (!r) return ETALE_OK;
+    if (r->host) cudaFreeHost(r->host);
+    cudaFree(r->head);
+    cudaFree(r->seed);
+    delete r;
     return ETALE_OK;
 }
 

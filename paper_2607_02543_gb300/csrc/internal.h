@@ -34,6 +34,13 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec = 0,
                           u32 rerank = 4, const u32 *nq_dev = nullptr, bool exact_rows = false,
                           u32 *elog = nullptr, u32 *elog_n = nullptr, u32 elog_cap = 0);
+// Serving ring (a bounded persistent search launch over host-mapped slots):
+// rows / out_ids / out_dist / tail / closed / done / served_by are device
+// views of host-mapped memory; head and seed are device memory.
+cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 max_hops, u32 k, u32 *out_ids,
+                               float *out_dist, u64 *seed, const SearchTuning &tune, u32 blocks, cudaStream_t st,
+                               u32 prec, u32 rerank, u64 *head, const u64 *tail, const u64 *closed, u64 *done,
+                               u32 *served_by, u32 seq, u64 max_ns);
 // Diagnostic: distinct ids each query evaluated (its log, elog_cap slots per
 // query, from a launch_search with elog set), not counting its n0 seeds;
 // out[0] += evaluations, out[1] += distinct non-seed ids, out[2] += overflows.

@@ -455,6 +455,164 @@ __global__ void __launch_bounds__(256) seed_kernel(SeedArgs a) {
     }
 }
 
+// One query's BeamSearch by one warp, for slot qi: the query row is
+// a.q + qi * mp, the beam starts from the seeds a.seed + qi * L (the L
+// nearest entry points, KEY_INF padded, n0 of them valid); query mode writes
+// the k results to a.out_ids / a.out_dist + qi * k, insert mode the expanded
+// keys of batch member qi.  The reference words of the seeds are sampled here.
+template <int P, bool LOG>
+__device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32 qi, int n0, u32 &phase,
+                                           u64 &nexp_tot, u64 &ndist, bool &timeout) {
+    const int lane = lane_id();
+    const Dev &d = a.d;
+    const u32 mp = d.mp;
+    const float *qrow = a.q + (size_t)qi * mp;
+    const u64 *seed_row = a.seed + (size_t)qi * a.L;
+    for (u32 i = lane * 4; i < mp; i += 128)
+        *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
+    for (u32 i = lane; i < a.seen_slots; i += 32) s.seen[i] = NIL;
+    __syncwarp();
+    float4 qr[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+        const u32 i = 4u * ((lane & 7) + 8 * t);
+        qr[t] = i < mp ? *reinterpret_cast<const float4 *>(s.qv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // initial beam: the L nearest members of the entry set E, computed by
+    // seed_kernel; the reference words are sampled here
+    for (int i = lane; i < n0; i += 32) {
+        const u64 k = seed_row[i];
+        const u32 id = key_id(k);
+        s.bkey[i] = k;
+        s.bref[i] = ld_ref(d, id);
+        s.bflag[i] = 0;
+        s.seen[seen_slot(id, a.seen_bits)] = id;
+    }
+    int n = n0;
+    __syncwarp();
+    u32 hops = 0, nexp = 0;
+    u32 qcnt = 0;
+    u32 *qlog = LOG ? a.elog + (size_t)qi * a.elog_cap : nullptr;
+    // slab entries of the predicted next expansion, loaded ahead of use
+    u32 pf_id = NIL, pf0 = NIL, pf1 = NIL;
+    int lo = 0;   // every beam entry before lo is expanded
+    for (;;) {
+        int first = -1;
+        for (int i0 = lo; i0 < n; i0 += 32) {
+            int i = i0 + lane;
+            u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
+            if (m) { first = i0 + __ffs(m) - 1; break; }
+        }
+        if (first < 0 || hops >= a.max_hops) break;
+        hops++;
+        lo = first + 1;
+        const u64 r = s.bref[first];
+        const u64 bkey = s.bkey[first];
+        const u32 fid = key_id(bkey);
+        const u32 sl = ref_slab(r), deg = sl == NIL ? 0 : ref_deg(r);
+        u32 e0 = NIL, e1 = NIL;
+        if (fid == pf_id) {
+            e0 = pf0; e1 = pf1;
+        } else {
+            if ((u32)lane < deg) e0 = d.slab[(size_t)sl * d.R + lane].x;
+            if ((u32)lane + 32 < deg) e1 = d.slab[(size_t)sl * d.R + lane + 32].x;
+        }
+        // predict the next expansion: the next unexpanded beam entry
+        pf_id = NIL;
+        for (int i0 = first + 1; i0 < n; i0 += 32) {
+            int i = i0 + lane;
+            u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
+            if (m) {
+                const int nx = i0 + __ffs(m) - 1;
+                const u64 r2 = s.bref[nx];
+                const u32 s2 = ref_slab(r2), d2 = s2 == NIL ? 0 : ref_deg(r2);
+                pf_id = key_id(s.bkey[nx]);
+                pf0 = (u32)lane < d2 ? d.slab[(size_t)s2 * d.R + lane].x : NIL;
+                pf1 = (u32)lane + 32 < d2 ? d.slab[(size_t)s2 * d.R + lane + 32].x : NIL;
+                break;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) s.bflag[first] = 1;
+        if (a.mode == 1 && lane == 0 && !ref_del(r)) a.exp_keys[(size_t)qi * a.max_hops + nexp] = bkey;
+        if (!ref_del(r)) nexp++;
+        __syncwarp();
+        for (u32 j0 = 0; j0 < deg; j0 += 32) {
+            u32 nb = j0 == 0 ? e0 : e1;
+            if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
+            n = eval_merge<P, LOG>(a, s, nb, n, phase, ndist, timeout, lo, qr, qlog, qcnt);
+        }
+    }
+    nexp_tot += hops;
+    if (LOG && lane == 0) a.elog_n[qi] = qcnt;
+    if (a.mode == 0 && P != 0 && !a.exact) {
+        // exact fp32 rerank of the best min(rerank * k, L) live candidates
+        u64 *rk = reinterpret_cast<u64 *>(s.stage);
+        const int want = (int)min(a.rerank * a.k, a.L);
+        int rn = 64;
+        while (rn < want) rn <<= 1;
+        int c = 0;
+        for (int i0 = 0; i0 < n && c < want; i0 += 32) {
+            const int i = i0 + lane;
+            const bool ok = i < n && !ref_del(s.bref[i]);
+            const u32 m = __ballot_sync(FULL, ok);
+            const int pos = c + __popc(m & lanemask_lt());
+            if (ok && pos < want) rk[pos] = s.bkey[i];
+            c = min(want, c + __popc(m));
+        }
+        __syncwarp();
+        const int grp = lane >> 3, g = lane & 7;
+        for (int r0 = 0; r0 < c; r0 += 4) {
+            const int cc = min(r0 + grp, c - 1);
+            const u32 id = key_id(rk[cc]);
+            const float dist = canon_dist<8>(s.qv, d.x + (size_t)id * mp, (int)mp, (int)d.metric, g);
+            __syncwarp();
+            if (r0 + grp < c && g == 0) rk[cc] = mkkey(dist, id);
+            __syncwarp();
+        }
+        for (int i = c + lane; i < rn; i += 32) rk[i] = KEY_INF;
+        __syncwarp();
+        warp_sort_u64(rk, rn);
+        // equal keys (an id seen twice) are adjacent after the sort: keep one
+        u32 outc = 0;
+        for (int i0 = 0; i0 < rn; i0 += 32) {
+            const int i = i0 + lane;
+            const bool ok = rk[i] != KEY_INF && (i == 0 || rk[i] != rk[i - 1]);
+            const u32 m = __ballot_sync(FULL, ok);
+            const u32 pos = outc + __popc(m & lanemask_lt());
+            if (ok && pos < a.k) {
+                a.out_ids[(size_t)qi * a.k + pos] = key_id(rk[i]);
+                a.out_dist[(size_t)qi * a.k + pos] = key_rho(rk[i]);
+            }
+            outc += __popc(m);
+        }
+        for (u32 p = outc + lane; p < a.k; p += 32) {
+            a.out_ids[(size_t)qi * a.k + p] = NIL;
+            a.out_dist[(size_t)qi * a.k + p] = __int_as_float(0x7f800000);
+        }
+    } else if (a.mode == 0) {
+        // first k beam entries whose sampled delta is 0
+        u32 c = 0;
+        for (int i0 = 0; i0 < n && c < a.k; i0 += 32) {
+            int i = i0 + lane;
+            bool ok = i < n && !ref_del(s.bref[i]);
+            u32 m = __ballot_sync(FULL, ok);
+            u32 pos = c + __popc(m & lanemask_lt());
+            if (ok && pos < a.k) {
+                a.out_ids[(size_t)qi * a.k + pos] = key_id(s.bkey[i]);
+                a.out_dist[(size_t)qi * a.k + pos] = key_rho(s.bkey[i]);
+            }
+            c += __popc(m);
+        }
+        for (u32 p = c + lane; p < a.k; p += 32) {
+            a.out_ids[(size_t)qi * a.k + p] = NIL;
+            a.out_dist[(size_t)qi * a.k + p] = __int_as_float(0x7f800000);
+        }
+    } else if (lane == 0) {
+        a.exp_count[qi] = nexp;
+    }
+}
+
 // WPB warps (queries in flight) per block; about 24 resident warps per SM.
 template <int P, bool LOG = false, int WPB = 4>
 __global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a) {
@@ -470,155 +628,136 @@ __global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a
     u64 nexp_tot = 0, ndist = 0;
     bool timeout = false;
     const u32 nq = a.nq_dev ? min(*a.nq_dev, a.nq) : a.nq;
+    const int n0 = (int)min(a.L, d.nent_dev ? *d.nent_dev : d.n_entries);
     for (;;) {
         u32 qi = 0;
         if (lane == 0) qi = (u32)atomicAdd(&d.ctr[a.wq], 1ull);
         qi = __shfl_sync(FULL, qi, 0);
         if (qi >= nq) break;
-        const float *qrow = a.q + (size_t)qi * mp;
-        for (u32 i = lane * 4; i < mp; i += 128)
-            *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
-        for (u32 i = lane; i < a.seen_slots; i += 32) s.seen[i] = NIL;
+        search_one<P, LOG>(a, s, qi, n0, phase, nexp_tot, ndist, timeout);
         __syncwarp();
-        float4 qr[4];
+    }
+    if (lane == 0) {
+        atomicAdd(&d.ctr[C_EXPAND], nexp_tot);
+        atomicAdd(&d.ctr[C_DIST], ndist);
+        if (timeout) atomicOr(&d.ctr[a.err], (u64)ERR_TIMEOUT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Serving ring: a bounded persistent launch that drains a ring of query
+// slots in host-mapped memory.  The host writes a query row into its slot,
+// then publishes the count of tickets submitted (tail, a release store).  A
+// warp claims the next ticket (head, device memory, by compare-and-swap
+// while head < tail), seeds the query from the entry set itself, runs the
+// BeamSearch and writes the k results into the slot's host-mapped result
+// rows, then publishes done[slot] = ticket + 1.  Queries submitted while the
+// launch runs are taken as warps free up.  A warp stops claiming once the
+// launch has run max_ns nanoseconds (globaltimer) or the ring is closed, so
+// every launch ends; slabs are recycled only between launches (Lemma 1).
+// ---------------------------------------------------------------------------
+struct RingArgs {
+    u64 *head;                 // device: tickets claimed
+    const u64 *tail;           // host-mapped: tickets submitted (host release store)
+    const u64 *closed;         // host-mapped: nonzero stops the claims
+    u64 *done;                 // host-mapped: done[slot] = ticket + 1 once written
+    u32 *served_by;            // host-mapped: launch sequence number that served the slot
+    u32 slots, seq;
+    u64 max_ns;
+};
+
+__device__ __forceinline__ u64 globaltimer_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ u64 ld_acquire_sys(const u64 *p) {
+    u64 v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(u64 *p, u64 v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr u32 RING_POLL_LIMIT = 1u << 22;   // each poll sleeps ~0.5 us at most
+
+// The L nearest entry points of the query in slot qi, by the same distances
+// and merge as seed_kernel (so the seeds equal a batch search's), into
+// a.seed + qi * L.  Uses s.qv (the query row), s.bkey and s.nkey.
+template <int P>
+__device__ void ring_seed(const SearchArgs &a, WarpSmem &s, u32 qi) {
+    const int lane = lane_id(), grp = lane >> 3, g = lane & 7;
+    const Dev &d = a.d;
+    const u32 mp = d.mp, L = a.L;
+    const float *qrow = a.q + (size_t)qi * mp;
+    for (u32 i = lane * 4; i < mp; i += 128)
+        *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
+    __syncwarp();
+    const u32 S = d.nent_dev ? *d.nent_dev : d.n_entries;
+    int n = 0;
+    for (u32 t0 = 0; t0 < S; t0 += 32) {
+        const int nt = (int)min(32u, S - t0);
+        u64 key = KEY_INF;
+        for (int r0 = 0; r0 < nt; r0 += 4) {
+            const int c = r0 + grp;
+            const int cc = c < nt ? c : nt - 1;
+            const u32 e = d.entries[t0 + cc];
+            const float dist = qdist<P>(s.qv, row_src<P>(d, e), P == 2 ? d.x8s[e] : 1.0f, (int)mp, (int)d.metric, g);
+            const u64 kk = mkkey(dist, e);
 #pragma unroll
-        for (int t = 0; t < 4; t++) {
-            const u32 i = 4u * ((lane & 7) + 8 * t);
-            qr[t] = i < mp ? *reinterpret_cast<const float4 *>(s.qv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int t = 0; t < 4; t++) {
+                const u64 v = __shfl_sync(FULL, kk, t * 8);
+                if (lane == r0 + t && r0 + t < nt) key = v;
+            }
         }
-        // initial beam: the L nearest members of the entry set E, computed by
-        // seed_kernel; the reference words are sampled here
+        n = seed_merge(s.bkey, s.nkey, key, n, (int)L);
+    }
+    u64 *seed_row = const_cast<u64 *>(a.seed) + (size_t)qi * L;   // the ring's own seed buffer
+    for (u32 i = lane; i < L; i += 32) seed_row[i] = (int)i < n ? s.bkey[i] : KEY_INF;
+    __syncwarp();
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, 4) ring_search_kernel(SearchArgs a, RingArgs r) {
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const Dev &d = a.d;
+    const size_t wb = search_warp_bytes(d.mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
+    WarpSmem s = carve(smem + warp * wb, d.mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
+    if (lane == 0) mbar_init(s.bar, 1);
+    __syncwarp();
+    u32 phase = 0;
+    u64 nexp_tot = 0, ndist = 0;
+    bool timeout = false;
+    const u64 t_end = globaltimer_ns() + r.max_ns;
+    for (;;) {
+        u64 t = KEY_INF;
+        if (lane == 0) {
+            for (u32 it = 0; it < RING_POLL_LIMIT; it++) {
+                // the lifetime bounds the launch even under steady arrivals
+                if (globaltimer_ns() >= t_end || ld_acquire_sys(r.closed)) break;
+                const u64 tail = ld_acquire_sys(r.tail);
+                const u64 h = *reinterpret_cast<volatile u64 *>(r.head);
+                if (h < tail) {
+                    if (atomicCAS(r.head, h, h + 1) == h) { t = h; break; }
+                    continue;
+                }
+                __nanosleep(500);
+            }
+        }
+        t = __shfl_sync(FULL, t, 0);
+        if (t == KEY_INF) break;
+        __threadfence_system();   // every lane reads the row after the claim's acquire
+        const u32 slot = (u32)(t % r.slots);
+        ring_seed<P>(a, s, slot);
         const int n0 = (int)min(a.L, d.nent_dev ? *d.nent_dev : d.n_entries);
-        for (int i = lane; i < n0; i += 32) {
-            const u64 k = a.seed[(size_t)qi * a.L + i];
-            const u32 id = key_id(k);
-            s.bkey[i] = k;
-            s.bref[i] = ld_ref(d, id);
-            s.bflag[i] = 0;
-            s.seen[seen_slot(id, a.seen_bits)] = id;
-        }
-        int n = n0;
+        search_one<P, false>(a, s, slot, n0, phase, nexp_tot, ndist, timeout);
         __syncwarp();
-        u32 hops = 0, nexp = 0;
-        u32 qcnt = 0;
-        u32 *qlog = LOG ? a.elog + (size_t)qi * a.elog_cap : nullptr;
-        // slab entries of the predicted next expansion, loaded ahead of use
-        u32 pf_id = NIL, pf0 = NIL, pf1 = NIL;
-        int lo = 0;   // every beam entry before lo is expanded
-        for (;;) {
-            int first = -1;
-            for (int i0 = lo; i0 < n; i0 += 32) {
-                int i = i0 + lane;
-                u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
-                if (m) { first = i0 + __ffs(m) - 1; break; }
-            }
-            if (first < 0 || hops >= a.max_hops) break;
-            hops++;
-            lo = first + 1;
-            const u64 r = s.bref[first];
-            const u64 bkey = s.bkey[first];
-            const u32 fid = key_id(bkey);
-            const u32 sl = ref_slab(r), deg = sl == NIL ? 0 : ref_deg(r);
-            u32 e0 = NIL, e1 = NIL;
-            if (fid == pf_id) {
-                e0 = pf0; e1 = pf1;
-            } else {
-                if ((u32)lane < deg) e0 = d.slab[(size_t)sl * d.R + lane].x;
-                if ((u32)lane + 32 < deg) e1 = d.slab[(size_t)sl * d.R + lane + 32].x;
-            }
-            // predict the next expansion: the next unexpanded beam entry
-            pf_id = NIL;
-            for (int i0 = first + 1; i0 < n; i0 += 32) {
-                int i = i0 + lane;
-                u32 m = __ballot_sync(FULL, i < n && !s.bflag[i]);
-                if (m) {
-                    const int nx = i0 + __ffs(m) - 1;
-                    const u64 r2 = s.bref[nx];
-                    const u32 s2 = ref_slab(r2), d2 = s2 == NIL ? 0 : ref_deg(r2);
-                    pf_id = key_id(s.bkey[nx]);
-                    pf0 = (u32)lane < d2 ? d.slab[(size_t)s2 * d.R + lane].x : NIL;
-                    pf1 = (u32)lane + 32 < d2 ? d.slab[(size_t)s2 * d.R + lane + 32].x : NIL;
-                    break;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) s.bflag[first] = 1;
-            if (a.mode == 1 && lane == 0 && !ref_del(r)) a.exp_keys[(size_t)qi * a.max_hops + nexp] = bkey;
-            if (!ref_del(r)) nexp++;
-            __syncwarp();
-            for (u32 j0 = 0; j0 < deg; j0 += 32) {
-                u32 nb = j0 == 0 ? e0 : e1;
-                if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
-                n = eval_merge<P, LOG>(a, s, nb, n, phase, ndist, timeout, lo, qr, qlog, qcnt);
-            }
-        }
-        nexp_tot += hops;
-        if (LOG && lane == 0) a.elog_n[qi] = qcnt;
-        if (a.mode == 0 && P != 0 && !a.exact) {
-            // exact fp32 rerank of the best min(rerank * k, L) live candidates
-            u64 *rk = reinterpret_cast<u64 *>(s.stage);
-            const int want = (int)min(a.rerank * a.k, a.L);
-            int rn = 64;
-            while (rn < want) rn <<= 1;
-            int c = 0;
-            for (int i0 = 0; i0 < n && c < want; i0 += 32) {
-                const int i = i0 + lane;
-                const bool ok = i < n && !ref_del(s.bref[i]);
-                const u32 m = __ballot_sync(FULL, ok);
-                const int pos = c + __popc(m & lanemask_lt());
-                if (ok && pos < want) rk[pos] = s.bkey[i];
-                c = min(want, c + __popc(m));
-            }
-            __syncwarp();
-            const int grp = lane >> 3, g = lane & 7;
-            for (int r0 = 0; r0 < c; r0 += 4) {
-                const int cc = min(r0 + grp, c - 1);
-                const u32 id = key_id(rk[cc]);
-                const float dist = canon_dist<8>(s.qv, d.x + (size_t)id * mp, (int)mp, (int)d.metric, g);
-                __syncwarp();
-                if (r0 + grp < c && g == 0) rk[cc] = mkkey(dist, id);
-                __syncwarp();
-            }
-            for (int i = c + lane; i < rn; i += 32) rk[i] = KEY_INF;
-            __syncwarp();
-            warp_sort_u64(rk, rn);
-            // equal keys (an id seen twice) are adjacent after the sort: keep one
-            u32 outc = 0;
-            for (int i0 = 0; i0 < rn; i0 += 32) {
-                const int i = i0 + lane;
-                const bool ok = rk[i] != KEY_INF && (i == 0 || rk[i] != rk[i - 1]);
-                const u32 m = __ballot_sync(FULL, ok);
-                const u32 pos = outc + __popc(m & lanemask_lt());
-                if (ok && pos < a.k) {
-                    a.out_ids[(size_t)qi * a.k + pos] = key_id(rk[i]);
-                    a.out_dist[(size_t)qi * a.k + pos] = key_rho(rk[i]);
-                }
-                outc += __popc(m);
-            }
-            for (u32 p = outc + lane; p < a.k; p += 32) {
-                a.out_ids[(size_t)qi * a.k + p] = NIL;
-                a.out_dist[(size_t)qi * a.k + p] = __int_as_float(0x7f800000);
-            }
-        } else if (a.mode == 0) {
-            // first k beam entries whose sampled delta is 0
-            u32 c = 0;
-            for (int i0 = 0; i0 < n && c < a.k; i0 += 32) {
-                int i = i0 + lane;
-                bool ok = i < n && !ref_del(s.bref[i]);
-                u32 m = __ballot_sync(FULL, ok);
-                u32 pos = c + __popc(m & lanemask_lt());
-                if (ok && pos < a.k) {
-                    a.out_ids[(size_t)qi * a.k + pos] = key_id(s.bkey[i]);
-                    a.out_dist[(size_t)qi * a.k + pos] = key_rho(s.bkey[i]);
-                }
-                c += __popc(m);
-            }
-            for (u32 p = c + lane; p < a.k; p += 32) {
-                a.out_ids[(size_t)qi * a.k + p] = NIL;
-                a.out_dist[(size_t)qi * a.k + p] = __int_as_float(0x7f800000);
-            }
-        } else if (lane == 0) {
-            a.exp_count[qi] = nexp;
+        if (lane == 0) {
+            r.served_by[slot] = r.seq;
+            __threadfence_system();   // the results and served_by before done
+            st_release_sys(r.done + slot, t + 1);
         }
         __syncwarp();
     }
@@ -627,6 +766,41 @@ __global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a
         atomicAdd(&d.ctr[C_DIST], ndist);
         if (timeout) atomicOr(&d.ctr[a.err], (u64)ERR_TIMEOUT);
     }
+}
+
+cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 max_hops, u32 k, u32 *out_ids,
+                               float *out_dist, u64 *seed, const SearchTuning &tune, u32 blocks, cudaStream_t st,
+                               u32 prec, u32 rerank, u64 *head, const u64 *tail, const u64 *closed, u64 *done,
+                               u32 *served_by, u32 seq, u64 max_ns) {
+    if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2 || blocks == 0) return cudaErrorInvalidValue;
+    SearchArgs a{};
+    a.d = d; a.q = rows; a.seed = seed; a.nq_dev = nullptr; a.nq = slots; a.L = L; a.max_hops = max_hops;
+    a.mode = 0; a.k = k; a.out_ids = out_ids; a.out_dist = out_dist;
+    a.stage_rows = tune.stage_rows;
+    a.seen_bits = tune.seen_bits;
+    a.seen_slots = 1u << tune.seen_bits;
+    a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
+    a.rerank = rerank;
+    a.exact = 0;
+    a.wq = C_WORK2;
+    a.err = C_ERR_S;
+    if (prec != 0) {
+        size_t rn = 64;
+        while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
+        if ((size_t)a.stage_rows * a.rowb < rn * 8) a.stage_rows = (u32)((rn * 8 + a.rowb - 1) / a.rowb);
+    }
+    RingArgs r{head, tail, closed, done, served_by, slots, seq, max_ns};
+    using K = void (*)(SearchArgs, RingArgs);
+    K fn = prec == 1 ? ring_search_kernel<1> : prec == 2 ? ring_search_kernel<2> : ring_search_kernel<0>;
+    const size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
+    cudaError_t e = smem_at_least((const void *)fn, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 128, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    fn<<<blocks, 128, smem, st>>>(a, r);
+    return cudaGetLastError();
 }
 
 size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 wpb) {

@@ -1,13 +1,20 @@
-"""Serving loop: continuous batching of queries and updates over one index.
+"""Serving loops: queries and updates over one index.
 
-Two worker threads share one index in concurrent mode (include/etale.h,
-etale_set_concurrent): a query worker and an update worker, each on its own
-CUDA stream, so their kernels overlap on the device as the paper's
-two-stream experiment does (Sec. 5.5).  A worker forms its next batch from
-every request that has arrived while its previous batch ran (continuous
-batching), up to a size cap.  The update worker admits an insert batch only
-when the free slab pool covers its worst case; otherwise it first reclaims
-(which returns tombstone slabs) and, if that is not enough, defers the batch.
+Updates run on their own CUDA stream in concurrent mode (include/etale.h,
+etale_set_concurrent), so their kernels overlap the queries' on the device as
+the paper's two-stream experiment does (Sec. 5.5).  The update worker admits
+an insert batch only when the free slab pool covers its worst case;
+otherwise it first reclaims (which returns tombstone slabs) and, if that is
+not enough, defers the batch.
+
+Queries are served in one of two ways:
+- Server: a query worker forms its next batch from every request that has
+  arrived while its previous batch ran, up to a size cap (batch-granular);
+- RingServer: slot-granular.  Arriving queries are written into the slots of
+  a serving ring (etale_ring_*) and published at once; one bounded persistent
+  launch is always in flight, and its warps take each query as soon as one
+  is free, including queries that arrived after the launch started.
+
 Latency of a request = completion time - arrival time.
 """
 from __future__ import annotations
@@ -190,3 +197,58 @@ def overlap_seconds(log) -> float:
         for ua, ub in u:
             tot += max(0.0, min(qb, ub) - max(qa, ua))
     return tot
+
+
+class RingServer(Server):
+    """Slot-granular serving: queries go through a serving ring while the
+    update worker of Server runs on the update stream.
+
+    slots: ring slots (a query waits for a free slot when all are in use);
+    max_us: the lifetime of one ring launch (a launch stops taking queries
+    after it, so writer calls, which wait for the last query launch before
+    recycling slabs, wait at most that long); blocks: thread blocks of a
+    launch (0: two per SM, leaving room for the update kernels).
+    """
+
+    def __init__(self, index, k: int = 10, beam: int = 64, slots: int = 4096, max_us: int = 2000,
+                 blocks: int = 0, max_update_batch: int = 4096, streams=(None, None), reclaim_every: int = 0):
+        super().__init__(index, k=k, beam=beam, max_update_batch=max_update_batch, streams=streams,
+                         reclaim_every=reclaim_every)
+        self.slots, self.max_us, self.blocks = slots, max_us, blocks
+
+    def run(self, requests: list[Request]) -> dict:
+        """Queries go through the ring (native submit / launch / collect
+        threads, etale_ring_serve) while this object's update worker runs on
+        the update stream."""
+        from .binding import Ring
+        queries = [r for r in requests if r.kind == "query"]
+        updates = [r for r in requests if r.kind != "query"]
+        ring = Ring(self.index, self.slots, self.k, self.beam)
+        self.index.set_concurrent(True)
+        t0 = time.perf_counter()
+        tu = threading.Thread(target=self._update_worker, args=(updates, t0))
+        tu.start()
+        res = None
+        if queries:
+            q = np.stack([r.payload for r in queries]).astype(np.float32)
+            arr = np.array([r.t for r in queries], dtype=np.float64)
+            # the native call counts time from its own start: shift arrivals
+            shift = time.perf_counter() - t0
+            res = ring.serve(q, np.maximum(arr - shift, 0.0), self.max_us, self.blocks, self.qstream)
+            for k, r in enumerate(queries):
+                r.issued = res["issued"][k] + shift
+                r.done = res["done"][k] + shift
+                r.result = (res["ids"][k], res["dists"][k])
+        tu.join()
+        wall = time.perf_counter() - t0
+        self.index.set_concurrent(False)
+        ring.close()
+        ql = [r.done - r.t for r in queries]
+        ul = [r.done - r.t for r in updates]
+        return {"wall_s": wall, "queries": percentiles(ql), "updates": percentiles(ul),
+                "query_throughput": len(queries) / wall if wall > 0 else 0.0,
+                "update_vectors_per_s": sum(len(r.payload) for r in updates) / wall if wall > 0 else 0.0,
+                "ring_launches": res["launches"] if res else 0,
+                "queries_taken_mid_launch": res["mid_launch"] if res else 0,
+                "update_batches": sum(1 for e in self.log if e[0] == "update"),
+                "deferred": self.deferred, "reclaims": self.reclaims}
