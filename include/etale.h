@@ -184,6 +184,12 @@ etale_status etale_set_search_precision(etale_index *idx, etale_precision p);
  * Recorded rounds use the precision in force when they are recorded.       */
 etale_status etale_set_insert_precision(etale_index *idx, etale_precision p);
 
+/* Size the grids of later eager update calls (insert, delete, reclaim) for
+ * this share of the SMs (0 < share <= 1; default 1), so that query launches
+ * running at the same time on another stream (concurrent mode, the serving
+ * ring) keep room on the device.  Results never depend on it.              */
+etale_status etale_set_writer_share(etale_index *idx, float share);
+
 /* Set cfg.rerank for later reduced-precision query searches (1..256).     */
 etale_status etale_set_rerank(etale_index *idx, uint32_t rerank);
 
@@ -505,6 +511,31 @@ etale_status etale_set_profiling(etale_index *idx, int enable);
 /* Copy accumulated milliseconds and launch counts for the first n phases
  * (either pointer may be NULL); reset = 1 clears the accumulators.         */
 etale_status etale_get_profile(etale_index *idx, double *ms, uint64_t *count, uint32_t n, int reset);
+
+/* Work tallies of the writer kernels (the paper has no counterpart; they
+ * give each kernel's algorithmic bytes for a roofline).  The kernels count,
+ * per warp, what their step of the method must move and add it once at the
+ * warp's end, always (no switch):
+ *   rows[k]  - bytes of vector rows gathered: the distinct rows of each
+ *              RobustPrune (Sec. 3.4.1) or distance step, in the copy that
+ *              step reads (fp32 rows, or the bf16 copy on the Gram path);
+ *   state[k] - bytes of graph state read or written: reference words,
+ *              slab entries, tombstone bits (Def. 1, Algorithm 1).
+ * Lists handed from one kernel to the next (candidate keys, offers, the
+ * replacement sets K(u, a)) are not counted.  Both accumulate over calls
+ * until reset = 1, which zeroes them after the copy.  Copies the first n
+ * kinds (either pointer may be NULL); synchronises the device.             */
+typedef enum {
+    ETALE_WK_PRUNE = 0,       /* forward RobustPrune + own publish              */
+    ETALE_WK_OFFER,           /* reverse-offer publication                      */
+    ETALE_WK_REFINE,          /* refine pass                                    */
+    ETALE_WK_REPAIR_K,        /* replacement sets K(u, a)                       */
+    ETALE_WK_REPAIR_FOLD,     /* repair publication                             */
+    ETALE_WK_COMPACT,         /* reclaim phase 1                                */
+    ETALE_WK_COUNT
+} etale_work_kind;
+
+etale_status etale_get_work(etale_index *idx, uint64_t *rows, uint64_t *state, uint32_t n, int reset);
 
 /* Query search that allocates nothing (the paper has no counterpart: this is
  * a deployment variant of etale_search).

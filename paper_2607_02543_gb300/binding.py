@@ -62,10 +62,12 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_load", "etale_search_eval_count", "etale_round_graph_create",
            "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy",
            "etale_set_insert_precision", "etale_set_rerank", "etale_autotune_beam", "etale_ring_create",
-           "etale_ring_buffers", "etale_ring_publish", "etale_ring_close", "etale_ring_launch", "etale_ring_destroy", "etale_ring_serve"]
+           "etale_ring_buffers", "etale_ring_publish", "etale_ring_close", "etale_ring_launch", "etale_ring_destroy", "etale_ring_serve", "etale_set_writer_share", "etale_get_work"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
+# etale_get_work kinds, in the header's order; each is timed as the phase named
+WORK_KINDS = ["prune", "offer_fold", "refine", "repair_k", "repair_fold", "compact"]
 
 _lock = threading.Lock()
 _lib = None
@@ -102,6 +104,8 @@ def load(path: str = LIB_PATH):
             "etale_set_search_precision": ([P, C.c_int], C.c_int),
             "etale_set_insert_precision": ([P, C.c_int], C.c_int),
             "etale_set_rerank": ([P, U32], C.c_int),
+            "etale_set_writer_share": ([P, C.c_float], C.c_int),
+            "etale_get_work": ([P, P, P, U32, C.c_int], C.c_int),
             "etale_ring_create": ([P, U32, U32, U32, C.POINTER(P)], C.c_int),
             "etale_ring_buffers": ([P, C.POINTER(P), C.POINTER(U32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                     C.POINTER(P)], C.c_int),
@@ -327,6 +331,10 @@ class Index:
         """"fp32", "bf16" or "fp8" for the BeamSearch of later inserts (rho stays exact fp32)."""
         self._check(self.lib.etale_set_insert_precision(self.h, {"fp32": 0, "bf16": 1, "fp8": 2}[prec]))
 
+    def set_writer_share(self, share: float):
+        """Grids of later eager update calls sized for this share of the SMs."""
+        self._check(self.lib.etale_set_writer_share(self.h, C.c_float(share)))
+
     def set_rerank(self, rerank: int):
         """Candidates re-scored in fp32 by reduced-precision queries: rerank * k (at most the beam)."""
         self._check(self.lib.etale_set_rerank(self.h, rerank))
@@ -422,6 +430,14 @@ class Index:
         cnt = np.zeros(n, np.uint64)
         self._check(self.lib.etale_get_profile(self.h, _ptr(ms), _ptr(cnt), n, int(reset)))
         return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    def work(self, reset: bool = False) -> dict:
+        """{kind: (row bytes, graph-state bytes)} tallied by the writer kernels."""
+        n = len(WORK_KINDS)
+        rows = np.zeros(n, np.uint64)
+        state = np.zeros(n, np.uint64)
+        self._check(self.lib.etale_get_work(self.h, _ptr(rows), _ptr(state), n, int(reset)))
+        return {k: (int(rows[i]), int(state[i])) for i, k in enumerate(WORK_KINDS)}
 
 
 class SearchGraph:

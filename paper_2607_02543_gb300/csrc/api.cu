@@ -75,6 +75,7 @@ u32 bits_for(u64 v) {
 
 struct etale_index {
     int device = 0, num_sms = 0, smem_optin = 0;
+    int writer_sms = 0;   // SMs the grids of update kernels are sized for (etale_set_writer_share)
     etale_config cfg{};
     u32 dim = 0, mp = 0, R = 0, metric = 0;
     u64 capacity = 0, pool = 0;
@@ -422,7 +423,7 @@ etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t 
             if (s != ETALE_OK) return s;
             {
                 PhaseScope ps(idx, ETALE_PH_OFFER_FOLD, st);
-                CK(launch_offer_fold(d, of, nullptr, seg_count, idx->cfg.cas_budget, idx->num_sms, st, (u32)lo,
+                CK(launch_offer_fold(d, of, nullptr, seg_count, idx->cfg.cas_budget, idx->writer_sms, st, (u32)lo,
                                      (u32)(lo + chunk)),
                    "offer fold");
             }
@@ -451,7 +452,7 @@ etale_status run_offers(etale_index *idx, u32 nslots, u64 targets, cudaStream_t 
     {
         PhaseScope ps(idx, ETALE_PH_OFFER_FOLD, st);
         CK(launch_offer_fold(d, of, as<u32>(idx->seg_start), seg_count, lockfree ? idx->cfg.cas_budget : 0,
-                             idx->num_sms, st),
+                             idx->writer_sms, st),
            "offer fold");
     }
     g_kernel_launches++;
@@ -504,14 +505,14 @@ SearchTuning fit_tuning(const etale_index *idx, u32 L, SearchTuning t) {
 // certified exact rerank when they apply, else the CUDA-core kernel; both
 // give the same seeds.  Returns the launches made.
 static etale_status seed_batch(etale_index *idx, const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, u32 prec,
-                               cudaStream_t st) {
+                               cudaStream_t st, int sms = 0) {
     const u32 S = idx->n_entries;
     if (prec == 0 && idx->seed_tc && !idx->concurrent && S > 0 && nq >= 32) {
         const SeedTcPlan p = seed_tc_plan(idx->dim, S, nq);
         if (!grow(idx->sd_A, p.bytes_A) || !grow(idx->sd_qstat, (size_t)nq * 16) ||
             !grow(idx->sd_keys, p.bytes_keys) || !grow(idx->sd_fb, (size_t)nq * 4) || !grow(idx->sd_ctr, 64))
             return idx->fail(ETALE_ENOMEM, "seed staging");
-        CK(launch_seed_tc(d, q, nq, S, L, seed, p, idx->seed_bufs(), idx->num_sms, st), "seed (tensor)");
+        CK(launch_seed_tc(d, q, nq, S, L, seed, p, idx->seed_bufs(), sms ? sms : idx->num_sms, st), "seed (tensor)");
         g_kernel_launches += 4;
         return ETALE_OK;
     }
@@ -533,14 +534,14 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     {
         PhaseScope ps(idx, ETALE_PH_SEED, st);
         etale_status s0 = seed_batch(idx, d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed),
-                                     idx->insert_prec, st);
+                                     idx->insert_prec, st, idx->writer_sms);
         if (s0 != ETALE_OK) return s0;
     }
     {
         PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
         CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr,
                          as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, L, idx->tune),
-                         idx->num_sms, st, idx->insert_prec, 4, nullptr, idx->insert_prec == 0 && exact_rows(idx)),
+                         idx->writer_sms, st, idx->insert_prec, 4, nullptr, idx->insert_prec == 0 && exact_rows(idx)),
            "insert search");
     }
     g_kernel_launches += 1;
@@ -550,7 +551,7 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
     {
         PhaseScope ps(idx, ETALE_PH_PRUNE, st);
         CK(launch_prune_insert(d, first, b, as<u64>(idx->exp_keys), as<u32>(idx->exp_count), H, idx->cfg.max_cand,
-                               as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->num_sms, st,
+                               as<u32>(idx->F_id), as<float>(idx->F_rho), as<u32>(idx->F_n), of, idx->writer_sms, st,
                                idx->insert_prec != 0),
            "prune insert");
     }
@@ -567,9 +568,9 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
         if (s != ETALE_OK) return s;
         {
             PhaseScope ps(idx, ETALE_PH_REFINE, st);
-            const size_t sb = refine_spill_bytes(d, idx->cfg.max_cand, idx->num_sms);
+            const size_t sb = refine_spill_bytes(d, idx->cfg.max_cand, idx->writer_sms);
             if (!grow(idx->refine_spill, sb)) return idx->fail(ETALE_ENOMEM, "refine spill lists");
-            CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->num_sms, st,
+            CK(launch_refine(d, first, b, rmode, idx->cfg.max_cand, of, idx->writer_sms, st,
                              static_cast<char *>(idx->refine_spill.p), sb),
                "refine");
         }
@@ -695,6 +696,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
     idx->alpha2 = cfg.alpha * cfg.alpha;
     cudaGetDevice(&idx->device);
     cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device);
+    idx->writer_sms = idx->num_sms;
     cudaDeviceGetAttribute(&idx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device);
     const size_t xb = (size_t)capacity * idx->mp * 4, rb = (size_t)capacity * 8;
     const size_t sb = (size_t)idx->pool * degree * 8, pb = (size_t)idx->pool * 4;
@@ -899,7 +901,7 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
     prof_begin(idx, ETALE_PH_REPAIR_K, st);
     CK(launch_fill_offer_keys(as<u32>(idx->pair_key), as<u32>(idx->pair_val), (u32)slots, invalid, st), "fill pairs");
     CK(launch_repair_k(d, as<u32>(idx->dt), n_dt, (u32)n, as<u32>(idx->pair_key), as<u32>(idx->pair_val),
-                       as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), idx->num_sms, st),
+                       as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), idx->writer_sms, st),
        "repair K");
     g_kernel_launches += 2;
     prof_end(idx, st);
@@ -914,7 +916,7 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
             prof_begin(idx, ETALE_PH_REPAIR_FOLD, st);
             CK(launch_repair_fold(d, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
                                   as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), nullptr, seg_count, chunk,
-                                  idx->cfg.cas_budget, idx->num_sms, st, lo),
+                                  idx->cfg.cas_budget, idx->writer_sms, st, lo),
                "repair fold");
             g_kernel_launches++;
             prof_end(idx, st);
@@ -938,7 +940,7 @@ etale_status etale_delete(etale_index *idx, const uint32_t *ids, uint64_t n, uin
     if (!lockfree) {
         CK(launch_repair_fold(d, as<u32>(idx->dt), as<u32>(idx->pair_key), as<u32>(idx->pair_val),
                               as<uint2>(idx->pair_K), as<u32>(idx->pair_Kn), as<u32>(idx->pair_seg), seg_count, slots,
-                              0, idx->num_sms, st),
+                              0, idx->writer_sms, st),
            "repair fold");
         g_kernel_launches++;
         prof_end(idx, st);
@@ -2410,6 +2412,13 @@ etale_status etale_load(const char *path, const etale_config *cfg_in, uint64_t c
     return ETALE_OK;
 }
 
+etale_status etale_set_writer_share(etale_index *idx, float share) {
+    if (!idx) return ETALE_EINVAL;
+    if (!(share > 0.f && share <= 1.f)) return idx->fail(ETALE_EINVAL, "share must be in (0, 1]");
+    idx->writer_sms = std::max(1, (int)(idx->num_sms * share + 0.5f));
+    return ETALE_OK;
+}
+
 etale_status etale_set_rerank(etale_index *idx, uint32_t rerank) {
     if (!idx) return ETALE_EINVAL;
     if (rerank == 0 || rerank > 256) return idx->fail(ETALE_EINVAL, "rerank must be 1..256");
@@ -2466,6 +2475,23 @@ etale_status etale_set_profiling(etale_index *idx, int enable) {
     }
     idx->prof = enable != 0;
     idx->nrec = 0;
+    return ETALE_OK;
+}
+
+static_assert((int)ETALE_WK_COUNT == (int)WK_N && (int)ETALE_WK_COMPACT == (int)WK_COMPACT,
+              "work kinds of the header and the kernels differ");
+
+etale_status etale_get_work(etale_index *idx, uint64_t *rows, uint64_t *state, uint32_t n, int reset) {
+    if (!idx) return ETALE_EINVAL;
+    if (n > ETALE_WK_COUNT) n = ETALE_WK_COUNT;
+    u64 w[2 * WK_N];
+    CK(cudaDeviceSynchronize(), "work tallies");
+    CK(cudaMemcpy(w, idx->ctr + C_WK, sizeof(w), cudaMemcpyDeviceToHost), "work tallies");
+    for (uint32_t i = 0; i < n; i++) {
+        if (rows) rows[i] = w[2 * i];
+        if (state) state[i] = w[2 * i + 1];
+    }
+    if (reset) CK(cudaMemset(idx->ctr + C_WK, 0, sizeof(w)), "work tallies");
     return ETALE_OK;
 }
 

@@ -45,8 +45,17 @@ enum : int {
     C_ERR_S = 13,      // error bits of query searches (kept apart from writers')
     C_RECYCLED = 14,   // blocks of the recycle launch that have finished copying
     C_INEXACT = 15,    // ingested rows whose bf16 copy differs from the fp32 row
-    C_NCTR = 16
+    C_WK = 16,         // work tallies of the writer kernels: two words per WK_* kind
+    C_NCTR = 32
 };
+// Work a writer kernel's method needs, tallied per warp and added once at the
+// warp's end: word 0 the bytes of vector rows gathered (distinct rows of each
+// prune or distance step, in the copy the step reads), word 1 the bytes of
+// graph state read or written (reference words, slab entries, tombstone bits).
+// Lists that pass between kernels (candidate keys, offers, replacement sets)
+// are not counted.
+enum : int { WK_PRUNE = 0, WK_OFFER, WK_REFINE, WK_REPAIR_K, WK_REPAIR_FOLD, WK_COMPACT, WK_N };
+static_assert(C_WK + 2 * WK_N <= C_NCTR, "work tallies exceed the counter array");
 
 // ---- reference word r(u) = <delta, d, s>: bit 63 delta, bits 48..55 d,
 //      bits 0..31 s (NIL = no slab).  Same packing as the paper's single

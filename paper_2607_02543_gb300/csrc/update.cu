@@ -29,6 +29,7 @@ struct Stage {
     bool timeout;
     char *gram;      // gram_bytes(gram_rows, mp) for the tensor-core Gram path (nullptr: canonical path)
     int gram_rows;   // candidates the Gram buffer holds (a multiple of 16, <= GRAM_NL)
+    u64 wk_rows, wk_state;   // this warp's work tallies (see WK_*), added by stage_done
 };
 
 // Tensor-core Gram tile: up to 64 candidates, K staged 128 columns at a time
@@ -89,13 +90,24 @@ __device__ __forceinline__ Stage stage_init(char *p, u32 ns, u32 mp, char *gram 
     st.timeout = false;
     st.gram = gram;
     st.gram_rows = (int)gram_rows;
+    st.wk_rows = st.wk_state = 0;
     if (lane_id() == 0) mbar_init(st.bar, 1);
     __syncwarp();
     return st;
 }
 
-__device__ __forceinline__ void stage_done(const Dev &d, const Stage &st) {
-    if (st.timeout && lane_id() == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_TIMEOUT);
+__device__ __forceinline__ void stage_done(const Dev &d, const Stage &st, int kind) {
+    if (lane_id() != 0) return;
+    if (st.timeout) atomicOr(&d.ctr[C_ERR], (u64)ERR_TIMEOUT);
+    if (st.wk_rows) atomicAdd(&d.ctr[C_WK + 2 * kind], st.wk_rows);
+    if (st.wk_state) atomicAdd(&d.ctr[C_WK + 2 * kind + 1], st.wk_state);
+}
+
+// Row bytes a prune of n candidates gathers: the bf16 copy on the Gram path
+// when the index keeps one, else the fp32 rows.
+__device__ __forceinline__ u64 prune_row_bytes(const Dev &d, const Stage &st, int n) {
+    const bool b16 = st.gram && n <= st.gram_rows && d.xb;
+    return (u64)n * (b16 ? 2ull * d.mb : 4ull * d.mp);
 }
 
 // Warps per block (<= 4) such that a block's shared memory stays <= 200 KB.
@@ -736,10 +748,12 @@ __device__ int apply_offer(const Dev &d, u32 *ids, float *rho, int n, u32 v, flo
     }
     // A full list of live entries that no earlier entry drops, with v after
     // all of them: the prune keeps the R entries in order and stops before v.
+    st.wk_state += 8ull * n;                 // the entries' reference words
     if (pruned && nl == n && below == nl) return n;
     if (lane == 0) keys[below] = kv;
     __syncwarp();
     const int cn = nl + 1;
+    st.wk_rows += prune_row_bytes(d, st, cn);
     int nout = warp_prune<GV>(d, keys, cn, alive, idx, oid, orho, st);
     for (int j = lane; j < nout; j += 32) { ids[j] = oid[j]; rho[j] = orho[j]; }
     __syncwarp();
@@ -823,10 +837,13 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(Prun
             __syncwarp();
             warp_sort_u64(keys, (int)a.np);
         }
+        // rows: the candidates (fp32 for the re-score, with v's own row)
+        st.wk_rows += a.rescore ? (u64)(n + 1) * 4 * d.mp : prune_row_bytes(d, st, n);
         const int nout = warp_prune<GV>(d, keys, n, alive, idx, oid, orho, st);
         u64 snap = 0;
         if (lane == 0) snap = ld_ref(d, v);
         snap = __shfl_sync(FULL, snap, 0);
+        st.wk_state += 8 + 8ull * nout + 8;     // v's word read, its list and word written
         if (!warp_publish(d, ws, v, oid, orho, nout, snap, true) && lane == 0)
             atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         const u32 invalid = (u32)d.capacity;
@@ -844,7 +861,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) prune_insert_kernel(Prun
         __syncwarp();
     }
     ws_finish(d, ws);
-    stage_done(d, st);
+    stage_done(d, st, WK_PRUNE);
 }
 
 cudaError_t launch_prune_insert(const Dev &d, u32 first, u32 b, const u64 *exp_keys, const u32 *exp_count,
@@ -947,6 +964,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
             const u32 w = a.of.key[lo];
             u64 snap;
             const int n0 = load_list(d, w, lid, lrho, snap);
+            st.wk_state += 8 + 8ull * n0;
             for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
             __syncwarp();
             int n = n0;
@@ -957,6 +975,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
                                 tid, trho, st, pruned);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
+                st.wk_state += 8ull * n + 8;
                 if (!warp_publish(d, ws, w, lid, lrho, n, snap, pruned) && lane == 0)
                     atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
@@ -969,6 +988,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
             for (u32 att = 0; att < a.budget && !done; att++) {
                 u64 snap;
                 const int n0 = load_list(d, w, lid, lrho, snap);
+                st.wk_state += 8 + 8ull * n0;
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
                 bool pruned = ref_pruned(snap) != 0;
@@ -979,6 +999,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
                     if (pf_t < nwork) { pf_w = a.of.key[pf_t + a.lo]; pf_v = a.of.src[pf_t + a.lo]; pf_vr = a.of.rho[pf_t + a.lo]; }
                 }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
+                st.wk_state += 8ull * n + 8;
                 done = warp_publish(d, ws, w, lid, lrho, n, snap, pruned);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
@@ -989,7 +1010,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) offer_fold_kernel(FoldAr
         __syncwarp();
     }
     ws_finish(d, ws);
-    stage_done(d, st);
+    stage_done(d, st, WK_OFFER);
 }
 
 cudaError_t launch_offer_fold(const Dev &d, const Offers &of, const u32 *seg_start, const u64 *seg_count,
@@ -1087,6 +1108,7 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         const u32 v = dev_first(d, a.first) + t;
         u64 snap;
         const int dv = load_list(d, v, nid, nrho, snap);
+        st.wk_state += 8 + 8ull * dv;
         // 1. raw two-hop ids (v, members of N(v), and for mode 2 non-members
         //    of the sub-batch excluded), kept as u64 for the sort; a member
         //    with more than cap_s of them is collected again into the spill
@@ -1096,13 +1118,16 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         u32 cap = a.cap_s;
         int nraw = 0;
         bool overflow = false;
+        u64 nb_state = 0;                       // the neighbours' words and lists
     collect:
         nraw = 0;
         overflow = false;
+        nb_state = 0;
         for (int i = 0; i < dv; i++) {
             const u64 rw = ld_ref(d, nid[i]);
             const u32 s = ref_slab(rw);
             const int dw = s == NIL ? 0 : (int)ref_deg(rw);
+            nb_state += 8 + 8ull * dw;
             for (int j0 = 0; j0 < dw; j0 += 32) {
                 u32 y = NIL;
                 if (j0 + lane < dw) y = d.slab[(size_t)s * R + j0 + lane].x;
@@ -1132,6 +1157,7 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
             if (lane == 0) atomicOr(&d.ctr[C_ERR], (u64)ERR_OVERFLOW);
             nraw = min(nraw, (int)a.cap);
         }
+        st.wk_state += nb_state;
         int np2 = 32;
         while (np2 < nraw) np2 <<= 1;
         for (int i = nraw + lane; i < np2; i += 32) buf[i] = KEY_INF;
@@ -1150,6 +1176,8 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         }
         __syncwarp();
         // 3. distances to v, then the live members of N(v)
+        st.wk_rows += (u64)(nu + 1) * 4 * d.mp;   // v's row and the peers'
+        st.wk_state += 8ull * ((a.mode != 2 ? nu : 0) + dv);   // liveness words
         const float *vrow = d.x + (size_t)v * d.mp;
         for (int r0 = 0; r0 < nu; r0 += 4) {
             const int c = r0 + grp;
@@ -1188,8 +1216,10 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
             __syncwarp();
             warp_sort_u64(buf, np3);
             const int n = min(nc, (int)a.max_cand);
+            st.wk_rows += prune_row_bytes(d, st, nc - nu);   // the members of N(v), not yet gathered
             nout = warp_prune<GV>(d, buf, n, alive, idx, oid, orho, st);
             if (!warp_same_list(oid, orho, nout, nid, nrho, dv)) {
+                st.wk_state += 8ull * nout + 8;
                 if (!warp_publish(d, ws, v, oid, orho, nout, snap, true) && lane == 0)
                     atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
@@ -1210,7 +1240,7 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         __syncwarp();
     }
     ws_finish(d, ws);
-    stage_done(d, st);
+    stage_done(d, st, WK_REFINE);
 }
 
 // Launch shape of the refine kernel (shared by launch_refine and the spill size).
@@ -1354,6 +1384,8 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
             bid[j] = d.slab[(size_t)s * R + j].x;
             bdel[j] = ref_del(ld_ref(d, bid[j]));
         }
+        st.wk_state += 8 + 16ull * nb;           // u's word, N(u), and the members' words
+        st.wk_rows += (u64)nb * 4 * d.mp;        // B's rows (the canonical table)
         __syncwarp();
         // distance table among B (symmetric).  These distances become the
         // stored rho of replacement edges, so they stay canonical.
@@ -1463,7 +1495,7 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
         }
         __syncwarp();
     }
-    stage_done(d, st);
+    stage_done(d, st, WK_REPAIR_K);
 }
 
 cudaError_t launch_repair_k(const Dev &d, const u32 *dt, const u64 *n_dt, u32 max_n, u32 *pair_key,
@@ -1573,6 +1605,7 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     // The list is full, live, without u, and no entry drops a later one; every
     // K key left sorts after it: the prune keeps the R entries in order and
     // stops before the first K key.
+    st.wk_state += 8ull * (n + nk);          // reference words of the list and of K(u, a)
     if (pruned && na == n && n == (int)d.R && !early) return n;
     for (int i = lane; i < na; i += 32) {
         const u64 k = ka[i];
@@ -1585,6 +1618,7 @@ __device__ int repair_apply(const Dev &d, u32 *lid, float *lrho, int n, u32 u, c
     }
     __syncwarp();
     const int cn = na + nb2;
+    st.wk_rows += prune_row_bytes(d, st, cn);
     const int nout = warp_prune<GV>(d, keys, cn, alive, idx, tid, trho, st);
     for (int j = lane; j < nout; j += 32) { lid[j] = tid[j]; lrho[j] = trho[j]; }
     __syncwarp();
@@ -1634,6 +1668,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
             const u32 w = a.pair_key[lo];
             u64 snap;
             const int n0 = load_list(d, w, lid, lrho, snap);
+            st.wk_state += 8 + 8ull * n0;
             for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
             __syncwarp();
             int n = n0;
@@ -1644,6 +1679,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
                                  ka, kb, alive, idx, (int)a.np, tid, trho, st, pruned);
             }
             if (!warp_same_list(lid, lrho, n, oid0, orho0, n0)) {
+                st.wk_state += 8ull * n + 8;
                 if (!warp_publish(d, ws, w, lid, lrho, n, snap, pruned) && lane == 0)
                     atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
             }
@@ -1655,6 +1691,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
             for (u32 att = 0; att < a.budget && !done; att++) {
                 u64 snap;
                 const int n0 = load_list(d, w, lid, lrho, snap);
+                st.wk_state += 8 + 8ull * n0;
                 for (int j = lane; j < n0; j += 32) { oid0[j] = lid[j]; orho0[j] = lrho[j]; }
                 __syncwarp();
                 bool pruned = ref_pruned(snap) != 0;
@@ -1666,6 +1703,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
                     if (pf_t < nwork) { pf_w = a.pair_key[pf_t + a.lo]; pf_pv = a.pair_val[pf_t + a.lo]; }
                 }
                 if (warp_same_list(lid, lrho, n, oid0, orho0, n0)) { done = true; break; }
+                st.wk_state += 8ull * n + 8;
                 done = warp_publish(d, ws, w, lid, lrho, n, snap, pruned);
                 u64 err = 0;
                 if (lane == 0) err = *reinterpret_cast<volatile u64 *>(&d.ctr[C_ERR]);
@@ -1676,7 +1714,7 @@ __global__ void __launch_bounds__(32, GV == 1 ? 1 : 12) repair_fold_kernel(Repai
         __syncwarp();
     }
     ws_finish(d, ws);
-    stage_done(d, st);
+    stage_done(d, st, WK_REPAIR_FOLD);
 }
 
 cudaError_t launch_repair_fold(const Dev &d, const u32 *dt, const u32 *pair_key, const u32 *pair_val,
@@ -1730,11 +1768,15 @@ __global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const 
     const u32 R = d.R;
     WarpSlabs ws;
     ws_init(ws);
+    // graph state: the words scanned, each live list with one tombstone bit
+    // per entry, and the lists republished
+    u64 wk = 8ull * (u64)min((u64)32, next_id - base);
     for (int t = 0; t < 32; t++) {
         const u64 r = __shfl_sync(FULL, myref, t);
         if (ref_del(r) || ref_slab(r) == NIL) continue;
         const u32 s = ref_slab(r);
         const int n = (int)ref_deg(r);
+        wk += 8ull * n + (u64)(n + 7) / 8;
         bool dirty = false;
         u32 ids[2];
         float rhos[2];
@@ -1761,11 +1803,13 @@ __global__ void __launch_bounds__(256) compact_kernel(Dev d, u64 next_id, const 
         __syncwarp();
         // a lost CAS here means another writer touched the node during the
         // reclaim launch, which the launch discipline forbids
+        wk += 8ull * nk + 8;
         if (!warp_publish(d, ws, (u32)(base + t), sid[warp], srho[warp], nk, r, ref_pruned(r) != 0) && lane == 0)
             atomicOr(&d.ctr[C_ERR], (u64)ERR_CAS);
         __syncwarp();
     }
     ws_finish(d, ws);
+    if (lane == 0) atomicAdd(&d.ctr[C_WK + 2 * WK_COMPACT + 1], wk);
 }
 
 cudaError_t launch_compact(const Dev &d, u64 next_id, const u32 *tomb_bits, cudaStream_t st) {

@@ -211,10 +211,12 @@ class RingServer(Server):
     """
 
     def __init__(self, index, k: int = 10, beam: int = 64, slots: int = 4096, max_us: int = 2000,
-                 blocks: int = 0, max_update_batch: int = 4096, streams=(None, None), reclaim_every: int = 0):
+                 blocks: int = 0, max_update_batch: int = 4096, streams=(None, None), reclaim_every: int = 0,
+                 writer_share: float = 0.5):
         super().__init__(index, k=k, beam=beam, max_update_batch=max_update_batch, streams=streams,
                          reclaim_every=reclaim_every)
         self.slots, self.max_us, self.blocks = slots, max_us, blocks
+        self.writer_share = writer_share
 
     def run(self, requests: list[Request]) -> dict:
         """Queries go through the ring (native submit / launch / collect
@@ -225,6 +227,8 @@ class RingServer(Server):
         updates = [r for r in requests if r.kind != "query"]
         ring = Ring(self.index, self.slots, self.k, self.beam)
         self.index.set_concurrent(True)
+        if hasattr(self.index, "set_writer_share"):
+            self.index.set_writer_share(self.writer_share)   # leave the ring room on the SMs
         t0 = time.perf_counter()
         tu = threading.Thread(target=self._update_worker, args=(updates, t0))
         tu.start()
@@ -242,6 +246,8 @@ class RingServer(Server):
         tu.join()
         wall = time.perf_counter() - t0
         self.index.set_concurrent(False)
+        if hasattr(self.index, "set_writer_share"):
+            self.index.set_writer_share(1.0)
         ring.close()
         ql = [r.done - r.t for r in queries]
         ul = [r.done - r.t for r in updates]

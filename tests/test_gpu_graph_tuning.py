@@ -89,3 +89,22 @@ def test_autotune_beam_picks_smallest_beam_for_target(index):
         assert chosen == tried[-1][0] and all(r < 0.97 for _, r in tried[:-1])
     else:
         assert chosen == beams[-1] and len(tried) == len(beams)
+
+
+def test_writer_share_does_not_change_results():
+    """Update kernels sized for a share of the SMs build the same graph, word
+    for word, in deterministic mode."""
+    from paper_2607_02543_gb300 import Index
+    w = W.scaled(W.SMALL, 4000, n_queries=10, rounds=1)
+    plan = W.make_plan(w)
+    out = []
+    for share in (1.0, 0.2):
+        g = Index(w.dim, w.metric, w.degree, w.capacity + 1000, build_beam=32, mode="deterministic")
+        g.set_writer_share(share)
+        g.insert(plan.base)
+        g.delete(np.arange(0, 4000, 7, dtype=np.uint32))
+        g.insert(W.Mixture(w).draw("inserts", 500))
+        g.reclaim()
+        out.append(g.export_graph())
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
