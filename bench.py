@@ -560,7 +560,7 @@ def run_serve(args):
         srv = Server(idx, k=w.k, beam=beam, streams=streams)
     else:
         srv = RingServer(idx, k=w.k, beam=beam, slots=16384, max_us=2000,
-                         blocks=3 * torch.cuda.get_device_properties(0).multi_processor_count,
+                         blocks=torch.cuda.get_device_properties(0).multi_processor_count,
                          streams=streams, writer_share=args.writer_share)
     out = srv.run(reqs)
     idx.reclaim()
@@ -584,6 +584,8 @@ def run_serve(args):
            "queries": out["queries"], "updates": out["updates"], "query_throughput": out["query_throughput"],
            "update_vectors_per_s": out["update_vectors_per_s"], "query_batches": out.get("query_batches"),
            "ring_launches": out.get("ring_launches"), "queries_taken_mid_launch": out.get("queries_taken_mid_launch"),
+           "ring_seed_ms_per_query": out.get("ring_seed_ms_per_query"),
+           "ring_search_ms_per_query": out.get("ring_search_ms_per_query"),
            "update_batches": out["update_batches"], "deferred": out["deferred"], "reclaims": out["reclaims"],
            "recall_at_10_anchor": {"before": rec0, "after": rec1}, "build_s": build_s,
            "precision_choice": [{"anchor_batch_ms": c[0] * 1e3, "precision": c[1], "beam": c[2], "recall": c[3]}

@@ -431,13 +431,16 @@ etale_status etale_ring_buffers(etale_ring *r, float **rows, uint32_t *row_strid
 /* Make tickets [0, tail) visible to launches (a release store; rows first). */
 etale_status etale_ring_publish(etale_ring *r, uint64_t tail);
 etale_status etale_ring_close(etale_ring *r, int closed);
-/* blocks: thread blocks of 4 warps (0 = 2 per SM); *seq (may be NULL)
+/* blocks: thread blocks of 4 warps (0 = 1 per SM); *seq (may be NULL)
  * receives the launch's sequence number.                                   */
 etale_status etale_ring_launch(etale_ring *r, uint32_t max_us, uint32_t blocks, uint32_t *seq, void *stream);
 /* Serve n queries (HOST rows, n x dim) arriving at arrival_s[i] seconds from
  * the call's start (ascending): native threads submit each query into the
- * ring at its arrival time (waiting for a free slot), keep one launch of at
- * most max_us microseconds in flight on `stream`, and collect completions.
+ * ring at its arrival time (waiting for a free slot), issue launches of
+ * max_us microseconds alternately on `stream` and a second stream of the
+ * ring's own (the next one when the current one has run three quarters of
+ * its lifetime, so tickets are always being taken while the previous launch
+ * finishes the queries it holds), and collect completions.
  * issued_s[i] (may be NULL) receives when query i was written into a slot,
  * completion_s[i] when its results were seen on the host; out_ids /
  * out_dists (n x k, may be NULL) the results; *mid_launch (may be NULL) the
@@ -449,6 +452,10 @@ etale_status etale_ring_serve(etale_ring *r, const float *queries, const double 
                               uint32_t max_us, uint32_t blocks, double *issued_s, double *completion_s,
                               uint32_t *out_ids, float *out_dists, uint64_t *mid_launch, uint32_t *launches,
                               void *stream);
+/* Totals over the ring's finished launches: queries served, and the
+ * nanoseconds their warps spent seeding and in the BeamSearch (device
+ * clock).  No synchronisation: a launch still running is not counted.     */
+etale_status etale_ring_stats(etale_ring *r, uint64_t *served, uint64_t *seed_ns, uint64_t *search_ns);
 etale_status etale_ring_destroy(etale_ring *r);
 
 /* How the last etale_ground_truth call ran: *path 0 CUDA cores, 1 tensor

@@ -62,7 +62,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_load", "etale_search_eval_count", "etale_round_graph_create",
            "etale_round_graph_launch", "etale_round_graph_sync", "etale_round_graph_destroy",
            "etale_set_insert_precision", "etale_set_rerank", "etale_autotune_beam", "etale_ring_create",
-           "etale_ring_buffers", "etale_ring_publish", "etale_ring_close", "etale_ring_launch", "etale_ring_destroy", "etale_ring_serve", "etale_set_writer_share", "etale_get_work"]
+           "etale_ring_buffers", "etale_ring_publish", "etale_ring_close", "etale_ring_launch", "etale_ring_destroy", "etale_ring_serve", "etale_set_writer_share", "etale_get_work", "etale_ring_stats"]
 PHASES = ["seed", "search_insert", "prune", "offer_sort", "offer_fold", "refine", "delete_prep",
           "repair_k", "repair_fold", "entries", "compact", "reclaim", "search_query", "recycle",
           "gt_prep", "gt_tensor", "gt_merge", "gt_exact"]
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
             "etale_set_rerank": ([P, U32], C.c_int),
             "etale_set_writer_share": ([P, C.c_float], C.c_int),
             "etale_get_work": ([P, P, P, U32, C.c_int], C.c_int),
+            "etale_ring_stats": ([P, P, P, P], C.c_int),
             "etale_ring_create": ([P, U32, U32, U32, C.POINTER(P)], C.c_int),
             "etale_ring_buffers": ([P, C.POINTER(P), C.POINTER(U32), C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                     C.POINTER(P)], C.c_int),
@@ -538,6 +539,12 @@ class Ring:
                                                           C.byref(nl), _stream(stream)))
         return {"issued": issued, "done": done, "ids": ids, "dists": dists, "mid_launch": mid.value,
                 "launches": nl.value}
+
+    def stats(self) -> dict:
+        """Queries served and device-clock seconds spent seeding / searching."""
+        v = [C.c_uint64(0) for _ in range(3)]
+        self.index._check(self.index.lib.etale_ring_stats(self.h, *(C.byref(x) for x in v)))
+        return {"served": v[0].value, "seed_s": v[1].value * 1e-9, "search_s": v[2].value * 1e-9}
 
     def close(self):
         if getattr(self, "h", None):

@@ -122,6 +122,8 @@ struct etale_index {
     std::mutex mu;                    // guards search_ev and its validity
     cudaEvent_t search_ev = nullptr;  // recorded after every query search
     bool search_ev_valid = false;
+    cudaEvent_t search_ev2 = nullptr; // the same for ring launches on a ring's second stream
+    bool search_ev2_valid = false;
     bool concurrent = false;
     // host-side state
     u64 next_id = 0, live = 0, tombs = 0, reclaimed = 0;
@@ -359,6 +361,7 @@ etale_status writer_begin(etale_index *idx, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(idx->mu);
         if (idx->search_ev_valid) CK(cudaStreamWaitEvent(st, idx->search_ev, 0), "wait for searches");
+        if (idx->search_ev2_valid) CK(cudaStreamWaitEvent(st, idx->search_ev2, 0), "wait for searches");
     }
     return recycle_now(idx, st);
 }
@@ -710,6 +713,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
               cudaMallocHost(&idx->host_ctr_st, C_NCTR * sizeof(u64)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&idx->stat_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&idx->search_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&idx->search_ev2, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&idx->nent_dev, 16) == cudaSuccess && cudaMemset(idx->nent_dev, 0, 16) == cudaSuccess &&
               cudaMalloc(&idx->rs, RS_N * sizeof(u64)) == cudaSuccess &&
               cudaMemset(idx->rs, 0, RS_N * sizeof(u64)) == cudaSuccess &&
@@ -773,6 +777,7 @@ etale_status etale_destroy(etale_index *idx) {
     if (idx->host_ctr_st) cudaFreeHost(idx->host_ctr_st);
     if (idx->stat_stream) cudaStreamDestroy(idx->stat_stream);
     if (idx->search_ev) cudaEventDestroy(idx->search_ev);
+    if (idx->search_ev2) cudaEventDestroy(idx->search_ev2);
     for (cudaEvent_t e : idx->pev) cudaEventDestroy(e);
     DevBuf *bufs[] = {&idx->stage, &idx->qpad, &idx->out_ids, &idx->out_dist, &idx->exp_keys, &idx->exp_count,
                       &idx->F_id, &idx->F_rho, &idx->F_n, &idx->of_key, &idx->of_val, &idx->of_key2,
@@ -1864,6 +1869,7 @@ struct etale_ring {
     u64 *d_done = nullptr, *d_ctl = nullptr;
     u64 *head = nullptr, *seed = nullptr; // device memory
     u64 tickets = 0;                      // tickets published so far (etale_ring_serve)
+    cudaStream_t alt = nullptr;           // etale_ring_serve's second launch stream
 };
 
 etale_status etale_ring_create(etale_index *idx, uint32_t slots, uint32_t k, uint32_t beam, etale_ring **out) {
@@ -1882,8 +1888,9 @@ etale_status etale_ring_create(etale_index *idx, uint32_t slots, uint32_t k, uin
     char *d = nullptr;
     bool ok = cudaHostAlloc(&r->host, total, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostGetDevicePointer((void **)&d, r->host, 0) == cudaSuccess &&
-              cudaMalloc(&r->head, 8) == cudaSuccess && cudaMemset(r->head, 0, 8) == cudaSuccess &&
-              cudaMalloc(&r->seed, (size_t)slots * L * 8) == cudaSuccess;
+              cudaMalloc(&r->head, 64) == cudaSuccess && cudaMemset(r->head, 0, 64) == cudaSuccess &&
+              cudaMalloc(&r->seed, (size_t)slots * L * 8) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&r->alt, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         etale_ring_destroy(r);
@@ -1929,7 +1936,7 @@ etale_status etale_ring_launch(etale_ring *r, uint32_t max_us, uint32_t blocks, 
     if (!r) return ETALE_EINVAL;
     etale_index *idx = r->idx;
     if (max_us == 0 || max_us > 1000000) return idx->fail(ETALE_EINVAL, "max_us must be 1..1e6");
-    if (blocks == 0) blocks = (u32)idx->num_sms * 2;
+    if (blocks == 0) blocks = (u32)idx->num_sms;   // two launches overlap in etale_ring_serve
     cudaStream_t st = (cudaStream_t)stream;
     const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * r->L;
     Dev d = idx->dev();
@@ -1942,9 +1949,24 @@ etale_status etale_ring_launch(etale_ring *r, uint32_t max_us, uint32_t blocks, 
     if (seq) *seq = sq;
     if (idx->concurrent) {
         std::lock_guard<std::mutex> lk(idx->mu);
-        CK(cudaEventRecord(idx->search_ev, st), "record search event");
-        idx->search_ev_valid = true;
+        if (st == r->alt) {
+            CK(cudaEventRecord(idx->search_ev2, st), "record search event");
+            idx->search_ev2_valid = true;
+        } else {
+            CK(cudaEventRecord(idx->search_ev, st), "record search event");
+            idx->search_ev_valid = true;
+        }
     }
+    return ETALE_OK;
+}
+
+etale_status etale_ring_stats(etale_ring *r, uint64_t *served, uint64_t *seed_ns, uint64_t *search_ns) {
+    if (!r) return ETALE_EINVAL;
+    u64 v[3];
+    CK2(r->idx, cudaMemcpy(v, r->head + 4, sizeof(v), cudaMemcpyDeviceToHost), "ring statistics");
+    if (served) *served = v[0];
+    if (seed_ns) *seed_ns = v[1];
+    if (search_ns) *search_ns = v[2];
     return ETALE_OK;
 }
 
@@ -1973,22 +1995,36 @@ etale_status etale_ring_serve(etale_ring *r, const float *queries, const double 
     std::vector<double> issued_local(issued_s ? 0 : n);
     double *iss = issued_s ? issued_s : issued_local.data();
     __atomic_store_n(&r->ctl[1], 0ull, __ATOMIC_RELEASE);
-    // one bounded launch always in flight
+    // Bounded launches, alternating between `stream` and the ring's second
+    // stream: the next launch is issued when the current one has run three
+    // quarters of its lifetime, so one launch is always taking tickets while
+    // the one before it finishes the queries it holds.
     std::thread launcher([&]() {
-        cudaStream_t st = (cudaStream_t)stream;
-        while (!finished.load()) {
+        cudaStream_t sts[2] = {(cudaStream_t)stream, r->alt};
+        for (u32 k = 0; !finished.load(); k++) {
+            cudaStream_t s = sts[k & 1];
             uint32_t sq = 0;
+            // the launch before last on this stream is past its lifetime
+            if (cudaStreamSynchronize(s) != cudaSuccess) {
+                launch_err.store(1);
+                break;
+            }
+            if (finished.load()) break;
             {
                 std::lock_guard<std::mutex> lk(seq_mu);
                 issue_of_seq.push_back(now_s());
             }
-            if (etale_ring_launch(r, max_us, blocks, &sq, stream) != ETALE_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+            if (etale_ring_launch(r, max_us, blocks, &sq, s) != ETALE_OK) {
                 launch_err.store(1);
-                finished.store(true);
                 break;
             }
             nlaunch++;
+            const double t_next = now_s() + 0.75e-6 * max_us;
+            for (double t = now_s(); !finished.load() && t < t_next; t = now_s())
+                std::this_thread::sleep_for(std::chrono::duration<double>(std::min(t_next - t, 200e-6)));
         }
+        for (cudaStream_t s : sts)
+            if (cudaStreamSynchronize(s) != cudaSuccess) launch_err.store(1);
     });
     // completions, in any order; results copied out before a slot is reused
     std::thread collector([&]() {
@@ -2056,6 +2092,10 @@ etale_status etale_ring_serve(etale_ring *r, const float *queries, const double 
 
 etale_status etale_ring_destroy(etale_ring *r) {
     if (!r) return ETALE_OK;
+    if (r->alt) {
+        cudaStreamSynchronize(r->alt);
+        cudaStreamDestroy(r->alt);
+    }
     if (r->host) cudaFreeHost(r->host);
     cudaFree(r->head);
     cudaFree(r->seed);

@@ -73,16 +73,18 @@ __device__ __forceinline__ float4 load4(const void *row, int i, float scale) {
     }
 }
 
-// The canonical reduction tree (see canon_dist) over a staged row of
-// precision P, 8 lanes per distance: fp32 arithmetic on dequantised values.
-template <int P>
-__device__ __forceinline__ float qdist(const float *__restrict__ q, const void *row, float scale, int mp, int metric,
-                                       int g) {
-    if (P == 0) return canon_dist<8>(q, reinterpret_cast<const float *>(row), mp, metric, g);
-    float p[4];
+// The canonical reduction tree (see canon_dist) over a row of precision P,
+// G lanes per distance (lane g of the group holds partials g, g + G, ...):
+// fp32 arithmetic on dequantised values.  Every G gives the same value.
+template <int P, int G>
+__device__ __forceinline__ float qdist_g(const float *__restrict__ q, const void *row, float scale, int mp, int metric,
+                                         int g) {
+    if (P == 0) return canon_dist<G>(q, reinterpret_cast<const float *>(row), mp, metric, g);
+    constexpr int T = 32 / G;
+    float p[T];
 #pragma unroll
-    for (int t = 0; t < 4; t++) {
-        const int j = g + 8 * t;
+    for (int t = 0; t < T; t++) {
+        const int j = g + G * t;
         float acc = 0.0f;
         for (int base = 0; base < mp; base += 128) {
             const int i = base + 4 * j;
@@ -106,12 +108,21 @@ __device__ __forceinline__ float qdist(const float *__restrict__ q, const void *
         }
         p[t] = acc;
     }
-    p[0] = __fadd_rn(p[0], p[2]);
-    p[1] = __fadd_rn(p[1], p[3]);
-    float s = __fadd_rn(p[0], p[1]);
 #pragma unroll
-    for (int h = 4; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
+    for (int hh = T / 2; hh >= 1; hh >>= 1)
+#pragma unroll
+        for (int t = 0; t < hh; t++) p[t] = __fadd_rn(p[t], p[t + hh]);
+    float s = p[0];
+#pragma unroll
+    for (int h = G / 2; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
     return metric == 0 ? s : __fsub_rn(1.0f, s);
+}
+
+// 8 lanes per distance (the staged search and seeding steps).
+template <int P>
+__device__ __forceinline__ float qdist(const float *__restrict__ q, const void *row, float scale, int mp, int metric,
+                                       int g) {
+    return qdist_g<P, 8>(q, row, scale, mp, metric, g);
 }
 
 // canon_dist<8> for rows of at most 128 floats with this lane's four query
@@ -658,6 +669,10 @@ __global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a
 // ---------------------------------------------------------------------------
 struct RingArgs {
     u64 *head;                 // device: tickets claimed
+    u64 *dtail;                // device: the submitted count as last read from the host
+    u64 *poll_ns;              // device: when a warp last read the host's count
+    u64 *dclosed;              // device: the host's stop flag, as last read (zeroed per launch)
+    u64 *stats;                // device: queries served, ns seeding, ns searching (accumulated)
     const u64 *tail;           // host-mapped: tickets submitted (host release store)
     const u64 *closed;         // host-mapped: nonzero stops the claims
     u64 *done;                 // host-mapped: done[slot] = ticket + 1 once written
@@ -680,37 +695,83 @@ __device__ __forceinline__ void st_release_sys(u64 *p, u64 v) {
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-constexpr u32 RING_POLL_LIMIT = 1u << 22;   // each poll sleeps ~0.5 us at most
+constexpr u32 RING_POLL_LIMIT = 1u << 22;   // each poll sleeps at most RING_SLEEP_MAX ns
+constexpr u32 RING_SLEEP_MAX = 8192;        // an idle warp's back-off doubles up to this
+constexpr u64 RING_HOST_POLL_NS = 2000;     // the host's count is read about this often
 
 // The L nearest entry points of the query in slot qi, by the same distances
 // and merge as seed_kernel (so the seeds equal a batch search's), into
 // a.seed + qi * L.  Uses s.qv (the query row), s.bkey and s.nkey.
+// One lane's whole distance (the canonical tree of qdist_g with G = 1): the
+// row is read in batches of sixteen independent 16-byte loads, so that a batch
+// is in flight at once instead of one load per partial.  Partial j still
+// accumulates its elements in ascending order and the tree is the same.
+template <int P>
+__device__ __forceinline__ float lane_dist(const float *__restrict__ q, const void *row, float scale, int mp,
+                                           int metric) {
+    float p[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) p[j] = 0.0f;
+    for (int base = 0; base < mp; base += 128) {
+#pragma unroll
+        for (int j0 = 0; j0 < 32; j0 += 16) {
+            float4 v[16];
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                const int i = base + 4 * (j0 + u);
+                v[u] = i < mp ? load4<P>(row, i, scale) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                const int i = base + 4 * (j0 + u);
+                if (i < mp) {
+                    const float4 w = *reinterpret_cast<const float4 *>(q + i);
+                    float acc = p[j0 + u];
+                    if (metric == 0) {
+                        const float d0 = __fsub_rn(w.x, v[u].x), d1 = __fsub_rn(w.y, v[u].y);
+                        const float d2 = __fsub_rn(w.z, v[u].z), d3 = __fsub_rn(w.w, v[u].w);
+                        acc = __fmaf_rn(d0, d0, acc);
+                        acc = __fmaf_rn(d1, d1, acc);
+                        acc = __fmaf_rn(d2, d2, acc);
+                        acc = __fmaf_rn(d3, d3, acc);
+                    } else {
+                        acc = __fmaf_rn(w.x, v[u].x, acc);
+                        acc = __fmaf_rn(w.y, v[u].y, acc);
+                        acc = __fmaf_rn(w.z, v[u].z, acc);
+                        acc = __fmaf_rn(w.w, v[u].w, acc);
+                    }
+                    p[j0 + u] = acc;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int hh = 16; hh >= 1; hh >>= 1)
+#pragma unroll
+        for (int t = 0; t < hh; t++) p[t] = __fadd_rn(p[t], p[t + hh]);
+    return metric == 0 ? p[0] : __fsub_rn(1.0f, p[0]);
+}
+
 template <int P>
 __device__ void ring_seed(const SearchArgs &a, WarpSmem &s, u32 qi) {
-    const int lane = lane_id(), grp = lane >> 3, g = lane & 7;
+    const int lane = lane_id();
     const Dev &d = a.d;
     const u32 mp = d.mp, L = a.L;
     const float *qrow = a.q + (size_t)qi * mp;
     for (u32 i = lane * 4; i < mp; i += 128)
         *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
     __syncwarp();
+    // one entry per lane: all 32 rows of a step in flight at once (a warp
+    // seeds alone here, with no block-wide tile to stage them in)
     const u32 S = d.nent_dev ? *d.nent_dev : d.n_entries;
     int n = 0;
+    u32 e_next = lane < S ? d.entries[lane] : 0u;
     for (u32 t0 = 0; t0 < S; t0 += 32) {
-        const int nt = (int)min(32u, S - t0);
+        const u32 e = e_next;
+        const bool ok = t0 + lane < S;
+        if (t0 + 32 + lane < S) e_next = d.entries[t0 + 32 + lane];
         u64 key = KEY_INF;
-        for (int r0 = 0; r0 < nt; r0 += 4) {
-            const int c = r0 + grp;
-            const int cc = c < nt ? c : nt - 1;
-            const u32 e = d.entries[t0 + cc];
-            const float dist = qdist<P>(s.qv, row_src<P>(d, e), P == 2 ? d.x8s[e] : 1.0f, (int)mp, (int)d.metric, g);
-            const u64 kk = mkkey(dist, e);
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const u64 v = __shfl_sync(FULL, kk, t * 8);
-                if (lane == r0 + t && r0 + t < nt) key = v;
-            }
-        }
+        if (ok) key = mkkey(lane_dist<P>(s.qv, row_src<P>(d, e), P == 2 ? d.x8s[e] : 1.0f, (int)mp, (int)d.metric), e);
         n = seed_merge(s.bkey, s.nkey, key, n, (int)L);
     }
     u64 *seed_row = const_cast<u64 *>(a.seed) + (size_t)qi * L;   // the ring's own seed buffer
@@ -719,7 +780,7 @@ __device__ void ring_seed(const SearchArgs &a, WarpSmem &s, u32 qi) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, 4) ring_search_kernel(SearchArgs a, RingArgs r) {
+__global__ void __launch_bounds__(128, 3) ring_search_kernel(SearchArgs a, RingArgs r) {
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
@@ -728,33 +789,58 @@ __global__ void __launch_bounds__(128, 4) ring_search_kernel(SearchArgs a, RingA
     if (lane == 0) mbar_init(s.bar, 1);
     __syncwarp();
     u32 phase = 0;
-    u64 nexp_tot = 0, ndist = 0;
+    u64 nexp_tot = 0, ndist = 0, served = 0, seed_ns = 0, search_ns = 0;
     bool timeout = false;
     const u64 t_end = globaltimer_ns() + r.max_ns;
     for (;;) {
         u64 t = KEY_INF;
         if (lane == 0) {
+            // Idle warps poll the device copy of the submitted count; one
+            // warp at a time, about every RING_HOST_POLL_NS, reads the host's
+            // count (acquire) and raises the copy after a fence, so the
+            // claiming warp's fence orders its row reads after the host's
+            // writes.  Polling the host from every idle warp would flood the
+            // link and the SMs' L1 with system-scope acquires.
+            u32 nap = 256;
             for (u32 it = 0; it < RING_POLL_LIMIT; it++) {
                 // the lifetime bounds the launch even under steady arrivals
-                if (globaltimer_ns() >= t_end || ld_acquire_sys(r.closed)) break;
-                const u64 tail = ld_acquire_sys(r.tail);
+                const u64 now = globaltimer_ns();
+                if (now >= t_end) break;
+                if (*reinterpret_cast<volatile u64 *>(r.dclosed)) break;
                 const u64 h = *reinterpret_cast<volatile u64 *>(r.head);
-                if (h < tail) {
+                if (h < *reinterpret_cast<volatile u64 *>(r.dtail)) {
                     if (atomicCAS(r.head, h, h + 1) == h) { t = h; break; }
                     continue;
                 }
-                __nanosleep(500);
+                const u64 last = *reinterpret_cast<volatile u64 *>(r.poll_ns);
+                if (now - last >= RING_HOST_POLL_NS && atomicCAS(r.poll_ns, last, now) == last) {
+                    if (ld_acquire_sys(r.closed)) {
+                        *reinterpret_cast<volatile u64 *>(r.dclosed) = 1;
+                        break;
+                    }
+                    const u64 tail = ld_acquire_sys(r.tail);
+                    __threadfence();
+                    atomicMax(reinterpret_cast<unsigned long long *>(r.dtail), (unsigned long long)tail);
+                    if (h < tail) continue;
+                }
+                __nanosleep(nap);
+                nap = min(2 * nap, RING_SLEEP_MAX);
             }
         }
         t = __shfl_sync(FULL, t, 0);
         if (t == KEY_INF) break;
         __threadfence_system();   // every lane reads the row after the claim's acquire
         const u32 slot = (u32)(t % r.slots);
+        const u64 t0 = globaltimer_ns();
         ring_seed<P>(a, s, slot);
+        const u64 t1 = globaltimer_ns();
         const int n0 = (int)min(a.L, d.nent_dev ? *d.nent_dev : d.n_entries);
         search_one<P, false>(a, s, slot, n0, phase, nexp_tot, ndist, timeout);
         __syncwarp();
         if (lane == 0) {
+            served++;
+            seed_ns += t1 - t0;
+            search_ns += globaltimer_ns() - t1;
             r.served_by[slot] = r.seq;
             __threadfence_system();   // the results and served_by before done
             st_release_sys(r.done + slot, t + 1);
@@ -764,6 +850,11 @@ __global__ void __launch_bounds__(128, 4) ring_search_kernel(SearchArgs a, RingA
     if (lane == 0) {
         atomicAdd(&d.ctr[C_EXPAND], nexp_tot);
         atomicAdd(&d.ctr[C_DIST], ndist);
+        if (served) {
+            atomicAdd(r.stats, served);
+            atomicAdd(r.stats + 1, seed_ns);
+            atomicAdd(r.stats + 2, search_ns);
+        }
         if (timeout) atomicOr(&d.ctr[a.err], (u64)ERR_TIMEOUT);
     }
 }
@@ -789,7 +880,8 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
         while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
         if ((size_t)a.stage_rows * a.rowb < rn * 8) a.stage_rows = (u32)((rn * 8 + a.rowb - 1) / a.rowb);
     }
-    RingArgs r{head, tail, closed, done, served_by, slots, seq, max_ns};
+    // head: claimed, device count, last host poll, stop flag, then the statistics
+    RingArgs r{head, head + 1, head + 2, head + 3, head + 4, tail, closed, done, served_by, slots, seq, max_ns};
     using K = void (*)(SearchArgs, RingArgs);
     K fn = prec == 1 ? ring_search_kernel<1> : prec == 2 ? ring_search_kernel<2> : ring_search_kernel<0>;
     const size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
@@ -799,6 +891,8 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, 128, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    e = cudaMemsetAsync(r.dclosed, 0, sizeof(u64), st);   // the stop flag of the launch before
+    if (e != cudaSuccess) return e;
     fn<<<blocks, 128, smem, st>>>(a, r);
     return cudaGetLastError();
 }
