@@ -499,7 +499,7 @@ bool exact_rows(const etale_index *idx) {
 // memory fits the device (long rows); results do not depend on the stage.
 SearchTuning fit_tuning(const etale_index *idx, u32 L, SearchTuning t) {
     while (t.stage_rows > 1 &&
-           search_smem_bytes(idx->mp, L, t.stage_rows, 1u << t.seen_bits, t.warps_per_block) > (size_t)idx->smem_optin)
+           search_smem_bytes(idx->mp, L, t.stage_rows, t.seen_bits, idx->capacity, t.warps_per_block) > (size_t)idx->smem_optin)
         t.stage_rows >>= 1;
     return t;
 }

@@ -18,7 +18,7 @@ struct SearchTuning {
 cudaError_t smem_at_least(const void *fn, size_t bytes);
 
 // search.cu
-size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 wpb);
+size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_bits, u64 capacity, u32 wpb);
 // seed_kernel: top-L of the entry set per query into `seed` (nq x L); it
 // must precede the search launch that reads `seed`.
 // qsel (optional): the batch is the queries qsel[0 .. n) (n = *nq_dev), each

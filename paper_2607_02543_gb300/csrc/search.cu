@@ -36,6 +36,9 @@ struct SearchArgs {
     u64 *exp_keys;       // insert: nq x max_hops expanded non-tombstone keys
     u32 *exp_count;
     u32 stage_rows, seen_slots, seen_bits;
+    // the evaluated-id cache (see seen_layout): 0 = whole ids, else 8- or
+    // 16-bit tags behind a validity bitmap of seen_words words
+    u32 seen_tag, seen_shift, seen_tmask, seen_hmask, seen_words;
     u32 rowb;            // bytes per gathered row (fp32, bf16 or fp8 copy)
     u32 wq, err;         // work-queue counter and error word (query searches
                          // use their own, so they can overlap a writer)
@@ -179,19 +182,45 @@ struct WarpSmem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 rowb) {
+// Layout of a warp's evaluated-id cache of 2^bits slots.  With ids below
+// 2^cb (cb >= bits, from the capacity), h = id * 2654435761 mod 2^cb is a
+// bijection of [0, 2^cb); slot = h >> (cb - bits) and tag = the low cb - bits
+// bits of h identify the id, so a slot need only hold the tag: 8 or 16 bits
+// when cb - bits allows, beside one validity bit per slot.  Otherwise the
+// slot holds the whole id (slot = the top bits of the 32-bit product).  A
+// hit is therefore never wrong; a slot overwritten by another id only costs
+// a repeated evaluation.
+struct SeenLayout {
+    u32 tag, shift, tmask, hmask, words;
+    size_t bytes;
+};
+inline SeenLayout seen_layout(u64 capacity, u32 bits) {
+    u32 cb = bits;
+    while (cb < 32 && (1ull << cb) < capacity) cb++;
+    SeenLayout l;
+    l.shift = cb - bits;
+    l.tag = l.shift <= 8 ? 8u : l.shift <= 16 ? 16u : 0u;
+    l.tmask = (1u << l.shift) - 1u;
+    l.hmask = cb >= 32 ? ~0u : (1u << cb) - 1u;
+    const size_t slots = (size_t)1 << bits;
+    l.words = (u32)(slots >= 32 ? slots / 32 : 1);
+    l.bytes = l.tag == 0 ? slots * 4 : (size_t)l.words * 4 + slots * (l.tag / 8);
+    return l;
+}
+
+__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, size_t seen_bytes, u32 rowb) {
     size_t b = 0;
     b += align_up((size_t)mp * 4, 128);
     b += align_up((size_t)stage_rows * rowb, 128);
     b += 2 * align_up((size_t)L * 8, 16);
     b += align_up((size_t)L, 16);
     b += 32 * 8 * 2 + 32 * 4 + 32 * 8 * 2;
-    b += align_up((size_t)seen_slots * 4, 16);
+    b += align_up(seen_bytes, 16);
     b += 16;
     return align_up(b, 128);
 }
 
-__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 rowb) {
+__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, size_t seen_bytes, u32 rowb) {
     WarpSmem s;
     s.qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 128);
     s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * rowb, 128);
@@ -203,12 +232,44 @@ __device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, u32 see
     s.ckey = reinterpret_cast<u64 *>(p); p += 32 * 8;
     s.cref = reinterpret_cast<u64 *>(p); p += 32 * 8;
     s.cid = reinterpret_cast<u32 *>(p); p += 32 * 4;
-    s.seen = reinterpret_cast<u32 *>(p); p += align_up((size_t)seen_slots * 4, 16);
+    s.seen = reinterpret_cast<u32 *>(p); p += align_up(seen_bytes, 16);
     s.bar = reinterpret_cast<u64 *>(p);
     return s;
 }
 
 __device__ __forceinline__ u32 seen_slot(u32 id, u32 bits) { return (id * 2654435761u) >> (32 - bits); }
+
+__host__ __device__ inline size_t seen_bytes(const SearchArgs &a) {
+    return a.seen_tag == 0 ? (size_t)a.seen_slots * 4 : (size_t)a.seen_words * 4 + (size_t)a.seen_slots * (a.seen_tag / 8);
+}
+
+__device__ __forceinline__ bool seen_has(const SearchArgs &a, const WarpSmem &s, u32 id) {
+    if (a.seen_tag == 0) return s.seen[seen_slot(id, a.seen_bits)] == id;
+    const u32 h = (id * 2654435761u) & a.seen_hmask, slot = h >> a.seen_shift, tag = h & a.seen_tmask;
+    if (!((s.seen[slot >> 5] >> (slot & 31)) & 1u)) return false;
+    const void *tags = s.seen + a.seen_words;
+    return a.seen_tag == 8 ? reinterpret_cast<const unsigned char *>(tags)[slot] == tag
+                           : reinterpret_cast<const unsigned short *>(tags)[slot] == tag;
+}
+
+// Lanes may record ids into the same slot at once: one tag stays, its bit set.
+__device__ __forceinline__ void seen_put(const SearchArgs &a, const WarpSmem &s, u32 id) {
+    if (a.seen_tag == 0) {
+        s.seen[seen_slot(id, a.seen_bits)] = id;
+        return;
+    }
+    const u32 h = (id * 2654435761u) & a.seen_hmask, slot = h >> a.seen_shift, tag = h & a.seen_tmask;
+    void *tags = s.seen + a.seen_words;
+    if (a.seen_tag == 8) reinterpret_cast<unsigned char *>(tags)[slot] = (unsigned char)tag;
+    else reinterpret_cast<unsigned short *>(tags)[slot] = (unsigned short)tag;
+    atomicOr(s.seen + (slot >> 5), 1u << (slot & 31));
+}
+
+__device__ __forceinline__ void seen_clear(const SearchArgs &a, const WarpSmem &s) {
+    const u32 n = a.seen_tag == 0 ? a.seen_slots : a.seen_words;
+    const u32 v = a.seen_tag == 0 ? NIL : 0u;
+    for (u32 i = lane_id(); i < n; i += 32) s.seen[i] = v;
+}
 
 __device__ __forceinline__ int lower_bound(const u64 *a, int n, u64 key) {
     int lo = 0, hi = n;
@@ -346,7 +407,7 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
     }
     const u64 key = lane < cnt ? s.ckey[lane] : KEY_INF;
     const u64 ref = lane < cnt ? s.cref[lane] : 0;
-    if (lane < cnt) s.seen[seen_slot(key_id(key), a.seen_bits)] = key_id(key);
+    if (lane < cnt) seen_put(a, s, key_id(key));
     return merge_beam(s, key, ref, n, (int)a.L, lo);
 }
 
@@ -481,7 +542,7 @@ __device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32
     const u64 *seed_row = a.seed + (size_t)qi * a.L;
     for (u32 i = lane * 4; i < mp; i += 128)
         *reinterpret_cast<float4 *>(s.qv + i) = *reinterpret_cast<const float4 *>(qrow + i);
-    for (u32 i = lane; i < a.seen_slots; i += 32) s.seen[i] = NIL;
+    seen_clear(a, s);
     __syncwarp();
     float4 qr[4];
 #pragma unroll
@@ -497,7 +558,7 @@ __device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32
         s.bkey[i] = k;
         s.bref[i] = ld_ref(d, id);
         s.bflag[i] = 0;
-        s.seen[seen_slot(id, a.seen_bits)] = id;
+        seen_put(a, s, id);
     }
     int n = n0;
     __syncwarp();
@@ -550,7 +611,7 @@ __device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32
         __syncwarp();
         for (u32 j0 = 0; j0 < deg; j0 += 32) {
             u32 nb = j0 == 0 ? e0 : e1;
-            if (nb != NIL && s.seen[seen_slot(nb, a.seen_bits)] == nb) nb = NIL;
+            if (nb != NIL && seen_has(a, s, nb)) nb = NIL;
             n = eval_merge<P, LOG>(a, s, nb, n, phase, ndist, timeout, lo, qr, qlog, qcnt);
         }
     }
@@ -631,8 +692,9 @@ __global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const u32 mp = d.mp;
-    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
-    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
+    const size_t sb = seen_bytes(a);
+    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, sb, a.rowb);
+    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, sb, a.rowb);
     if (lane == 0) mbar_init(s.bar, 1);
     __syncwarp();
     u32 phase = 0;
@@ -784,8 +846,9 @@ __global__ void __launch_bounds__(128, 3) ring_search_kernel(SearchArgs a, RingA
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
-    const size_t wb = search_warp_bytes(d.mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
-    WarpSmem s = carve(smem + warp * wb, d.mp, a.L, a.stage_rows, a.seen_slots, a.rowb);
+    const size_t sb = seen_bytes(a);
+    const size_t wb = search_warp_bytes(d.mp, a.L, a.stage_rows, sb, a.rowb);
+    WarpSmem s = carve(smem + warp * wb, d.mp, a.L, a.stage_rows, sb, a.rowb);
     if (lane == 0) mbar_init(s.bar, 1);
     __syncwarp();
     u32 phase = 0;
@@ -859,6 +922,18 @@ __global__ void __launch_bounds__(128, 3) ring_search_kernel(SearchArgs a, RingA
     }
 }
 
+static SeenLayout set_seen(SearchArgs &a, const Dev &d, u32 bits) {
+    const SeenLayout l = seen_layout(d.capacity, bits);
+    a.seen_bits = bits;
+    a.seen_slots = 1u << bits;
+    a.seen_tag = l.tag;
+    a.seen_shift = l.shift;
+    a.seen_tmask = l.tmask;
+    a.seen_hmask = l.hmask;
+    a.seen_words = l.words;
+    return l;
+}
+
 cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 max_hops, u32 k, u32 *out_ids,
                                float *out_dist, u64 *seed, const SearchTuning &tune, u32 blocks, cudaStream_t st,
                                u32 prec, u32 rerank, u64 *head, const u64 *tail, const u64 *closed, u64 *done,
@@ -868,8 +943,7 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
     a.d = d; a.q = rows; a.seed = seed; a.nq_dev = nullptr; a.nq = slots; a.L = L; a.max_hops = max_hops;
     a.mode = 0; a.k = k; a.out_ids = out_ids; a.out_dist = out_dist;
     a.stage_rows = tune.stage_rows;
-    a.seen_bits = tune.seen_bits;
-    a.seen_slots = 1u << tune.seen_bits;
+    const SeenLayout sl = set_seen(a, d, tune.seen_bits);
     a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
     a.rerank = rerank;
     a.exact = 0;
@@ -884,7 +958,7 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
     RingArgs r{head, head + 1, head + 2, head + 3, head + 4, tail, closed, done, served_by, slots, seq, max_ns};
     using K = void (*)(SearchArgs, RingArgs);
     K fn = prec == 1 ? ring_search_kernel<1> : prec == 2 ? ring_search_kernel<2> : ring_search_kernel<0>;
-    const size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
+    const size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.rowb);
     cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -897,8 +971,8 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
     return cudaGetLastError();
 }
 
-size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_slots, u32 wpb) {
-    return (size_t)wpb * search_warp_bytes(mp, L, stage_rows, seen_slots, mp * 4);
+size_t search_smem_bytes(u32 mp, u32 L, u32 stage_rows, u32 seen_bits, u64 capacity, u32 wpb) {
+    return (size_t)wpb * search_warp_bytes(mp, L, stage_rows, seen_layout(capacity, seen_bits).bytes, mp * 4);
 }
 
 cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, cudaStream_t st, u32 prec,
@@ -931,8 +1005,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.k = k;
     a.out_ids = out_ids; a.out_dist = out_dist; a.exp_keys = exp_keys; a.exp_count = exp_count;
     a.stage_rows = tune.stage_rows;
-    a.seen_bits = tune.seen_bits;
-    a.seen_slots = 1u << tune.seen_bits;
+    const SeenLayout sl = set_seen(a, d, tune.seen_bits);
     a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
     a.rerank = rerank;
     a.exact = exact_rows ? 1u : 0u;
@@ -957,7 +1030,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     else if (wpb == 2) fn = prec == 1 ? search_kernel<1, false, 2> : prec == 2 ? search_kernel<2, false, 2> : search_kernel<0, false, 2>;
     else if (wpb == 8) fn = prec == 1 ? search_kernel<1, false, 8> : prec == 2 ? search_kernel<2, false, 8> : search_kernel<0, false, 8>;
     else fn = prec == 1 ? search_kernel<1> : prec == 2 ? search_kernel<2> : search_kernel<0>;
-    size_t smem = (size_t)wpb * search_warp_bytes(d.mp, L, a.stage_rows, a.seen_slots, a.rowb);
+    size_t smem = (size_t)wpb * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.rowb);
     cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
