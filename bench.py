@@ -51,8 +51,14 @@ def parse():
     ap.add_argument("--exact-steps", type=int, default=2,
                     help="extra rounds timed with fp32 BeamSearches gathering the BF16 copy, which holds every "
                          "row of the integer-valued workload exactly (0: skip); reported apart from the headline")
-    ap.add_argument("--graph-steps", type=int, default=5,
-                    help="extra rounds replayed from a recorded round graph (0: skip); reported apart")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="rounds after the timed ones with the library's phase events on (phase times, "
+                         "writer-kernel rooflines); the timed rounds run without them")
+    ap.add_argument("--eager", action="store_true",
+                    help="time the headline rounds through the eager calls (etale_delete / etale_insert / "
+                         "etale_reclaim) instead of the recorded round graph")
+    ap.add_argument("--eager-steps", type=int, default=5,
+                    help="rounds also timed through the eager calls, reported beside the headline (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-recall-every-round", dest="recall_every_round", action="store_false",
                     help="skip the per-round Recall@10 (exact top-10 after every timed round, untimed)")
@@ -276,6 +282,8 @@ def config_dict(w, args):
             "search_beam": args.search_beam if args.search_beam_fixed else
             f"smallest of 64..256 with Recall@10 >= {0.95 + args.recall_margin:.3f} on the built index",
             "mode": args.mode, "n_entry": args.n_entry, "max_cand": args.max_cand or 2 * w.build_beam,
+            "round_path": "eager calls (etale_delete, etale_insert, etale_reclaim)" if args.eager else
+                          "recorded round graph (etale_round_graph_launch), one launch per round",
             "l2": "working set (index > 600 MB) larger than L2; no flush" if w.n_base >= 1_000_000 else
                   "small index; no flush", "parallelism": f"replicas x{args.gpus}"}
 
@@ -799,10 +807,10 @@ def main():
 
     from paper_2607_02543_gb300 import Index, build as B
     B.build()
-    main_rounds = args.warmup + args.steps * (1 if args.no_e2e else 2)
+    eager_rounds = 0 if args.eager else args.eager_steps * (1 if args.no_e2e else 2)
+    main_rounds = args.warmup + args.steps * (1 if args.no_e2e else 2) + eager_rounds + args.profile_steps
     exact_rounds = 1 + args.exact_steps if args.exact_steps > 0 else 0
-    graph_rounds = 2 * (1 + args.graph_steps) if args.graph_steps > 0 else 0
-    total_rounds = main_rounds + exact_rounds + graph_rounds
+    total_rounds = main_rounds + exact_rounds
     wr = W.dataclasses.replace(w, rounds=total_rounds)
     plan = W.make_plan(wr)
     n_entry = args.n_entry
@@ -871,8 +879,32 @@ def main():
         best = min(tried, key=lambda t: t[2])
         tuning = {"stage_rows": best[0], "seen_bits": best[1], "warps_per_block": best[3],
                   "tried": [list(t) for t in tried]}
-    for r in range(args.warmup):
+    for r in range(args.warmup - (0 if args.eager else 1)):
         round_dev(r)
+        idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+    torch.cuda.synchronize()
+    # The headline path: one round (delete -> insert with refine -> reclaim)
+    # recorded once as a CUDA graph and replayed with one launch per round;
+    # its buffers take each round's delete ids and rows.  Recorded after the
+    # eager warm-up rounds and query batches have sized the index's scratch.
+    g_del = torch.empty((w.n_delete,), dtype=torch.int32, device=dev)
+    g_ins = torch.empty((w.n_insert, w.dim), dtype=torch.float32, device=dev)
+    rgraph = None
+    if not args.eager:
+        rgraph = idx.round_graph(g_del, g_ins, None, None, k=w.k, beam=beam)
+
+    def round_head(r, src_del=None, src_ins=None):
+        """One headline round: the graph replay (with the copy of its inputs
+        into the recorded buffers), or the eager calls."""
+        if rgraph is None:
+            round_dev(r)
+            return
+        g_del.copy_(d_del[r] if src_del is None else src_del, non_blocking=True)
+        g_ins.copy_(d_ins[r] if src_ins is None else src_ins, non_blocking=True)
+        rgraph.launch(stream)
+
+    if rgraph is not None:                # the last warm-up round through the graph
+        round_head(args.warmup - 1)
         idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
     torch.cuda.synchronize()
     # the graph the timed rounds start from, for the oracle's timing (setup)
@@ -883,9 +915,7 @@ def main():
     barrier()
     clocks = Clocks(local)
     clocks.start()
-    idx.set_profiling(True)
     idx.profile(reset=True)
-    idx.work(reset=True)
     if args.nvtx:
         torch.cuda.nvtx.range_push("timed")
     ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(args.steps)]
@@ -898,11 +928,15 @@ def main():
     for i in range(args.steps):
         r = args.warmup + i
         ev[i][0].record(stream)
-        round_dev(r)
+        round_head(r)
         ev[i][1].record(stream)
         a = idx.stats()
         ev[i][2].record(stream)
+        # phase events only around the query search: its kernel's time for
+        # the roofline (the rounds run without the library's events)
+        idx.set_profiling(True)
         idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+        idx.set_profiling(False)
         ev[i][3].record(stream)
         b = idx.stats()
         search_stats.append((a, b))
@@ -921,8 +955,6 @@ def main():
     barrier()
     clk = clocks.stop()
     prof = idx.profile(reset=True)
-    work = idx.work(reset=True)
-    idx.set_profiling(False)
     launches = idx.kernel_launches() - l0
     maint_ms = [e[0].elapsed_time(e[1]) for e in ev]
     search_ms = [e[2].elapsed_time(e[3]) for e in ev]
@@ -981,31 +1013,84 @@ def main():
     sq_ms, sq_n = prof["search_query"]
     kernel_ms = sq_ms / max(sq_n, 1)          # one query-mode search_kernel launch per step
     achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    phases = {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]}
-    writers = writer_rooflines(work, prof, args.steps, peak, peak_kind)
-    # e2e: same rounds through the API with pinned host buffers
+    # e2e: the next rounds on the same path from pinned host buffers, the
+    # host -> device copies of each round's inputs inside the timed region;
+    # the graph path reads the round's counts back (etale_round_graph_sync),
+    # the eager calls return the new ids
     e2e = None
+    r_next = args.warmup + args.steps
+    h_q = torch.from_numpy(plan.queries).pin_memory()
     if not args.no_e2e:
-        h_del = [torch.from_numpy(dels[args.warmup + args.steps + i].astype(np.int32)).pin_memory().numpy()
-                 for i in range(args.steps)]
-        h_ins = [torch.from_numpy(plan.inserts[args.warmup + args.steps + i]).pin_memory().numpy()
-                 for i in range(args.steps)]
-        h_q = torch.from_numpy(plan.queries).pin_memory().numpy()
+        h_del = [torch.from_numpy(dels[r_next + i].astype(np.int32)).pin_memory() for i in range(args.steps)]
+        h_ins = [torch.from_numpy(plan.inserts[r_next + i]).pin_memory() for i in range(args.steps)]
         torch.cuda.synchronize()
         walls = []
         for i in range(args.steps):
             t = time.perf_counter()
-            idx.delete(h_del[i].view(np.uint32), stream)
-            idx.insert(h_ins[i], stream)
-            idx.reclaim(stream)
+            if rgraph is not None:
+                round_head(r_next + i, h_del[i], h_ins[i])
+                rgraph.sync()
+            else:
+                idx.delete(h_del[i].numpy().view(np.uint32), stream)
+                idx.insert(h_ins[i].numpy(), stream)
+                idx.reclaim(stream)
             walls.append((time.perf_counter() - t) * 1e3)
+        r_next += args.steps
         t = time.perf_counter()
-        idx.search(h_q, w.k, beam, stream)
+        idx.search(h_q.numpy(), w.k, beam, stream)
         e2e_search = (time.perf_counter() - t) * 1e3
         e2e = {"value": float(np.mean(walls)), "unit": "ms",
-               "h2d_bytes_per_step": int(w.n_insert * m * 4 + w.n_delete * 4 + w.n_queries * m * 4),
-               "d2h_bytes_per_step": int(w.n_insert * 4 + 8 + w.n_queries * w.k * 8),
-               "qps": w.n_queries / (e2e_search * 1e-3)}
+               "h2d_bytes_per_step": int(w.n_insert * m * 4 + w.n_delete * 4),
+               "d2h_bytes_per_step": 64 if rgraph is not None else int(w.n_insert * 4 + 8),
+               "path": "round graph" if rgraph is not None else "eager calls",
+               "qps": w.n_queries / (e2e_search * 1e-3),
+               "search_h2d_bytes": int(w.n_queries * m * 4), "search_d2h_bytes": int(w.n_queries * w.k * 8)}
+    # the same rounds through the eager calls (each call launches its kernels
+    # and waits for them), device-timed and from host buffers
+    eager_block = None
+    if rgraph is not None and args.eager_steps > 0:
+        eager_block = {"steps": args.eager_steps}
+        torch.cuda.synchronize()
+        eve = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(2)) for _ in range(args.eager_steps)]
+        for i in range(args.eager_steps):
+            eve[i][0].record(stream)
+            round_dev(r_next + i)
+            eve[i][1].record(stream)
+        torch.cuda.synchronize()
+        eager_block["ms"] = float(np.mean([e[0].elapsed_time(e[1]) for e in eve]))
+        r_next += args.eager_steps
+        if not args.no_e2e:
+            walls = []
+            for i in range(args.eager_steps):
+                hd = torch.from_numpy(dels[r_next + i].astype(np.int32)).pin_memory()
+                hi = torch.from_numpy(plan.inserts[r_next + i]).pin_memory()
+                t = time.perf_counter()
+                idx.delete(hd.numpy().view(np.uint32), stream)
+                idx.insert(hi.numpy(), stream)
+                idx.reclaim(stream)
+                walls.append((time.perf_counter() - t) * 1e3)
+            eager_block["e2e_ms"] = float(np.mean(walls))
+            r_next += args.eager_steps
+    # phase times and the writer kernels' rooflines: rounds after the timed
+    # (and e2e) ones through the eager calls, with the library's phase events on
+    r_prof = r_next
+    idx.set_profiling(True)
+    idx.profile(reset=True)
+    idx.work(reset=True)
+    for i in range(args.profile_steps):
+        round_dev(r_prof + i)
+    torch.cuda.synchronize()
+    wprof = idx.profile(reset=True)
+    work = idx.work(reset=True)
+    idx.set_profiling(False)
+    nps = max(args.profile_steps, 1)
+    phases = {k: round(v[0] / nps, 4) for k, v in wprof.items() if v[1]}
+    phases["search_query"] = round(prof["search_query"][0] / max(args.steps, 1), 4)
+    phases["seed_query"] = round(prof["seed"][0] / max(args.steps, 1), 4)
+    writers = writer_rooflines(work, wprof, nps, peak, peak_kind) if args.profile_steps else {}
+    if rgraph is not None:
+        rgraph.close()                   # the later blocks use eager calls only
+        rgraph = None
     # supplementary: the same rounds with fp32 BeamSearches gathering the bf16
     # copy while it holds every stored row exactly (bit-identical distances,
     # half the row bytes); not the headline, which gathers the fp32 rows
@@ -1056,41 +1141,6 @@ def main():
                 "note": "rows gathered from the bf16 copy, which holds every stored row exactly; distances "
                         "bit-identical to the fp32 rows (tests/test_gpu_exact_rows.py)"}
         idx.set_exact_rows(False)
-    # the same rounds recorded once as a CUDA graph (etale_round_graph_*) and
-    # replayed with one launch each: round only (as `value`), then round +
-    # the query batch (as ms_per_step).  Each timed step includes the copy of
-    # its delete ids and rows into the recorded buffers.
-    graph_block = None
-    if args.graph_steps > 0:
-        r0 = main_rounds + exact_rounds
-        g_del = torch.empty((w.n_delete,), dtype=torch.int32, device=dev)
-        g_ins = torch.empty((w.n_insert, w.dim), dtype=torch.float32, device=dev)
-        graph_block = {"steps": args.graph_steps}
-        for name, with_q in (("round", False), ("round_and_queries", True)):
-            rgraph = idx.round_graph(g_del, g_ins, d_q if with_q else None, (out_ids, out_d) if with_q else None,
-                                     k=w.k, beam=beam)
-            evg = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(2)) for _ in range(1 + args.graph_steps)]
-            l0g = idx.kernel_launches()
-            for i in range(1 + args.graph_steps):      # the first replay is a warm-up
-                evg[i][0].record(stream)
-                g_del.copy_(d_del[r0], non_blocking=True)
-                g_ins.copy_(d_ins[r0], non_blocking=True)
-                rgraph.launch(stream)
-                evg[i][1].record(stream)
-                r0 += 1
-            rgraph.sync()
-            ms_g = [e[0].elapsed_time(e[1]) for e in evg[1:]]
-            graph_block[name + "_ms"] = float(np.mean(ms_g))
-            graph_block[name + "_launches_per_step"] = (idx.kernel_launches() - l0g) / (1 + args.graph_steps)
-            if with_q:
-                gtg, _ = idx.ground_truth(d_q, w.k, stream)
-                graph_block["recall_at_10"] = float(np.mean([
-                    len(set(u.tolist()) & set(v.tolist())) / w.k
-                    for u, v in zip(out_ids.cpu().numpy().view(np.uint32), gtg.cpu().numpy().view(np.uint32))]))
-                graph_block["qps"] = w.n_queries / ((graph_block["round_and_queries_ms"] - graph_block["round_ms"]) * 1e-3)
-            rgraph.close()
-        st_g = idx.stats()
-        graph_block["used_slabs_eq_live"] = st_g["used_slabs"] == st_g["live"]
     # max over ranks
     ms_round, ms_search = reduce_max([ms_round, ms_search], world, dev)
     st = idx.stats()
@@ -1130,8 +1180,11 @@ def main():
                             "frac_with_reevaluations": kernel_bytes / (kernel_ms * 1e-3) / 1e9 / peak,
                             "rows_gathered": "bf16 copy (exact for every stored row)" if exact_copy else "fp32",
                             "kernel_ms": kernel_ms},
-               "phase_ms_per_step": phases, "writer_rooflines": writers, "ground_truth": gt_block, "search_tuning": tuning,
-               "precision": prec_block, "exact_bf16_rows": exact_block, "round_graph": graph_block,
+               "phase_ms_per_step": phases,
+               "phase_ms_source": f"{args.profile_steps} rounds after the timed ones with the library's phase "
+                                  "events on; search_query and seed_query: the timed steps' query batches",
+               "writer_rooflines": writers, "ground_truth": gt_block, "search_tuning": tuning,
+               "precision": prec_block, "exact_bf16_rows": exact_block, "eager_calls": eager_block,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)
