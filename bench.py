@@ -101,21 +101,44 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
     return W.scaled(w, n_live) if n_live else w
 
 
-# DRAM bytes of one query-mode BeamSearch launch on the 1M x 128 workload, from
-# the ncu capture in profiles/search_kernel_int256-1m-d128_dram.md; valid only
-# for the search.cu revision it was taken on (first 16 hex digits of SHA-256).
-SEARCH_DRAM_BYTES = {"int256-1m-d128": (10_486_715_904 + 1_275_904, "b7a690c3dfe366f4")}
+# DRAM bytes per BeamSearch expansion of the query-mode launch on the 1M x 128
+# workload, from the full-size ncu capture in
+# profiles/search_kernel_int256-1m-d128_dram.md (9,387,749,888 bytes over
+# 1,287,324 expansions at beam 128); a launch's traffic is this figure times
+# its expansions.  Valid only for the search.cu revision it was taken on
+# (first 16 hex digits of SHA-256).
+SEARCH_DRAM_BYTES_PER_EXPANSION = {"int256-1m-d128": (9_387_749_888 / 1_287_324, "113aadf19177b3a2")}
 
 
-def search_traffic(workload_name: str):
-    """DRAM bytes per query-mode search launch if measured for this source, else None."""
+# DRAM bytes of each writer kernel over one round of 10,000 deletes + 10,000
+# inserts on the 1M x 128 workload (the same capture; offer_fold: the insert
+# offers and the refine offers).  Valid only for the update.cu revision given.
+WRITER_DRAM_BYTES = {"int256-1m-d128": ({"prune": 94_413_056, "offer_fold": 455_783_168, "refine": 84_920_576,
+                                         "repair_k": 173_362_688, "repair_fold": 822_257_664,
+                                         "compact": 296_149_504}, "122d52ac54be7b33")}
+
+
+def writer_traffic(workload_name: str):
+    """{kind: DRAM bytes per round} if measured for this update.cu, else {}."""
     import hashlib
-    entry = SEARCH_DRAM_BYTES.get(workload_name)
+    entry = WRITER_DRAM_BYTES.get(workload_name)
+    if entry is None:
+        return {}
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2607_02543_gb300", "csrc", "update.cu")
+    rev = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return entry[0] if rev == entry[1] else {}
+
+
+def search_traffic(workload_name: str, n_expand: float):
+    """DRAM bytes of a query-mode search launch with n_expand expansions, if
+    measured for this source, else None."""
+    import hashlib
+    entry = SEARCH_DRAM_BYTES_PER_EXPANSION.get(workload_name)
     if entry is None:
         return None
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2607_02543_gb300", "csrc", "search.cu")
     rev = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return entry[0] if rev == entry[1] else None
+    return entry[0] * n_expand if rev == entry[1] else None
 
 
 def load_peaks(key: str = "hbm_gbs"):
@@ -603,10 +626,12 @@ def run_serve(args):
     print(json.dumps(res), flush=True)
 
 
-def writer_rooflines(work, prof, steps, peak, peak_kind):
+def writer_rooflines(work, prof, steps, peak, peak_kind, traffic=None):
     """Per writer kernel: the bytes its step of the method moves (the
     kernels' own tallies, etale_get_work: vector rows gathered plus graph
-    state read and written) over the phase's CUDA-event time."""
+    state read and written) over the phase's CUDA-event time; `traffic`, the
+    ncu DRAM bytes per round where measured for this source."""
+    traffic = traffic or {}
     out = {}
     for kind, (rows_b, state_b) in work.items():
         ms, n = prof.get(kind, (0.0, 0))
@@ -616,7 +641,8 @@ def writer_rooflines(work, prof, steps, peak, peak_kind):
         ach = b / (ms / steps * 1e-3) / 1e9
         out[kind] = {"ms_per_step": ms / steps, "launches_per_step": n / steps, "alg_bytes_per_step": b,
                      "row_bytes_per_step": rows_b / steps, "state_bytes_per_step": state_b / steps,
-                     "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": peak_kind}
+                     "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": peak_kind,
+                     "traffic_per_step": traffic.get(kind)}
     return out
 
 
@@ -1087,7 +1113,9 @@ def main():
     phases = {k: round(v[0] / nps, 4) for k, v in wprof.items() if v[1]}
     phases["search_query"] = round(prof["search_query"][0] / max(args.steps, 1), 4)
     phases["seed_query"] = round(prof["seed"][0] / max(args.steps, 1), 4)
-    writers = writer_rooflines(work, wprof, nps, peak, peak_kind) if args.profile_steps else {}
+    writers = writer_rooflines(work, wprof, nps, peak, peak_kind,
+                               writer_traffic(w.name) if (w.n_delete, w.n_insert) == (10_000, 10_000) else None) \
+        if args.profile_steps else {}
     if rgraph is not None:
         rgraph.close()                   # the later blocks use eager calls only
         rgraph = None
@@ -1171,7 +1199,7 @@ def main():
                "qps": world * w.n_queries / (ms_search * 1e-3),
                "search_ms_per_10k": ms_search, "build_s": build_s,
                "roofline": {"bound": "hbm", "kernel": "search_kernel (query mode)", "achieved": achieved,
-                            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": search_traffic(w.name),
+                            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": search_traffic(w.name, nexp),
                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
                             "alg_bytes_basis": "expansions x 8R + distinct non-seed evaluations x (row + 8) + "
                                                "queries x (4m + 8k)",
