@@ -908,6 +908,7 @@ def main():
     for r in range(args.warmup - (0 if args.eager else 1)):
         round_dev(r)
         idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))
+    idx.search(d_q, w.k, beam, stream, out=(out_ids, out_d))   # the query scratch at its size
     torch.cuda.synchronize()
     # The headline path: one round (delete -> insert with refine -> reclaim)
     # recorded once as a CUDA graph and replayed with one launch per round;
