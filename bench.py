@@ -653,7 +653,7 @@ def run_varbatch(args):
     log-uniform [1, 16,384] queries through one captured query graph (batch
     size read from device memory).  The BeamSearch launch shape is tuned by
     the library's autotuner and EF_SEARCH is the smallest beam reaching
-    Recall@10 >= 0.95 on 1,000 anchor queries.  Reports ms per round against
+    Recall@10 >= 0.95 + margin on 1,000 anchor queries.  Reports ms per round against
     the batch sizes, QPS, Recall@10 of the anchors after the run, and the
     query batches' algorithmic bytes per second against the measured HBM peak."""
     import torch
@@ -698,11 +698,13 @@ def run_varbatch(args):
         gt_np = gt_a.cpu().numpy().view(np.uint32)
 
     refresh_gt()
+    # the same margin as the headline: the 30 rounds delete up to 2% of the
+    # live set each, and Recall@10 at a fixed beam declines over them
     beam, sweep = 256, []
     for b in (64, 96, 128, 160, 192, 256):
         rec = anchor_recall(b)
         sweep.append([b, rec])
-        if rec >= 0.95:
+        if rec >= 0.95 + args.recall_margin:
             beam = b
             break
     tried = idx.autotune_search(d_pool[:4096].contiguous(), w.k, beam, stream)
