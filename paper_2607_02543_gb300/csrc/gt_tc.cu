@@ -12,7 +12,9 @@
 //      segment is used, otherwise all three (hi.hi + hi.lo + lo.hi).
 //   2. gt_tc_kernel: persistent CTAs; TMA (cp.async.bulk.tensor, 128-byte
 //      swizzle) streams 256-row boxes of the row copy through a shared
-//      memory ring while the query tile stays resident; one thread issues
+//      memory ring while the query tile stays resident (or, when the query
+//      tile's K does not fit shared memory, travels through the ring beside
+//      each row box, one 64-column block at a time); one thread issues
 //      tcgen05.mma (M = 128, N = 256, bf16 -> fp32) into a double-buffered TMEM
 //      accumulator; eight epilogue warps read it with tcgen05.ld and write,
 //      per query and per block of 32 rows, the smallest approximate key
@@ -63,6 +65,7 @@ __host__ __device__ constexpr u32 tc_idesc(u32 n) {
 struct TcArgs {
     u32 nq, n_tiles, kblocks, n_msub, bn, m_tiles, chunks, tiles_per_chunk, stages;
     u32 all_keys;         // 0: smallest key per block of 32 rows; 1: every key
+    u32 stream_a;         // 1: the query boxes travel through the ring with the row boxes
     u32 ld;               // row length of the output (blocks or keys)
     float s;              // -2 (L2) or -1 (IP)
     const float *xn;      // n_tiles * bn key bases (+inf for dead rows and padding)
@@ -119,11 +122,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ u32 tmem_base;
     __shared__ volatile int abort_flag;
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = sm;
-    unsigned char *sB = sm + (size_t)a.n_msub * a.kblocks * TC_BOX;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const u32 items = a.m_tiles * a.chunks;
     const u32 bbox = a.bn * TC_KBOX * 2;            // bytes of one row box
+    // resident: sA holds the query tile (n_msub x kblocks boxes), then the
+    // ring of row boxes; streamed: each ring stage is a row box followed by
+    // the n_msub query boxes of the same 64 columns
+    const u32 abox = a.n_msub * TC_BOX;
+    const u32 sbytes = bbox + (a.stream_a ? abox : 0u);
+    unsigned char *sA = sm;
+    unsigned char *sB = sm + (a.stream_a ? 0u : (size_t)a.kblocks * abox);
 
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < a.stages; i++) {
@@ -165,23 +173,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
                 const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
-                if (!first) {
-                    if (!mbar_wait(&a_empty, a_ph, WAIT_LIMIT)) { fail(); break; }
-                    a_ph ^= 1;
+                if (!a.stream_a) {
+                    if (!first) {
+                        if (!mbar_wait(&a_empty, a_ph, WAIT_LIMIT)) { fail(); break; }
+                        a_ph ^= 1;
+                    }
+                    first = false;
+                    mbar_expect_tx(&a_full, a.kblocks * abox);
+                    for (u32 s = 0; s < a.n_msub; s++)
+                        for (u32 kb = 0; kb < a.kblocks; kb++)
+                            tma_load_2d(sA + (size_t)(s * a.kblocks + kb) * TC_BOX, &tmA, (int)(kb * TC_KBOX),
+                                        (int)((mt * a.n_msub + s) * TC_ROWS), &a_full);
+                    a_issued++;
                 }
-                first = false;
-                mbar_expect_tx(&a_full, a.n_msub * a.kblocks * TC_BOX);
-                for (u32 s = 0; s < a.n_msub; s++)
-                    for (u32 kb = 0; kb < a.kblocks; kb++)
-                        tma_load_2d(sA + (size_t)(s * a.kblocks + kb) * TC_BOX, &tmA, (int)(kb * TC_KBOX),
-                                    (int)((mt * a.n_msub + s) * TC_ROWS), &a_full);
-                a_issued++;
                 for (u32 t = t0; t < t1 && !abort_flag; t++) {
                     for (u32 kb = 0; kb < a.kblocks; kb++) {
                         if (!mbar_wait(&empty[stage], ph ^ 1, WAIT_LIMIT)) { fail(); break; }
-                        mbar_expect_tx(&full[stage], bbox);
-                        tma_load_2d(sB + (size_t)stage * bbox, &tmB, (int)(kb * TC_KBOX), (int)(t * a.bn),
-                                    &full[stage]);
+                        unsigned char *sb = sB + (size_t)stage * sbytes;
+                        mbar_expect_tx(&full[stage], sbytes);
+                        tma_load_2d(sb, &tmB, (int)(kb * TC_KBOX), (int)(t * a.bn), &full[stage]);
+                        if (a.stream_a)
+                            for (u32 s = 0; s < a.n_msub; s++)
+                                tma_load_2d(sb + bbox + (size_t)s * TC_BOX, &tmA, (int)(kb * TC_KBOX),
+                                            (int)((mt * a.n_msub + s) * TC_ROWS), &full[stage]);
                         issued |= 1u << stage;
                         lastpar = (lastpar & ~(1u << stage)) | (ph << stage);
                         if (++stage == a.stages) {
@@ -203,9 +217,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
                 const u32 ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
-                if (!mbar_wait(&a_full, a_ph, WAIT_LIMIT)) { fail(); break; }
-                a_ph ^= 1;
-                tc_fence_after();
+                if (!a.stream_a) {
+                    if (!mbar_wait(&a_full, a_ph, WAIT_LIMIT)) { fail(); break; }
+                    a_ph ^= 1;
+                    tc_fence_after();
+                }
                 for (u32 t = t0; t < t1 && !abort_flag; t++, tcount++) {
                     const u32 b = tcount & 1;
                     if (!mbar_wait(&t_empty[b], ((tcount >> 1) & 1) ^ 1, WAIT_LIMIT)) { fail(); break; }
@@ -217,13 +233,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (u32 kb = 0; kb < a.kblocks; kb++) {
                         if (!mbar_wait(&full[stage], ph, WAIT_LIMIT)) { ok = false; break; }
                         tc_fence_after();
-                        const u32 bb = smem_addr(sB + (size_t)stage * bbox);
+                        const u32 bb = smem_addr(sB + (size_t)stage * sbytes);
                         const u32 idesc = tc_idesc(a.bn);
 #pragma unroll
                         for (u32 k = 0; k < TC_KBOX / 16; k++) {
                             const u64 bd = sw128_desc(bb + k * 32);
                             for (u32 s = 0; s < a.n_msub; s++) {
-                                const u32 aa = smem_addr(sA + (size_t)(s * a.kblocks + kb) * TC_BOX) + k * 32;
+                                const u32 aa = (a.stream_a ? bb + bbox + s * TC_BOX
+                                                           : smem_addr(sA + (size_t)(s * a.kblocks + kb) * TC_BOX)) +
+                                               k * 32;
                                 tc_mma(tmem + b * TC_ACC + s * TC_ROWS, sw128_desc(aa), bd, idesc, (kb | k) != 0);
                             }
                         }
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         break;
                     }
                 }
-                tc_commit(&a_empty);
+                if (!a.stream_a) tc_commit(&a_empty);
             }
             // all MMAs and key-base copies issued by this thread are complete
             // before TMEM and shared memory are released
@@ -794,12 +812,20 @@ void gt_tc_configure(GtTcPlan &p, u32 nq, bool split) {
     p.n_msub = 1;
     p.bn = TC_ACC / p.n_msub;
     const u32 bbox = p.bn * TC_KBOX * 2;
-    if ((u64)p.n_msub * p.kblocks * TC_BOX + 2ull * bbox > smem_max || p.n_pad == 0) {
+    if (p.n_pad == 0) {
         p.usable = false;
         return;
     }
-    p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - p.n_msub * p.kblocks * TC_BOX) / bbox);
-    p.smem = p.n_msub * p.kblocks * TC_BOX + p.stages * bbox + 1024;
+    // the query tile stays resident when it fits beside two ring stages;
+    // otherwise its boxes travel through the ring with the row boxes
+    p.stream_a = (u64)p.n_msub * p.kblocks * TC_BOX + 2ull * bbox > smem_max;
+    if (p.stream_a) {
+        p.stages = std::min<u32>(TC_MAX_STAGES, smem_max / (bbox + p.n_msub * TC_BOX));
+        p.smem = p.stages * (bbox + p.n_msub * TC_BOX) + 1024;
+    } else {
+        p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - p.n_msub * p.kblocks * TC_BOX) / bbox);
+        p.smem = p.n_msub * p.kblocks * TC_BOX + p.stages * bbox + 1024;
+    }
     p.n_tiles = (u32)(p.n_pad / p.bn);
     p.nblk = (u32)(p.n_pad / 32);
     // queries per pass: the block-minimum buffer stays under 4 GiB
@@ -840,6 +866,7 @@ cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const 
     a.tiles_per_chunk = (p.n_tiles + best_c - 1) / best_c;
     a.chunks = (p.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
     a.stages = p.stages;
+    a.stream_a = p.stream_a ? 1u : 0u;
     a.all_keys = 0;
     a.ld = p.nblk;
     a.s = d.metric == 0 ? -2.0f : -1.0f;
@@ -888,9 +915,16 @@ SeedTcPlan seed_tc_plan(u32 dim, u32 n_entry, u32 nq) {
     const u32 smem_max = 227 * 1024 - 1024 - 4096;
     const u32 bbox = TC_ACC * TC_KBOX * 2;
     const u32 abytes = (p.kb / TC_KBOX) * TC_BOX;
-    p.usable = abytes + 2 * bbox <= smem_max && n_entry > 0;
-    p.stages = p.usable ? std::min<u32>(TC_MAX_STAGES, (smem_max - abytes) / bbox) : 0;
-    p.smem = abytes + p.stages * bbox + 1024;
+    p.usable = n_entry > 0;
+    // the query tile resident when it fits beside two ring stages, else streamed
+    p.stream_a = abytes + 2 * bbox > smem_max;
+    if (p.stream_a) {
+        p.stages = std::min<u32>(TC_MAX_STAGES, smem_max / (bbox + TC_BOX));
+        p.smem = p.stages * (bbox + TC_BOX) + 1024;
+    } else {
+        p.stages = std::min<u32>(TC_MAX_STAGES, (smem_max - abytes) / bbox);
+        p.smem = abytes + p.stages * bbox + 1024;
+    }
     p.bytes_E = (size_t)n_entry * p.kb * 2;
     p.bytes_A = (size_t)nq * p.kb * 2;
     p.bytes_keys = (size_t)nq * p.s_pad * 4;
@@ -936,6 +970,7 @@ cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u
     a.tiles_per_chunk = (a.n_tiles + best_c - 1) / best_c;
     a.chunks = (a.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
     a.stages = p.stages;
+    a.stream_a = p.stream_a ? 1u : 0u;
     a.all_keys = 1;
     a.ld = p.s_pad;
     a.s = d.metric == 0 ? -2.0f : -1.0f;

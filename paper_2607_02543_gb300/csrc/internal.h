@@ -136,6 +136,7 @@ struct GtTcPlan {
     u32 kprime = 0, kblocks = 0, n_msub = 0, bn = 0, stages = 0, smem = 0, n_tiles = 0, nblk = 0;
     u32 qgroup = 0;                 // queries per candidate pass
     bool split = false, usable = false;
+    bool stream_a = false;          // the query tile travels through the ring (K too large to stay resident)
 };
 struct GtTcBufs {
     void *A, *B;                    // query and row bf16 copies
@@ -149,6 +150,7 @@ struct SeedTcPlan {
     u32 kp1 = 0, kb = 0, s_pad = 0, stages = 0, smem = 0;
     size_t bytes_E = 0, bytes_A = 0, bytes_keys = 0;
     bool usable = false;
+    bool stream_a = false;          // as GtTcPlan::stream_a
 };
 struct SeedTcBufs {
     void *E, *A;                    // entry and query bf16 copies ([hi | lo | hi], [hi | hi | lo])

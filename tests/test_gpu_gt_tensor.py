@@ -32,10 +32,13 @@ def _pair_indices(w, n, deleted_every, **kw):
     ("gauss", 4_000 + 5, 10, "tensor_split"),
     ("unit", 3_000 + 31, 7, "tensor_split"),
     ("int", 300, 32, "tensor"),
+    ("wide", 2_000 + 3, 10, "tensor_split"),    # 300-d: the query tile streams through the ring
+    ("gist", 1_500 + 11, 10, "tensor_split"),   # 960-d non-negative mixture, streamed
 ])
 def test_tensor_ground_truth_matches_exact(oracle_mod, wname, n, k, path):
     base = {"int": W.SIFT_LIKE_1M, "gauss": W.SMALL,
-            "unit": dataclasses.replace(W.SMALL, metric="ip", kind="unit", dim=96)}[wname]
+            "unit": dataclasses.replace(W.SMALL, metric="ip", kind="unit", dim=96),
+            "wide": dataclasses.replace(W.SMALL, dim=300), "gist": W.GIST_LIKE_1M}[wname]
     plan, (gt_tc, gt_cc) = _pair_indices(base, n, 9)
     ti, td = gt_tc.ground_truth(plan.queries, k)
     info = gt_tc.ground_truth_info()

@@ -1,9 +1,10 @@
 """Entry-set seeding on tensor cores (certified exact rerank) against the
 CUDA-core seed kernel: in deterministic mode the two must build bit-identical
 graphs and return identical searches, on integer data (exact in bf16) and on
-Gaussian and unit-vector data (hi/lo split), with entry sets smaller and
-larger than the beam and insert batches above and below the tensor path's
-minimum batch."""
+Gaussian and unit-vector data (hi/lo split), at dimensions where the query
+tile stays in shared memory and where it streams through the copy ring, with
+entry sets smaller and larger than the beam and insert batches above and
+below the tensor path's minimum batch."""
 import dataclasses
 
 import numpy as np
@@ -20,11 +21,14 @@ pytestmark = pytest.mark.gpu
     ("gauss", 5_000, 700, 64),
     ("unit", 4_000, 256, 96),
     ("int", 3_000, 40, 64),          # fewer entries than the beam: every entry is a seed
+    ("wide", 3_000, 512, 64),        # 300-d: the query tile streams through the ring
+    ("gist", 2_000, 300, 48),        # 960-d non-negative mixture, streamed
 ])
 def test_tensor_seeds_build_the_same_graph(wname, n, n_entry, beam):
     from paper_2607_02543_gb300 import Index
     base = {"int": W.SIFT_LIKE_1M, "gauss": W.SMALL,
-            "unit": dataclasses.replace(W.SMALL, metric="ip", kind="unit", dim=96)}[wname]
+            "unit": dataclasses.replace(W.SMALL, metric="ip", kind="unit", dim=96),
+            "wide": dataclasses.replace(W.SMALL, dim=300), "gist": W.GIST_LIKE_1M}[wname]
     w = dataclasses.replace(W.scaled(base, n, n_queries=500), rounds=2)
     plan = W.make_plan(w)
     out = []
