@@ -346,7 +346,14 @@ typedef struct etale_search_graph etale_search_graph;
  * size and the entry-set size from device memory, so one graph serves every
  * batch size and stays valid across later updates of the index.  The search
  * precision and launch shape in force at creation are baked in.  The graph
- * owns its scratch (allocated here, freed by destroy).                     */
+ * owns its scratch (allocated here, freed by destroy).
+ * Seeding: when the index seeds on tensor cores, fp32 search, the entry set
+ * is full (n_entry entries), nq_max >= 32 and the index is not in
+ * concurrent mode, the graph seeds on tensor cores as etale_search does
+ * (same seeds) and pins the index's entry copies; a launch is then refused
+ * (EINVAL) if the entry set changed size or concurrent mode is on, and
+ * etale_destroy refuses while such a graph lives.  Otherwise it seeds on
+ * CUDA cores.                                                              */
 etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32_t k, uint32_t beam,
                                        const float *queries, uint32_t *out_ids, float *out_dists,
                                        const uint32_t *nq_dev, etale_search_graph **out);

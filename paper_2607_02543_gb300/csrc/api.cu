@@ -95,7 +95,7 @@ struct etale_index {
     bool rows_exact = true;         // every ingested row's bf16 copy is exact (C_INEXACT == 0)
     u32 *nent_dev = nullptr;        // |E| in device memory
     u64 *rs = nullptr;              // round state (RS_* words) of recorded rounds
-    int round_graphs = 0;           // live round graphs
+    int round_graphs = 0;           // live graphs that pin index buffers (round graphs, tensor-seeded query graphs)
     bool graph_pending = false;     // a round graph ran since the host state was read
     cudaEvent_t graph_ev = nullptr; // recorded after the last round-graph launch
     u64 *host_ctr = nullptr;   // pinned mirror
@@ -609,6 +609,14 @@ struct etale_search_graph {
     cudaGraphExec_t exec = nullptr;
     float *qpad = nullptr;
     u64 *seed = nullptr;
+    // tensor-core seeding: the graph's own query-side staging; the entry
+    // copies are the index's, pinned while the graph lives
+    bool tc = false;
+    u32 S = 0;                            // |E| recorded
+    void *tA = nullptr;
+    float *tqstat = nullptr, *tkeys = nullptr;
+    u32 *tfb = nullptr, *tctr = nullptr;
+    u32 launches = 3;                     // kernels per replay
 };
 
 // ===========================================================================
@@ -765,7 +773,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
 etale_status etale_destroy(etale_index *idx) {
     if (!idx) return ETALE_OK;
     if (idx->round_graphs) {
-        t_last_error = "destroy the index's round graphs first";
+        t_last_error = "destroy the index's round graphs and tensor-seeded query graphs first";
         return ETALE_EINVAL;
     }
     cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
@@ -1456,9 +1464,39 @@ etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32
     }
     const Dev d = idx->dev();
     const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
+    // Seeds on tensor cores (the batch size read on the device) when the
+    // entry set is full, so that its size cannot change under the graph, and
+    // writers do not run concurrently; else the CUDA-core seed kernel.
+    const u32 S = idx->n_entries;
+    SeedTcPlan tp{};
+    SeedTcBufs tb{};
+    if (idx->search_prec == 0 && idx->seed_tc && !idx->concurrent && S > 0 && S == idx->cfg.n_entry &&
+        nq_max >= 32) {
+        tp = seed_tc_plan(idx->dim, S, nq_max);
+        if (idx->sd_E.p && cudaMalloc(&g->tA, tp.bytes_A) == cudaSuccess &&
+            cudaMalloc(&g->tqstat, (size_t)nq_max * 16) == cudaSuccess &&
+            cudaMalloc(&g->tkeys, tp.bytes_keys) == cudaSuccess &&
+            cudaMalloc(&g->tfb, (size_t)nq_max * 4) == cudaSuccess && cudaMalloc(&g->tctr, 64) == cudaSuccess) {
+            g->tc = true;
+            g->S = S;
+            g->launches = 6;
+            tb = idx->seed_bufs();
+            tb.A = g->tA;
+            tb.qstat = g->tqstat;
+            tb.keys = g->tkeys;
+            tb.fb = g->tfb;
+            tb.ctr = g->tctr;
+            for (DevBuf *p : {&idx->sd_E, &idx->sd_en, &idx->sd_estat}) p->pins++;
+            idx->round_graphs++;
+        } else {
+            cudaGetLastError();
+        }
+    }
     auto enqueue = [&]() {
         cudaError_t e = launch_ingest(g->qpad, idx->mp, queries, idx->dim, nq_max, cs, nq_dev);
-        if (e == cudaSuccess) e = launch_seed(d, g->qpad, nq_max, L, g->seed, cs, idx->search_prec, nq_dev);
+        if (e == cudaSuccess)
+            e = g->tc ? launch_seed_tc(d, g->qpad, nq_max, S, L, g->seed, tp, tb, idx->num_sms, cs, nq_dev)
+                      : launch_seed(d, g->qpad, nq_max, L, g->seed, cs, idx->search_prec, nq_dev);
         if (e == cudaSuccess)
             e = launch_search(d, g->qpad, nq_max, L, H, 0, k, out_ids, out_dists, nullptr, nullptr, g->seed,
                               fit_tuning(idx, L, idx->tune), idx->num_sms, cs, idx->search_prec, idx->cfg.rerank, nq_dev);
@@ -1485,9 +1523,12 @@ etale_status etale_search_graph_create(etale_index *idx, uint32_t nq_max, uint32
 
 etale_status etale_search_graph_launch(etale_search_graph *g, void *stream) {
     if (!g) return ETALE_EINVAL;
+    if (g->tc && (g->idx->n_entries != g->S || g->idx->concurrent))
+        return g->idx->fail(ETALE_EINVAL, "graph recorded with tensor-core seeding: the entry set must keep its "
+                                          "size and writers must not run concurrently");
     cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return g->idx->cuda_fail(e, "graph launch");
-    g_kernel_launches += 3;
+    g_kernel_launches += g->launches;
     if (g->idx->concurrent) {
         std::lock_guard<std::mutex> lk(g->idx->mu);
         CK2(g->idx, cudaEventRecord(g->idx->search_ev, (cudaStream_t)stream), "record search event");
@@ -1507,6 +1548,15 @@ etale_status etale_search_graph_destroy(etale_search_graph *g) {
     if (g->graph) cudaGraphDestroy(g->graph);
     cudaFree(g->qpad);
     cudaFree(g->seed);
+    if (g->tc) {
+        for (DevBuf *p : {&g->idx->sd_E, &g->idx->sd_en, &g->idx->sd_estat}) p->pins--;
+        g->idx->round_graphs--;
+    }
+    cudaFree(g->tA);
+    cudaFree(g->tqstat);
+    cudaFree(g->tkeys);
+    cudaFree(g->tfb);
+    cudaFree(g->tctr);
     delete g;
     return ETALE_OK;
 }

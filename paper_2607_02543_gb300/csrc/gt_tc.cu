@@ -66,6 +66,7 @@ struct TcArgs {
     u32 nq, n_tiles, kblocks, n_msub, bn, m_tiles, chunks, tiles_per_chunk, stages;
     u32 all_keys;         // 0: smallest key per block of 32 rows; 1: every key
     u32 stream_a;         // 1: the query boxes travel through the ring with the row boxes
+    const u32 *nq_dev;    // when set, the batch size is read here (nq is its cap); later query tiles are skipped
     u32 ld;               // row length of the output (blocks or keys)
     float s;              // -2 (L2) or -1 (IP)
     const float *xn;      // n_tiles * bn key bases (+inf for dead rows and padding)
@@ -125,6 +126,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const u32 items = a.m_tiles * a.chunks;
     const u32 bbox = a.bn * TC_KBOX * 2;            // bytes of one row box
+    // query tiles past the batch size in device memory are skipped, the same
+    // items by every role
+    const u32 nq_eff = a.nq_dev ? min(*a.nq_dev, a.nq) : a.nq;
+    const u32 mt_eff = (nq_eff + a.n_msub * TC_ROWS - 1) / (a.n_msub * TC_ROWS);
     // resident: sA holds the query tile (n_msub x kblocks boxes), then the
     // ring of row boxes; streamed: each ring stage is a row box followed by
     // the n_msub query boxes of the same 64 columns
@@ -173,6 +178,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
                 const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
+                if (mt >= mt_eff) continue;
                 if (!a.stream_a) {
                     if (!first) {
                         if (!mbar_wait(&a_empty, a_ph, WAIT_LIMIT)) { fail(); break; }
@@ -217,6 +223,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (u32 it = blockIdx.x; it < items && !abort_flag; it += gridDim.x) {
                 const u32 ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
+                if (it % a.m_tiles >= mt_eff) continue;
                 if (!a.stream_a) {
                     if (!mbar_wait(&a_full, a_ph, WAIT_LIMIT)) { fail(); break; }
                     a_ph ^= 1;
@@ -281,8 +288,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (u32 it = blockIdx.x; it < items && ok; it += gridDim.x) {
                 const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
+                if (mt >= mt_eff) continue;
                 const u32 q = (mt * a.n_msub + ms) * TC_ROWS + row;
-                const bool valid = q < a.nq;
+                const bool valid = q < nq_eff;
                 float4 *dst = reinterpret_cast<float4 *>(a.out + (size_t)(valid ? q : 0) * a.ld);
                 for (u32 t = t0; t < t1; t++, tcount++) {
                     const u32 b = tcount & 1;
@@ -449,10 +457,10 @@ __global__ void gt_prep_rows(Dev d, const u32 *ids, u64 next_id, u32 n_pad, bool
 
 // qstat per query: |q|^2, |q|, |lo_q|, |e_q|; copy as [hi | hi | lo]
 __global__ void gt_prep_queries(const float *q, u32 mp, u32 dim, u32 nq, u32 kp1, u32 kb, u32 *A, float *qstat,
-                                u32 *gstat) {
+                                u32 *gstat, const u32 *nq_dev = nullptr) {
     const u32 r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
-    if (r >= nq) return;
+    if (r >= (nq_dev ? min(*nq_dev, nq) : nq)) return;
     const float *qr = q + (size_t)r * mp;
     uint2 *ar = reinterpret_cast<uint2 *>(A + (size_t)r * (kb / 2));
     float sq = 0.0f, lo2 = 0.0f, e2 = 0.0f;
@@ -634,6 +642,7 @@ struct SeedSelArgs {
     u64 *seed;            // nq x L
     u32 *fb;              // queries left to the CUDA-core seed kernel
     u32 *ctr;             // [0] their count, [1] error word of the candidate pass
+    const u32 *nq_dev;    // when set, the batch size (nq is its cap)
 };
 
 // A warp per query: tau = the want-th smallest approximate key; every entry
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(SS_WARPS * 32) seed_select_kernel(Dev d, SeedS
     __shared__ u64 ckey[SS_WARPS][SS_CAP];
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const u32 qi = blockIdx.x * SS_WARPS + warp;
-    if (qi >= a.nq || a.ctr[1]) return;
+    if (qi >= (a.nq_dev ? min(*a.nq_dev, a.nq) : a.nq) || a.ctr[1]) return;
     const float *row = a.keys + (size_t)qi * a.ld;
     u32 tau = ~0u;                                   // all entries when S <= want
     if (a.S > a.want) {
@@ -940,12 +949,12 @@ cudaError_t launch_seed_tc_entries(const Dev &d, u32 S, const SeedTcPlan &p, con
 }
 
 cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u64 *seed, const SeedTcPlan &p,
-                           const SeedTcBufs &b, int num_sms, cudaStream_t st) {
+                           const SeedTcBufs &b, int num_sms, cudaStream_t st, const u32 *nq_dev) {
     if (nq == 0 || S == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(b.ctr, 0, 8 * sizeof(u32), st);
     if (e != cudaSuccess) return e;
     gt_prep_queries<<<(unsigned)(((size_t)nq * 32 + 255) / 256), 256, 0, st>>>(
-        q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<u32 *>(b.A), b.qstat, b.ctr + 4);
+        q, d.mp, d.dim, nq, p.kp1, p.kb, reinterpret_cast<u32 *>(b.A), b.qstat, b.ctr + 4, nq_dev);
     CUtensorMap ta, tb;
     if (!encode_bf16(&ta, b.A, nq, p.kb, TC_ROWS) || !encode_bf16(&tb, b.E, S, p.kb, TC_ACC))
         return cudaErrorInvalidValue;
@@ -971,6 +980,7 @@ cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u
     a.chunks = (a.n_tiles + a.tiles_per_chunk - 1) / a.tiles_per_chunk;
     a.stages = p.stages;
     a.stream_a = p.stream_a ? 1u : 0u;
+    a.nq_dev = nq_dev;
     a.all_keys = 1;
     a.ld = p.s_pad;
     a.s = d.metric == 0 ? -2.0f : -1.0f;
@@ -998,6 +1008,7 @@ cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u
     r.seed = seed;
     r.fb = b.fb;
     r.ctr = b.ctr;
+    r.nq_dev = nq_dev;
     seed_select_kernel<<<(nq + SS_WARPS - 1) / SS_WARPS, SS_WARPS * 32, 0, st>>>(d, r);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

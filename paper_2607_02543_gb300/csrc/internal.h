@@ -164,7 +164,7 @@ SeedTcPlan seed_tc_plan(u32 dim, u32 n_entry, u32 nq);
 cudaError_t launch_seed_tc_entries(const Dev &d, u32 S, const SeedTcPlan &p, const SeedTcBufs &b, cudaStream_t st);
 // Exact top-L of the S entries for each query (same result as launch_seed with fp32 rows).
 cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u64 *seed, const SeedTcPlan &p,
-                           const SeedTcBufs &b, int num_sms, cudaStream_t st);
+                           const SeedTcBufs &b, int num_sms, cudaStream_t st, const u32 *nq_dev = nullptr);
 GtTcPlan gt_tc_plan(u32 dim, u64 next_id, u32 nq);
 cudaError_t launch_gt_tc_prep(const Dev &d, u64 next_id, const float *q, u32 nq, const GtTcPlan &p,
                               const GtTcBufs &b, cudaStream_t st);

@@ -108,3 +108,34 @@ def test_writer_share_does_not_change_results():
         out.append(g.export_graph())
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_graph_with_tensor_seeds_at_960_dims():
+    """A query graph on a 960-d index seeds on tensor cores (the query tile
+    streamed through the copy ring, the batch size read on the device) and
+    returns what etale_search returns for every batch size."""
+    import torch
+    from paper_2607_02543_gb300 import Index
+    w = W.scaled(W.GIST_LIKE_1M, 2000, n_queries=256, rounds=1)
+    plan = W.make_plan(w)
+    dev = torch.device("cuda", 0)
+    g = Index(w.dim, w.metric, w.degree, w.capacity, build_beam=32, n_entry=256, mode="deterministic")
+    g.insert(plan.base)
+    nq_max, k, beam = 256, 10, 48
+    qbuf = torch.zeros((nq_max, w.dim), dtype=torch.float32, device=dev)
+    oid = torch.empty((nq_max, k), dtype=torch.int32, device=dev)
+    od = torch.empty((nq_max, k), dtype=torch.float32, device=dev)
+    nq = torch.zeros(1, dtype=torch.int32, device=dev)
+    graph = g.search_graph(qbuf, oid, od, nq, k, beam)
+    stream = torch.cuda.Stream()
+    for n in (1, 40, 129, 256):
+        qbuf[:n] = torch.from_numpy(plan.queries[:n]).to(dev)
+        nq.fill_(n)
+        torch.cuda.synchronize()
+        graph.launch(stream)
+        graph.check(stream)
+        ref_ids, ref_d = g.search(plan.queries[:n], k, beam)
+        assert (oid[:n].cpu().numpy().view(np.uint32) == ref_ids).all(), n
+        assert np.array_equal(od[:n].cpu().numpy().view(np.uint32), ref_d.view(np.uint32)), n
+    graph.close()
+    g.close()
