@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--exact-steps", type=int, default=2,
                     help="extra rounds timed with fp32 BeamSearches gathering the BF16 copy, which holds every "
                          "row of the integer-valued workload exactly (0: skip); reported apart from the headline")
+    ap.add_argument("--no-max-cand-default", action="store_true",
+                    help="skip the block that reruns the headline workload at the library's default max_cand")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="rounds after the timed ones with the library's phase events on (phase times, "
                          "writer-kernel rooflines); the timed rounds run without them")
@@ -353,6 +355,67 @@ def precision_sweep(idx, d_q, gt_np, plan, w, stream, out_ids, out_d) -> dict:
                      "qps": len(plan.queries) / (best * 1e-3), "max_rel_dist_err_vs_fp64": err}
     idx.set_search_precision("fp32")
     return out
+
+
+def max_cand_block(args, stream, rounds: int = 5) -> dict:
+    """The headline workload at the library's default candidate cap (max_cand
+    = 2 x build beam = 256, the paper's whole visited set up to that cap)
+    instead of the headline's 64: build time, ms per 1% churn round (eager
+    calls, CUDA events, mean of `rounds` after one warm-up round), the
+    smallest beam reaching Recall@10 >= 0.95 + margin on the built index, its
+    query-batch QPS, and Recall@10 at that beam after the rounds."""
+    import torch
+    from paper_2607_02543_gb300 import Index
+    w = W.SIFT_LIKE_1M if not args.n_live else W.scaled(W.SIFT_LIKE_1M, args.n_live)
+    wr = W.dataclasses.replace(w, rounds=1 + rounds)
+    plan = W.make_plan(wr)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    idx = Index(w.dim, w.metric, w.degree, wr.capacity, build_beam=w.build_beam, mode=args.mode,
+                n_entry=args.n_entry, max_cand=0)
+    t0 = time.perf_counter()
+    idx.insert(torch.from_numpy(plan.base).to(dev), stream)
+    idx.reclaim(stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    d_q = torch.from_numpy(plan.queries).to(dev)
+    beam, _ = idx.autotune_beam(d_q, w.k, 0.95 + args.recall_margin, stream=stream)
+    rng = np.random.default_rng(w.seed + 7)
+    alive = np.zeros(wr.capacity, bool)
+    alive[:w.n_base] = True
+    nxt = w.n_base
+    ms = []
+    for r in range(1 + rounds):
+        dele = W.choose_deletes(rng, np.nonzero(alive)[0].astype(np.uint32), w.n_delete)
+        d_del = torch.from_numpy(dele.view(np.int32)).to(dev)
+        d_ins = torch.from_numpy(plan.inserts[r]).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        idx.delete(d_del, stream)
+        idx.insert(d_ins, stream)
+        idx.reclaim(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            ms.append(e0.elapsed_time(e1))
+        alive[dele] = False
+        alive[nxt:nxt + w.n_insert] = True
+        nxt += w.n_insert
+    gt, _ = idx.ground_truth(d_q, w.k, stream)
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ids, _ = idx.search(d_q, w.k, beam, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    got, g = ids.cpu().numpy().view(np.uint32), gt.cpu().numpy().view(np.uint32)
+    rec = float(np.mean([len(set(a.tolist()) & set(b.tolist())) / w.k for a, b in zip(got, g)]))
+    idx.close()
+    torch.cuda.empty_cache()
+    return {"max_cand": 2 * w.build_beam, "build_s": build_s, "rounds": rounds, "ms_per_round": float(np.mean(ms)),
+            "search_beam": beam, "qps": w.n_queries / (best * 1e-3), "recall_at_10_after": rec,
+            "path": "eager calls"}
 
 
 def precision_forms(args, stream, forms=("fp32", "bf16", "fp8")) -> dict:
@@ -1191,6 +1254,12 @@ def main():
             idx.close()
         torch.cuda.empty_cache()
         prec_block = precision_forms(args, stream, tuple(f for f in args.forms.split(",") if f))
+    # the same workload at the library's default candidate cap (its own index)
+    mc_block = None
+    if rank == 0 and world == 1 and args.workload == "int256-1m-d128" and not args.no_max_cand_default:
+        idx.close()                      # idempotent: the blocks above may have released it
+        torch.cuda.empty_cache()
+        mc_block = max_cand_block(args, stream)
     if rank == 0:
         out = {"metric": "ms per 1% churn round", "value": ms_round, "unit": "ms", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
@@ -1216,6 +1285,7 @@ def main():
                                   "events on; search_query and seed_query: the timed steps' query batches",
                "writer_rooflines": writers, "ground_truth": gt_block, "search_tuning": tuning,
                "precision": prec_block, "exact_bf16_rows": exact_block, "eager_calls": eager_block,
+               "max_cand_default": mc_block,
                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                "stats": {k: st[k] for k in ("live", "used_slabs", "n_cas_retry", "n_dropped", "n_publish")}}
         print(json.dumps(out), flush=True)
