@@ -1404,15 +1404,40 @@ __global__ void __launch_bounds__(128, 1) repair_k_kernel(RepairKArgs a) {
             y = yy;
             x = q - yy * (yy - 1) / 2;
         };
-        for (int q0 = 0; q0 < npair; q0 += 8) {
-            const int q = q0 + grp, q2 = q + 4;
-            int x, y, x2, y2;
-            pair_of(q < npair ? q : npair - 1, x, y);
-            pair_of(q2 < npair ? q2 : npair - 1, x2, y2);
-            const float dd = canon_dist<8>(brow(x), brow(y), (int)d.mp, (int)d.metric, g);
-            const float dd2 = canon_dist<8>(brow(x2), brow(y2), (int)d.mp, (int)d.metric, g);
-            if (q < npair && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
-            if (q2 < npair && g == 0) { M[x2 * R + y2] = dd2; M[y2 * R + x2] = dd2; }
+        if (d.mp <= 128) {
+            // rows of at most 128 floats: each lane's four float4 of both rows
+            // of a pair in registers, so the canonical distance runs with no
+            // column loop; each group's pair cursor steps by 8 in the same
+            // sequence instead of recomputing it with a square root
+            int x = 0, y = 1, x2 = 0, y2 = 1;
+            if (grp < npair) pair_of(grp, x, y);
+            if (grp + 4 < npair) pair_of(grp + 4, x2, y2);
+            for (int q0 = 0; q0 < npair; q0 += 8) {
+                const int q = q0 + grp, q2 = q + 4;
+                const bool v1 = q < npair, v2 = q2 < npair;
+                float4 ra[4], rb[4], rc[4], rd[4];
+                canon_row_q8(brow(v1 ? x : 0), (int)d.mp, g, ra);
+                canon_row_q8(brow(v1 ? y : 1), (int)d.mp, g, rb);
+                canon_row_q8(brow(v2 ? x2 : 0), (int)d.mp, g, rc);
+                canon_row_q8(brow(v2 ? y2 : 1), (int)d.mp, g, rd);
+                const float dd = canon_dist_q8v(ra, rb, (int)d.mp, (int)d.metric, g);
+                const float dd2 = canon_dist_q8v(rc, rd, (int)d.mp, (int)d.metric, g);
+                if (v1 && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
+                if (v2 && g == 0) { M[x2 * R + y2] = dd2; M[y2 * R + x2] = dd2; }
+                for (x += 8; x >= y; y++) x -= y;
+                for (x2 += 8; x2 >= y2; y2++) x2 -= y2;
+            }
+        } else {
+            for (int q0 = 0; q0 < npair; q0 += 8) {
+                const int q = q0 + grp, q2 = q + 4;
+                int x, y, x2, y2;
+                pair_of(q < npair ? q : npair - 1, x, y);
+                pair_of(q2 < npair ? q2 : npair - 1, x2, y2);
+                const float dd = canon_dist<8>(brow(x), brow(y), (int)d.mp, (int)d.metric, g);
+                const float dd2 = canon_dist<8>(brow(x2), brow(y2), (int)d.mp, (int)d.metric, g);
+                if (q < npair && g == 0) { M[x * R + y] = dd; M[y * R + x] = dd; }
+                if (q2 < npair && g == 0) { M[x2 * R + y2] = dd2; M[y2 * R + x2] = dd2; }
+            }
         }
         __syncwarp();
         // K(u, a) for every a in B, one lane per a: the candidates b != a, live,
