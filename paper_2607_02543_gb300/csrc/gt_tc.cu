@@ -65,7 +65,7 @@ __host__ __device__ constexpr u32 tc_idesc(u32 n) {
 struct TcArgs {
     u32 nq, n_tiles, kblocks, n_msub, bn, m_tiles, chunks, tiles_per_chunk, stages;
     u32 all_keys;         // 0: smallest key per block of 32 rows; 1: every key
-    u32 stream_a;         // 1: the query boxes travel through the ring with the row boxes
+    u32 stream_a;         // 1: the query boxes travel through the ring (selects gt_tc_kernel<true>)
     const u32 *nq_dev;    // when set, the batch size is read here (nq is its cap); later query tiles are skipped
     u32 ld;               // row length of the output (blocks or keys)
     float s;              // -2 (L2) or -1 (IP)
@@ -114,6 +114,9 @@ __device__ __forceinline__ void tmem_ld64(u32 taddr, u32 *r) {
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---- candidate pass ---------------------------------------------------------
+// STREAM_A: the query boxes travel through the ring with the row boxes (a
+// compile-time choice, so the resident form's MMA issue loop carries no test).
+template <bool STREAM_A>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gt_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     extern __shared__ unsigned char tc_raw[];
@@ -134,9 +137,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ring of row boxes; streamed: each ring stage is a row box followed by
     // the n_msub query boxes of the same 64 columns
     const u32 abox = a.n_msub * TC_BOX;
-    const u32 sbytes = bbox + (a.stream_a ? abox : 0u);
+    const u32 sbytes = bbox + (STREAM_A ? abox : 0u);
     unsigned char *sA = sm;
-    unsigned char *sB = sm + (a.stream_a ? 0u : (size_t)a.kblocks * abox);
+    unsigned char *sB = sm + (STREAM_A ? 0u : (size_t)a.kblocks * abox);
 
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < a.stages; i++) {
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const u32 mt = it % a.m_tiles, ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
                 if (mt >= mt_eff) continue;
-                if (!a.stream_a) {
+                if (!STREAM_A) {
                     if (!first) {
                         if (!mbar_wait(&a_empty, a_ph, WAIT_LIMIT)) { fail(); break; }
                         a_ph ^= 1;
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         unsigned char *sb = sB + (size_t)stage * sbytes;
                         mbar_expect_tx(&full[stage], sbytes);
                         tma_load_2d(sb, &tmB, (int)(kb * TC_KBOX), (int)(t * a.bn), &full[stage]);
-                        if (a.stream_a)
+                        if (STREAM_A)
                             for (u32 s = 0; s < a.n_msub; s++)
                                 tma_load_2d(sb + bbox + (size_t)s * TC_BOX, &tmA, (int)(kb * TC_KBOX),
                                             (int)((mt * a.n_msub + s) * TC_ROWS), &full[stage]);
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const u32 ch = it / a.m_tiles;
                 const u32 t0 = ch * a.tiles_per_chunk, t1 = min(a.n_tiles, t0 + a.tiles_per_chunk);
                 if (it % a.m_tiles >= mt_eff) continue;
-                if (!a.stream_a) {
+                if (!STREAM_A) {
                     if (!mbar_wait(&a_full, a_ph, WAIT_LIMIT)) { fail(); break; }
                     a_ph ^= 1;
                     tc_fence_after();
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         for (u32 k = 0; k < TC_KBOX / 16; k++) {
                             const u64 bd = sw128_desc(bb + k * 32);
                             for (u32 s = 0; s < a.n_msub; s++) {
-                                const u32 aa = (a.stream_a ? bb + bbox + s * TC_BOX
+                                const u32 aa = (STREAM_A ? bb + bbox + s * TC_BOX
                                                            : smem_addr(sA + (size_t)(s * a.kblocks + kb) * TC_BOX)) +
                                                k * 32;
                                 tc_mma(tmem + b * TC_ACC + s * TC_ROWS, sw128_desc(aa), bd, idesc, (kb | k) != 0);
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         break;
                     }
                 }
-                if (!a.stream_a) tc_commit(&a_empty);
+                if (!STREAM_A) tc_commit(&a_empty);
             }
             // all MMAs and key-base copies issued by this thread are complete
             // before TMEM and shared memory are released
@@ -882,11 +885,13 @@ cudaError_t launch_gt_tc(const Dev &d, u32 q0, u32 nq, const GtTcPlan &p, const 
     a.xn = b.xn;
     a.out = b.bmin;
     a.err = b.err;
-    cudaError_t e = smem_at_least((const void *)gt_tc_kernel, p.smem);
+    const void *fn = p.stream_a ? (const void *)gt_tc_kernel<true> : (const void *)gt_tc_kernel<false>;
+    cudaError_t e = smem_at_least(fn, p.smem);
     if (e != cudaSuccess) return e;
     const u32 items = a.m_tiles * a.chunks;
     const u32 grid = std::min<u32>(items, (u32)num_sms);
-    gt_tc_kernel<<<grid, TC_THREADS, p.smem, st>>>(ta, tb, a);
+    if (p.stream_a) gt_tc_kernel<true><<<grid, TC_THREADS, p.smem, st>>>(ta, tb, a);
+    else gt_tc_kernel<false><<<grid, TC_THREADS, p.smem, st>>>(ta, tb, a);
     return cudaGetLastError();
 }
 
@@ -987,10 +992,12 @@ cudaError_t launch_seed_tc(const Dev &d, const float *q, u32 nq, u32 S, u32 L, u
     a.xn = b.en;
     a.out = b.keys;
     a.err = b.ctr + 1;
-    e = smem_at_least((const void *)gt_tc_kernel, p.smem);
+    const void *fn = p.stream_a ? (const void *)gt_tc_kernel<true> : (const void *)gt_tc_kernel<false>;
+    e = smem_at_least(fn, p.smem);
     if (e != cudaSuccess) return e;
     const u32 items = a.m_tiles * a.chunks;
-    gt_tc_kernel<<<std::min<u32>(items, (u32)num_sms), TC_THREADS, p.smem, st>>>(ta, tb, a);
+    if (p.stream_a) gt_tc_kernel<true><<<std::min<u32>(items, (u32)num_sms), TC_THREADS, p.smem, st>>>(ta, tb, a);
+    else gt_tc_kernel<false><<<std::min<u32>(items, (u32)num_sms), TC_THREADS, p.smem, st>>>(ta, tb, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SeedSelArgs r{};

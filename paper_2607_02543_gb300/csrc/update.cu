@@ -650,13 +650,29 @@ __device__ int warp_prune(const Dev &d, const u64 *ck, int n, unsigned char *ali
         }
         __syncwarp();
         const float *hrow = row(head);
-        for (int r0 = 0; r0 < m_cnt; r0 += 4) {
-            const int c = r0 + grp;
-            const int cc = c < m_cnt ? c : m_cnt - 1;
-            const u32 j = idx[cc];
-            const u64 kj = ck[j];
-            float dd = canon_dist<8>(hrow, row((int)j), (int)d.mp, (int)d.metric, g);
-            if (c < m_cnt && g == 0 && __fmul_rn(d.alpha2, dd) <= key_rho(kj)) alive[j] = 0;
+        if (d.mp <= 128) {
+            // the head's four float4 per lane stay in registers
+            float4 hr[4];
+            canon_row_q8(hrow, (int)d.mp, g, hr);
+            for (int r0 = 0; r0 < m_cnt; r0 += 4) {
+                const int c = r0 + grp;
+                const int cc = c < m_cnt ? c : m_cnt - 1;
+                const u32 j = idx[cc];
+                const u64 kj = ck[j];
+                float4 v[4];
+                canon_row_q8(row((int)j), (int)d.mp, g, v);
+                const float dd = canon_dist_q8v(hr, v, (int)d.mp, (int)d.metric, g);
+                if (c < m_cnt && g == 0 && __fmul_rn(d.alpha2, dd) <= key_rho(kj)) alive[j] = 0;
+            }
+        } else {
+            for (int r0 = 0; r0 < m_cnt; r0 += 4) {
+                const int c = r0 + grp;
+                const int cc = c < m_cnt ? c : m_cnt - 1;
+                const u32 j = idx[cc];
+                const u64 kj = ck[j];
+                float dd = canon_dist<8>(hrow, row((int)j), (int)d.mp, (int)d.metric, g);
+                if (c < m_cnt && g == 0 && __fmul_rn(d.alpha2, dd) <= key_rho(kj)) alive[j] = 0;
+            }
         }
         __syncwarp();
         start = head + 1;
@@ -1179,12 +1195,27 @@ __global__ void __launch_bounds__(64, GV == 1 ? 1 : 6) refine_kernel(RefineArgs 
         st.wk_rows += (u64)(nu + 1) * 4 * d.mp;   // v's row and the peers'
         st.wk_state += 8ull * ((a.mode != 2 ? nu : 0) + dv);   // liveness words
         const float *vrow = d.x + (size_t)v * d.mp;
-        for (int r0 = 0; r0 < nu; r0 += 4) {
-            const int c = r0 + grp;
-            const int cc = c < nu ? c : nu - 1;
-            const u32 y = uid[cc];
-            float dd = canon_dist<8>(vrow, d.x + (size_t)y * d.mp, (int)d.mp, (int)d.metric, g);
-            if (c < nu && g == 0) buf[c] = mkkey(dd, y);
+        if (d.mp <= 128) {
+            // v's four float4 per lane stay in registers
+            float4 vr[4];
+            canon_row_q8(vrow, (int)d.mp, g, vr);
+            for (int r0 = 0; r0 < nu; r0 += 4) {
+                const int c = r0 + grp;
+                const int cc = c < nu ? c : nu - 1;
+                const u32 y = uid[cc];
+                float4 w4[4];
+                canon_row_q8(d.x + (size_t)y * d.mp, (int)d.mp, g, w4);
+                const float dd = canon_dist_q8v(vr, w4, (int)d.mp, (int)d.metric, g);
+                if (c < nu && g == 0) buf[c] = mkkey(dd, y);
+            }
+        } else {
+            for (int r0 = 0; r0 < nu; r0 += 4) {
+                const int c = r0 + grp;
+                const int cc = c < nu ? c : nu - 1;
+                const u32 y = uid[cc];
+                float dd = canon_dist<8>(vrow, d.x + (size_t)y * d.mp, (int)d.mp, (int)d.metric, g);
+                if (c < nu && g == 0) buf[c] = mkkey(dd, y);
+            }
         }
         __syncwarp();
         int nc = nu;
