@@ -322,9 +322,7 @@ __device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L, int &lo) 
             k2 = bk[i];
             r2 = s.bref[i];
             f2 = s.bflag[i];
-            int cnt = 0;
-            for (int j = 0; j < c; j++) cnt += (s.nkey[j] < k2);
-            pos = i + cnt;
+            pos = i + lower_bound(s.nkey, c, k2);   // new keys below it (sorted, distinct)
         }
         __syncwarp();
         if (pos < L) { s.bkey[pos] = k2; s.bref[pos] = r2; s.bflag[pos] = f2; }
