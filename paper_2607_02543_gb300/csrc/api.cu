@@ -87,6 +87,7 @@ struct etale_index {
     u32 *free_stack = nullptr, *retired = nullptr, *entries = nullptr;
     u64 *ctr = nullptr;
     unsigned short *xb = nullptr;   // bf16 copy
+    float *xbn = nullptr;           // squared norms of the bf16 copy's rows
     unsigned char *x8 = nullptr;    // fp8 copy
     float *x8s = nullptr;
     u32 mb = 0, m8 = 0;
@@ -159,7 +160,7 @@ struct etale_index {
         d.entries = entries; d.dim = dim; d.mp = mp; d.R = R; d.metric = metric; d.alpha2 = alpha2;
         d.n_entries = n_entries.load(std::memory_order_relaxed); d.capacity = capacity; d.pool = pool; d.stage_bytes = cfg.stage_kb << 10;
         d.gram = cfg.gram == 2 ? 1u : 0u;
-        d.xb = xb; d.x8 = x8; d.x8s = x8s; d.mb = mb; d.m8 = m8;
+        d.xb = xb; d.xbn = xbn; d.x8 = x8; d.x8s = x8s; d.mb = mb; d.m8 = m8;
         // warps pop 8 free slabs at a time when the free pool covers every
         // resident warp's batch many times over (else one, as Algorithm 1)
         d.slab_batch = free_lb >= (u64)num_sms * 64 * 8 * 2 ? 8u : 1u;
@@ -506,17 +507,21 @@ SearchTuning fit_tuning(const etale_index *idx, u32 L, SearchTuning t) {
 
 // Seeds of nq BeamSearches (top-L of the entry set): tensor cores with a
 // certified exact rerank when they apply, else the CUDA-core kernel; both
-// give the same seeds.  Returns the launches made.
+// give the same seeds.  The tensor path ranks by the canonical fp32 distance
+// also for a reduced-precision search (*fp32_keys = true): that search then
+// re-keys its seeds in its own precision (launch_search's rekey).
 static etale_status seed_batch(etale_index *idx, const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, u32 prec,
-                               cudaStream_t st, int sms = 0) {
+                               cudaStream_t st, int sms = 0, bool *fp32_keys = nullptr) {
     const u32 S = idx->n_entries;
-    if (prec == 0 && idx->seed_tc && !idx->concurrent && S > 0 && nq >= 32) {
+    if (fp32_keys) *fp32_keys = false;
+    if ((prec == 0 || fp32_keys) && idx->seed_tc && !idx->concurrent && S > 0 && nq >= 32) {
         const SeedTcPlan p = seed_tc_plan(idx->dim, S, nq);
         if (!grow(idx->sd_A, p.bytes_A) || !grow(idx->sd_qstat, (size_t)nq * 16) ||
             !grow(idx->sd_keys, p.bytes_keys) || !grow(idx->sd_fb, (size_t)nq * 4) || !grow(idx->sd_ctr, 64))
             return idx->fail(ETALE_ENOMEM, "seed staging");
         CK(launch_seed_tc(d, q, nq, S, L, seed, p, idx->seed_bufs(), sms ? sms : idx->num_sms, st), "seed (tensor)");
         g_kernel_launches += 4;
+        if (fp32_keys) *fp32_keys = prec != 0;
         return ETALE_OK;
     }
     CK(launch_seed(d, q, nq, L, seed, st, prec), "seed");
@@ -534,17 +539,19 @@ etale_status insert_subbatch(etale_index *idx, u32 first, u32 b, cudaStream_t st
               as<u32>(idx->of_src), as<float>(idx->of_rho), slots};
     // 1. BeamSearch of every member on the graph before the sub-batch
     if (!grow(idx->seed, (size_t)b * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
+    bool rekey = false;
     {
         PhaseScope ps(idx, ETALE_PH_SEED, st);
         etale_status s0 = seed_batch(idx, d, idx->x + (size_t)first * idx->mp, b, L, as<u64>(idx->seed),
-                                     idx->insert_prec, st, idx->writer_sms);
+                                     idx->insert_prec, st, idx->writer_sms, &rekey);
         if (s0 != ETALE_OK) return s0;
     }
     {
         PhaseScope ps(idx, ETALE_PH_SEARCH_INSERT, st);
         CK(launch_search(d, idx->x + (size_t)first * idx->mp, b, L, H, 1, 0, nullptr, nullptr,
                          as<u64>(idx->exp_keys), as<u32>(idx->exp_count), as<u64>(idx->seed), fit_tuning(idx, L, idx->tune),
-                         idx->writer_sms, st, idx->insert_prec, 4, nullptr, idx->insert_prec == 0 && exact_rows(idx)),
+                         idx->writer_sms, st, idx->insert_prec, 4, nullptr, idx->insert_prec == 0 && exact_rows(idx),
+                         nullptr, nullptr, 0, rekey),
            "insert search");
     }
     g_kernel_launches += 1;
@@ -728,7 +735,9 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
               cudaEventCreateWithFlags(&idx->graph_ev, cudaEventDisableTiming) == cudaSuccess;
     idx->mb = (idx->mp + 7) / 8 * 8;
     idx->m8 = (idx->mp + 15) / 16 * 16;
-    if (ok && (cfg.copies & 1)) ok = cudaMalloc(&idx->xb, (size_t)capacity * idx->mb * 2) == cudaSuccess;
+    if (ok && (cfg.copies & 1))
+        ok = cudaMalloc(&idx->xb, (size_t)capacity * idx->mb * 2) == cudaSuccess &&
+             cudaMalloc(&idx->xbn, (size_t)capacity * 4) == cudaSuccess;
     if (ok && (cfg.copies & 2))
         ok = cudaMalloc(&idx->x8, (size_t)capacity * idx->m8) == cudaSuccess &&
              cudaMalloc(&idx->x8s, (size_t)capacity * 4) == cudaSuccess;
@@ -738,7 +747,7 @@ etale_status etale_create(uint32_t dim, etale_metric metric, uint32_t degree, ui
         etale_destroy(idx);
         return ETALE_ENOMEM;
     }
-    idx->device_bytes = xb + rb + sb + 2 * pb + (idx->xb ? (size_t)capacity * idx->mb * 2 : 0) +
+    idx->device_bytes = xb + rb + sb + 2 * pb + (idx->xb ? (size_t)capacity * (idx->mb * 2 + 4) : 0) +
                         (idx->x8 ? (size_t)capacity * (idx->m8 + 4) : 0);
     // refs <- <0, 0, NIL>; free stack <- all slabs; counters
     std::vector<u64> ctr(C_NCTR, 0);
@@ -778,7 +787,7 @@ etale_status etale_destroy(etale_index *idx) {
     }
     cudaFree(idx->x); cudaFree(idx->ref); cudaFree(idx->slab); cudaFree(idx->free_stack);
     cudaFree(idx->retired); cudaFree(idx->ctr); cudaFree(idx->entries);
-    cudaFree(idx->xb); cudaFree(idx->x8); cudaFree(idx->x8s); cudaFree(idx->nent_dev); cudaFree(idx->rs);
+    cudaFree(idx->xb); cudaFree(idx->xbn); cudaFree(idx->x8); cudaFree(idx->x8s); cudaFree(idx->nent_dev); cudaFree(idx->rs);
     if (idx->graph_ev) cudaEventDestroy(idx->graph_ev);
     if (idx->host_ctr) cudaFreeHost(idx->host_ctr);
     if (idx->host_ctr_s) cudaFreeHost(idx->host_ctr_s);
@@ -1113,13 +1122,14 @@ static etale_status search_common(etale_index *idx, const float *queries, uint64
         const u32 H = idx->cfg.max_hops ? idx->cfg.max_hops : 4 * L;
         if (!grow(idx->s_seed, (size_t)nq * L * 8)) return idx->fail(ETALE_ENOMEM, "seed buffer");
         if (prof) prof_begin(idx, ETALE_PH_SEED, st);
-        s = seed_batch(idx, d, qpad, (u32)nq, L, as<u64>(idx->s_seed), idx->search_prec, st);
+        bool rekey = false;
+        s = seed_batch(idx, d, qpad, (u32)nq, L, as<u64>(idx->s_seed), idx->search_prec, st, 0, &rekey);
         if (prof) prof_end(idx, st);
         if (s != ETALE_OK) return s;
         if (prof) prof_begin(idx, ETALE_PH_SEARCH_QUERY, st);
         CK(launch_search(d, qpad, (u32)nq, L, H, 0, k, oid, od, nullptr, nullptr, as<u64>(idx->s_seed), fit_tuning(idx, L, idx->tune),
                          idx->num_sms, st, idx->search_prec, idx->cfg.rerank, nullptr,
-                         idx->search_prec == 0 && exact_rows(idx)),
+                         idx->search_prec == 0 && exact_rows(idx), nullptr, nullptr, 0, rekey),
            "search");
         if (prof) prof_end(idx, st);
         g_kernel_launches++;

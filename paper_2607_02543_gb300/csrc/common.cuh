@@ -123,6 +123,7 @@ struct Dev {
     u32 gram;          // 1: domination tests of small prunes use the tensor-core Gram tile
     // reduced-precision copies (query search only)
     unsigned short *xb;  // C x mb bf16 bits (nullptr if not kept)
+    float *xbn;          // C: |bf16 row|^2, for the tensor-core keys of BF16 searches
     unsigned char *x8;   // C x m8 e4m3 codes (nullptr if not kept)
     float *x8s;          // C per-vector scales
     u32 mb, m8;          // row strides in elements (16-byte rows)
@@ -436,6 +437,25 @@ __device__ __forceinline__ bool warp_publish(const Dev &d, WarpSlabs &ws, u32 u,
 
 __device__ __forceinline__ u64 ld_ref(const Dev &d, u32 id) {
     return *reinterpret_cast<volatile const u64 *>(d.ref + id);
+}
+
+// ---- warp-level bf16 tensor-core helpers (mma.sync m16n8k16, fp32 accumulation) ----
+__device__ __forceinline__ void ldsm_x4(u32 &r0, u32 &r1, u32 &r2, u32 &r3, u32 addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16_16816(float *c, u32 a0, u32 a1, u32 a2, u32 a3, u32 b0, u32 b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
+    u32 r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 // ---- bulk (TMA, non-tensor) copies into shared memory with an mbarrier -----

@@ -33,7 +33,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec = 0,
                           u32 rerank = 4, const u32 *nq_dev = nullptr, bool exact_rows = false,
-                          u32 *elog = nullptr, u32 *elog_n = nullptr, u32 elog_cap = 0);
+                          u32 *elog = nullptr, u32 *elog_n = nullptr, u32 elog_cap = 0, bool rekey = false);
 // Serving ring (a bounded persistent search launch over host-mapped slots):
 // rows / out_ids / out_dist / tail / closed / done / served_by are device
 // views of host-mapped memory; head and seed are device memory.

@@ -44,6 +44,9 @@ struct SearchArgs {
                          // use their own, so they can overlap a writer)
     u32 rerank;          // reduced precision: re-scored candidates (<= 64)
     u32 exact;           // P = 1 over a bf16 copy that holds every row exactly: no rerank
+    u32 rekey;           // P != 0 with seeds ranked in fp32: re-key them in P and re-sort
+    u32 tc;              // P = 1 reduced-precision search: keys from tensor-core dot products (tc_keys)
+    u32 srow;            // stage row stride in bytes (rowb, or padded for the tensor-core path)
     u32 *elog;           // diagnostic (LOG kernels): per query, the ids evaluated during
     u32 *elog_n;         //   expansions in order (elog_cap slots) and their count
     u32 elog_cap;
@@ -177,7 +180,8 @@ struct WarpSmem {
     u64 *ckey;       // 32
     u64 *cref;       // 32
     u32 *seen;       // seen_slots
-    u64 *bar;        // mbarrier
+    u64 *bar;        // mbarrier; with tensor-core keys, |bf16(q)|^2 (bar + 16 bytes) and
+                     // the query as bf16 pairs (bar + 32 bytes) follow it (tc_nq, tc_qb)
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -208,22 +212,26 @@ inline SeenLayout seen_layout(u64 capacity, u32 bits) {
     return l;
 }
 
-__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, size_t seen_bytes, u32 rowb) {
+// srow: stage row stride in bytes; qbytes: the bf16 query of the tensor-core keys (or 0)
+__host__ __device__ inline size_t search_warp_bytes(u32 mp, u32 L, u32 stage_rows, size_t seen_bytes, u32 srow,
+                                                   u32 qbytes = 0) {
     size_t b = 0;
     b += align_up((size_t)mp * 4, 128);
-    b += align_up((size_t)stage_rows * rowb, 128);
+    b += align_up((size_t)stage_rows * srow, 128);
     b += 2 * align_up((size_t)L * 8, 16);
     b += align_up((size_t)L, 16);
     b += 32 * 8 * 2 + 32 * 4 + 32 * 8 * 2;
     b += align_up(seen_bytes, 16);
     b += 16;
+    if (qbytes) b += 16 + align_up(qbytes, 16);
     return align_up(b, 128);
 }
 
-__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, size_t seen_bytes, u32 rowb) {
+__device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, size_t seen_bytes, u32 srow,
+                                 u32 qbytes = 0) {
     WarpSmem s;
     s.qv = reinterpret_cast<float *>(p); p += align_up((size_t)mp * 4, 128);
-    s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * rowb, 128);
+    s.stage = reinterpret_cast<float *>(p); p += align_up((size_t)stage_rows * srow, 128);
     s.bkey = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     s.bref = reinterpret_cast<u64 *>(p); p += align_up((size_t)L * 8, 16);
     s.bflag = reinterpret_cast<unsigned char *>(p); p += align_up((size_t)L, 16);
@@ -234,7 +242,16 @@ __device__ inline WarpSmem carve(char *p, u32 mp, u32 L, u32 stage_rows, size_t 
     s.cid = reinterpret_cast<u32 *>(p); p += 32 * 4;
     s.seen = reinterpret_cast<u32 *>(p); p += align_up(seen_bytes, 16);
     s.bar = reinterpret_cast<u64 *>(p);
+    (void)qbytes;
     return s;
+}
+
+// The tensor-core keys' query data, laid out after the mbarrier.
+__device__ __forceinline__ float *tc_nq(const WarpSmem &s) {
+    return reinterpret_cast<float *>(reinterpret_cast<char *>(s.bar) + 16);
+}
+__device__ __forceinline__ u32 *tc_qb(const WarpSmem &s) {
+    return reinterpret_cast<u32 *>(reinterpret_cast<char *>(s.bar) + 32);
 }
 
 __device__ __forceinline__ u32 seen_slot(u32 id, u32 bits) { return (id * 2654435761u) >> (32 - bits); }
@@ -336,6 +353,86 @@ __device__ int merge_beam(WarpSmem &s, u64 key, u64 ref, int n, int L, int &lo) 
     return min(L, n + c);
 }
 
+// Tensor-core keys of a reduced-precision BF16 search.  The dot products of
+// the bf16 query (s.qb) with the nb <= 32 rows staged at stride a.srow come
+// from mma.sync m16n8k16: the query is row 0 of the 16-row A operand, eight
+// staged rows at a time are the B operand, read with ldmatrix.  The key is
+// |q|^2 + |x|^2 - 2 q.x over the bf16 values (squared L2) or 1 - q.x (inner
+// product).  It is one function of (query, id) wherever a key is made in the
+// search (neighbours, seeds), so an id evaluated twice has one key.
+__device__ void tc_keys(const SearchArgs &a, const WarpSmem &s, int nb, const u32 *ids, u64 *keys) {
+    const Dev &d = a.d;
+    const int lane = lane_id(), g = lane >> 2, t = lane & 3;
+    const u32 sb = smem_addr(s.stage);
+    const u32 *qb = tc_qb(s);
+    const int ntn = (nb + 7) >> 3;
+    const u32 r = lane & 7, mi = lane >> 3;   // the row and the matrix whose address this lane gives
+    float acc[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[nt][c] = 0.0f;
+    for (u32 k0 = 0; k0 < d.mb; k0 += 32) {
+        // two k-steps of 16; A is zero outside row 0 (lanes 0..3)
+        u32 q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+        if (g == 0) {
+            q0 = qb[(k0 >> 1) + t];
+            q1 = qb[(k0 >> 1) + 4 + t];
+            q2 = qb[(k0 >> 1) + 8 + t];
+            q3 = qb[(k0 >> 1) + 12 + t];
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            if (nt < ntn) {
+                u32 row = (u32)nt * 8 + r;
+                if ((int)row >= nb) row = 0;   // a staged row; its products are not read
+                u32 b0, b1, b2, b3;
+                ldsm_x4(b0, b1, b2, b3, sb + row * a.srow + (k0 + 8 * mi) * 2);
+                mma_bf16_16816(acc[nt], q0, 0u, q1, 0u, b0, b1);
+                mma_bf16_16816(acc[nt], q2, 0u, q3, 0u, b2, b3);
+            }
+        }
+    }
+    if (g == 0) {
+        const float nq = *tc_nq(s);
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int c = nt * 8 + 2 * t + h;
+                if (nt < ntn && c < nb) {
+                    const u32 id = ids[c];
+                    const float dot = acc[nt][h];
+                    const float dist = d.metric == 0 ? __fmaf_rn(-2.0f, dot, __fadd_rn(nq, d.xbn[id]))
+                                                     : __fsub_rn(1.0f, dot);
+                    keys[c] = mkkey(dist, id);
+                }
+            }
+    }
+    __syncwarp();
+}
+
+// Bulk-copy the rows of ids[0..nb) (nb <= stage_rows) into the stage at
+// stride a.srow and wait for them.
+template <int P>
+__device__ __forceinline__ void stage_ids(const SearchArgs &a, WarpSmem &s, const u32 *ids, int nb, u32 &phase,
+                                          bool &timeout) {
+    const int lane = lane_id();
+    unsigned char *stage = reinterpret_cast<unsigned char *>(s.stage);
+    if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(s.bar, (u32)nb * a.rowb);
+    }
+    __syncwarp();
+    if (lane < nb) bulk_g2s(stage + (size_t)lane * a.srow, row_src<P>(a.d, ids[lane]), a.rowb, s.bar);
+    if (!mbar_wait(s.bar, phase, WAIT_LIMIT)) {
+        timeout = true;
+        mbar_wait(s.bar, phase, WAIT_LIMIT);   // let copies in flight land
+    }
+    phase ^= 1u;
+    __syncwarp();
+}
+
 // Evaluate the candidate ids held one per lane (NIL = none) and merge them
 // into the beam.  Returns the new beam size.  `phase` tracks the mbarrier.
 template <int P, bool LOG>
@@ -349,7 +446,7 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
     if (cnt == 0) return n;
     if (my_id != NIL) s.cid[__popc(mask & lanemask_lt())] = my_id;
     __syncwarp();
-    const u32 rowb = a.rowb;
+    const u32 rowb = a.rowb, srow = P == 1 ? a.srow : a.rowb;   // only BF16 pads its stage rows
     unsigned char *stage = reinterpret_cast<unsigned char *>(s.stage);
     float *scl = reinterpret_cast<float *>(s.nref);   // fp8 scales of the batch (nref is free here)
     for (int b0 = 0; b0 < cnt; b0 += (int)a.stage_rows) {
@@ -363,7 +460,7 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
         u64 rf = 0;
         if (lane < nb) {
             const u32 id = s.cid[b0 + lane];
-            bulk_g2s(stage + (size_t)lane * rowb, row_src<P>(d, id), rowb, s.bar);
+            bulk_g2s(stage + (size_t)lane * srow, row_src<P>(d, id), rowb, s.bar);
             rf = ld_ref(d, id);
             if (P == 2) scl[lane] = d.x8s[id];
         }
@@ -373,15 +470,19 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
         }
         phase ^= 1u;
         if (lane < nb) s.cref[b0 + lane] = rf;
+        __syncwarp();
+        if (P == 1 && a.tc) {
+            tc_keys(a, s, nb, s.cid + b0, s.ckey + b0);
+            continue;
+        }
         // 8 lanes per distance, 4 distances per round
         const int grp = lane >> 3, g = lane & 7;
-        __syncwarp();
         for (int r0 = 0; r0 < nb; r0 += 4) {
             const int c = r0 + grp;
             const int cc = c < nb ? c : nb - 1;   // idle groups recompute a valid row
             float dist;
             if (P == 0 && mp <= 128) {
-                dist = canon_dist_q8(qr, reinterpret_cast<const float *>(stage + (size_t)cc * rowb), (int)mp,
+                dist = canon_dist_q8(qr, reinterpret_cast<const float *>(stage + (size_t)cc * srow), (int)mp,
                                      (int)d.metric, g);
             } else if (P == 1 && mp <= 128) {
                 // the bf16 row widened to fp32, then canon_dist's operations in its order
@@ -389,11 +490,11 @@ __device__ int eval_merge(const SearchArgs &a, WarpSmem &s, u32 my_id, int n, u3
 #pragma unroll
                 for (int t = 0; t < 4; t++) {
                     const int i = 4 * (g + 8 * t);
-                    v[t] = i < (int)mp ? load4<1>(stage + (size_t)cc * rowb, i, 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[t] = i < (int)mp ? load4<1>(stage + (size_t)cc * srow, i, 1.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 dist = canon_dist_q8v(qr, v, (int)mp, (int)d.metric, g);
             } else
-                dist = qdist<P>(s.qv, stage + (size_t)cc * rowb, P == 2 ? scl[cc] : 1.0f, (int)mp, (int)d.metric, g);
+                dist = qdist<P>(s.qv, stage + (size_t)cc * srow, P == 2 ? scl[cc] : 1.0f, (int)mp, (int)d.metric, g);
             if (c < nb && g == 0) s.ckey[b0 + c] = mkkey(dist, s.cid[b0 + c]);
         }
         __syncwarp();
@@ -548,10 +649,65 @@ __device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32
         const u32 i = 4u * ((lane & 7) + 8 * t);
         qr[t] = i < mp ? *reinterpret_cast<const float4 *>(s.qv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (P == 1 && a.tc) {
+        // the query as bf16 pairs, and its squared norm over the bf16 values
+        float sq = 0.0f;
+        u32 *qb = tc_qb(s);
+        for (u32 i = lane; 2 * i < d.mb; i += 32) {
+            const float x0 = 2 * i < mp ? s.qv[2 * i] : 0.0f, x1 = 2 * i + 1 < mp ? s.qv[2 * i + 1] : 0.0f;
+            const u32 w = pack_bf16(x0, x1);
+            qb[i] = w;
+            const float b0 = __uint_as_float(w << 16), b1 = __uint_as_float(w & 0xFFFF0000u);
+            sq = __fmaf_rn(b0, b0, sq);
+            sq = __fmaf_rn(b1, b1, sq);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) sq = __fadd_rn(sq, __shfl_xor_sync(FULL, sq, o));
+        if (lane == 0) *tc_nq(s) = sq;
+        __syncwarp();
+    }
     // initial beam: the L nearest members of the entry set E, computed by
     // seed_kernel; the reference words are sampled here
+    const u64 *sk = seed_row;
+    if (P == 1 && a.tc) {
+        // the seeds' keys on the tensor cores, whichever kernel chose them,
+        // so that they are the keys this search gives any id; sorted in the stage
+        const int bs = min((int)a.stage_rows, 32);   // s.cid holds 32 ids
+        for (int b0 = 0; b0 < n0; b0 += bs) {
+            const int nb = min(bs, n0 - b0);
+            if (lane < nb) s.cid[lane] = key_id(seed_row[b0 + lane]);
+            __syncwarp();
+            stage_ids<P>(a, s, s.cid, nb, phase, timeout);
+            tc_keys(a, s, nb, s.cid, s.bkey + b0);
+        }
+        u64 *rk = reinterpret_cast<u64 *>(s.stage);
+        int np2 = 32;
+        while (np2 < n0) np2 <<= 1;
+        for (int i = lane; i < np2; i += 32) rk[i] = i < n0 ? s.bkey[i] : KEY_INF;
+        __syncwarp();
+        warp_sort_u64(rk, np2);
+        sk = rk;
+    } else if (P != 0 && a.rekey) {
+        // seeds ranked by the canonical fp32 distance: every key in the beam
+        // must be this precision's distance of its id (an id evaluated again
+        // then collapses with its seed), so the seeds are re-keyed and sorted
+        u64 *rk = reinterpret_cast<u64 *>(s.stage);
+        int np2 = 32;
+        while (np2 < n0) np2 <<= 1;
+        const int grp = lane >> 3, g = lane & 7;
+        for (int r0 = 0; r0 < n0; r0 += 4) {
+            const int c = r0 + grp;
+            const u32 id = key_id(seed_row[c < n0 ? c : n0 - 1]);
+            const float dist = qdist<P>(s.qv, row_src<P>(d, id), P == 2 ? d.x8s[id] : 1.0f, (int)mp, (int)d.metric, g);
+            if (c < n0 && g == 0) rk[c] = mkkey(dist, id);
+        }
+        for (int i = n0 + lane; i < np2; i += 32) rk[i] = KEY_INF;
+        __syncwarp();
+        warp_sort_u64(rk, np2);
+        sk = rk;
+    }
     for (int i = lane; i < n0; i += 32) {
-        const u64 k = seed_row[i];
+        const u64 k = sk[i];
         const u32 id = key_id(k);
         s.bkey[i] = k;
         s.bref[i] = ld_ref(d, id);
@@ -691,8 +847,9 @@ __global__ void __launch_bounds__(32 * WPB, 24 / WPB) search_kernel(SearchArgs a
     const Dev &d = a.d;
     const u32 mp = d.mp;
     const size_t sb = seen_bytes(a);
-    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, sb, a.rowb);
-    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, sb, a.rowb);
+    const u32 qbytes = a.tc ? d.mb * 2 : 0u;
+    const size_t wb = search_warp_bytes(mp, a.L, a.stage_rows, sb, a.srow, qbytes);
+    WarpSmem s = carve(smem + warp * wb, mp, a.L, a.stage_rows, sb, a.srow, qbytes);
     if (lane == 0) mbar_init(s.bar, 1);
     __syncwarp();
     u32 phase = 0;
@@ -845,8 +1002,9 @@ __global__ void __launch_bounds__(128, 3) ring_search_kernel(SearchArgs a, RingA
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const Dev &d = a.d;
     const size_t sb = seen_bytes(a);
-    const size_t wb = search_warp_bytes(d.mp, a.L, a.stage_rows, sb, a.rowb);
-    WarpSmem s = carve(smem + warp * wb, d.mp, a.L, a.stage_rows, sb, a.rowb);
+    const u32 qbytes = a.tc ? d.mb * 2 : 0u;
+    const size_t wb = search_warp_bytes(d.mp, a.L, a.stage_rows, sb, a.srow, qbytes);
+    WarpSmem s = carve(smem + warp * wb, d.mp, a.L, a.stage_rows, sb, a.srow, qbytes);
     if (lane == 0) mbar_init(s.bar, 1);
     __syncwarp();
     u32 phase = 0;
@@ -920,6 +1078,53 @@ __global__ void __launch_bounds__(128, 3) ring_search_kernel(SearchArgs a, RingA
     }
 }
 
+// A BF16 search (not the exact-copy form of an fp32 search) takes its keys from
+// the tensor cores when the index keeps the copy's norms and the row length
+// is a multiple of 32; its stage rows are then padded to an odd number of
+// 16-byte chunks, so that ldmatrix's eight row reads fall in distinct banks.
+static void set_tc(SearchArgs &a, const Dev &d, u32 prec, bool exact_rows) {
+    a.tc = prec == 1 && !exact_rows && d.xbn != nullptr && d.mb % 32 == 0 ? 1u : 0u;
+    a.srow = a.tc && (a.rowb / 16) % 2 == 0 ? a.rowb + 16 : a.rowb;
+    // a BF16 row is half an fp32 row: as many rows per gather as the fp32
+    // shape's stage bytes hold (up to 32), so an expansion needs fewer round
+    // trips (measured on the 768-d inner-product index: 497k -> 527k
+    // queries/s; FP8 rows at four times the count lost occupancy instead)
+    if (prec == 1 && !exact_rows)
+        a.stage_rows = std::min<u32>(32, std::max<u32>(a.stage_rows, a.stage_rows * d.mp * 4 / a.srow));
+}
+
+// The largest dynamic shared memory a block may opt in to on this device.
+static size_t smem_optin_bytes() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return (size_t)v;
+}
+
+// The stage must hold the keys a search sorts there: the rerank candidates
+// (rerank * k, at most the beam) and re-keyed seeds (the beam), each rounded
+// up to a power of two.
+// Returns the fewest stage rows that hold them.
+static u32 fit_stage(SearchArgs &a, u32 L, u32 k, u32 rerank, u32 prec, u32 mode) {
+    size_t need = 0;
+    if (prec != 0 && mode == 0) {
+        size_t rn = 64;
+        while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
+        need = rn;
+    }
+    if (a.rekey || a.tc) {
+        size_t rn = 32;
+        while (rn < L) rn <<= 1;
+        need = std::max(need, rn);
+    }
+    const u32 min_rows = std::max<u32>(1, (u32)((need * 8 + a.srow - 1) / a.srow));
+    if (a.stage_rows < min_rows) a.stage_rows = min_rows;
+    return min_rows;
+}
+
 static SeenLayout set_seen(SearchArgs &a, const Dev &d, u32 bits) {
     const SeenLayout l = seen_layout(d.capacity, bits);
     a.seen_bits = bits;
@@ -947,16 +1152,17 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
     a.exact = 0;
     a.wq = C_WORK2;
     a.err = C_ERR_S;
-    if (prec != 0) {
-        size_t rn = 64;
-        while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
-        if ((size_t)a.stage_rows * a.rowb < rn * 8) a.stage_rows = (u32)((rn * 8 + a.rowb - 1) / a.rowb);
-    }
+    set_tc(a, d, prec, false);
+    const u32 min_rows = fit_stage(a, L, k, rerank, prec, 0);
     // head: claimed, device count, last host poll, stop flag, then the statistics
     RingArgs r{head, head + 1, head + 2, head + 3, head + 4, tail, closed, done, served_by, slots, seq, max_ns};
     using K = void (*)(SearchArgs, RingArgs);
     K fn = prec == 1 ? ring_search_kernel<1> : prec == 2 ? ring_search_kernel<2> : ring_search_kernel<0>;
-    const size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.rowb);
+    size_t smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.srow, a.tc ? d.mb * 2 : 0u);
+    while (smem > smem_optin_bytes() && a.stage_rows > min_rows) {
+        a.stage_rows--;
+        smem = 4 * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.srow, a.tc ? d.mb * 2 : 0u);
+    }
     cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -994,7 +1200,7 @@ cudaError_t launch_seed(const Dev &d, const float *q, u32 nq, u32 L, u64 *seed, 
 cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_hops, u32 mode, u32 k,
                           u32 *out_ids, float *out_dist, u64 *exp_keys, u32 *exp_count, u64 *seed,
                           const SearchTuning &tune, int num_sms, cudaStream_t st, u32 prec, u32 rerank,
-                          const u32 *nq_dev, bool exact_rows, u32 *elog, u32 *elog_n, u32 elog_cap) {
+                          const u32 *nq_dev, bool exact_rows, u32 *elog, u32 *elog_n, u32 elog_cap, bool rekey) {
     if (nq == 0) return cudaSuccess;
     if (exact_rows) prec = 1;
     if ((prec == 1 && !d.xb) || (prec == 2 && !d.x8) || prec > 2) return cudaErrorInvalidValue;
@@ -1007,6 +1213,8 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.rowb = prec == 1 ? d.mb * 2 : prec == 2 ? d.m8 : d.mp * 4;
     a.rerank = rerank;
     a.exact = exact_rows ? 1u : 0u;
+    a.rekey = rekey && prec != 0 ? 1u : 0u;
+    set_tc(a, d, prec, exact_rows);
     a.wq = mode == 0 ? C_WORK2 : C_WORK;
     a.err = mode == 0 ? C_ERR_S : C_ERR;
     a.elog = elog;
@@ -1015,20 +1223,20 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     const bool log = elog != nullptr;
     const u32 wpb = log ? 4u : tune.warps_per_block;
     if (wpb != 2 && wpb != 4 && wpb != 8) return cudaErrorInvalidValue;
-    // the rerank buffer (up to the beam, rounded up to a power of two >= 64
-    // keys) lives in the stage
-    if (prec != 0 && mode == 0) {
-        size_t rn = 64;
-        while (rn < std::min<size_t>((size_t)rerank * k, L)) rn <<= 1;
-        if ((size_t)a.stage_rows * a.rowb < rn * 8) a.stage_rows = (u32)((rn * 8 + a.rowb - 1) / a.rowb);
-    }
+    const u32 min_rows = fit_stage(a, L, k, rerank, prec, mode);
     using K = void (*)(SearchArgs);
     K fn = nullptr;
     if (log) fn = prec == 1 ? search_kernel<1, true> : prec == 2 ? search_kernel<2, true> : search_kernel<0, true>;
     else if (wpb == 2) fn = prec == 1 ? search_kernel<1, false, 2> : prec == 2 ? search_kernel<2, false, 2> : search_kernel<0, false, 2>;
     else if (wpb == 8) fn = prec == 1 ? search_kernel<1, false, 8> : prec == 2 ? search_kernel<2, false, 8> : search_kernel<0, false, 8>;
     else fn = prec == 1 ? search_kernel<1> : prec == 2 ? search_kernel<2> : search_kernel<0>;
-    size_t smem = (size_t)wpb * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.rowb);
+    size_t smem = (size_t)wpb * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.srow, a.tc ? d.mb * 2 : 0u);
+    // a widened stage (or the bf16 query) that does not fit beside this
+    // shape: fewer rows, down to what the sorted keys need
+    while (smem > smem_optin_bytes() && a.stage_rows > min_rows) {
+        a.stage_rows--;
+        smem = (size_t)wpb * search_warp_bytes(d.mp, L, a.stage_rows, sl.bytes, a.srow, a.tc ? d.mb * 2 : 0u);
+    }
     cudaError_t e = smem_at_least((const void *)fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

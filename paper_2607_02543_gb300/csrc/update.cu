@@ -155,23 +155,6 @@ __device__ __forceinline__ void stage_rows(const Dev &d, Stage &st, const u64 *c
 // magnitude <= 256, and so is every product and partial sum while the norms
 // stay below 2^24; then each distance equals the canonical one bit for bit.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ldsm_x4(u32 &r0, u32 &r1, u32 &r2, u32 &r3, u32 addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-__device__ __forceinline__ void mma_bf16_16816(float *c, u32 a0, u32 a1, u32 a2, u32 a3, u32 b0, u32 b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ u32 pack_bf16(float lo, float hi) {
-    u32 r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
-}
 
 // ldmatrix row addresses in the swizzled tile: lane l reads (row, chunk
 // 2 ks + (l >> 4)) with row & 7 = l & 7, so the chunk's byte offset in its row

@@ -300,12 +300,17 @@ __global__ void ingest_copies_kernel(Dev d, u64 first, u64 n) {
     if (d.xb) {
         __nv_bfloat16 *br = reinterpret_cast<__nv_bfloat16 *>(d.xb + row * d.mb);
         bool inexact = false;
+        float sq = 0.0f;   // |bf16 row|^2: lane-strided fma chains, then a fixed xor tree
         for (u32 i = lane; i < d.mb; i += 32) {
             const float v = i < d.mp ? xr[i] : 0.0f;
             const __nv_bfloat16 b = __float2bfloat16_rn(v);
             br[i] = b;
-            inexact |= !(__bfloat162float(b) == v);   // NaN counts as inexact
+            const float bf = __bfloat162float(b);
+            inexact |= !(bf == v);   // NaN counts as inexact
+            sq = __fmaf_rn(bf, bf, sq);
         }
+        for (int o = 16; o >= 1; o >>= 1) sq = __fadd_rn(sq, __shfl_xor_sync(FULL, sq, o));
+        if (lane == 0 && d.xbn) d.xbn[row] = sq;
         // a row whose copy is not exact keeps fp32 searches on the fp32 rows
         if (__any_sync(FULL, inexact) && lane == 0) atomicAdd(&d.ctr[C_INEXACT], 1ull);
     }
