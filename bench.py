@@ -105,30 +105,11 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
 
 # DRAM bytes per BeamSearch expansion of the query-mode launch on the 1M x 128
 # workload, from the full-size ncu capture in
-# profiles/search_kernel_int256-1m-d128_dram.md (9,387,749,888 bytes over
+# profiles/search_kernel_int256-1m-d128_dram.md (9,383,231,744 bytes over
 # 1,287,324 expansions at beam 128); a launch's traffic is this figure times
 # its expansions.  Valid only for the search.cu revision it was taken on
 # (first 16 hex digits of SHA-256).
-SEARCH_DRAM_BYTES_PER_EXPANSION = {"int256-1m-d128": (9_387_749_888 / 1_287_324, "113aadf19177b3a2")}
-
-
-# DRAM bytes of each writer kernel over one round of 10,000 deletes + 10,000
-# inserts on the 1M x 128 workload (the same capture; offer_fold: the insert
-# offers and the refine offers).  Valid only for the update.cu revision given.
-WRITER_DRAM_BYTES = {"int256-1m-d128": ({"prune": 94_413_056, "offer_fold": 455_783_168, "refine": 84_920_576,
-                                         "repair_k": 173_362_688, "repair_fold": 822_257_664,
-                                         "compact": 296_149_504}, "122d52ac54be7b33")}
-
-
-def writer_traffic(workload_name: str):
-    """{kind: DRAM bytes per round} if measured for this update.cu, else {}."""
-    import hashlib
-    entry = WRITER_DRAM_BYTES.get(workload_name)
-    if entry is None:
-        return {}
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2607_02543_gb300", "csrc", "update.cu")
-    rev = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return entry[0] if rev == entry[1] else {}
+SEARCH_DRAM_BYTES_PER_EXPANSION = {"int256-1m-d128": (9_383_231_744 / 1_287_324, "0ceb86fd05b94e33")}
 
 
 def search_traffic(workload_name: str, n_expand: float):
