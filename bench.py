@@ -112,6 +112,25 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
 SEARCH_DRAM_BYTES_PER_EXPANSION = {"int256-1m-d128": (9_383_231_744 / 1_287_324, "0ceb86fd05b94e33")}
 
 
+# DRAM bytes of each writer kernel over one round of 10,000 deletes + 10,000
+# inserts on the 1M x 128 workload (the same capture; offer_fold: the insert
+# offers and the refine offers).  Valid only for the update.cu revision given.
+WRITER_DRAM_BYTES = {"int256-1m-d128": ({"prune": 94_628_864, "offer_fold": 456_289_792, "refine": 84_670_720,
+                                         "repair_k": 173_777_920, "repair_fold": 821_889_536,
+                                         "compact": 295_994_368}, "d1687973a1e58402")}
+
+
+def writer_traffic(workload_name: str):
+    """{kind: DRAM bytes per round} if measured for this update.cu, else {}."""
+    import hashlib
+    entry = WRITER_DRAM_BYTES.get(workload_name)
+    if entry is None:
+        return {}
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2607_02543_gb300", "csrc", "update.cu")
+    rev = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return entry[0] if rev == entry[1] else {}
+
+
 def search_traffic(workload_name: str, n_expand: float):
     """DRAM bytes of a query-mode search launch with n_expand expansions, if
     measured for this source, else None."""
