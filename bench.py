@@ -503,7 +503,7 @@ def precision_forms(args, stream, forms=("fp32", "bf16", "fp8")) -> dict:
             return best
 
         sweep, chosen = [], None
-        for rr in ((1,) if form == "fp32" else (4, 8, 25)):
+        for rr in ((1,) if form == "fp32" else (1, 2, 4, 8, 25)):
             idx.set_rerank(rr)
             for b in (64, 96, 128, 160, 192, 256):
                 idx.search(d_q, w.k, b, stream, out=(out_ids, out_d))

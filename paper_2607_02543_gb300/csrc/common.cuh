@@ -196,6 +196,59 @@ __device__ __forceinline__ float canon_dist(const float *__restrict__ a, const f
     return metric == 0 ? s : __fsub_rn(1.0f, s);
 }
 
+// canon_dist<G> with the column blocks outermost: the T loads of one block
+// are in flight together (more registers, fewer round trips for rows read
+// from global memory); every p[t] sums its elements in the same order, so
+// the result is bit-identical to canon_dist<G>.
+template <int G>
+__device__ __forceinline__ float canon_dist_wide(const float *__restrict__ a, const float *__restrict__ b,
+                                                 int mp, int metric, int g) {
+    constexpr int T = 32 / G;
+    float p[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) p[t] = 0.0f;
+    for (int base = 0; base < mp; base += 128) {
+        float4 u[T], v[T];
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const int i = base + 4 * (g + G * t);
+            if (i < mp) {
+                u[t] = *reinterpret_cast<const float4 *>(a + i);
+                v[t] = *reinterpret_cast<const float4 *>(b + i);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const int i = base + 4 * (g + G * t);
+            if (i < mp) {
+                float acc = p[t];
+                if (metric == 0) {
+                    float d0 = __fsub_rn(u[t].x, v[t].x), d1 = __fsub_rn(u[t].y, v[t].y);
+                    float d2 = __fsub_rn(u[t].z, v[t].z), d3 = __fsub_rn(u[t].w, v[t].w);
+                    acc = __fmaf_rn(d0, d0, acc);
+                    acc = __fmaf_rn(d1, d1, acc);
+                    acc = __fmaf_rn(d2, d2, acc);
+                    acc = __fmaf_rn(d3, d3, acc);
+                } else {
+                    acc = __fmaf_rn(u[t].x, v[t].x, acc);
+                    acc = __fmaf_rn(u[t].y, v[t].y, acc);
+                    acc = __fmaf_rn(u[t].z, v[t].z, acc);
+                    acc = __fmaf_rn(u[t].w, v[t].w, acc);
+                }
+                p[t] = acc;
+            }
+        }
+    }
+#pragma unroll
+    for (int hh = T / 2; hh >= 1; hh >>= 1)
+#pragma unroll
+        for (int t = 0; t < hh; t++) p[t] = __fadd_rn(p[t], p[t + hh]);
+    float s = p[0];
+#pragma unroll
+    for (int h = G / 2; h >= 1; h >>= 1) s = __fadd_rn(s, __shfl_xor_sync(FULL, s, h));
+    return metric == 0 ? s : __fsub_rn(1.0f, s);
+}
+
 // canon_dist<8> for rows of at most 128 floats, in two steps so that several
 // rows' loads can be in flight: canon_row_q8 loads this lane's four row float4
 // (elements 4 (g + 8 t) .. + 3, t = 0..3; zero past the row), canon_dist_q8v
@@ -469,6 +522,11 @@ __device__ __forceinline__ void mbar_init(u64 *bar, u32 count) {
 __device__ __forceinline__ void mbar_expect_tx(u64 *bar, u32 bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+// Fire-and-forget bulk prefetch of [src, src + bytes) into L2 (src 16-byte
+// aligned, bytes a multiple of 16); nothing waits on it.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, u32 bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *bar) {
     asm volatile(

@@ -586,6 +586,12 @@ __global__ void __launch_bounds__(RR_WARPS * 32) gt_rerank_kernel(Dev d, RerankA
     const int grp = lane >> 3, g = lane & 7;
     for (u32 i = 0; i < (over ? 0u : cnt); i++) {
         const u32 b = cblk[warp][i];
+        if (lane == 0 && i + 1 < cnt) {
+            // the next candidate block's rows on their way to L2
+            const u64 r0 = (u64)cblk[warp][i + 1] * 32u;
+            const u64 nr = min((u64)32, a.n_rows - r0);
+            bulk_prefetch_l2(d.x + r0 * d.mp, (u32)(nr * d.mp * 4u));
+        }
         u64 cand = KEY_INF;
         for (int r0 = 0; r0 < 32; r0 += 4) {
             const u32 id = b * 32 + r0 + grp;
@@ -596,7 +602,7 @@ __global__ void __launch_bounds__(RR_WARPS * 32) gt_rerank_kernel(Dev d, RerankA
                 live = !ref_del(rf) && ref_slab(rf) != NIL;
             }
             // every lane computes (the distance shuffles over the full warp)
-            const float dd = canon_dist<8>(qv, d.x + (size_t)(inr ? id : 0u) * d.mp, (int)d.mp, (int)d.metric, g);
+            const float dd = canon_dist_wide<8>(qv, d.x + (size_t)(inr ? id : 0u) * d.mp, (int)d.mp, (int)d.metric, g);
             const u64 kk = live ? mkkey(dd, id) : KEY_INF;
 #pragma unroll
             for (int t = 0; t < 4; t++) {
@@ -743,7 +749,7 @@ __global__ void __launch_bounds__(SS_WARPS * 32) seed_select_kernel(Dev d, SeedS
             for (u32 r0 = 0; r0 < cnt; r0 += 4) {
                 const u32 i = r0 + grp;
                 const u32 id = d.entries[cidx[warp][i < cnt ? i : cnt - 1]];
-                const float dd = canon_dist<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
+                const float dd = canon_dist_wide<8>(qv, d.x + (size_t)id * d.mp, (int)d.mp, (int)d.metric, g);
                 if (i < cnt && g == 0) ckey[warp][i] = mkkey(dd, id);
             }
         }

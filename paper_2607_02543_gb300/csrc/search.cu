@@ -788,13 +788,47 @@ __device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32
         }
         __syncwarp();
         const int grp = lane >> 3, g = lane & 7;
-        for (int r0 = 0; r0 < c; r0 += 4) {
-            const int cc = min(r0 + grp, c - 1);
-            const u32 id = key_id(rk[cc]);
-            const float dist = canon_dist<8>(s.qv, d.x + (size_t)id * mp, (int)mp, (int)d.metric, g);
-            __syncwarp();
-            if (r0 + grp < c && g == 0) rk[cc] = mkkey(dist, id);
-            __syncwarp();
+        // the fp32 rows go through the stage behind the keys, as many per bulk
+        // copy as fit; a stage too small for one row reads them in place
+        const u32 rowf = mp * 4u, rkb = (u32)rn * 8u;
+        const u32 stb = a.stage_rows * a.srow;
+        const int per = stb > rkb ? (int)min(32u, (stb - rkb) / rowf) : 0;
+        if (per > 0) {
+            unsigned char *rows = reinterpret_cast<unsigned char *>(s.stage) + rkb;
+            for (int b0 = 0; b0 < c; b0 += per) {
+                const int nb = min(per, c - b0);
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(s.bar, (u32)nb * rowf);
+                }
+                __syncwarp();
+                if (lane < nb) bulk_g2s(rows + (size_t)lane * rowf, d.x + (size_t)key_id(rk[b0 + lane]) * mp, rowf, s.bar);
+                if (!mbar_wait(s.bar, phase, WAIT_LIMIT)) {
+                    timeout = true;
+                    mbar_wait(s.bar, phase, WAIT_LIMIT);   // let copies in flight land
+                }
+                phase ^= 1u;
+                __syncwarp();
+                for (int r0 = 0; r0 < nb; r0 += 4) {
+                    const int cc = min(r0 + grp, nb - 1);
+                    const u32 id = key_id(rk[b0 + cc]);
+                    const float dist = canon_dist<8>(s.qv, reinterpret_cast<const float *>(rows + (size_t)cc * rowf),
+                                                     (int)mp, (int)d.metric, g);
+                    __syncwarp();
+                    if (r0 + grp < nb && g == 0) rk[b0 + cc] = mkkey(dist, id);
+                    __syncwarp();
+                }
+            }
+        } else {
+            for (int i = lane; i < c; i += 32) bulk_prefetch_l2(d.x + (size_t)key_id(rk[i]) * mp, rowf);
+            for (int r0 = 0; r0 < c; r0 += 4) {
+                const int cc = min(r0 + grp, c - 1);
+                const u32 id = key_id(rk[cc]);
+                const float dist = canon_dist<8>(s.qv, d.x + (size_t)id * mp, (int)mp, (int)d.metric, g);
+                __syncwarp();
+                if (r0 + grp < c && g == 0) rk[cc] = mkkey(dist, id);
+                __syncwarp();
+            }
         }
         for (int i = c + lane; i < rn; i += 32) rk[i] = KEY_INF;
         __syncwarp();
