@@ -304,6 +304,8 @@ typedef struct {
     uint32_t seen_bits;   /* log2 slots of the evaluated-id cache             */
     float ms;             /* measured: seeding + search of the tuning batch   */
     uint32_t warps_per_block; /* queries in flight per thread block: 2, 4, 8 */
+    uint32_t keys_tc;     /* BF16 searches: keys from the tensor cores (1) or
+                             the CUDA cores (0); 1 for other precisions       */
 } etale_tuning;
 
 /* Turn the exact-copy gathers of cfg.exact_rows on (1) or off (0) for the
@@ -316,11 +318,23 @@ etale_status etale_set_exact_rows(etale_index *idx, int on);
 etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint32_t seen_bits,
                                      uint32_t warps_per_block);
 
+/* Where a BF16 search (etale_set_search_precision 1; insert or query) takes
+ * the keys that order its beam: tensor = 1 (default), |q|^2 + |x|^2 - 2 q.x
+ * with the dot product from bf16 tensor-core MMAs; tensor = 0, the CUDA
+ * cores' fp32 reduction of the fp32 query against the widened bf16 row.
+ * Both are approximations of the fp32 distance, so the beam order, and
+ * with it the candidates that reach the exact rerank, may differ between
+ * them; returned distances are exact fp32 either way.  Other precisions
+ * ignore it.  EINVAL unless tensor is 0 or 1.                              */
+etale_status etale_set_search_keys(etale_index *idx, int tensor);
+
 /* Time seeding + BeamSearch of the given DEVICE query batch under each
  * candidate launch shape (stage rows 2/4/8/16 x cache 2^7..2^10 slots x
- * 2/4/8 warps per block; shapes whose shared memory does not fit the device
+ * 2/4/8 warps per block, and for a BF16 search precision both key paths of
+ * etale_set_search_keys; shapes whose shared memory does not fit the device
  * are skipped), keep the fastest for this index, and report up to n_out
- * tried shapes in out.  Results do not depend on the launch shape.         */
+ * tried shapes in out.  Results do not depend on the launch shape; a BF16
+ * search's key path may change which candidates reach its exact rerank.  */
 etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k,
                                    uint32_t beam, etale_tuning *out, uint32_t n_out, uint32_t *n_tried,
                                    void *stream);

@@ -38,7 +38,7 @@ class Config(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("stage_rows", C.c_uint32), ("seen_bits", C.c_uint32), ("ms", C.c_float),
-                ("warps_per_block", C.c_uint32)]
+                ("warps_per_block", C.c_uint32), ("keys_tc", C.c_uint32)]
 
 
 class Stats(C.Structure):
@@ -56,7 +56,7 @@ EXPORTS = ["etale_config_default", "etale_create", "etale_destroy", "etale_inser
            "etale_get_entries", "etale_stats", "etale_get_config", "etale_last_error",
            "etale_kernel_launches", "etale_set_profiling", "etale_get_profile", "etale_search_static",
            "etale_set_search_precision", "etale_export_copies", "etale_set_concurrent",
-           "etale_set_search_tuning", "etale_autotune_search", "etale_search_graph_create",
+           "etale_set_search_tuning", "etale_set_search_keys", "etale_autotune_search", "etale_search_graph_create",
            "etale_search_graph_launch", "etale_search_graph_check", "etale_search_graph_destroy",
            "etale_selftest_bounded_wait", "etale_ground_truth_info", "etale_set_exact_rows", "etale_save",
            "etale_load", "etale_search_eval_count", "etale_round_graph_create",
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
             "etale_export_copies": ([P, U64, U64, P, P, P], C.c_int),
             "etale_set_concurrent": ([P, C.c_int], C.c_int),
             "etale_set_search_tuning": ([P, U32, U32, U32], C.c_int),
+            "etale_set_search_keys": ([P, C.c_int], C.c_int),
             "etale_set_exact_rows": ([P, C.c_int], C.c_int),
             "etale_autotune_search": ([P, P, U64, U32, U32, P, U32, C.POINTER(U32), P], C.c_int),
             "etale_search_graph_create": ([P, U32, U32, U32, P, P, P, P, C.POINTER(P)], C.c_int),
@@ -284,14 +285,19 @@ class Index:
     def set_search_tuning(self, stage_rows: int, seen_bits: int, warps_per_block: int = 0):
         self._check(self.lib.etale_set_search_tuning(self.h, stage_rows, seen_bits, warps_per_block))
 
+    def set_search_keys(self, tensor: bool):
+        """BF16 searches: beam keys from the tensor cores (True) or the CUDA cores (False)."""
+        self._check(self.lib.etale_set_search_keys(self.h, 1 if tensor else 0))
+
     def autotune_search(self, queries, k: int, beam: int, stream=None):
         """Time the launch shapes on a device query batch; keep the fastest.
-        Returns [(stage_rows, seen_bits, ms, warps_per_block), ...] for the shapes tried."""
-        out = (Tuning * 64)()
+        Returns [(stage_rows, seen_bits, ms, warps_per_block, keys_tc), ...] for the shapes tried."""
+        out = (Tuning * 128)()
         n = C.c_uint32(0)
-        self._check(self.lib.etale_autotune_search(self.h, _ptr(queries), queries.shape[0], k, beam, out, 64,
+        self._check(self.lib.etale_autotune_search(self.h, _ptr(queries), queries.shape[0], k, beam, out, 128,
                                                    C.byref(n), _stream(stream)))
-        return [(out[i].stage_rows, out[i].seen_bits, out[i].ms, out[i].warps_per_block) for i in range(n.value)]
+        return [(out[i].stage_rows, out[i].seen_bits, out[i].ms, out[i].warps_per_block, out[i].keys_tc)
+                for i in range(min(n.value, 128))]
 
     def autotune_beam(self, queries, k: int, target: float, beams=(64, 96, 112, 128, 144, 160, 192, 256),
                       stream=None):

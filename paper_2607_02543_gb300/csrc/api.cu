@@ -1323,6 +1323,13 @@ etale_status etale_set_search_tuning(etale_index *idx, uint32_t stage_rows, uint
     return ETALE_OK;
 }
 
+etale_status etale_set_search_keys(etale_index *idx, int tensor) {
+    if (!idx) return ETALE_EINVAL;
+    if (tensor != 0 && tensor != 1) return idx->fail(ETALE_EINVAL, "tensor must be 0 or 1");
+    idx->tune.keys_tc = (u32)tensor;
+    return ETALE_OK;
+}
+
 etale_status etale_autotune_search(etale_index *idx, const float *queries, uint64_t nq, uint32_t k, uint32_t beam,
                                    etale_tuning *out, uint32_t n_out, uint32_t *n_tried, void *stream) {
     if (!idx) return ETALE_EINVAL;
@@ -1350,6 +1357,9 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
     SearchTuning best_t = saved;
     u32 tried = 0;
     const u32 rows[4] = {2, 4, 8, 16}, bits[4] = {7, 8, 9, 10}, wpbs[3] = {2, 4, 8};
+    // BF16 searches also try both key paths (tensor cores, CUDA cores)
+    const u32 n_keys = idx->search_prec == 1 ? 2u : 1u;
+    for (u32 kp = 0; kp < n_keys; kp++)
     for (u32 c = 0; c < 3; c++)
     for (u32 a = 0; a < 4; a++)
         for (u32 b = 0; b < 4; b++) {
@@ -1357,6 +1367,7 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
             t.stage_rows = rows[a];
             t.seen_bits = bits[b];
             t.warps_per_block = wpbs[c];
+            t.keys_tc = kp == 0 ? 1u : 0u;
             if (fit_tuning(idx, L, t).stage_rows != t.stage_rows) continue;   // does not fit: not a shape
             float ms_best = 1e30f;
             bool ok = true;
@@ -1374,7 +1385,8 @@ etale_status etale_autotune_search(etale_index *idx, const float *queries, uint6
             }
             cudaGetLastError();   // a shape that does not fit is skipped
             if (!ok) continue;
-            if (out && tried < n_out) out[tried] = etale_tuning{t.stage_rows, t.seen_bits, ms_best, t.warps_per_block};
+            if (out && tried < n_out)
+                out[tried] = etale_tuning{t.stage_rows, t.seen_bits, ms_best, t.warps_per_block, t.keys_tc};
             tried++;
             if (ms_best < best) { best = ms_best; best_t = t; }
         }

@@ -9,6 +9,7 @@ struct SearchTuning {
     u32 stage_rows = 16;       // rows gathered per bulk-copy batch
     u32 seen_bits = 9;         // log2 of the evaluated-id cache slots
     u32 warps_per_block = 4;   // queries in flight per block: 2, 4 or 8
+    u32 keys_tc = 1;           // BF16 searches: keys from the tensor cores (1) or the CUDA cores (0)
 };
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes`.  The

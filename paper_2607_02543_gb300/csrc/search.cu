@@ -1116,8 +1116,8 @@ __global__ void __launch_bounds__(128, 3) ring_search_kernel(SearchArgs a, RingA
 // the tensor cores when the index keeps the copy's norms and the row length
 // is a multiple of 32; its stage rows are then padded to an odd number of
 // 16-byte chunks, so that ldmatrix's eight row reads fall in distinct banks.
-static void set_tc(SearchArgs &a, const Dev &d, u32 prec, bool exact_rows) {
-    a.tc = prec == 1 && !exact_rows && d.xbn != nullptr && d.mb % 32 == 0 ? 1u : 0u;
+static void set_tc(SearchArgs &a, const Dev &d, u32 prec, bool exact_rows, u32 keys_tc) {
+    a.tc = keys_tc && prec == 1 && !exact_rows && d.xbn != nullptr && d.mb % 32 == 0 ? 1u : 0u;
     a.srow = a.tc && (a.rowb / 16) % 2 == 0 ? a.rowb + 16 : a.rowb;
     // a BF16 row is half an fp32 row: as many rows per gather as the fp32
     // shape's stage bytes hold (up to 32), so an expansion needs fewer round
@@ -1186,7 +1186,7 @@ cudaError_t launch_ring_search(const Dev &d, float *rows, u32 slots, u32 L, u32 
     a.exact = 0;
     a.wq = C_WORK2;
     a.err = C_ERR_S;
-    set_tc(a, d, prec, false);
+    set_tc(a, d, prec, false, tune.keys_tc);
     const u32 min_rows = fit_stage(a, L, k, rerank, prec, 0);
     // head: claimed, device count, last host poll, stop flag, then the statistics
     RingArgs r{head, head + 1, head + 2, head + 3, head + 4, tail, closed, done, served_by, slots, seq, max_ns};
@@ -1248,7 +1248,7 @@ cudaError_t launch_search(const Dev &d, const float *q, u32 nq, u32 L, u32 max_h
     a.rerank = rerank;
     a.exact = exact_rows ? 1u : 0u;
     a.rekey = rekey && prec != 0 ? 1u : 0u;
-    set_tc(a, d, prec, exact_rows);
+    set_tc(a, d, prec, exact_rows, tune.keys_tc);
     a.wq = mode == 0 ? C_WORK2 : C_WORK;
     a.err = mode == 0 ? C_ERR_S : C_ERR;
     a.elog = elog;

@@ -80,3 +80,35 @@ def test_reranked_search(oracle_mod, prec):
     h = Index(w.dim, w.metric, w.degree, 100)
     with pytest.raises(EtaleError):
         h.set_search_precision(prec)
+
+
+@pytest.mark.parametrize("dim", [96, 320])
+def test_bf16_key_paths(oracle_mod, dim):
+    """Both places a BF16 search may take its beam keys from (tensor-core
+    dot products, CUDA-core reduction of the widened row) reach the fp32
+    search's recall and return exact canonical fp32 distances, in order; the
+    autotuner reports which path each shape used."""
+    w = W.Workload("unit-ip", 3000, dim, "ip", 32, 64, 1, 40, 40, 300, 10, 64, 32, "unit")
+    plan = W.make_plan(w)
+    g = _index(w, plan)
+    gt, _ = g.ground_truth(plan.queries, 10)
+    ids32, _ = g.search(plan.queries, 10, 64)
+    r32 = recall_at_k(ids32, gt)
+    g.set_search_precision("bf16")
+    for tensor in (True, False):
+        g.set_search_keys(tensor)
+        ids, dist = g.search(plan.queries, 10, 64)
+        assert recall_at_k(ids, gt) >= r32 - 0.02, (dim, tensor)
+        for t in range(0, plan.queries.shape[0], 29):
+            for j in range(10):
+                if ids[t, j] != NIL:
+                    assert oracle_mod.dist(plan.queries[t], plan.base[ids[t, j]], "ip") == float(dist[t, j])
+            row = dist[t][ids[t] != NIL]
+            assert (np.diff(row) >= 0).all()
+    from paper_2607_02543_gb300 import EtaleError
+    with pytest.raises(EtaleError):
+        g._check(g.lib.etale_set_search_keys(g.h, 2))
+    import torch
+    q = torch.from_numpy(plan.queries[:256]).cuda()
+    tried = g.autotune_search(q, 10, 64)
+    assert {t[4] for t in tried} == {0, 1}
