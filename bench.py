@@ -105,19 +105,19 @@ def workload(name: str, n_live: int = 0) -> W.Workload:
 
 # DRAM bytes per BeamSearch expansion of the query-mode launch on the 1M x 128
 # workload, from the full-size ncu capture in
-# profiles/search_kernel_int256-1m-d128_dram.md (9,385,906,688 bytes over
+# profiles/search_kernel_int256-1m-d128_dram.md (9,384,713,728 bytes over
 # 1,287,324 expansions at beam 128); a launch's traffic is this figure times
 # its expansions.  Valid only for the search.cu revision it was taken on
 # (first 16 hex digits of SHA-256).
-SEARCH_DRAM_BYTES_PER_EXPANSION = {"int256-1m-d128": (9_385_906_688 / 1_287_324, "74e96c4a73e842cb")}
+SEARCH_DRAM_BYTES_PER_EXPANSION = {"int256-1m-d128": (9_384_713_728 / 1_287_324, "d44d14f8e67edf2a")}
 
 
 # DRAM bytes of each writer kernel over one round of 10,000 deletes + 10,000
 # inserts on the 1M x 128 workload (the same capture; offer_fold: the insert
 # offers and the refine offers).  Valid only for the update.cu revision given.
-WRITER_DRAM_BYTES = {"int256-1m-d128": ({"prune": 94_704_896, "offer_fold": 456_045_056, "refine": 84_686_592,
-                                         "repair_k": 173_755_904, "repair_fold": 822_939_904,
-                                         "compact": 295_894_272}, "d1687973a1e58402")}
+WRITER_DRAM_BYTES = {"int256-1m-d128": ({"prune": 94_937_088, "offer_fold": 456_001_536, "refine": 84_663_296,
+                                         "repair_k": 173_829_120, "repair_fold": 822_004_736,
+                                         "compact": 295_891_456}, "d1687973a1e58402")}
 
 
 def writer_traffic(workload_name: str):
@@ -425,8 +425,9 @@ def precision_forms(args, stream, forms=("fp32", "bf16", "fp8")) -> dict:
     on the bf16 tensor-core Gram tile, insert BeamSearch on the copy with the
     candidates re-scored in fp32) and queried in it (exact fp32 rerank).  Per form: build time, ms per 1% churn round (CUDA
     events, mean of `rounds`), then the cheapest (beam, rerank) reaching
-    Recall@10 >= 0.95 against the exact top-10 of the live set (query launch
-    shape from the library's autotuner at beam 64), its QPS, and
+    Recall@10 >= 0.95 against the exact top-10 of the live set (the launch
+    shape of the rounds and the queries from the library's autotuner on the
+    query batch at beam 64, after the build), its QPS, and
     the largest relative error of returned distances against fp64 on 200
     sampled queries."""
     import torch
@@ -460,6 +461,15 @@ def precision_forms(args, stream, forms=("fp32", "bf16", "fp8")) -> dict:
         idx.reclaim(stream)
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
+        # the rounds and the query launches take the shape the library's
+        # autotuner picks for this form's own queries (as the headline's do)
+        tried = idx.autotune_search(d_q, w.k, 64, stream) if not args.no_autotune else []
+        tuning = None
+        if tried:
+            best = min(tried, key=lambda t: t[2])
+            tuning = {"stage_rows": best[0], "seen_bits": best[1], "warps_per_block": best[3]}
+            if form == "bf16":
+                tuning["keys"] = "tensor cores" if best[4] else "CUDA cores"
         rng = np.random.default_rng(w.seed + 5)
         alive = np.zeros(wr.capacity, bool)
         alive[:w.n_base] = True
@@ -485,15 +495,6 @@ def precision_forms(args, stream, forms=("fp32", "bf16", "fp8")) -> dict:
             nxt += w.n_insert
         phases = {k: round(v[0] / rounds, 3) for k, v in idx.profile(reset=True).items() if v[1]}
         idx.set_profiling(False)
-        # the query launches take the shape the library's autotuner picks for
-        # this form's own queries (as the headline's do)
-        tried = idx.autotune_search(d_q, w.k, 64, stream) if not args.no_autotune else []
-        tuning = None
-        if tried:
-            best = min(tried, key=lambda t: t[2])
-            tuning = {"stage_rows": best[0], "seen_bits": best[1], "warps_per_block": best[3]}
-            if form == "bf16":
-                tuning["keys"] = "tensor cores" if best[4] else "CUDA cores"
         gt, _ = idx.ground_truth(d_q, w.k, stream)
         gt_np = gt.cpu().numpy().view(np.uint32)
 

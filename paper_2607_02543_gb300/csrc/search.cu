@@ -690,18 +690,31 @@ __device__ __forceinline__ void search_one(const SearchArgs &a, WarpSmem &s, u32
     } else if (P != 0 && a.rekey) {
         // seeds ranked by the canonical fp32 distance: every key in the beam
         // must be this precision's distance of its id (an id evaluated again
-        // then collapses with its seed), so the seeds are re-keyed and sorted
+        // then collapses with its seed), so the seeds are re-keyed and sorted.
+        // Their rows go through the stage like a neighbour batch; the keys
+        // wait in the beam until the stage is free for the sort.
+        const int bs = min((int)a.stage_rows, 32);   // s.cid holds 32 ids
+        const int grp = lane >> 3, g = lane & 7;
+        const unsigned char *stage = reinterpret_cast<const unsigned char *>(s.stage);
+        for (int b0 = 0; b0 < n0; b0 += bs) {
+            const int nb = min(bs, n0 - b0);
+            if (lane < nb) s.cid[lane] = key_id(seed_row[b0 + lane]);
+            __syncwarp();
+            stage_ids<P>(a, s, s.cid, nb, phase, timeout);
+            for (int r0 = 0; r0 < nb; r0 += 4) {
+                const int c = r0 + grp;
+                const int cc = c < nb ? c : nb - 1;
+                const u32 id = s.cid[cc];
+                const float dist = qdist<P>(s.qv, stage + (size_t)cc * a.srow, P == 2 ? d.x8s[id] : 1.0f, (int)mp,
+                                            (int)d.metric, g);
+                if (c < nb && g == 0) s.bkey[b0 + c] = mkkey(dist, id);
+            }
+            __syncwarp();
+        }
         u64 *rk = reinterpret_cast<u64 *>(s.stage);
         int np2 = 32;
         while (np2 < n0) np2 <<= 1;
-        const int grp = lane >> 3, g = lane & 7;
-        for (int r0 = 0; r0 < n0; r0 += 4) {
-            const int c = r0 + grp;
-            const u32 id = key_id(seed_row[c < n0 ? c : n0 - 1]);
-            const float dist = qdist<P>(s.qv, row_src<P>(d, id), P == 2 ? d.x8s[id] : 1.0f, (int)mp, (int)d.metric, g);
-            if (c < n0 && g == 0) rk[c] = mkkey(dist, id);
-        }
-        for (int i = n0 + lane; i < np2; i += 32) rk[i] = KEY_INF;
+        for (int i = lane; i < np2; i += 32) rk[i] = i < n0 ? s.bkey[i] : KEY_INF;
         __syncwarp();
         warp_sort_u64(rk, np2);
         sk = rk;
