@@ -29,9 +29,8 @@
  * one sub-batch search the pre-insert graph; reverse offers are grouped by
  * target and applied in ascending source id; each target publishes once.
  *
- * Parity unpinned: the refine pass in mode 1 (two hops over all ids) has no
- * hand-derived example; mode 2 (batch peers) and everything else is pinned by
- * the tests named in the design notes.
+ * Every mode, the refine pass in both readings included, is pinned by the
+ * hand-derived cases and the other tests named in the design notes.
  *
  * Floating point: the canonical distance below fixes the order of every fp32
  * operation, so a GPU implementation of the same order reproduces each

@@ -177,6 +177,62 @@ def test_hand_derived_refine_pass(oracle_mod):
 
 
 # ---------------------------------------------------------------------------
+# Hand derivation 2b: the same points with the refine pass in its other
+# reading, two-hop ids admitted from every sub-batch (refine mode 1),
+# tests/golden/refine_all_hand.json.
+#
+# Base inserts (one per sub-batch): each refine sees only ids its own
+# phases already considered, so nothing changes and after_base is that of
+# derivation 2:
+#   id0: N(0) = [] -> no candidates.
+#   id1: N(1) = [0]; via N(0) = [1] nothing new -> [0(289)] unchanged.
+#   id2: N(2) = [1, 0]; via N(1) = [2, 0] and N(0) = [2, 1] nothing new ->
+#        [1(16), 0(169)] unchanged.
+# Batch phases 1-3 as in derivation 2: N(0) = [4(4), 3(49), 2(169)],
+# N(1) = [5(1), 2(16), 0(289)], N(2) = [5(9), 0(169)], N(3) = [0(49), 1(576)],
+# N(4) = [0(4), 2(225)], N(5) = [1(1), 2(9), 0(256)].
+# Phase 4 on that graph, every live two-hop id admitted:
+#   v3: N(3) = [0(49), 1(576)]; via N(0): 4 (25), 2 (400); via N(1): 5 (529).
+#       Prune 4(25), 0(49), 2(400), 5(529), 1(576): keep 4; 0: 2.25*4 = 9 <=
+#       49 -> dropped; 2: 2.25*225 = 506.25 <= 400? no; keep 2; 5: 729 <= 529?
+#       no, 2.25*9 = 20.25 <= 529 -> dropped; 1: 812.25 <= 576? no, 2.25*16 =
+#       36 <= 576 -> dropped.  F'3 = [4(25), 2(400)]: publish; gained 4 and 2.
+#       (The peers-only reading cannot admit 2, a base node, and keeps 5.)
+#   v4: N(4) = [0(4), 2(225)]; via N(0): 3 (25); via N(2): 5 (324).  Prune
+#       0(4), 3(25), 2(225), 5(324): keep 0; 3: 110.25 <= 25? no; keep 3; 2:
+#       380.25 <= 225? no, 900 <= 225? no; keep 2 (R).  F'4 = [0(4), 3(25),
+#       2(225)]: publish; gained 3.
+#   v5: N(5) = [1, 2, 0]; via N(0): 4 (324), 3 (529).  Prune 1(1), 2(9),
+#       0(256), 4(324), 3(529): 1; 2 (36 <= 9? no); 0 (650.25, 380.25 > 256)
+#       -> R reached, unchanged: no publish, nothing gained.
+#   Offers of the gained edges, by target in ascending source:
+#       2 <- 3(400): N(2) = [5(9), 0(169)] below R -> [5(9), 0(169), 3(400)].
+#       3 <- 4(25): present, no-op.  4 <- 3(25): present, no-op.
+#       (Offering every edge of F'4 would also send 2 <- 4(225), and the
+#       re-prune of {5(9), 0(169), 4(225), 3(400)} drops 4 (2.25*4 <= 225) and
+#       3 (2.25*49 <= 400), leaving N(2) = [5, 0].)
+# Publishes: 6 (base) + 3 own + 3 targets + 2 refined + 1 (N(2)) = 15.
+# ---------------------------------------------------------------------------
+GOLD_REFINE_ALL = os.path.join(os.path.dirname(__file__), "golden", "refine_all_hand.json")
+
+
+def test_hand_derived_refine_pass_all_ids(oracle_mod):
+    g = json.load(open(GOLD_REFINE_ALL))
+    nb, nt = len(g["base_x"]), len(g["batch_x"])
+    X = np.zeros((nb + nt, g["dim"]), np.float32)
+    X[:, 0] = g["base_x"] + g["batch_x"]
+    o = oracle_mod.Oracle(g["dim"], "l2", g["degree"], 100, build_beam=g["build_beam"],
+                          alpha=g["alpha"], refine=g["refine"], max_batch=g["max_batch"],
+                          n_entry=g["n_entry"])
+    for i in range(nb):
+        assert o.insert(X[i:i + 1]).tolist() == [i]
+    _check_lists(o, g["after_base"])
+    assert o.insert(X[nb:]).tolist() == list(range(nb, nb + nt))
+    _check_lists(o, g["after_batch"])
+    assert o.stats()["n_publish"] == g["n_publish"]
+
+
+# ---------------------------------------------------------------------------
 # Hand derivation 3: two deletions sharing a live out-neighbour whose list is
 # at capacity (Algorithm 3), tests/golden/repair_two_deletions_hand.json.
 # R = 2, alpha = 2 (alpha^2 = 4), E = {smallest live id}, refine off, one
