@@ -59,3 +59,29 @@ def test_binding_has_no_cpu_fallback(tmp_path):
 def test_build_targets_sm103a():
     from paper_2607_02543_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets that a
+    C compiler gives the structures of include/etale.h."""
+    from paper_2607_02543_gb300 import binding
+    pairs = [("etale_config", binding.Config), ("etale_tuning", binding.Tuning), ("etale_stats_t", binding.Stats)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "etale.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'    printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    import ctypes
+    for cname, py in pairs:
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
